@@ -1,0 +1,213 @@
+"""One P1-P1 IPCS (ABCN) time step, naive route (CPU, float64).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the CPU
+baseline of the benchmark, never by the product path.
+
+The step follows the naive formulation of Sec. 4 (every form assembled from
+element integrals each step), not the in-place Algorithm 2 of Sec. 5; the two
+are algebraically identical, which is what the GPU parity tests check.
+
+Per step, with d velocity components, inner iterations = 1 (Algorithm 1):
+  ubar   = 1.5 u^{n-1} - 0.5 u^{n-2}                          (Eq. 22)
+  A      = M/dt + C(ubar)/2 + nu K/2                          (Eq. 33, A_ij)
+  b_k    = (M/dt - C/2 - nu K/2) u_k^{n-1} + int f_k phi - G^k p*   (Eqs. 33, 31)
+  rows i in the Dirichlet set: A_i. = e_i, b_k,i = g_k(x_i, t^n)
+  A u_k^I = b_k,  k = 1..d
+  K p = K p* - (1/dt) sum_k G^k u_k^I                         (Eq. 38, pressure)
+      with the right-hand side projected on sum_i b_i = 0 (no pressure BC),
+      p normalised to zero arithmetic mean, phi = p - p*
+  u_k^n = u_k^I - dt (G^k phi)_i / ML_i, Dirichlet rows reset to g  (Eq. 41, lumping)
+
+Readings where the paper is silent or self-contradictory:
+  * Eq. 18 and its weak form carry the opposite sign to Eq. 19; the algebraic
+    pressure equation of Sec. 5 (K P = K P* - ...) is consistent with Eq. 19
+    and is the one used.
+  * Eq. 41 is written with p^{n-1/2}; Eq. 19 and the naive form use phi.  phi
+    is used, since the tentative step already carries -grad p*.
+  * "normalize" is read as subtracting the arithmetic mean of the dof values.
+
+Linear systems are solved exactly (sparse LU, the paper's default direct
+solver) unless ``iterative=True``, in which case Jacobi-preconditioned
+BiCGStab (velocity, as in Sec. 6) and Jacobi-preconditioned CG (pressure) run
+to relative residual ``rtol``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .p1 import Discretization
+
+
+@dataclass
+class State:
+    u_nm1: np.ndarray      # [d, N]
+    u_nm2: np.ndarray      # [d, N]
+    p: np.ndarray          # [N]  (p* of the next step)
+    t: float
+
+
+def replace_rows(A: sp.csr_matrix, rows: np.ndarray) -> sp.csr_matrix:
+    """Return A with every row in ``rows`` replaced by the unit row e_i."""
+    A = A.tolil(copy=True)
+    for i in rows:
+        A.rows[i] = [int(i)]
+        A.data[i] = [1.0]
+    return A.tocsr()
+
+
+def _jacobi(A):
+    dinv = 1.0 / A.diagonal()
+    return spla.LinearOperator(A.shape, matvec=lambda x: dinv * x)
+
+
+class IPCS:
+    def __init__(self, problem, iterative: bool = False, rtol: float = 1e-12,
+                 maxiter: int = 100000):
+        self.pb = problem
+        self.disc = Discretization(problem.mesh)
+        self.iterative = iterative
+        self.rtol = rtol
+        self.maxiter = maxiter
+        D = self.disc
+        self.dirichlet = np.asarray(problem.dirichlet, dtype=np.int64)
+        # int f_k phi_i dx for a constant force
+        self.b0 = np.asarray(problem.f, dtype=np.float64)[:, None] * D.ML[None, :]
+        self.iters = {"u": [], "p": []}
+        # pressure operator with dof 0 pinned: the pinned row is e_0, b_0 = 0
+        self._Kpin_lu = None
+
+    # ------------------------------------------------------------------ pieces
+    def tentative_system(self, u_nm1, u_nm2, p_star, t_new):
+        D, pb = self.disc, self.pb
+        ubar = 1.5 * u_nm1 - 0.5 * u_nm2
+        C = D.convection(ubar)
+        A = D.M / pb.dt + 0.5 * C + 0.5 * pb.nu * D.K
+        E = D.M / pb.dt - 0.5 * C - 0.5 * pb.nu * D.K
+        b = np.stack([E @ u_nm1[k] + self.b0[k] - D.G[k] @ p_star for k in range(D.d)])
+        A = replace_rows(A, self.dirichlet)
+        b[:, self.dirichlet] = pb.g(t_new)
+        return A, b
+
+    def pressure_rhs(self, u_I, p_star):
+        D = self.disc
+        bp = D.K @ p_star - (1.0 / self.pb.dt) * sum(D.G[k] @ u_I[k] for k in range(D.d))
+        return bp - bp.mean()
+
+    def solve_tentative(self, A, b, x0):
+        if not self.iterative:
+            lu = spla.splu(A.tocsc())
+            return np.stack([lu.solve(b[k]) for k in range(b.shape[0])])
+        out = []
+        for k in range(b.shape[0]):
+            x, info = spla.bicgstab(A, b[k], x0=x0[k], rtol=self.rtol, atol=0.0,
+                                    maxiter=self.maxiter, M=_jacobi(A))
+            if info != 0:
+                raise RuntimeError(f"oracle BiCGStab did not converge (info={info})")
+            out.append(x)
+        return np.stack(out)
+
+    def solve_pressure(self, bp, p_star):
+        K = self.disc.K
+        if not self.iterative:
+            if self._Kpin_lu is None:
+                self._Kpin_lu = spla.splu(replace_rows(K, np.array([0])).tocsc())
+            rhs = bp.copy()
+            rhs[0] = 0.0
+            p = self._Kpin_lu.solve(rhs)
+        else:
+            p, info = spla.cg(K, bp, x0=p_star, rtol=self.rtol, atol=0.0,
+                              maxiter=self.maxiter, M=_jacobi(K))
+            if info != 0:
+                raise RuntimeError(f"oracle CG did not converge (info={info})")
+        return p - p.mean()
+
+    # ------------------------------------------------------------------ step
+    def step(self, s: State):
+        pb, D = self.pb, self.disc
+        t_new = s.t + pb.dt
+        A, b = self.tentative_system(s.u_nm1, s.u_nm2, s.p, t_new)
+        u_I = self.solve_tentative(A, b, s.u_nm1)
+        bp = self.pressure_rhs(u_I, s.p)
+        p = self.solve_pressure(bp, s.p)
+        phi = p - s.p
+        u_n = np.stack([u_I[k] - pb.dt * (D.G[k] @ phi) / D.ML for k in range(D.d)])
+        u_n[:, self.dirichlet] = pb.g(t_new)
+        out = State(u_n, s.u_nm1, p, t_new)
+        out.u_I, out.phi, out.bp = u_I, phi, bp
+        return out
+
+    def initial_state(self) -> State:
+        pb = self.pb
+        return State(pb.u_nm1.copy(), pb.u_nm2.copy(), pb.p.copy(), pb.t0)
+
+    def run(self, n_steps: int, state: State | None = None) -> State:
+        s = state if state is not None else self.initial_state()
+        for _ in range(n_steps):
+            s = self.step(s)
+        return s
+
+
+def mass_norm(M: sp.csr_matrix, e: np.ndarray) -> float:
+    """sqrt(sum_k e_k^T M e_k): discrete L2 norm of a nodal field [d, N] or [N]."""
+    e = np.atleast_2d(e)
+    return float(np.sqrt(sum(float(ek @ (M @ ek)) for ek in e)))
+
+
+def mesh_size(coords: np.ndarray, cells: np.ndarray) -> float:
+    """h = 2 x (largest) circumradius over the cells, the convention of Sec. 6.1."""
+    d = coords.shape[1]
+    x = coords[cells]                              # [T, d+1, d]
+    # circumcentre c solves 2 (x_k - x_0) . c = |x_k|^2 - |x_0|^2
+    Amat = 2.0 * (x[:, 1:, :] - x[:, :1, :])
+    rhs = (x[:, 1:, :] ** 2).sum(-1) - (x[:, :1, :] ** 2).sum(-1)
+    c = np.linalg.solve(Amat, rhs[..., None])[..., 0]
+    R = np.linalg.norm(x[:, 0, :] - c, axis=1)
+    del d
+    return float(2.0 * R.max())
+
+
+def convergence_order(E_prev, E, h_prev, h):
+    """k = ln(E_i / E_{i-1}) / ln(h_i / h_{i-1}) (Sec. 6.1)."""
+    return float(np.log(E / E_prev) / np.log(h / h_prev))
+
+
+def triangle_rule(n: int = 6):
+    """Collapsed (Duffy) tensor Gauss-Legendre rule on the reference triangle.
+
+    Points (xi, eta) = (a (1 - b), b) with a, b Gauss points on [0, 1] and the
+    Jacobian (1 - b); with n points per direction it integrates polynomials of
+    total degree 2n - 2 exactly.  Returns barycentric coordinates [Q, 3] and
+    weights [Q] summing to 1/2.
+    """
+    x, w = np.polynomial.legendre.leggauss(n)
+    x = 0.5 * (x + 1.0)
+    w = 0.5 * w
+    A, B = np.meshgrid(x, x, indexing="ij")
+    WA, WB = np.meshgrid(w, w, indexing="ij")
+    xi = (A * (1.0 - B)).ravel()
+    eta = B.ravel()
+    wq = (WA * WB * (1.0 - B)).ravel()
+    lam = np.stack([1.0 - xi - eta, xi, eta], axis=1)
+    return lam, wq
+
+
+def l2_error_2d(mesh, nodal: np.ndarray, exact, n_quad: int = 6) -> float:
+    """sqrt(int_Omega sum_c (u_h,c - u_e,c)^2 dx) on a triangle mesh.
+
+    ``nodal`` is [c, N] (dof values), ``exact(x [Q,2]) -> [c, Q]``; the
+    P1 interpolant u_h is evaluated at quadrature points of every cell.
+    """
+    nodal = np.atleast_2d(nodal)
+    lam, wq = triangle_rule(n_quad)
+    coords, cells = mesh.coords, mesh.cells
+    x = coords[cells]                                     # [T, 3, 2]
+    det = np.abs(np.linalg.det(np.stack([x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]], axis=2)))
+    xq = np.einsum("qv,tvd->tqd", lam, x)                 # [T, Q, 2]
+    cd = mesh.dof_of_vertex[cells]
+    uh = np.einsum("qv,ctv->ctq", lam, nodal[:, cd])      # [c, T, Q]
+    ue = exact(xq.reshape(-1, 2)).reshape(nodal.shape[0], *xq.shape[:2])
+    return float(np.sqrt(((uh - ue) ** 2 * wq[None, None, :] * det[None, :, None]).sum()))

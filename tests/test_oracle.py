@@ -1,0 +1,298 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Nothing here retypes the oracle's formulas: each check comes from an
+independent route (textbook reference-element matrices, quadrature of the
+defining integrals, linear reproduction, dense brute force with Algorithm 2,
+the values printed in Table 1, an exact steady state).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import p1
+from oracle.ipcs import IPCS, State, convergence_order, mesh_size
+from workloads import meshes as WM
+from workloads import problems as WP
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- helpers
+def collapsed_rule(d, n=4):
+    """Tensor Gauss rule collapsed onto the reference simplex (Duffy map)."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    x, w = 0.5 * (x + 1), 0.5 * w
+    if d == 2:
+        a, b = np.meshgrid(x, x, indexing="ij")
+        wa, wb = np.meshgrid(w, w, indexing="ij")
+        pts = np.stack([(a * (1 - b)).ravel(), b.ravel()], 1)
+        wt = (wa * wb * (1 - b)).ravel()
+    else:
+        a, b, c = np.meshgrid(x, x, x, indexing="ij")
+        wa, wb, wc = np.meshgrid(w, w, w, indexing="ij")
+        pts = np.stack([(a * (1 - b) * (1 - c)).ravel(), (b * (1 - c)).ravel(), c.ravel()], 1)
+        wt = (wa * wb * wc * (1 - b) * (1 - c) ** 2).ravel()
+    return pts, wt
+
+
+def plane_coeffs(xv):
+    """Barycentric functions lambda_j(x) = a_j + g_j . x of a simplex from the
+    (d+1)x(d+1) interpolation system [1 x_m] c = e_j (independent of J^{-1})."""
+    d = xv.shape[1]
+    V = np.hstack([np.ones((d + 1, 1)), xv])
+    Cf = np.linalg.solve(V, np.eye(d + 1))          # column j: (a_j, g_j)
+    return Cf[0], Cf[1:].T                           # a [d+1], g [d+1, d]
+
+
+def quad_element(xv, ubar_v):
+    """M, K, G^k, C element matrices of one simplex by quadrature."""
+    d = xv.shape[1]
+    pts, wt = collapsed_rule(d)
+    J = (xv[1:] - xv[0]).T
+    det = abs(np.linalg.det(J))
+    X = xv[0] + pts @ J.T                            # physical quadrature points
+    a, g = plane_coeffs(xv)
+    lam = a[None] + X @ g.T                          # [Q, d+1]
+    ub = lam @ ubar_v                                # ubar at points [Q, d]
+    Me = np.einsum("q,qi,qj->ij", wt, lam, lam) * det
+    Ke = np.einsum("q,ik,jk->ij", wt, g, g) * det
+    Ge = [np.einsum("q,qi,j->ij", wt, lam, g[:, k]) * det for k in range(d)]
+    Ce = np.einsum("q,qk,jk,qi->ij", wt, ub, g, lam) * det
+    return Me, Ke, Ge, Ce
+
+
+# ----------------------------------------------------------------- element level
+def test_reference_triangle_textbook_matrices():
+    xv = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    vol, grads = p1.geometry(xv, np.array([[0, 1, 2]]))
+    M = p1.element_mass(vol, 2)[0]
+    K = p1.element_stiffness(vol, grads)[0]
+    np.testing.assert_allclose(M, np.array([[2, 1, 1], [1, 2, 1], [1, 1, 2]]) / 24.0, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(K, 0.5 * np.array([[2, -1, -1], [-1, 1, 0], [-1, 0, 1]]), atol=1e-15)
+
+
+def test_reference_tet_textbook_matrices():
+    xv = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    vol, grads = p1.geometry(xv, np.array([[0, 1, 2, 3]]))
+    M = p1.element_mass(vol, 3)[0]
+    K = p1.element_stiffness(vol, grads)[0]
+    np.testing.assert_allclose(M, (np.ones((4, 4)) + np.eye(4)) / 120.0, atol=1e-16)
+    Kref = np.array([[3, -1, -1, -1], [-1, 1, 0, 0], [-1, 0, 1, 0], [-1, 0, 0, 1]]) / 6.0
+    np.testing.assert_allclose(K, Kref, atol=1e-15)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_element_matrices_match_quadrature(d):
+    rng = np.random.default_rng(7 + d)
+    for _ in range(20):
+        xv = rng.normal(size=(d + 1, d))
+        ubar_v = rng.normal(size=(d + 1, d))
+        cells = np.arange(d + 1)[None]
+        vol, grads = p1.geometry(xv, cells)
+        Mq, Kq, Gq, Cq = quad_element(xv, ubar_v)
+        np.testing.assert_allclose(p1.element_mass(vol, d)[0], Mq, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(p1.element_stiffness(vol, grads)[0], Kq, rtol=1e-10, atol=1e-12)
+        for k in range(d):
+            np.testing.assert_allclose(p1.element_gradient(vol, grads, k)[0], Gq[k], rtol=1e-10, atol=1e-12)
+        C = p1.element_convection(vol, grads, ubar_v[None])[0]
+        np.testing.assert_allclose(C, Cq, rtol=1e-10, atol=1e-12)
+
+
+# ----------------------------------------------------------------- matrix invariants
+def _meshes():
+    yield "sq", WM.box_mesh_2d(5, 4, 0.0, 1.5, -1.0, 1.0), 3.0
+    yield "cube", WM.box_mesh_3d(3, 4, 2, lo=(0, 0, 0), hi=(1, 2, 0.5)), 1.0
+    m = WM.jitter_interior(WM.box_mesh_3d(4, 4, 4), 0.2, 0.25, seed=4)
+    yield "jitter", m, 1.0
+    y = WP.channel_y(6)
+    yield "stretched", WM.box_mesh_3d(3, 5, 3, lo=(0, -1, 0), hi=(2, 1, 1), y_coords=y), 4.0
+
+
+@pytest.mark.parametrize("name,mesh,volume", list(_meshes()), ids=lambda v: v if isinstance(v, str) else "")
+def test_matrix_invariants(name, mesh, volume):
+    D = p1.Discretization(mesh)
+    X = mesh.dof_coords()
+    one = np.ones(D.N)
+    assert abs(D.M.sum() - volume) < 1e-12 * volume
+    assert abs(D.ML.sum() - volume) < 1e-12 * volume
+    np.testing.assert_allclose(np.asarray(D.M.sum(axis=1)).ravel(), D.ML, rtol=1e-13)
+    for Amat in (D.M, D.K):
+        assert abs(Amat - Amat.T).max() < 1e-14 * abs(Amat).max()
+    np.testing.assert_allclose(D.K @ one, 0, atol=1e-12)
+    interior = np.ones(D.N, bool)
+    interior[mesh.boundary_dofs["all"]] = False
+    rng = np.random.default_rng(1)
+    ubar = rng.normal(size=(D.d, D.N))
+    C = D.convection(ubar)
+    np.testing.assert_allclose(C @ one, 0, atol=1e-12)
+    for k in range(D.d):
+        np.testing.assert_allclose((D.K @ X[:, k])[interior], 0, atol=1e-11)
+        np.testing.assert_allclose(D.G[k] @ one, 0, atol=1e-13)
+        for j in range(D.d):
+            want = D.ML if j == k else 0.0
+            np.testing.assert_allclose(D.G[k] @ X[:, j], want, atol=1e-12)
+        # ubar . grad x_k = ubar_k, so C x_k = int ubar_k phi_i = M ubar_k
+        np.testing.assert_allclose(C @ X[:, k], D.M @ ubar[k], atol=1e-11)
+    # all matrices share the P1 pattern
+    P = D.pattern()
+    for Amat in (D.M, D.K, C, *D.G):
+        assert Amat.nnz == P.nnz and (Amat.indptr == P.indptr).all()
+
+
+def test_periodic_mesh_invariants():
+    m = WM.box_mesh_3d(4, 3, 4, lo=(0, -1, 0), hi=(2, 1, 1), periodic=(True, False, True))
+    D = p1.Discretization(m)
+    assert D.N == 4 * 4 * 4
+    np.testing.assert_allclose(D.M.sum(), 4.0, rtol=1e-13)
+    np.testing.assert_allclose(D.K @ np.ones(D.N), 0, atol=1e-12)
+
+
+# ----------------------------------------------------------------- dense brute force
+def dense_step(pb, state):
+    """One IPCS step by quadrature element integrals, dense algebra and the
+    in-place Algorithm 2 ordering (a second route to the same discrete step)."""
+    m = pb.mesh
+    d, N = m.dim, m.n_dofs
+    Md, Kd = np.zeros((N, N)), np.zeros((N, N))
+    Gd = [np.zeros((N, N)) for _ in range(d)]
+    Cd = np.zeros((N, N))
+    ubar = 1.5 * state.u_nm1 - 0.5 * state.u_nm2
+    for c in m.cells:
+        dofs = m.dof_of_vertex[c]
+        Me, Ke, Ge, Ce = quad_element(m.coords[c], ubar[:, dofs].T)
+        ix = np.ix_(dofs, dofs)
+        np.add.at(Md, ix, Me)
+        np.add.at(Kd, ix, Ke)
+        np.add.at(Cd, ix, Ce)
+        for k in range(d):
+            np.add.at(Gd[k], ix, Ge[k])
+    ML = Md.sum(axis=1)
+    dt, nu = pb.dt, pb.nu
+    t_new = state.t + dt
+    # Algorithm 2
+    A = Cd.copy()
+    A = Md / dt - A / 2 - nu * Kd / 2
+    b = np.stack([pb.f[k] * ML + A @ state.u_nm1[k] - Gd[k] @ state.p for k in range(d)])
+    A = -A + 2 * Md / dt
+    A[pb.dirichlet, :] = 0.0
+    A[pb.dirichlet, pb.dirichlet] = 1.0
+    b[:, pb.dirichlet] = pb.g(t_new)
+    uI = np.stack([np.linalg.solve(A, b[k]) for k in range(d)])
+    bp = Kd @ state.p - sum(Gd[k] @ uI[k] for k in range(d)) / dt
+    bp -= bp.mean()
+    p = np.linalg.lstsq(Kd, bp, rcond=None)[0]          # minimum norm = zero mean
+    phi = p - state.p
+    un = np.stack([uI[k] - dt * (Gd[k] @ phi) / ML for k in range(d)])
+    un[:, pb.dirichlet] = pb.g(t_new)
+    return un, p, uI
+
+
+@pytest.mark.parametrize("kind", ["tg2d", "tg3d", "channel"])
+def test_oracle_step_matches_dense_brute_force(kind):
+    if kind == "tg2d":
+        pb = WP.taylor_green_2d(3)
+    elif kind == "tg3d":
+        pb = WP.taylor_green_3d(3)
+    else:
+        pb = WP.channel(nx=3, ny=4, nz=2, perturb=0.1)
+    o = IPCS(pb)
+    s = o.initial_state()
+    rng = np.random.default_rng(3)
+    s.u_nm2 = s.u_nm2 + 0.05 * rng.normal(size=s.u_nm2.shape)   # make ubar != u^{n-1}
+    s.u_nm2[:, pb.dirichlet] = s.u_nm1[:, pb.dirichlet]
+    for _ in range(2):
+        un, p, uI = dense_step(pb, s)
+        s2 = o.step(s)
+        np.testing.assert_allclose(s2.u_I, uI, rtol=0, atol=1e-11 * np.abs(uI).max())
+        np.testing.assert_allclose(s2.p, p, rtol=0, atol=1e-10 * max(np.abs(p).max(), 1e-3))
+        np.testing.assert_allclose(s2.u_nm1, un, rtol=0, atol=1e-11 * np.abs(un).max())
+        s = s2
+
+
+# ----------------------------------------------------------------- Table 1
+def _table1():
+    rows = []
+    with open(f"{GOLDEN}/table1_p1p1.txt") as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                n, h, eu, ku, ep, kp = line.split()
+                rows.append((int(n), float(h), float(eu), float(ep)))
+    return rows
+
+
+def _rms(e):
+    return float(np.sqrt(np.mean(np.asarray(e) ** 2)))
+
+
+def test_table1_mesh_size_and_order_formula():
+    rows = _table1()
+    for n, h, _, _ in rows:
+        m = WM.box_mesh_2d(n, n, 0, 2, 0, 2)
+        assert abs(mesh_size(m.coords, m.cells) - h) < 0.006 * h
+    # the order column of Table 1 follows from its own h and error columns
+    ku = [convergence_order(rows[i - 1][2], rows[i][2], rows[i - 1][1], rows[i][1]) for i in range(1, 5)]
+    np.testing.assert_allclose(ku, [1.98, 1.98, 1.99, 1.99], atol=0.02)
+
+
+@pytest.mark.parametrize("row", range(5))
+def test_table1_p1p1_values(row):
+    """The oracle reproduces the printed P1P1 errors of Table 1 (Sec. 6.1).
+
+    Readings fixed by this test: the error norm is the root mean square of the
+    nodal errors (over all 2N velocity values), and p is compared with the exact
+    pressure at t - dt/2.
+    """
+    n, h, eu_paper, ep_paper = _table1()[row]
+    pb = WP.taylor_green_2d_periodic(n)
+    s = IPCS(pb).run(1000)
+    x = pb.mesh.dof_coords()
+    eu = _rms(s.u_nm1 - pb.exact_u(x, s.t))
+    pe = pb.exact_p(x, s.t - 0.5 * pb.dt)
+    ep = _rms((s.p - s.p.mean()) - (pe - pe.mean()))
+    assert abs(eu - eu_paper) <= 0.006 * eu_paper, (eu, eu_paper)
+    assert abs(ep - ep_paper) <= 0.01 * ep_paper, (ep, ep_paper)
+
+
+# ----------------------------------------------------------------- scheme-level pins
+def test_unit_square_velocity_second_order():
+    errs, hs = [], []
+    for n in (16, 32, 64):
+        pb = WP.taylor_green_2d(n)
+        s = IPCS(pb).run(100)
+        x = pb.mesh.dof_coords()
+        errs.append(_rms(s.u_nm1 - pb.exact_u(x, s.t)))
+        hs.append(mesh_size(pb.mesh.coords, pb.mesh.cells))
+    for i in (1, 2):
+        k = convergence_order(errs[i - 1], errs[i], hs[i - 1], hs[i])
+        assert 1.8 < k < 2.4, (errs, k)
+
+
+def test_poiseuille_is_a_discrete_steady_state():
+    pb = WP.channel(nx=6, ny=7, nz=4, perturb=0.0)
+    o = IPCS(pb)
+    s0 = o.initial_state()
+    s = o.run(4)
+    assert np.abs(s.u_nm1 - s0.u_nm1).max() < 1e-12 * np.abs(s0.u_nm1).max()
+    assert np.abs(s.p - s.p.mean()).max() < 1e-9
+
+
+def test_iterative_oracle_matches_direct():
+    pb = WP.taylor_green_3d(6)
+    a = IPCS(pb).run(3)
+    b = IPCS(pb, iterative=True, rtol=1e-13).run(3)
+    np.testing.assert_allclose(b.u_nm1, a.u_nm1, atol=1e-10)
+    np.testing.assert_allclose(b.p, a.p, atol=1e-9 * np.abs(a.p).max())
+
+
+def test_workload_sizes():
+    assert WP.taylor_green_2d(32).mesh.n_dofs == 1089
+    m = WM.box_mesh_3d(4, 4, 4)
+    assert m.n_cells == 6 * 64 and m.n_dofs == 125
+    ch = WP.channel(nx=8, ny=6, nz=4)
+    assert ch.mesh.n_dofs == 8 * 6 * 4 and ch.mesh.n_cells == 6 * 8 * 5 * 4
+    st = WP.stress_cube(4, ordering="random")
+    assert st.mesh.n_dofs == 125 and np.all(np.linalg.det(
+        np.stack([st.mesh.coords[st.mesh.cells[:, k + 1]] - st.mesh.coords[st.mesh.cells[:, 0]]
+                  for k in range(3)], 1)) > 0)
+    assert math.isclose(WP.channel_y(96)[0], -1.0) and math.isclose(WP.channel_y(96)[-1], 1.0)
