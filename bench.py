@@ -1,0 +1,348 @@
+"""Benchmark: IPCS steps/s of the GB300 path on a seeded synthetic workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload tg3d_64|tg2d_32|channel|stress128_rcm|stress128_random]
+
+One "step" is one full IPCS time step (assembly + Algorithm 2, d-RHS BiCGStab,
+pressure CG, normalisation, lumped update) on the device, every solve to the
+same relative residual (1e-8).  Default workload: the 3D Taylor-Green vortex on
+[-pi, pi]^3 with 64^3 x 6 tetrahedra (274,625 dofs), mixed precision, the
+three velocity components in one 3-RHS solve, the step captured in one CUDA graph.
+
+Prints one JSON line.  Under torchrun (N > 1) every rank runs an independent
+replica of the workload on its own GPU (the single-GPU method has no exchange
+step); the whole-job value is the steps of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IPCS steps/s at matched residual, mixed+learned vs FP64; SpMV HBM GB/s"
+RTOL = 1e-8
+
+
+def workload(name):
+    from workloads import problems as WP
+    if name == "tg3d_64":
+        return WP.taylor_green_3d(64, n_steps=200, rtol=RTOL)
+    if name == "tg2d_32":
+        return WP.taylor_green_2d(32)
+    if name == "channel":
+        return WP.channel()
+    if name.startswith("stress128"):
+        return WP.stress_cube(128, ordering=name.split("_")[1] if "_" in name else "natural")
+    raise ValueError(name)
+
+
+def workload_config(name, pb, precision):
+    return {"workload": name, "n_dofs": int(pb.mesh.n_dofs), "n_cells": int(pb.mesh.n_cells),
+            "dt": pb.dt, "nu": pb.nu, "rtol": RTOL, "precision": precision,
+            "batch_rhs": True, "cuda_graph": True, "l2": "flushed between steps (256 MiB write)"}
+
+
+# ---------------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------- ours
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_1602_03643_gb300 import build, capi
+    from paper_1602_03643_gb300.driver import IPCSRun
+
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    pb = workload(args.workload)
+    N = pb.mesh.n_dofs
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make(precision, graph=1, guess=capi.OASIS_GUESS_PREV_PHI):
+        return IPCSRun(pb, precision=precision, rtol_u=RTOL, rtol_p=RTOL, max_it_u=5000, max_it_p=200000,
+                       inner_rtol=args.inner_rtol, use_graph=graph, guess=guess, stream=stream)
+
+    def timed_steps(run, k):
+        evs = []
+        stats = []
+        with torch.cuda.stream(stream):
+            for _ in range(k):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                capi.oasis_step(run.solver, stream, want_stats=False)
+                e1.record(stream)
+                evs.append((e0, e1))
+                stats.append(capi.oasis_last_stats(run.solver).as_dict())
+        torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(b) for a, b in evs), stats
+
+    # ---- the headline form: mixed precision + batched + graph (+ previous-phi guess)
+    run = make(capi.OASIS_MIXED)
+    run.set_dirichlet_for_next_step()
+    for _ in range(args.warmup):
+        capi.oasis_step(run.solver, stream, want_stats=False)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with Clocks(local) as clk:
+        ms, stats = timed_steps(run, args.steps)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    bad = [s for s in stats if s["status"] != 0]
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    # ---- e2e: the same step through the public API with host buffers each step
+    g_host = torch.empty((pb.mesh.dim, max(1, len(pb.dirichlet))), dtype=torch.float64).pin_memory()
+    g_host.numpy()[:] = pb.g(0.0) if len(pb.dirichlet) else 0.0
+    u_host = torch.empty((pb.mesh.dim, N), dtype=torch.float64).pin_memory()
+    p_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    k_e2e = max(3, args.steps // 2)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        if len(pb.dirichlet):
+            capi.oasis_set_dirichlet(run.solver, g_host.numpy(), False, stream)
+        capi.oasis_step(run.solver, stream, want_stats=False)
+        capi.oasis_get_fields(run.solver, pb.mesh.dim, N, False, u=u_host.numpy(), p=p_host.numpy(),
+                              phi=None, stream=stream)
+    e2e_s = time.perf_counter() - t0
+    h2d = len(pb.dirichlet) * pb.mesh.dim * 8
+    d2h = (pb.mesh.dim + 1) * N * 8
+
+    # ---- dominant kernel, timed live with CUDA events (eager steps, same solver)
+    run_e = make(capi.OASIS_MIXED, graph=0)
+    run_e.set_dirichlet_for_next_step()
+    capi.oasis_step(run_e.solver, stream, want_stats=False)
+    capi.oasis_profile(run_e.solver, True)
+    for _ in range(2):
+        flush.fill_(1.0)
+        capi.oasis_step(run_e.solver, stream, want_stats=False)
+    torch.cuda.synchronize(dev)
+    fam = {f: capi.oasis_profile_read(run_e.solver, f) for f in capi.PROF_FAMILIES}
+    run_e.close()
+    nnz = run.nnz
+    n_spmv, ms_spmv = fam["pcg_spmv"]
+    # algorithmic bytes of one pressure-CG product q = K p (float32 values, int32 columns):
+    # values + columns (8 nnz) + row pointers (4 N) + z, p_old read, p_new, q written (16 N)
+    spmv_bytes = 8 * nnz + 4 * (N + 1) + 16 * N
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = spmv_bytes / (ms_spmv / max(n_spmv, 1) / 1e3) / 1e9 if n_spmv else None
+    roofline = {"bound": "hbm", "kernel": "k_pcg_q<float,16> (pressure CG, q = K p)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": spmv_bytes, "launches_timed": n_spmv,
+                "avg_launch_us": (ms_spmv / n_spmv * 1e3) if n_spmv else None,
+                "traffic": None,
+                "note": "K + col (33 MB) + vectors stay L2-resident inside the CG loop at this size"}
+    kernel_share = {f: {"launches": n, "ms": m} for f, (n, m) in fam.items()}
+
+    # ---- the plain float64 GPU form at the same residual (comparison)
+    fp64 = None
+    if not args.skip_fp64:
+        run64 = make(capi.OASIS_FP64, guess=capi.OASIS_GUESS_ZERO)
+        run64.set_dirichlet_for_next_step()
+        for _ in range(max(1, args.warmup // 2)):
+            capi.oasis_step(run64.solver, stream, want_stats=False)
+        k64 = max(3, args.steps // 2)
+        ms64, st64 = timed_steps(run64, k64)
+        run64.close()
+        fp64 = {"steps_per_s": k64 / (ms64 / 1e3), "ms_per_step": ms64 / k64,
+                "it_u_mean": float(np.mean([max(s["it_u"]) for s in st64])),
+                "it_p_mean": float(np.mean([s["it_p"] for s in st64]))}
+
+    it_u = float(np.mean([max(s["it_u"]) for s in stats]))
+    it_p = float(np.mean([s["it_p"] for s in stats]))
+    sw_u = float(np.mean([s["sweeps_u"] for s in stats]))
+    sw_p = float(np.mean([s["sweeps_p"] for s in stats]))
+    # kernels per step in the graph: assembly 3, pressure rhs + guess 2, update 1,
+    # 2 per refinement sweep (residual + correction), 5 per BiCGStab and 2 per CG iteration
+    launches = int(round(args.steps * (6 + 2 * (sw_u + sw_p) + 5 * it_u + 2 * it_p)))
+    run.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed: f32 inner Krylov, f64 residual)",
+        "data": "synthetic (seeded Taylor-Green initial field on a Kuhn tetrahedral mesh)",
+        "config": workload_config(args.workload, pb, "mixed") | {"parallelism": f"replicas x{world}"},
+        "e2e": {"value": world * k_e2e / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": roofline,
+        "solver": {"it_u_mean": it_u, "it_p_mean": it_p, "sweeps_u_mean": sw_u, "sweeps_p_mean": sw_p,
+                   "failed_steps": len(bad), "res_p_last": stats[-1]["res_p"]},
+        "fp64_gpu": fp64,
+        "kernel_time_eager_2steps": kernel_share,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, pb, budget_s=args.cpu_budget)
+    return line
+
+
+# ---------------------------------------------------------------------- oracle (CPU)
+def cpu_baseline(args, pb, budget_s=20.0):
+    """The CPU float64 oracle, as it stands, on this host (iterative solves at 1e-8)."""
+    import numpy as np  # noqa: F401
+    from oracle.ipcs import IPCS
+    t0 = time.perf_counter()
+    o = IPCS(pb, iterative=True, rtol=RTOL)
+    setup = time.perf_counter() - t0
+    s = o.initial_state()
+    n = 0
+    t1 = time.perf_counter()
+    while True:
+        s = o.step(s)
+        n += 1
+        if time.perf_counter() - t1 > budget_s or n >= args.steps:
+            break
+    el = time.perf_counter() - t1
+    return {"value": n / el, "unit": "steps/s", "cores": _threads(), "kind": "oracle",
+            "sample": f"{n} full steps of the same workload (float64, scipy BiCGStab/CG + Jacobi at rtol 1e-8, "
+                      f"setup {setup:.1f} s excluded)"}
+
+
+def _threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    pb = workload(args.workload)
+    from oracle.ipcs import IPCS
+    o = IPCS(pb, iterative=True, rtol=RTOL)
+    s = o.initial_state()
+    for _ in range(min(args.warmup, 1)):
+        s = o.step(s)
+    n, t0 = 0, time.perf_counter()
+    while n < args.steps and time.perf_counter() - t0 < args.cpu_budget * 4:
+        s = o.step(s)
+        n += 1
+    el = time.perf_counter() - t0
+    v = n / el
+    cores = _threads()
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world,
+            "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.workload, pb, "fp64 (CPU oracle)"),
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} full steps (iterative float64 oracle, rtol 1e-8)"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tg3d_64")
+    ap.add_argument("--inner-rtol", type=float, default=1e-4)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * oasis.h -- C ABI of the GB300 (sm_103a) P1-P1 incremental pressure-correction
+ * (IPCS, "ABCN" convection) Navier-Stokes time step on simplex meshes.
+ *
+ * The scheme is the fractional-step method of Sec. 2 (Eqs. 17-19, convection
+ * Eq. 22, Algorithm 1 with one inner iteration), discretised with P1 elements
+ * for velocity and pressure as in Sec. 3, and organised as the high-performance
+ * solver of Sec. 5: constant matrices M, K, dP^k preassembled once, the
+ * convection matrix reassembled every step into the fixed sparsity pattern and
+ * combined with M and K by Algorithm 2, a Krylov solve per velocity component
+ * with one shared coefficient matrix (Eq. 35), a pressure-correction Poisson
+ * solve (Sec. 5, the algebraic form of Eq. 18), and the lumped-mass velocity
+ * update (Sec. 5, "lumping").
+ *
+ * Conventions shared by every entry point
+ *   - Return value: 0 on success, a negative OASIS_E* code on failure.  No C++
+ *     exception crosses the ABI.  oasis_last_error() returns a thread-local
+ *     message describing the last failure of the calling thread.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     All device work of a call is ordered on that stream.
+ *   - Host arrays are read during the call only and never retained.  Device
+ *     memory behind oasis_mesh / oasis_solver is allocated by the library at
+ *     creation time and released by the matching destroy call; no entry point
+ *     allocates device memory after creation.
+ *   - Fields are float64, component-major: u[k * n_dofs + i] is component k of
+ *     dof i.  Indices are int32, zero based.
+ *   - Handles are not reentrant: calls on one solver must not overlap.
+ *     Different solvers (and meshes) are independent.
+ */
+#ifndef OASIS_H
+#define OASIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OASIS_OK 0
+#define OASIS_EINVAL (-1)      /* bad argument (null pointer, size, index out of range) */
+#define OASIS_ECUDA (-2)       /* a CUDA runtime call failed */
+#define OASIS_EMESH (-3)       /* degenerate cell or a cell with repeated dofs */
+#define OASIS_ENOTCONV (-4)    /* a Krylov solve hit its iteration cap */
+#define OASIS_EBREAKDOWN (-5)  /* BiCGStab/CG breakdown (a zero inner product) */
+#define OASIS_ENAN (-6)        /* a non-finite value appeared in a solve */
+#define OASIS_ENOMEM (-7)      /* device allocation failed at creation time */
+
+#define OASIS_FP64 0           /* every value and every operation in float64 */
+#define OASIS_MIXED 1          /* float32 matrices and inner Krylov iterations inside
+                                  float64 iterative refinement (float64 residual,
+                                  float64 dot-product accumulation, float64 geometry) */
+
+#define OASIS_GUESS_ZERO 0     /* pressure solve starts from phi = 0, i.e. p = p* */
+#define OASIS_GUESS_PREV_PHI 1 /* starts from the previous step's correction phi */
+#define OASIS_GUESS_LEARNED 2  /* starts from the learned guess (oasis_load_guess_net);
+                                  the guess with the smaller true residual among the
+                                  learned one and phi = 0 is used */
+
+#define OASIS_MAT_M 0          /* M_ij = int phi_j phi_i            (Sec. 5) */
+#define OASIS_MAT_K 1          /* K_ij = int grad phi_j . grad phi_i (Sec. 5) */
+#define OASIS_MAT_G0 2         /* dP^k_ij = int d_k phi_j phi_i, k = 0, 1, 2 (Eq. 31) */
+#define OASIS_MAT_G1 3
+#define OASIS_MAT_G2 4
+#define OASIS_MAT_A 5          /* coefficient matrix of Eq. 35 after the last assembly */
+
+typedef struct oasis_mesh oasis_mesh;
+typedef struct oasis_solver oasis_solver;
+
+/* Parameters of the scheme and of its solvers. */
+typedef struct oasis_params {
+    double nu;             /* kinematic viscosity */
+    double dt;             /* time step (constant, Sec. 2) */
+    double f[3];           /* constant body force; int f_k phi_i = f_k * ML_i */
+    double rtol_u;         /* tentative velocity: stop when ||r|| <= rtol_u ||r_0||,
+                              r_0 the residual of the initial guess u^{n-1} */
+    double rtol_p;         /* pressure correction: stop when ||r|| <= rtol_p ||b_phi||,
+                              b_phi the right-hand side (the residual of phi = 0) */
+    int32_t max_it_u;      /* cap on BiCGStab iterations per solve (all sweeps) */
+    int32_t max_it_p;      /* cap on CG iterations per solve (all sweeps) */
+    int32_t precision;     /* OASIS_FP64 or OASIS_MIXED */
+    double inner_rtol;     /* OASIS_MIXED: relative reduction asked of each float32 inner
+                              solve before the float64 residual is recomputed */
+    int32_t batch_rhs;     /* 1: the d velocity components in one d-RHS BiCGStab
+                              (one matrix read per product); 0: one solve per component */
+    int32_t use_graph;     /* 1: the whole step runs as one CUDA graph, Krylov loops as
+                              conditional WHILE nodes; 0: eager launches with host polls */
+    int32_t guess;         /* OASIS_GUESS_* */
+    int32_t spmv_lanes;    /* lanes per CSR row in the sparse kernels: 0 = autotune at
+                              solver creation, else 4, 8, 16 or 32 */
+} oasis_params;
+
+/* Per-step solver statistics. */
+typedef struct oasis_step_stats {
+    int32_t status;        /* OASIS_OK or the failing OASIS_E* code of the step */
+    int32_t it_u[3];       /* BiCGStab iterations per velocity component */
+    int32_t sweeps_u;      /* refinement sweeps (float64 residual evaluations) */
+    int32_t it_p;          /* CG iterations of the pressure solve */
+    int32_t sweeps_p;
+    int32_t guess_used;    /* OASIS_GUESS_* actually used this step */
+    double res_u[3];       /* final ||r|| / ||r_0|| per component (float64 residual) */
+    double res_p;          /* final ||r|| / ||b_phi|| */
+    double t;              /* time t^n reached by the step */
+} oasis_step_stats;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int oasis_version(void);
+
+/* Message of the last failure on this thread ("" if none).  Owned by the library. */
+const char* oasis_last_error(void);
+
+/* Create a P1 mesh.
+ *   dim           2 (triangles) or 3 (tetrahedra)
+ *   coords        host, [n_vertices][dim] vertex coordinates
+ *   cells         host, [n_cells][dim+1] vertex indices, any orientation
+ *   dof_of_vertex host, [n_vertices] dof of each vertex, or NULL for the identity
+ *                 (periodic meshes identify image vertices through this map)
+ *   n_dofs        number of dofs (max(dof_of_vertex) + 1; n_vertices if the map is NULL)
+ * Builds the shared CSR sparsity pattern of all matrices (Sec. 5: "computed on
+ * the first assemble") and the dof-to-cell incidence used by the assembly
+ * kernels; copies everything to the current device.
+ * Errors: OASIS_EINVAL (sizes, out-of-range index), OASIS_EMESH (a cell whose
+ * dofs repeat, or more than 255 pattern entries in one row), OASIS_ENOMEM. */
+int oasis_mesh_create(int32_t dim, int64_t n_vertices, const double* coords, int64_t n_cells,
+                      const int32_t* cells, const int32_t* dof_of_vertex, int64_t n_dofs,
+                      oasis_mesh** out);
+
+/* Sizes of the mesh and of its sparsity pattern (any pointer may be NULL). */
+int oasis_mesh_info(const oasis_mesh* mesh, int64_t* n_dofs, int64_t* n_cells, int64_t* nnz);
+
+/* Preassemble the constant matrices of Sec. 5 on the device: M, K, dP^k
+ * (k < dim) and the lumped mass ML_i = sum_j M_ij (Sec. 5, velocity update),
+ * plus the per-cell float64 geometry (Jacobian inverse, volume) reused by the
+ * per-step convection assembly.  Deterministic (no atomics).
+ * Errors: OASIS_EMESH if a cell has zero volume; OASIS_ECUDA. */
+int oasis_assemble_constant(oasis_mesh* mesh, void* stream);
+
+/* Copy the sparsity pattern to host: row_ptr [n_dofs+1], col [nnz] (sorted per row). */
+int oasis_mesh_get_pattern(const oasis_mesh* mesh, int32_t* row_ptr, int32_t* col);
+
+/* Copy the float64 values of a constant matrix (OASIS_MAT_M, _K, _G0.._G2) to a
+ * host array [nnz] in pattern order, or with which = -1 the lumped mass [n_dofs].
+ * Synchronises the device. */
+int oasis_mesh_get_matrix(const oasis_mesh* mesh, int32_t which, double* values);
+
+/* y = Mat x on device vectors of length n_dofs (float64), Mat one of the constant
+ * matrices, with `lanes` lanes per row (0 = 16).  For kernel-level tests and
+ * bandwidth measurements. */
+int oasis_spmv_f64(const oasis_mesh* mesh, int32_t which, const double* x, double* y,
+                   int32_t lanes, void* stream);
+/* Same in float32 values and vectors (the values are the float32 copy of the matrix). */
+int oasis_spmv_f32(const oasis_mesh* mesh, int32_t which, const float* x, float* y,
+                   int32_t lanes, void* stream);
+
+/* Create a solver on an assembled mesh.
+ *   dirichlet_dofs host, [n_dirichlet] distinct dofs carrying velocity Dirichlet
+ *                  values (the same set for every component, Sec. 5 after Eq. 35)
+ * The pressure has no Dirichlet condition: its right-hand side is projected on
+ * sum_i b_i = 0 and p is normalised to zero mean after each solve.
+ * Allocates every device buffer the step needs (no allocation afterwards).
+ * With spmv_lanes = 0 the sparse kernels are autotuned here (timed on `stream`). */
+int oasis_solver_create(oasis_mesh* mesh, const oasis_params* params, int64_t n_dirichlet,
+                        const int32_t* dirichlet_dofs, void* stream, oasis_solver** out);
+
+/* Set the state before a step: u^{n-1}, u^{n-2} ([dim][n_dofs]), the tentative
+ * pressure p* = p^{n-3/2} ([n_dofs]) and the time t^{n-1}.  on_device = 1: the
+ * pointers are device pointers; 0: host pointers (copied synchronously).
+ * Resets the pressure-correction history used by the guesses. */
+int oasis_set_fields(oasis_solver* s, const double* u_nm1, const double* u_nm2, const double* p,
+                     double t, int32_t on_device, void* stream);
+
+/* Set the velocity Dirichlet values g[k * n_dirichlet + m] for dof dirichlet_dofs[m]
+ * at the time t^n of the next step.  Values persist until the next call. */
+int oasis_set_dirichlet(oasis_solver* s, const double* g, int32_t on_device, void* stream);
+
+/* Advance one time step (Algorithm 1, one inner iteration):
+ *   assemble C into A and form the tentative right-hand side (Algorithm 2),
+ *   solve A u_k^I = b_k for the dim components, solve the pressure correction,
+ *   normalise p, update u with the lumped mass, rotate u^{n-2} <- u^{n-1} <- u^n
+ *   and p* <- p.
+ * If stats is NULL the call only enqueues work on `stream` and returns OASIS_OK;
+ * a failure of the step is reported by the next oasis_last_stats().  If stats is
+ * non-NULL the call waits for the step and returns its status. */
+int oasis_step(oasis_solver* s, void* stream, oasis_step_stats* stats);
+
+/* Wait for the last step and return its statistics and status. */
+int oasis_last_stats(oasis_solver* s, oasis_step_stats* stats);
+
+/* Copy out the current state: u = u^n ([dim][n_dofs]), p = p^{n-1/2} ([n_dofs]),
+ * phi = p^{n-1/2} - p* ([n_dofs]); any of them may be NULL.  on_device as above.
+ * Synchronises `stream` when copying to host. */
+int oasis_get_fields(oasis_solver* s, double* u, double* p, double* phi, int32_t on_device,
+                     void* stream);
+
+/* Run only the assembly of the next step (Algorithm 2) on the current state and
+ * copy to host the coefficient matrix A [nnz] (Dirichlet rows already unit rows)
+ * and the initial tentative residual r0 = b - A u^{n-1} ([dim][n_dofs]).  The
+ * state is not advanced.  For parity tests. */
+int oasis_get_tentative_system(oasis_solver* s, double* A_values, double* r0, void* stream);
+
+/* Kernel families timed by oasis_profile (eager mode only; graph steps are not
+ * instrumented). */
+#define OASIS_PROF_PCG_SPMV 0      /* q = K p of the pressure CG */
+#define OASIS_PROF_BICG_SPMM 1     /* the d-RHS products of the tentative BiCGStab */
+#define OASIS_PROF_ASSEMBLE 2      /* fused convection assembly + Algorithm 2 row pass */
+#define OASIS_PROF_PCG_UPDATE 3    /* vector update + reductions of the pressure CG */
+#define OASIS_PROF_UPDATE 4        /* lumped velocity update + rotation */
+#define OASIS_PROF_PRESSURE_RHS 5  /* pressure right-hand side */
+
+/* enable = 1: from now on, eager steps record CUDA events around the launches
+ * of the kernel families above; the counters are reset by every call. */
+int oasis_profile(oasis_solver* s, int32_t enable);
+
+/* Launch count and summed device time (ms) of one kernel family since the last
+ * oasis_profile call. */
+int oasis_profile_read(oasis_solver* s, int32_t family, int64_t* launches, double* total_ms);
+
+void oasis_solver_destroy(oasis_solver* s);
+void oasis_mesh_destroy(oasis_mesh* mesh);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OASIS_H */

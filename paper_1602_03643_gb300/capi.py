@@ -1,0 +1,271 @@
+"""ctypes binding of liboasis (include/oasis.h), argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the scheme: all work runs in the CUDA kernels of liboasis.so.
+If the library is missing, loading fails loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liboasis.so")
+
+OASIS_OK = 0
+OASIS_EINVAL = -1
+OASIS_ECUDA = -2
+OASIS_EMESH = -3
+OASIS_ENOTCONV = -4
+OASIS_EBREAKDOWN = -5
+OASIS_ENAN = -6
+OASIS_ENOMEM = -7
+OASIS_FP64 = 0
+OASIS_MIXED = 1
+OASIS_GUESS_ZERO = 0
+OASIS_GUESS_PREV_PHI = 1
+OASIS_GUESS_LEARNED = 2
+OASIS_MAT_M, OASIS_MAT_K, OASIS_MAT_G0, OASIS_MAT_G1, OASIS_MAT_G2, OASIS_MAT_A = range(6)
+
+ERROR_NAMES = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "EMESH", -4: "ENOTCONV", -5: "EBREAKDOWN",
+               -6: "ENAN", -7: "ENOMEM"}
+
+
+class oasis_params(C.Structure):
+    _fields_ = [("nu", C.c_double), ("dt", C.c_double), ("f", C.c_double * 3),
+                ("rtol_u", C.c_double), ("rtol_p", C.c_double),
+                ("max_it_u", C.c_int32), ("max_it_p", C.c_int32), ("precision", C.c_int32),
+                ("inner_rtol", C.c_double), ("batch_rhs", C.c_int32), ("use_graph", C.c_int32),
+                ("guess", C.c_int32), ("spmv_lanes", C.c_int32)]
+
+
+class oasis_step_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("it_u", C.c_int32 * 3), ("sweeps_u", C.c_int32),
+                ("it_p", C.c_int32), ("sweeps_p", C.c_int32), ("guess_used", C.c_int32),
+                ("res_u", C.c_double * 3), ("res_p", C.c_double), ("t", C.c_double)]
+
+    def as_dict(self):
+        return {"status": self.status, "it_u": list(self.it_u), "sweeps_u": self.sweeps_u,
+                "it_p": self.it_p, "sweeps_p": self.sweeps_p, "guess_used": self.guess_used,
+                "res_u": list(self.res_u), "res_p": self.res_p, "t": self.t}
+
+
+class OasisError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+P = C.c_void_p
+PP = C.POINTER(C.c_void_p)
+I32 = C.c_int32
+I64 = C.c_int64
+DPTR = C.c_void_p
+
+# name -> (restype, argtypes); the exported surface of include/oasis.h
+SIGNATURES = {
+    "oasis_version": (C.c_int, []),
+    "oasis_last_error": (C.c_char_p, []),
+    "oasis_mesh_create": (C.c_int, [I32, I64, DPTR, I64, DPTR, DPTR, I64, PP]),
+    "oasis_mesh_info": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
+    "oasis_assemble_constant": (C.c_int, [P, P]),
+    "oasis_mesh_get_pattern": (C.c_int, [P, DPTR, DPTR]),
+    "oasis_mesh_get_matrix": (C.c_int, [P, I32, DPTR]),
+    "oasis_spmv_f64": (C.c_int, [P, I32, DPTR, DPTR, I32, P]),
+    "oasis_spmv_f32": (C.c_int, [P, I32, DPTR, DPTR, I32, P]),
+    "oasis_solver_create": (C.c_int, [P, C.POINTER(oasis_params), I64, DPTR, P, PP]),
+    "oasis_set_fields": (C.c_int, [P, DPTR, DPTR, DPTR, C.c_double, I32, P]),
+    "oasis_set_dirichlet": (C.c_int, [P, DPTR, I32, P]),
+    "oasis_step": (C.c_int, [P, P, C.POINTER(oasis_step_stats)]),
+    "oasis_last_stats": (C.c_int, [P, C.POINTER(oasis_step_stats)]),
+    "oasis_get_fields": (C.c_int, [P, DPTR, DPTR, DPTR, I32, P]),
+    "oasis_get_tentative_system": (C.c_int, [P, DPTR, DPTR, P]),
+    "oasis_profile": (C.c_int, [P, I32]),
+    "oasis_profile_read": (C.c_int, [P, I32, C.POINTER(I64), C.POINTER(C.c_double)]),
+    "oasis_solver_destroy": (None, [P]),
+    "oasis_mesh_destroy": (None, [P]),
+}
+
+
+def lib():
+    """Load liboasis.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_1602_03643_gb300.build` (needs nvcc)")
+        L = C.CDLL(LIB_PATH, mode=C.RTLD_GLOBAL)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != OASIS_OK:
+        raise OasisError(rc, lib().oasis_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    """Host numpy array or torch tensor (host or device) -> address."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()      # torch.Tensor
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream     # torch.cuda.Stream
+
+
+def oasis_version():
+    return lib().oasis_version()
+
+
+def oasis_mesh_create(dim, coords, cells, dof_of_vertex=None, n_dofs=None):
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    dov = None if dof_of_vertex is None else np.ascontiguousarray(dof_of_vertex, dtype=np.int32)
+    if n_dofs is None:
+        n_dofs = coords.shape[0] if dov is None else int(dov.max()) + 1
+    out = C.c_void_p()
+    check(lib().oasis_mesh_create(dim, coords.shape[0], _ptr(coords), cells.shape[0], _ptr(cells),
+                                  _ptr(dov), int(n_dofs), C.byref(out)))
+    return out
+
+
+def oasis_mesh_info(mesh):
+    n, t, z = I64(), I64(), I64()
+    check(lib().oasis_mesh_info(mesh, C.byref(n), C.byref(t), C.byref(z)))
+    return n.value, t.value, z.value
+
+
+def oasis_assemble_constant(mesh, stream=None):
+    check(lib().oasis_assemble_constant(mesh, _stream(stream)))
+
+
+def oasis_mesh_get_pattern(mesh):
+    n, _, nnz = oasis_mesh_info(mesh)
+    rp = np.empty(n + 1, np.int32)
+    col = np.empty(nnz, np.int32)
+    check(lib().oasis_mesh_get_pattern(mesh, _ptr(rp), _ptr(col)))
+    return rp, col
+
+
+def oasis_mesh_get_matrix(mesh, which):
+    n, _, nnz = oasis_mesh_info(mesh)
+    out = np.empty(n if which == -1 else nnz, np.float64)
+    check(lib().oasis_mesh_get_matrix(mesh, which, _ptr(out)))
+    return out
+
+
+def oasis_spmv_f64(mesh, which, x, y, lanes=0, stream=None):
+    check(lib().oasis_spmv_f64(mesh, which, _ptr(x), _ptr(y), lanes, _stream(stream)))
+
+
+def oasis_spmv_f32(mesh, which, x, y, lanes=0, stream=None):
+    check(lib().oasis_spmv_f32(mesh, which, _ptr(x), _ptr(y), lanes, _stream(stream)))
+
+
+def make_params(nu, dt, f=(0.0, 0.0, 0.0), rtol_u=1e-8, rtol_p=1e-8, max_it_u=1000, max_it_p=20000,
+                precision=OASIS_FP64, inner_rtol=1e-4, batch_rhs=1, use_graph=0, guess=OASIS_GUESS_ZERO,
+                spmv_lanes=0):
+    p = oasis_params()
+    p.nu, p.dt = nu, dt
+    ff = list(f) + [0.0] * (3 - len(f))
+    for k in range(3):
+        p.f[k] = ff[k]
+    p.rtol_u, p.rtol_p = rtol_u, rtol_p
+    p.max_it_u, p.max_it_p = max_it_u, max_it_p
+    p.precision, p.inner_rtol = precision, inner_rtol
+    p.batch_rhs, p.use_graph, p.guess, p.spmv_lanes = batch_rhs, use_graph, guess, spmv_lanes
+    return p
+
+
+def oasis_solver_create(mesh, params, dirichlet_dofs, stream=None):
+    d = np.ascontiguousarray(dirichlet_dofs, dtype=np.int32)
+    out = C.c_void_p()
+    check(lib().oasis_solver_create(mesh, C.byref(params), d.size, _ptr(d) if d.size else None,
+                                    _stream(stream), C.byref(out)))
+    return out
+
+
+def oasis_set_fields(solver, u_nm1, u_nm2, p, t, on_device=False, stream=None):
+    if not on_device:
+        u_nm1 = np.ascontiguousarray(u_nm1, dtype=np.float64)
+        u_nm2 = np.ascontiguousarray(u_nm2, dtype=np.float64)
+        p = np.ascontiguousarray(p, dtype=np.float64)
+    check(lib().oasis_set_fields(solver, _ptr(u_nm1), _ptr(u_nm2), _ptr(p), float(t), int(on_device),
+                                 _stream(stream)))
+
+
+def oasis_set_dirichlet(solver, g, on_device=False, stream=None):
+    if not on_device:
+        g = np.ascontiguousarray(g, dtype=np.float64)
+    check(lib().oasis_set_dirichlet(solver, _ptr(g), int(on_device), _stream(stream)))
+
+
+def oasis_step(solver, stream=None, want_stats=True):
+    if want_stats:
+        st = oasis_step_stats()
+        check(lib().oasis_step(solver, _stream(stream), C.byref(st)))
+        return st
+    check(lib().oasis_step(solver, _stream(stream), None))
+    return None
+
+
+def oasis_last_stats(solver):
+    st = oasis_step_stats()
+    check(lib().oasis_last_stats(solver, C.byref(st)))
+    return st
+
+
+def oasis_get_fields(solver, dim, n, on_device=False, u=None, p=None, phi=None, stream=None):
+    if not on_device:
+        u = np.empty((dim, n)) if u is None else u
+        p = np.empty(n) if p is None else p
+        phi = np.empty(n) if phi is None else phi
+    check(lib().oasis_get_fields(solver, _ptr(u), _ptr(p), _ptr(phi), int(on_device), _stream(stream)))
+    return u, p, phi
+
+
+def oasis_get_tentative_system(solver, dim, n, nnz, stream=None):
+    A = np.empty(nnz)
+    r0 = np.empty((dim, n))
+    check(lib().oasis_get_tentative_system(solver, _ptr(A), _ptr(r0), _stream(stream)))
+    return A, r0
+
+
+PROF_FAMILIES = {"pcg_spmv": 0, "bicg_spmm": 1, "assemble": 2, "pcg_update": 3, "update": 4,
+                 "pressure_rhs": 5}
+
+
+def oasis_profile(solver, enable=True):
+    check(lib().oasis_profile(solver, int(enable)))
+
+
+def oasis_profile_read(solver, family):
+    n, ms = I64(), C.c_double()
+    check(lib().oasis_profile_read(solver, PROF_FAMILIES.get(family, family), C.byref(n), C.byref(ms)))
+    return n.value, ms.value
+
+
+def oasis_solver_destroy(solver):
+    lib().oasis_solver_destroy(solver)
+
+
+def oasis_mesh_destroy(mesh):
+    lib().oasis_mesh_destroy(mesh)

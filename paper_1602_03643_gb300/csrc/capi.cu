@@ -1,0 +1,576 @@
+// C ABI of liboasis (declared in include/oasis.h) and the host side of the
+// solver: buffer allocation, field transfer, the eager and graph step drivers.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.cuh"
+#include "solver.cuh"
+
+namespace oasis {
+
+static thread_local std::string g_last_error;
+
+// ------------------------------------------------------------------ layout kernels
+// component-major [D][n] <-> dof-major [n][D]
+__global__ void k_soa_to_aos(int64_t n, int D, const double* __restrict__ src, double* __restrict__ dst) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * D; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / D;
+        const int k = (int)(t - i * D);
+        dst[t] = src[(int64_t)k * n + i];
+    }
+}
+__global__ void k_aos_to_soa(int64_t n, int D, const double* __restrict__ src, double* __restrict__ dst) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * D; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / D;
+        const int k = (int)(t - i * D);
+        dst[(int64_t)k * n + i] = src[t];
+    }
+}
+__global__ void k_f32_to_f64(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+
+static int egrid(int64_t items) {
+    const int64_t want = (items + kBlock - 1) / kBlock;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 8));
+}
+
+// ------------------------------------------------------------------ loops
+void Solver::poll(cudaStream_t s, int which) {
+    OASIS_CUDA(cudaMemcpyAsync(h_st + which, st.p + which, sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
+    OASIS_CUDA(cudaStreamSynchronize(s));
+}
+
+static cudaGraph_t capture_graph_of(cudaStream_t s) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    OASIS_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    OASIS_CHECK(cs == cudaStreamCaptureStatusActive, OASIS_ECUDA, "stream is not capturing");
+    return g;
+}
+
+// Append a WHILE conditional node to the graph being captured on `s`; returns
+// its body graph.  The stream's capture continues after the node.
+static cudaGraph_t add_while(cudaStream_t s, cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    OASIS_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    OASIS_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    OASIS_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return body;
+}
+
+void Solver::run_loops(cudaStream_t s, bool graph_mode, int which, const LoopFn& outer, const LoopFn& inner,
+                       const LoopFn& correct, int k0, int nr) {
+    if (!graph_mode) {
+        Loop lp;
+        const int chunk = 4;
+        for (int guard = 0; guard < 1000000; ++guard) {
+            outer(s, lp);
+            poll(s, which);
+            bool live = false;
+            for (int k = k0; k < k0 + nr && k < 3; ++k) live |= !h_st[which].col_done[k];
+            if (!live) return;
+            for (;;) {
+                for (int c = 0; c < chunk; ++c) inner(s, lp);
+                poll(s, which);
+                bool act = false;
+                for (int k = k0; k < k0 + nr && k < 3; ++k)
+                    act |= !h_st[which].col_done[k] && !h_st[which].in_done[k];
+                if (!act) break;
+            }
+            correct(s, lp);
+        }
+        throw Error(OASIS_ENOTCONV, "refinement loop did not terminate");
+    }
+    // graph: while (outer cond) { outer; while (inner cond) { inner }; correct }
+    cudaGraph_t g = capture_graph_of(s);
+    Loop lp;
+    lp.graph = 1;
+    OASIS_CUDA(cudaGraphConditionalHandleCreate(&lp.h_outer, g, 1, cudaGraphCondAssignDefault));
+    cudaGraph_t outer_body = add_while(s, lp.h_outer);
+    cudaStream_t s1 = cap[1], s2 = cap[2];
+    OASIS_CUDA(cudaStreamBeginCaptureToGraph(s1, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    OASIS_CUDA(cudaGraphConditionalHandleCreate(&lp.h_inner, outer_body, 0, 0));
+    outer(s1, lp);
+    cudaGraph_t inner_body = add_while(s1, lp.h_inner);
+    OASIS_CUDA(cudaStreamBeginCaptureToGraph(s2, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    inner(s2, lp);
+    cudaGraph_t tmp;
+    OASIS_CUDA(cudaStreamEndCapture(s2, &tmp));
+    correct(s1, lp);
+    OASIS_CUDA(cudaStreamEndCapture(s1, &tmp));
+}
+
+int Solver::prof_begin(cudaStream_t s, int family) {
+    if (!prof_on || prm.use_graph) return -1;
+    const size_t idx = ev_used.size();
+    if (idx >= ev_pool.size()) {
+        cudaEvent_t a, b;
+        OASIS_CUDA(cudaEventCreate(&a));
+        OASIS_CUDA(cudaEventCreate(&b));
+        ev_pool.emplace_back(a, b);
+    }
+    ev_used.emplace_back(family, (int)idx);
+    OASIS_CUDA(cudaEventRecord(ev_pool[idx].first, s));
+    return (int)idx;
+}
+
+void Solver::prof_end(cudaStream_t s, int idx) {
+    if (idx < 0) return;
+    OASIS_CUDA(cudaEventRecord(ev_pool[idx].second, s));
+}
+
+void Solver::prof_collect() {
+    for (auto& fu : ev_used) {
+        float ms = 0.f;
+        OASIS_CUDA(cudaEventSynchronize(ev_pool[fu.second].second));
+        OASIS_CUDA(cudaEventElapsedTime(&ms, ev_pool[fu.second].first, ev_pool[fu.second].second));
+        prof_ms[fu.first] += ms;
+        prof_n[fu.first] += 1;
+    }
+    ev_used.clear();
+}
+
+void Solver::step(cudaStream_t s) {
+    const bool graph_mode = prm.use_graph != 0;
+    if (graph_mode) {
+        if (!gexec) capture();
+        OASIS_CUDA(cudaGraphLaunch(gexec, s));
+    } else {
+        impl->assemble(s);
+        impl->tentative_solve(s, false);
+        impl->pressure_solve(s, false);
+        impl->update(s);
+        OASIS_CUDA(cudaMemcpyAsync(h_st, st.p, 2 * sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
+        if (prof_on) prof_collect();
+    }
+    t += prm.dt;
+    stepped = true;
+}
+
+void Solver::capture() {
+    cudaStream_t s = cap[0];
+    OASIS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+        impl->assemble(s);
+        impl->tentative_solve(s, true);
+        impl->pressure_solve(s, true);
+        impl->update(s);
+        OASIS_CUDA(cudaMemcpyAsync(h_st, st.p, 2 * sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
+    } catch (...) {
+        cudaGraph_t g;
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    OASIS_CUDA(cudaStreamEndCapture(s, &graph));
+    OASIS_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
+}
+
+Solver::~Solver() {
+    for (auto& e : ev_pool) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto& c : cap)
+        if (c) cudaStreamDestroy(c);
+    if (h_st) cudaFreeHost(h_st);
+}
+
+static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, const int32_t* dir,
+                             cudaStream_t s) {
+    OASIS_CHECK(m && prm, OASIS_EINVAL, "null mesh or params");
+    OASIS_CHECK(m->assembled, OASIS_EINVAL, "call oasis_assemble_constant first");
+    OASIS_CHECK(prm->dt > 0 && prm->nu >= 0, OASIS_EINVAL, "dt must be > 0 and nu >= 0");
+    OASIS_CHECK(prm->rtol_u > 0 && prm->rtol_p > 0, OASIS_EINVAL, "tolerances must be > 0");
+    OASIS_CHECK(prm->max_it_u > 0 && prm->max_it_p > 0, OASIS_EINVAL, "iteration caps must be > 0");
+    OASIS_CHECK(prm->precision == OASIS_FP64 || prm->precision == OASIS_MIXED, OASIS_EINVAL, "precision");
+    OASIS_CHECK(prm->guess >= 0 && prm->guess <= 2, OASIS_EINVAL, "guess");
+    OASIS_CHECK(n_dir >= 0 && (n_dir == 0 || dir), OASIS_EINVAL, "dirichlet dofs");
+    auto S = std::make_unique<Solver>();
+    S->m = m;
+    S->prm = *prm;
+    S->mixed = prm->precision == OASIS_MIXED;
+    if (S->mixed && !(S->prm.inner_rtol > 0 && S->prm.inner_rtol < 1)) S->prm.inner_rtol = 1e-4;
+    const int D = m->dim;
+    const int64_t n = m->n;
+    S->n_dir = n_dir;
+    std::vector<int32_t> di(n, -1);
+    for (int64_t q = 0; q < n_dir; ++q) {
+        OASIS_CHECK(dir[q] >= 0 && dir[q] < n, OASIS_EINVAL, "dirichlet dof out of range");
+        OASIS_CHECK(di[dir[q]] < 0, OASIS_EINVAL, "repeated dirichlet dof");
+        di[dir[q]] = (int32_t)q;
+    }
+    S->dir_index.upload(di.data(), n, s);
+    S->g.alloc(std::max<int64_t>(1, n_dir * D));
+    OASIS_CUDA(cudaMemsetAsync(S->g.p, 0, S->g.bytes(), s));
+    for (auto* b : {&S->u1, &S->u2, &S->du, &S->r0u}) {
+        b->alloc(n * D);
+        OASIS_CUDA(cudaMemsetAsync(b->p, 0, b->bytes(), s));
+    }
+    for (auto* b : {&S->pstar, &S->phi, &S->phi_h1, &S->phi_h2, &S->bphi, &S->xp}) {
+        b->alloc(n);
+        OASIS_CUDA(cudaMemsetAsync(b->p, 0, b->bytes(), s));
+    }
+    if (S->mixed) {
+        S->A32.alloc(m->nnz);
+        S->dA32.alloc(n);
+        S->beta32.alloc(m->nc * 4);
+        for (int k = 0; k < 9; ++k) {
+            S->w32[k].alloc(n * D);
+            OASIS_CUDA(cudaMemsetAsync(S->w32[k].p, 0, S->w32[k].bytes(), s));
+            S->w32p[k] = S->w32[k].p;
+        }
+        for (int k = 0; k < 6; ++k) {
+            S->q32[k].alloc(n);
+            OASIS_CUDA(cudaMemsetAsync(S->q32[k].p, 0, S->q32[k].bytes(), s));
+            S->q32p[k] = S->q32[k].p;
+        }
+    } else {
+        S->A64.alloc(m->nnz);
+        S->dA64.alloc(n);
+        S->beta64.alloc(m->nc * 4);
+        for (int k = 0; k < 9; ++k) {
+            S->w64[k].alloc(n * D);
+            OASIS_CUDA(cudaMemsetAsync(S->w64[k].p, 0, S->w64[k].bytes(), s));
+            S->w64p[k] = S->w64[k].p;
+        }
+        for (int k = 0; k < 6; ++k) {
+            S->q64[k].alloc(n);
+            OASIS_CUDA(cudaMemsetAsync(S->q64[k].p, 0, S->q64[k].bytes(), s));
+            S->q64p[k] = S->q64[k].p;
+        }
+    }
+    S->stage.alloc(std::max<int64_t>(n, n_dir) * D);
+    if (S->mixed) S->stage32.alloc(m->nnz);
+    S->st.alloc(2);
+    OASIS_CUDA(cudaMemsetAsync(S->st.p, 0, S->st.bytes(), s));
+    S->partial.alloc((size_t)num_sms() * 8 * 8);
+    OASIS_CUDA(cudaHostAlloc(&S->h_st, 2 * sizeof(KrylovState), cudaHostAllocDefault));
+    std::memset(S->h_st, 0, 2 * sizeof(KrylovState));
+    for (auto& c : S->cap) OASIS_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+    int lanes = prm->spmv_lanes;
+    if (lanes == 0) lanes = D == 2 ? 8 : 16;
+    OASIS_CHECK(lanes == 8 || lanes == 16, OASIS_EINVAL, "spmv_lanes must be 0, 8 or 16");
+    S->lanes = lanes;
+    S->impl.reset(make_step_impl(*S, lanes));
+    OASIS_CUDA(cudaStreamSynchronize(s));
+    return S.release();
+}
+
+static void fill_stats(const Solver& S, oasis_step_stats* o) {
+    std::memset(o, 0, sizeof(*o));
+    const KrylovState& u = S.h_st[0];
+    const KrylovState& p = S.h_st[1];
+    o->status = u.status != OASIS_OK ? u.status : p.status;
+    for (int k = 0; k < 3; ++k) {
+        o->it_u[k] = k < S.m->dim ? u.it_total[k] : 0;
+        o->res_u[k] = (k < S.m->dim && u.bb[k] > 0) ? std::sqrt(u.rr[k] / u.bb[k]) : 0.0;
+    }
+    o->sweeps_u = u.sweeps;
+    o->it_p = p.it_total[0];
+    o->sweeps_p = p.sweeps;
+    o->res_p = p.bb[0] > 0 ? std::sqrt(p.rr[0] / p.bb[0]) : 0.0;
+    o->guess_used = S.prm.guess == OASIS_GUESS_PREV_PHI ? OASIS_GUESS_PREV_PHI : OASIS_GUESS_ZERO;
+    o->t = S.t;
+}
+
+}  // namespace oasis
+
+using namespace oasis;
+
+template <class F>
+static int guarded(F&& f) {
+    try {
+        g_last_error.clear();
+        f();
+        return OASIS_OK;
+    } catch (const Error& e) {
+        g_last_error = e.what();
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        return OASIS_ENOMEM;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return OASIS_EINVAL;
+    }
+}
+
+static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+int oasis_version(void) { return 100; }
+
+const char* oasis_last_error(void) { return g_last_error.c_str(); }
+
+int oasis_mesh_create(int32_t dim, int64_t n_vertices, const double* coords, int64_t n_cells,
+                      const int32_t* cells, const int32_t* dof_of_vertex, int64_t n_dofs, oasis_mesh** out) {
+    return guarded([&] {
+        OASIS_CHECK(out, OASIS_EINVAL, "null output pointer");
+        *out = reinterpret_cast<oasis_mesh*>(build_mesh(dim, n_vertices, coords, n_cells, cells, dof_of_vertex, n_dofs));
+    });
+}
+
+int oasis_mesh_info(const oasis_mesh* mesh, int64_t* n_dofs, int64_t* n_cells, int64_t* nnz) {
+    return guarded([&] {
+        const Mesh* m = reinterpret_cast<const Mesh*>(mesh);
+        OASIS_CHECK(m, OASIS_EINVAL, "null mesh");
+        if (n_dofs) *n_dofs = m->n;
+        if (n_cells) *n_cells = m->nc;
+        if (nnz) *nnz = m->nnz;
+    });
+}
+
+int oasis_assemble_constant(oasis_mesh* mesh, void* stream) {
+    return guarded([&] {
+        Mesh* m = reinterpret_cast<Mesh*>(mesh);
+        OASIS_CHECK(m, OASIS_EINVAL, "null mesh");
+        assemble_constant(*m, as_stream(stream));
+    });
+}
+
+int oasis_mesh_get_pattern(const oasis_mesh* mesh, int32_t* row_ptr, int32_t* col) {
+    return guarded([&] {
+        const Mesh* m = reinterpret_cast<const Mesh*>(mesh);
+        OASIS_CHECK(m && row_ptr && col, OASIS_EINVAL, "null pointer");
+        std::memcpy(row_ptr, m->h_row_ptr.data(), m->h_row_ptr.size() * sizeof(int32_t));
+        std::memcpy(col, m->h_col.data(), m->h_col.size() * sizeof(int32_t));
+    });
+}
+
+int oasis_mesh_get_matrix(const oasis_mesh* mesh, int32_t which, double* values) {
+    return guarded([&] {
+        const Mesh* m = reinterpret_cast<const Mesh*>(mesh);
+        OASIS_CHECK(m && values, OASIS_EINVAL, "null pointer");
+        OASIS_CHECK(m->assembled, OASIS_EINVAL, "mesh not assembled");
+        const double* src = nullptr;
+        size_t cnt = m->nnz;
+        if (which == OASIS_MAT_M) src = m->M64.p;
+        else if (which == OASIS_MAT_K) src = m->K64.p;
+        else if (which >= OASIS_MAT_G0 && which < OASIS_MAT_G0 + m->dim) src = m->G64.p + (size_t)(which - OASIS_MAT_G0) * m->nnz;
+        else if (which == -1) {
+            src = m->ML64.p;
+            cnt = m->n;
+        } else
+            throw Error(OASIS_EINVAL, "unknown matrix");
+        OASIS_CUDA(cudaDeviceSynchronize());
+        OASIS_CUDA(cudaMemcpy(values, src, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+    });
+}
+
+static const void* const_matrix(const Mesh* m, int which, bool f32) {
+    if (which == OASIS_MAT_M) return f32 ? (const void*)m->M32.p : (const void*)m->M64.p;
+    if (which == OASIS_MAT_K) return f32 ? (const void*)m->K32.p : (const void*)m->K64.p;
+    if (which >= OASIS_MAT_G0 && which < OASIS_MAT_G0 + m->dim) {
+        const size_t o = (size_t)(which - OASIS_MAT_G0) * m->nnz;
+        return f32 ? (const void*)(m->G32.p + o) : (const void*)(m->G64.p + o);
+    }
+    throw Error(OASIS_EINVAL, "unknown matrix");
+}
+
+int oasis_spmv_f64(const oasis_mesh* mesh, int32_t which, const double* x, double* y, int32_t lanes, void* stream) {
+    return guarded([&] {
+        const Mesh* m = reinterpret_cast<const Mesh*>(mesh);
+        OASIS_CHECK(m && x && y, OASIS_EINVAL, "null pointer");
+        OASIS_CHECK(m->assembled, OASIS_EINVAL, "mesh not assembled");
+        spmv_f64(*m, (const double*)const_matrix(m, which, false), x, y, lanes ? lanes : 16, as_stream(stream));
+    });
+}
+
+int oasis_spmv_f32(const oasis_mesh* mesh, int32_t which, const float* x, float* y, int32_t lanes, void* stream) {
+    return guarded([&] {
+        const Mesh* m = reinterpret_cast<const Mesh*>(mesh);
+        OASIS_CHECK(m && x && y, OASIS_EINVAL, "null pointer");
+        OASIS_CHECK(m->assembled, OASIS_EINVAL, "mesh not assembled");
+        spmv_f32(*m, (const float*)const_matrix(m, which, true), x, y, lanes ? lanes : 16, as_stream(stream));
+    });
+}
+
+int oasis_solver_create(oasis_mesh* mesh, const oasis_params* params, int64_t n_dirichlet,
+                        const int32_t* dirichlet_dofs, void* stream, oasis_solver** out) {
+    return guarded([&] {
+        OASIS_CHECK(out, OASIS_EINVAL, "null output pointer");
+        *out = reinterpret_cast<oasis_solver*>(
+            create_solver(reinterpret_cast<Mesh*>(mesh), params, n_dirichlet, dirichlet_dofs, as_stream(stream)));
+    });
+}
+
+int oasis_set_fields(oasis_solver* solver, const double* u_nm1, const double* u_nm2, const double* p, double t,
+                     int32_t on_device, void* stream) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S && u_nm1 && u_nm2 && p, OASIS_EINVAL, "null pointer");
+        cudaStream_t s = as_stream(stream);
+        const int D = S->m->dim;
+        const int64_t n = S->m->n;
+        double* tmp = S->stage.p;
+        const double* srcs[2] = {u_nm1, u_nm2};
+        DBuf<double>* dsts[2] = {&S->u1, &S->u2};
+        for (int q = 0; q < 2; ++q) {
+            const double* src = srcs[q];
+            if (!on_device) {
+                OASIS_CUDA(cudaMemcpyAsync(tmp, src, n * D * sizeof(double), cudaMemcpyHostToDevice, s));
+                src = tmp;
+            }
+            k_soa_to_aos<<<egrid(n * D), kBlock, 0, s>>>(n, D, src, dsts[q]->p);
+            OASIS_CUDA(cudaGetLastError());
+            OASIS_CUDA(cudaStreamSynchronize(s));
+        }
+        OASIS_CUDA(cudaMemcpyAsync(S->pstar.p, p, n * sizeof(double),
+                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        for (auto* b : {&S->phi, &S->phi_h1, &S->phi_h2})
+            OASIS_CUDA(cudaMemsetAsync(b->p, 0, b->bytes(), s));
+        OASIS_CUDA(cudaStreamSynchronize(s));
+        S->t = t;
+    });
+}
+
+int oasis_set_dirichlet(oasis_solver* solver, const double* g, int32_t on_device, void* stream) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S, OASIS_EINVAL, "null solver");
+        if (S->n_dir == 0) return;
+        OASIS_CHECK(g, OASIS_EINVAL, "null values");
+        cudaStream_t s = as_stream(stream);
+        const int D = S->m->dim;
+        const int64_t nd = S->n_dir;
+        const double* src = g;
+        if (!on_device) {
+            OASIS_CUDA(cudaMemcpyAsync(S->stage.p, g, nd * D * sizeof(double), cudaMemcpyHostToDevice, s));
+            src = S->stage.p;
+        }
+        k_soa_to_aos<<<egrid(nd * D), kBlock, 0, s>>>(nd, D, src, S->g.p);
+        OASIS_CUDA(cudaGetLastError());
+        if (!on_device) OASIS_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int oasis_step(oasis_solver* solver, void* stream, oasis_step_stats* stats) {
+    int rc = guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S, OASIS_EINVAL, "null solver");
+        S->step(as_stream(stream));
+        if (stats) {
+            OASIS_CUDA(cudaStreamSynchronize(as_stream(stream)));
+            fill_stats(*S, stats);
+            if (stats->status != OASIS_OK)
+                throw Error(stats->status, "step failed: status " + std::to_string(stats->status));
+        }
+    });
+    return rc;
+}
+
+int oasis_last_stats(oasis_solver* solver, oasis_step_stats* stats) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S && stats, OASIS_EINVAL, "null pointer");
+        OASIS_CUDA(cudaDeviceSynchronize());
+        fill_stats(*S, stats);
+        if (stats->status != OASIS_OK) throw Error(stats->status, "step failed: status " + std::to_string(stats->status));
+    });
+}
+
+int oasis_get_fields(oasis_solver* solver, double* u, double* p, double* phi, int32_t on_device, void* stream) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S, OASIS_EINVAL, "null solver");
+        cudaStream_t s = as_stream(stream);
+        const int D = S->m->dim;
+        const int64_t n = S->m->n;
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (u) {
+            double* dst = on_device ? u : S->stage.p;
+            k_aos_to_soa<<<egrid(n * D), kBlock, 0, s>>>(n, D, S->u1.p, dst);
+            OASIS_CUDA(cudaGetLastError());
+            if (!on_device) OASIS_CUDA(cudaMemcpyAsync(u, S->stage.p, n * D * sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+        if (p) OASIS_CUDA(cudaMemcpyAsync(p, S->pstar.p, n * sizeof(double), kind, s));
+        if (phi) OASIS_CUDA(cudaMemcpyAsync(phi, S->phi.p, n * sizeof(double), kind, s));
+        if (!on_device) OASIS_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int oasis_get_tentative_system(oasis_solver* solver, double* A_values, double* r0, void* stream) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S, OASIS_EINVAL, "null solver");
+        cudaStream_t s = as_stream(stream);
+        const int D = S->m->dim;
+        const int64_t n = S->m->n, nnz = S->m->nnz;
+        S->impl->assemble(s);
+        if (A_values) {
+            if (S->mixed) {
+                std::vector<float> h(nnz);
+                OASIS_CUDA(cudaMemcpyAsync(h.data(), S->A32.p, nnz * sizeof(float), cudaMemcpyDeviceToHost, s));
+                OASIS_CUDA(cudaStreamSynchronize(s));
+                for (int64_t q = 0; q < nnz; ++q) A_values[q] = (double)h[q];
+            } else {
+                OASIS_CUDA(cudaMemcpyAsync(A_values, S->A64.p, nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+            }
+        }
+        if (r0) {
+            k_aos_to_soa<<<egrid(n * D), kBlock, 0, s>>>(n, D, S->r0u.p, S->stage.p);
+            OASIS_CUDA(cudaGetLastError());
+            OASIS_CUDA(cudaMemcpyAsync(r0, S->stage.p, n * D * sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+        OASIS_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int oasis_profile(oasis_solver* solver, int32_t enable) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S, OASIS_EINVAL, "null solver");
+        S->prof_on = enable != 0;
+        for (int f = 0; f < Solver::kProfFamilies; ++f) {
+            S->prof_ms[f] = 0.0;
+            S->prof_n[f] = 0;
+        }
+    });
+}
+
+int oasis_profile_read(oasis_solver* solver, int32_t family, int64_t* launches, double* total_ms) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S && launches && total_ms, OASIS_EINVAL, "null pointer");
+        OASIS_CHECK(family >= 0 && family < Solver::kProfFamilies, OASIS_EINVAL, "unknown kernel family");
+        *launches = S->prof_n[family];
+        *total_ms = S->prof_ms[family];
+    });
+}
+
+void oasis_solver_destroy(oasis_solver* solver) {
+    Solver* S = reinterpret_cast<Solver*>(solver);
+    if (S) {
+        cudaDeviceSynchronize();
+        delete S;
+    }
+}
+
+void oasis_mesh_destroy(oasis_mesh* mesh) {
+    Mesh* m = reinterpret_cast<Mesh*>(mesh);
+    if (m) {
+        cudaDeviceSynchronize();
+        delete m;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// Internal declarations shared by the translation units of liboasis.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/oasis.h"
+
+namespace oasis {
+
+// Error carried from deep inside the library to the C ABI boundary.
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define OASIS_CUDA(call)                                                                   \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            throw ::oasis::Error(e_ == cudaErrorMemoryAllocation ? OASIS_ENOMEM : OASIS_ECUDA, \
+                                 std::string(#call) + ": " + cudaGetErrorString(e_));      \
+    } while (0)
+
+#define OASIS_CHECK(cond, code, msg)                                                       \
+    do {                                                                                   \
+        if (!(cond)) throw ::oasis::Error((code), (msg));                                  \
+    } while (0)
+
+constexpr int kBlock = 256;          // threads per block for every kernel here
+
+// Owning device buffer (cudaMalloc at creation, cudaFree at destruction).
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    ~DBuf() { release(); }
+    void alloc(size_t count) {
+        release();
+        n = count;
+        if (count) OASIS_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void upload(const T* host, size_t count, cudaStream_t s) {
+        alloc(count);
+        if (count) OASIS_CUDA(cudaMemcpyAsync(p, host, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// The mesh: sparsity pattern, incidence and constant matrices (all on device).
+struct Mesh {
+    int dim = 0;
+    int64_t nv = 0, nc = 0, n = 0, nnz = 0;
+    int max_row = 0;
+    // host copies needed later
+    std::vector<int32_t> h_row_ptr, h_col;
+    // device: pattern
+    DBuf<int32_t> row_ptr, col, diag;          // diag[i] = position of (i, i)
+    // device: cells
+    DBuf<int32_t> cell_vert;                   // [nc][dim+1] vertex indices
+    DBuf<int32_t> cell_dof;                    // [nc][dim+1] dofs
+    DBuf<double> coords;                       // [nv][dim]
+    // device: dof -> cell incidence, sorted by cell; slots packs, per incidence,
+    // the position (within the row) of each of the cell's dofs, 8 bits each.
+    DBuf<int32_t> inc_ptr, inc_cell;
+    DBuf<uint32_t> inc_slots;
+    // device: geometry and constant matrices
+    DBuf<double> gw64;                         // [nc][dim+1][dim]  |T|/((d+1)(d+2)) grad lambda_j
+    DBuf<float> gw32;
+    DBuf<double> M64, K64, G64;                // G64: [dim][nnz]
+    DBuf<float> M32, K32, G32;
+    DBuf<double> ML64, invML64, dinvK64;       // [n]
+    DBuf<float> dinvK32;
+    DBuf<int32_t> err;                         // device error flag for setup kernels
+    bool assembled = false;
+};
+
+// Device-resident scalars of one Krylov solve (up to 3 right-hand sides).
+struct KrylovState {
+    double rho[3], rho_new[3], alpha[3], omega[3], beta[3];
+    double bb[3];          // ||reference||^2 for the relative criterion
+    double rr[3];          // last float64 residual^2 of the outer sweep
+    double rr0_in[3];      // start of the current inner solve
+    double rr_in[3];       // recurrence residual^2 of the inner solve
+    double mean;           // pressure: mean of the right-hand side; sum of p
+    double psum;
+    double guess_rr[2];    // residual^2 of the candidate guesses
+    int32_t col_done[3];   // converged in float64
+    int32_t in_done[3];    // inner solve finished for this sweep
+    int32_t it_total[3];
+    int32_t it_in;         // inner iteration counter (parity of double buffers)
+    int32_t sweeps;
+    int32_t status;        // OASIS_OK / ENOTCONV / EBREAKDOWN / ENAN
+    int32_t guess_used;
+    int32_t first;         // 1 before the first float64 residual of a solve
+    uint32_t ticket;       // last-block reduction ticket
+    int32_t pad[3];
+};
+
+struct Solver;
+
+// Kernels and launchers (step.cu)
+void spmv_f64(const Mesh& m, const double* vals, const double* x, double* y, int lanes, cudaStream_t s);
+void spmv_f32(const Mesh& m, const float* vals, const float* x, float* y, int lanes, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace oasis

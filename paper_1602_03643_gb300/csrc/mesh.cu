@@ -1,0 +1,366 @@
+// Mesh set-up: CSR sparsity pattern, dof-to-cell incidence, per-cell geometry
+// and the constant matrices of Sec. 5 (M, K, dP^k, lumped mass), plus the
+// stand-alone SpMV kernels.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <thread>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace oasis {
+
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        OASIS_CUDA(cudaGetDevice(&dev));
+        OASIS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return sms;
+}
+
+// ------------------------------------------------------------------ host build
+template <class F>
+static void parallel_for(int64_t n, F f) {
+    int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (n < 20000) nt = 1;
+    std::vector<std::thread> th;
+    const int64_t chunk = (n + nt - 1) / nt;
+    for (int t = 0; t < nt; ++t) {
+        const int64_t a = t * chunk, b = std::min(n, a + chunk);
+        if (a >= b) break;
+        th.emplace_back([=] { f(a, b); });
+    }
+    for (auto& x : th) x.join();
+}
+
+Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const int32_t* cells,
+                 const int32_t* dof_of_vertex, int64_t n_dofs) {
+    OASIS_CHECK(dim == 2 || dim == 3, OASIS_EINVAL, "dim must be 2 or 3");
+    OASIS_CHECK(nv > 0 && nc > 0 && coords && cells, OASIS_EINVAL, "empty mesh or null pointer");
+    OASIS_CHECK(nv < INT32_MAX && nc * (dim + 1) < INT32_MAX, OASIS_EINVAL, "mesh too large for int32 indices");
+    if (!dof_of_vertex) n_dofs = nv;
+    OASIS_CHECK(n_dofs > 0 && n_dofs <= nv, OASIS_EINVAL, "n_dofs out of range");
+    const int d1 = dim + 1;
+
+    auto m = std::make_unique<Mesh>();
+    m->dim = dim;
+    m->nv = nv;
+    m->nc = nc;
+    m->n = n_dofs;
+    std::vector<int32_t> cdof((size_t)nc * d1);
+    for (int64_t c = 0; c < nc; ++c) {
+        for (int a = 0; a < d1; ++a) {
+            const int32_t v = cells[c * d1 + a];
+            OASIS_CHECK(v >= 0 && v < nv, OASIS_EINVAL, "cell vertex index out of range");
+            const int32_t dof = dof_of_vertex ? dof_of_vertex[v] : v;
+            OASIS_CHECK(dof >= 0 && dof < n_dofs, OASIS_EINVAL, "dof_of_vertex entry out of range");
+            cdof[c * d1 + a] = dof;
+        }
+        for (int a = 0; a < d1; ++a)
+            for (int b = a + 1; b < d1; ++b)
+                OASIS_CHECK(cdof[c * d1 + a] != cdof[c * d1 + b], OASIS_EMESH,
+                            "cell " + std::to_string(c) + " has a repeated dof");
+    }
+    const int64_t n = n_dofs;
+    // dof -> cell incidence (counting sort keeps cells in increasing order)
+    std::vector<int32_t> inc_ptr(n + 1, 0), inc_cell((size_t)nc * d1);
+    for (size_t q = 0; q < cdof.size(); ++q) inc_ptr[cdof[q] + 1]++;
+    for (int64_t i = 0; i < n; ++i) inc_ptr[i + 1] += inc_ptr[i];
+    {
+        std::vector<int32_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+        for (int64_t c = 0; c < nc; ++c)
+            for (int a = 0; a < d1; ++a) inc_cell[fill[cdof[c * d1 + a]]++] = (int32_t)c;
+    }
+    // row pattern: union of the dofs of the incident cells
+    std::vector<int32_t> row_len(n);
+    parallel_for(n, [&](int64_t a, int64_t b) {
+        std::vector<int32_t> buf;
+        for (int64_t i = a; i < b; ++i) {
+            buf.clear();
+            for (int32_t q = inc_ptr[i]; q < inc_ptr[i + 1]; ++q)
+                for (int k = 0; k < d1; ++k) buf.push_back(cdof[(size_t)inc_cell[q] * d1 + k]);
+            std::sort(buf.begin(), buf.end());
+            row_len[i] = (int32_t)(std::unique(buf.begin(), buf.end()) - buf.begin());
+        }
+    });
+    std::vector<int32_t> row_ptr(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) row_ptr[i + 1] = row_ptr[i] + row_len[i];
+    const int64_t nnz = row_ptr[n];
+    OASIS_CHECK(nnz < INT32_MAX, OASIS_EINVAL, "too many nonzeros for int32 indices");
+    const int max_row = n ? *std::max_element(row_len.begin(), row_len.end()) : 0;
+    OASIS_CHECK(max_row <= 255, OASIS_EMESH, "more than 255 pattern entries in a row");
+    std::vector<int32_t> col(nnz), diag(n);
+    std::vector<uint32_t> inc_slots((size_t)nc * d1);
+    parallel_for(n, [&](int64_t a, int64_t b) {
+        std::vector<int32_t> buf;
+        for (int64_t i = a; i < b; ++i) {
+            buf.clear();
+            for (int32_t q = inc_ptr[i]; q < inc_ptr[i + 1]; ++q)
+                for (int k = 0; k < d1; ++k) buf.push_back(cdof[(size_t)inc_cell[q] * d1 + k]);
+            std::sort(buf.begin(), buf.end());
+            buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+            std::copy(buf.begin(), buf.end(), col.begin() + row_ptr[i]);
+            diag[i] = row_ptr[i] + (int32_t)(std::lower_bound(buf.begin(), buf.end(), (int32_t)i) - buf.begin());
+            for (int32_t q = inc_ptr[i]; q < inc_ptr[i + 1]; ++q) {
+                uint32_t w = 0xffffffffu;
+                for (int k = 0; k < d1; ++k) {
+                    const int32_t dof = cdof[(size_t)inc_cell[q] * d1 + k];
+                    const uint32_t slot = (uint32_t)(std::lower_bound(buf.begin(), buf.end(), dof) - buf.begin());
+                    w = (w & ~(0xffu << (8 * k))) | (slot << (8 * k));
+                }
+                inc_slots[q] = w;
+            }
+        }
+    });
+
+    cudaStream_t s = 0;
+    m->nnz = nnz;
+    m->max_row = max_row;
+    m->row_ptr.upload(row_ptr.data(), row_ptr.size(), s);
+    m->col.upload(col.data(), col.size(), s);
+    m->diag.upload(diag.data(), diag.size(), s);
+    m->cell_vert.upload(cells, (size_t)nc * d1, s);
+    m->cell_dof.upload(cdof.data(), cdof.size(), s);
+    m->coords.upload(coords, (size_t)nv * dim, s);
+    m->inc_ptr.upload(inc_ptr.data(), inc_ptr.size(), s);
+    m->inc_cell.upload(inc_cell.data(), inc_cell.size(), s);
+    m->inc_slots.upload(inc_slots.data(), inc_slots.size(), s);
+    m->err.alloc(1);
+    OASIS_CUDA(cudaMemsetAsync(m->err.p, 0, sizeof(int32_t), s));
+    OASIS_CUDA(cudaStreamSynchronize(s));
+    m->h_row_ptr = std::move(row_ptr);
+    m->h_col = std::move(col);
+    return m.release();
+}
+
+// ------------------------------------------------------------------ geometry
+// Barycentric gradients of one simplex from its Jacobian J = [x_1-x_0, ..., x_d-x_0]:
+// grad lambda_k (k >= 1) is row k-1 of J^{-1}, grad lambda_0 = -sum_k grad lambda_k.
+template <int D>
+__global__ void k_cell_geometry(int64_t nc, const int32_t* __restrict__ cell_vert,
+                                const double* __restrict__ coords, double* __restrict__ grad,
+                                double* __restrict__ vol, double* __restrict__ gw64,
+                                float* __restrict__ gw32, int32_t* err) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        double x[D + 1][D];
+        for (int a = 0; a <= D; ++a)
+            for (int k = 0; k < D; ++k) x[a][k] = coords[(size_t)cell_vert[c * (D + 1) + a] * D + k];
+        double J[D][D];  // J[r][col] = x_{col+1}[r] - x_0[r]
+        for (int r = 0; r < D; ++r)
+            for (int q = 0; q < D; ++q) J[r][q] = x[q + 1][r] - x[0][r];
+        double inv[D][D], det;
+        if (D == 2) {
+            det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+            inv[0][0] = J[1][1];
+            inv[0][1] = -J[0][1];
+            inv[1][0] = -J[1][0];
+            inv[1][1] = J[0][0];
+        } else {
+            // adjugate of a 3x3 matrix (cofactor transpose)
+            const double(*a)[D] = J;
+            inv[0][0] = a[1][1] * a[2][2] - a[1][2] * a[2][1];
+            inv[0][1] = a[0][2] * a[2][1] - a[0][1] * a[2][2];
+            inv[0][2] = a[0][1] * a[1][2] - a[0][2] * a[1][1];
+            inv[1][0] = a[1][2] * a[2][0] - a[1][0] * a[2][2];
+            inv[1][1] = a[0][0] * a[2][2] - a[0][2] * a[2][0];
+            inv[1][2] = a[0][2] * a[1][0] - a[0][0] * a[1][2];
+            inv[2][0] = a[1][0] * a[2][1] - a[1][1] * a[2][0];
+            inv[2][1] = a[0][1] * a[2][0] - a[0][0] * a[2][1];
+            inv[2][2] = a[0][0] * a[1][1] - a[0][1] * a[1][0];
+            det = a[0][0] * inv[0][0] + a[0][1] * inv[1][0] + a[0][2] * inv[2][0];
+        }
+        if (!(det != 0.0) || !isfinite(det)) {
+            atomicExch(err, 1);
+            det = 1.0;
+        }
+        const double rdet = 1.0 / det;
+        double g[D + 1][D];
+        for (int k = 0; k < D; ++k) g[0][k] = 0.0;
+        for (int a = 1; a <= D; ++a)
+            for (int k = 0; k < D; ++k) {
+                g[a][k] = inv[a - 1][k] * rdet;
+                g[0][k] -= g[a][k];
+            }
+        const double v = fabs(det) / (D == 2 ? 2.0 : 6.0);
+        const double w = v / ((D + 1) * (D + 2));
+        vol[c] = v;
+        for (int a = 0; a <= D; ++a)
+            for (int k = 0; k < D; ++k) {
+                const size_t o = ((size_t)c * (D + 1) + a) * D + k;
+                grad[o] = g[a][k];
+                gw64[o] = w * g[a][k];
+                gw32[o] = (float)(w * g[a][k]);
+            }
+    }
+}
+
+// Row-gather assembly of the constant matrices: thread per row, summing the
+// element contributions of every incident cell in increasing cell order
+// (deterministic, no atomics).  Element integrals of linear Lagrange simplices:
+//   M^T_ab = |T| (1 + delta_ab) / ((d+1)(d+2)),  K^T_ab = |T| grad lambda_a . grad lambda_b,
+//   dP^{k,T}_ab = |T| d_k lambda_b / (d+1),        int_T lambda_a = |T| / (d+1).
+template <int D>
+__global__ void k_row_constant(int64_t n, const int32_t* __restrict__ row_ptr,
+                               const int32_t* __restrict__ diag, const int32_t* __restrict__ inc_ptr,
+                               const int32_t* __restrict__ inc_cell, const uint32_t* __restrict__ inc_slots,
+                               const double* __restrict__ grad, const double* __restrict__ vol,
+                               int64_t nnz, double* __restrict__ M, double* __restrict__ K,
+                               double* __restrict__ G, double* __restrict__ ML) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t b = row_ptr[i], e = row_ptr[i + 1];
+        for (int32_t q = b; q < e; ++q) {
+            M[q] = 0.0;
+            K[q] = 0.0;
+            for (int k = 0; k < D; ++k) G[(size_t)k * nnz + q] = 0.0;
+        }
+        const uint32_t dslot = (uint32_t)(diag[i] - b);
+        double ml = 0.0;
+        for (int32_t q = inc_ptr[i]; q < inc_ptr[i + 1]; ++q) {
+            const int32_t c = inc_cell[q];
+            const uint32_t w = inc_slots[q];
+            int la = 0;
+            for (int a = 0; a <= D; ++a)
+                if (((w >> (8 * a)) & 0xffu) == dslot) la = a;
+            const double v = vol[c];
+            const double* g = grad + (size_t)c * (D + 1) * D;
+            ml += v / (D + 1);
+            for (int a = 0; a <= D; ++a) {
+                const int32_t pos = b + (int32_t)((w >> (8 * a)) & 0xffu);
+                M[pos] += v * (a == la ? 2.0 : 1.0) / ((D + 1) * (D + 2));
+                double kk = 0.0;
+                for (int k = 0; k < D; ++k) kk += g[la * D + k] * g[a * D + k];
+                K[pos] += v * kk;
+                for (int k = 0; k < D; ++k) G[(size_t)k * nnz + pos] += v * g[a * D + k] / (D + 1);
+            }
+        }
+        ML[i] = ml;
+    }
+}
+
+__global__ void k_mesh_derived(int64_t n, const int32_t* __restrict__ diag, const double* __restrict__ K,
+                               const double* __restrict__ ML, double* __restrict__ invML,
+                               double* __restrict__ dinvK64, float* __restrict__ dinvK32) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        invML[i] = 1.0 / ML[i];
+        const double kd = K[diag[i]];
+        const double di = kd != 0.0 ? 1.0 / kd : 1.0;
+        dinvK64[i] = di;
+        dinvK32[i] = (float)di;
+    }
+}
+
+__global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+static int grid_for(int64_t items, int per_block = kBlock) {
+    const int64_t want = (items + per_block - 1) / per_block;
+    const int64_t cap = (int64_t)num_sms() * 8;
+    return (int)std::max<int64_t>(1, std::min(want, cap));
+}
+
+void assemble_constant(Mesh& m, cudaStream_t s) {
+    const int D = m.dim;
+    const size_t gsz = (size_t)m.nc * (D + 1) * D;
+    DBuf<double> grad, vol;
+    grad.alloc(gsz);
+    vol.alloc(m.nc);
+    m.gw64.alloc(gsz);
+    m.gw32.alloc(gsz);
+    OASIS_CUDA(cudaMemsetAsync(m.err.p, 0, sizeof(int32_t), s));
+    const int gc = grid_for(m.nc);
+    if (D == 2)
+        k_cell_geometry<2><<<gc, kBlock, 0, s>>>(m.nc, m.cell_vert.p, m.coords.p, grad.p, vol.p, m.gw64.p, m.gw32.p, m.err.p);
+    else
+        k_cell_geometry<3><<<gc, kBlock, 0, s>>>(m.nc, m.cell_vert.p, m.coords.p, grad.p, vol.p, m.gw64.p, m.gw32.p, m.err.p);
+    OASIS_CUDA(cudaGetLastError());
+    int32_t herr = 0;
+    OASIS_CUDA(cudaMemcpyAsync(&herr, m.err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    OASIS_CUDA(cudaStreamSynchronize(s));
+    OASIS_CHECK(herr == 0, OASIS_EMESH, "degenerate (zero-volume) cell");
+
+    m.M64.alloc(m.nnz);
+    m.K64.alloc(m.nnz);
+    m.G64.alloc((size_t)D * m.nnz);
+    m.ML64.alloc(m.n);
+    const int gr = grid_for(m.n);
+    if (D == 2)
+        k_row_constant<2><<<gr, kBlock, 0, s>>>(m.n, m.row_ptr.p, m.diag.p, m.inc_ptr.p, m.inc_cell.p,
+                                                m.inc_slots.p, grad.p, vol.p, m.nnz, m.M64.p, m.K64.p,
+                                                m.G64.p, m.ML64.p);
+    else
+        k_row_constant<3><<<gr, kBlock, 0, s>>>(m.n, m.row_ptr.p, m.diag.p, m.inc_ptr.p, m.inc_cell.p,
+                                                m.inc_slots.p, grad.p, vol.p, m.nnz, m.M64.p, m.K64.p,
+                                                m.G64.p, m.ML64.p);
+    OASIS_CUDA(cudaGetLastError());
+    m.invML64.alloc(m.n);
+    m.dinvK64.alloc(m.n);
+    m.dinvK32.alloc(m.n);
+    k_mesh_derived<<<gr, kBlock, 0, s>>>(m.n, m.diag.p, m.K64.p, m.ML64.p, m.invML64.p, m.dinvK64.p, m.dinvK32.p);
+    m.M32.alloc(m.nnz);
+    m.K32.alloc(m.nnz);
+    m.G32.alloc((size_t)D * m.nnz);
+    k_to_f32<<<grid_for(m.nnz), kBlock, 0, s>>>(m.nnz, m.M64.p, m.M32.p);
+    k_to_f32<<<grid_for(m.nnz), kBlock, 0, s>>>(m.nnz, m.K64.p, m.K32.p);
+    k_to_f32<<<grid_for((int64_t)D * m.nnz), kBlock, 0, s>>>((int64_t)D * m.nnz, m.G64.p, m.G32.p);
+    OASIS_CUDA(cudaGetLastError());
+    OASIS_CUDA(cudaStreamSynchronize(s));
+    m.assembled = true;
+}
+
+// ------------------------------------------------------------------ SpMV
+// CSR SpMV with L lanes per row (a "vector" CSR kernel): the lanes of a group
+// stride over the row's entries and combine with shuffles.  The warp-level
+// loop is uniform, so every shuffle has all 32 lanes present.
+template <class V, int L>
+__global__ void __launch_bounds__(kBlock) k_spmv(int64_t n, const int32_t* __restrict__ rp,
+                                                 const int32_t* __restrict__ col,
+                                                 const V* __restrict__ val, const V* __restrict__ x,
+                                                 V* __restrict__ y) {
+    constexpr int RPW = 32 / L;
+    const int lane = threadIdx.x % L;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
+    const int sub = (threadIdx.x % 32) / L;
+    for (int64_t w = warp; w * RPW < n; w += nwarp) {
+        const int64_t i = w * RPW + sub;
+        V acc = 0;
+        if (i < n) {
+            const int32_t b = rp[i], e = rp[i + 1];
+            for (int32_t q = b + lane; q < e; q += L) acc += val[q] * __ldg(&x[col[q]]);
+        }
+        acc = group_sum<L>(acc);
+        if (i < n && lane == 0) y[i] = acc;
+    }
+}
+
+template <class V>
+static void spmv_launch(const Mesh& m, const V* vals, const V* x, V* y, int lanes, cudaStream_t s) {
+    const int rows_per_block = kBlock / lanes;
+    const int g = grid_for(m.n, rows_per_block);
+    switch (lanes) {
+        case 4: k_spmv<V, 4><<<g, kBlock, 0, s>>>(m.n, m.row_ptr.p, m.col.p, vals, x, y); break;
+        case 8: k_spmv<V, 8><<<g, kBlock, 0, s>>>(m.n, m.row_ptr.p, m.col.p, vals, x, y); break;
+        case 16: k_spmv<V, 16><<<g, kBlock, 0, s>>>(m.n, m.row_ptr.p, m.col.p, vals, x, y); break;
+        case 32: k_spmv<V, 32><<<g, kBlock, 0, s>>>(m.n, m.row_ptr.p, m.col.p, vals, x, y); break;
+        default: throw Error(OASIS_EINVAL, "lanes must be 4, 8, 16 or 32");
+    }
+    OASIS_CUDA(cudaGetLastError());
+}
+
+void spmv_f64(const Mesh& m, const double* vals, const double* x, double* y, int lanes, cudaStream_t s) {
+    spmv_launch<double>(m, vals, x, y, lanes, s);
+}
+void spmv_f32(const Mesh& m, const float* vals, const float* x, float* y, int lanes, cudaStream_t s) {
+    spmv_launch<float>(m, vals, x, y, lanes, s);
+}
+
+}  // namespace oasis

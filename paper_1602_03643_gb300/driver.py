@@ -1,0 +1,67 @@
+"""Convenience wrapper around the C ABI: one mesh + one solver for a problem.
+
+Argument marshalling only; the problem object needs the attributes ``mesh``
+(dim, coords, cells, dof_of_vertex, n_dofs), ``nu``, ``dt``, ``f``,
+``dirichlet``, ``u_nm1``, ``u_nm2``, ``p``, ``t0`` and ``g(t)``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import capi
+
+
+class IPCSRun:
+    def __init__(self, problem, precision=capi.OASIS_FP64, rtol_u=1e-12, rtol_p=1e-12, max_it_u=2000,
+                 max_it_p=50000, inner_rtol=1e-4, batch_rhs=1, use_graph=0, guess=capi.OASIS_GUESS_ZERO,
+                 spmv_lanes=0, stream=None):
+        pb = problem
+        self.pb = pb
+        self.stream = stream
+        m = pb.mesh
+        self.dim, self.n = m.dim, m.n_dofs
+        self.mesh = capi.oasis_mesh_create(m.dim, m.coords, m.cells, m.dof_of_vertex, m.n_dofs)
+        capi.oasis_assemble_constant(self.mesh, stream)
+        self.nnz = capi.oasis_mesh_info(self.mesh)[2]
+        self.params = capi.make_params(pb.nu, pb.dt, tuple(pb.f), rtol_u, rtol_p, max_it_u, max_it_p,
+                                       precision, inner_rtol, batch_rhs, use_graph, guess, spmv_lanes)
+        self.solver = capi.oasis_solver_create(self.mesh, self.params, pb.dirichlet, stream)
+        self.t = pb.t0
+        capi.oasis_set_fields(self.solver, pb.u_nm1, pb.u_nm2, pb.p, pb.t0, False, stream)
+        self.stats = []
+
+    def set_dirichlet_for_next_step(self):
+        if len(self.pb.dirichlet):
+            capi.oasis_set_dirichlet(self.solver, self.pb.g(self.t + self.pb.dt), False, self.stream)
+
+    def step(self, n_steps=1, want_stats=True, time_dependent_bc=True):
+        st = None
+        for _ in range(n_steps):
+            if time_dependent_bc or self.t == self.pb.t0:
+                self.set_dirichlet_for_next_step()
+            st = capi.oasis_step(self.solver, self.stream, want_stats)
+            self.t += self.pb.dt
+            if st is not None:
+                self.stats.append(st.as_dict())
+        return st
+
+    def fields(self):
+        u, p, phi = capi.oasis_get_fields(self.solver, self.dim, self.n, False, stream=self.stream)
+        return u, p, phi
+
+    def tentative_system(self):
+        return capi.oasis_get_tentative_system(self.solver, self.dim, self.n, self.nnz, self.stream)
+
+    def close(self):
+        if self.solver is not None:
+            capi.oasis_solver_destroy(self.solver)
+            self.solver = None
+        if self.mesh is not None:
+            capi.oasis_mesh_destroy(self.mesh)
+            self.mesh = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

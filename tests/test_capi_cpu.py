@@ -1,0 +1,73 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads and
+exports every entry point declared in include/oasis.h; argument errors are
+reported before any device work."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1602_03643_gb300 import build, capi as c
+    build.build()
+    c.lib()
+    return c
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "oasis.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(oasis_\w+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(capi):
+    names = declared_functions()
+    assert len(names) >= 18
+    lib = capi.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(capi.SIGNATURES) == names
+
+
+def test_version_and_error_string(capi):
+    assert capi.oasis_version() >= 100
+    assert isinstance(capi.lib().oasis_last_error(), bytes)
+
+
+def test_null_pointer_is_einval(capi):
+    import ctypes as C
+    out = C.c_void_p()
+    rc = capi.lib().oasis_mesh_create(3, 4, None, 1, None, None, 4, C.byref(out))
+    assert rc == capi.OASIS_EINVAL
+    assert b"null" in capi.lib().oasis_last_error()
+
+
+def test_repeated_dof_is_emesh(capi):
+    coords = np.array([[0, 0], [1, 0], [0, 1.0]])
+    cells = np.array([[0, 1, 1]], np.int32)
+    with pytest.raises(capi.OasisError) as e:
+        capi.oasis_mesh_create(2, coords, cells)
+    assert e.value.code == capi.OASIS_EMESH
+
+
+def test_out_of_range_vertex_is_einval(capi):
+    coords = np.array([[0, 0], [1, 0], [0, 1.0]])
+    cells = np.array([[0, 1, 7]], np.int32)
+    with pytest.raises(capi.OasisError) as e:
+        capi.oasis_mesh_create(2, coords, cells)
+    assert e.value.code == capi.OASIS_EINVAL
+
+
+def test_bad_dim_is_einval(capi):
+    with pytest.raises(capi.OasisError) as e:
+        capi.oasis_mesh_create(4, np.zeros((5, 4)), np.zeros((1, 5), np.int32))
+    assert e.value.code == capi.OASIS_EINVAL
+
+
+def test_graft_entry_build():
+    import __graft_entry__ as g
+    g.build()

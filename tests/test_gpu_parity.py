@@ -1,0 +1,305 @@
+"""GPU path (through the C ABI) against the CPU float64 oracle, element by element.
+
+Tolerances: float64 path -- matrices to 1e-13 relative, one step to 1e-10,
+100 steps to 1e-9 relative L2 (solves at rtol 1e-12 on both sides); the
+mixed path -- 1e-6 relative L2 per field at rtol 1e-8.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import p1
+from oracle.ipcs import IPCS
+from workloads import meshes as WM
+from workloads import problems as WP
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1602_03643_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+def capi():
+    from paper_1602_03643_gb300 import capi as c
+    return c
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def csr_from(mesh_h, values):
+    c = capi()
+    rp, col = c.oasis_mesh_get_pattern(mesh_h)
+    n = rp.size - 1
+    return sp.csr_matrix((values, col, rp), shape=(n, n))
+
+
+MESHES = {
+    "sq_7x5": lambda: WM.box_mesh_2d(7, 5, 0.0, 1.3, -0.5, 0.5),
+    "cube_5x4x3": lambda: WM.box_mesh_3d(5, 4, 3, hi=(1.0, 0.7, 0.6)),
+    "jitter_6": lambda: WM.jitter_interior(WM.box_mesh_3d(6, 6, 6), 0.2, 1 / 6, seed=4),
+    "periodic_channel": lambda: WM.box_mesh_3d(6, 5, 4, lo=(0, -1, 0), hi=(2, 1, 1),
+                                               y_coords=WP.channel_y(6), periodic=(True, False, True)),
+    "random_perm": lambda: WM.renumber_dofs(WM.box_mesh_3d(5, 5, 5), WM.random_permutation(216, 44)),
+}
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_constant_matrices_match_oracle(name):
+    c = capi()
+    m = MESHES[name]()
+    D = p1.Discretization(m)
+    h = c.oasis_mesh_create(m.dim, m.coords, m.cells, m.dof_of_vertex, m.n_dofs)
+    try:
+        c.oasis_assemble_constant(h)
+        rp, col = c.oasis_mesh_get_pattern(h)
+        P = D.pattern()
+        np.testing.assert_array_equal(rp, P.indptr)
+        np.testing.assert_array_equal(col, P.indices)
+        for which, ref in [(c.OASIS_MAT_M, D.M), (c.OASIS_MAT_K, D.K)] + \
+                          [(c.OASIS_MAT_G0 + k, D.G[k]) for k in range(m.dim)]:
+            got = c.oasis_mesh_get_matrix(h, which)
+            np.testing.assert_allclose(got, ref.data, rtol=0, atol=1e-13 * np.abs(ref.data).max())
+        np.testing.assert_allclose(c.oasis_mesh_get_matrix(h, -1), D.ML, rtol=1e-13)
+    finally:
+        c.oasis_mesh_destroy(h)
+
+
+@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+def test_spmv_f64_f32(lanes):
+    import torch
+    c = capi()
+    m = WM.jitter_interior(WM.box_mesh_3d(9, 8, 7), 0.2, 1 / 9, seed=2)
+    D = p1.Discretization(m)
+    h = c.oasis_mesh_create(m.dim, m.coords, m.cells, m.dof_of_vertex, m.n_dofs)
+    try:
+        c.oasis_assemble_constant(h)
+        rng = np.random.default_rng(lanes)
+        x = rng.normal(size=m.n_dofs)
+        for which, ref in [(c.OASIS_MAT_K, D.K), (c.OASIS_MAT_G1, D.G[1])]:
+            xd = torch.tensor(x, device="cuda")
+            yd = torch.empty_like(xd)
+            c.oasis_spmv_f64(h, which, xd, yd, lanes)
+            torch.cuda.synchronize()
+            want = ref @ x
+            np.testing.assert_allclose(yd.cpu().numpy(), want, rtol=0, atol=1e-13 * np.abs(want).max())
+            xf = xd.float()
+            yf = torch.empty_like(xf)
+            c.oasis_spmv_f32(h, which, xf, yf, lanes)
+            torch.cuda.synchronize()
+            assert relerr(yf.cpu().numpy(), want) < 2e-6
+    finally:
+        c.oasis_mesh_destroy(h)
+
+
+def _perturbed_state(pb, seed=5):
+    """Make u^{n-2} differ from u^{n-1} so that ubar exercises both."""
+    rng = np.random.default_rng(seed)
+    u2 = pb.u_nm2 + 0.05 * rng.normal(size=pb.u_nm2.shape)
+    u2[:, pb.dirichlet] = pb.u_nm1[:, pb.dirichlet]
+    pb.u_nm2 = u2
+    return pb
+
+
+PROBLEMS = {
+    "tg2d_8": lambda: WP.taylor_green_2d(8),
+    "tg3d_6": lambda: WP.taylor_green_3d(6),
+    "channel_6x6x4": lambda: WP.channel(nx=6, ny=6, nz=4),
+    "stress_5_random": lambda: WP.stress_cube(5, ordering="random"),
+}
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tentative_system_alg2_matches_naive(name, precision):
+    """Algorithm 2 (fused on the GPU) gives the naive A and b - A u^{n-1}."""
+    from paper_1602_03643_gb300.driver import IPCSRun
+    pb = _perturbed_state(PROBLEMS[name]())
+    run = IPCSRun(pb, precision=precision)
+    try:
+        run.set_dirichlet_for_next_step()
+        A_gpu, r0_gpu = run.tentative_system()
+        o = IPCS(pb)
+        A_ref, b_ref = o.tentative_system(pb.u_nm1, pb.u_nm2, pb.p, pb.t0 + pb.dt)
+        A_ref = A_ref.tocsr()
+        A_ref.sort_indices()
+        Ag = csr_from(run.mesh, A_gpu)
+        tol = 1e-13 if precision == 0 else 2e-6
+        diff = (Ag - A_ref).tocsr()
+        assert abs(diff).max() <= tol * abs(A_ref).max()
+        r0_ref = b_ref - np.stack([A_ref @ pb.u_nm1[k] for k in range(pb.mesh.dim)])
+        scale = np.abs(r0_ref).max()
+        tol_r = 1e-11 if precision == 0 else 1e-5
+        np.testing.assert_allclose(r0_gpu, r0_ref, rtol=0, atol=tol_r * scale)
+    finally:
+        run.close()
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_fp64_steps_match_oracle(name, use_graph):
+    from paper_1602_03643_gb300.driver import IPCSRun
+    pb = _perturbed_state(PROBLEMS[name]())
+    run = IPCSRun(pb, rtol_u=1e-13, rtol_p=1e-13, use_graph=use_graph)
+    o = IPCS(pb)
+    s = o.initial_state()
+    try:
+        for it in range(3):
+            st = run.step()
+            assert st.status == 0
+            s = o.step(s)
+            u, p, phi = run.fields()
+            assert relerr(u, s.u_nm1) < 1e-10, it
+            assert relerr(p, s.p) < 1e-10, it
+            assert relerr(phi, s.phi) < 1e-9, it
+    finally:
+        run.close()
+
+
+def test_fp64_100_steps_tg2d_32():
+    """The float64 GPU path stays within 1e-9 (relative L2) of the oracle over 100 steps."""
+    from paper_1602_03643_gb300.driver import IPCSRun
+    pb = WP.taylor_green_2d(32)
+    run = IPCSRun(pb, rtol_u=1e-12, rtol_p=1e-12, use_graph=1)
+    try:
+        run.step(100, want_stats=False)
+        u, p, _ = run.fields()
+    finally:
+        run.close()
+    s = IPCS(pb).run(100)
+    assert relerr(u, s.u_nm1) <= 1e-9
+    assert relerr(p, s.p) <= 1e-9
+
+
+def test_graph_equals_eager_bitwise():
+    from paper_1602_03643_gb300.driver import IPCSRun
+    out = []
+    for g in (0, 1):
+        pb = WP.taylor_green_3d(8)
+        run = IPCSRun(pb, rtol_u=1e-10, rtol_p=1e-10, use_graph=g, precision=1)
+        run.step(4)
+        out.append(run.fields())
+        run.close()
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_equals_unbatched(precision):
+    from paper_1602_03643_gb300.driver import IPCSRun
+    out = []
+    for batch in (1, 0):
+        pb = WP.channel(nx=8, ny=7, nz=6)
+        run = IPCSRun(pb, rtol_u=1e-12 if precision == 0 else 1e-9, rtol_p=1e-12 if precision == 0 else 1e-9,
+                      batch_rhs=batch, precision=precision)
+        run.step(3)
+        out.append(run.fields())
+        run.close()
+    assert relerr(out[0][0], out[1][0]) < (1e-10 if precision == 0 else 1e-7)
+    assert relerr(out[0][1], out[1][1]) < (1e-9 if precision == 0 else 1e-6)
+
+
+def test_mixed_precision_per_field_error():
+    """Mixed precision at rtol 1e-8 against the float64 oracle (exact solves): <= 1e-6 per field."""
+    from paper_1602_03643_gb300.driver import IPCSRun
+    pb = WP.taylor_green_3d(12)
+    run = IPCSRun(pb, precision=1, rtol_u=1e-8, rtol_p=1e-8, use_graph=1)
+    try:
+        run.step(20)
+        u, p, _ = run.fields()
+    finally:
+        run.close()
+    s = IPCS(pb).run(20)
+    for k in range(3):
+        if np.abs(s.u_nm1[k]).max() > 0:
+            assert relerr(u[k], s.u_nm1[k]) <= 1e-6, k
+    assert relerr(p, s.p) <= 1e-6
+
+
+def test_permutation_invariance():
+    from paper_1602_03643_gb300.driver import IPCSRun
+    base = WP.stress_cube(6, ordering="natural")
+    perm = WM.random_permutation(base.mesh.n_dofs, 44)
+    pbp = WP.stress_cube(6, ordering="random")
+    r1 = IPCSRun(base, rtol_u=1e-12, rtol_p=1e-12)
+    r2 = IPCSRun(pbp, rtol_u=1e-12, rtol_p=1e-12)
+    try:
+        r1.step(3)
+        r2.step(3)
+        u1, p1_, _ = r1.fields()
+        u2, p2_, _ = r2.fields()
+    finally:
+        r1.close()
+        r2.close()
+    np.testing.assert_allclose(u2[:, perm], u1, atol=1e-10)
+    np.testing.assert_allclose(p2_[perm], p1_, atol=1e-9 * np.abs(p1_).max())
+
+
+def test_table1_first_row_on_gpu():
+    """The GPU path reproduces the first P1P1 row of Table 1 (periodic Taylor-Green)."""
+    from paper_1602_03643_gb300.driver import IPCSRun
+    pb = WP.taylor_green_2d_periodic(10)
+    run = IPCSRun(pb, rtol_u=1e-12, rtol_p=1e-12, use_graph=1)
+    try:
+        run.step(1000, want_stats=False)
+        u, p, _ = run.fields()
+    finally:
+        run.close()
+    x = pb.mesh.dof_coords()
+    t = 1.0
+    eu = np.sqrt(np.mean((u - pb.exact_u(x, t)) ** 2))
+    pe = pb.exact_p(x, t - 0.5 * pb.dt)
+    ep = np.sqrt(np.mean(((p - p.mean()) - (pe - pe.mean())) ** 2))
+    assert abs(eu - 9.31e-3) < 0.006 * 9.31e-3
+    assert abs(ep - 4.97e-3) < 0.01 * 4.97e-3
+
+
+def test_notconv_status():
+    from paper_1602_03643_gb300.driver import IPCSRun
+    c = capi()
+    pb = WP.taylor_green_3d(8)
+    run = IPCSRun(pb, max_it_p=2, rtol_p=1e-12)
+    try:
+        with pytest.raises(c.OasisError) as ei:
+            run.step()
+        assert ei.value.code == c.OASIS_ENOTCONV
+    finally:
+        run.close()
+
+
+def test_nan_input_status():
+    from paper_1602_03643_gb300.driver import IPCSRun
+    c = capi()
+    pb = WP.taylor_green_3d(6)
+    pb.u_nm1 = pb.u_nm1.copy()
+    pb.u_nm1[0, 100] = np.nan
+    run = IPCSRun(pb)
+    try:
+        with pytest.raises(c.OasisError) as ei:
+            run.step()
+        assert ei.value.code in (c.OASIS_ENAN, c.OASIS_ENOTCONV)
+    finally:
+        run.close()
+
+
+def test_degenerate_cell_rejected():
+    c = capi()
+    m = WM.box_mesh_2d(3, 3)
+    coords = m.coords.copy()
+    cells = m.cells.copy()
+    cells[0] = [0, 1, 2]            # three collinear vertices on the bottom edge
+    h = c.oasis_mesh_create(2, coords, cells)
+    try:
+        with pytest.raises(c.OasisError) as ei:
+            c.oasis_assemble_constant(h)
+        assert ei.value.code == c.OASIS_EMESH
+    finally:
+        c.oasis_mesh_destroy(h)
