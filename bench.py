@@ -120,9 +120,10 @@ def run_ours(args, rank, world):
     N = pb.mesh.n_dofs
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def make(precision, graph=1, guess=capi.OASIS_GUESS_PREV_PHI):
+    def make(precision, graph=1, guess=capi.OASIS_GUESS_PREV_PHI, batch=1):
         return IPCSRun(pb, precision=precision, rtol_u=RTOL, rtol_p=RTOL, max_it_u=5000, max_it_p=200000,
-                       inner_rtol=args.inner_rtol, use_graph=graph, guess=guess, stream=stream)
+                       inner_rtol=args.inner_rtol, use_graph=graph, guess=guess, batch_rhs=batch,
+                       stream=stream)
 
     def timed_steps(run, k):
         evs = []
@@ -141,7 +142,7 @@ def run_ours(args, rank, world):
         return sum(a.elapsed_time(b) for a, b in evs), stats
 
     # ---- the headline form: mixed precision + batched + graph (+ previous-phi guess)
-    run = make(capi.OASIS_MIXED)
+    run = make(capi.OASIS_MIXED, graph=0 if args.eager else 1)
     run.set_dirichlet_for_next_step()
     for _ in range(args.warmup):
         capi.oasis_step(run.solver, stream, want_stats=False)
@@ -157,6 +158,8 @@ def run_ours(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     clocks = clk.summary()
+    if args.minimal:
+        return {"minimal": True, "ms_per_step": ms / args.steps, "stats_last": stats[-1]}
     bad = [s for s in stats if s["status"] != 0]
     ms_per_step = ms / args.steps
     value = world * args.steps / (ms / 1e3)
@@ -212,17 +215,19 @@ def run_ours(args, rank, world):
                 "note": "K + col (33 MB) + vectors stay L2-resident inside the CG loop at this size"}
     kernel_share = {f: {"launches": n, "ms": m} for f, (n, m) in fam.items()}
 
-    # ---- the plain float64 GPU form at the same residual (comparison)
+    # ---- the plain float64 GPU form at the same residual (comparison): float64,
+    # one solve per velocity component, eager launches, pressure guess p = p*
     fp64 = None
     if not args.skip_fp64:
-        run64 = make(capi.OASIS_FP64, guess=capi.OASIS_GUESS_ZERO)
+        run64 = make(capi.OASIS_FP64, graph=0, guess=capi.OASIS_GUESS_ZERO, batch=0)
         run64.set_dirichlet_for_next_step()
         for _ in range(max(1, args.warmup // 2)):
             capi.oasis_step(run64.solver, stream, want_stats=False)
         k64 = max(3, args.steps // 2)
         ms64, st64 = timed_steps(run64, k64)
         run64.close()
-        fp64 = {"steps_per_s": k64 / (ms64 / 1e3), "ms_per_step": ms64 / k64,
+        fp64 = {"form": "float64, unbatched, eager, guess p*",
+                "steps_per_s": k64 / (ms64 / 1e3), "ms_per_step": ms64 / k64,
                 "it_u_mean": float(np.mean([max(s["it_u"]) for s in st64])),
                 "it_p_mean": float(np.mean([s["it_p"] for s in st64]))}
 
@@ -322,6 +327,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--minimal", action="store_true",
+                    help="only the warm-up and timed steps (for profiler captures)")
+    ap.add_argument("--eager", action="store_true",
+                    help="run the headline form as eager launches (profilers cannot see kernels "
+                         "inside graphs with conditional nodes)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -13,32 +13,6 @@ namespace oasis {
 
 static thread_local std::string g_last_error;
 
-// ------------------------------------------------------------------ layout kernels
-// component-major [D][n] <-> dof-major [n][D]
-__global__ void k_soa_to_aos(int64_t n, int D, const double* __restrict__ src, double* __restrict__ dst) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * D; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / D;
-        const int k = (int)(t - i * D);
-        dst[t] = src[(int64_t)k * n + i];
-    }
-}
-__global__ void k_aos_to_soa(int64_t n, int D, const double* __restrict__ src, double* __restrict__ dst) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * D; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / D;
-        const int k = (int)(t - i * D);
-        dst[(int64_t)k * n + i] = src[t];
-    }
-}
-__global__ void k_f32_to_f64(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        b[i] = (double)a[i];
-}
-
-static int egrid(int64_t items) {
-    const int64_t want = (items + kBlock - 1) / kBlock;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 8));
-}
-
 // ------------------------------------------------------------------ loops
 void Solver::poll(cudaStream_t s, int which) {
     OASIS_CUDA(cudaMemcpyAsync(h_st + which, st.p + which, sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
@@ -159,7 +133,6 @@ void Solver::step(cudaStream_t s) {
         if (prof_on) prof_collect();
     }
     t += prm.dt;
-    stepped = true;
 }
 
 void Solver::capture() {
@@ -203,6 +176,7 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     OASIS_CHECK(prm->precision == OASIS_FP64 || prm->precision == OASIS_MIXED, OASIS_EINVAL, "precision");
     OASIS_CHECK(prm->guess >= 0 && prm->guess <= 2, OASIS_EINVAL, "guess");
     OASIS_CHECK(n_dir >= 0 && (n_dir == 0 || dir), OASIS_EINVAL, "dirichlet dofs");
+    OASIS_CHECK(m->max_row <= 64, OASIS_EMESH, "rows with more than 64 pattern entries are not supported");
     auto S = std::make_unique<Solver>();
     S->m = m;
     S->prm = *prm;
@@ -210,6 +184,8 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     if (S->mixed && !(S->prm.inner_rtol > 0 && S->prm.inner_rtol < 1)) S->prm.inner_rtol = 1e-4;
     const int D = m->dim;
     const int64_t n = m->n;
+    const size_t vb = S->mixed ? sizeof(float) : sizeof(double);   // value bytes
+    const size_t sb = 8;                                             // state bytes (double or float2)
     S->n_dir = n_dir;
     std::vector<int32_t> di(n, -1);
     for (int64_t q = 0; q < n_dir; ++q) {
@@ -218,58 +194,23 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
         di[dir[q]] = (int32_t)q;
     }
     S->dir_index.upload(di.data(), n, s);
-    S->g.alloc(std::max<int64_t>(1, n_dir * D));
-    OASIS_CUDA(cudaMemsetAsync(S->g.p, 0, S->g.bytes(), s));
-    for (auto* b : {&S->u1, &S->u2, &S->du, &S->r0u}) {
-        b->alloc(n * D);
-        OASIS_CUDA(cudaMemsetAsync(b->p, 0, b->bytes(), s));
-    }
-    for (auto* b : {&S->pstar, &S->phi, &S->phi_h1, &S->phi_h2, &S->bphi, &S->xp}) {
-        b->alloc(n);
-        OASIS_CUDA(cudaMemsetAsync(b->p, 0, b->bytes(), s));
-    }
-    if (S->mixed) {
-        S->A32.alloc(m->nnz);
-        S->dA32.alloc(n);
-        S->beta32.alloc(m->nc * 4);
-        for (int k = 0; k < 9; ++k) {
-            S->w32[k].alloc(n * D);
-            OASIS_CUDA(cudaMemsetAsync(S->w32[k].p, 0, S->w32[k].bytes(), s));
-            S->w32p[k] = S->w32[k].p;
-        }
-        for (int k = 0; k < 6; ++k) {
-            S->q32[k].alloc(n);
-            OASIS_CUDA(cudaMemsetAsync(S->q32[k].p, 0, S->q32[k].bytes(), s));
-            S->q32p[k] = S->q32[k].p;
-        }
-    } else {
-        S->A64.alloc(m->nnz);
-        S->dA64.alloc(n);
-        S->beta64.alloc(m->nc * 4);
-        for (int k = 0; k < 9; ++k) {
-            S->w64[k].alloc(n * D);
-            OASIS_CUDA(cudaMemsetAsync(S->w64[k].p, 0, S->w64[k].bytes(), s));
-            S->w64p[k] = S->w64[k].p;
-        }
-        for (int k = 0; k < 6; ++k) {
-            S->q64[k].alloc(n);
-            OASIS_CUDA(cudaMemsetAsync(S->q64[k].p, 0, S->q64[k].bytes(), s));
-            S->q64p[k] = S->q64[k].p;
-        }
-    }
+    S->g.alloc(sb * std::max<int64_t>(1, n_dir * D), s);
+    for (RBuf* b : {&S->u1, &S->u2, &S->du, &S->r0}) b->alloc(sb * n * D, s);
+    for (RBuf* b : {&S->pstar, &S->x, &S->b, &S->phi, &S->phi_h1, &S->phi_h2}) b->alloc(sb * n, s);
+    S->A.alloc(vb * m->nnz, s);
+    S->dinvA.alloc(vb * n, s);
+    S->beta.alloc(vb * m->nc * 4, s);
+    for (auto& w : S->w) w.alloc(vb * n * D, s);
+    for (auto& w : S->pw) w.alloc(vb * n, s);
+    S->uIv.alloc(vb * n * D, s);
     S->stage.alloc(std::max<int64_t>(n, n_dir) * D);
-    if (S->mixed) S->stage32.alloc(m->nnz);
     S->st.alloc(2);
     OASIS_CUDA(cudaMemsetAsync(S->st.p, 0, S->st.bytes(), s));
-    S->partial.alloc((size_t)num_sms() * 8 * 8);
+    S->partial.alloc((size_t)num_sms() * 8 * 8 * 8, s);
     OASIS_CUDA(cudaHostAlloc(&S->h_st, 2 * sizeof(KrylovState), cudaHostAllocDefault));
     std::memset(S->h_st, 0, 2 * sizeof(KrylovState));
     for (auto& c : S->cap) OASIS_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
-    int lanes = prm->spmv_lanes;
-    if (lanes == 0) lanes = D == 2 ? 8 : 16;
-    OASIS_CHECK(lanes == 8 || lanes == 16, OASIS_EINVAL, "spmv_lanes must be 0, 8 or 16");
-    S->lanes = lanes;
-    S->impl.reset(make_step_impl(*S, lanes));
+    S->impl.reset(make_step_impl(*S));
     OASIS_CUDA(cudaStreamSynchronize(s));
     return S.release();
 }
@@ -421,23 +362,19 @@ int oasis_set_fields(oasis_solver* solver, const double* u_nm1, const double* u_
         cudaStream_t s = as_stream(stream);
         const int D = S->m->dim;
         const int64_t n = S->m->n;
-        double* tmp = S->stage.p;
-        const double* srcs[2] = {u_nm1, u_nm2};
-        DBuf<double>* dsts[2] = {&S->u1, &S->u2};
-        for (int q = 0; q < 2; ++q) {
+        const double* srcs[3] = {u_nm1, u_nm2, p};
+        const int ids[3] = {ST_U1, ST_U2, ST_PSTAR};
+        const int comps[3] = {D, D, 1};
+        for (int q = 0; q < 3; ++q) {
             const double* src = srcs[q];
             if (!on_device) {
-                OASIS_CUDA(cudaMemcpyAsync(tmp, src, n * D * sizeof(double), cudaMemcpyHostToDevice, s));
-                src = tmp;
+                OASIS_CUDA(cudaMemcpyAsync(S->stage.p, src, n * comps[q] * sizeof(double), cudaMemcpyHostToDevice, s));
+                src = S->stage.p;
             }
-            k_soa_to_aos<<<egrid(n * D), kBlock, 0, s>>>(n, D, src, dsts[q]->p);
-            OASIS_CUDA(cudaGetLastError());
+            S->impl->to_state(s, src, ids[q], n, comps[q]);
             OASIS_CUDA(cudaStreamSynchronize(s));
         }
-        OASIS_CUDA(cudaMemcpyAsync(S->pstar.p, p, n * sizeof(double),
-                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-        for (auto* b : {&S->phi, &S->phi_h1, &S->phi_h2})
-            OASIS_CUDA(cudaMemsetAsync(b->p, 0, b->bytes(), s));
+        for (RBuf* b : {&S->phi, &S->phi_h1, &S->phi_h2}) OASIS_CUDA(cudaMemsetAsync(b->p, 0, b->bytes, s));
         OASIS_CUDA(cudaStreamSynchronize(s));
         S->t = t;
     });
@@ -457,8 +394,7 @@ int oasis_set_dirichlet(oasis_solver* solver, const double* g, int32_t on_device
             OASIS_CUDA(cudaMemcpyAsync(S->stage.p, g, nd * D * sizeof(double), cudaMemcpyHostToDevice, s));
             src = S->stage.p;
         }
-        k_soa_to_aos<<<egrid(nd * D), kBlock, 0, s>>>(nd, D, src, S->g.p);
-        OASIS_CUDA(cudaGetLastError());
+        S->impl->to_state(s, src, ST_G, nd, D);
         if (!on_device) OASIS_CUDA(cudaStreamSynchronize(s));
     });
 }
@@ -495,16 +431,18 @@ int oasis_get_fields(oasis_solver* solver, double* u, double* p, double* phi, in
         cudaStream_t s = as_stream(stream);
         const int D = S->m->dim;
         const int64_t n = S->m->n;
-        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-        if (u) {
-            double* dst = on_device ? u : S->stage.p;
-            k_aos_to_soa<<<egrid(n * D), kBlock, 0, s>>>(n, D, S->u1.p, dst);
-            OASIS_CUDA(cudaGetLastError());
-            if (!on_device) OASIS_CUDA(cudaMemcpyAsync(u, S->stage.p, n * D * sizeof(double), cudaMemcpyDeviceToHost, s));
+        double* outs[3] = {u, p, phi};
+        const int ids[3] = {ST_U1, ST_PSTAR, ST_PHI};
+        const int comps[3] = {D, 1, 1};
+        for (int q = 0; q < 3; ++q) {
+            if (!outs[q]) continue;
+            double* dst = on_device ? outs[q] : S->stage.p;
+            S->impl->from_state(s, dst, ids[q], n, comps[q]);
+            if (!on_device) {
+                OASIS_CUDA(cudaMemcpyAsync(outs[q], S->stage.p, n * comps[q] * sizeof(double), cudaMemcpyDeviceToHost, s));
+                OASIS_CUDA(cudaStreamSynchronize(s));
+            }
         }
-        if (p) OASIS_CUDA(cudaMemcpyAsync(p, S->pstar.p, n * sizeof(double), kind, s));
-        if (phi) OASIS_CUDA(cudaMemcpyAsync(phi, S->phi.p, n * sizeof(double), kind, s));
-        if (!on_device) OASIS_CUDA(cudaStreamSynchronize(s));
     });
 }
 
@@ -517,18 +455,14 @@ int oasis_get_tentative_system(oasis_solver* solver, double* A_values, double* r
         const int64_t n = S->m->n, nnz = S->m->nnz;
         S->impl->assemble(s);
         if (A_values) {
-            if (S->mixed) {
-                std::vector<float> h(nnz);
-                OASIS_CUDA(cudaMemcpyAsync(h.data(), S->A32.p, nnz * sizeof(float), cudaMemcpyDeviceToHost, s));
-                OASIS_CUDA(cudaStreamSynchronize(s));
-                for (int64_t q = 0; q < nnz; ++q) A_values[q] = (double)h[q];
-            } else {
-                OASIS_CUDA(cudaMemcpyAsync(A_values, S->A64.p, nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
-            }
+            DBuf<double> tmp;
+            tmp.alloc(nnz);
+            S->impl->a_to_double(s, tmp.p);
+            OASIS_CUDA(cudaMemcpyAsync(A_values, tmp.p, nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+            OASIS_CUDA(cudaStreamSynchronize(s));
         }
         if (r0) {
-            k_aos_to_soa<<<egrid(n * D), kBlock, 0, s>>>(n, D, S->r0u.p, S->stage.p);
-            OASIS_CUDA(cudaGetLastError());
+            S->impl->from_state(s, S->stage.p, ST_R0, n, D);
             OASIS_CUDA(cudaMemcpyAsync(r0, S->stage.p, n * D * sizeof(double), cudaMemcpyDeviceToHost, s));
         }
         OASIS_CUDA(cudaStreamSynchronize(s));

@@ -82,31 +82,35 @@ struct Mesh {
     DBuf<double> M64, K64, G64;                // G64: [dim][nnz]
     DBuf<float> M32, K32, G32;
     DBuf<double> ML64, invML64, dinvK64;       // [n]
-    DBuf<float> dinvK32;
+    DBuf<float> ML32, invML32, dinvK32;
+    DBuf<float2> Kff;                          // K as float-float (hi, lo)
+    int tile_cap = 0;                          // max entries of a 256-row tile
     DBuf<int32_t> err;                         // device error flag for setup kernels
     bool assembled = false;
 };
 
 // Device-resident scalars of one Krylov solve (up to 3 right-hand sides).
+// Float copies of the coefficients are kept so that float32 kernels never
+// convert from float64 (a float64 instruction is ~64x a float32 one on GB300).
 struct KrylovState {
     double rho[3], rho_new[3], alpha[3], omega[3], beta[3];
     double bb[3];          // ||reference||^2 for the relative criterion
-    double rr[3];          // last float64 residual^2 of the outer sweep
+    double rr[3];          // last float64-quality residual^2 of the outer sweep
     double rr0_in[3];      // start of the current inner solve
     double rr_in[3];       // recurrence residual^2 of the inner solve
-    double mean;           // pressure: mean of the right-hand side; sum of p
-    double psum;
-    double guess_rr[2];    // residual^2 of the candidate guesses
-    int32_t col_done[3];   // converged in float64
+    double mean;           // pressure: mean of the right-hand side
+    double psum;           // pressure: sum of p* + phi (normalisation)
+    float alpha_f[3], omega_f[3], beta_f[3];
+    float mean_hi, mean_lo, meanp_hi, meanp_lo;
+    int32_t col_done[3];   // converged (float64-quality residual)
     int32_t in_done[3];    // inner solve finished for this sweep
     int32_t it_total[3];
     int32_t it_in;         // inner iteration counter (parity of double buffers)
     int32_t sweeps;
     int32_t status;        // OASIS_OK / ENOTCONV / EBREAKDOWN / ENAN
     int32_t guess_used;
-    int32_t first;         // 1 before the first float64 residual of a solve
+    int32_t first;         // 1 before the first residual of a solve
     uint32_t ticket;       // last-block reduction ticket
-    int32_t pad[3];
 };
 
 struct Solver;

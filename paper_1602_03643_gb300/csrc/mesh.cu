@@ -119,6 +119,10 @@ Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const in
     cudaStream_t s = 0;
     m->nnz = nnz;
     m->max_row = max_row;
+    for (int64_t r0 = 0; r0 < n; r0 += kBlock) {
+        const int64_t r1 = std::min<int64_t>(n, r0 + kBlock);
+        m->tile_cap = std::max<int>(m->tile_cap, row_ptr[r1] - row_ptr[r0]);
+    }
     m->row_ptr.upload(row_ptr.data(), row_ptr.size(), s);
     m->col.upload(col.data(), col.size(), s);
     m->diag.upload(diag.data(), diag.size(), s);
@@ -244,14 +248,26 @@ __global__ void k_row_constant(int64_t n, const int32_t* __restrict__ row_ptr,
 
 __global__ void k_mesh_derived(int64_t n, const int32_t* __restrict__ diag, const double* __restrict__ K,
                                const double* __restrict__ ML, double* __restrict__ invML,
-                               double* __restrict__ dinvK64, float* __restrict__ dinvK32) {
+                               double* __restrict__ dinvK64, float* __restrict__ dinvK32,
+                               float* __restrict__ ML32, float* __restrict__ invML32) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         invML[i] = 1.0 / ML[i];
+        ML32[i] = (float)ML[i];
+        invML32[i] = (float)(1.0 / ML[i]);
         const double kd = K[diag[i]];
         const double di = kd != 0.0 ? 1.0 / kd : 1.0;
         dinvK64[i] = di;
         dinvK32[i] = (float)di;
+    }
+}
+
+// K split into float-float (hi = K rounded to float, lo = the remainder)
+__global__ void k_to_ff(int64_t n, const double* __restrict__ a, float2* __restrict__ b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float hi = (float)a[i];
+        b[i] = make_float2(hi, (float)(a[i] - (double)hi));
     }
 }
 
@@ -304,7 +320,12 @@ void assemble_constant(Mesh& m, cudaStream_t s) {
     m.invML64.alloc(m.n);
     m.dinvK64.alloc(m.n);
     m.dinvK32.alloc(m.n);
-    k_mesh_derived<<<gr, kBlock, 0, s>>>(m.n, m.diag.p, m.K64.p, m.ML64.p, m.invML64.p, m.dinvK64.p, m.dinvK32.p);
+    m.ML32.alloc(m.n);
+    m.invML32.alloc(m.n);
+    k_mesh_derived<<<gr, kBlock, 0, s>>>(m.n, m.diag.p, m.K64.p, m.ML64.p, m.invML64.p, m.dinvK64.p, m.dinvK32.p,
+                                         m.ML32.p, m.invML32.p);
+    m.Kff.alloc(m.nnz);
+    k_to_ff<<<grid_for(m.nnz), kBlock, 0, s>>>(m.nnz, m.K64.p, m.Kff.p);
     m.M32.alloc(m.nnz);
     m.K32.alloc(m.nnz);
     m.G32.alloc((size_t)D * m.nnz);

@@ -10,89 +10,67 @@
 
 namespace oasis {
 
-template <class V>
-struct AsmArgs {
-    const int32_t *rp, *col, *diag, *inc_ptr, *inc_cell;
+// Raw device buffer whose element type depends on the precision policy
+// (8-byte state entries are double in float64 mode and float2 float-float in
+// mixed mode; V entries are double or float).
+struct RBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    RBuf() = default;
+    RBuf(const RBuf&) = delete;
+    RBuf& operator=(const RBuf&) = delete;
+    ~RBuf() {
+        if (p) cudaFree(p);
+    }
+    void alloc(size_t b, cudaStream_t s) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = b;
+        if (b) {
+            OASIS_CUDA(cudaMalloc(&p, b));
+            OASIS_CUDA(cudaMemsetAsync(p, 0, b, s));
+        }
+    }
+    template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+template <class P>
+struct StepData {
+    using V = typename P::V;
+    using S = typename P::S;
+    // pattern / mesh
+    const int32_t *rp, *col, *diag, *inc_ptr, *inc_cell, *cell_dof;
     const uint32_t* inc_slots;
-    const V* beta;
-    const V *M, *K, *G;
-    const double* ML;
-    const double *u1, *u2, *pstar;
+    const V *M, *K, *G, *gw, *ML;     // G: [D][nnz]; gw: [nc][D+1][D]
+    const S* Kout;                    // float64-quality K for the pressure residual
+    const V *dinvK, *invML;
+    // state (S)
+    S *u1, *u2, *du, *r0, *pstar, *x, *b, *phi, *phi_h1, *phi_h2;
+    const S* g;                       // [n_dir][D]
     const int32_t* dir_index;
-    const double* g;
+    // tentative system (V)
+    V *A, *dinvA, *beta;
+    // BiCGStab work [n][D] (V)
+    V *r, *rh, *p, *v, *s, *t, *ph, *sh, *dl;
+    // CG work [n] (V)
+    V *pr, *pz, *pp0, *pp1, *pq, *pdl, *xv;
+    V* uIv;                           // u^I rounded to V, [n][D]
+    KrylovState *stu, *stp;
+    void* partial;
     double f[3];
     double dt, nu;
-    V* A;
-    V* dinv;
-    double* r0;
-    KrylovState* st;
-    double* partial;
-    int64_t n, nnz;
+    int64_t n, nnz, nc;
+    int max_row;
 };
 
-template <class V>
-struct BicgArgs {
-    const int32_t *rp, *col;
-    const V* A;
-    const V* dinv;
-    const double* r0;
-    double* du;
-    V *r, *rh, *p, *v, *s, *t, *ph, *sh, *dl;
-    KrylovState* st;
-    double* partial;
-    int64_t n;
-    int k0;
-};
-
-struct BicgCtl {
+struct Ctl {
     double rtol2;       // float64 stopping test: ||r||^2 <= rtol2 * bb
     double inner2;      // inner solve: relative reduction^2 of its own start residual
-    double abs2;        // inner solve: ||r_in||^2 <= abs2 * bb also ends the sweep
+    double abs2;        // inner solve also ends at ||r_in||^2 <= abs2 * bb
     int max_it;         // total iterations over all sweeps
     int sweep_cap;      // iterations per sweep
     int use_cond;       // 1 inside a captured graph
     cudaGraphConditionalHandle h_outer, h_inner;
-};
-
-template <class V>
-struct PresArgs {
-    const int32_t *rp, *col;
-    const V* G;
-    const double *u1, *du;
-    double* b;
-    double dt;
-    KrylovState* st;
-    double* partial;
-    int64_t n, nnz;
-};
-
-template <class V>
-struct PcgArgs {
-    const int32_t *rp, *col;
-    const V* K;
-    const double* K64;
-    const V* dinv;
-    const double* b;
-    double* x;
-    const double* pstar;
-    V *r, *z, *p0, *p1, *q, *dl;
-    KrylovState* st;
-    double* partial;
-    int64_t n;
-};
-
-template <class V>
-struct UpdArgs {
-    const int32_t *rp, *col;
-    const V* G;
-    const double* invML;
-    const double *x, *du;
-    double *u1, *u2, *pstar, *phi_out, *phi_h1, *phi_h2;
-    const int32_t* dir_index;
-    const double* g;
-    double dt;
-    const KrylovState* stp;
-    int64_t n, nnz;
 };
 
 struct Loop {
@@ -106,7 +84,13 @@ struct StepImpl {
     virtual void tentative_solve(cudaStream_t s, bool graph) = 0;
     virtual void pressure_solve(cudaStream_t s, bool graph) = 0;
     virtual void update(cudaStream_t s) = 0;
+    virtual void to_state(cudaStream_t s, const double* src_soa, int which, int64_t count, int comps) = 0;
+    virtual void from_state(cudaStream_t s, double* dst_soa, int which, int64_t count, int comps) = 0;
+    virtual void a_to_double(cudaStream_t s, double* dst) = 0;
 };
+
+// state buffers addressable by to_state / from_state
+enum StateId { ST_U1 = 0, ST_U2, ST_PSTAR, ST_PHI, ST_G, ST_R0, ST_COUNT };
 
 using LoopFn = std::function<void(cudaStream_t, const Loop&)>;
 
@@ -114,57 +98,34 @@ struct Solver {
     Mesh* m = nullptr;
     oasis_params prm{};
     bool mixed = false;
-    int lanes = 16;
     int64_t n_dir = 0;
     double t = 0.0;
     DBuf<int32_t> dir_index;
-    DBuf<double> g;                            // [n_dir][D]
-    DBuf<double> u1, u2, du, r0u;              // [n][D]
-    DBuf<double> pstar, phi, phi_h1, phi_h2, bphi, xp;   // [n]
-    DBuf<double> A64, dA64, beta64;
-    DBuf<float> A32, dA32, beta32;
-    DBuf<double> w64[9];
-    DBuf<float> w32[9];
-    DBuf<double> q64[6];
-    DBuf<float> q32[6];
-    double* w64p[9];
-    float* w32p[9];
-    double* q64p[6];
-    float* q32p[6];
-    DBuf<KrylovState> st;                      // [0] velocity, [1] pressure
-    DBuf<double> partial;
-    KrylovState* h_st = nullptr;               // pinned mirror [2]
+    RBuf g, u1, u2, du, r0, pstar, x, b, phi, phi_h1, phi_h2;          // S
+    RBuf A, dinvA, beta;                                               // V
+    RBuf w[9];                                                         // V [n][D]
+    RBuf pw[7];                                                        // V [n]
+    RBuf uIv;                                                          // V [n][D]
+    RBuf Kout;                                                         // S [nnz]
+    DBuf<double> stage;                                                // [max(n, n_dir) * D]
+    DBuf<KrylovState> st;                                              // [0] velocity, [1] pressure
+    RBuf partial;
+    KrylovState* h_st = nullptr;                                       // pinned mirror [2]
     std::unique_ptr<StepImpl> impl;
     cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
-    bool stepped = false;
-    DBuf<double> stage;                        // [n][D] staging for host transfers
-    DBuf<float> stage32;                       // [nnz] float32 -> float64 staging
     // eager-mode kernel timing (CUDA events around selected launches)
     static constexpr int kProfFamilies = 6;
     bool prof_on = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
-    std::vector<std::pair<int, int>> ev_used;  // (family, pool index)
+    std::vector<std::pair<int, int>> ev_used;
     double prof_ms[kProfFamilies] = {0};
     int64_t prof_n[kProfFamilies] = {0};
     int prof_begin(cudaStream_t s, int family);
     void prof_end(cudaStream_t s, int idx);
     void prof_collect();
 
-    template <class V> V* beta();
-    template <class V> const V* gw();
-    template <class V> V* A();
-    template <class V> V* dinvA();
-    template <class V> V** work();
-    template <class V> V** pwork();
-    template <class V> const V* mat(const DBuf<double>& d, const DBuf<float>& f) {
-        if constexpr (sizeof(V) == 8) return (const V*)(const void*)d.p;
-        else return (const V*)(const void*)f.p;
-    }
-
-    // Runs a refinement loop: outer(); while(inner active) inner(); correct(); ...
-    // `which` selects the KrylovState (0 velocity, 1 pressure); [k0, k0+nr) the columns.
     void run_loops(cudaStream_t s, bool graph_mode, int which, const LoopFn& outer, const LoopFn& inner,
                    const LoopFn& correct, int k0 = 0, int nr = 3);
     void poll(cudaStream_t s, int which);
@@ -173,20 +134,7 @@ struct Solver {
     ~Solver();
 };
 
-template <> inline double* Solver::beta<double>() { return beta64.p; }
-template <> inline float* Solver::beta<float>() { return beta32.p; }
-template <> inline const double* Solver::gw<double>() { return m->gw64.p; }
-template <> inline const float* Solver::gw<float>() { return m->gw32.p; }
-template <> inline double* Solver::A<double>() { return A64.p; }
-template <> inline float* Solver::A<float>() { return A32.p; }
-template <> inline double* Solver::dinvA<double>() { return dA64.p; }
-template <> inline float* Solver::dinvA<float>() { return dA32.p; }
-template <> inline double** Solver::work<double>() { return w64p; }
-template <> inline float** Solver::work<float>() { return w32p; }
-template <> inline double** Solver::pwork<double>() { return q64p; }
-template <> inline float** Solver::pwork<float>() { return q32p; }
-
-StepImpl* make_step_impl(Solver& s, int lanes);
+StepImpl* make_step_impl(Solver& s);
 Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const int32_t* cells,
                  const int32_t* dof_of_vertex, int64_t n_dofs);
 void assemble_constant(Mesh& m, cudaStream_t s);

@@ -10,25 +10,22 @@
 // Delta = u^I - u^{n-1} with right-hand side r_0 = b - A u^{n-1}, and the
 // pressure solve for phi = p - p* with right-hand side
 // b_phi = -(1/dt) sum_k dP^k u_k^I (the K p* term of the algebraic pressure
-// equation cancels).  The systems and their solutions are those of Sec. 5;
-// only the initial residual is formed without the O(1/dt) cancellation of
-// b - A u^{n-1}, which keeps float32 inner solves accurate.
+// equation of Sec. 5 cancels).  The systems and their solutions are those of
+// Sec. 5; only the initial residual is formed without the O(1/dt) cancellation
+// of b - A u^{n-1}, which keeps float32 inner solves accurate.
+//
+// Sparse kernels use row tiles (kern.cuh): an entry-parallel phase with
+// coalesced reads writes one product per pattern entry to shared memory, and a
+// row-parallel phase sums each row and runs its epilogue.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
 
-#include "device.cuh"
-#include "internal.cuh"
+#include "kern.cuh"
 #include "solver.cuh"
 
 namespace oasis {
-
-static int grid_rows(int64_t rows, int rows_per_block) {
-    const int64_t want = (rows + rows_per_block - 1) / rows_per_block;
-    const int64_t cap = (int64_t)num_sms() * 8;
-    return (int)std::max<int64_t>(1, std::min(want, cap));
-}
 
 // Upper bound on refinement sweeps of one solve (each sweep also does at least
 // one counted iteration, so max_it bounds them as well).
@@ -38,131 +35,157 @@ __device__ __forceinline__ void set_cond(int use, cudaGraphConditionalHandle h, 
     if (use) cudaGraphSetConditional(h, v ? 1u : 0u);
 }
 
-// =====================================================================  assembly
-// beta[c][j] = w_T grad lambda_j . sum_m ubar_m, ubar = 1.5 u^{n-1} - 0.5 u^{n-2}
-// (Eq. 22).  With it the P1 convection element matrix is
-//   C^T_ij = w_T grad lambda_j . (sum_m ubar_m + ubar_i) = beta[T][j] + ubar_i . w_T grad lambda_j,
-// w_T = |T| / ((d+1)(d+2)); the second term summed over the cells of an edge is
-// ubar_i . dP_ij / (d+2) and is added in the row pass.
-template <class V, int D>
-__global__ void __launch_bounds__(kBlock) k_cell_beta(int64_t nc, const int32_t* __restrict__ cell_dof,
-                                                      const V* __restrict__ gw, const double* __restrict__ u1,
-                                                      const double* __restrict__ u2, V* __restrict__ beta) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        double S[D];
+// A solver coefficient in the kernel's value type, read from its float64 value
+// (float64 path) or its float mirror (mixed path).
+template <class P>
+__device__ __forceinline__ typename P::V coef(double d, float f) {
+    if constexpr (P::mixed) return f;
+    else return d;
+}
+
+__device__ __forceinline__ double acc_of_s(double a) { return a; }
+__device__ __forceinline__ ff acc_of_s(float2 a) { return {a.x, a.y}; }
+__device__ __forceinline__ double s_of_acc(double a) { return a; }
+__device__ __forceinline__ float2 s_of_acc(ff a) { return make_float2(a.hi, a.lo); }
+// S * V as an accumulator
+__device__ __forceinline__ double acc_mul_sv(double s, double v) { return s * v; }
+__device__ __forceinline__ ff acc_mul_sv(float2 s, float v) { return ff_mul_f({s.x, s.y}, v); }
+
+// Scalar constants of a step in the kernel value type (computed on the host so
+// that float32 kernels never touch float64 arithmetic).
+template <class V>
+struct Consts {
+    V rdt, dt, nu, hnu, f[3];
+};
+
+// ================================================================ assembly
+// beta[c][m] = w_T grad lambda_m . sum_l ubar_l, ubar = 1.5 u^{n-1} - 0.5 u^{n-2}
+// (Eq. 22), w_T = |T| / ((d+1)(d+2)).  With it the P1 convection element matrix is
+//   C^T_im = w_T grad lambda_m . (sum_l ubar_l + ubar_i) = beta[T][m] + ubar_i . w_T grad lambda_m;
+// the second term summed over the cells sharing an edge is ubar_i . dP_im / (d+2)
+// and is added in the row pass.
+template <class P, int D>
+__global__ void __launch_bounds__(kBlock) k_cell_beta(StepData<P> a) {
+    using V = typename P::V;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < a.nc; c += (int64_t)gridDim.x * blockDim.x) {
+        V S[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) S[k] = 0.0;
+        for (int k = 0; k < D; ++k) S[k] = 0;
 #pragma unroll
         for (int m = 0; m <= D; ++m) {
-            const size_t j = (size_t)__ldg(&cell_dof[c * (D + 1) + m]) * D;
+            const size_t j = (size_t)__ldg(&a.cell_dof[c * (D + 1) + m]) * D;
 #pragma unroll
-            for (int k = 0; k < D; ++k) S[k] += 1.5 * __ldg(&u1[j + k]) - 0.5 * __ldg(&u2[j + k]);
+            for (int k = 0; k < D; ++k) S[k] += (V)1.5 * s_v(a.u1[j + k]) - (V)0.5 * s_v(a.u2[j + k]);
         }
         V out[4];
 #pragma unroll
         for (int m = 0; m <= D; ++m) {
             V acc = 0;
 #pragma unroll
-            for (int k = 0; k < D; ++k) acc += __ldg(&gw[((size_t)c * (D + 1) + m) * D + k]) * (V)S[k];
+            for (int k = 0; k < D; ++k) acc += __ldg(&a.gw[((size_t)c * (D + 1) + m) * D + k]) * S[k];
             out[m] = acc;
         }
         if (D == 2) out[3] = 0;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) beta[c * 4 + m] = out[m];
+        for (int m = 0; m < 4; ++m) a.beta[c * 4 + m] = out[m];
     }
 }
 
-// Row pass of the convection assembly fused with Algorithm 2: for row i the
-// lanes of a group own the row's pattern entries; they collect the cell terms
-// beta from the incident cells (deterministic order, no atomics), add the
-// dP term, and form
-//   A_ij = M_ij/dt + C_ij/2 + nu K_ij/2                         (Eq. 34)
-//   r0_i = f_k ML_i - sum_j (C_ij + nu K_ij) u_k,j - sum_j dP^k_ij p*_j
-// which equals b_k - A u_k^{n-1} with b_k the right-hand side of Eq. 34
-// (b_k = f_k ML + (2M/dt - A) u^{n-1} - dP^k p*, Algorithm 2).  Dirichlet rows
-// become unit rows of A with r0 = g - u^{n-1}.
-template <class V, int D, int L>
-__global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs<V> a) {
-    constexpr int RPW = 32 / L;
-    const int lane = threadIdx.x % L;
-    const int sub = (threadIdx.x % 32) / L;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
-    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
-    double part[D];
+// Row pass of the convection assembly fused with Algorithm 2.  Per tile:
+//  A (thread per row): the cell terms beta of the incident cells are summed
+//    into a per-row, per-slot buffer in shared memory (increasing cell order,
+//    no atomics);
+//  B (entry-parallel): C_ij = t1 + ubar_i . dP_ij / (d+2),
+//    A_ij = M_ij/dt + C_ij/2 + nu K_ij/2 (Eq. 34), and the entry's share of
+//    -(C_ij + nu K_ij) u_j^{n-1} - dP^k_ij p*_j;
+//  C (thread per row): r0_i = f_k ML_i + sum of the shares, which is
+//    b_k - A u_k^{n-1} for b_k = f_k ML + (2M/dt - A) u^{n-1} - dP^k p*, the
+//    right-hand side formed by Algorithm 2.
+// Dirichlet rows become unit rows of A with r0 = g - u^{n-1}.
+template <class P, int D>
+__global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typename P::V> k_) {
+    using V = typename P::V;
+    using S = typename P::S;
+    using Acc = typename P::Acc;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    V* s_t1 = reinterpret_cast<V*>(dsm);                       // [max_row][kTile]
+    V* s_con = s_t1 + (size_t)a.max_row * kTile;               // [tile_cap][D]
+    __shared__ int32_t s_rp[kTile + 1];
+    __shared__ V s_ub[D][kTile];
+    __shared__ int32_t s_dir[kTile];
+    Acc part[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) part[k] = 0.0;
-    const V rdt = (V)(1.0 / a.dt), hnu = (V)(0.5 * a.nu), nu = (V)a.nu;
-    for (int64_t w = warp; w * RPW < a.n; w += nwarp) {
-        const int64_t i = w * RPW + sub;
-        V racc[D];
+    for (int k = 0; k < D; ++k) acc_zero(part[k]);
+    const V inv_d2 = (V)1 / (V)(D + 2);
+    const int r = threadIdx.x;
+    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
+        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
+        const int64_t i = T.r0 + r;
+        if (r < T.nr) {
+            const int32_t len = s_rp[r + 1] - s_rp[r];
+            for (int32_t sl = 0; sl < len; ++sl) s_t1[sl * kTile + r] = 0;
+            for (int32_t q = a.inc_ptr[i]; q < a.inc_ptr[i + 1]; ++q) {
+                const int32_t c = a.inc_cell[q];
+                const uint32_t w = a.inc_slots[q];
 #pragma unroll
-        for (int k = 0; k < D; ++k) racc[k] = 0;
-        int dir = -1;
-        if (i < a.n) {
-            const int32_t b = a.rp[i], len = a.rp[i + 1] - b;
-            const int32_t dslot = a.diag[i] - b;
-            dir = a.dir_index[i];
-            V ub[D];
-#pragma unroll
-            for (int k = 0; k < D; ++k) ub[k] = (V)(1.5 * a.u1[i * D + k] - 0.5 * a.u2[i * D + k]);
-            const int32_t q0 = a.inc_ptr[i], q1 = a.inc_ptr[i + 1];
-            for (int32_t s0 = 0; s0 < len; s0 += L) {
-                const int32_t s = s0 + lane;
-                const bool valid = s < len;
-                const uint32_t key = (uint32_t)s * 0x01010101u;
-                V t1 = 0;
-                for (int32_t q = q0; q < q1; ++q) {
-                    const uint32_t wd = __ldg(&a.inc_slots[q]);
-                    const uint32_t mt = __vcmpeq4(wd, key);
-                    if (valid && mt) {
-                        const int loc = (__ffs(mt) - 1) >> 3;
-                        t1 += __ldg(&a.beta[(size_t)__ldg(&a.inc_cell[q]) * 4 + loc]);
-                    }
-                }
-                if (valid) {
-                    const int32_t e = b + s;
-                    const int32_t j = a.col[e];
-                    V gdot = 0;
-                    V gv[D];
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        gv[k] = a.G[(size_t)k * a.nnz + e];
-                        gdot += ub[k] * gv[k];
-                    }
-                    const V c = t1 + gdot * (V)(1.0 / (D + 2));
-                    const V kv = a.K[e];
-                    V av = a.M[e] * rdt + (V)0.5 * c + hnu * kv;
-                    if (dir >= 0) av = (s == dslot) ? (V)1 : (V)0;
-                    a.A[e] = av;
-                    if (s == dslot) a.dinv[i] = (V)1 / av;
-                    const V ck = c + nu * kv;
-                    const double ps = a.pstar[j];
-#pragma unroll
-                    for (int k = 0; k < D; ++k) racc[k] -= ck * (V)a.u1[(size_t)j * D + k] + gv[k] * (V)ps;
-                }
+                for (int m = 0; m <= D; ++m) s_t1[((w >> (8 * m)) & 0xffu) * kTile + r] += a.beta[(size_t)c * 4 + m];
             }
-        }
 #pragma unroll
-        for (int k = 0; k < D; ++k) racc[k] = group_sum<L>(racc[k]);
-        if (i < a.n && lane == 0) {
+            for (int k = 0; k < D; ++k) s_ub[k][r] = (V)1.5 * s_v(a.u1[i * D + k]) - (V)0.5 * s_v(a.u2[i * D + k]);
+            s_dir[r] = a.dir_index[i];
+        }
+        __syncthreads();
+        for (int32_t e = T.e0 + r; e < T.e1; e += kTile) {
+            const int rr = tile_row_of(s_rp, T.nr, e);
+            const int32_t sl = e - s_rp[rr];
+            const int64_t ii = T.r0 + rr;
+            const int32_t j = a.col[e];
+            V gv[D], gdot = 0;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                double r = dir >= 0 ? a.g[(size_t)dir * D + k] - a.u1[i * D + k]
-                                    : a.f[k] * a.ML[i] + (double)racc[k];
-                a.r0[i * D + k] = r;
-                part[k] += r * r;
+                gv[k] = a.G[(size_t)k * a.nnz + e];
+                gdot += s_ub[k][rr] * gv[k];
+            }
+            const V c = s_t1[sl * kTile + rr] + gdot * inv_d2;
+            const V kv = a.K[e];
+            V av = a.M[e] * k_.rdt + (V)0.5 * c + k_.hnu * kv;
+            if (s_dir[rr] >= 0) av = (j == ii) ? (V)1 : (V)0;
+            a.A[e] = av;
+            if (j == ii) a.dinvA[ii] = (V)1 / av;
+            const V ck = c + k_.nu * kv;
+            const V ps = s_v(a.pstar[j]);
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                s_con[(size_t)(e - T.e0) * D + k] = -(ck * s_v(a.u1[(size_t)j * D + k]) + gv[k] * ps);
+        }
+        __syncthreads();
+        if (r < T.nr) {
+            const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
+            const int dir = s_dir[r];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                V acc = 0;
+                for (int32_t q = b0; q < b1; ++q) acc += s_con[(size_t)q * D + k];
+                S r0v;
+                if (dir >= 0) r0v = s_sub(a.g[(size_t)dir * D + k], a.u1[i * D + k]);
+                else r0v = s_addv(s_from(k_.f[k] * a.ML[i]), acc);
+                a.r0[i * D + k] = r0v;
+                a.du[i * D + k] = s_zero<S>();
+                const V rv = s_v(r0v);
+                acc_prod(part[k], rv, rv);
             }
         }
+        __syncthreads();
     }
-    if (grid_sum<D>(part, a.partial, &a.st->ticket) && threadIdx.x == 0) {
-        KrylovState* st = a.st;
+    double tot[D];
+    if (grid_sum<D, Acc>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0) {
+        KrylovState* st = a.stu;
         for (int k = 0; k < 3; ++k) {
-            st->bb[k] = k < D ? part[k] : 0.0;
+            st->bb[k] = k < D ? tot[k] : 0.0;
             st->col_done[k] = k < D ? 0 : 1;
             st->in_done[k] = 1;
             st->it_total[k] = 0;
-            st->rr[k] = k < D ? part[k] : 0.0;
+            st->rr[k] = k < D ? tot[k] : 0.0;
         }
         st->sweeps = 0;
         st->it_in = 0;
@@ -171,88 +194,90 @@ __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs<V> a) {
     }
 }
 
-// Zero Delta (the tentative correction, float64) before the solve.
-template <int D>
-__global__ void k_zero_du(int64_t n, double* du) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * D; t += (int64_t)gridDim.x * blockDim.x)
-        du[t] = 0.0;
-}
-
-// =====================================================================  BiCGStab
-// Right-preconditioned BiCGStab (van der Vorst), Jacobi M = diag(A), run per
-// column k on A Delta_k = r0_k, inside float64 refinement sweeps: every sweep
-// starts from the float64 residual r = r0 - A Delta and ends with Delta += delta.
+// ================================================================ BiCGStab
+// Right-preconditioned BiCGStab (van der Vorst 1992) with Jacobi M = diag(A),
+// per column k on A Delta_k = r0_k, inside refinement sweeps: every sweep starts
+// from the float64-quality residual r = r0 - A Delta and ends with Delta += delta.
 template <int NR>
-__device__ __forceinline__ void load_active(const KrylovState* st, int k0, int (&act)[NR], bool& any) {
-    any = false;
+__device__ __forceinline__ bool load_active(const KrylovState* st, int k0, int (&act)[NR]) {
+    bool any = false;
 #pragma unroll
     for (int c = 0; c < NR; ++c) {
         act[c] = !st->col_done[k0 + c] && !st->in_done[k0 + c];
         any |= act[c] != 0;
     }
+    return any;
 }
 
 template <int NR>
-__device__ __forceinline__ void publish_inner(KrylovState* st, int k0, const BicgCtl& ctl) {
+__device__ __forceinline__ int any_inner(const KrylovState* st, int k0) {
     int any = 0;
     for (int c = 0; c < NR; ++c) any |= (!st->col_done[k0 + c] && !st->in_done[k0 + c]);
-    set_cond(ctl.use_cond, ctl.h_inner, any);
+    return any;
 }
 
-// Outer sweep: float64 residual r = r0 - A Delta, convergence test, and start
-// of a new inner solve (r, rhat = r, p = v = delta = 0).
-template <class V, int D, int NR, int L>
-__global__ void __launch_bounds__(kBlock) k_bicg_outer(BicgArgs<V> a, BicgCtl ctl) {
-    constexpr int RPW = 32 / L;
-    const int lane = threadIdx.x % L, sub = (threadIdx.x % 32) / L;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
-    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
+__device__ __forceinline__ void mirror_coefs(KrylovState* st, int k) {
+    st->alpha_f[k] = (float)st->alpha[k];
+    st->omega_f[k] = (float)st->omega[k];
+    st->beta_f[k] = (float)st->beta[k];
+}
+
+// Outer sweep: r = r0 - A Delta with float64-quality products (float-float in
+// the mixed path), convergence test, start of a new inner solve.
+template <class P, int D, int NR>
+__global__ void __launch_bounds__(kBlock) k_bicg_outer(StepData<P> a, int k0, Ctl ctl) {
+    using V = typename P::V;
+    using S = typename P::S;
+    using Acc = typename P::Acc;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    Acc* s_prod = reinterpret_cast<Acc*>(dsm);                 // [tile_cap][NR]
+    __shared__ int32_t s_rp[kTile + 1];
     int live[NR];
 #pragma unroll
-    for (int c = 0; c < NR; ++c) live[c] = !a.st->col_done[a.k0 + c];
-    double part[2 * NR];
+    for (int c = 0; c < NR; ++c) live[c] = !a.stu->col_done[k0 + c];
+    Acc part[NR];
 #pragma unroll
-    for (int c = 0; c < 2 * NR; ++c) part[c] = 0.0;
-    for (int64_t w = warp; w * RPW < a.n; w += nwarp) {
-        const int64_t i = w * RPW + sub;
-        double acc[NR];
+    for (int c = 0; c < NR; ++c) acc_zero(part[c]);
+    const int r = threadIdx.x;
+    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
+        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
+        for (int32_t e = T.e0 + r; e < T.e1; e += kTile) {
+            const V av = a.A[e];
+            const size_t j = (size_t)a.col[e] * D + k0;
 #pragma unroll
-        for (int c = 0; c < NR; ++c) acc[c] = 0.0;
-        if (i < a.n) {
-            const int32_t b = a.rp[i], e = a.rp[i + 1];
-            for (int32_t q = b + lane; q < e; q += L) {
-                const double av = (double)a.A[q];
-                const size_t j = (size_t)a.col[q] * D + a.k0;
-#pragma unroll
-                for (int c = 0; c < NR; ++c) acc[c] += av * a.du[j + c];
-            }
+            for (int c = 0; c < NR; ++c) s_prod[(size_t)(e - T.e0) * NR + c] = acc_mul_sv(a.du[j + c], av);
         }
-#pragma unroll
-        for (int c = 0; c < NR; ++c) acc[c] = group_sum<L>(acc[c]);
-        if (i < a.n && lane == 0) {
+        __syncthreads();
+        if (r < T.nr) {
+            const int64_t i = T.r0 + r;
+            const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
 #pragma unroll
             for (int c = 0; c < NR; ++c) {
                 if (!live[c]) continue;
-                const size_t o = (size_t)i * D + a.k0 + c;
-                const double r = a.r0[o] - acc[c];
-                const V rv = (V)r;
+                Acc ax;
+                acc_zero(ax);
+                for (int32_t q = b0; q < b1; ++q) acc_add(ax, s_prod[(size_t)q * NR + c]);
+                const size_t o = (size_t)i * D + k0 + c;
+                const S rs = s_sub(a.r0[o], s_of_acc(ax));
+                const V rv = s_v(rs);
                 a.r[o] = rv;
                 a.rh[o] = rv;
                 a.p[o] = 0;
                 a.v[o] = 0;
                 a.dl[o] = 0;
-                part[c] += r * r;
-                part[NR + c] += (double)rv * (double)rv;
+                acc_prod(part[c], rv, rv);
             }
         }
+        __syncthreads();
     }
-    if (grid_sum<2 * NR>(part, a.partial, &a.st->ticket) && threadIdx.x == 0) {
-        KrylovState* st = a.st;
+    double tot[NR];
+    if (grid_sum<NR, Acc>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0) {
+        KrylovState* st = a.stu;
         int outer = 0;
         for (int c = 0; c < NR; ++c) {
-            const int k = a.k0 + c;
+            const int k = k0 + c;
             if (st->col_done[k]) continue;
-            const double rr = part[c];
+            const double rr = tot[c];
             st->rr[k] = rr;
             if (!isfinite(rr)) {
                 st->status = OASIS_ENAN;
@@ -268,38 +293,38 @@ __global__ void __launch_bounds__(kBlock) k_bicg_outer(BicgArgs<V> a, BicgCtl ct
                 st->alpha[k] = 1.0;
                 st->omega[k] = 1.0;
                 st->beta[k] = 0.0;
-                st->rho_new[k] = part[NR + c];
-                st->rr0_in[k] = part[NR + c];
-                st->rr_in[k] = part[NR + c];
+                mirror_coefs(st, k);
+                st->rho_new[k] = rr;
+                st->rr0_in[k] = rr;
+                st->rr_in[k] = rr;
                 outer = 1;
             }
         }
         st->sweeps += 1;
         st->it_in = 0;
         set_cond(ctl.use_cond, ctl.h_outer, outer);
-        publish_inner<NR>(st, a.k0, ctl);
+        set_cond(ctl.use_cond, ctl.h_inner, any_inner<NR>(st, k0));
     }
 }
 
 // p = r + beta (p - omega v),  ph = D^{-1} p
-template <class V, int D, int NR>
-__global__ void __launch_bounds__(kBlock) k_bicg_dir(BicgArgs<V> a) {
+template <class P, int D, int NR>
+__global__ void __launch_bounds__(kBlock) k_bicg_dir(StepData<P> a, int k0) {
+    using V = typename P::V;
     int act[NR];
-    bool any;
-    load_active<NR>(a.st, a.k0, act, any);
-    if (!any) return;
+    if (!load_active<NR>(a.stu, k0, act)) return;
     V beta[NR], omega[NR];
 #pragma unroll
     for (int c = 0; c < NR; ++c) {
-        beta[c] = (V)a.st->beta[a.k0 + c];
-        omega[c] = (V)a.st->omega[a.k0 + c];
+        beta[c] = coef<P>(a.stu->beta[k0 + c], a.stu->beta_f[k0 + c]);
+        omega[c] = coef<P>(a.stu->omega[k0 + c], a.stu->omega_f[k0 + c]);
     }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const V di = a.dinv[i];
+        const V di = a.dinvA[i];
 #pragma unroll
         for (int c = 0; c < NR; ++c) {
             if (!act[c]) continue;
-            const size_t o = (size_t)i * D + a.k0 + c;
+            const size_t o = (size_t)i * D + k0 + c;
             const V pv = a.r[o] + beta[c] * (a.p[o] - omega[c] * a.v[o]);
             a.p[o] = pv;
             a.ph[o] = di * pv;
@@ -307,96 +332,94 @@ __global__ void __launch_bounds__(kBlock) k_bicg_dir(BicgArgs<V> a) {
     }
 }
 
-// y = A x (x = ph or sh) with the dot products needed next:
+// y = A x with the dot products needed next:
 //   MODE 0: v = A ph, <rhat, v>          -> alpha = rho / <rhat, v>
 //   MODE 1: t = A sh, <t, s>, <t, t>     -> omega = <t, s> / <t, t>
-template <class V, int D, int NR, int L, int MODE>
-__global__ void __launch_bounds__(kBlock) k_bicg_spmm(BicgArgs<V> a, BicgCtl ctl) {
+template <class P, int D, int NR, int MODE>
+__global__ void __launch_bounds__(kBlock) k_bicg_spmm(StepData<P> a, int k0, Ctl ctl) {
+    using V = typename P::V;
+    using Acc = typename P::Acc;
     int act[NR];
-    bool any;
-    load_active<NR>(a.st, a.k0, act, any);
-    if (!any) return;
-    constexpr int RPW = 32 / L;
+    if (!load_active<NR>(a.stu, k0, act)) return;
     constexpr int NV = MODE == 0 ? NR : 2 * NR;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    V* s_prod = reinterpret_cast<V*>(dsm);                     // [tile_cap][NR]
+    __shared__ int32_t s_rp[kTile + 1];
     const V* __restrict__ x = MODE == 0 ? a.ph : a.sh;
     V* __restrict__ y = MODE == 0 ? a.v : a.t;
-    const int lane = threadIdx.x % L, sub = (threadIdx.x % 32) / L;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
-    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
-    double part[NV];
+    Acc part[NV];
 #pragma unroll
-    for (int c = 0; c < NV; ++c) part[c] = 0.0;
-    for (int64_t w = warp; w * RPW < a.n; w += nwarp) {
-        const int64_t i = w * RPW + sub;
-        V acc[NR];
+    for (int c = 0; c < NV; ++c) acc_zero(part[c]);
+    const int r = threadIdx.x;
+    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
+        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
+        for (int32_t e = T.e0 + r; e < T.e1; e += kTile) {
+            const V av = a.A[e];
+            const size_t j = (size_t)a.col[e] * D + k0;
 #pragma unroll
-        for (int c = 0; c < NR; ++c) acc[c] = 0;
-        if (i < a.n) {
-            const int32_t b = a.rp[i], e = a.rp[i + 1];
-            for (int32_t q = b + lane; q < e; q += L) {
-                const V av = a.A[q];
-                const size_t j = (size_t)a.col[q] * D + a.k0;
-#pragma unroll
-                for (int c = 0; c < NR; ++c) acc[c] += av * x[j + c];
-            }
+            for (int c = 0; c < NR; ++c) s_prod[(size_t)(e - T.e0) * NR + c] = av * x[j + c];
         }
-#pragma unroll
-        for (int c = 0; c < NR; ++c) acc[c] = group_sum<L>(acc[c]);
-        if (i < a.n && lane == 0) {
+        __syncthreads();
+        if (r < T.nr) {
+            const int64_t i = T.r0 + r;
+            const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
 #pragma unroll
             for (int c = 0; c < NR; ++c) {
                 if (!act[c]) continue;
-                const size_t o = (size_t)i * D + a.k0 + c;
-                y[o] = acc[c];
+                V acc = 0;
+                for (int32_t q = b0; q < b1; ++q) acc += s_prod[(size_t)q * NR + c];
+                const size_t o = (size_t)i * D + k0 + c;
+                y[o] = acc;
                 if (MODE == 0) {
-                    part[c] += (double)a.rh[o] * (double)acc[c];
+                    acc_prod(part[c], a.rh[o], acc);
                 } else {
-                    const double sv = (double)a.s[o];
-                    part[c] += (double)acc[c] * sv;
-                    part[NR + c] += (double)acc[c] * (double)acc[c];
+                    acc_prod(part[c], acc, a.s[o]);
+                    acc_prod(part[NR + c], acc, acc);
                 }
             }
         }
+        __syncthreads();
     }
-    if (grid_sum<NV>(part, a.partial, &a.st->ticket) && threadIdx.x == 0) {
-        KrylovState* st = a.st;
+    double tot[NV];
+    if (grid_sum<NV, Acc>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0) {
+        KrylovState* st = a.stu;
         for (int c = 0; c < NR; ++c) {
             if (!act[c]) continue;
-            const int k = a.k0 + c;
+            const int k = k0 + c;
             if (MODE == 0) {
-                const double rv = part[c];
+                const double rv = tot[c];
                 if (rv == 0.0 || !isfinite(rv)) {
-                    st->in_done[k] = 1;      // breakdown: restart from the float64 residual
+                    st->in_done[k] = 1;      // breakdown: restart from the float64-quality residual
                     st->it_total[k] += 1;    // counted, so that restarts end at the cap
                     st->alpha[k] = 0.0;
                 } else {
                     st->alpha[k] = st->rho_new[k] / rv;
                 }
             } else {
-                const double ts = part[c], tt = part[NR + c];
+                const double ts = tot[c], tt = tot[NR + c];
                 st->omega[k] = (tt > 0.0 && isfinite(tt)) ? ts / tt : 0.0;
             }
+            mirror_coefs(st, k);
         }
-        if (MODE == 0) publish_inner<NR>(st, a.k0, ctl);
+        if (MODE == 0) set_cond(ctl.use_cond, ctl.h_inner, any_inner<NR>(st, k0));
     }
 }
 
 // s = r - alpha v,  sh = D^{-1} s
-template <class V, int D, int NR>
-__global__ void __launch_bounds__(kBlock) k_bicg_s(BicgArgs<V> a) {
+template <class P, int D, int NR>
+__global__ void __launch_bounds__(kBlock) k_bicg_s(StepData<P> a, int k0) {
+    using V = typename P::V;
     int act[NR];
-    bool any;
-    load_active<NR>(a.st, a.k0, act, any);
-    if (!any) return;
+    if (!load_active<NR>(a.stu, k0, act)) return;
     V alpha[NR];
 #pragma unroll
-    for (int c = 0; c < NR; ++c) alpha[c] = (V)a.st->alpha[a.k0 + c];
+    for (int c = 0; c < NR; ++c) alpha[c] = coef<P>(a.stu->alpha[k0 + c], a.stu->alpha_f[k0 + c]);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const V di = a.dinv[i];
+        const V di = a.dinvA[i];
 #pragma unroll
         for (int c = 0; c < NR; ++c) {
             if (!act[c]) continue;
-            const size_t o = (size_t)i * D + a.k0 + c;
+            const size_t o = (size_t)i * D + k0 + c;
             const V sv = a.r[o] - alpha[c] * a.v[o];
             a.s[o] = sv;
             a.sh[o] = di * sv;
@@ -405,63 +428,65 @@ __global__ void __launch_bounds__(kBlock) k_bicg_s(BicgArgs<V> a) {
 }
 
 // delta += alpha ph + omega sh,  r = s - omega t,  <rhat, r>, <r, r>
-template <class V, int D, int NR>
-__global__ void __launch_bounds__(kBlock) k_bicg_xr(BicgArgs<V> a, BicgCtl ctl) {
+template <class P, int D, int NR>
+__global__ void __launch_bounds__(kBlock) k_bicg_xr(StepData<P> a, int k0, Ctl ctl) {
+    using V = typename P::V;
+    using Acc = typename P::Acc;
     int act[NR];
-    bool any;
-    load_active<NR>(a.st, a.k0, act, any);
-    if (!any) return;
+    if (!load_active<NR>(a.stu, k0, act)) return;
     V alpha[NR], omega[NR];
 #pragma unroll
     for (int c = 0; c < NR; ++c) {
-        alpha[c] = (V)a.st->alpha[a.k0 + c];
-        omega[c] = (V)a.st->omega[a.k0 + c];
+        alpha[c] = coef<P>(a.stu->alpha[k0 + c], a.stu->alpha_f[k0 + c]);
+        omega[c] = coef<P>(a.stu->omega[k0 + c], a.stu->omega_f[k0 + c]);
     }
-    double part[2 * NR];
+    Acc part[2 * NR];
 #pragma unroll
-    for (int c = 0; c < 2 * NR; ++c) part[c] = 0.0;
+    for (int c = 0; c < 2 * NR; ++c) acc_zero(part[c]);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < NR; ++c) {
             if (!act[c]) continue;
-            const size_t o = (size_t)i * D + a.k0 + c;
+            const size_t o = (size_t)i * D + k0 + c;
             a.dl[o] += alpha[c] * a.ph[o] + omega[c] * a.sh[o];
             const V rv = a.s[o] - omega[c] * a.t[o];
             a.r[o] = rv;
-            part[c] += (double)a.rh[o] * (double)rv;
-            part[NR + c] += (double)rv * (double)rv;
+            acc_prod(part[c], a.rh[o], rv);
+            acc_prod(part[NR + c], rv, rv);
         }
     }
-    if (grid_sum<2 * NR>(part, a.partial, &a.st->ticket) && threadIdx.x == 0) {
-        KrylovState* st = a.st;
+    double tot[2 * NR];
+    if (grid_sum<2 * NR, Acc>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0) {
+        KrylovState* st = a.stu;
         for (int c = 0; c < NR; ++c) {
             if (!act[c]) continue;
-            const int k = a.k0 + c;
-            const double rho_new = part[c], rr = part[NR + c];
+            const int k = k0 + c;
+            const double rho_new = tot[c], rr = tot[NR + c];
             st->it_total[k] += 1;
             const double om = st->omega[k];
             st->beta[k] = (st->rho_new[k] != 0.0 && om != 0.0) ? (rho_new / st->rho_new[k]) * (st->alpha[k] / om) : 0.0;
             st->rho[k] = st->rho_new[k];
             st->rho_new[k] = rho_new;
             st->rr_in[k] = rr;
-            const bool stop = !isfinite(rr) || rr <= ctl.inner2 * st->rr0_in[k] ||
-                              rr <= ctl.abs2 * st->bb[k] || om == 0.0 || rho_new == 0.0 ||
-                              st->it_total[k] >= ctl.max_it || st->it_in + 1 >= ctl.sweep_cap;
+            mirror_coefs(st, k);
+            const bool stop = !isfinite(rr) || rr <= ctl.inner2 * st->rr0_in[k] || rr <= ctl.abs2 * st->bb[k] ||
+                              om == 0.0 || rho_new == 0.0 || st->it_total[k] >= ctl.max_it ||
+                              st->it_in + 1 >= ctl.sweep_cap;
             if (stop) st->in_done[k] = 1;
         }
         st->it_in += 1;
-        publish_inner<NR>(st, a.k0, ctl);
+        set_cond(ctl.use_cond, ctl.h_inner, any_inner<NR>(st, k0));
     }
 }
 
-// Delta += delta (float64) for the columns refined in this sweep.
-template <class V, int D, int NR>
-__global__ void __launch_bounds__(kBlock) k_bicg_correct(BicgArgs<V> a) {
+// Delta += delta for the columns refined in this sweep.
+template <class P, int D, int NR>
+__global__ void __launch_bounds__(kBlock) k_bicg_correct(StepData<P> a, int k0) {
     int live[NR];
     bool any = false;
 #pragma unroll
     for (int c = 0; c < NR; ++c) {
-        live[c] = !a.st->col_done[a.k0 + c];
+        live[c] = !a.stu->col_done[k0 + c];
         any |= live[c] != 0;
     }
     if (!any) return;
@@ -469,44 +494,60 @@ __global__ void __launch_bounds__(kBlock) k_bicg_correct(BicgArgs<V> a) {
 #pragma unroll
         for (int c = 0; c < NR; ++c) {
             if (!live[c]) continue;
-            const size_t o = (size_t)i * D + a.k0 + c;
-            a.du[o] += (double)a.dl[o];
+            const size_t o = (size_t)i * D + k0 + c;
+            a.du[o] = s_addv(a.du[o], a.dl[o]);
         }
     }
 }
 
-// =====================================================================  pressure
-// b_phi_i = -(1/dt) sum_k sum_j dP^k_ij u_k,j^I, u^I = u^{n-1} + Delta (Sec. 5,
-// algebraic pressure equation); its mean is stored for the projection on
-// sum_i b_i = 0, and the pressure solve state is reset.
-template <class V, int D, int L>
-__global__ void __launch_bounds__(kBlock) k_pressure_rhs(PresArgs<V> a) {
-    constexpr int RPW = 32 / L;
-    const int lane = threadIdx.x % L, sub = (threadIdx.x % 32) / L;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
-    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
-    double part[1] = {0.0};
-    for (int64_t w = warp; w * RPW < a.n; w += nwarp) {
-        const int64_t i = w * RPW + sub;
-        V acc = 0;
-        if (i < a.n) {
-            const int32_t b = a.rp[i], e = a.rp[i + 1];
-            for (int32_t q = b + lane; q < e; q += L) {
-                const size_t j = (size_t)a.col[q] * D;
+// ================================================================ pressure
+// u^I = u^{n-1} + Delta rounded to the value type (for the divergence products).
+template <class P, int D>
+__global__ void __launch_bounds__(kBlock) k_make_uI(StepData<P> a) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.n * D; t += (int64_t)gridDim.x * blockDim.x)
+        a.uIv[t] = s_v(s_add(a.u1[t], a.du[t]));
+}
+
+// b_phi_i = -(1/dt) sum_k sum_j dP^k_ij u_k,j^I (Sec. 5, algebraic pressure
+// equation); its mean is stored for the projection on sum_i b_i = 0, and the
+// pressure solve state is reset.
+template <class P, int D>
+__global__ void __launch_bounds__(kBlock) k_pressure_rhs(StepData<P> a, Consts<typename P::V> k_) {
+    using V = typename P::V;
+    using Acc = typename P::Acc;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    V* s_prod = reinterpret_cast<V*>(dsm);
+    __shared__ int32_t s_rp[kTile + 1];
+    Acc part[1];
+    acc_zero(part[0]);
+    const int r = threadIdx.x;
+    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
+        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
+        for (int32_t e = T.e0 + r; e < T.e1; e += kTile) {
+            const size_t j = (size_t)a.col[e] * D;
+            V acc = 0;
 #pragma unroll
-                for (int k = 0; k < D; ++k) acc += a.G[(size_t)k * a.nnz + q] * (V)(a.u1[j + k] + a.du[j + k]);
-            }
+            for (int k = 0; k < D; ++k) acc += a.G[(size_t)k * a.nnz + e] * a.uIv[j + k];
+            s_prod[e - T.e0] = acc;
         }
-        acc = group_sum<L>(acc);
-        if (i < a.n && lane == 0) {
-            const double bi = -(double)acc / a.dt;
-            a.b[i] = bi;
-            part[0] += bi;
+        __syncthreads();
+        if (r < T.nr) {
+            const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
+            V acc = 0;
+            for (int32_t q = b0; q < b1; ++q) acc += s_prod[q];
+            const V bi = -acc * k_.rdt;
+            a.b[T.r0 + r] = s_from(bi);
+            acc_addv(part[0], bi);
         }
+        __syncthreads();
     }
-    if (grid_sum<1>(part, a.partial, &a.st->ticket) && threadIdx.x == 0) {
-        KrylovState* st = a.st;
-        st->mean = part[0] / (double)a.n;
+    double tot[1];
+    if (grid_sum<1, Acc>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
+        KrylovState* st = a.stp;
+        st->mean = tot[0] / (double)a.n;
+        const float mh = (float)st->mean;
+        st->mean_hi = mh;
+        st->mean_lo = (float)(st->mean - (double)mh);
         for (int k = 0; k < 3; ++k) {
             st->col_done[k] = k == 0 ? 0 : 1;
             st->in_done[k] = 1;
@@ -520,58 +561,90 @@ __global__ void __launch_bounds__(kBlock) k_pressure_rhs(PresArgs<V> a) {
 }
 
 // Initial guess for phi: 0 or the previous step's correction.
-__global__ void k_phi_guess(int64_t n, int mode, const double* __restrict__ prev, double* __restrict__ x) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = mode == OASIS_GUESS_PREV_PHI ? prev[i] : 0.0;
+template <class P>
+__global__ void k_phi_guess(StepData<P> a, int mode) {
+    using S = typename P::S;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
+        a.x[i] = mode == OASIS_GUESS_PREV_PHI ? a.phi_h1[i] : s_zero<S>();
 }
 
-// Outer sweep of the pressure CG: r = (b - mean b) - K x in float64 with the
-// float64 K; starts an inner float32/float64 CG (z = D^{-1} r, p = 0, delta = 0);
-// also accumulates sum_i (p*_i + x_i) for the normalisation of p.
-template <class V, int L>
-__global__ void __launch_bounds__(kBlock) k_pcg_outer(PcgArgs<V> a, BicgCtl ctl) {
-    constexpr int RPW = 32 / L;
-    const int lane = threadIdx.x % L, sub = (threadIdx.x % 32) / L;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
-    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
-    const bool live = !a.st->col_done[0];
-    const double mean = a.st->mean;
-    double part[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t w = warp; w * RPW < a.n; w += nwarp) {
-        const int64_t i = w * RPW + sub;
-        double acc = 0.0;
-        if (i < a.n) {
-            const int32_t b = a.rp[i], e = a.rp[i + 1];
-            for (int32_t q = b + lane; q < e; q += L) acc += a.K64[q] * a.x[a.col[q]];
-        }
-        acc = group_sum<L>(acc);
-        if (i < a.n && lane == 0) {
-            const double bi = a.b[i] - mean;
-            const double r = bi - acc;
-            const V rv = (V)r, zv = a.dinv[i] * rv;
+// mean of the pressure right-hand side (of_p = false) or of p = p* + phi
+// (of_p = true) as a state value
+template <class S>
+__device__ __forceinline__ S mean_s(const KrylovState* st, bool of_p);
+template <>
+__device__ __forceinline__ double mean_s<double>(const KrylovState* st, bool of_p) {
+    return of_p ? st->psum : st->mean;
+}
+template <>
+__device__ __forceinline__ float2 mean_s<float2>(const KrylovState* st, bool of_p) {
+    return of_p ? make_float2(st->meanp_hi, st->meanp_lo) : make_float2(st->mean_hi, st->mean_lo);
+}
+
+// Outer sweep of the pressure CG: r = (b - mean b) - K x with float64-quality
+// products (float64 K, or K split into float-float in the mixed path); starts an
+// inner CG (z = D^{-1} r, p = 0, delta = 0); also sums p* + x for the
+// normalisation of p and writes x rounded to the value type.
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_pcg_outer(StepData<P> a, Ctl ctl) {
+    using V = typename P::V;
+    using S = typename P::S;
+    using Acc = typename P::Acc;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    Acc* s_prod = reinterpret_cast<Acc*>(dsm);
+    __shared__ int32_t s_rp[kTile + 1];
+    const bool live = !a.stp->col_done[0];
+    const S mean = mean_s<S>(a.stp, false);
+    Acc part[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc_zero(part[k]);
+    const int r = threadIdx.x;
+    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
+        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
+        for (int32_t e = T.e0 + r; e < T.e1; e += kTile)
+            s_prod[e - T.e0] = acc_of_s(s_mul_s(a.Kout[e], a.x[a.col[e]]));
+        __syncthreads();
+        if (r < T.nr) {
+            const int64_t i = T.r0 + r;
+            const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
+            Acc kx;
+            acc_zero(kx);
+            for (int32_t q = b0; q < b1; ++q) acc_add(kx, s_prod[q]);
+            const S bi = s_sub(a.b[i], mean);
+            const S rs = s_sub(bi, s_of_acc(kx));
+            const V rv = s_v(rs), zv = a.dinvK[i] * rv;
+            const V xv = s_v(a.x[i]);
             if (live) {
-                a.r[i] = rv;
-                a.z[i] = zv;
-                a.p0[i] = 0;
-                a.p1[i] = 0;
-                a.dl[i] = 0;
+                a.pr[i] = rv;
+                a.pz[i] = zv;
+                a.pp0[i] = 0;
+                a.pp1[i] = 0;
+                a.pdl[i] = 0;
             }
-            part[0] += r * r;
-            part[1] += (double)rv * (double)zv;
-            part[2] += bi * bi;
-            part[3] += a.pstar[i] + a.x[i];
+            a.xv[i] = xv;
+            acc_prod(part[0], rv, rv);
+            acc_prod(part[1], rv, zv);
+            const V bv = s_v(bi);
+            acc_prod(part[2], bv, bv);
+            acc_addv(part[3], s_v(a.pstar[i]));
+            acc_addv(part[3], xv);
         }
+        __syncthreads();
     }
-    if (grid_sum<4>(part, a.partial, &a.st->ticket) && threadIdx.x == 0) {
-        KrylovState* st = a.st;
+    double tot[4];
+    if (grid_sum<4, Acc>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
+        KrylovState* st = a.stp;
         if (st->first) {
-            st->bb[0] = part[2];
+            st->bb[0] = tot[2];
             st->first = 0;
         }
-        st->psum = part[3];
+        const double meanp = tot[3] / (double)a.n;
+        st->psum = meanp;
+        st->meanp_hi = (float)meanp;
+        st->meanp_lo = (float)(meanp - (double)(float)meanp);
         int outer = 0;
         if (!st->col_done[0]) {
-            const double rr = part[0];
+            const double rr = tot[0];
             st->rr[0] = rr;
             if (!isfinite(rr)) {
                 st->status = OASIS_ENAN;
@@ -583,8 +656,9 @@ __global__ void __launch_bounds__(kBlock) k_pcg_outer(PcgArgs<V> a, BicgCtl ctl)
                 st->col_done[0] = 1;
             } else {
                 st->in_done[0] = 0;
-                st->rho[0] = part[1];
+                st->rho[0] = tot[1];
                 st->beta[0] = 0.0;
+                mirror_coefs(st, 0);
                 st->rr0_in[0] = rr;
                 outer = 1;
             }
@@ -598,39 +672,44 @@ __global__ void __launch_bounds__(kBlock) k_pcg_outer(PcgArgs<V> a, BicgCtl ctl)
 
 // q = K p_new with p_new = z + beta p_old formed on the fly (double-buffered by
 // the parity of the inner iteration), <p_new, q> -> alpha = rho / <p, q>.
-template <class V, int L>
-__global__ void __launch_bounds__(kBlock) k_pcg_q(PcgArgs<V> a, BicgCtl ctl) {
-    if (a.st->col_done[0] || a.st->in_done[0]) return;
-    constexpr int RPW = 32 / L;
-    const int lane = threadIdx.x % L, sub = (threadIdx.x % 32) / L;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
-    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
-    const int par = a.st->it_in & 1;
-    const V* __restrict__ pold = par ? a.p1 : a.p0;
-    V* __restrict__ pnew = par ? a.p0 : a.p1;
-    const V beta = (V)a.st->beta[0];
-    double part[1] = {0.0};
-    for (int64_t w = warp; w * RPW < a.n; w += nwarp) {
-        const int64_t i = w * RPW + sub;
-        V acc = 0;
-        if (i < a.n) {
-            const int32_t b = a.rp[i], e = a.rp[i + 1];
-            for (int32_t q = b + lane; q < e; q += L) {
-                const int32_t j = a.col[q];
-                acc += a.K[q] * (a.z[j] + beta * pold[j]);
-            }
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_pcg_q(StepData<P> a, Ctl ctl) {
+    using V = typename P::V;
+    using Acc = typename P::Acc;
+    if (a.stp->col_done[0] || a.stp->in_done[0]) return;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    V* s_prod = reinterpret_cast<V*>(dsm);
+    __shared__ int32_t s_rp[kTile + 1];
+    const int par = a.stp->it_in & 1;
+    const V* __restrict__ pold = par ? a.pp1 : a.pp0;
+    V* __restrict__ pnew = par ? a.pp0 : a.pp1;
+    const V beta = coef<P>(a.stp->beta[0], a.stp->beta_f[0]);
+    Acc part[1];
+    acc_zero(part[0]);
+    const int r = threadIdx.x;
+    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
+        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
+        for (int32_t e = T.e0 + r; e < T.e1; e += kTile) {
+            const int32_t j = a.col[e];
+            s_prod[e - T.e0] = a.K[e] * (a.pz[j] + beta * pold[j]);
         }
-        acc = group_sum<L>(acc);
-        if (i < a.n && lane == 0) {
-            const V pv = a.z[i] + beta * pold[i];
+        __syncthreads();
+        if (r < T.nr) {
+            const int64_t i = T.r0 + r;
+            const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
+            V q = 0;
+            for (int32_t k = b0; k < b1; ++k) q += s_prod[k];
+            const V pv = a.pz[i] + beta * pold[i];
             pnew[i] = pv;
-            a.q[i] = acc;
-            part[0] += (double)pv * (double)acc;
+            a.pq[i] = q;
+            acc_prod(part[0], pv, q);
         }
+        __syncthreads();
     }
-    if (grid_sum<1>(part, a.partial, &a.st->ticket) && threadIdx.x == 0) {
-        KrylovState* st = a.st;
-        const double pq = part[0];
+    double tot[1];
+    if (grid_sum<1, Acc>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
+        KrylovState* st = a.stp;
+        const double pq = tot[0];
         if (!(pq > 0.0) || !isfinite(pq)) {
             st->in_done[0] = 1;
             st->it_total[0] += 1;
@@ -639,33 +718,40 @@ __global__ void __launch_bounds__(kBlock) k_pcg_q(PcgArgs<V> a, BicgCtl ctl) {
         } else {
             st->alpha[0] = st->rho[0] / pq;
         }
+        mirror_coefs(st, 0);
     }
 }
 
 // delta += alpha p, r -= alpha q, z = D^{-1} r, <r, z> -> beta, <r, r> -> stop test
-template <class V>
-__global__ void __launch_bounds__(kBlock) k_pcg_update(PcgArgs<V> a, BicgCtl ctl) {
-    if (a.st->col_done[0] || a.st->in_done[0]) return;
-    const int par = a.st->it_in & 1;
-    const V* __restrict__ pnew = par ? a.p0 : a.p1;
-    const V alpha = (V)a.st->alpha[0];
-    double part[2] = {0.0, 0.0};
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_pcg_update(StepData<P> a, Ctl ctl) {
+    using V = typename P::V;
+    using Acc = typename P::Acc;
+    if (a.stp->col_done[0] || a.stp->in_done[0]) return;
+    const int par = a.stp->it_in & 1;
+    const V* __restrict__ pnew = par ? a.pp0 : a.pp1;
+    const V alpha = coef<P>(a.stp->alpha[0], a.stp->alpha_f[0]);
+    Acc part[2];
+    acc_zero(part[0]);
+    acc_zero(part[1]);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-        a.dl[i] += alpha * pnew[i];
-        const V rv = a.r[i] - alpha * a.q[i];
-        const V zv = a.dinv[i] * rv;
-        a.r[i] = rv;
-        a.z[i] = zv;
-        part[0] += (double)rv * (double)zv;
-        part[1] += (double)rv * (double)rv;
+        a.pdl[i] += alpha * pnew[i];
+        const V rv = a.pr[i] - alpha * a.pq[i];
+        const V zv = a.dinvK[i] * rv;
+        a.pr[i] = rv;
+        a.pz[i] = zv;
+        acc_prod(part[0], rv, zv);
+        acc_prod(part[1], rv, rv);
     }
-    if (grid_sum<2>(part, a.partial, &a.st->ticket) && threadIdx.x == 0) {
-        KrylovState* st = a.st;
-        const double rz = part[0], rr = part[1];
+    double tot[2];
+    if (grid_sum<2, Acc>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
+        KrylovState* st = a.stp;
+        const double rz = tot[0], rr = tot[1];
         st->it_total[0] += 1;
         st->beta[0] = st->rho[0] != 0.0 ? rz / st->rho[0] : 0.0;
         st->rho[0] = rz;
         st->rr_in[0] = rr;
+        mirror_coefs(st, 0);
         const bool stop = !isfinite(rr) || rr <= ctl.inner2 * st->rr0_in[0] || rr <= ctl.abs2 * st->bb[0] ||
                           rz == 0.0 || st->it_total[0] >= ctl.max_it || st->it_in + 1 >= ctl.sweep_cap;
         if (stop) st->in_done[0] = 1;
@@ -674,144 +760,232 @@ __global__ void __launch_bounds__(kBlock) k_pcg_update(PcgArgs<V> a, BicgCtl ctl
     }
 }
 
-template <class V>
-__global__ void __launch_bounds__(kBlock) k_pcg_correct(PcgArgs<V> a) {
-    if (a.st->col_done[0]) return;
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_pcg_correct(StepData<P> a) {
+    if (a.stp->col_done[0]) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
-        a.x[i] += (double)a.dl[i];
+        a.x[i] = s_addv(a.x[i], a.pdl[i]);
 }
 
-// =====================================================================  update
+// ================================================================ update
 // u_k^n = u_k^I - dt (dP^k phi)_i / ML_i (Sec. 5, lumping), Dirichlet rows = g;
 // p = p* + phi normalised to zero mean; rotation u^{n-2} <- u^{n-1} <- u^n,
 // p* <- p, and the history of normalised corrections.
-template <class V, int D, int L>
-__global__ void __launch_bounds__(kBlock) k_update(UpdArgs<V> a) {
-    constexpr int RPW = 32 / L;
-    const int lane = threadIdx.x % L, sub = (threadIdx.x % 32) / L;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
-    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
-    const double mean_p = a.stp->psum / (double)a.n;
-    for (int64_t w = warp; w * RPW < a.n; w += nwarp) {
-        const int64_t i = w * RPW + sub;
-        V acc[D];
+template <class P, int D>
+__global__ void __launch_bounds__(kBlock) k_update(StepData<P> a, Consts<typename P::V> k_) {
+    using V = typename P::V;
+    using S = typename P::S;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    V* s_prod = reinterpret_cast<V*>(dsm);                     // [tile_cap][D]
+    __shared__ int32_t s_rp[kTile + 1];
+    const S meanp = mean_s<S>(a.stp, true);
+    const int r = threadIdx.x;
+    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
+        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
+        for (int32_t e = T.e0 + r; e < T.e1; e += kTile) {
+            const V ph = a.xv[a.col[e]];
 #pragma unroll
-        for (int k = 0; k < D; ++k) acc[k] = 0;
-        if (i < a.n) {
-            const int32_t b = a.rp[i], e = a.rp[i + 1];
-            for (int32_t q = b + lane; q < e; q += L) {
-                const V ph = (V)a.x[a.col[q]];
-#pragma unroll
-                for (int k = 0; k < D; ++k) acc[k] += a.G[(size_t)k * a.nnz + q] * ph;
-            }
+            for (int k = 0; k < D; ++k) s_prod[(size_t)(e - T.e0) * D + k] = a.G[(size_t)k * a.nnz + e] * ph;
         }
-#pragma unroll
-        for (int k = 0; k < D; ++k) acc[k] = group_sum<L>(acc[k]);
-        if (i < a.n && lane == 0) {
+        __syncthreads();
+        if (r < T.nr) {
+            const int64_t i = T.r0 + r;
+            const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
             const int dir = a.dir_index[i];
-            const double iml = a.invML[i];
+            const V iml = a.invML[i];
 #pragma unroll
             for (int k = 0; k < D; ++k) {
+                V gp = 0;
+                for (int32_t q = b0; q < b1; ++q) gp += s_prod[(size_t)q * D + k];
                 const size_t o = (size_t)i * D + k;
-                const double u1 = a.u1[o];
-                double un = u1 + a.du[o] - a.dt * (double)acc[k] * iml;
+                const S u1 = a.u1[o];
+                S un = s_sub(s_add(u1, a.du[o]), s_from(k_.dt * gp * iml));
                 if (dir >= 0) un = a.g[(size_t)dir * D + k];
                 a.u2[o] = u1;
                 a.u1[o] = un;
             }
-            const double ps = a.pstar[i];
-            const double pn = ps + a.x[i] - mean_p;
-            const double ph = pn - ps;
+            const S ps = a.pstar[i];
+            const S pn = s_sub(s_add(ps, a.x[i]), meanp);
+            const S ph = s_sub(pn, ps);
             a.pstar[i] = pn;
-            a.phi_out[i] = ph;
+            a.phi[i] = ph;
             a.phi_h2[i] = a.phi_h1[i];
             a.phi_h1[i] = ph;
         }
+        __syncthreads();
     }
 }
 
-// =====================================================================  driver
-template <class V, int D, int L>
-struct StepImplT final : StepImpl {
-    Solver& S;
-    explicit StepImplT(Solver& s) : S(s) {}
+// ================================================================ conversions
+template <class P>
+__global__ void k_to_state(const double* __restrict__ src, typename P::S* __restrict__ dst, int64_t n, int comps) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * comps; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / comps;
+        const int k = (int)(t - i * comps);
+        dst[t] = s_of_double<typename P::S>(src[(int64_t)k * n + i]);
+    }
+}
+template <class P>
+__global__ void k_from_state(const typename P::S* __restrict__ src, double* __restrict__ dst, int64_t n, int comps) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * comps; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / comps;
+        const int k = (int)(t - i * comps);
+        dst[(int64_t)k * n + i] = s_to_double(src[t]);
+    }
+}
+template <class V>
+__global__ void k_v_to_double(const V* __restrict__ a, double* __restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
 
-    AsmArgs<V> asm_args() {
-        Mesh& m = *S.m;
-        AsmArgs<V> a{};
+// ================================================================ driver
+// The kernel's dynamic shared memory limit is raised to the device maximum (the
+// attribute is per kernel, shared by every solver of the process), and the
+// occupancy for this solver's actual size gives the grid.
+static int smem_optin() {
+    static int v = 0;
+    if (!v) {
+        int dev = 0;
+        OASIS_CUDA(cudaGetDevice(&dev));
+        OASIS_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    }
+    return v;
+}
+
+template <class K>
+static int tile_grid(K kernel, size_t smem, int64_t tiles) {
+    cudaFuncAttributes fa{};
+    OASIS_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    const size_t room = (size_t)smem_optin() - fa.sharedSizeBytes;
+    OASIS_CHECK(smem <= room, OASIS_EINVAL, "a row tile needs more shared memory than the device offers");
+    OASIS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room));
+    int per_sm = 0;
+    OASIS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, smem));
+    OASIS_CHECK(per_sm > 0, OASIS_EINVAL, "a row tile does not fit in shared memory");
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)per_sm * num_sms()));
+}
+
+static int elem_grid(int64_t items) {
+    const int64_t want = (items + kBlock - 1) / kBlock;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 8));
+}
+
+template <class P, int D>
+struct StepImplT final : StepImpl {
+    using V = typename P::V;
+    using S = typename P::S;
+    using Acc = typename P::Acc;
+    Solver& Sv;
+    StepData<P> a{};
+    Consts<V> k_{};
+    int64_t tiles = 0;
+    size_t sm_asm = 0, sm_out_u = 0, sm_out_u1 = 0, sm_spmm = 0, sm_spmm1 = 0, sm_outp = 0, sm_v1 = 0, sm_vd = 0;
+    int g_asm = 1, g_out_u = 1, g_out_u1 = 1, g_spmm0 = 1, g_spmm1 = 1, g_spmm0_1 = 1, g_spmm1_1 = 1, g_outp = 1,
+        g_q = 1, g_rhs = 1, g_upd = 1;
+    int ge_n = 1, ge_nd = 1, ge_c = 1;
+
+    template <class T>
+    static T* mat(const DBuf<double>& d, const DBuf<float>& f) {
+        if constexpr (sizeof(T) == 8) return (T*)(void*)d.p;
+        else return (T*)(void*)f.p;
+    }
+
+    explicit StepImplT(Solver& s) : Sv(s) {
+        Mesh& m = *Sv.m;
         a.rp = m.row_ptr.p;
         a.col = m.col.p;
         a.diag = m.diag.p;
         a.inc_ptr = m.inc_ptr.p;
         a.inc_cell = m.inc_cell.p;
+        a.cell_dof = m.cell_dof.p;
         a.inc_slots = m.inc_slots.p;
-        a.beta = S.template beta<V>();
-        a.M = S.template mat<V>(m.M64, m.M32);
-        a.K = S.template mat<V>(m.K64, m.K32);
-        a.G = S.template mat<V>(m.G64, m.G32);
-        a.ML = m.ML64.p;
-        a.u1 = S.u1.p;
-        a.u2 = S.u2.p;
-        a.pstar = S.pstar.p;
-        a.dir_index = S.dir_index.p;
-        a.g = S.g.p;
-        for (int k = 0; k < 3; ++k) a.f[k] = S.prm.f[k];
-        a.dt = S.prm.dt;
-        a.nu = S.prm.nu;
-        a.A = S.template A<V>();
-        a.dinv = S.template dinvA<V>();
-        a.r0 = S.r0u.p;
-        a.st = S.st.p;
-        a.partial = S.partial.p;
+        a.M = mat<V>(m.M64, m.M32);
+        a.K = mat<V>(m.K64, m.K32);
+        a.G = mat<V>(m.G64, m.G32);
+        a.gw = mat<V>(m.gw64, m.gw32);
+        a.ML = mat<V>(m.ML64, m.ML32);
+        a.dinvK = mat<V>(m.dinvK64, m.dinvK32);
+        a.invML = mat<V>(m.invML64, m.invML32);
+        if constexpr (P::mixed) a.Kout = reinterpret_cast<const S*>(m.Kff.p);
+        else a.Kout = reinterpret_cast<const S*>(m.K64.p);
+        a.u1 = Sv.u1.as<S>();
+        a.u2 = Sv.u2.as<S>();
+        a.du = Sv.du.as<S>();
+        a.r0 = Sv.r0.as<S>();
+        a.pstar = Sv.pstar.as<S>();
+        a.x = Sv.x.as<S>();
+        a.b = Sv.b.as<S>();
+        a.phi = Sv.phi.as<S>();
+        a.phi_h1 = Sv.phi_h1.as<S>();
+        a.phi_h2 = Sv.phi_h2.as<S>();
+        a.g = Sv.g.as<S>();
+        a.dir_index = Sv.dir_index.p;
+        a.A = Sv.A.as<V>();
+        a.dinvA = Sv.dinvA.as<V>();
+        a.beta = Sv.beta.as<V>();
+        V** w[9] = {&a.r, &a.rh, &a.p, &a.v, &a.s, &a.t, &a.ph, &a.sh, &a.dl};
+        for (int q = 0; q < 9; ++q) *w[q] = Sv.w[q].as<V>();
+        V** pw[7] = {&a.pr, &a.pz, &a.pp0, &a.pp1, &a.pq, &a.pdl, &a.xv};
+        for (int q = 0; q < 7; ++q) *pw[q] = Sv.pw[q].as<V>();
+        a.uIv = Sv.uIv.as<V>();
+        a.stu = Sv.st.p;
+        a.stp = Sv.st.p + 1;
+        a.partial = Sv.partial.p;
+        for (int k = 0; k < 3; ++k) a.f[k] = Sv.prm.f[k];
+        a.dt = Sv.prm.dt;
+        a.nu = Sv.prm.nu;
         a.n = m.n;
         a.nnz = m.nnz;
-        return a;
+        a.nc = m.nc;
+        a.max_row = m.max_row;
+        k_.rdt = (V)(1.0 / Sv.prm.dt);
+        k_.dt = (V)Sv.prm.dt;
+        k_.nu = (V)Sv.prm.nu;
+        k_.hnu = (V)(0.5 * Sv.prm.nu);
+        for (int k = 0; k < 3; ++k) k_.f[k] = (V)Sv.prm.f[k];
+
+        tiles = (m.n + kTile - 1) / kTile;
+        const size_t cap = (size_t)std::max(1, m.tile_cap);
+        sm_asm = (size_t)m.max_row * kTile * sizeof(V) + cap * D * sizeof(V);
+        sm_out_u = cap * D * sizeof(Acc);
+        sm_out_u1 = cap * sizeof(Acc);
+        sm_spmm = cap * D * sizeof(V);
+        sm_spmm1 = cap * sizeof(V);
+        sm_outp = cap * sizeof(Acc);
+        sm_v1 = cap * sizeof(V);
+        sm_vd = cap * D * sizeof(V);
+        g_asm = tile_grid(k_assemble<P, D>, sm_asm, tiles);
+        g_out_u = tile_grid(k_bicg_outer<P, D, D>, sm_out_u, tiles);
+        g_out_u1 = tile_grid(k_bicg_outer<P, D, 1>, sm_out_u1, tiles);
+        g_spmm0 = tile_grid(k_bicg_spmm<P, D, D, 0>, sm_spmm, tiles);
+        g_spmm1 = tile_grid(k_bicg_spmm<P, D, D, 1>, sm_spmm, tiles);
+        g_spmm0_1 = tile_grid(k_bicg_spmm<P, D, 1, 0>, sm_spmm1, tiles);
+        g_spmm1_1 = tile_grid(k_bicg_spmm<P, D, 1, 1>, sm_spmm1, tiles);
+        g_outp = tile_grid(k_pcg_outer<P>, sm_outp, tiles);
+        g_q = tile_grid(k_pcg_q<P>, sm_v1, tiles);
+        g_rhs = tile_grid(k_pressure_rhs<P, D>, sm_v1, tiles);
+        g_upd = tile_grid(k_update<P, D>, sm_vd, tiles);
+        ge_n = elem_grid(m.n);
+        ge_nd = elem_grid(m.n * D);
+        ge_c = elem_grid(m.nc);
     }
 
     void assemble(cudaStream_t s) override {
-        Mesh& m = *S.m;
-        k_cell_beta<V, D><<<grid_rows(m.nc, kBlock), kBlock, 0, s>>>(m.nc, m.cell_dof.p, S.template gw<V>(),
-                                                                      S.u1.p, S.u2.p, S.template beta<V>());
-        const int pa = S.prof_begin(s, OASIS_PROF_ASSEMBLE);
-        k_assemble<V, D, L><<<grid_rows(m.n, kBlock / L), kBlock, 0, s>>>(asm_args());
-        S.prof_end(s, pa);
-        k_zero_du<D><<<grid_rows(m.n * D, kBlock), kBlock, 0, s>>>(m.n, S.du.p);
+        k_cell_beta<P, D><<<ge_c, kBlock, 0, s>>>(a);
+        const int pa = Sv.prof_begin(s, OASIS_PROF_ASSEMBLE);
+        k_assemble<P, D><<<g_asm, kBlock, sm_asm, s>>>(a, k_);
+        Sv.prof_end(s, pa);
         OASIS_CUDA(cudaGetLastError());
     }
 
-    BicgArgs<V> bicg_args(int k0) {
-        Mesh& m = *S.m;
-        BicgArgs<V> a{};
-        a.rp = m.row_ptr.p;
-        a.col = m.col.p;
-        a.A = S.template A<V>();
-        a.dinv = S.template dinvA<V>();
-        a.r0 = S.r0u.p;
-        a.du = S.du.p;
-        V** w = S.template work<V>();
-        a.r = w[0];
-        a.rh = w[1];
-        a.p = w[2];
-        a.v = w[3];
-        a.s = w[4];
-        a.t = w[5];
-        a.ph = w[6];
-        a.sh = w[7];
-        a.dl = w[8];
-        a.st = S.st.p;
-        a.partial = S.partial.p;
-        a.n = m.n;
-        a.k0 = k0;
-        return a;
-    }
-
-    BicgCtl ctl_u(const Loop& lp) {
-        BicgCtl c{};
-        c.rtol2 = S.prm.rtol_u * S.prm.rtol_u;
-        c.inner2 = S.mixed ? S.prm.inner_rtol * S.prm.inner_rtol : 0.0;
+    Ctl ctl_u(const Loop& lp) const {
+        Ctl c{};
+        c.rtol2 = Sv.prm.rtol_u * Sv.prm.rtol_u;
+        c.inner2 = P::mixed ? Sv.prm.inner_rtol * Sv.prm.inner_rtol : 0.0;
         c.abs2 = 0.25 * c.rtol2;
-        c.max_it = S.prm.max_it_u;
-        c.sweep_cap = S.mixed ? 400 : 1 << 30;
+        c.max_it = Sv.prm.max_it_u;
+        c.sweep_cap = P::mixed ? 400 : (1 << 30);
         c.use_cond = lp.graph;
         c.h_outer = lp.h_outer;
         c.h_inner = lp.h_inner;
@@ -819,98 +993,50 @@ struct StepImplT final : StepImpl {
     }
 
     template <int NR>
-    void bicg_outer(cudaStream_t s, int k0, const Loop& lp) {
-        const int64_t n = S.m->n;
-        k_bicg_outer<V, D, NR, L><<<grid_rows(n, kBlock / L), kBlock, 0, s>>>(bicg_args(k0), ctl_u(lp));
-        OASIS_CUDA(cudaGetLastError());
-    }
-    template <int NR>
-    void bicg_iter(cudaStream_t s, int k0, const Loop& lp) {
-        const int64_t n = S.m->n;
-        const int ge = grid_rows(n, kBlock), gr = grid_rows(n, kBlock / L);
-        auto a = bicg_args(k0);
-        auto c = ctl_u(lp);
-        k_bicg_dir<V, D, NR><<<ge, kBlock, 0, s>>>(a);
-        int pb = S.prof_begin(s, OASIS_PROF_BICG_SPMM);
-        k_bicg_spmm<V, D, NR, L, 0><<<gr, kBlock, 0, s>>>(a, c);
-        S.prof_end(s, pb);
-        k_bicg_s<V, D, NR><<<ge, kBlock, 0, s>>>(a);
-        pb = S.prof_begin(s, OASIS_PROF_BICG_SPMM);
-        k_bicg_spmm<V, D, NR, L, 1><<<gr, kBlock, 0, s>>>(a, c);
-        S.prof_end(s, pb);
-        k_bicg_xr<V, D, NR><<<ge, kBlock, 0, s>>>(a, c);
-        OASIS_CUDA(cudaGetLastError());
-    }
-    template <int NR>
-    void bicg_correct(cudaStream_t s, int k0) {
-        k_bicg_correct<V, D, NR><<<grid_rows(S.m->n, kBlock), kBlock, 0, s>>>(bicg_args(k0));
-        OASIS_CUDA(cudaGetLastError());
-    }
-
-    template <int NR>
     void bicg_solve(cudaStream_t s, int k0, bool graph) {
-        S.run_loops(
-            s, graph, 0, [&](cudaStream_t ss, const Loop& lp) { bicg_outer<NR>(ss, k0, lp); },
-            [&](cudaStream_t ss, const Loop& lp) { bicg_iter<NR>(ss, k0, lp); },
-            [&](cudaStream_t ss, const Loop&) { bicg_correct<NR>(ss, k0); }, k0, NR);
+        const int go = NR == 1 ? g_out_u1 : g_out_u;
+        const size_t so = NR == 1 ? sm_out_u1 : sm_out_u;
+        const int gs0 = NR == 1 ? g_spmm0_1 : g_spmm0, gs1 = NR == 1 ? g_spmm1_1 : g_spmm1;
+        const size_t ss = NR == 1 ? sm_spmm1 : sm_spmm;
+        Sv.run_loops(
+            s, graph, 0,
+            [&](cudaStream_t ss_, const Loop& lp) {
+                k_bicg_outer<P, D, NR><<<go, kBlock, so, ss_>>>(a, k0, ctl_u(lp));
+                OASIS_CUDA(cudaGetLastError());
+            },
+            [&](cudaStream_t ss_, const Loop& lp) {
+                const Ctl c = ctl_u(lp);
+                k_bicg_dir<P, D, NR><<<ge_n, kBlock, 0, ss_>>>(a, k0);
+                int pb = Sv.prof_begin(ss_, OASIS_PROF_BICG_SPMM);
+                k_bicg_spmm<P, D, NR, 0><<<gs0, kBlock, ss, ss_>>>(a, k0, c);
+                Sv.prof_end(ss_, pb);
+                k_bicg_s<P, D, NR><<<ge_n, kBlock, 0, ss_>>>(a, k0);
+                pb = Sv.prof_begin(ss_, OASIS_PROF_BICG_SPMM);
+                k_bicg_spmm<P, D, NR, 1><<<gs1, kBlock, ss, ss_>>>(a, k0, c);
+                Sv.prof_end(ss_, pb);
+                k_bicg_xr<P, D, NR><<<ge_n, kBlock, 0, ss_>>>(a, k0, c);
+                OASIS_CUDA(cudaGetLastError());
+            },
+            [&](cudaStream_t ss_, const Loop&) {
+                k_bicg_correct<P, D, NR><<<ge_n, kBlock, 0, ss_>>>(a, k0);
+                OASIS_CUDA(cudaGetLastError());
+            },
+            k0, NR);
     }
 
     void tentative_solve(cudaStream_t s, bool graph) override {
-        if (S.prm.batch_rhs) {
-            bicg_solve<D>(s, 0, graph);
-        } else {
+        if (Sv.prm.batch_rhs) bicg_solve<D>(s, 0, graph);
+        else
             for (int k = 0; k < D; ++k) bicg_solve<1>(s, k, graph);
-        }
     }
 
-    PresArgs<V> pres_args() {
-        Mesh& m = *S.m;
-        PresArgs<V> a{};
-        a.rp = m.row_ptr.p;
-        a.col = m.col.p;
-        a.G = S.template mat<V>(m.G64, m.G32);
-        a.u1 = S.u1.p;
-        a.du = S.du.p;
-        a.b = S.bphi.p;
-        a.dt = S.prm.dt;
-        a.st = S.st.p + 1;
-        a.partial = S.partial.p;
-        a.n = m.n;
-        a.nnz = m.nnz;
-        return a;
-    }
-
-    PcgArgs<V> pcg_args() {
-        Mesh& m = *S.m;
-        PcgArgs<V> a{};
-        a.rp = m.row_ptr.p;
-        a.col = m.col.p;
-        a.K = S.template mat<V>(m.K64, m.K32);
-        a.K64 = m.K64.p;
-        a.dinv = S.mixed ? (const V*)(const void*)m.dinvK32.p : (const V*)(const void*)m.dinvK64.p;
-        a.b = S.bphi.p;
-        a.x = S.xp.p;
-        a.pstar = S.pstar.p;
-        V** w = S.template pwork<V>();
-        a.r = w[0];
-        a.z = w[1];
-        a.p0 = w[2];
-        a.p1 = w[3];
-        a.q = w[4];
-        a.dl = w[5];
-        a.st = S.st.p + 1;
-        a.partial = S.partial.p;
-        a.n = m.n;
-        return a;
-    }
-
-    BicgCtl ctl_p(const Loop& lp) {
-        BicgCtl c{};
-        c.rtol2 = S.prm.rtol_p * S.prm.rtol_p;
-        c.inner2 = S.mixed ? S.prm.inner_rtol * S.prm.inner_rtol : 0.0;
+    Ctl ctl_p(const Loop& lp) const {
+        Ctl c{};
+        c.rtol2 = Sv.prm.rtol_p * Sv.prm.rtol_p;
+        c.inner2 = P::mixed ? Sv.prm.inner_rtol * Sv.prm.inner_rtol : 0.0;
         c.abs2 = 0.25 * c.rtol2;
-        c.max_it = S.prm.max_it_p;
-        c.sweep_cap = S.mixed ? 4000 : 1 << 30;
+        c.max_it = Sv.prm.max_it_p;
+        c.sweep_cap = P::mixed ? 4000 : (1 << 30);
         c.use_cond = lp.graph;
         c.h_outer = lp.h_outer;
         c.h_inner = lp.h_inner;
@@ -918,80 +1044,76 @@ struct StepImplT final : StepImpl {
     }
 
     void pressure_solve(cudaStream_t s, bool graph) override {
-        Mesh& m = *S.m;
-        const int64_t n = m.n;
-        const int ge = grid_rows(n, kBlock), gr = grid_rows(n, kBlock / L);
-        const int pr = S.prof_begin(s, OASIS_PROF_PRESSURE_RHS);
-        k_pressure_rhs<V, D, L><<<gr, kBlock, 0, s>>>(pres_args());
-        S.prof_end(s, pr);
-        const int mode = S.prm.guess == OASIS_GUESS_PREV_PHI ? OASIS_GUESS_PREV_PHI : OASIS_GUESS_ZERO;
-        k_phi_guess<<<ge, kBlock, 0, s>>>(n, mode, S.phi_h1.p, S.xp.p);
+        k_make_uI<P, D><<<ge_nd, kBlock, 0, s>>>(a);
+        const int pr = Sv.prof_begin(s, OASIS_PROF_PRESSURE_RHS);
+        k_pressure_rhs<P, D><<<g_rhs, kBlock, sm_v1, s>>>(a, k_);
+        Sv.prof_end(s, pr);
+        const int mode = Sv.prm.guess == OASIS_GUESS_PREV_PHI ? OASIS_GUESS_PREV_PHI : OASIS_GUESS_ZERO;
+        k_phi_guess<P><<<ge_n, kBlock, 0, s>>>(a, mode);
         OASIS_CUDA(cudaGetLastError());
-        S.run_loops(
+        Sv.run_loops(
             s, graph, 1,
             [&](cudaStream_t ss, const Loop& lp) {
-                k_pcg_outer<V, L><<<gr, kBlock, 0, ss>>>(pcg_args(), ctl_p(lp));
+                k_pcg_outer<P><<<g_outp, kBlock, sm_outp, ss>>>(a, ctl_p(lp));
                 OASIS_CUDA(cudaGetLastError());
             },
             [&](cudaStream_t ss, const Loop& lp) {
-                auto a = pcg_args();
-                auto c = ctl_p(lp);
-                const int pq = S.prof_begin(ss, OASIS_PROF_PCG_SPMV);
-                k_pcg_q<V, L><<<gr, kBlock, 0, ss>>>(a, c);
-                S.prof_end(ss, pq);
-                const int pu = S.prof_begin(ss, OASIS_PROF_PCG_UPDATE);
-                k_pcg_update<V><<<ge, kBlock, 0, ss>>>(a, c);
-                S.prof_end(ss, pu);
+                const Ctl c = ctl_p(lp);
+                const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
+                k_pcg_q<P><<<g_q, kBlock, sm_v1, ss>>>(a, c);
+                Sv.prof_end(ss, pq);
+                const int pu = Sv.prof_begin(ss, OASIS_PROF_PCG_UPDATE);
+                k_pcg_update<P><<<ge_n, kBlock, 0, ss>>>(a, c);
+                Sv.prof_end(ss, pu);
                 OASIS_CUDA(cudaGetLastError());
             },
             [&](cudaStream_t ss, const Loop&) {
-                k_pcg_correct<V><<<ge, kBlock, 0, ss>>>(pcg_args());
+                k_pcg_correct<P><<<ge_n, kBlock, 0, ss>>>(a);
                 OASIS_CUDA(cudaGetLastError());
             },
             0, 1);
     }
 
     void update(cudaStream_t s) override {
-        Mesh& m = *S.m;
-        UpdArgs<V> a{};
-        a.rp = m.row_ptr.p;
-        a.col = m.col.p;
-        a.G = S.template mat<V>(m.G64, m.G32);
-        a.invML = m.invML64.p;
-        a.x = S.xp.p;
-        a.du = S.du.p;
-        a.u1 = S.u1.p;
-        a.u2 = S.u2.p;
-        a.pstar = S.pstar.p;
-        a.phi_out = S.phi.p;
-        a.phi_h1 = S.phi_h1.p;
-        a.phi_h2 = S.phi_h2.p;
-        a.dir_index = S.dir_index.p;
-        a.g = S.g.p;
-        a.dt = S.prm.dt;
-        a.stp = S.st.p + 1;
-        a.n = m.n;
-        a.nnz = m.nnz;
-        const int pu = S.prof_begin(s, OASIS_PROF_UPDATE);
-        k_update<V, D, L><<<grid_rows(m.n, kBlock / L), kBlock, 0, s>>>(a);
-        S.prof_end(s, pu);
+        const int pu = Sv.prof_begin(s, OASIS_PROF_UPDATE);
+        k_update<P, D><<<g_upd, kBlock, sm_vd, s>>>(a, k_);
+        Sv.prof_end(s, pu);
+        OASIS_CUDA(cudaGetLastError());
+    }
+
+    S* state_ptr(int which) {
+        switch (which) {
+            case ST_U1: return a.u1;
+            case ST_U2: return a.u2;
+            case ST_PSTAR: return a.pstar;
+            case ST_PHI: return a.phi;
+            case ST_G: return const_cast<S*>(a.g);
+            case ST_R0: return a.r0;
+            default: throw Error(OASIS_EINVAL, "unknown state buffer");
+        }
+    }
+
+    void to_state(cudaStream_t s, const double* src, int which, int64_t count, int comps) override {
+        k_to_state<P><<<elem_grid(count * comps), kBlock, 0, s>>>(src, state_ptr(which), count, comps);
+        OASIS_CUDA(cudaGetLastError());
+    }
+    void from_state(cudaStream_t s, double* dst, int which, int64_t count, int comps) override {
+        k_from_state<P><<<elem_grid(count * comps), kBlock, 0, s>>>(state_ptr(which), dst, count, comps);
+        OASIS_CUDA(cudaGetLastError());
+    }
+    void a_to_double(cudaStream_t s, double* dst) override {
+        k_v_to_double<V><<<elem_grid(a.nnz), kBlock, 0, s>>>(a.A, dst, a.nnz);
         OASIS_CUDA(cudaGetLastError());
     }
 };
 
-template <class V, int D>
-static StepImpl* make_impl_l(Solver& s, int L) {
-    switch (L) {
-        case 8: return new StepImplT<V, D, 8>(s);
-        case 16: return new StepImplT<V, D, 16>(s);
-        default: throw Error(OASIS_EINVAL, "step kernels support 8 or 16 lanes per row");
+StepImpl* make_step_impl(Solver& s) {
+    if (s.m->dim == 2) {
+        if (s.mixed) return new StepImplT<Mixed, 2>(s);
+        return new StepImplT<Fp64, 2>(s);
     }
-}
-
-StepImpl* make_step_impl(Solver& s, int lanes) {
-    const bool mixed = s.mixed;
-    if (s.m->dim == 2) return mixed ? make_impl_l<float, 2>(s, lanes) : make_impl_l<double, 2>(s, lanes);
-    return mixed ? make_impl_l<float, 3>(s, lanes) : make_impl_l<double, 3>(s, lanes);
+    if (s.mixed) return new StepImplT<Mixed, 3>(s);
+    return new StepImplT<Fp64, 3>(s);
 }
 
 }  // namespace oasis
