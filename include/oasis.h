@@ -152,6 +152,15 @@ int oasis_spmv_f64(const oasis_mesh* mesh, int32_t which, const double* x, doubl
 int oasis_spmv_f32(const oasis_mesh* mesh, int32_t which, const float* x, float* y,
                    int32_t lanes, void* stream);
 
+/* y = Mat x and *xy = x . y in float64 (for K this is the energy product p . K p
+ * of the CG iteration, Sec. 6 solvers), on device vectors of length n_dofs; xy
+ * is one double in device memory.  Row tiles of 256 rows, one partial sum per
+ * tile in scratch owned by the mesh (allocated by oasis_assemble_constant), and
+ * a deterministic final sum in tile order.  Calls on one mesh must not overlap
+ * on the GPU (they share that scratch). */
+int oasis_spmv_dot_f64(const oasis_mesh* mesh, int32_t which, const double* x, double* y, double* xy,
+                       void* stream);
+
 /* Create a solver on an assembled mesh.
  *   dirichlet_dofs host, [n_dirichlet] distinct dofs carrying velocity Dirichlet
  *                  values (the same set for every component, Sec. 5 after Eq. 35)

@@ -345,6 +345,17 @@ int oasis_spmv_f32(const oasis_mesh* mesh, int32_t which, const float* x, float*
     });
 }
 
+int oasis_spmv_dot_f64(const oasis_mesh* mesh, int32_t which, const double* x, double* y, double* xy,
+                       void* stream) {
+    return guarded([&] {
+        const Mesh* m = reinterpret_cast<const Mesh*>(mesh);
+        OASIS_CHECK(m && x && y && xy, OASIS_EINVAL, "null pointer");
+        OASIS_CHECK(m->assembled, OASIS_EINVAL, "mesh not assembled");
+        spmv_dot_f64(*m, (const double*)const_matrix(m, which, false), x, y, xy, m->red_partial.p, m->red_ticket.p,
+                     as_stream(stream));
+    });
+}
+
 int oasis_solver_create(oasis_mesh* mesh, const oasis_params* params, int64_t n_dirichlet,
                         const int32_t* dirichlet_dofs, void* stream, oasis_solver** out) {
     return guarded([&] {

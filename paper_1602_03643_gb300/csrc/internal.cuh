@@ -85,6 +85,8 @@ struct Mesh {
     DBuf<float> ML32, invML32, dinvK32;
     DBuf<float2> Kff;                          // K as float-float (hi, lo)
     int tile_cap = 0;                          // max entries of a 256-row tile
+    DBuf<double> red_partial;                  // one partial sum per 256-row tile
+    DBuf<uint32_t> red_ticket;
     DBuf<int32_t> err;                         // device error flag for setup kernels
     bool assembled = false;
 };
@@ -118,6 +120,8 @@ struct Solver;
 // Kernels and launchers (step.cu)
 void spmv_f64(const Mesh& m, const double* vals, const double* x, double* y, int lanes, cudaStream_t s);
 void spmv_f32(const Mesh& m, const float* vals, const float* x, float* y, int lanes, cudaStream_t s);
+void spmv_dot_f64(const Mesh& m, const double* vals, const double* x, double* y, double* xy, double* tile_partial,
+                  uint32_t* ticket, cudaStream_t s);
 
 int num_sms();
 

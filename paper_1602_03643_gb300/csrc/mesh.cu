@@ -333,6 +333,9 @@ void assemble_constant(Mesh& m, cudaStream_t s) {
     k_to_f32<<<grid_for(m.nnz), kBlock, 0, s>>>(m.nnz, m.K64.p, m.K32.p);
     k_to_f32<<<grid_for((int64_t)D * m.nnz), kBlock, 0, s>>>((int64_t)D * m.nnz, m.G64.p, m.G32.p);
     OASIS_CUDA(cudaGetLastError());
+    m.red_partial.alloc((size_t)((m.n + kBlock - 1) / kBlock));
+    m.red_ticket.alloc(1);
+    OASIS_CUDA(cudaMemsetAsync(m.red_ticket.p, 0, sizeof(uint32_t), s));
     OASIS_CUDA(cudaStreamSynchronize(s));
     m.assembled = true;
 }
@@ -374,6 +377,78 @@ static void spmv_launch(const Mesh& m, const V* vals, const V* x, V* y, int lane
         case 32: k_spmv<V, 32><<<g, kBlock, 0, s>>>(m.n, m.row_ptr.p, m.col.p, vals, x, y); break;
         default: throw Error(OASIS_EINVAL, "lanes must be 4, 8, 16 or 32");
     }
+    OASIS_CUDA(cudaGetLastError());
+}
+
+// y = Mat x and x . y in float64 with 256-row tiles: an entry-parallel product
+// phase into shared memory, a thread-per-row sum, one partial sum per tile in
+// `tile_partial`, and a deterministic final sum (in tile order) by the block
+// that takes the last ticket.  `ticket` must be zero at launch; it is left zero.
+__global__ void __launch_bounds__(kBlock) k_spmv_dot_tiles(int64_t n, const int32_t* __restrict__ rp,
+                                                           const int32_t* __restrict__ col,
+                                                           const double* __restrict__ val,
+                                                           const double* __restrict__ x, double* __restrict__ y,
+                                                           double* __restrict__ tile_partial, uint32_t* ticket,
+                                                           double* __restrict__ xy) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    double* s_prod = reinterpret_cast<double*>(dsm);
+    __shared__ int32_t s_rp[kBlock + 1];
+    const int64_t ntiles = (n + kBlock - 1) / kBlock;
+    const int r = threadIdx.x;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * kBlock;
+        const int nr = (int)min((int64_t)kBlock, n - r0);
+        for (int k = r; k <= nr; k += blockDim.x) s_rp[k] = rp[r0 + k];
+        __syncthreads();
+        const int32_t e0 = s_rp[0], e1 = s_rp[nr];
+        for (int32_t e = e0 + r; e < e1; e += kBlock) s_prod[e - e0] = val[e] * x[col[e]];
+        __syncthreads();
+        double v[1] = {0.0};
+        if (r < nr) {
+            double acc = 0.0;
+            for (int32_t q = s_rp[r] - e0; q < s_rp[r + 1] - e0; ++q) acc += s_prod[q];
+            y[r0 + r] = acc;
+            v[0] = x[r0 + r] * acc;
+        }
+        block_sum<1>(v);
+        if (r == 0) tile_partial[tile] = v[0];
+        __syncthreads();
+    }
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s[1] = {0.0};
+    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) s[0] += __ldcg(&tile_partial[t]);
+    block_sum<1>(s);
+    if (threadIdx.x == 0) {
+        *xy = s[0];
+        *ticket = 0u;
+    }
+}
+
+void spmv_dot_f64(const Mesh& m, const double* vals, const double* x, double* y, double* xy, double* tile_partial,
+                  uint32_t* ticket, cudaStream_t s) {
+    const int64_t ntiles = (m.n + kBlock - 1) / kBlock;
+    const size_t smem = (size_t)std::max(1, m.tile_cap) * sizeof(double);
+    static int room = 0;
+    if (!room) {
+        int dev = 0, optin = 0;
+        OASIS_CUDA(cudaGetDevice(&dev));
+        OASIS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        cudaFuncAttributes fa{};
+        OASIS_CUDA(cudaFuncGetAttributes(&fa, k_spmv_dot_tiles));
+        room = optin - (int)fa.sharedSizeBytes;
+        OASIS_CUDA(cudaFuncSetAttribute(k_spmv_dot_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, room));
+    }
+    OASIS_CHECK(smem <= (size_t)room, OASIS_EINVAL, "a row tile needs more shared memory than the device offers");
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * 4));
+    OASIS_CUDA(cudaMemsetAsync(ticket, 0, sizeof(uint32_t), s));
+    k_spmv_dot_tiles<<<grid, kBlock, smem, s>>>(m.n, m.row_ptr.p, m.col.p, vals, x, y, tile_partial, ticket, xy);
     OASIS_CUDA(cudaGetLastError());
 }
 

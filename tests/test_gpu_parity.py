@@ -100,6 +100,29 @@ def test_spmv_f64_f32(lanes):
         c.oasis_mesh_destroy(h)
 
 
+@pytest.mark.parametrize("name", ["jitter_6", "random_perm", "sq_7x5"])
+def test_spmv_dot_f64(name):
+    import torch
+    c = capi()
+    m = MESHES[name]()
+    D = p1.Discretization(m)
+    h = c.oasis_mesh_create(m.dim, m.coords, m.cells, m.dof_of_vertex, m.n_dofs)
+    try:
+        c.oasis_assemble_constant(h)
+        x = np.random.default_rng(3).normal(size=m.n_dofs)
+        xd = torch.tensor(x, device="cuda")
+        yd = torch.empty_like(xd)
+        xy = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            c.oasis_spmv_dot_f64(h, c.OASIS_MAT_K, xd, yd, xy)
+            torch.cuda.synchronize()
+            want = D.K @ x
+            np.testing.assert_allclose(yd.cpu().numpy(), want, rtol=0, atol=1e-13 * np.abs(want).max())
+            assert abs(xy.item() - x @ want) <= 1e-12 * abs(x) @ abs(want)
+    finally:
+        c.oasis_mesh_destroy(h)
+
+
 def _perturbed_state(pb, seed=5):
     """Make u^{n-2} differ from u^{n-1} so that ubar exercises both."""
     rng = np.random.default_rng(seed)
