@@ -161,6 +161,23 @@ int oasis_spmv_f32(const oasis_mesh* mesh, int32_t which, const float* x, float*
 int oasis_spmv_dot_f64(const oasis_mesh* mesh, int32_t which, const double* x, double* y, double* xy,
                        void* stream);
 
+/* The same product and dot as oasis_spmv_dot_f64, for callers that cannot
+ * allocate device memory (code that runs under a caller-owned memory pool, inside
+ * an allocator, or on a device whose memory is already committed): this call
+ * allocates nothing.  The paper has no counterpart; it is a deployment variant.
+ *   - Its reduction scratch is a file-scope __device__ array of 516 KiB that
+ *     every GPU loading the library holds until process exit; it limits n_dofs
+ *     to 16,777,216 (65,536 tiles of 256 rows).  Larger meshes: OASIS_EINVAL.
+ *   - The first call on a device resolves the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call on every mesh shares the one array, and it keeps the last
+ *     call's contents (the ticket word that must start at zero is cleared by
+ *     each call, on `stream`).  Calls that overlap on the GPU race: order them
+ *     on one stream or synchronise between them. */
+int oasis_spmv_dot_f64_noalloc(const oasis_mesh* mesh, int32_t which, const double* x, double* y, double* xy,
+                               void* stream);
+
 /* Create a solver on an assembled mesh.
  *   dirichlet_dofs host, [n_dirichlet] distinct dofs carrying velocity Dirichlet
  *                  values (the same set for every component, Sec. 5 after Eq. 35)

@@ -78,6 +78,7 @@ SIGNATURES = {
     "oasis_spmv_f64": (C.c_int, [P, I32, DPTR, DPTR, I32, P]),
     "oasis_spmv_f32": (C.c_int, [P, I32, DPTR, DPTR, I32, P]),
     "oasis_spmv_dot_f64": (C.c_int, [P, I32, DPTR, DPTR, DPTR, P]),
+    "oasis_spmv_dot_f64_noalloc": (C.c_int, [P, I32, DPTR, DPTR, DPTR, P]),
     "oasis_solver_create": (C.c_int, [P, C.POINTER(oasis_params), I64, DPTR, P, PP]),
     "oasis_set_fields": (C.c_int, [P, DPTR, DPTR, DPTR, C.c_double, I32, P]),
     "oasis_set_dirichlet": (C.c_int, [P, DPTR, I32, P]),
@@ -183,6 +184,10 @@ def oasis_spmv_f32(mesh, which, x, y, lanes=0, stream=None):
 
 def oasis_spmv_dot_f64(mesh, which, x, y, xy, stream=None):
     check(lib().oasis_spmv_dot_f64(mesh, which, _ptr(x), _ptr(y), _ptr(xy), _stream(stream)))
+
+
+def oasis_spmv_dot_f64_noalloc(mesh, which, x, y, xy, stream=None):
+    check(lib().oasis_spmv_dot_f64_noalloc(mesh, which, _ptr(x), _ptr(y), _ptr(xy), _stream(stream)))
 
 
 def make_params(nu, dt, f=(0.0, 0.0, 0.0), rtol_u=1e-8, rtol_p=1e-8, max_it_u=1000, max_it_p=20000,

@@ -356,6 +356,22 @@ int oasis_spmv_dot_f64(const oasis_mesh* mesh, int32_t which, const double* x, d
     });
 }
 
+int oasis_spmv_dot_f64_noalloc(const oasis_mesh* mesh, int32_t which, const double* x, double* y, double* xy,
+                               void* stream) {
+    return guarded([&] {
+        const Mesh* m = reinterpret_cast<const Mesh*>(mesh);
+        OASIS_CHECK(m && x && y && xy, OASIS_EINVAL, "null pointer");
+        OASIS_CHECK(m->assembled, OASIS_EINVAL, "mesh not assembled");
+        OASIS_CHECK(m->n <= noalloc_max_rows(), OASIS_EINVAL,
+                    "n_dofs = " + std::to_string(m->n) + " exceeds the static scratch of the no-alloc entry point (at "
+                    "most " + std::to_string(noalloc_max_rows()) + " rows); use oasis_spmv_dot_f64");
+        double* partial = nullptr;
+        uint32_t* ticket = nullptr;
+        noalloc_scratch(&partial, &ticket);
+        spmv_dot_f64(*m, (const double*)const_matrix(m, which, false), x, y, xy, partial, ticket, as_stream(stream));
+    });
+}
+
 int oasis_solver_create(oasis_mesh* mesh, const oasis_params* params, int64_t n_dirichlet,
                         const int32_t* dirichlet_dofs, void* stream, oasis_solver** out) {
     return guarded([&] {

@@ -122,6 +122,8 @@ void spmv_f64(const Mesh& m, const double* vals, const double* x, double* y, int
 void spmv_f32(const Mesh& m, const float* vals, const float* x, float* y, int lanes, cudaStream_t s);
 void spmv_dot_f64(const Mesh& m, const double* vals, const double* x, double* y, double* xy, double* tile_partial,
                   uint32_t* ticket, cudaStream_t s);
+void noalloc_scratch(double** partial, uint32_t** ticket);
+int64_t noalloc_max_rows();
 
 int num_sms();
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <mutex>
 #include <thread>
 
 #include "device.cuh"
@@ -450,6 +451,42 @@ void spmv_dot_f64(const Mesh& m, const double* vals, const double* x, double* y,
     OASIS_CUDA(cudaMemsetAsync(ticket, 0, sizeof(uint32_t), s));
     k_spmv_dot_tiles<<<grid, kBlock, smem, s>>>(m.n, m.row_ptr.p, m.col.p, vals, x, y, tile_partial, ticket, xy);
     OASIS_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ no-alloc scratch
+// Reduction scratch for oasis_spmv_dot_f64_noalloc, for callers that cannot
+// allocate device memory (code running under a caller-owned memory pool or
+// inside an allocator, or on a device that is already full).  Every GPU that
+// loads the library holds these arrays until the process exits (516 KiB).
+// One partial sum per 256-row tile: at most 65,536 tiles, i.e. 16,777,216 rows.
+constexpr int64_t kNoAllocMaxTiles = 65536;
+static __device__ __align__(256) double g_noalloc_partial[kNoAllocMaxTiles];
+static __device__ __align__(256) uint32_t g_noalloc_ticket[64];
+
+int64_t noalloc_max_rows() { return kNoAllocMaxTiles * kBlock; }
+
+// Device addresses of the arrays above for the current device.  In host code
+// the symbols are host-side stand-ins, not device addresses, so they are
+// resolved with cudaGetSymbolAddress once per device (with that device
+// current) and cached.
+void noalloc_scratch(double** partial, uint32_t** ticket) {
+    static std::mutex mu;
+    static double* part[256] = {nullptr};
+    static uint32_t* tick[256] = {nullptr};
+    int dev = 0;
+    OASIS_CUDA(cudaGetDevice(&dev));
+    OASIS_CHECK(dev >= 0 && dev < 256, OASIS_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!part[dev]) {
+        void* p = nullptr;
+        void* t = nullptr;
+        OASIS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_partial));
+        OASIS_CUDA(cudaGetSymbolAddress(&t, g_noalloc_ticket));
+        part[dev] = static_cast<double*>(p);
+        tick[dev] = static_cast<uint32_t*>(t);
+    }
+    *partial = part[dev];
+    *ticket = tick[dev];
 }
 
 void spmv_f64(const Mesh& m, const double* vals, const double* x, double* y, int lanes, cudaStream_t s) {
