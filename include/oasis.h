@@ -45,6 +45,8 @@ extern "C" {
 #define OASIS_EBREAKDOWN (-5)  /* BiCGStab/CG breakdown (a zero inner product) */
 #define OASIS_ENAN (-6)        /* a non-finite value appeared in a solve */
 #define OASIS_ENOMEM (-7)      /* device allocation failed at creation time */
+#define OASIS_EWAIT (-8)       /* a bounded device-side wait exceeded its time limit (~2 s);
+                                  the kernel returned without hanging */
 
 #define OASIS_FP64 0           /* every value and every operation in float64 */
 #define OASIS_MIXED 1          /* float32 matrices and inner Krylov iterations inside

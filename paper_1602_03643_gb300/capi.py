@@ -22,6 +22,7 @@ OASIS_ENOTCONV = -4
 OASIS_EBREAKDOWN = -5
 OASIS_ENAN = -6
 OASIS_ENOMEM = -7
+OASIS_EWAIT = -8
 OASIS_FP64 = 0
 OASIS_MIXED = 1
 OASIS_GUESS_ZERO = 0
@@ -30,7 +31,7 @@ OASIS_GUESS_LEARNED = 2
 OASIS_MAT_M, OASIS_MAT_K, OASIS_MAT_G0, OASIS_MAT_G1, OASIS_MAT_G2, OASIS_MAT_A = range(6)
 
 ERROR_NAMES = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "EMESH", -4: "ENOTCONV", -5: "EBREAKDOWN",
-               -6: "ENAN", -7: "ENOMEM"}
+               -6: "ENAN", -7: "ENOMEM", -8: "EWAIT"}
 
 
 class oasis_params(C.Structure):

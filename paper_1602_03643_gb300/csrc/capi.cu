@@ -8,6 +8,7 @@
 #include "device.cuh"
 #include "internal.cuh"
 #include "solver.cuh"
+#include "kern.cuh"
 
 namespace oasis {
 
@@ -206,7 +207,7 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     S->stage.alloc(std::max<int64_t>(n, n_dir) * D);
     S->st.alloc(2);
     OASIS_CUDA(cudaMemsetAsync(S->st.p, 0, S->st.bytes(), s));
-    S->partial.alloc((size_t)num_sms() * 8 * 8 * 8, s);
+    S->partial.alloc((size_t)num_sms() * 8 * 8 * 8 * 2, s);
     OASIS_CUDA(cudaHostAlloc(&S->h_st, 2 * sizeof(KrylovState), cudaHostAllocDefault));
     std::memset(S->h_st, 0, 2 * sizeof(KrylovState));
     for (auto& c : S->cap) OASIS_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));

@@ -85,6 +85,15 @@ struct Mesh {
     DBuf<float> ML32, invML32, dinvK32;
     DBuf<float2> Kff;                          // K as float-float (hi, lo)
     int tile_cap = 0;                          // max entries of a 256-row tile
+    // SELL-32 (sliced ELLPACK, slices of 32 rows, column-major inside a slice):
+    // entry k of row 32 s + l sits at sell_ptr[s] + 32 k + l; short rows are
+    // padded with their own index and a zero value.  sell_of_csr maps a CSR
+    // entry to its SELL position.
+    int64_t n_sell = 0;
+    DBuf<int32_t> sell_ptr, sell_len, sell_col, sell_of_csr;
+    DBuf<float> K32s;
+    DBuf<double> K64s;
+    DBuf<float2> Kffs;
     DBuf<double> red_partial;                  // one partial sum per 256-row tile
     DBuf<uint32_t> red_ticket;
     DBuf<int32_t> err;                         // device error flag for setup kernels

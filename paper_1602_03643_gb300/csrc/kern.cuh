@@ -147,12 +147,12 @@ __device__ __forceinline__ ff acc_shfl(ff a, int o) {
 }
 
 // Block-wide sum of NV accumulators (float-float or double), valid in thread 0.
-// Fixed shuffle/shared-memory tree: deterministic.
+// Fixed shuffle/shared-memory tree: deterministic.  Any block size up to 1024.
 template <int NV, class A>
 __device__ __forceinline__ void block_reduce(A (&v)[NV]) {
     static_assert(NV <= 8, "too many reduction values");
-    __shared__ A sh[NV][kBlock / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ A sh[NV][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
 #pragma unroll
@@ -165,7 +165,7 @@ __device__ __forceinline__ void block_reduce(A (&v)[NV]) {
         for (int k = 0; k < NV; ++k) {
             A x;
             acc_zero(x);
-            if (lane < kBlock / 32) x = sh[k][lane];
+            if (lane < nw) x = sh[k][lane];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc_add(x, acc_shfl(x, o));
             v[k] = x;
@@ -218,6 +218,112 @@ __device__ __forceinline__ bool grid_sum(A (&v)[NV], double (&tot)[NV], void* pa
     return true;
 }
 
+// Lightweight deterministic grid sum for per-iteration Krylov scalars: values in
+// the kernel's value type T (float in the mixed path, whose inner iterations are
+// float32 anyway; double in the float64 path), shuffle trees inside warps and
+// blocks, one partial per block, and a pairwise-ordered sum of the partials by
+// the block that takes the last ticket.  A handful of instructions per value
+// and warp, against ~100 for a float-float tree.
+template <int NV, class T>
+__device__ __forceinline__ bool grid_sum_lite(T (&v)[NV], double (&tot)[NV], void* partial_raw, uint32_t* ticket) {
+    T* partial = reinterpret_cast<T*>(partial_raw);
+    __shared__ T sh[NV][32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        if (lane == 0) sh[k][wid] = v[k];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            T x = lane < nw ? sh[k][lane] : (T)0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) partial[(size_t)blockIdx.x * NV + k] = x;
+        }
+        if (lane == 0) {
+            __threadfence();
+            last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        }
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    T s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s[k] = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] += __ldcg(&partial[(size_t)b * NV + k]);
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+        if (lane == 0) sh[k][wid] = s[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            T x = 0;
+            for (int w = 0; w < nw; ++w) x += sh[k][w];
+            tot[k] = (double)x;
+        }
+        *ticket = 0u;
+    }
+    return true;
+}
+
+// Limit of every bounded device-side wait (~2 s at 2 GHz).
+constexpr long long kBarrierLimitCycles = 4000000000LL;
+
+// ------------------------------------------------------------------ TMA bulk copies
+// 1D bulk copies global -> shared (cp.async.bulk, the Blackwell/Hopper TMA engine)
+// completing on an mbarrier.  Source and destination must be 16-byte aligned and
+// the size a multiple of 16 bytes; callers copy aligned supersets of their ranges.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase with the given parity to complete, for at most ~2 s.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kBarrierLimitCycles) return false;
+    return true;
+}
+
 // ------------------------------------------------------------------ row tiles
 // A tile is kTile consecutive rows; its pattern entries [e0, e1) are
 // contiguous.  Sparse kernels run in two phases per tile: an entry-parallel
@@ -254,6 +360,33 @@ __device__ __forceinline__ int tile_row_of(const int32_t* s_rp, int nr, int32_t 
         else hi = mid;
     }
     return lo;
+}
+
+template <class T, int N>
+struct Vec {
+    T v[N];
+};
+
+// Entry phase of a tile with U entries per thread in flight: `load(e)` reads
+// everything an entry needs (its value, column and gathered vector entries) into
+// an Item, `use(e, item)` consumes it.  All U loads of a thread are issued
+// before any use, so a block does not wait on U serialised load chains.  Out of
+// range slots load entry e0 (always valid) and are not used.
+template <int U, class Item, class LoadF, class UseF>
+__device__ __forceinline__ void tile_entries(const TileRange& T, LoadF&& load, UseF&& use) {
+    for (int32_t base = T.e0 + (int32_t)threadIdx.x; base < T.e1; base += kTile * U) {
+        Item it[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int32_t e = base + u * kTile;
+            it[u] = load(e < T.e1 ? e : T.e0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int32_t e = base + u * kTile;
+            if (e < T.e1) use(e, it[u]);
+        }
+    }
 }
 
 }  // namespace oasis

@@ -124,8 +124,16 @@ Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const in
         const int64_t r1 = std::min<int64_t>(n, r0 + kBlock);
         m->tile_cap = std::max<int>(m->tile_cap, row_ptr[r1] - row_ptr[r0]);
     }
-    m->row_ptr.upload(row_ptr.data(), row_ptr.size(), s);
-    m->col.upload(col.data(), col.size(), s);
+    // row_ptr and col carry 8 padding entries so that 16-byte aligned bulk copies
+    // of a tile's range never read past the allocation
+    {
+        std::vector<int32_t> rp_pad(row_ptr);
+        rp_pad.resize(row_ptr.size() + 8, row_ptr.back());
+        m->row_ptr.upload(rp_pad.data(), rp_pad.size(), s);
+        std::vector<int32_t> col_pad(col);
+        col_pad.resize(col.size() + 8, 0);
+        m->col.upload(col_pad.data(), col_pad.size(), s);
+    }
     m->diag.upload(diag.data(), diag.size(), s);
     m->cell_vert.upload(cells, (size_t)nc * d1, s);
     m->cell_dof.upload(cdof.data(), cdof.size(), s);
@@ -136,6 +144,40 @@ Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const in
     m->err.alloc(1);
     OASIS_CUDA(cudaMemsetAsync(m->err.p, 0, sizeof(int32_t), s));
     OASIS_CUDA(cudaStreamSynchronize(s));
+    // SELL-32 layout of the pattern
+    {
+        const int64_t ns = (n + 31) / 32;
+        std::vector<int32_t> sptr(ns + 1, 0), slen(ns, 0);
+        for (int64_t sl = 0; sl < ns; ++sl) {
+            int mx = 0;
+            for (int64_t i = sl * 32; i < std::min<int64_t>(n, sl * 32 + 32); ++i) mx = std::max(mx, row_len[i]);
+            slen[sl] = mx;
+            sptr[sl + 1] = sptr[sl] + 32 * mx;
+        }
+        const int64_t nsell = sptr[ns];
+        OASIS_CHECK(nsell < INT32_MAX, OASIS_EINVAL, "too many padded entries for int32 indices");
+        std::vector<int32_t> scol(nsell), sof(nnz);
+        for (int64_t sl = 0; sl < ns; ++sl) {
+            for (int l = 0; l < 32; ++l) {
+                const int64_t i = sl * 32 + l;
+                for (int k = 0; k < slen[sl]; ++k) {
+                    const int64_t pos = sptr[sl] + 32 * k + l;
+                    if (i < n && k < row_len[i]) {
+                        scol[pos] = col[row_ptr[i] + k];
+                        sof[row_ptr[i] + k] = (int32_t)pos;
+                    } else {
+                        scol[pos] = (int32_t)std::min<int64_t>(i, n - 1);
+                    }
+                }
+            }
+        }
+        m->n_sell = nsell;
+        m->sell_ptr.upload(sptr.data(), sptr.size(), s);
+        m->sell_len.upload(slen.data(), slen.size(), s);
+        m->sell_col.upload(scol.data(), scol.size(), s);
+        m->sell_of_csr.upload(sof.data(), sof.size(), s);
+        OASIS_CUDA(cudaStreamSynchronize(s));
+    }
     m->h_row_ptr = std::move(row_ptr);
     m->h_col = std::move(col);
     return m.release();
@@ -278,6 +320,19 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restr
         b[i] = (float)a[i];
 }
 
+// K in the SELL-32 layout, in float64, float32 and float-float.
+__global__ void k_csr_to_sell(int64_t nnz, const int32_t* __restrict__ sof, const double* __restrict__ v,
+                              double* __restrict__ v64, float* __restrict__ v32, float2* __restrict__ vff) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = sof[e];
+        const double x = v[e];
+        const float hi = (float)x;
+        v64[q] = x;
+        v32[q] = hi;
+        vff[q] = make_float2(hi, (float)(x - (double)hi));
+    }
+}
+
 static int grid_for(int64_t items, int per_block = kBlock) {
     const int64_t want = (items + per_block - 1) / per_block;
     const int64_t cap = (int64_t)num_sms() * 8;
@@ -305,7 +360,8 @@ void assemble_constant(Mesh& m, cudaStream_t s) {
     OASIS_CHECK(herr == 0, OASIS_EMESH, "degenerate (zero-volume) cell");
 
     m.M64.alloc(m.nnz);
-    m.K64.alloc(m.nnz);
+    m.K64.alloc(m.nnz + 8);
+    OASIS_CUDA(cudaMemsetAsync(m.K64.p, 0, (m.nnz + 8) * sizeof(double), s));
     m.G64.alloc((size_t)D * m.nnz);
     m.ML64.alloc(m.n);
     const int gr = grid_for(m.n);
@@ -328,12 +384,20 @@ void assemble_constant(Mesh& m, cudaStream_t s) {
     m.Kff.alloc(m.nnz);
     k_to_ff<<<grid_for(m.nnz), kBlock, 0, s>>>(m.nnz, m.K64.p, m.Kff.p);
     m.M32.alloc(m.nnz);
-    m.K32.alloc(m.nnz);
+    m.K32.alloc(m.nnz + 8);
+    OASIS_CUDA(cudaMemsetAsync(m.K32.p, 0, (m.nnz + 8) * sizeof(float), s));
     m.G32.alloc((size_t)D * m.nnz);
     k_to_f32<<<grid_for(m.nnz), kBlock, 0, s>>>(m.nnz, m.M64.p, m.M32.p);
     k_to_f32<<<grid_for(m.nnz), kBlock, 0, s>>>(m.nnz, m.K64.p, m.K32.p);
     k_to_f32<<<grid_for((int64_t)D * m.nnz), kBlock, 0, s>>>((int64_t)D * m.nnz, m.G64.p, m.G32.p);
     OASIS_CUDA(cudaGetLastError());
+    m.K32s.alloc(m.n_sell);
+    m.K64s.alloc(m.n_sell);
+    m.Kffs.alloc(m.n_sell);
+    OASIS_CUDA(cudaMemsetAsync(m.K32s.p, 0, m.n_sell * sizeof(float), s));
+    OASIS_CUDA(cudaMemsetAsync(m.K64s.p, 0, m.n_sell * sizeof(double), s));
+    OASIS_CUDA(cudaMemsetAsync(m.Kffs.p, 0, m.n_sell * sizeof(float2), s));
+    k_csr_to_sell<<<grid_for(m.nnz), kBlock, 0, s>>>(m.nnz, m.sell_of_csr.p, m.K64.p, m.K64s.p, m.K32s.p, m.Kffs.p);
     m.red_partial.alloc((size_t)((m.n + kBlock - 1) / kBlock));
     m.red_ticket.alloc(1);
     OASIS_CUDA(cudaMemsetAsync(m.red_ticket.p, 0, sizeof(uint32_t), s));

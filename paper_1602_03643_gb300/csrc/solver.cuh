@@ -52,8 +52,8 @@ struct StepData {
     V *A, *dinvA, *beta;
     // BiCGStab work [n][D] (V)
     V *r, *rh, *p, *v, *s, *t, *ph, *sh, *dl;
-    // CG work [n] (V)
-    V *pr, *pz, *pp0, *pp1, *pq, *pdl, *xv;
+    // CG work [n] (V): r, w = A M^{-1} r, s = A p double-buffered; p; delta; x rounded
+    V *pr0, *pr1, *pw0, *pw1, *ps0, *ps1, *pp, *pdl, *xv;
     V* uIv;                           // u^I rounded to V, [n][D]
     KrylovState *stu, *stp;
     void* partial;
@@ -61,6 +61,12 @@ struct StepData {
     double dt, nu;
     int64_t n, nnz, nc;
     int max_row;
+    int tile_cap;
+    // SELL-32 copy of K
+    int64_t n_slices;
+    const int32_t *sell_ptr, *sell_len, *sell_col;
+    const V* Ks;
+    const S* Kouts;
 };
 
 struct Ctl {
@@ -104,7 +110,7 @@ struct Solver {
     RBuf g, u1, u2, du, r0, pstar, x, b, phi, phi_h1, phi_h2;          // S
     RBuf A, dinvA, beta;                                               // V
     RBuf w[9];                                                         // V [n][D]
-    RBuf pw[7];                                                        // V [n]
+    RBuf pw[9];                                                        // V [n]
     RBuf uIv;                                                          // V [n][D]
     RBuf Kout;                                                         // S [nnz]
     DBuf<double> stage;                                                // [max(n, n_dir) * D]

@@ -241,12 +241,20 @@ __global__ void __launch_bounds__(kBlock) k_bicg_outer(StepData<P> a, int k0, Ct
     const int r = threadIdx.x;
     for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
         const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
-        for (int32_t e = T.e0 + r; e < T.e1; e += kTile) {
-            const V av = a.A[e];
-            const size_t j = (size_t)a.col[e] * D + k0;
+        tile_entries<4, Vec<Acc, NR>>(
+            T,
+            [&](int32_t e) {
+                const V av = a.A[e];
+                const size_t j = (size_t)a.col[e] * D + k0;
+                Vec<Acc, NR> it;
 #pragma unroll
-            for (int c = 0; c < NR; ++c) s_prod[(size_t)(e - T.e0) * NR + c] = acc_mul_sv(a.du[j + c], av);
-        }
+                for (int c = 0; c < NR; ++c) it.v[c] = acc_mul_sv(a.du[j + c], av);
+                return it;
+            },
+            [&](int32_t e, const Vec<Acc, NR>& it) {
+#pragma unroll
+                for (int c = 0; c < NR; ++c) s_prod[(size_t)(e - T.e0) * NR + c] = it.v[c];
+            });
         __syncthreads();
         if (r < T.nr) {
             const int64_t i = T.r0 + r;
@@ -347,18 +355,24 @@ __global__ void __launch_bounds__(kBlock) k_bicg_spmm(StepData<P> a, int k0, Ctl
     __shared__ int32_t s_rp[kTile + 1];
     const V* __restrict__ x = MODE == 0 ? a.ph : a.sh;
     V* __restrict__ y = MODE == 0 ? a.v : a.t;
-    Acc part[NV];
-#pragma unroll
-    for (int c = 0; c < NV; ++c) acc_zero(part[c]);
+    V part[NV] = {};
     const int r = threadIdx.x;
     for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
         const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
-        for (int32_t e = T.e0 + r; e < T.e1; e += kTile) {
-            const V av = a.A[e];
-            const size_t j = (size_t)a.col[e] * D + k0;
+        tile_entries<8, Vec<V, NR>>(
+            T,
+            [&](int32_t e) {
+                const V av = a.A[e];
+                const size_t j = (size_t)a.col[e] * D + k0;
+                Vec<V, NR> it;
 #pragma unroll
-            for (int c = 0; c < NR; ++c) s_prod[(size_t)(e - T.e0) * NR + c] = av * x[j + c];
-        }
+                for (int c = 0; c < NR; ++c) it.v[c] = av * x[j + c];
+                return it;
+            },
+            [&](int32_t e, const Vec<V, NR>& it) {
+#pragma unroll
+                for (int c = 0; c < NR; ++c) s_prod[(size_t)(e - T.e0) * NR + c] = it.v[c];
+            });
         __syncthreads();
         if (r < T.nr) {
             const int64_t i = T.r0 + r;
@@ -371,17 +385,17 @@ __global__ void __launch_bounds__(kBlock) k_bicg_spmm(StepData<P> a, int k0, Ctl
                 const size_t o = (size_t)i * D + k0 + c;
                 y[o] = acc;
                 if (MODE == 0) {
-                    acc_prod(part[c], a.rh[o], acc);
+                    part[c] += a.rh[o] * acc;
                 } else {
-                    acc_prod(part[c], acc, a.s[o]);
-                    acc_prod(part[NR + c], acc, acc);
+                    part[c] += acc * a.s[o];
+                    part[NR + c] += acc * acc;
                 }
             }
         }
         __syncthreads();
     }
     double tot[NV];
-    if (grid_sum<NV, Acc>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0) {
+    if (grid_sum_lite<NV, V>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0) {
         KrylovState* st = a.stu;
         for (int c = 0; c < NR; ++c) {
             if (!act[c]) continue;
@@ -440,9 +454,7 @@ __global__ void __launch_bounds__(kBlock) k_bicg_xr(StepData<P> a, int k0, Ctl c
         alpha[c] = coef<P>(a.stu->alpha[k0 + c], a.stu->alpha_f[k0 + c]);
         omega[c] = coef<P>(a.stu->omega[k0 + c], a.stu->omega_f[k0 + c]);
     }
-    Acc part[2 * NR];
-#pragma unroll
-    for (int c = 0; c < 2 * NR; ++c) acc_zero(part[c]);
+    V part[2 * NR] = {};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < NR; ++c) {
@@ -451,12 +463,12 @@ __global__ void __launch_bounds__(kBlock) k_bicg_xr(StepData<P> a, int k0, Ctl c
             a.dl[o] += alpha[c] * a.ph[o] + omega[c] * a.sh[o];
             const V rv = a.s[o] - omega[c] * a.t[o];
             a.r[o] = rv;
-            acc_prod(part[c], a.rh[o], rv);
-            acc_prod(part[NR + c], rv, rv);
+            part[c] += a.rh[o] * rv;
+            part[NR + c] += rv * rv;
         }
     }
     double tot[2 * NR];
-    if (grid_sum<2 * NR, Acc>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0) {
+    if (grid_sum_lite<2 * NR, V>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0) {
         KrylovState* st = a.stu;
         for (int c = 0; c < NR; ++c) {
             if (!act[c]) continue;
@@ -523,13 +535,16 @@ __global__ void __launch_bounds__(kBlock) k_pressure_rhs(StepData<P> a, Consts<t
     const int r = threadIdx.x;
     for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
         const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
-        for (int32_t e = T.e0 + r; e < T.e1; e += kTile) {
-            const size_t j = (size_t)a.col[e] * D;
-            V acc = 0;
+        tile_entries<8, V>(
+            T,
+            [&](int32_t e) {
+                const size_t j = (size_t)a.col[e] * D;
+                V acc = 0;
 #pragma unroll
-            for (int k = 0; k < D; ++k) acc += a.G[(size_t)k * a.nnz + e] * a.uIv[j + k];
-            s_prod[e - T.e0] = acc;
-        }
+                for (int k = 0; k < D; ++k) acc += a.G[(size_t)k * a.nnz + e] * a.uIv[j + k];
+                return acc;
+            },
+            [&](int32_t e, V v) { s_prod[e - T.e0] = v; });
         __syncthreads();
         if (r < T.nr) {
             const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
@@ -581,64 +596,68 @@ __device__ __forceinline__ float2 mean_s<float2>(const KrylovState* st, bool of_
     return of_p ? make_float2(st->meanp_hi, st->meanp_lo) : make_float2(st->mean_hi, st->mean_lo);
 }
 
-// Outer sweep of the pressure CG: r = (b - mean b) - K x with float64-quality
-// products (float64 K, or K split into float-float in the mixed path); starts an
-// inner CG (z = D^{-1} r, p = 0, delta = 0); also sums p* + x for the
-// normalisation of p and writes x rounded to the value type.
+// ---------------------------------------------------------------- SELL-32 CG
+// The pressure CG kernels on K stored as SELL-32 (one warp per slice of 32 rows,
+// lane l owns row 32 s + l): every load of a column index or value is one
+// 128-byte line per warp, the gathers of consecutive rows' k-th neighbours are
+// consecutive for structured orderings, and row sums stay in registers.
 template <class P>
-__global__ void __launch_bounds__(kBlock) k_pcg_outer(StepData<P> a, Ctl ctl) {
+__device__ __forceinline__ bool sell_lane(const StepData<P>& a, int64_t& i, int& len, int64_t& base, int& lane) {
+    lane = threadIdx.x & 31;
+    const int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (sl >= a.n_slices) return false;
+    i = sl * 32 + lane;
+    len = a.sell_len[sl];
+    base = (int64_t)a.sell_ptr[sl] + lane;
+    return true;
+}
+
+// Outer sweep: r = (b - mean b) - K x with float64-quality products.
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_pcg_outer_sell(StepData<P> a, Ctl ctl) {
     using V = typename P::V;
     using S = typename P::S;
     using Acc = typename P::Acc;
-    extern __shared__ __align__(16) unsigned char dsm[];
-    Acc* s_prod = reinterpret_cast<Acc*>(dsm);
-    __shared__ int32_t s_rp[kTile + 1];
     const bool live = !a.stp->col_done[0];
     const S mean = mean_s<S>(a.stp, false);
-    Acc part[4];
+    Acc part[3];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc_zero(part[k]);
-    const int r = threadIdx.x;
-    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
-        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
-        for (int32_t e = T.e0 + r; e < T.e1; e += kTile)
-            s_prod[e - T.e0] = acc_of_s(s_mul_s(a.Kout[e], a.x[a.col[e]]));
-        __syncthreads();
-        if (r < T.nr) {
-            const int64_t i = T.r0 + r;
-            const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
-            Acc kx;
-            acc_zero(kx);
-            for (int32_t q = b0; q < b1; ++q) acc_add(kx, s_prod[q]);
+    for (int k = 0; k < 3; ++k) acc_zero(part[k]);
+    int64_t i, base;
+    int len, lane;
+    if (sell_lane(a, i, len, base, lane)) {
+        Acc kx;
+        acc_zero(kx);
+        for (int k = 0; k < len; ++k) {
+            const int64_t q = base + 32 * (int64_t)k;
+            acc_add(kx, acc_of_s(s_mul_s(a.Kouts[q], a.x[a.sell_col[q]])));
+        }
+        if (i < a.n) {
             const S bi = s_sub(a.b[i], mean);
-            const S rs = s_sub(bi, s_of_acc(kx));
-            const V rv = s_v(rs), zv = a.dinvK[i] * rv;
+            const V rv = s_v(s_sub(bi, s_of_acc(kx)));
             const V xv = s_v(a.x[i]);
             if (live) {
-                a.pr[i] = rv;
-                a.pz[i] = zv;
-                a.pp0[i] = 0;
-                a.pp1[i] = 0;
+                a.pr0[i] = rv;
+                a.ps0[i] = 0;
+                a.pp[i] = 0;
                 a.pdl[i] = 0;
             }
             a.xv[i] = xv;
             acc_prod(part[0], rv, rv);
-            acc_prod(part[1], rv, zv);
             const V bv = s_v(bi);
-            acc_prod(part[2], bv, bv);
-            acc_addv(part[3], s_v(a.pstar[i]));
-            acc_addv(part[3], xv);
+            acc_prod(part[1], bv, bv);
+            acc_addv(part[2], s_v(a.pstar[i]));
+            acc_addv(part[2], xv);
         }
-        __syncthreads();
     }
-    double tot[4];
-    if (grid_sum<4, Acc>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
+    double tot[3];
+    if (grid_sum<3, Acc>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
         KrylovState* st = a.stp;
         if (st->first) {
-            st->bb[0] = tot[2];
+            st->bb[0] = tot[1];
             st->first = 0;
         }
-        const double meanp = tot[3] / (double)a.n;
+        const double meanp = tot[2] / (double)a.n;
         st->psum = meanp;
         st->meanp_hi = (float)meanp;
         st->meanp_lo = (float)(meanp - (double)(float)meanp);
@@ -656,9 +675,6 @@ __global__ void __launch_bounds__(kBlock) k_pcg_outer(StepData<P> a, Ctl ctl) {
                 st->col_done[0] = 1;
             } else {
                 st->in_done[0] = 0;
-                st->rho[0] = tot[1];
-                st->beta[0] = 0.0;
-                mirror_coefs(st, 0);
                 st->rr0_in[0] = rr;
                 outer = 1;
             }
@@ -670,90 +686,120 @@ __global__ void __launch_bounds__(kBlock) k_pcg_outer(StepData<P> a, Ctl ctl) {
     }
 }
 
-// q = K p_new with p_new = z + beta p_old formed on the fly (double-buffered by
-// the parity of the inner iteration), <p_new, q> -> alpha = rho / <p, q>.
+// Start of an inner CG: w_0 = K M^{-1} r_0, gamma_0, delta_0, alpha_0.
 template <class P>
-__global__ void __launch_bounds__(kBlock) k_pcg_q(StepData<P> a, Ctl ctl) {
+__global__ void __launch_bounds__(kBlock, P::mixed ? 8 : 4) k_pcg_init_sell(StepData<P> a, Ctl ctl) {
     using V = typename P::V;
     using Acc = typename P::Acc;
     if (a.stp->col_done[0] || a.stp->in_done[0]) return;
-    extern __shared__ __align__(16) unsigned char dsm[];
-    V* s_prod = reinterpret_cast<V*>(dsm);
-    __shared__ int32_t s_rp[kTile + 1];
-    const int par = a.stp->it_in & 1;
-    const V* __restrict__ pold = par ? a.pp1 : a.pp0;
-    V* __restrict__ pnew = par ? a.pp0 : a.pp1;
-    const V beta = coef<P>(a.stp->beta[0], a.stp->beta_f[0]);
-    Acc part[1];
-    acc_zero(part[0]);
-    const int r = threadIdx.x;
-    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
-        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
-        for (int32_t e = T.e0 + r; e < T.e1; e += kTile) {
-            const int32_t j = a.col[e];
-            s_prod[e - T.e0] = a.K[e] * (a.pz[j] + beta * pold[j]);
+    V part[2] = {};
+    int64_t i, base;
+    int len, lane;
+    if (sell_lane(a, i, len, base, lane)) {
+        V w = 0;
+        for (int k = 0; k < len; ++k) {
+            const int64_t q = base + 32 * (int64_t)k;
+            const int32_t j = a.sell_col[q];
+            w += a.Ks[q] * (a.dinvK[j] * a.pr0[j]);
         }
-        __syncthreads();
-        if (r < T.nr) {
-            const int64_t i = T.r0 + r;
-            const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
-            V q = 0;
-            for (int32_t k = b0; k < b1; ++k) q += s_prod[k];
-            const V pv = a.pz[i] + beta * pold[i];
-            pnew[i] = pv;
-            a.pq[i] = q;
-            acc_prod(part[0], pv, q);
+        if (i < a.n) {
+            a.pw0[i] = w;
+            const V u = a.dinvK[i] * a.pr0[i];
+            part[0] += a.pr0[i] * u;
+            part[1] += w * u;
         }
-        __syncthreads();
     }
-    double tot[1];
-    if (grid_sum<1, Acc>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
+    double tot[2];
+    if (grid_sum_lite<2, V>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
         KrylovState* st = a.stp;
-        const double pq = tot[0];
-        if (!(pq > 0.0) || !isfinite(pq)) {
+        const double g0 = tot[0], d0 = tot[1];
+        if (!(d0 > 0.0) || !isfinite(d0) || !isfinite(g0)) {
             st->in_done[0] = 1;
             st->it_total[0] += 1;
             st->alpha[0] = 0.0;
             set_cond(ctl.use_cond, ctl.h_inner, 0);
         } else {
-            st->alpha[0] = st->rho[0] / pq;
+            st->rho[0] = g0;
+            st->alpha[0] = g0 / d0;
         }
+        st->beta[0] = 0.0;
         mirror_coefs(st, 0);
     }
 }
 
-// delta += alpha p, r -= alpha q, z = D^{-1} r, <r, z> -> beta, <r, r> -> stop test
+// Fused Chronopoulos-Gear iteration (see k_pcg_iter) on SELL-32.
 template <class P>
-__global__ void __launch_bounds__(kBlock) k_pcg_update(StepData<P> a, Ctl ctl) {
+__global__ void __launch_bounds__(kBlock, P::mixed ? 8 : 4) k_pcg_iter_sell(StepData<P> a, Ctl ctl) {
     using V = typename P::V;
     using Acc = typename P::Acc;
     if (a.stp->col_done[0] || a.stp->in_done[0]) return;
     const int par = a.stp->it_in & 1;
-    const V* __restrict__ pnew = par ? a.pp0 : a.pp1;
+    const V* r_o = par ? a.pr1 : a.pr0;
+    const V* w_o = par ? a.pw1 : a.pw0;
+    const V* s_o = par ? a.ps1 : a.ps0;
+    V* r_n = par ? a.pr0 : a.pr1;
+    V* w_n = par ? a.pw0 : a.pw1;
+    V* s_n = par ? a.ps0 : a.ps1;
     const V alpha = coef<P>(a.stp->alpha[0], a.stp->alpha_f[0]);
-    Acc part[2];
-    acc_zero(part[0]);
-    acc_zero(part[1]);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-        a.pdl[i] += alpha * pnew[i];
-        const V rv = a.pr[i] - alpha * a.pq[i];
-        const V zv = a.dinvK[i] * rv;
-        a.pr[i] = rv;
-        a.pz[i] = zv;
-        acc_prod(part[0], rv, zv);
-        acc_prod(part[1], rv, rv);
+    const V beta = coef<P>(a.stp->beta[0], a.stp->beta_f[0]);
+    V part[3] = {};
+    int64_t i, base;
+    int len, lane;
+    if (sell_lane(a, i, len, base, lane)) {
+        V w = 0;
+        int k = 0;
+        for (; k + 2 <= len; k += 2) {
+            V g[2], kv[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t q = base + 32 * (int64_t)(k + u);
+                const int32_t j = a.sell_col[q];
+                kv[u] = a.Ks[q];
+                const V sj = w_o[j] + beta * s_o[j];
+                g[u] = a.dinvK[j] * (r_o[j] - alpha * sj);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) w += kv[u] * g[u];
+        }
+        for (; k < len; ++k) {
+            const int64_t q = base + 32 * (int64_t)k;
+            const int32_t j = a.sell_col[q];
+            const V sj = w_o[j] + beta * s_o[j];
+            w += a.Ks[q] * (a.dinvK[j] * (r_o[j] - alpha * sj));
+        }
+        if (i < a.n) {
+            const V di = a.dinvK[i];
+            const V ro = r_o[i];
+            const V pv = di * ro + beta * a.pp[i];
+            const V sv = w_o[i] + beta * s_o[i];
+            a.pp[i] = pv;
+            s_n[i] = sv;
+            a.pdl[i] += alpha * pv;
+            const V rn = ro - alpha * sv;
+            r_n[i] = rn;
+            w_n[i] = w;
+            const V un = di * rn;
+            part[0] += rn * un;
+            part[1] += w * un;
+            part[2] += rn * rn;
+        }
     }
-    double tot[2];
-    if (grid_sum<2, Acc>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
+    double tot[3];
+    if (grid_sum_lite<3, V>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
         KrylovState* st = a.stp;
-        const double rz = tot[0], rr = tot[1];
+        const double g = tot[0], dl = tot[1], rr = tot[2];
         st->it_total[0] += 1;
-        st->beta[0] = st->rho[0] != 0.0 ? rz / st->rho[0] : 0.0;
-        st->rho[0] = rz;
+        const double g_old = st->rho[0], a_old = st->alpha[0];
+        const double b_new = g_old != 0.0 ? g / g_old : 0.0;
+        const double den = a_old != 0.0 ? dl - b_new * g / a_old : 0.0;
+        const bool brk = !(den > 0.0) || !isfinite(den) || !isfinite(g) || g_old == 0.0;
+        st->beta[0] = b_new;
+        st->alpha[0] = brk ? 0.0 : g / den;
+        st->rho[0] = g;
         st->rr_in[0] = rr;
         mirror_coefs(st, 0);
-        const bool stop = !isfinite(rr) || rr <= ctl.inner2 * st->rr0_in[0] || rr <= ctl.abs2 * st->bb[0] ||
-                          rz == 0.0 || st->it_total[0] >= ctl.max_it || st->it_in + 1 >= ctl.sweep_cap;
+        const bool stop = brk || !isfinite(rr) || rr <= ctl.inner2 * st->rr0_in[0] || rr <= ctl.abs2 * st->bb[0] ||
+                          st->it_total[0] >= ctl.max_it || st->it_in + 1 >= ctl.sweep_cap;
         if (stop) st->in_done[0] = 1;
         st->it_in += 1;
         set_cond(ctl.use_cond, ctl.h_inner, !stop);
@@ -782,11 +828,19 @@ __global__ void __launch_bounds__(kBlock) k_update(StepData<P> a, Consts<typenam
     const int r = threadIdx.x;
     for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
         const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
-        for (int32_t e = T.e0 + r; e < T.e1; e += kTile) {
-            const V ph = a.xv[a.col[e]];
+        tile_entries<8, Vec<V, D>>(
+            T,
+            [&](int32_t e) {
+                const V ph = a.xv[a.col[e]];
+                Vec<V, D> it;
 #pragma unroll
-            for (int k = 0; k < D; ++k) s_prod[(size_t)(e - T.e0) * D + k] = a.G[(size_t)k * a.nnz + e] * ph;
-        }
+                for (int k = 0; k < D; ++k) it.v[k] = a.G[(size_t)k * a.nnz + e] * ph;
+                return it;
+            },
+            [&](int32_t e, const Vec<V, D>& it) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) s_prod[(size_t)(e - T.e0) * D + k] = it.v[k];
+            });
         __syncthreads();
         if (r < T.nr) {
             const int64_t i = T.r0 + r;
@@ -881,9 +935,11 @@ struct StepImplT final : StepImpl {
     Consts<V> k_{};
     int64_t tiles = 0;
     size_t sm_asm = 0, sm_out_u = 0, sm_out_u1 = 0, sm_spmm = 0, sm_spmm1 = 0, sm_outp = 0, sm_v1 = 0, sm_vd = 0;
-    int g_asm = 1, g_out_u = 1, g_out_u1 = 1, g_spmm0 = 1, g_spmm1 = 1, g_spmm0_1 = 1, g_spmm1_1 = 1, g_outp = 1,
-        g_q = 1, g_rhs = 1, g_upd = 1;
+    int g_asm = 1, g_out_u = 1, g_out_u1 = 1, g_spmm0 = 1, g_spmm1 = 1, g_spmm0_1 = 1, g_spmm1_1 = 1,
+        g_rhs = 1, g_upd = 1;
     int ge_n = 1, ge_nd = 1, ge_c = 1;
+    int g_sell = 1;
+
 
     template <class T>
     static T* mat(const DBuf<double>& d, const DBuf<float>& f) {
@@ -926,8 +982,8 @@ struct StepImplT final : StepImpl {
         a.beta = Sv.beta.as<V>();
         V** w[9] = {&a.r, &a.rh, &a.p, &a.v, &a.s, &a.t, &a.ph, &a.sh, &a.dl};
         for (int q = 0; q < 9; ++q) *w[q] = Sv.w[q].as<V>();
-        V** pw[7] = {&a.pr, &a.pz, &a.pp0, &a.pp1, &a.pq, &a.pdl, &a.xv};
-        for (int q = 0; q < 7; ++q) *pw[q] = Sv.pw[q].as<V>();
+        V** pw[9] = {&a.pr0, &a.pr1, &a.pw0, &a.pw1, &a.ps0, &a.ps1, &a.pp, &a.pdl, &a.xv};
+        for (int q = 0; q < 9; ++q) *pw[q] = Sv.pw[q].as<V>();
         a.uIv = Sv.uIv.as<V>();
         a.stu = Sv.st.p;
         a.stp = Sv.st.p + 1;
@@ -939,6 +995,14 @@ struct StepImplT final : StepImpl {
         a.nnz = m.nnz;
         a.nc = m.nc;
         a.max_row = m.max_row;
+        a.tile_cap = m.tile_cap;
+        a.n_slices = (m.n + 31) / 32;
+        a.sell_ptr = m.sell_ptr.p;
+        a.sell_len = m.sell_len.p;
+        a.sell_col = m.sell_col.p;
+        a.Ks = mat<V>(m.K64s, m.K32s);
+        if constexpr (P::mixed) a.Kouts = reinterpret_cast<const S*>(m.Kffs.p);
+        else a.Kouts = reinterpret_cast<const S*>(m.K64s.p);
         k_.rdt = (V)(1.0 / Sv.prm.dt);
         k_.dt = (V)Sv.prm.dt;
         k_.nu = (V)Sv.prm.nu;
@@ -962,8 +1026,7 @@ struct StepImplT final : StepImpl {
         g_spmm1 = tile_grid(k_bicg_spmm<P, D, D, 1>, sm_spmm, tiles);
         g_spmm0_1 = tile_grid(k_bicg_spmm<P, D, 1, 0>, sm_spmm1, tiles);
         g_spmm1_1 = tile_grid(k_bicg_spmm<P, D, 1, 1>, sm_spmm1, tiles);
-        g_outp = tile_grid(k_pcg_outer<P>, sm_outp, tiles);
-        g_q = tile_grid(k_pcg_q<P>, sm_v1, tiles);
+        g_sell = (int)std::max<int64_t>(1, ((m.n + 31) / 32 + kBlock / 32 - 1) / (kBlock / 32));
         g_rhs = tile_grid(k_pressure_rhs<P, D>, sm_v1, tiles);
         g_upd = tile_grid(k_update<P, D>, sm_vd, tiles);
         ge_n = elem_grid(m.n);
@@ -1054,17 +1117,18 @@ struct StepImplT final : StepImpl {
         Sv.run_loops(
             s, graph, 1,
             [&](cudaStream_t ss, const Loop& lp) {
-                k_pcg_outer<P><<<g_outp, kBlock, sm_outp, ss>>>(a, ctl_p(lp));
+                const Ctl c = ctl_p(lp);
+                k_pcg_outer_sell<P><<<g_sell, kBlock, 0, ss>>>(a, c);
+                const int pu = Sv.prof_begin(ss, OASIS_PROF_PCG_UPDATE);
+                k_pcg_init_sell<P><<<g_sell, kBlock, 0, ss>>>(a, c);
+                Sv.prof_end(ss, pu);
                 OASIS_CUDA(cudaGetLastError());
             },
             [&](cudaStream_t ss, const Loop& lp) {
                 const Ctl c = ctl_p(lp);
                 const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
-                k_pcg_q<P><<<g_q, kBlock, sm_v1, ss>>>(a, c);
+                k_pcg_iter_sell<P><<<g_sell, kBlock, 0, ss>>>(a, c);
                 Sv.prof_end(ss, pq);
-                const int pu = Sv.prof_begin(ss, OASIS_PROF_PCG_UPDATE);
-                k_pcg_update<P><<<ge_n, kBlock, 0, ss>>>(a, c);
-                Sv.prof_end(ss, pu);
                 OASIS_CUDA(cudaGetLastError());
             },
             [&](cudaStream_t ss, const Loop&) {
