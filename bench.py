@@ -195,9 +195,12 @@ def run_ours(args, rank, world):
     run_e.close()
     nnz = run.nnz
     n_spmv, ms_spmv = fam["pcg_spmv"]
-    # algorithmic bytes of one pressure-CG product q = K p (float32 values, int32 columns):
-    # values + columns (8 nnz) + row pointers (4 N) + z, p_old read, p_new, q written (16 N)
-    spmv_bytes = 8 * nnz + 4 * (N + 1) + 16 * N
+    # algorithmic bytes of one fused pressure-CG iteration (SELL-32 K, float32
+    # values, int32 columns): K values + columns 8 nnz; slice pointers/lengths
+    # 8 per 32 rows; vectors read dinv, r, w, s, p, x-delta (24 N) and written
+    # p, s, x-delta, r, w (20 N)
+    n_slices = (N + 31) // 32
+    spmv_bytes = 8 * nnz + 44 * N + 8 * n_slices
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -205,14 +208,18 @@ def run_ours(args, rank, world):
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = spmv_bytes / (ms_spmv / max(n_spmv, 1) / 1e3) / 1e9 if n_spmv else None
-    roofline = {"bound": "hbm", "kernel": "k_pcg_q<float,16> (pressure CG, q = K p)",
+    roofline = {"bound": "hbm",
+                "kernel": "k_pcg_iter_sell<Mixed> (fused CG iteration: w = K M^-1 r on SELL-32 + vector updates + 3 dots)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
+                "peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if "hbm_gbs" in peaks
+                                else "of fallback 6.8 TB/s"),
                 "algorithmic_bytes_per_launch": spmv_bytes, "launches_timed": n_spmv,
                 "avg_launch_us": (ms_spmv / n_spmv * 1e3) if n_spmv else None,
                 "traffic": None,
-                "note": "K + col (33 MB) + vectors stay L2-resident inside the CG loop at this size"}
+                "note": ("algorithmic bytes %.1f MB per launch vs 129 MB L2: at this size the matrix and vectors "
+                         "stay L2-resident across CG iterations" % (spmv_bytes / 1e6))
+                if spmv_bytes < 100e6 else "working set larger than L2"}
     kernel_share = {f: {"launches": n, "ms": m} for f, (n, m) in fam.items()}
 
     # ---- the plain float64 GPU form at the same residual (comparison): float64,
@@ -235,9 +242,11 @@ def run_ours(args, rank, world):
     it_p = float(np.mean([s["it_p"] for s in stats]))
     sw_u = float(np.mean([s["sweeps_u"] for s in stats]))
     sw_p = float(np.mean([s["sweeps_p"] for s in stats]))
-    # kernels per step in the graph: assembly 3, pressure rhs + guess 2, update 1,
-    # 2 per refinement sweep (residual + correction), 5 per BiCGStab and 2 per CG iteration
-    launches = int(round(args.steps * (6 + 2 * (sw_u + sw_p) + 5 * it_u + 2 * it_p)))
+    # kernels per step in the graph: beta + assembly 2; velocity: per sweep a residual
+    # and (all but the last) a correction, 5 per BiCGStab iteration; pressure: u^I,
+    # rhs and guess 3, per sweep residual + CG start + (all but the last) correction,
+    # 1 per CG iteration; update 1
+    launches = int(round(args.steps * (4 + 2 * sw_u + 3 * sw_p + 5 * it_u + it_p)))
     run.close()
 
     line = {

@@ -55,9 +55,9 @@ extern "C" {
 
 #define OASIS_GUESS_ZERO 0     /* pressure solve starts from phi = 0, i.e. p = p* */
 #define OASIS_GUESS_PREV_PHI 1 /* starts from the previous step's correction phi */
-#define OASIS_GUESS_LEARNED 2  /* starts from the learned guess (oasis_load_guess_net);
-                                  the guess with the smaller true residual among the
-                                  learned one and phi = 0 is used */
+#define OASIS_GUESS_LEARNED 2  /* starts from the network's guess (oasis_solver_set_guess_net)
+                                  when its residual ||b - K phi0|| is smaller than that of
+                                  the fallback phi^{n-1} (the residual is the judge) */
 
 #define OASIS_MAT_M 0          /* M_ij = int phi_j phi_i            (Sec. 5) */
 #define OASIS_MAT_K 1          /* K_ij = int grad phi_j . grad phi_i (Sec. 5) */
@@ -103,6 +103,8 @@ typedef struct oasis_step_stats {
     double res_u[3];       /* final ||r|| / ||r_0|| per component (float64 residual) */
     double res_p;          /* final ||r|| / ||b_phi|| */
     double t;              /* time t^n reached by the step */
+    double guess_res[2];   /* OASIS_GUESS_LEARNED: ||b - K phi0|| / ||b|| of the network's
+                              guess [0] and of the fallback phi^{n-1} [1]; else 0 */
 } oasis_step_stats;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -225,6 +227,46 @@ int oasis_get_fields(oasis_solver* s, double* u, double* p, double* phi, int32_t
  * and the initial tentative residual r0 = b - A u^{n-1} ([dim][n_dofs]).  The
  * state is not advanced.  For parity tests. */
 int oasis_get_tentative_system(oasis_solver* s, double* A_values, double* r0, void* stream);
+
+/* ---- Learned initial guess for the pressure-correction solve -------------------
+ * The paper has no learned component: this is a project addition.  A two-layer
+ * message-passing network on the sparsity graph of the mesh (width 32, bfloat16
+ * weights, float32 accumulation) maps per-dof inputs
+ *   x_i = (b_i / s_b, phi^{n-1}_i / s_phi, phi^{n-2}_i / s_phi),
+ * b the projected right-hand side, s_b = rms(b), s_phi = rms(phi^{n-1}), to y_i;
+ * the guess is phi0 = s_phi y.  Training minimises mean (y_i - phi_i / s_phi)^2.
+ * Parameters: 2339 floats in the order W1a[32][3], W1b[32][3], c1[32],
+ * W2a[32][32], W2b[32][32], c2[32], w3[32], c3, a[2]. */
+#define OASIS_NET_PARAMS 2339
+typedef struct oasis_net oasis_net;
+
+/* Network with work buffers for the mesh's dofs; parameters start at zero. */
+int oasis_net_create(const oasis_mesh* mesh, oasis_net** out);
+/* Set / get the float32 master parameters (host arrays of OASIS_NET_PARAMS);
+ * setting also refreshes the bfloat16 copy used by the kernels and resets Adam. */
+int oasis_net_set_params(oasis_net* net, const float* params);
+int oasis_net_get_params(const oasis_net* net, float* params);
+/* y = net(features); device arrays [n_dofs][3] and [n_dofs]. */
+int oasis_net_forward(oasis_net* net, const float* features, float* y, void* stream);
+/* Gradient of the loss with respect to the parameters (device [OASIS_NET_PARAMS],
+ * or NULL for the network's own buffer) and the loss (device [1] or NULL) for one
+ * sample (features, target: device). */
+int oasis_net_backward(oasis_net* net, const float* features, const float* target, float* grad, float* loss,
+                       void* stream);
+/* One Adam step (Kingma & Ba) with the given gradient (device, NULL = own buffer). */
+int oasis_net_adam(oasis_net* net, const float* grad, float lr, float beta1, float beta2, float eps,
+                   int32_t step, void* stream);
+void oasis_net_destroy(oasis_net* net);
+/* Attach a network (or NULL) to a solver created on the same mesh; used when
+ * params.guess == OASIS_GUESS_LEARNED.  Drops a captured graph (recaptured at the
+ * next step). */
+int oasis_solver_set_guess_net(oasis_solver* s, oasis_net* net);
+/* on = 1: compute the network inputs every step, so that oasis_get_guess_sample
+ * can return training samples. */
+int oasis_solver_record_guess(oasis_solver* s, int32_t on);
+/* Training sample of the last step: the inputs [n_dofs][3] and the target
+ * phi / s_phi [n_dofs] (device arrays). */
+int oasis_get_guess_sample(oasis_solver* s, float* features, float* target, void* stream);
 
 /* Kernel families timed by oasis_profile (eager mode only; graph steps are not
  * instrumented). */

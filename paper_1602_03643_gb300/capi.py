@@ -45,12 +45,14 @@ class oasis_params(C.Structure):
 class oasis_step_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("it_u", C.c_int32 * 3), ("sweeps_u", C.c_int32),
                 ("it_p", C.c_int32), ("sweeps_p", C.c_int32), ("guess_used", C.c_int32),
-                ("res_u", C.c_double * 3), ("res_p", C.c_double), ("t", C.c_double)]
+                ("res_u", C.c_double * 3), ("res_p", C.c_double), ("t", C.c_double),
+                ("guess_res", C.c_double * 2)]
 
     def as_dict(self):
         return {"status": self.status, "it_u": list(self.it_u), "sweeps_u": self.sweeps_u,
                 "it_p": self.it_p, "sweeps_p": self.sweeps_p, "guess_used": self.guess_used,
-                "res_u": list(self.res_u), "res_p": self.res_p, "t": self.t}
+                "res_u": list(self.res_u), "res_p": self.res_p, "t": self.t,
+                "guess_res": list(self.guess_res)}
 
 
 class OasisError(RuntimeError):
@@ -89,6 +91,16 @@ SIGNATURES = {
     "oasis_get_tentative_system": (C.c_int, [P, DPTR, DPTR, P]),
     "oasis_profile": (C.c_int, [P, I32]),
     "oasis_profile_read": (C.c_int, [P, I32, C.POINTER(I64), C.POINTER(C.c_double)]),
+    "oasis_net_create": (C.c_int, [P, PP]),
+    "oasis_net_set_params": (C.c_int, [P, DPTR]),
+    "oasis_net_get_params": (C.c_int, [P, DPTR]),
+    "oasis_net_forward": (C.c_int, [P, DPTR, DPTR, P]),
+    "oasis_net_backward": (C.c_int, [P, DPTR, DPTR, DPTR, DPTR, P]),
+    "oasis_net_adam": (C.c_int, [P, DPTR, C.c_float, C.c_float, C.c_float, C.c_float, I32, P]),
+    "oasis_net_destroy": (None, [P]),
+    "oasis_solver_set_guess_net": (C.c_int, [P, P]),
+    "oasis_solver_record_guess": (C.c_int, [P, I32]),
+    "oasis_get_guess_sample": (C.c_int, [P, DPTR, DPTR, P]),
     "oasis_solver_destroy": (None, [P]),
     "oasis_mesh_destroy": (None, [P]),
 }
@@ -272,6 +284,55 @@ def oasis_profile_read(solver, family):
     n, ms = I64(), C.c_double()
     check(lib().oasis_profile_read(solver, PROF_FAMILIES.get(family, family), C.byref(n), C.byref(ms)))
     return n.value, ms.value
+
+
+OASIS_NET_PARAMS = 2339
+
+
+def oasis_net_create(mesh):
+    out = C.c_void_p()
+    check(lib().oasis_net_create(mesh, C.byref(out)))
+    return out
+
+
+def oasis_net_set_params(net, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == OASIS_NET_PARAMS
+    check(lib().oasis_net_set_params(net, _ptr(p)))
+
+
+def oasis_net_get_params(net):
+    p = np.empty(OASIS_NET_PARAMS, np.float32)
+    check(lib().oasis_net_get_params(net, _ptr(p)))
+    return p
+
+
+def oasis_net_forward(net, features, y, stream=None):
+    check(lib().oasis_net_forward(net, _ptr(features), _ptr(y), _stream(stream)))
+
+
+def oasis_net_backward(net, features, target, grad=None, loss=None, stream=None):
+    check(lib().oasis_net_backward(net, _ptr(features), _ptr(target), _ptr(grad), _ptr(loss), _stream(stream)))
+
+
+def oasis_net_adam(net, grad=None, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, step=1, stream=None):
+    check(lib().oasis_net_adam(net, _ptr(grad), lr, beta1, beta2, eps, int(step), _stream(stream)))
+
+
+def oasis_net_destroy(net):
+    lib().oasis_net_destroy(net)
+
+
+def oasis_solver_set_guess_net(solver, net):
+    check(lib().oasis_solver_set_guess_net(solver, net))
+
+
+def oasis_solver_record_guess(solver, on=True):
+    check(lib().oasis_solver_record_guess(solver, int(on)))
+
+
+def oasis_get_guess_sample(solver, features, target, stream=None):
+    check(lib().oasis_get_guess_sample(solver, _ptr(features), _ptr(target), _stream(stream)))
 
 
 def oasis_solver_destroy(solver):

@@ -9,6 +9,7 @@
 #include "internal.cuh"
 #include "solver.cuh"
 #include "kern.cuh"
+#include "net.cuh"
 
 namespace oasis {
 
@@ -204,10 +205,17 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     for (auto& w : S->w) w.alloc(vb * n * D, s);
     for (auto& w : S->pw) w.alloc(vb * n, s);
     S->uIv.alloc(vb * n * D, s);
+    S->feat.alloc((size_t)n * 3);
+    S->gy.alloc((size_t)n);
+    OASIS_CUDA(cudaMemsetAsync(S->feat.p, 0, S->feat.bytes(), s));
+    OASIS_CUDA(cudaMemsetAsync(S->gy.p, 0, S->gy.bytes(), s));
     S->stage.alloc(std::max<int64_t>(n, n_dir) * D);
     S->st.alloc(2);
     OASIS_CUDA(cudaMemsetAsync(S->st.p, 0, S->st.bytes(), s));
-    S->partial.alloc((size_t)num_sms() * 8 * 8 * 8 * 2, s);
+    // per-block partial sums: up to 8 values of 16 bytes per block, for grids of
+    // at most max(8 blocks per SM, one block per 256 rows)
+    const int64_t max_blocks = std::max<int64_t>((int64_t)num_sms() * 8, (n + kBlock - 1) / kBlock + 1);
+    S->partial.alloc((size_t)max_blocks * 8 * 16, s);
     OASIS_CUDA(cudaHostAlloc(&S->h_st, 2 * sizeof(KrylovState), cudaHostAllocDefault));
     std::memset(S->h_st, 0, 2 * sizeof(KrylovState));
     for (auto& c : S->cap) OASIS_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
@@ -229,7 +237,10 @@ static void fill_stats(const Solver& S, oasis_step_stats* o) {
     o->it_p = p.it_total[0];
     o->sweeps_p = p.sweeps;
     o->res_p = p.bb[0] > 0 ? std::sqrt(p.rr[0] / p.bb[0]) : 0.0;
-    o->guess_used = S.prm.guess == OASIS_GUESS_PREV_PHI ? OASIS_GUESS_PREV_PHI : OASIS_GUESS_ZERO;
+    if (S.prm.guess == OASIS_GUESS_LEARNED && S.net) {
+        o->guess_used = p.guess_used;
+        for (int k = 0; k < 2; ++k) o->guess_res[k] = p.bb[0] > 0 ? std::sqrt(p.guess_rr[k] / p.bb[0]) : 0.0;
+    } else o->guess_used = S.prm.guess == OASIS_GUESS_ZERO ? OASIS_GUESS_ZERO : OASIS_GUESS_PREV_PHI;
     o->t = S.t;
 }
 
@@ -516,6 +527,105 @@ int oasis_profile_read(oasis_solver* solver, int32_t family, int64_t* launches, 
         OASIS_CHECK(family >= 0 && family < Solver::kProfFamilies, OASIS_EINVAL, "unknown kernel family");
         *launches = S->prof_n[family];
         *total_ms = S->prof_ms[family];
+    });
+}
+
+// ------------------------------------------------------------------ learned guess
+static void drop_graph(Solver* S) {
+    if (S->gexec) cudaGraphExecDestroy(S->gexec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    S->gexec = nullptr;
+    S->graph = nullptr;
+}
+
+int oasis_net_create(const oasis_mesh* mesh, oasis_net** out) {
+    return guarded([&] {
+        const Mesh* m = reinterpret_cast<const Mesh*>(mesh);
+        OASIS_CHECK(m && out, OASIS_EINVAL, "null pointer");
+        *out = reinterpret_cast<oasis_net*>(net_create(*m));
+    });
+}
+
+int oasis_net_set_params(oasis_net* net, const float* params) {
+    return guarded([&] {
+        Net* N = reinterpret_cast<Net*>(net);
+        OASIS_CHECK(N && params, OASIS_EINVAL, "null pointer");
+        net_set_params(*N, params);
+    });
+}
+
+int oasis_net_get_params(const oasis_net* net, float* params) {
+    return guarded([&] {
+        const Net* N = reinterpret_cast<const Net*>(net);
+        OASIS_CHECK(N && params, OASIS_EINVAL, "null pointer");
+        OASIS_CUDA(cudaDeviceSynchronize());
+        OASIS_CUDA(cudaMemcpy(params, N->p32.p, kNetParams * sizeof(float), cudaMemcpyDeviceToHost));
+    });
+}
+
+int oasis_net_forward(oasis_net* net, const float* features, float* y, void* stream) {
+    return guarded([&] {
+        Net* N = reinterpret_cast<Net*>(net);
+        OASIS_CHECK(N && features && y, OASIS_EINVAL, "null pointer");
+        net_forward(*N, features, y, as_stream(stream));
+    });
+}
+
+int oasis_net_backward(oasis_net* net, const float* features, const float* target, float* grad, float* loss,
+                       void* stream) {
+    return guarded([&] {
+        Net* N = reinterpret_cast<Net*>(net);
+        OASIS_CHECK(N && features && target, OASIS_EINVAL, "null pointer");
+        net_backward(*N, features, target, grad, loss, as_stream(stream));
+    });
+}
+
+int oasis_net_adam(oasis_net* net, const float* grad, float lr, float beta1, float beta2, float eps, int32_t step,
+                   void* stream) {
+    return guarded([&] {
+        Net* N = reinterpret_cast<Net*>(net);
+        OASIS_CHECK(N && step >= 1 && lr > 0, OASIS_EINVAL, "bad arguments");
+        net_adam(*N, grad, lr, beta1, beta2, eps, step, as_stream(stream));
+    });
+}
+
+void oasis_net_destroy(oasis_net* net) {
+    Net* N = reinterpret_cast<Net*>(net);
+    if (N) {
+        cudaDeviceSynchronize();
+        delete N;
+    }
+}
+
+int oasis_solver_set_guess_net(oasis_solver* solver, oasis_net* net) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S, OASIS_EINVAL, "null solver");
+        Net* N = reinterpret_cast<Net*>(net);
+        OASIS_CHECK(!N || N->m == S->m, OASIS_EINVAL, "the network was created on another mesh");
+        S->net = N;
+        drop_graph(S);
+    });
+}
+
+int oasis_solver_record_guess(oasis_solver* solver, int32_t on) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S, OASIS_EINVAL, "null solver");
+        S->record = on != 0;
+        drop_graph(S);
+    });
+}
+
+int oasis_get_guess_sample(oasis_solver* solver, float* features, float* target, void* stream) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S && features && target, OASIS_EINVAL, "null pointer");
+        OASIS_CHECK(S->record || (S->prm.guess == OASIS_GUESS_LEARNED && S->net), OASIS_EINVAL,
+                    "enable oasis_solver_record_guess (or a learned guess) before the step");
+        cudaStream_t s = as_stream(stream);
+        OASIS_CUDA(cudaMemcpyAsync(features, S->feat.p, S->feat.bytes(), cudaMemcpyDeviceToDevice, s));
+        S->impl->guess_target(s, target);
     });
 }
 

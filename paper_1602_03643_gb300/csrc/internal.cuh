@@ -113,6 +113,9 @@ struct KrylovState {
     double psum;           // pressure: sum of p* + phi (normalisation)
     float alpha_f[3], omega_f[3], beta_f[3];
     float mean_hi, mean_lo, meanp_hi, meanp_lo;
+    double gscale[2];      // learned guess: rms of the right-hand side and of phi^{n-1}
+    float gscale_f[2];
+    double guess_rr[2];    // residual^2 of the learned guess and of the fallback
     int32_t col_done[3];   // converged (float64-quality residual)
     int32_t in_done[3];    // inner solve finished for this sweep
     int32_t it_total[3];

@@ -55,6 +55,8 @@ struct StepData {
     // CG work [n] (V): r, w = A M^{-1} r, s = A p double-buffered; p; delta; x rounded
     V *pr0, *pr1, *pw0, *pw1, *ps0, *ps1, *pp, *pdl, *xv;
     V* uIv;                           // u^I rounded to V, [n][D]
+    float* feat;                      // learned guess: features [n][3]
+    float* gy;                        // learned guess: network output [n]
     KrylovState *stu, *stp;
     void* partial;
     double f[3];
@@ -93,6 +95,7 @@ struct StepImpl {
     virtual void to_state(cudaStream_t s, const double* src_soa, int which, int64_t count, int comps) = 0;
     virtual void from_state(cudaStream_t s, double* dst_soa, int which, int64_t count, int comps) = 0;
     virtual void a_to_double(cudaStream_t s, double* dst) = 0;
+    virtual void guess_target(cudaStream_t s, float* target) = 0;
 };
 
 // state buffers addressable by to_state / from_state
@@ -112,6 +115,9 @@ struct Solver {
     RBuf w[9];                                                         // V [n][D]
     RBuf pw[9];                                                        // V [n]
     RBuf uIv;                                                          // V [n][D]
+    DBuf<float> feat, gy;                                              // learned-guess features / output
+    struct Net* net = nullptr;                                         // attached network (not owned)
+    bool record = false;                                               // compute features every step
     RBuf Kout;                                                         // S [nnz]
     DBuf<double> stage;                                                // [max(n, n_dir) * D]
     DBuf<KrylovState> st;                                              // [0] velocity, [1] pressure

@@ -23,6 +23,7 @@
 #include <memory>
 
 #include "kern.cuh"
+#include "net.cuh"
 #include "solver.cuh"
 
 namespace oasis {
@@ -575,14 +576,6 @@ __global__ void __launch_bounds__(kBlock) k_pressure_rhs(StepData<P> a, Consts<t
     }
 }
 
-// Initial guess for phi: 0 or the previous step's correction.
-template <class P>
-__global__ void k_phi_guess(StepData<P> a, int mode) {
-    using S = typename P::S;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
-        a.x[i] = mode == OASIS_GUESS_PREV_PHI ? a.phi_h1[i] : s_zero<S>();
-}
-
 // mean of the pressure right-hand side (of_p = false) or of p = p* + phi
 // (of_p = true) as a state value
 template <class S>
@@ -596,11 +589,6 @@ __device__ __forceinline__ float2 mean_s<float2>(const KrylovState* st, bool of_
     return of_p ? make_float2(st->meanp_hi, st->meanp_lo) : make_float2(st->mean_hi, st->mean_lo);
 }
 
-// ---------------------------------------------------------------- SELL-32 CG
-// The pressure CG kernels on K stored as SELL-32 (one warp per slice of 32 rows,
-// lane l owns row 32 s + l): every load of a column index or value is one
-// 128-byte line per warp, the gathers of consecutive rows' k-th neighbours are
-// consecutive for structured orderings, and row sums stay in registers.
 template <class P>
 __device__ __forceinline__ bool sell_lane(const StepData<P>& a, int64_t& i, int& len, int64_t& base, int& lane) {
     lane = threadIdx.x & 31;
@@ -611,6 +599,105 @@ __device__ __forceinline__ bool sell_lane(const StepData<P>& a, int64_t& i, int&
     base = (int64_t)a.sell_ptr[sl] + lane;
     return true;
 }
+
+// ---------------------------------------------------------------- learned guess
+// Scales of the network inputs: s_b = rms(b - mean b), s_phi = rms(phi^{n-1})
+// (1 where zero).
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_guess_scales(StepData<P> a) {
+    using V = typename P::V;
+    using S = typename P::S;
+    const S mean = mean_s<S>(a.stp, false);
+    V part[2] = {};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const V bv = s_v(s_sub(a.b[i], mean)), f1 = s_v(a.phi_h1[i]);
+        part[0] += bv * bv;
+        part[1] += f1 * f1;
+    }
+    double tot[2];
+    if (grid_sum_lite<2, V>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
+        for (int k = 0; k < 2; ++k) {
+            const double r = sqrt(tot[k] / (double)a.n);
+            a.stp->gscale[k] = r > 0.0 ? r : 1.0;
+            a.stp->gscale_f[k] = (float)a.stp->gscale[k];
+        }
+    }
+}
+
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_guess_features(StepData<P> a) {
+    using S = typename P::S;
+    const S mean = mean_s<S>(a.stp, false);
+    const float ib = 1.f / a.stp->gscale_f[0], ip = 1.f / a.stp->gscale_f[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        a.feat[i * 3] = (float)s_v(s_sub(a.b[i], mean)) * ib;
+        a.feat[i * 3 + 1] = (float)s_v(a.phi_h1[i]) * ip;
+        a.feat[i * 3 + 2] = (float)s_v(a.phi_h2[i]) * ip;
+    }
+}
+
+// The residual is the judge: ||(b - mean) - K phi0|| of the learned guess
+// phi0 = s_phi y against that of the fallback phi^{n-1}; the smaller one is used.
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_guess_judge(StepData<P> a) {
+    using V = typename P::V;
+    using S = typename P::S;
+    const S mean = mean_s<S>(a.stp, false);
+    const V sp = (V)a.stp->gscale_f[1];
+    V part[2] = {};
+    int64_t i, base;
+    int len, lane;
+    if (sell_lane(a, i, len, base, lane)) {
+        V kl = 0, kp = 0;
+        for (int k = 0; k < len; ++k) {
+            const int64_t q = base + 32 * (int64_t)k;
+            const int32_t j = a.sell_col[q];
+            const V kv = a.Ks[q];
+            kl += kv * (sp * (V)a.gy[j]);
+            kp += kv * s_v(a.phi_h1[j]);
+        }
+        if (i < a.n) {
+            const V bv = s_v(s_sub(a.b[i], mean));
+            part[0] += (bv - kl) * (bv - kl);
+            part[1] += (bv - kp) * (bv - kp);
+        }
+    }
+    double tot[2];
+    if (grid_sum_lite<2, V>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
+        a.stp->guess_rr[0] = tot[0];
+        a.stp->guess_rr[1] = tot[1];
+        a.stp->guess_used = (isfinite(tot[0]) && tot[0] < tot[1]) ? OASIS_GUESS_LEARNED : OASIS_GUESS_PREV_PHI;
+    }
+}
+
+// Initial guess for phi: 0, the previous step's correction, or (mode LEARNED)
+// the candidate the judge chose.
+template <class P>
+__global__ void k_phi_guess(StepData<P> a, int mode) {
+    using S = typename P::S;
+    const bool learned = mode == OASIS_GUESS_LEARNED && a.stp->guess_used == OASIS_GUESS_LEARNED;
+    const float sp = a.stp->gscale_f[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (learned) a.x[i] = s_from((typename P::V)(sp * a.gy[i]));
+        else if (mode == OASIS_GUESS_ZERO) a.x[i] = s_zero<S>();
+        else a.x[i] = a.phi_h1[i];
+    }
+}
+
+// Training target of the last step: t = phi / s_phi.
+template <class P>
+__global__ void k_guess_target(StepData<P> a, float* t) {
+    const float ip = 1.f / a.stp->gscale_f[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
+        t[i] = (float)s_v(a.phi[i]) * ip;
+}
+
+
+// ---------------------------------------------------------------- SELL-32 CG
+// The pressure CG kernels on K stored as SELL-32 (one warp per slice of 32 rows,
+// lane l owns row 32 s + l): every load of a column index or value is one
+// 128-byte line per warp, the gathers of consecutive rows' k-th neighbours are
+// consecutive for structured orderings, and row sums stay in registers.
 
 // Outer sweep: r = (b - mean b) - K x with float64-quality products.
 template <class P>
@@ -985,6 +1072,8 @@ struct StepImplT final : StepImpl {
         V** pw[9] = {&a.pr0, &a.pr1, &a.pw0, &a.pw1, &a.ps0, &a.ps1, &a.pp, &a.pdl, &a.xv};
         for (int q = 0; q < 9; ++q) *pw[q] = Sv.pw[q].as<V>();
         a.uIv = Sv.uIv.as<V>();
+        a.feat = Sv.feat.p;
+        a.gy = Sv.gy.p;
         a.stu = Sv.st.p;
         a.stp = Sv.st.p + 1;
         a.partial = Sv.partial.p;
@@ -1111,7 +1200,19 @@ struct StepImplT final : StepImpl {
         const int pr = Sv.prof_begin(s, OASIS_PROF_PRESSURE_RHS);
         k_pressure_rhs<P, D><<<g_rhs, kBlock, sm_v1, s>>>(a, k_);
         Sv.prof_end(s, pr);
-        const int mode = Sv.prm.guess == OASIS_GUESS_PREV_PHI ? OASIS_GUESS_PREV_PHI : OASIS_GUESS_ZERO;
+        const bool learned = Sv.prm.guess == OASIS_GUESS_LEARNED && Sv.net;
+        int mode = Sv.prm.guess == OASIS_GUESS_ZERO ? OASIS_GUESS_ZERO : OASIS_GUESS_PREV_PHI;
+        if (learned || Sv.record) {
+            k_guess_scales<P><<<ge_n, kBlock, 0, s>>>(a);
+            k_guess_features<P><<<ge_n, kBlock, 0, s>>>(a);
+            OASIS_CUDA(cudaGetLastError());
+        }
+        if (learned) {
+            net_forward(*Sv.net, a.feat, a.gy, s);
+            k_guess_judge<P><<<g_sell, kBlock, 0, s>>>(a);
+            OASIS_CUDA(cudaGetLastError());
+            mode = OASIS_GUESS_LEARNED;
+        }
         k_phi_guess<P><<<ge_n, kBlock, 0, s>>>(a, mode);
         OASIS_CUDA(cudaGetLastError());
         Sv.run_loops(
@@ -1165,6 +1266,11 @@ struct StepImplT final : StepImpl {
         k_from_state<P><<<elem_grid(count * comps), kBlock, 0, s>>>(state_ptr(which), dst, count, comps);
         OASIS_CUDA(cudaGetLastError());
     }
+    void guess_target(cudaStream_t s, float* target) override {
+        k_guess_target<P><<<ge_n, kBlock, 0, s>>>(a, target);
+        OASIS_CUDA(cudaGetLastError());
+    }
+
     void a_to_double(cudaStream_t s, double* dst) override {
         k_v_to_double<V><<<elem_grid(a.nnz), kBlock, 0, s>>>(a.A, dst, a.nnz);
         OASIS_CUDA(cudaGetLastError());

@@ -29,6 +29,7 @@ class IPCSRun:
         self.t = pb.t0
         capi.oasis_set_fields(self.solver, pb.u_nm1, pb.u_nm2, pb.p, pb.t0, False, stream)
         self.stats = []
+        self.net = None
 
     def set_dirichlet_for_next_step(self):
         if len(self.pb.dirichlet):
@@ -44,6 +45,22 @@ class IPCSRun:
             if st is not None:
                 self.stats.append(st.as_dict())
         return st
+
+    def attach_guess_net(self, net):
+        """Use a GuessNet (or None) when the solver's guess is OASIS_GUESS_LEARNED."""
+        capi.oasis_solver_set_guess_net(self.solver, None if net is None else net.handle)
+        self.net = net
+
+    def record_guess(self, on=True):
+        capi.oasis_solver_record_guess(self.solver, on)
+
+    def guess_sample(self):
+        """(features [n][3], target [n]) of the last step, as new device tensors."""
+        import torch
+        feat = torch.empty((self.n, 3), dtype=torch.float32, device="cuda")
+        target = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        capi.oasis_get_guess_sample(self.solver, feat, target, self.stream)
+        return feat, target
 
     def fields(self):
         u, p, phi = capi.oasis_get_fields(self.solver, self.dim, self.n, False, stream=self.stream)
