@@ -141,23 +141,52 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize(dev)
         return sum(a.elapsed_time(b) for a, b in evs), stats
 
-    # ---- the headline form: mixed precision + batched + graph (+ previous-phi guess)
-    run = make(capi.OASIS_MIXED, graph=0 if args.eager else 1)
+    def timed_form(run):
+        """W untimed steps, barrier, then K timed steps (max over ranks)."""
+        for _ in range(args.warmup):
+            capi.oasis_step(run.solver, stream, want_stats=False)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        with Clocks(local) as clk:
+            ms, stats = timed_steps(run, args.steps)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, stats, clk.summary()
+
+    # ---- the headline form: mixed precision + batched + graph + learned guess
+    # (the network is trained first, untimed, on samples the solver records
+    # during the first steps of the same run)
+    learned = args.guess == "learned"
+    run = make(capi.OASIS_MIXED, graph=0 if args.eager else 1,
+               guess=capi.OASIS_GUESS_LEARNED if learned else capi.OASIS_GUESS_PREV_PHI)
     run.set_dirichlet_for_next_step()
-    for _ in range(args.warmup):
-        capi.oasis_step(run.solver, stream, want_stats=False)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize(dev)
-    with Clocks(local) as clk:
-        ms, stats = timed_steps(run, args.steps)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    clocks = clk.summary()
+    train_info = None
+    if learned:
+        from paper_1602_03643_gb300.guess import GuessNet
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            run.record_guess(True)
+            samples = []
+            for k in range(args.train_steps):
+                capi.oasis_step(run.solver, stream, want_stats=False)
+                if k >= 2:
+                    samples.append(run.guess_sample())
+            run.record_guess(False)
+            net = GuessNet(run.mesh, run.n, seed=1)
+            losses = net.fit(samples, epochs=args.train_epochs, lr=2e-3)
+            run.attach_guess_net(net)
+        torch.cuda.synchronize(dev)
+        train_info = {"samples": len(samples), "epochs": args.train_epochs,
+                      "adam_updates": len(samples) * args.train_epochs,
+                      "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1]),
+                      "setup_s": time.perf_counter() - t0}
+        del samples
+    ms, stats, clocks = timed_form(run)
     if args.minimal:
         return {"minimal": True, "ms_per_step": ms / args.steps, "stats_last": stats[-1]}
     bad = [s for s in stats if s["status"] != 0]
@@ -238,6 +267,21 @@ def run_ours(args, rank, world):
                 "it_u_mean": float(np.mean([max(s["it_u"]) for s in st64])),
                 "it_p_mean": float(np.mean([s["it_p"] for s in st64]))}
 
+    prev_form = None
+    if learned and not args.skip_compare:
+        runp = make(capi.OASIS_MIXED, graph=0 if args.eager else 1, guess=capi.OASIS_GUESS_PREV_PHI)
+        runp.set_dirichlet_for_next_step()
+        msp, stp, _ = timed_form(runp)
+        runp.close()
+        prev_form = {"form": "mixed, batched, graph, previous-phi guess (no network)",
+                     "steps_per_s": world * args.steps / (msp / 1e3), "ms_per_step": msp / args.steps,
+                     "it_p_mean": float(np.mean([s["it_p"] for s in stp]))}
+    if learned:
+        gr = np.array([s["guess_res"] for s in stats])
+        train_info |= {"used_fraction": float(np.mean([s["guess_used"] == capi.OASIS_GUESS_LEARNED
+                                                       for s in stats])),
+                       "residual_ratio_mean": float(np.mean(gr[:, 0] / np.maximum(gr[:, 1], 1e-300)))}
+
     it_u = float(np.mean([max(s["it_u"]) for s in stats]))
     it_p = float(np.mean([s["it_p"] for s in stats]))
     sw_u = float(np.mean([s["sweeps_u"] for s in stats]))
@@ -246,15 +290,19 @@ def run_ours(args, rank, world):
     # and (all but the last) a correction, 5 per BiCGStab iteration; pressure: u^I,
     # rhs and guess 3, per sweep residual + CG start + (all but the last) correction,
     # 1 per CG iteration; update 1
-    launches = int(round(args.steps * (4 + 2 * sw_u + 3 * sw_p + 5 * it_u + it_p)))
+    # learned guess: input scales, inputs, two network layers, judge
+    launches = int(round(args.steps * (4 + 2 * sw_u + 3 * sw_p + 5 * it_u + it_p + (5 if learned else 0))))
     run.close()
 
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed: f32 inner Krylov, f64 residual)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed: f32 inner Krylov, f64 residual)"
+                 + ("; bf16 network weights, f32 accumulation" if learned else ""),
         "data": "synthetic (seeded Taylor-Green initial field on a Kuhn tetrahedral mesh)",
-        "config": workload_config(args.workload, pb, "mixed") | {"parallelism": f"replicas x{world}"},
+        "config": workload_config(args.workload, pb, "mixed") | {
+            "parallelism": f"replicas x{world}",
+            "pressure_guess": "learned (judged against previous phi)" if learned else "previous phi"},
         "e2e": {"value": world * k_e2e / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -263,6 +311,8 @@ def run_ours(args, rank, world):
         "solver": {"it_u_mean": it_u, "it_p_mean": it_p, "sweeps_u_mean": sw_u, "sweeps_p_mean": sw_p,
                    "failed_steps": len(bad), "res_p_last": stats[-1]["res_p"]},
         "fp64_gpu": fp64,
+        "mixed_prev_phi": prev_form,
+        "learned_guess": train_info,
         "kernel_time_eager_2steps": kernel_share,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -336,6 +386,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-compare", action="store_true",
+                    help="do not time the previous-phi form beside the learned one")
+    ap.add_argument("--guess", default="learned", choices=["learned", "prev"])
+    ap.add_argument("--train-steps", type=int, default=14)
+    ap.add_argument("--train-epochs", type=int, default=60)
     ap.add_argument("--minimal", action="store_true",
                     help="only the warm-up and timed steps (for profiler captures)")
     ap.add_argument("--eager", action="store_true",

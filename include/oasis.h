@@ -270,12 +270,14 @@ int oasis_get_guess_sample(oasis_solver* s, float* features, float* target, void
 
 /* Kernel families timed by oasis_profile (eager mode only; graph steps are not
  * instrumented). */
-#define OASIS_PROF_PCG_SPMV 0      /* q = K p of the pressure CG */
+#define OASIS_PROF_PCG_SPMV 0      /* fused pressure-CG iteration: w = K M^-1 r on SELL-32
+                                      with the vector updates and the three dot products */
 #define OASIS_PROF_BICG_SPMM 1     /* the d-RHS products of the tentative BiCGStab */
 #define OASIS_PROF_ASSEMBLE 2      /* fused convection assembly + Algorithm 2 row pass */
-#define OASIS_PROF_PCG_UPDATE 3    /* vector update + reductions of the pressure CG */
+#define OASIS_PROF_PCG_UPDATE 3    /* CG start of each refinement sweep (w0 = K M^-1 r0, dots) */
 #define OASIS_PROF_UPDATE 4        /* lumped velocity update + rotation */
 #define OASIS_PROF_PRESSURE_RHS 5  /* pressure right-hand side */
+#define OASIS_PROF_GUESS 6         /* learned guess: input scaling, network forward, judge */
 
 /* enable = 1: from now on, eager steps record CUDA events around the launches
  * of the kernel families above; the counters are reset by every call. */

@@ -273,7 +273,7 @@ def oasis_get_tentative_system(solver, dim, n, nnz, stream=None):
 
 
 PROF_FAMILIES = {"pcg_spmv": 0, "bicg_spmm": 1, "assemble": 2, "pcg_update": 3, "update": 4,
-                 "pressure_rhs": 5}
+                 "pressure_rhs": 5, "guess": 6}
 
 
 def oasis_profile(solver, enable=True):

@@ -1202,6 +1202,7 @@ struct StepImplT final : StepImpl {
         Sv.prof_end(s, pr);
         const bool learned = Sv.prm.guess == OASIS_GUESS_LEARNED && Sv.net;
         int mode = Sv.prm.guess == OASIS_GUESS_ZERO ? OASIS_GUESS_ZERO : OASIS_GUESS_PREV_PHI;
+        const int pg = Sv.prof_begin(s, OASIS_PROF_GUESS);
         if (learned || Sv.record) {
             k_guess_scales<P><<<ge_n, kBlock, 0, s>>>(a);
             k_guess_features<P><<<ge_n, kBlock, 0, s>>>(a);
@@ -1213,6 +1214,7 @@ struct StepImplT final : StepImpl {
             OASIS_CUDA(cudaGetLastError());
             mode = OASIS_GUESS_LEARNED;
         }
+        Sv.prof_end(s, pg);
         k_phi_guess<P><<<ge_n, kBlock, 0, s>>>(a, mode);
         OASIS_CUDA(cudaGetLastError());
         Sv.run_loops(
