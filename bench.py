@@ -187,6 +187,7 @@ def run_ours(args, rank, world):
                       "setup_s": time.perf_counter() - t0}
         del samples
     ms, stats, clocks = timed_form(run)
+    tuning = capi.oasis_get_tuning(run.solver)
     if args.minimal:
         return {"minimal": True, "ms_per_step": ms / args.steps, "stats_last": stats[-1]}
     bad = [s for s in stats if s["status"] != 0]
@@ -212,7 +213,12 @@ def run_ours(args, rank, world):
     d2h = (pb.mesh.dim + 1) * N * 8
 
     # ---- dominant kernel, timed live with CUDA events (eager steps, same solver)
-    run_e = make(capi.OASIS_MIXED, graph=0)
+    run_e = make(capi.OASIS_MIXED, graph=0,
+                 guess=capi.OASIS_GUESS_LEARNED if learned else capi.OASIS_GUESS_PREV_PHI)
+    net_e = None
+    if learned:
+        net_e = GuessNet(run_e.mesh, run_e.n, params=net.get_params())
+        run_e.attach_guess_net(net_e)
     run_e.set_dirichlet_for_next_step()
     capi.oasis_step(run_e.solver, stream, want_stats=False)
     capi.oasis_profile(run_e.solver, True)
@@ -313,6 +319,7 @@ def run_ours(args, rank, world):
         "fp64_gpu": fp64,
         "mixed_prev_phi": prev_form,
         "learned_guess": train_info,
+        "cg_autotune": tuning,
         "kernel_time_eager_2steps": kernel_share,
     }
     if rank == 0 and not args.no_cpu_baseline:

@@ -88,9 +88,23 @@ typedef struct oasis_params {
     int32_t use_graph;     /* 1: the whole step runs as one CUDA graph, Krylov loops as
                               conditional WHILE nodes; 0: eager launches with host polls */
     int32_t guess;         /* OASIS_GUESS_* */
-    int32_t spmv_lanes;    /* lanes per CSR row in the sparse kernels: 0 = autotune at
-                              solver creation, else 4, 8, 16 or 32 */
+    int32_t spmv_variant;  /* shape of the pressure-CG iteration kernel: 0 = autotune at
+                              solver creation (every candidate timed on this matrix, the
+                              fastest kept); k >= 1 = candidate k of oasis_get_tuning */
 } oasis_params;
+
+/* Candidate shapes of the pressure-CG iteration kernel (SELL-32, one warp per
+ * 32 rows) and what the autotuner measured.  A shape is the number of entries
+ * per lane whose column/value loads are issued before their gathers, and the
+ * resident blocks per SM that the register budget is sized for. */
+#define OASIS_MAX_VARIANTS 16
+typedef struct oasis_tuning {
+    int32_t n_variants;
+    int32_t chosen;                        /* 1-based candidate in use */
+    int32_t chunk[OASIS_MAX_VARIANTS];
+    int32_t min_blocks[OASIS_MAX_VARIANTS];
+    double us[OASIS_MAX_VARIANTS];         /* median time per launch; 0 if not timed */
+} oasis_tuning;
 
 /* Per-step solver statistics. */
 typedef struct oasis_step_stats {
@@ -188,7 +202,9 @@ int oasis_spmv_dot_f64_noalloc(const oasis_mesh* mesh, int32_t which, const doub
  * The pressure has no Dirichlet condition: its right-hand side is projected on
  * sum_i b_i = 0 and p is normalised to zero mean after each solve.
  * Allocates every device buffer the step needs (no allocation afterwards).
- * With spmv_lanes = 0 the sparse kernels are autotuned here (timed on `stream`). */
+ * With spmv_variant = 0 the CG iteration kernel is autotuned here (timed on
+ * `stream`; every candidate computes the same sums in the same order, so the
+ * choice changes the speed, not the result). */
 int oasis_solver_create(oasis_mesh* mesh, const oasis_params* params, int64_t n_dirichlet,
                         const int32_t* dirichlet_dofs, void* stream, oasis_solver** out);
 
@@ -267,6 +283,9 @@ int oasis_solver_record_guess(oasis_solver* s, int32_t on);
 /* Training sample of the last step: the inputs [n_dofs][3] and the target
  * phi / s_phi [n_dofs] (device arrays). */
 int oasis_get_guess_sample(oasis_solver* s, float* features, float* target, void* stream);
+
+/* What the autotuner of oasis_solver_create chose for this solver. */
+int oasis_get_tuning(const oasis_solver* s, oasis_tuning* out);
 
 /* Kernel families timed by oasis_profile (eager mode only; graph steps are not
  * instrumented). */

@@ -39,7 +39,18 @@ class oasis_params(C.Structure):
                 ("rtol_u", C.c_double), ("rtol_p", C.c_double),
                 ("max_it_u", C.c_int32), ("max_it_p", C.c_int32), ("precision", C.c_int32),
                 ("inner_rtol", C.c_double), ("batch_rhs", C.c_int32), ("use_graph", C.c_int32),
-                ("guess", C.c_int32), ("spmv_lanes", C.c_int32)]
+                ("guess", C.c_int32), ("spmv_variant", C.c_int32)]
+
+
+class oasis_tuning(C.Structure):
+    _fields_ = [("n_variants", C.c_int32), ("chosen", C.c_int32), ("chunk", C.c_int32 * 16),
+                ("min_blocks", C.c_int32 * 16), ("us", C.c_double * 16)]
+
+    def as_dict(self):
+        n = self.n_variants
+        return {"chosen": self.chosen,
+                "candidates": [{"chunk": self.chunk[k], "min_blocks": self.min_blocks[k], "us": self.us[k]}
+                               for k in range(n)]}
 
 
 class oasis_step_stats(C.Structure):
@@ -101,6 +112,7 @@ SIGNATURES = {
     "oasis_solver_set_guess_net": (C.c_int, [P, P]),
     "oasis_solver_record_guess": (C.c_int, [P, I32]),
     "oasis_get_guess_sample": (C.c_int, [P, DPTR, DPTR, P]),
+    "oasis_get_tuning": (C.c_int, [P, C.POINTER(oasis_tuning)]),
     "oasis_solver_destroy": (None, [P]),
     "oasis_mesh_destroy": (None, [P]),
 }
@@ -205,7 +217,7 @@ def oasis_spmv_dot_f64_noalloc(mesh, which, x, y, xy, stream=None):
 
 def make_params(nu, dt, f=(0.0, 0.0, 0.0), rtol_u=1e-8, rtol_p=1e-8, max_it_u=1000, max_it_p=20000,
                 precision=OASIS_FP64, inner_rtol=1e-4, batch_rhs=1, use_graph=0, guess=OASIS_GUESS_ZERO,
-                spmv_lanes=0):
+                spmv_variant=0):
     p = oasis_params()
     p.nu, p.dt = nu, dt
     ff = list(f) + [0.0] * (3 - len(f))
@@ -214,7 +226,7 @@ def make_params(nu, dt, f=(0.0, 0.0, 0.0), rtol_u=1e-8, rtol_p=1e-8, max_it_u=10
     p.rtol_u, p.rtol_p = rtol_u, rtol_p
     p.max_it_u, p.max_it_p = max_it_u, max_it_p
     p.precision, p.inner_rtol = precision, inner_rtol
-    p.batch_rhs, p.use_graph, p.guess, p.spmv_lanes = batch_rhs, use_graph, guess, spmv_lanes
+    p.batch_rhs, p.use_graph, p.guess, p.spmv_variant = batch_rhs, use_graph, guess, spmv_variant
     return p
 
 
@@ -333,6 +345,12 @@ def oasis_solver_record_guess(solver, on=True):
 
 def oasis_get_guess_sample(solver, features, target, stream=None):
     check(lib().oasis_get_guess_sample(solver, _ptr(features), _ptr(target), _stream(stream)))
+
+
+def oasis_get_tuning(solver):
+    t = oasis_tuning()
+    check(lib().oasis_get_tuning(solver, C.byref(t)))
+    return t.as_dict()
 
 
 def oasis_solver_destroy(solver):

@@ -177,6 +177,7 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     OASIS_CHECK(prm->max_it_u > 0 && prm->max_it_p > 0, OASIS_EINVAL, "iteration caps must be > 0");
     OASIS_CHECK(prm->precision == OASIS_FP64 || prm->precision == OASIS_MIXED, OASIS_EINVAL, "precision");
     OASIS_CHECK(prm->guess >= 0 && prm->guess <= 2, OASIS_EINVAL, "guess");
+    OASIS_CHECK(prm->spmv_variant >= 0 && prm->spmv_variant <= OASIS_MAX_VARIANTS, OASIS_EINVAL, "spmv_variant");
     OASIS_CHECK(n_dir >= 0 && (n_dir == 0 || dir), OASIS_EINVAL, "dirichlet dofs");
     OASIS_CHECK(m->max_row <= 64, OASIS_EMESH, "rows with more than 64 pattern entries are not supported");
     auto S = std::make_unique<Solver>();
@@ -204,6 +205,7 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     S->beta.alloc(vb * m->nc * 4, s);
     for (auto& w : S->w) w.alloc(vb * n * D, s);
     for (auto& w : S->pw) w.alloc(vb * n, s);
+    for (auto& q : S->pq) q.alloc(4 * vb * n, s);
     S->uIv.alloc(vb * n * D, s);
     S->feat.alloc((size_t)n * 3);
     S->gy.alloc((size_t)n);
@@ -220,6 +222,7 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     std::memset(S->h_st, 0, 2 * sizeof(KrylovState));
     for (auto& c : S->cap) OASIS_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
     S->impl.reset(make_step_impl(*S));
+    S->impl->tune(s, prm->spmv_variant);
     OASIS_CUDA(cudaStreamSynchronize(s));
     return S.release();
 }
@@ -626,6 +629,15 @@ int oasis_get_guess_sample(oasis_solver* solver, float* features, float* target,
         cudaStream_t s = as_stream(stream);
         OASIS_CUDA(cudaMemcpyAsync(features, S->feat.p, S->feat.bytes(), cudaMemcpyDeviceToDevice, s));
         S->impl->guess_target(s, target);
+    });
+}
+
+int oasis_get_tuning(const oasis_solver* solver, oasis_tuning* out) {
+    return guarded([&] {
+        const Solver* S = reinterpret_cast<const Solver*>(solver);
+        OASIS_CHECK(S && out, OASIS_EINVAL, "null pointer");
+        std::memset(out, 0, sizeof(*out));
+        S->impl->tuning(out);
     });
 }
 

@@ -256,7 +256,22 @@ __device__ __forceinline__ bool grid_sum_lite(T (&v)[NV], double (&tot)[NV], voi
     T s[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) s[k] = 0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    // the block's partials are read 4 per thread at a time (independent loads in
+    // flight) and added in the same order as a plain strided loop would
+    const int G = (int)gridDim.x, B = (int)blockDim.x;
+    int b = threadIdx.x;
+    for (; b + 3 * B < G; b += 4 * B) {
+        T x[4][NV];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) x[u][k] = __ldcg(&partial[(size_t)(b + u * B) * NV + k]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) s[k] += x[u][k];
+    }
+    for (; b < G; b += B) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) s[k] += __ldcg(&partial[(size_t)b * NV + k]);
     }

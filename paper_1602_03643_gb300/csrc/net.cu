@@ -33,7 +33,7 @@ constexpr int kWarps = kBlock / 32;
 
 // all weights as float in shared memory; W2a and W2b also transposed for
 // conflict-free per-lane reads of a column
-struct SW {
+struct alignas(16) SW {
     float w1a[kH * 3], w1b[kH * 3], c1[kH];
     float w2a[kH * kH], w2b[kH * kH];     // [k][l] (row k = output channel)
     float w2aT[kH * kH], w2bT[kH * kH];   // [l][k]
@@ -94,32 +94,153 @@ __device__ __forceinline__ void mean3(const int32_t* __restrict__ rp, const int3
     m[2] = wsum(s2) * invdeg;
 }
 
+// Sum over the neighbours j != i of v[j][lane] (rows of 32 floats): the row's
+// column indices are loaded once, 32 at a time, by the lanes of the warp and
+// broadcast with shuffles, and 8 neighbour rows are requested before any of
+// them is added, so that the warp has 8 independent 128-byte loads in flight.
+// The additions run in the row's column order (skipped entries add 0).
+__device__ __forceinline__ float neighbour_sum(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                               const float* __restrict__ v, int64_t i, int lane) {
+    constexpr int kU = 8;
+    const int32_t b = rp[i], e = rp[i + 1];
+    float s = 0.f;
+    for (int32_t c0 = b; c0 < e; c0 += 32) {
+        const int cnt = min(32, (int)(e - c0));
+        const int32_t mine = lane < cnt ? col[c0 + lane] : -1;
+        for (int t = 0; t < cnt; t += kU) {
+            float x[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int32_t j = __shfl_sync(0xffffffffu, mine, (t + u) & 31);
+                x[u] = (t + u < cnt && j != i) ? v[(size_t)j * kH + lane] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) s += x[u];
+        }
+    }
+    return s;
+}
+
 // mean of h1 over the neighbours, channel = lane
 __device__ __forceinline__ float mean_h(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                         const float* __restrict__ h, int64_t i, int lane, float invdeg) {
-    const int32_t b = rp[i], e = rp[i + 1];
-    float s = 0.f;
-    for (int32_t q = b; q < e; ++q) {
-        const int32_t j = col[q];
-        if (j != i) s += h[(size_t)j * kH + lane];
-    }
-    return s * invdeg;
+    return neighbour_sum(rp, col, h, i, lane) * invdeg;
 }
 
 // ------------------------------------------------------------------ forward
+// The forward layers run 4 rows per warp: a row is served by a group of 8
+// lanes, lane g of the group owning channels 4g..4g+3, so that a neighbour's
+// h1 row is one 16-byte load per lane and a warp keeps 4 rows' loads in flight.
+constexpr int kGroup = 8, kRowsPerWarp = 4;
+
+__device__ __forceinline__ float gsum8(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    return v;
+}
+
 __global__ void __launch_bounds__(kBlock) k_net_l1(NetArgs a) {
     __shared__ SW s;
     load_weights(s, a.p16);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, lg = lane & (kGroup - 1);
     const int64_t w0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * kBlock) >> 5;
-    for (int64_t i = w0; i < a.n; i += nw) {
-        float m[3], invdeg;
-        mean3(a.rp, a.col, a.x, i, lane, m, invdeg);
-        const float* xi = a.x + (size_t)i * 3;
-        float z = s.c1[lane];
+    for (int64_t r0 = w0 * kRowsPerWarp; r0 < a.n; r0 += nw * kRowsPerWarp) {
+        const int64_t i = r0 + (lane >> 3);
+        const bool ok = i < a.n;
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f, cnt = 0.f;
+        float xi[3] = {0.f, 0.f, 0.f};
+        if (ok) {
+            const int32_t b = a.rp[i], e = a.rp[i + 1];
+            for (int32_t q = b + lg; q < e; q += kGroup) {
+                const int32_t j = a.col[q];
+                if (j != i) {
+                    m0 += a.x[(size_t)j * 3];
+                    m1 += a.x[(size_t)j * 3 + 1];
+                    m2 += a.x[(size_t)j * 3 + 2];
+                    cnt += 1.f;
+                }
+            }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) z += s.w1a[lane * 3 + c] * xi[c] + s.w1b[lane * 3 + c] * m[c];
-        a.h1[(size_t)i * kH + lane] = fmaxf(z, 0.f);
+            for (int c = 0; c < 3; ++c) xi[c] = a.x[(size_t)i * 3 + c];
+        }
+        cnt = gsum8(cnt);
+        const float invdeg = cnt > 0.f ? 1.f / cnt : 0.f;
+        const float mm[3] = {gsum8(m0) * invdeg, gsum8(m1) * invdeg, gsum8(m2) * invdeg};
+        if (ok) {
+            float h[4];
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4) {
+                const int k = 4 * lg + c4;
+                float z = s.c1[k];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) z += s.w1a[k * 3 + c] * xi[c] + s.w1b[k * 3 + c] * mm[c];
+                h[c4] = fmaxf(z, 0.f);
+            }
+            reinterpret_cast<float4*>(a.h1)[(size_t)i * (kH / 4) + lg] = make_float4(h[0], h[1], h[2], h[3]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_net_l2(NetArgs a) {
+    __shared__ SW s;
+    load_weights(s, a.p16);
+    const int lane = threadIdx.x & 31, lg = lane & (kGroup - 1), gb = lane & ~(kGroup - 1);
+    const float4* __restrict__ h4 = reinterpret_cast<const float4*>(a.h1);
+    const int64_t w0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * kBlock) >> 5;
+    for (int64_t r0 = w0 * kRowsPerWarp; r0 < a.n; r0 += nw * kRowsPerWarp) {
+        const int64_t i = r0 + (lane >> 3);
+        const bool ok = i < a.n;
+        const int32_t b = ok ? a.rp[i] : 0, e = ok ? a.rp[i + 1] : 0;
+        const int cnt = (int)(e - b);
+        const int maxcnt = __reduce_max_sync(0xffffffffu, cnt);
+        float4 hk = ok ? h4[(size_t)i * (kH / 4) + lg] : make_float4(0.f, 0.f, 0.f, 0.f);
+        // neighbour sum of h1 (entries in column order, 8 loads in flight per lane)
+        float4 ms = make_float4(0.f, 0.f, 0.f, 0.f);
+        float deg = 0.f;
+        for (int c0 = 0; c0 < maxcnt; c0 += kGroup) {
+            const int32_t mine = c0 + lg < cnt ? a.col[b + c0 + lg] : -1;
+            float4 x[kGroup];
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+                const int32_t j = __shfl_sync(0xffffffffu, mine, gb + u);
+                const bool use = j >= 0 && j != i;
+                x[u] = use ? h4[(size_t)j * (kH / 4) + lg] : make_float4(0.f, 0.f, 0.f, 0.f);
+                deg += use ? 1.f : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+                ms.x += x[u].x;
+                ms.y += x[u].y;
+                ms.z += x[u].z;
+                ms.w += x[u].w;
+            }
+        }
+        const float invdeg = deg > 0.f ? 1.f / deg : 0.f;
+        const float hv[4] = {hk.x, hk.y, hk.z, hk.w};
+        const float mv[4] = {ms.x * invdeg, ms.y * invdeg, ms.z * invdeg, ms.w * invdeg};
+        float z[4];
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) z[c4] = s.c2[4 * lg + c4];
+#pragma unroll
+        for (int l = 0; l < kH; ++l) {
+            const float hl = __shfl_sync(0xffffffffu, hv[l & 3], gb + (l >> 2));
+            const float ml = __shfl_sync(0xffffffffu, mv[l & 3], gb + (l >> 2));
+            const float4 wa = reinterpret_cast<const float4*>(s.w2aT)[l * (kH / 4) + lg];
+            const float4 wb = reinterpret_cast<const float4*>(s.w2bT)[l * (kH / 4) + lg];
+            z[0] += wa.x * hl + wb.x * ml;
+            z[1] += wa.y * hl + wb.y * ml;
+            z[2] += wa.z * hl + wb.z * ml;
+            z[3] += wa.w * hl + wb.w * ml;
+        }
+        float y = 0.f;
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) y += s.w3[4 * lg + c4] * fmaxf(z[c4], 0.f);
+        y = gsum8(y);
+        if (ok && lg == 0) {
+            const float* xi = a.x + (size_t)i * 3;
+            a.y[i] = y + s.c3 + s.a0 * xi[1] + s.a1 * xi[2];
+        }
     }
 }
 
@@ -145,23 +266,6 @@ __device__ __forceinline__ float inv_degree(const int32_t* __restrict__ rp, cons
     for (int32_t q = b + lane; q < e; q += 32) cnt += col[q] != i;
     cnt = (int)wsum((float)cnt);
     return cnt > 0 ? 1.f / (float)cnt : 0.f;
-}
-
-__global__ void __launch_bounds__(kBlock) k_net_l2(NetArgs a) {
-    __shared__ SW s;
-    load_weights(s, a.p16);
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * kBlock) >> 5;
-    for (int64_t i = w0; i < a.n; i += nw) {
-        const float invdeg = inv_degree(a.rp, a.col, i, lane);
-        float hk, m2k;
-        const float z = layer2(s, a, i, lane, invdeg, hk, m2k);
-        const float y = wsum(s.w3[lane] * fmaxf(z, 0.f));
-        if (lane == 0) {
-            const float* xi = a.x + (size_t)i * 3;
-            a.y[i] = y + s.c3 + s.a0 * xi[1] + s.a1 * xi[2];
-        }
-    }
 }
 
 // ------------------------------------------------------------------ backward
@@ -249,11 +353,7 @@ __global__ void __launch_bounds__(kBlock) k_net_bwd1(NetArgs a) {
         float dh = 0.f;
 #pragma unroll
         for (int l = 0; l < kH; ++l) dh += s.w2a[l * kH + lane] * __shfl_sync(0xffffffffu, dzi, l);
-        const int32_t b = a.rp[i], e = a.rp[i + 1];
-        for (int32_t q = b; q < e; ++q) {
-            const int32_t j = a.col[q];
-            if (j != i) dh += a.g[(size_t)j * kH + lane];
-        }
+        dh += neighbour_sum(a.rp, a.col, a.g, i, lane);
         const float dz = z > 0.f ? dh : 0.f;
         gc1 += dz;
 #pragma unroll
@@ -356,14 +456,15 @@ NetArgs net_args(Net& N, const float* x, float* y, const float* t) {
 
 void net_forward(Net& N, const float* x, float* y, cudaStream_t s) {
     const NetArgs a = net_args(N, x, y, nullptr);
-    k_net_l1<<<N.grid, kBlock, 0, s>>>(a);
-    k_net_l2<<<N.grid, kBlock, 0, s>>>(a);
+    const int g4 = net_grid((N.n + kRowsPerWarp - 1) / kRowsPerWarp);
+    k_net_l1<<<g4, kBlock, 0, s>>>(a);
+    k_net_l2<<<g4, kBlock, 0, s>>>(a);
     OASIS_CUDA(cudaGetLastError());
 }
 
 void net_backward(Net& N, const float* x, const float* t, float* grad, float* loss, cudaStream_t s) {
     const NetArgs a = net_args(N, x, nullptr, t);
-    k_net_l1<<<N.grid, kBlock, 0, s>>>(a);
+    k_net_l1<<<net_grid((N.n + kRowsPerWarp - 1) / kRowsPerWarp), kBlock, 0, s>>>(a);
     k_net_bwd2<<<N.grid, kBlock, 0, s>>>(a);
     k_net_bwd1<<<N.grid, kBlock, 0, s>>>(a);
     k_net_reduce<<<(kNetParams + 1 + 255) / 256, 256, 0, s>>>(N.partial.p, N.grid, grad ? grad : N.grad.p,

@@ -34,6 +34,14 @@ struct RBuf {
     template <class T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// Per-row state of the pressure CG that neighbours gather: the residual r,
+// w = K M^-1 r, s = K p and M^-1 = 1 / K_ii, as one aligned 4-vector so that a
+// neighbour costs one 16-byte (float) or 32-byte (double) load.
+template <class V>
+struct alignas(4 * sizeof(V)) CgQuad {
+    V r, w, s, d;
+};
+
 template <class P>
 struct StepData {
     using V = typename P::V;
@@ -52,8 +60,9 @@ struct StepData {
     V *A, *dinvA, *beta;
     // BiCGStab work [n][D] (V)
     V *r, *rh, *p, *v, *s, *t, *ph, *sh, *dl;
-    // CG work [n] (V): r, w = A M^{-1} r, s = A p double-buffered; p; delta; x rounded
-    V *pr0, *pr1, *pw0, *pw1, *ps0, *ps1, *pp, *pdl, *xv;
+    // CG work: gathered quads double-buffered by iteration parity; p; delta; x rounded
+    CgQuad<V> *pq0, *pq1;
+    V *pp, *pdl, *xv;
     V* uIv;                           // u^I rounded to V, [n][D]
     float* feat;                      // learned guess: features [n][3]
     float* gy;                        // learned guess: network output [n]
@@ -96,6 +105,10 @@ struct StepImpl {
     virtual void from_state(cudaStream_t s, double* dst_soa, int which, int64_t count, int comps) = 0;
     virtual void a_to_double(cudaStream_t s, double* dst) = 0;
     virtual void guess_target(cudaStream_t s, float* target) = 0;
+    // time the candidate shapes of the CG iteration kernel on this matrix and keep
+    // the fastest (forced = k >= 1 takes shape k untimed)
+    virtual void tune(cudaStream_t s, int forced) = 0;
+    virtual void tuning(oasis_tuning* out) const = 0;
 };
 
 // state buffers addressable by to_state / from_state
@@ -113,7 +126,8 @@ struct Solver {
     RBuf g, u1, u2, du, r0, pstar, x, b, phi, phi_h1, phi_h2;          // S
     RBuf A, dinvA, beta;                                               // V
     RBuf w[9];                                                         // V [n][D]
-    RBuf pw[9];                                                        // V [n]
+    RBuf pw[3];                                                        // V [n]
+    RBuf pq[2];                                                        // CgQuad<V> [n]
     RBuf uIv;                                                          // V [n][D]
     DBuf<float> feat, gy;                                              // learned-guess features / output
     struct Net* net = nullptr;                                         // attached network (not owned)

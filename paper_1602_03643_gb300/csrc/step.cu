@@ -724,8 +724,12 @@ __global__ void __launch_bounds__(kBlock) k_pcg_outer_sell(StepData<P> a, Ctl ct
             const V rv = s_v(s_sub(bi, s_of_acc(kx)));
             const V xv = s_v(a.x[i]);
             if (live) {
-                a.pr0[i] = rv;
-                a.ps0[i] = 0;
+                CgQuad<V> q0;
+                q0.r = rv;
+                q0.w = 0;
+                q0.s = 0;
+                q0.d = a.dinvK[i];
+                a.pq0[i] = q0;
                 a.pp[i] = 0;
                 a.pdl[i] = 0;
             }
@@ -773,12 +777,15 @@ __global__ void __launch_bounds__(kBlock) k_pcg_outer_sell(StepData<P> a, Ctl ct
     }
 }
 
-// Start of an inner CG: w_0 = K M^{-1} r_0, gamma_0, delta_0, alpha_0.
+// Start of an inner CG: w_0 = K M^{-1} r_0, gamma_0, delta_0, alpha_0.  Reads
+// the quads {r_0, 0, 0, M^-1} of pq0 and writes {r_0, w_0, 0, M^-1} to pq1,
+// where the first iteration reads them.
 template <class P>
 __global__ void __launch_bounds__(kBlock, P::mixed ? 8 : 4) k_pcg_init_sell(StepData<P> a, Ctl ctl) {
     using V = typename P::V;
-    using Acc = typename P::Acc;
+    using Q = CgQuad<V>;
     if (a.stp->col_done[0] || a.stp->in_done[0]) return;
+    const Q* __restrict__ q0 = a.pq0;
     V part[2] = {};
     int64_t i, base;
     int len, lane;
@@ -786,13 +793,15 @@ __global__ void __launch_bounds__(kBlock, P::mixed ? 8 : 4) k_pcg_init_sell(Step
         V w = 0;
         for (int k = 0; k < len; ++k) {
             const int64_t q = base + 32 * (int64_t)k;
-            const int32_t j = a.sell_col[q];
-            w += a.Ks[q] * (a.dinvK[j] * a.pr0[j]);
+            const Q g = q0[a.sell_col[q]];
+            w += a.Ks[q] * (g.d * g.r);
         }
         if (i < a.n) {
-            a.pw0[i] = w;
-            const V u = a.dinvK[i] * a.pr0[i];
-            part[0] += a.pr0[i] * u;
+            Q qi = q0[i];
+            qi.w = w;
+            a.pq1[i] = qi;
+            const V u = qi.d * qi.r;
+            part[0] += qi.r * u;
             part[1] += w * u;
         }
     }
@@ -814,19 +823,23 @@ __global__ void __launch_bounds__(kBlock, P::mixed ? 8 : 4) k_pcg_init_sell(Step
     }
 }
 
-// Fused Chronopoulos-Gear iteration (see k_pcg_iter) on SELL-32.
-template <class P>
-__global__ void __launch_bounds__(kBlock, P::mixed ? 8 : 4) k_pcg_iter_sell(StepData<P> a, Ctl ctl) {
+// Fused Chronopoulos-Gear iteration on SELL-32.  With the coefficients of the
+// last reduction, every row forms s = w + beta s, r' = r - alpha s and
+// u' = M^-1 r'; w' = K u' needs u' of the neighbours, which each lane rebuilds
+// from the neighbour's gathered quad instead of waiting for a grid-wide sync.
+// Iteration it_in reads the quads of one buffer and writes the other (parity).
+// C entries per lane have their column and value loads issued together, then
+// their C gathers, then the C products: C trades registers (and so resident
+// warps, MINB blocks per SM) for loads in flight per warp.  The products are
+// summed in entry order for every C, so every shape gives the same bits.
+template <class P, int C, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_pcg_iter_sell(StepData<P> a, Ctl ctl) {
     using V = typename P::V;
-    using Acc = typename P::Acc;
+    using Q = CgQuad<V>;
     if (a.stp->col_done[0] || a.stp->in_done[0]) return;
     const int par = a.stp->it_in & 1;
-    const V* r_o = par ? a.pr1 : a.pr0;
-    const V* w_o = par ? a.pw1 : a.pw0;
-    const V* s_o = par ? a.ps1 : a.ps0;
-    V* r_n = par ? a.pr0 : a.pr1;
-    V* w_n = par ? a.pw0 : a.pw1;
-    V* s_n = par ? a.ps0 : a.ps1;
+    const Q* __restrict__ qo = par ? a.pq0 : a.pq1;
+    Q* __restrict__ qn = par ? a.pq1 : a.pq0;
     const V alpha = coef<P>(a.stp->alpha[0], a.stp->alpha_f[0]);
     const V beta = coef<P>(a.stp->beta[0], a.stp->beta_f[0]);
     V part[3] = {};
@@ -834,41 +847,39 @@ __global__ void __launch_bounds__(kBlock, P::mixed ? 8 : 4) k_pcg_iter_sell(Step
     int len, lane;
     if (sell_lane(a, i, len, base, lane)) {
         V w = 0;
-        int k = 0;
-        for (; k + 2 <= len; k += 2) {
-            V g[2], kv[2];
+        for (int k = 0; k < len; k += C) {
+            int32_t j[C];
+            V kv[C];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < C; ++u) {
                 const int64_t q = base + 32 * (int64_t)(k + u);
-                const int32_t j = a.sell_col[q];
-                kv[u] = a.Ks[q];
-                const V sj = w_o[j] + beta * s_o[j];
-                g[u] = a.dinvK[j] * (r_o[j] - alpha * sj);
+                const bool ok = k + u < len;
+                j[u] = ok ? a.sell_col[q] : 0;
+                kv[u] = ok ? a.Ks[q] : V(0);
             }
+            Q g[C];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) w += kv[u] * g[u];
-        }
-        for (; k < len; ++k) {
-            const int64_t q = base + 32 * (int64_t)k;
-            const int32_t j = a.sell_col[q];
-            const V sj = w_o[j] + beta * s_o[j];
-            w += a.Ks[q] * (a.dinvK[j] * (r_o[j] - alpha * sj));
+            for (int u = 0; u < C; ++u) g[u] = qo[j[u]];
+#pragma unroll
+            for (int u = 0; u < C; ++u)
+                if (k + u < len) w += kv[u] * (g[u].d * (g[u].r - alpha * (g[u].w + beta * g[u].s)));
         }
         if (i < a.n) {
-            const V di = a.dinvK[i];
-            const V ro = r_o[i];
-            const V pv = di * ro + beta * a.pp[i];
-            const V sv = w_o[i] + beta * s_o[i];
+            const Q qi = qo[i];
+            const V pv = qi.d * qi.r + beta * a.pp[i];
+            const V sv = qi.w + beta * qi.s;
             a.pp[i] = pv;
-            s_n[i] = sv;
             a.pdl[i] += alpha * pv;
-            const V rn = ro - alpha * sv;
-            r_n[i] = rn;
-            w_n[i] = w;
-            const V un = di * rn;
-            part[0] += rn * un;
+            Q out;
+            out.r = qi.r - alpha * sv;
+            out.w = w;
+            out.s = sv;
+            out.d = qi.d;
+            qn[i] = out;
+            const V un = qi.d * out.r;
+            part[0] += out.r * un;
             part[1] += w * un;
-            part[2] += rn * rn;
+            part[2] += out.r * out.r;
         }
     }
     double tot[3];
@@ -890,6 +901,31 @@ __global__ void __launch_bounds__(kBlock, P::mixed ? 8 : 4) k_pcg_iter_sell(Step
         if (stop) st->in_done[0] = 1;
         st->it_in += 1;
         set_cond(ctl.use_cond, ctl.h_inner, !stop);
+    }
+}
+
+// Candidate shapes (C, blocks per SM) of the CG iteration for the autotuner.
+template <class P>
+struct IterVariant {
+    void (*fn)(StepData<P>, Ctl);
+    int chunk, minb;
+};
+
+template <class P>
+static const IterVariant<P>* iter_variant_table(int& count) {
+    if constexpr (P::mixed) {
+        static const IterVariant<P> t[] = {
+            {k_pcg_iter_sell<P, 2, 8>, 2, 8}, {k_pcg_iter_sell<P, 4, 8>, 4, 8}, {k_pcg_iter_sell<P, 4, 6>, 4, 6},
+            {k_pcg_iter_sell<P, 8, 4>, 8, 4}, {k_pcg_iter_sell<P, 8, 3>, 8, 3}, {k_pcg_iter_sell<P, 16, 2>, 16, 2}};
+        count = (int)(sizeof(t) / sizeof(t[0]));
+        return t;
+    } else {
+        static const IterVariant<P> t[] = {{k_pcg_iter_sell<P, 2, 4>, 2, 4},
+                                           {k_pcg_iter_sell<P, 4, 4>, 4, 4},
+                                           {k_pcg_iter_sell<P, 4, 3>, 4, 3},
+                                           {k_pcg_iter_sell<P, 8, 2>, 8, 2}};
+        count = (int)(sizeof(t) / sizeof(t[0]));
+        return t;
     }
 }
 
@@ -1026,6 +1062,8 @@ struct StepImplT final : StepImpl {
         g_rhs = 1, g_upd = 1;
     int ge_n = 1, ge_nd = 1, ge_c = 1;
     int g_sell = 1;
+    int iter_v = 0;                                   // chosen CG iteration shape
+    double tune_us[OASIS_MAX_VARIANTS] = {0};
 
 
     template <class T>
@@ -1069,8 +1107,10 @@ struct StepImplT final : StepImpl {
         a.beta = Sv.beta.as<V>();
         V** w[9] = {&a.r, &a.rh, &a.p, &a.v, &a.s, &a.t, &a.ph, &a.sh, &a.dl};
         for (int q = 0; q < 9; ++q) *w[q] = Sv.w[q].as<V>();
-        V** pw[9] = {&a.pr0, &a.pr1, &a.pw0, &a.pw1, &a.ps0, &a.ps1, &a.pp, &a.pdl, &a.xv};
-        for (int q = 0; q < 9; ++q) *pw[q] = Sv.pw[q].as<V>();
+        V** pw[3] = {&a.pp, &a.pdl, &a.xv};
+        for (int q = 0; q < 3; ++q) *pw[q] = Sv.pw[q].as<V>();
+        a.pq0 = Sv.pq[0].as<CgQuad<V>>();
+        a.pq1 = Sv.pq[1].as<CgQuad<V>>();
         a.uIv = Sv.uIv.as<V>();
         a.feat = Sv.feat.p;
         a.gy = Sv.gy.p;
@@ -1230,7 +1270,7 @@ struct StepImplT final : StepImpl {
             [&](cudaStream_t ss, const Loop& lp) {
                 const Ctl c = ctl_p(lp);
                 const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
-                k_pcg_iter_sell<P><<<g_sell, kBlock, 0, ss>>>(a, c);
+                iter_variants()[iter_v].fn<<<g_sell, kBlock, 0, ss>>>(a, c);
                 Sv.prof_end(ss, pq);
                 OASIS_CUDA(cudaGetLastError());
             },
@@ -1268,6 +1308,67 @@ struct StepImplT final : StepImpl {
         k_from_state<P><<<elem_grid(count * comps), kBlock, 0, s>>>(state_ptr(which), dst, count, comps);
         OASIS_CUDA(cudaGetLastError());
     }
+    const IterVariant<P>* iter_variants() const {
+        int c = 0;
+        return iter_variant_table<P>(c);
+    }
+
+    // Autotuner: every candidate shape of the CG iteration runs on this matrix
+    // (2 untimed + 7 timed launches, CUDA events around each launch, median
+    // kept) against a scratch Krylov state, so the solver's own state is not
+    // touched; the iteration buffers hold no solve yet.  Every shape computes
+    // the same bits, so only speed decides.
+    void tune(cudaStream_t s, int forced) override {
+        int count = 0;
+        const IterVariant<P>* t = iter_variant_table<P>(count);
+        OASIS_CHECK(forced <= count, OASIS_EINVAL, "spmv_variant: no such candidate");
+        for (auto& u : tune_us) u = 0.0;
+        if (forced >= 1) {
+            iter_v = forced - 1;
+            return;
+        }
+        DBuf<KrylovState> scratch;
+        scratch.alloc(1);
+        StepData<P> d = a;
+        d.stp = scratch.p;
+        const Ctl c{};
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        OASIS_CUDA(cudaEventCreate(&e0));
+        OASIS_CUDA(cudaEventCreate(&e1));
+        constexpr int kWarm = 2, kTimed = 7;
+        int best = 0;
+        for (int v = 0; v < count; ++v) {
+            float ts[kTimed];
+            for (int r = 0; r < kWarm + kTimed; ++r) {
+                OASIS_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(KrylovState), s));
+                OASIS_CUDA(cudaEventRecord(e0, s));
+                t[v].fn<<<g_sell, kBlock, 0, s>>>(d, c);
+                OASIS_CUDA(cudaGetLastError());
+                OASIS_CUDA(cudaEventRecord(e1, s));
+                OASIS_CUDA(cudaEventSynchronize(e1));
+                if (r >= kWarm) OASIS_CUDA(cudaEventElapsedTime(&ts[r - kWarm], e0, e1));
+            }
+            std::sort(ts, ts + kTimed);
+            tune_us[v] = 1e3 * (double)ts[kTimed / 2];
+            if (tune_us[v] < tune_us[best]) best = v;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        iter_v = best;
+    }
+
+    void tuning(oasis_tuning* out) const override {
+        int count = 0;
+        const IterVariant<P>* t = iter_variant_table<P>(count);
+        out->n_variants = count;
+        out->chosen = iter_v + 1;
+        for (int v = 0; v < count; ++v) {
+            out->chunk[v] = t[v].chunk;
+            out->min_blocks[v] = t[v].minb;
+            out->us[v] = tune_us[v];
+        }
+    }
+
     void guess_target(cudaStream_t s, float* target) override {
         k_guess_target<P><<<ge_n, kBlock, 0, s>>>(a, target);
         OASIS_CUDA(cudaGetLastError());

@@ -216,6 +216,37 @@ def test_graph_equals_eager_bitwise():
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_cg_shapes_bitwise_equal_and_tuned(precision):
+    """Every candidate shape of the CG iteration kernel gives the same bits; the
+    autotuner timed every candidate and kept the fastest."""
+    from paper_1602_03643_gb300.driver import IPCSRun
+    c = capi()
+    pb = WP.stress_cube(12, ordering="random")
+    run = IPCSRun(pb, precision=precision, rtol_u=1e-9, rtol_p=1e-9, use_graph=1)
+    try:
+        tun = c.oasis_get_tuning(run.solver)
+    finally:
+        run.close()
+    cands = tun["candidates"]
+    assert len(cands) >= 3
+    assert all(x["us"] > 0 for x in cands)
+    assert cands[tun["chosen"] - 1]["us"] == min(x["us"] for x in cands)
+    out = []
+    for v in range(1, len(cands) + 1):
+        run = IPCSRun(pb, precision=precision, rtol_u=1e-9, rtol_p=1e-9, use_graph=1, spmv_variant=v)
+        try:
+            assert c.oasis_get_tuning(run.solver)["chosen"] == v
+            st = run.step(3)
+            out.append((run.fields(), st.it_p))
+        finally:
+            run.close()
+    for f, it in out[1:]:
+        assert it == out[0][1]
+        for a, b in zip(f, out[0][0]):
+            np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_batched_equals_unbatched(precision):
     from paper_1602_03643_gb300.driver import IPCSRun
     out = []
