@@ -104,6 +104,23 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------------- ranks
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time: every rank times its own replica of the workload."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(steps, world, ms_max):
+    """Steps of all ranks over the slowest rank's time (weak scaling: one replica per GPU)."""
+    return world * steps / (ms_max / 1e3)
+
+
 # ---------------------------------------------------------------------- ours
 def run_ours(args, rank, world):
     import numpy as np
@@ -152,11 +169,7 @@ def run_ours(args, rank, world):
         with Clocks(local) as clk:
             ms, stats = timed_steps(run, args.steps)
         torch.cuda.synchronize(dev)
-        if world > 1:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, stats, clk.summary()
+        return max_over_ranks(ms, world, dev), stats, clk.summary()
 
     # ---- the headline form: mixed precision + batched + graph + learned guess
     # (the network is trained first, untimed, on samples the solver records
@@ -192,7 +205,7 @@ def run_ours(args, rank, world):
         return {"minimal": True, "ms_per_step": ms / args.steps, "stats_last": stats[-1]}
     bad = [s for s in stats if s["status"] != 0]
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = whole_job_value(args.steps, world, ms)
 
     # ---- e2e: the same step through the public API with host buffers each step
     g_host = torch.empty((pb.mesh.dim, max(1, len(pb.dirichlet))), dtype=torch.float64).pin_memory()
@@ -201,6 +214,8 @@ def run_ours(args, rank, world):
     p_host = torch.empty(N, dtype=torch.float64).pin_memory()
     k_e2e = max(3, args.steps // 2)
     torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     for _ in range(k_e2e):
         if len(pb.dirichlet):
@@ -208,7 +223,8 @@ def run_ours(args, rank, world):
         capi.oasis_step(run.solver, stream, want_stats=False)
         capi.oasis_get_fields(run.solver, pb.mesh.dim, N, False, u=u_host.numpy(), p=p_host.numpy(),
                               phi=None, stream=stream)
-    e2e_s = time.perf_counter() - t0
+    torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(1e3 * (time.perf_counter() - t0), world, dev) / 1e3
     h2d = len(pb.dirichlet) * pb.mesh.dim * 8
     d2h = (pb.mesh.dim + 1) * N * 8
 

@@ -1,0 +1,60 @@
+"""Multi-rank bench logic on CPU (gloo, world size 2): every rank times its own
+replica, rank 0 reports the steps of all ranks over the slowest rank's time,
+and the reference arm runs on rank 0 only."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = 100.0 * (rank + 1)
+        m = bench.max_over_ranks(ms, world, "cpu")
+        v = bench.whole_job_value(10, world, m)
+
+        class A:
+            steps, warmup, workload, cpu_budget = 1, 3, "tg2d_32", 1.0
+        ref = bench.run_reference(A, rank, world)
+        out.put((rank, m, v, ref is None))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_max_time_and_whole_job_value():
+    torch = pytest.importorskip("torch")
+    mp = torch.multiprocessing.get_context("spawn")
+    q = mp.Queue()
+    port = _free_port()
+    procs = [mp.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=240) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, m, v, ref_none in res:
+        assert m == 200.0                      # the slowest rank's time on every rank
+        assert v == pytest.approx(2 * 10 / 0.2)
+        assert ref_none == (rank != 0)         # reference arm: rank 0 only
+
+
+def test_single_rank_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(12.5, 1, "cpu") == 12.5
+    assert bench.whole_job_value(4, 1, 500.0) == pytest.approx(8.0)

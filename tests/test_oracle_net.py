@@ -1,6 +1,8 @@
-"""Pins of the learned-guess oracle: finite differences of the loss, the
-gradient of the mean aggregation, bfloat16 rounding, and a training sanity
-check (the loss of a solvable toy problem falls)."""
+"""Pins of the learned-guess oracle: closed forms of the forward pass on a path
+graph (each term and each weight's orientation isolated by a choice of
+weights, neighbour means taken from the graph itself), permutation
+equivariance, finite differences of the loss, the mean aggregation,
+bfloat16 rounding, and a training sanity check."""
 import numpy as np
 import pytest
 
@@ -82,3 +84,90 @@ def test_features_scale_invariance():
     x2, s2 = N.features(7 * b, 3 * f1, 3 * f2)
     np.testing.assert_allclose(x1, x2, rtol=1e-12)
     assert abs(s2 / s1 - 3) < 1e-12
+
+
+# ---------------------------------------------------------------- forward pins
+def _path_graph(n):
+    """CSR pattern of a path 0-1-...-(n-1) with its diagonal (like a P1 pattern)."""
+    rp, col = [0], []
+    for i in range(n):
+        col += [j for j in (i - 1, i, i + 1) if 0 <= j < n]
+        rp.append(len(col))
+    return np.array(rp), np.array(col)
+
+
+def _neighbour_mean_path(v):
+    """Mean over the path neighbours, written from the graph, not the operator."""
+    n = v.shape[0]
+    out = np.empty_like(v)
+    for i in range(n):
+        nb = [j for j in (i - 1, i + 1) if 0 <= j < n]
+        out[i] = sum(v[j] for j in nb) / len(nb)
+    return out
+
+
+def _zero():
+    return {name: np.zeros(shape) for name, shape in N.SHAPES}
+
+
+def test_forward_readout_skip_terms_closed_form():
+    rp, col = _path_graph(7)
+    x = np.random.default_rng(1).normal(size=(7, 3))
+    P = _zero()
+    P["c3"][0], P["a"][:] = 0.25, [0.5, -2.0]
+    y, _ = N.forward(N.pack(P), x, N.mean_operator(rp, col))
+    np.testing.assert_allclose(y, 0.25 + 0.5 * x[:, 1] - 2.0 * x[:, 2], rtol=0, atol=1e-15)
+
+
+def test_forward_neighbour_mean_and_weight_orientation():
+    """Layer 1 through W1b only, layer 2 through a shift in W2a: y = relu(mean x_0)."""
+    rp, col = _path_graph(9)
+    x = np.random.default_rng(2).normal(size=(9, 3))
+    P = _zero()
+    for c in range(3):
+        P["W1b"][c, c] = 1.0              # h1_c = relu(mean_N x_c)
+    for k in range(1, N.H):
+        P["W2a"][k, k - 1] = 1.0          # h2_k = relu(h1_{k-1}): row k = output channel
+    P["w3"][1] = 1.0
+    y, _ = N.forward(N.pack(P), x, N.mean_operator(rp, col))
+    np.testing.assert_allclose(y, np.maximum(_neighbour_mean_path(x)[:, 0], 0.0), rtol=0, atol=1e-14)
+
+
+def test_forward_second_aggregation_and_biases():
+    """Layer 1 through W1a, layer 2 through W2b: y = mean_N relu(x_1) + biases."""
+    rp, col = _path_graph(8)
+    x = np.random.default_rng(3).normal(size=(8, 3))
+    P = _zero()
+    for c in range(3):
+        P["W1a"][c, c] = 1.0              # h1_c = relu(x_c)
+    P["W2b"][4, 1] = 1.0                  # h2_4 = relu(mean_N h1_1 + c2_4)
+    P["c2"][4] = 0.5
+    P["w3"][4] = 2.0
+    P["c3"][0] = -1.0
+    y, _ = N.forward(N.pack(P), x, N.mean_operator(rp, col))
+    want = 2.0 * np.maximum(_neighbour_mean_path(np.maximum(x, 0.0))[:, 1] + 0.5, 0.0) - 1.0
+    np.testing.assert_allclose(y, want, rtol=0, atol=1e-14)
+    # the layer-1 bias reaches the output through W2a
+    P = _zero()
+    P["c1"][:] = 1.0
+    P["W2a"][0, :] = 1.0 / N.H
+    P["c2"][0] = -0.25
+    P["w3"][0] = 3.0
+    y, _ = N.forward(N.pack(P), x, N.mean_operator(rp, col))
+    np.testing.assert_allclose(y, 3.0 * 0.75, rtol=0, atol=1e-14)
+
+
+def test_forward_permutation_equivariance():
+    m = WM.jitter_interior(WM.box_mesh_3d(3, 3, 2), 0.2, 1 / 3, seed=5)
+    rp, col = _graph(m)
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(m.n_dofs, 3))
+    p = N.init_params(7)
+    y, _ = N.forward(p, x, N.mean_operator(rp, col))
+    perm = rng.permutation(m.n_dofs)
+    mp = WM.renumber_dofs(m, perm)
+    rp2, col2 = _graph(mp)
+    xp = np.empty_like(x)
+    xp[perm] = x                          # dof d of the old numbering is perm[d] in the new one
+    y2, _ = N.forward(p, xp, N.mean_operator(rp2, col2))
+    np.testing.assert_allclose(y2[perm], y, rtol=0, atol=1e-12)
