@@ -243,15 +243,16 @@ def run_ours(args, rank, world):
         capi.oasis_step(run_e.solver, stream, want_stats=False)
     torch.cuda.synchronize(dev)
     fam = {f: capi.oasis_profile_read(run_e.solver, f) for f in capi.PROF_FAMILIES}
-    run_e.close()
     nnz = run.nnz
     n_spmv, ms_spmv = fam["pcg_spmv"]
     # algorithmic bytes of one fused pressure-CG iteration (SELL-32 K, float32
-    # values, int32 columns): K values + columns 8 nnz; slice pointers/lengths
-    # 8 per 32 rows; vectors read dinv, r, w, s, p, x-delta (24 N) and written
-    # p, s, x-delta, r, w (20 N)
+    # values, int32 columns or 16-bit offsets, as the tuned kernel reads them):
+    # K values + columns; slice pointers/lengths 8 per 32 rows; vectors read
+    # dinv, r, w, s, p, x-delta (24 N) and written p, s, x-delta, r, w (20 N)
     n_slices = (N + 31) // 32
-    spmv_bytes = 8 * nnz + 44 * N + 8 * n_slices
+    tun_e = capi.oasis_get_tuning(run_e.solver)
+    col_bytes = 2 if tun_e["candidates"][tun_e["chosen"] - 1]["col16"] else 4
+    spmv_bytes = (4 + col_bytes) * nnz + 44 * N + 8 * n_slices
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -259,8 +260,10 @@ def run_ours(args, rank, world):
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = spmv_bytes / (ms_spmv / max(n_spmv, 1) / 1e3) / 1e9 if n_spmv else None
+    run_e.close()
     roofline = {"bound": "hbm",
                 "kernel": "k_pcg_iter_sell<Mixed> (fused CG iteration: w = K M^-1 r on SELL-32 + vector updates + 3 dots)",
+                "shape": tun_e["candidates"][tun_e["chosen"] - 1],
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if "hbm_gbs" in peaks

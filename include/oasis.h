@@ -95,14 +95,24 @@ typedef struct oasis_params {
 
 /* Candidate shapes of the pressure-CG iteration kernel (SELL-32, one warp per
  * 32 rows) and what the autotuner measured.  A shape is the number of entries
- * per lane whose column/value loads are issued before their gathers, and the
- * resident blocks per SM that the register budget is sized for. */
+ * per lane whose column/value loads are issued before their gathers, the
+ * resident blocks per SM that the register budget is sized for, whether the
+ * next chunk's loads are issued before the current products (prefetch), and
+ * whether columns are read as 16-bit offsets from the row taken modulo the dof
+ * count (col16; only where every offset fits, else the candidate is not timed),
+ * and whether the slice's values and columns are streamed into shared memory
+ * by the bulk-copy engine, two slices ahead per warp (streamed). */
 #define OASIS_MAX_VARIANTS 16
 typedef struct oasis_tuning {
     int32_t n_variants;
     int32_t chosen;                        /* 1-based candidate in use */
     int32_t chunk[OASIS_MAX_VARIANTS];
     int32_t min_blocks[OASIS_MAX_VARIANTS];
+    int32_t prefetch[OASIS_MAX_VARIANTS];
+    int32_t col16[OASIS_MAX_VARIANTS];
+    int32_t streamed[OASIS_MAX_VARIANTS];  /* 1: values and columns streamed into shared
+                                              memory by bulk copies (persistent grid) */
+    int32_t warps_per_block[OASIS_MAX_VARIANTS];
     double us[OASIS_MAX_VARIANTS];         /* median time per launch; 0 if not timed */
 } oasis_tuning;
 

@@ -44,12 +44,16 @@ class oasis_params(C.Structure):
 
 class oasis_tuning(C.Structure):
     _fields_ = [("n_variants", C.c_int32), ("chosen", C.c_int32), ("chunk", C.c_int32 * 16),
-                ("min_blocks", C.c_int32 * 16), ("us", C.c_double * 16)]
+                ("min_blocks", C.c_int32 * 16), ("prefetch", C.c_int32 * 16), ("col16", C.c_int32 * 16),
+                ("streamed", C.c_int32 * 16), ("warps_per_block", C.c_int32 * 16), ("us", C.c_double * 16)]
 
     def as_dict(self):
         n = self.n_variants
         return {"chosen": self.chosen,
-                "candidates": [{"chunk": self.chunk[k], "min_blocks": self.min_blocks[k], "us": self.us[k]}
+                "candidates": [{"chunk": self.chunk[k], "min_blocks": self.min_blocks[k],
+                                "prefetch": self.prefetch[k], "col16": self.col16[k],
+                                "streamed": self.streamed[k], "warps_per_block": self.warps_per_block[k],
+                                "us": self.us[k]}
                                for k in range(n)]}
 
 

@@ -91,6 +91,10 @@ struct Mesh {
     // entry to its SELL position.
     int64_t n_sell = 0;
     DBuf<int32_t> sell_ptr, sell_len, sell_col, sell_of_csr;
+    // The same columns as 16-bit offsets from the row, taken modulo n (so that
+    // periodic wrap-around neighbours stay short): j = row + d, then + n if
+    // negative, - n if >= n.  Built only when every offset fits (empty else).
+    DBuf<int16_t> sell_dcol;
     DBuf<float> K32s;
     DBuf<double> K64s;
     DBuf<float2> Kffs;

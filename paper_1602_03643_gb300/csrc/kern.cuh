@@ -224,11 +224,12 @@ __device__ __forceinline__ bool grid_sum(A (&v)[NV], double (&tot)[NV], void* pa
 // blocks, one partial per block, and a pairwise-ordered sum of the partials by
 // the block that takes the last ticket.  A handful of instructions per value
 // and warp, against ~100 for a float-float tree.
+// Stage 1: the block's sum of v (warp shuffle trees, then the warps' sums in a
+// shuffle tree) stored as partial[index][0..NV).  Every thread of the block
+// calls it; on return the shared scratch may be reused.
 template <int NV, class T>
-__device__ __forceinline__ bool grid_sum_lite(T (&v)[NV], double (&tot)[NV], void* partial_raw, uint32_t* ticket) {
-    T* partial = reinterpret_cast<T*>(partial_raw);
+__device__ __forceinline__ void block_partial_lite(T (&v)[NV], T* partial, int64_t index) {
     __shared__ T sh[NV][32];
-    __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
@@ -243,12 +244,23 @@ __device__ __forceinline__ bool grid_sum_lite(T (&v)[NV], double (&tot)[NV], voi
             T x = lane < nw ? sh[k][lane] : (T)0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0) partial[(size_t)blockIdx.x * NV + k] = x;
+            if (lane == 0) partial[(size_t)index * NV + k] = x;
         }
-        if (lane == 0) {
-            __threadfence();
-            last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-        }
+    }
+    __syncthreads();
+}
+
+// Stage 2: after the block has stored its partials, the block that takes the
+// last ticket sums all `count` partials (pairwise order fixed by the block
+// size) and returns true with the totals; the ticket is reset for the next use.
+template <int NV, class T>
+__device__ __forceinline__ bool grid_finish_lite(double (&tot)[NV], const T* partial, int64_t count, uint32_t* ticket) {
+    __shared__ T sh[NV][32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return false;
@@ -256,10 +268,10 @@ __device__ __forceinline__ bool grid_sum_lite(T (&v)[NV], double (&tot)[NV], voi
     T s[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) s[k] = 0;
-    // the block's partials are read 4 per thread at a time (independent loads in
+    // the partials are read 4 per thread at a time (independent loads in
     // flight) and added in the same order as a plain strided loop would
-    const int G = (int)gridDim.x, B = (int)blockDim.x;
-    int b = threadIdx.x;
+    const int64_t G = count, B = (int64_t)blockDim.x;
+    int64_t b = threadIdx.x;
     for (; b + 3 * B < G; b += 4 * B) {
         T x[4][NV];
 #pragma unroll
@@ -292,6 +304,14 @@ __device__ __forceinline__ bool grid_sum_lite(T (&v)[NV], double (&tot)[NV], voi
         *ticket = 0u;
     }
     return true;
+}
+
+// One partial per block, then the last block sums them.
+template <int NV, class T>
+__device__ __forceinline__ bool grid_sum_lite(T (&v)[NV], double (&tot)[NV], void* partial_raw, uint32_t* ticket) {
+    T* partial = reinterpret_cast<T*>(partial_raw);
+    block_partial_lite<NV, T>(v, partial, blockIdx.x);
+    return grid_finish_lite<NV, T>(tot, partial, gridDim.x, ticket);
 }
 
 // Limit of every bounded device-side wait (~2 s at 2 GHz).

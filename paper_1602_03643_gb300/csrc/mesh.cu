@@ -171,6 +171,29 @@ Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const in
                 }
             }
         }
+        // modular 16-bit offsets, when they fit (the host copy lives until the
+        // stream synchronisation below)
+        std::vector<int16_t> dcol(nsell);
+        {
+            bool fits = true;
+            for (int64_t sl = 0; sl < ns && fits; ++sl) {
+                for (int l = 0; l < 32 && fits; ++l) {
+                    const int64_t i = sl * 32 + l;
+                    for (int k = 0; k < slen[sl]; ++k) {
+                        const int64_t pos = sptr[sl] + 32 * k + l;
+                        int64_t d = ((int64_t)scol[pos] - i) % n;
+                        if (d < 0) d += n;
+                        if (d > n / 2) d -= n;
+                        if (d < -32768 || d > 32767) {
+                            fits = false;
+                            break;
+                        }
+                        dcol[pos] = (int16_t)d;
+                    }
+                }
+            }
+            if (fits) m->sell_dcol.upload(dcol.data(), dcol.size(), s);
+        }
         m->n_sell = nsell;
         m->sell_ptr.upload(sptr.data(), sptr.size(), s);
         m->sell_len.upload(slen.data(), slen.size(), s);

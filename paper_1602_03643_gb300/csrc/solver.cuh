@@ -76,6 +76,7 @@ struct StepData {
     // SELL-32 copy of K
     int64_t n_slices;
     const int32_t *sell_ptr, *sell_len, *sell_col;
+    const int16_t* sell_dcol;         // modular 16-bit column offsets, or null
     const V* Ks;
     const S* Kouts;
 };

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <type_traits>
 
 #include "kern.cuh"
 #include "net.cuh"
@@ -753,6 +754,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_outer_sell(StepData<P> a, Ctl ct
         st->meanp_hi = (float)meanp;
         st->meanp_lo = (float)(meanp - (double)(float)meanp);
         int outer = 0;
+        if (st->status != OASIS_OK) st->col_done[0] = 1;
         if (!st->col_done[0]) {
             const double rr = tot[0];
             st->rr[0] = rr;
@@ -823,16 +825,56 @@ __global__ void __launch_bounds__(kBlock, P::mixed ? 8 : 4) k_pcg_init_sell(Step
     }
 }
 
+// Last block of a CG iteration: beta, alpha of the next iteration from the
+// three reduced dot products (gamma = <r, u>, delta = <w, u>, <r, r>), the
+// inner stopping test, and the loop condition.
+template <class P>
+__device__ __forceinline__ void pcg_iter_finish(const StepData<P>& a, const Ctl& ctl, const double (&tot)[3]) {
+    KrylovState* st = a.stp;
+    const double g = tot[0], dl = tot[1], rr = tot[2];
+    st->it_total[0] += 1;
+    const double g_old = st->rho[0], a_old = st->alpha[0];
+    const double b_new = g_old != 0.0 ? g / g_old : 0.0;
+    const double den = a_old != 0.0 ? dl - b_new * g / a_old : 0.0;
+    const bool brk = !(den > 0.0) || !isfinite(den) || !isfinite(g) || g_old == 0.0;
+    st->beta[0] = b_new;
+    st->alpha[0] = brk ? 0.0 : g / den;
+    st->rho[0] = g;
+    st->rr_in[0] = rr;
+    mirror_coefs(st, 0);
+    const bool stop = brk || st->status != OASIS_OK || !isfinite(rr) || rr <= ctl.inner2 * st->rr0_in[0] ||
+                      rr <= ctl.abs2 * st->bb[0] || st->it_total[0] >= ctl.max_it || st->it_in + 1 >= ctl.sweep_cap;
+    if (stop) st->in_done[0] = 1;
+    st->it_in += 1;
+    set_cond(ctl.use_cond, ctl.h_inner, !stop);
+}
+
+// Column of SELL entry q of row `row`: the int32 index, or the 16-bit offset
+// from the row taken modulo n.
+template <bool D16, class P>
+__device__ __forceinline__ int32_t sell_j(const StepData<P>& a, int64_t q, int32_t row) {
+    if constexpr (D16) {
+        int32_t j = row + (int32_t)a.sell_dcol[q];
+        const int32_t n = (int32_t)a.n;
+        j = j < 0 ? j + n : j;
+        return j >= n ? j - n : j;
+    } else {
+        return a.sell_col[q];
+    }
+}
+
 // Fused Chronopoulos-Gear iteration on SELL-32.  With the coefficients of the
 // last reduction, every row forms s = w + beta s, r' = r - alpha s and
 // u' = M^-1 r'; w' = K u' needs u' of the neighbours, which each lane rebuilds
 // from the neighbour's gathered quad instead of waiting for a grid-wide sync.
 // Iteration it_in reads the quads of one buffer and writes the other (parity).
-// C entries per lane have their column and value loads issued together, then
-// their C gathers, then the C products: C trades registers (and so resident
-// warps, MINB blocks per SM) for loads in flight per warp.  The products are
-// summed in entry order for every C, so every shape gives the same bits.
-template <class P, int C, int MINB>
+// Shape parameters (chosen by the autotuner): C entries per lane have their
+// column and value loads issued together, then their C gathers, then the C
+// products; PF also issues the next chunk's column and value loads before the
+// current products; D16 reads 16-bit column offsets.  C and PF trade registers
+// (and so resident warps, MINB blocks per SM) for loads in flight per warp.
+// The products are summed in entry order for every shape: same bits.
+template <class P, int C, int MINB, bool PF, bool D16>
 __global__ void __launch_bounds__(kBlock, MINB) k_pcg_iter_sell(StepData<P> a, Ctl ctl) {
     using V = typename P::V;
     using Q = CgQuad<V>;
@@ -846,23 +888,37 @@ __global__ void __launch_bounds__(kBlock, MINB) k_pcg_iter_sell(StepData<P> a, C
     int64_t i, base;
     int len, lane;
     if (sell_lane(a, i, len, base, lane)) {
+        const int32_t row = (int32_t)i;
         V w = 0;
-        for (int k = 0; k < len; k += C) {
-            int32_t j[C];
-            V kv[C];
+        int32_t j[C];
+        V kv[C];
+        auto fetch = [&](int k, int32_t (&jj)[C], V (&kk)[C]) {
 #pragma unroll
             for (int u = 0; u < C; ++u) {
                 const int64_t q = base + 32 * (int64_t)(k + u);
                 const bool ok = k + u < len;
-                j[u] = ok ? a.sell_col[q] : 0;
-                kv[u] = ok ? a.Ks[q] : V(0);
+                jj[u] = ok ? sell_j<D16>(a, q, row) : 0;
+                kk[u] = ok ? a.Ks[q] : V(0);
             }
+        };
+        if constexpr (PF) fetch(0, j, kv);
+        for (int k = 0; k < len; k += C) {
+            if constexpr (!PF) fetch(k, j, kv);
             Q g[C];
 #pragma unroll
             for (int u = 0; u < C; ++u) g[u] = qo[j[u]];
+            V kc[C];
+            if constexpr (PF) {
+#pragma unroll
+                for (int u = 0; u < C; ++u) kc[u] = kv[u];
+                if (k + C < len) fetch(k + C, j, kv);
+            } else {
+#pragma unroll
+                for (int u = 0; u < C; ++u) kc[u] = kv[u];
+            }
 #pragma unroll
             for (int u = 0; u < C; ++u)
-                if (k + u < len) w += kv[u] * (g[u].d * (g[u].r - alpha * (g[u].w + beta * g[u].s)));
+                if (k + u < len) w += kc[u] * (g[u].d * (g[u].r - alpha * (g[u].w + beta * g[u].s)));
         }
         if (i < a.n) {
             const Q qi = qo[i];
@@ -883,51 +939,193 @@ __global__ void __launch_bounds__(kBlock, MINB) k_pcg_iter_sell(StepData<P> a, C
         }
     }
     double tot[3];
-    if (grid_sum_lite<3, V>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
-        KrylovState* st = a.stp;
-        const double g = tot[0], dl = tot[1], rr = tot[2];
-        st->it_total[0] += 1;
-        const double g_old = st->rho[0], a_old = st->alpha[0];
-        const double b_new = g_old != 0.0 ? g / g_old : 0.0;
-        const double den = a_old != 0.0 ? dl - b_new * g / a_old : 0.0;
-        const bool brk = !(den > 0.0) || !isfinite(den) || !isfinite(g) || g_old == 0.0;
-        st->beta[0] = b_new;
-        st->alpha[0] = brk ? 0.0 : g / den;
-        st->rho[0] = g;
-        st->rr_in[0] = rr;
-        mirror_coefs(st, 0);
-        const bool stop = brk || !isfinite(rr) || rr <= ctl.inner2 * st->rr0_in[0] || rr <= ctl.abs2 * st->bb[0] ||
-                          st->it_total[0] >= ctl.max_it || st->it_in + 1 >= ctl.sweep_cap;
-        if (stop) st->in_done[0] = 1;
-        st->it_in += 1;
-        set_cond(ctl.use_cond, ctl.h_inner, !stop);
-    }
+    if (grid_sum_lite<3, V>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) pcg_iter_finish<P>(a, ctl, tot);
 }
 
-// Candidate shapes (C, blocks per SM) of the CG iteration for the autotuner.
+// The same iteration with K streamed into shared memory by the bulk-copy
+// (TMA) engine, in a persistent grid.  The slices are grouped in "virtual
+// blocks" of 8 consecutive slices — exactly the rows one 256-thread block
+// covers in k_pcg_iter_sell — and block b takes virtual blocks b, b + G, ...
+// (G blocks), warp w the slice 8 vb + w of each.  Every warp owns a two-stage
+// ring in shared memory: while it works on one slice, the values and columns
+// of its next slice (contiguous in SELL order) are in flight as two
+// cp.async.bulk copies completing on the stage's mbarrier; the lanes then read
+// columns and values from shared memory, so the only global round trips left
+// in the chain are the C gathers of the quads and the row's own loads, which
+// are issued before the wait.  One partial per virtual block is stored with the
+// same trees as the one-block-per-8-slices kernels, so every shape gives the
+// same bits.  Every wait is bounded: on time-out the warp records OASIS_EWAIT,
+// stops issuing and processing, waits (bounded) for its copies in flight, and
+// the last block ends the solve.
+template <class P, int WPB, int C, int MINB, bool D16>
+__global__ void __launch_bounds__(WPB * 32, MINB) k_pcg_iter_tma(StepData<P> a, Ctl ctl) {
+    using V = typename P::V;
+    using Q = CgQuad<V>;
+    using Col = typename std::conditional<D16, int16_t, int32_t>::type;
+    static_assert(P::mixed, "the streamed CG iteration is built for float32 values");
+    static_assert(WPB * 32 == kBlock, "virtual blocks are the 8-slice blocks of k_pcg_iter_sell");
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t bars[WPB][2];
+    if (a.stp->col_done[0] || a.stp->in_done[0]) return;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int par = a.stp->it_in & 1;
+    const Q* __restrict__ qo = par ? a.pq0 : a.pq1;
+    Q* __restrict__ qn = par ? a.pq1 : a.pq0;
+    const V alpha = coef<P>(a.stp->alpha[0], a.stp->alpha_f[0]);
+    const V beta = coef<P>(a.stp->beta[0], a.stp->beta_f[0]);
+    const Col* __restrict__ cols = D16 ? reinterpret_cast<const Col*>(a.sell_dcol)
+                                       : reinterpret_cast<const Col*>(a.sell_col);
+    // stage layout: [max_row * 32] values, then [max_row * 32] columns (128-byte aligned)
+    const size_t vbytes = (size_t)a.max_row * 32 * sizeof(V);
+    const size_t sbytes = (vbytes + (size_t)a.max_row * 32 * sizeof(Col) + 127) & ~(size_t)127;
+    unsigned char* wbase = dsm + (size_t)wib * 2 * sbytes;
+    auto stage_v = [&](int st) { return reinterpret_cast<V*>(wbase + st * sbytes); };
+    auto stage_c = [&](int st) { return reinterpret_cast<Col*>(wbase + st * sbytes + vbytes); };
+    if (lane == 0) {
+        mbar_init(&bars[wib][0], 1);
+        mbar_init(&bars[wib][1], 1);
+        fence_barrier_init();
+    }
+    __syncwarp();
+    uint32_t issued[2] = {0u, 0u}, used[2] = {0u, 0u};     // copies per stage (same in every lane)
+    auto issue = [&](int64_t sl, int st) {
+        if (lane == 0) {
+            const int64_t p0 = a.sell_ptr[sl];
+            const uint32_t len = (uint32_t)a.sell_len[sl];
+            const uint32_t vb = len * 32 * (uint32_t)sizeof(V), cb = len * 32 * (uint32_t)sizeof(Col);
+            fence_proxy_async();
+            mbar_expect_tx(&bars[wib][st], vb + cb);
+            bulk_copy_g2s(stage_v(st), a.Ks + p0, vb, &bars[wib][st]);
+            bulk_copy_g2s(stage_c(st), cols + p0, cb, &bars[wib][st]);
+        }
+        ++issued[st];
+    };
+    const int64_t n_vb = (a.n_slices + WPB - 1) / WPB;
+    const int64_t G = gridDim.x;
+    bool timed_out = false;
+    int k = 0;
+    int64_t vb = blockIdx.x;
+    if (vb < n_vb && vb * WPB + wib < a.n_slices) issue(vb * WPB + wib, 0);
+    for (; vb < n_vb; vb += G, ++k) {
+        const int st = k & 1;
+        const int64_t sl = vb * WPB + wib;
+        const int64_t nsl = (vb + G) * WPB + wib;
+        if (!timed_out && vb + G < n_vb && nsl < a.n_slices) issue(nsl, st ^ 1);
+        V part[3] = {};
+        if (!timed_out && sl < a.n_slices) {
+            const int64_t i = sl * 32 + lane;
+            const int32_t row = (int32_t)i;
+            const bool own = i < a.n;
+            Q qi{};
+            V ppi = 0, pdli = 0;
+            if (own) {
+                qi = qo[i];
+                ppi = a.pp[i];
+                pdli = a.pdl[i];
+            }
+            const int len = a.sell_len[sl];
+            if (!mbar_wait_bounded(&bars[wib][st], used[st] & 1u)) {
+                timed_out = true;
+            } else {
+                ++used[st];
+                const V* __restrict__ sv = stage_v(st);
+                const Col* __restrict__ sc = stage_c(st);
+                V w = 0;
+                for (int k0 = 0; k0 < len; k0 += C) {
+                    int32_t j[C];
+                    V kv[C];
+#pragma unroll
+                    for (int u = 0; u < C; ++u) {
+                        const bool ok = k0 + u < len;
+                        const int e = (k0 + u) * 32 + lane;
+                        int32_t jj = 0;
+                        if (ok) {
+                            if constexpr (D16) {
+                                const int32_t n = (int32_t)a.n;
+                                jj = row + (int32_t)sc[e];
+                                jj = jj < 0 ? jj + n : jj;
+                                jj = jj >= n ? jj - n : jj;
+                            } else {
+                                jj = sc[e];
+                            }
+                        }
+                        j[u] = jj;
+                        kv[u] = ok ? sv[e] : V(0);
+                    }
+                    Q g[C];
+#pragma unroll
+                    for (int u = 0; u < C; ++u) g[u] = qo[j[u]];
+#pragma unroll
+                    for (int u = 0; u < C; ++u)
+                        if (k0 + u < len) w += kv[u] * (g[u].d * (g[u].r - alpha * (g[u].w + beta * g[u].s)));
+                }
+                if (own) {
+                    const V pv = qi.d * qi.r + beta * ppi;
+                    const V sv2 = qi.w + beta * qi.s;
+                    a.pp[i] = pv;
+                    a.pdl[i] = pdli + alpha * pv;
+                    Q out;
+                    out.r = qi.r - alpha * sv2;
+                    out.w = w;
+                    out.s = sv2;
+                    out.d = qi.d;
+                    qn[i] = out;
+                    const V un = qi.d * out.r;
+                    part[0] += out.r * un;
+                    part[1] += w * un;
+                    part[2] += out.r * out.r;
+                }
+            }
+            __syncwarp();
+        }
+        block_partial_lite<3, V>(part, reinterpret_cast<V*>(a.partial), vb);
+    }
+    if (timed_out) {
+        // record the failure; let the copies this warp started finish (bounded)
+        if (lane == 0) {
+            a.stp->status = OASIS_EWAIT;
+            for (int st = 0; st < 2; ++st)
+                if (issued[st] > used[st]) mbar_wait_bounded(&bars[wib][st], (issued[st] - 1u) & 1u);
+        }
+        __syncwarp();
+    }
+    double tot[3];
+    if (grid_finish_lite<3, V>(tot, reinterpret_cast<const V*>(a.partial), n_vb, &a.stp->ticket) &&
+        threadIdx.x == 0)
+        pcg_iter_finish<P>(a, ctl, tot);
+}
+
+// Candidate shapes of the CG iteration for the autotuner.
 template <class P>
 struct IterVariant {
     void (*fn)(StepData<P>, Ctl);
-    int chunk, minb;
+    int chunk, minb, pf, d16, tma, wpb;
 };
 
+#define OASIS_ITER(C, B, PF, D16) {k_pcg_iter_sell<P, C, B, PF, D16>, C, B, PF, D16, 0, kBlock / 32}
+#define OASIS_ITER_TMA(W, C, B, D16) {k_pcg_iter_tma<P, W, C, B, D16>, C, B, 0, D16, 1, W}
 template <class P>
 static const IterVariant<P>* iter_variant_table(int& count) {
     if constexpr (P::mixed) {
         static const IterVariant<P> t[] = {
-            {k_pcg_iter_sell<P, 2, 8>, 2, 8}, {k_pcg_iter_sell<P, 4, 8>, 4, 8}, {k_pcg_iter_sell<P, 4, 6>, 4, 6},
-            {k_pcg_iter_sell<P, 8, 4>, 8, 4}, {k_pcg_iter_sell<P, 8, 3>, 8, 3}, {k_pcg_iter_sell<P, 16, 2>, 16, 2}};
+            OASIS_ITER(2, 8, false, false),   OASIS_ITER(4, 8, false, false),   OASIS_ITER(4, 6, false, false),
+            OASIS_ITER(8, 4, false, false),   OASIS_ITER(8, 3, false, false),   OASIS_ITER(16, 2, false, false),
+            OASIS_ITER(2, 6, true, false),    OASIS_ITER(4, 6, true, false),    OASIS_ITER(2, 8, false, true),
+            OASIS_ITER(4, 8, false, true),    OASIS_ITER(2, 6, true, true),     OASIS_ITER(4, 6, true, true),
+            OASIS_ITER_TMA(8, 8, 4, false),   OASIS_ITER_TMA(8, 8, 4, true),    OASIS_ITER_TMA(8, 16, 3, true),
+            OASIS_ITER_TMA(8, 4, 4, true)};
         count = (int)(sizeof(t) / sizeof(t[0]));
         return t;
     } else {
-        static const IterVariant<P> t[] = {{k_pcg_iter_sell<P, 2, 4>, 2, 4},
-                                           {k_pcg_iter_sell<P, 4, 4>, 4, 4},
-                                           {k_pcg_iter_sell<P, 4, 3>, 4, 3},
-                                           {k_pcg_iter_sell<P, 8, 2>, 8, 2}};
+        static const IterVariant<P> t[] = {OASIS_ITER(2, 4, false, false), OASIS_ITER(4, 4, false, false),
+                                           OASIS_ITER(4, 3, false, false), OASIS_ITER(8, 2, false, false),
+                                           OASIS_ITER(4, 3, true, false),  OASIS_ITER(4, 4, false, true)};
         count = (int)(sizeof(t) / sizeof(t[0]));
         return t;
     }
 }
+#undef OASIS_ITER_TMA
+#undef OASIS_ITER
 
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_pcg_correct(StepData<P> a) {
@@ -1064,6 +1262,8 @@ struct StepImplT final : StepImpl {
     int g_sell = 1;
     int iter_v = 0;                                   // chosen CG iteration shape
     double tune_us[OASIS_MAX_VARIANTS] = {0};
+    int it_grid[OASIS_MAX_VARIANTS] = {0}, it_block[OASIS_MAX_VARIANTS] = {0};
+    size_t it_smem[OASIS_MAX_VARIANTS] = {0};
 
 
     template <class T>
@@ -1129,6 +1329,7 @@ struct StepImplT final : StepImpl {
         a.sell_ptr = m.sell_ptr.p;
         a.sell_len = m.sell_len.p;
         a.sell_col = m.sell_col.p;
+        a.sell_dcol = m.sell_dcol.p;
         a.Ks = mat<V>(m.K64s, m.K32s);
         if constexpr (P::mixed) a.Kouts = reinterpret_cast<const S*>(m.Kffs.p);
         else a.Kouts = reinterpret_cast<const S*>(m.K64s.p);
@@ -1270,7 +1471,7 @@ struct StepImplT final : StepImpl {
             [&](cudaStream_t ss, const Loop& lp) {
                 const Ctl c = ctl_p(lp);
                 const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
-                iter_variants()[iter_v].fn<<<g_sell, kBlock, 0, ss>>>(a, c);
+                iter_variants()[iter_v].fn<<<it_grid[iter_v], it_block[iter_v], it_smem[iter_v], ss>>>(a, c);
                 Sv.prof_end(ss, pq);
                 OASIS_CUDA(cudaGetLastError());
             },
@@ -1313,6 +1514,36 @@ struct StepImplT final : StepImpl {
         return iter_variant_table<P>(c);
     }
 
+    // Launch configuration of candidate v: one wave of 256-thread blocks over the
+    // slices; the streamed shapes run as many blocks as fit (persistent), with
+    // two stages of the longest slice per warp in shared memory.  False if the
+    // candidate cannot run on this mesh.
+    bool iter_config(const IterVariant<P>& t, int v) {
+        if (!t.tma) {
+            it_grid[v] = g_sell;
+            it_block[v] = kBlock;
+            it_smem[v] = 0;
+            return true;
+        }
+        const size_t vb = (size_t)a.max_row * 32 * sizeof(V);
+        const size_t cb = (size_t)a.max_row * 32 * (t.d16 ? 2 : 4);
+        const size_t stage = (vb + cb + 127) & ~(size_t)127;
+        const size_t smem = (size_t)t.wpb * 2 * stage;
+        cudaFuncAttributes fa{};
+        OASIS_CUDA(cudaFuncGetAttributes(&fa, t.fn));
+        const size_t cap = (size_t)smem_optin() - fa.sharedSizeBytes;
+        if (smem > cap) return false;
+        OASIS_CUDA(cudaFuncSetAttribute(t.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+        int per_sm = 0;
+        OASIS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, t.fn, t.wpb * 32, smem));
+        if (per_sm < 1) return false;
+        const int64_t want = (a.n_slices + t.wpb - 1) / t.wpb;
+        it_grid[v] = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)per_sm * num_sms()));
+        it_block[v] = t.wpb * 32;
+        it_smem[v] = smem;
+        return true;
+    }
+
     // Autotuner: every candidate shape of the CG iteration runs on this matrix
     // (2 untimed + 7 timed launches, CUDA events around each launch, median
     // kept) against a scratch Krylov state, so the solver's own state is not
@@ -1322,6 +1553,13 @@ struct StepImplT final : StepImpl {
         int count = 0;
         const IterVariant<P>* t = iter_variant_table<P>(count);
         OASIS_CHECK(forced <= count, OASIS_EINVAL, "spmv_variant: no such candidate");
+        const bool have16 = a.sell_dcol != nullptr;
+        OASIS_CHECK(forced < 1 || have16 || !t[forced - 1].d16, OASIS_EINVAL,
+                    "spmv_variant: 16-bit column offsets do not fit this mesh's ordering");
+        bool usable[OASIS_MAX_VARIANTS];
+        for (int v = 0; v < count; ++v) usable[v] = iter_config(t[v], v) && (have16 || !t[v].d16);
+        OASIS_CHECK(forced < 1 || usable[forced - 1], OASIS_EINVAL,
+                    "spmv_variant: the streamed shape does not fit this mesh's rows in shared memory");
         for (auto& u : tune_us) u = 0.0;
         if (forced >= 1) {
             iter_v = forced - 1;
@@ -1336,13 +1574,14 @@ struct StepImplT final : StepImpl {
         OASIS_CUDA(cudaEventCreate(&e0));
         OASIS_CUDA(cudaEventCreate(&e1));
         constexpr int kWarm = 2, kTimed = 7;
-        int best = 0;
+        int best = -1;
         for (int v = 0; v < count; ++v) {
+            if (!usable[v]) continue;
             float ts[kTimed];
             for (int r = 0; r < kWarm + kTimed; ++r) {
                 OASIS_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(KrylovState), s));
                 OASIS_CUDA(cudaEventRecord(e0, s));
-                t[v].fn<<<g_sell, kBlock, 0, s>>>(d, c);
+                t[v].fn<<<it_grid[v], it_block[v], it_smem[v], s>>>(d, c);
                 OASIS_CUDA(cudaGetLastError());
                 OASIS_CUDA(cudaEventRecord(e1, s));
                 OASIS_CUDA(cudaEventSynchronize(e1));
@@ -1350,7 +1589,7 @@ struct StepImplT final : StepImpl {
             }
             std::sort(ts, ts + kTimed);
             tune_us[v] = 1e3 * (double)ts[kTimed / 2];
-            if (tune_us[v] < tune_us[best]) best = v;
+            if (best < 0 || tune_us[v] < tune_us[best]) best = v;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -1365,6 +1604,10 @@ struct StepImplT final : StepImpl {
         for (int v = 0; v < count; ++v) {
             out->chunk[v] = t[v].chunk;
             out->min_blocks[v] = t[v].minb;
+            out->prefetch[v] = t[v].pf;
+            out->col16[v] = t[v].d16;
+            out->streamed[v] = t[v].tma;
+            out->warps_per_block[v] = t[v].wpb;
             out->us[v] = tune_us[v];
         }
     }

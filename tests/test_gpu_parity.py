@@ -215,13 +215,14 @@ def test_graph_equals_eager_bitwise():
         np.testing.assert_array_equal(a, b)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_cg_shapes_bitwise_equal_and_tuned(precision):
-    """Every candidate shape of the CG iteration kernel gives the same bits; the
-    autotuner timed every candidate and kept the fastest."""
+@pytest.mark.parametrize("precision,case", [(0, "stress"), (1, "stress"), (1, "channel")])
+def test_cg_shapes_bitwise_equal_and_tuned(precision, case):
+    """Every candidate shape of the CG iteration kernel (including 16-bit column
+    offsets taken modulo n, which the periodic channel needs) gives the same
+    bits; the autotuner timed every candidate and kept the fastest."""
     from paper_1602_03643_gb300.driver import IPCSRun
     c = capi()
-    pb = WP.stress_cube(12, ordering="random")
+    pb = WP.stress_cube(12, ordering="random") if case == "stress" else WP.channel(nx=12, ny=9, nz=10)
     run = IPCSRun(pb, precision=precision, rtol_u=1e-9, rtol_p=1e-9, use_graph=1)
     try:
         tun = c.oasis_get_tuning(run.solver)
