@@ -137,10 +137,12 @@ def run_ours(args, rank, world):
     N = pb.mesh.n_dofs
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def make(precision, graph=1, guess=capi.OASIS_GUESS_PREV_PHI, batch=1):
+    pc = capi.OASIS_PC_AMG if args.pc == "amg" else capi.OASIS_PC_JACOBI
+
+    def make(precision, graph=1, guess=capi.OASIS_GUESS_PREV_PHI, batch=1, pressure_pc=None):
         return IPCSRun(pb, precision=precision, rtol_u=RTOL, rtol_p=RTOL, max_it_u=5000, max_it_p=200000,
                        inner_rtol=args.inner_rtol, use_graph=graph, guess=guess, batch_rhs=batch,
-                       stream=stream)
+                       pressure_pc=pc if pressure_pc is None else pressure_pc, stream=stream)
 
     def timed_steps(run, k):
         evs = []
@@ -251,8 +253,18 @@ def run_ours(args, rank, world):
     # dinv, r, w, s, p, x-delta (24 N) and written p, s, x-delta, r, w (20 N)
     n_slices = (N + 31) // 32
     tun_e = capi.oasis_get_tuning(run_e.solver)
-    col_bytes = 2 if tun_e["candidates"][tun_e["chosen"] - 1]["col16"] else 4
-    spmv_bytes = (4 + col_bytes) * nnz + 44 * N + 8 * n_slices
+    amg_info = capi.oasis_get_amg_info(run_e.solver) if pc == capi.OASIS_PC_AMG else None
+    if pc == capi.OASIS_PC_AMG:
+        # w = K u on SELL-32 with three dot products: K values + int32 columns, u
+        # gathered (4 N), r read (4 N), w written (4 N), slice pointers/lengths
+        kernel = "k_amg_cg_spmv<Mixed> (multigrid CG: w = K u on SELL-32 + 3 dots)"
+        shape = None
+        spmv_bytes = 8 * nnz + 12 * N + 8 * n_slices
+    else:
+        kernel = "k_pcg_iter_sell<Mixed> (fused CG iteration: w = K M^-1 r on SELL-32 + vector updates + 3 dots)"
+        shape = tun_e["candidates"][tun_e["chosen"] - 1]
+        col_bytes = 2 if shape["col16"] else 4
+        spmv_bytes = (4 + col_bytes) * nnz + 44 * N + 8 * n_slices
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -261,9 +273,7 @@ def run_ours(args, rank, world):
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = spmv_bytes / (ms_spmv / max(n_spmv, 1) / 1e3) / 1e9 if n_spmv else None
     run_e.close()
-    roofline = {"bound": "hbm",
-                "kernel": "k_pcg_iter_sell<Mixed> (fused CG iteration: w = K M^-1 r on SELL-32 + vector updates + 3 dots)",
-                "shape": tun_e["candidates"][tun_e["chosen"] - 1],
+    roofline = {"bound": "hbm", "kernel": kernel, "shape": shape,
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if "hbm_gbs" in peaks
@@ -280,14 +290,15 @@ def run_ours(args, rank, world):
     # one solve per velocity component, eager launches, pressure guess p = p*
     fp64 = None
     if not args.skip_fp64:
-        run64 = make(capi.OASIS_FP64, graph=0, guess=capi.OASIS_GUESS_ZERO, batch=0)
+        run64 = make(capi.OASIS_FP64, graph=0, guess=capi.OASIS_GUESS_ZERO, batch=0,
+                     pressure_pc=capi.OASIS_PC_JACOBI)
         run64.set_dirichlet_for_next_step()
         for _ in range(max(1, args.warmup // 2)):
             capi.oasis_step(run64.solver, stream, want_stats=False)
         k64 = max(3, args.steps // 2)
         ms64, st64 = timed_steps(run64, k64)
         run64.close()
-        fp64 = {"form": "float64, unbatched, eager, guess p*",
+        fp64 = {"form": "float64, unbatched, eager, guess p*, Jacobi-PCG",
                 "steps_per_s": k64 / (ms64 / 1e3), "ms_per_step": ms64 / k64,
                 "it_u_mean": float(np.mean([max(s["it_u"]) for s in st64])),
                 "it_p_mean": float(np.mean([s["it_p"] for s in st64]))}
@@ -295,6 +306,7 @@ def run_ours(args, rank, world):
     prev_form = None
     if learned and not args.skip_compare:
         runp = make(capi.OASIS_MIXED, graph=0 if args.eager else 1, guess=capi.OASIS_GUESS_PREV_PHI)
+
         runp.set_dirichlet_for_next_step()
         msp, stp, _ = timed_form(runp)
         runp.close()
@@ -315,8 +327,16 @@ def run_ours(args, rank, world):
     # and (all but the last) a correction, 5 per BiCGStab iteration; pressure: u^I,
     # rhs and guess 3, per sweep residual + CG start + (all but the last) correction,
     # 1 per CG iteration; update 1
-    # learned guess: input scales, inputs, two network layers, judge
-    launches = int(round(args.steps * (4 + 2 * sw_u + 3 * sw_p + 5 * it_u + it_p + (5 if learned else 0))))
+    # learned guess: input scales, inputs, two network layers, judge.  Multigrid:
+    # a V-cycle is 4 kernels per operator level + the dense coarsest solve; per
+    # sweep residual, start, V-cycle, product (and all but the last a
+    # correction); per iteration update, V-cycle, product.
+    if amg_info:
+        vk = 4 * (amg_info["levels"] - 1) + 1
+        p_kernels = sw_p * (4 + vk) + it_p * (2 + vk)
+    else:
+        p_kernels = 3 * sw_p + it_p
+    launches = int(round(args.steps * (4 + 2 * sw_u + 5 * it_u + p_kernels + (5 if learned else 0))))
     run.close()
 
     line = {
@@ -327,7 +347,8 @@ def run_ours(args, rank, world):
         "data": "synthetic (seeded Taylor-Green initial field on a Kuhn tetrahedral mesh)",
         "config": workload_config(args.workload, pb, "mixed") | {
             "parallelism": f"replicas x{world}",
-            "pressure_guess": "learned (judged against previous phi)" if learned else "previous phi"},
+            "pressure_guess": "learned (judged against previous phi)" if learned else "previous phi",
+            "pressure_pc": args.pc},
         "e2e": {"value": world * k_e2e / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -339,6 +360,7 @@ def run_ours(args, rank, world):
         "mixed_prev_phi": prev_form,
         "learned_guess": train_info,
         "cg_autotune": tuning,
+        "multigrid": amg_info,
         "kernel_time_eager_2steps": kernel_share,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -415,6 +437,8 @@ def main():
     ap.add_argument("--skip-compare", action="store_true",
                     help="do not time the previous-phi form beside the learned one")
     ap.add_argument("--guess", default="learned", choices=["learned", "prev"])
+    ap.add_argument("--pc", default="amg", choices=["amg", "jacobi"],
+                    help="pressure-CG preconditioner (multigrid V-cycle or Jacobi)")
     ap.add_argument("--train-steps", type=int, default=14)
     ap.add_argument("--train-epochs", type=int, default=60)
     ap.add_argument("--minimal", action="store_true",

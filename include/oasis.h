@@ -91,7 +91,18 @@ typedef struct oasis_params {
     int32_t spmv_variant;  /* shape of the pressure-CG iteration kernel: 0 = autotune at
                               solver creation (every candidate timed on this matrix, the
                               fastest kept); k >= 1 = candidate k of oasis_get_tuning */
+    int32_t pressure_pc;   /* OASIS_PC_JACOBI or OASIS_PC_AMG (preconditioner of the
+                              pressure CG) */
 } oasis_params;
+
+/* Preconditioners of the pressure CG.  The paper preconditions its pressure solve
+ * with algebraic multigrid (Sec. 6); OASIS_PC_AMG is a smoothed-aggregation
+ * hierarchy of K built once per mesh on the host (strength threshold 0.08,
+ * greedy aggregation, Jacobi-smoothed prolongator, Galerkin coarse operators,
+ * dense coarsest level <= 400 dofs) applied as one V(1,1) cycle with damped
+ * Jacobi smoothing: a symmetric positive semi-definite preconditioner. */
+#define OASIS_PC_JACOBI 0
+#define OASIS_PC_AMG 1
 
 /* Candidate shapes of the pressure-CG iteration kernel (SELL-32, one warp per
  * 32 rows) and what the autotuner measured.  A shape is the number of entries
@@ -294,6 +305,20 @@ int oasis_solver_record_guess(oasis_solver* s, int32_t on);
  * phi / s_phi [n_dofs] (device arrays). */
 int oasis_get_guess_sample(oasis_solver* s, float* features, float* target, void* stream);
 
+/* Multigrid hierarchy of a solver created with OASIS_PC_AMG. */
+typedef struct oasis_amg_info {
+    int32_t levels;                /* operator levels, the dense coarsest one included */
+    int64_t rows[16];
+    int64_t nnz[16];
+    double setup_s;                /* host setup time (once per mesh) */
+} oasis_amg_info;
+int oasis_get_amg_info(const oasis_solver* s, oasis_amg_info* out);
+
+/* u = M r with one V-cycle of the solver's hierarchy, in the solver's inner
+ * precision (float64 for OASIS_FP64, float32 for OASIS_MIXED); r, u device
+ * arrays of n_dofs values.  Synchronises `stream`.  Test hook. */
+int oasis_amg_apply(oasis_solver* s, const void* r, void* u, void* stream);
+
 /* What the autotuner of oasis_solver_create chose for this solver. */
 int oasis_get_tuning(const oasis_solver* s, oasis_tuning* out);
 
@@ -307,6 +332,7 @@ int oasis_get_tuning(const oasis_solver* s, oasis_tuning* out);
 #define OASIS_PROF_UPDATE 4        /* lumped velocity update + rotation */
 #define OASIS_PROF_PRESSURE_RHS 5  /* pressure right-hand side */
 #define OASIS_PROF_GUESS 6         /* learned guess: input scaling, network forward, judge */
+#define OASIS_PROF_AMG 7           /* multigrid V-cycles of the pressure CG */
 
 /* enable = 1: from now on, eager steps record CUDA events around the launches
  * of the kernel families above; the counters are reset by every call. */

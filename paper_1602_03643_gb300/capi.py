@@ -28,6 +28,8 @@ OASIS_MIXED = 1
 OASIS_GUESS_ZERO = 0
 OASIS_GUESS_PREV_PHI = 1
 OASIS_GUESS_LEARNED = 2
+OASIS_PC_JACOBI = 0
+OASIS_PC_AMG = 1
 OASIS_MAT_M, OASIS_MAT_K, OASIS_MAT_G0, OASIS_MAT_G1, OASIS_MAT_G2, OASIS_MAT_A = range(6)
 
 ERROR_NAMES = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "EMESH", -4: "ENOTCONV", -5: "EBREAKDOWN",
@@ -39,7 +41,12 @@ class oasis_params(C.Structure):
                 ("rtol_u", C.c_double), ("rtol_p", C.c_double),
                 ("max_it_u", C.c_int32), ("max_it_p", C.c_int32), ("precision", C.c_int32),
                 ("inner_rtol", C.c_double), ("batch_rhs", C.c_int32), ("use_graph", C.c_int32),
-                ("guess", C.c_int32), ("spmv_variant", C.c_int32)]
+                ("guess", C.c_int32), ("spmv_variant", C.c_int32), ("pressure_pc", C.c_int32)]
+
+
+class oasis_amg_info(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("rows", C.c_int64 * 16), ("nnz", C.c_int64 * 16),
+                ("setup_s", C.c_double)]
 
 
 class oasis_tuning(C.Structure):
@@ -117,6 +124,8 @@ SIGNATURES = {
     "oasis_solver_record_guess": (C.c_int, [P, I32]),
     "oasis_get_guess_sample": (C.c_int, [P, DPTR, DPTR, P]),
     "oasis_get_tuning": (C.c_int, [P, C.POINTER(oasis_tuning)]),
+    "oasis_get_amg_info": (C.c_int, [P, C.POINTER(oasis_amg_info)]),
+    "oasis_amg_apply": (C.c_int, [P, DPTR, DPTR, P]),
     "oasis_solver_destroy": (None, [P]),
     "oasis_mesh_destroy": (None, [P]),
 }
@@ -221,7 +230,7 @@ def oasis_spmv_dot_f64_noalloc(mesh, which, x, y, xy, stream=None):
 
 def make_params(nu, dt, f=(0.0, 0.0, 0.0), rtol_u=1e-8, rtol_p=1e-8, max_it_u=1000, max_it_p=20000,
                 precision=OASIS_FP64, inner_rtol=1e-4, batch_rhs=1, use_graph=0, guess=OASIS_GUESS_ZERO,
-                spmv_variant=0):
+                spmv_variant=0, pressure_pc=0):
     p = oasis_params()
     p.nu, p.dt = nu, dt
     ff = list(f) + [0.0] * (3 - len(f))
@@ -231,6 +240,7 @@ def make_params(nu, dt, f=(0.0, 0.0, 0.0), rtol_u=1e-8, rtol_p=1e-8, max_it_u=10
     p.max_it_u, p.max_it_p = max_it_u, max_it_p
     p.precision, p.inner_rtol = precision, inner_rtol
     p.batch_rhs, p.use_graph, p.guess, p.spmv_variant = batch_rhs, use_graph, guess, spmv_variant
+    p.pressure_pc = pressure_pc
     return p
 
 
@@ -289,7 +299,7 @@ def oasis_get_tentative_system(solver, dim, n, nnz, stream=None):
 
 
 PROF_FAMILIES = {"pcg_spmv": 0, "bicg_spmm": 1, "assemble": 2, "pcg_update": 3, "update": 4,
-                 "pressure_rhs": 5, "guess": 6}
+                 "pressure_rhs": 5, "guess": 6, "amg": 7}
 
 
 def oasis_profile(solver, enable=True):
@@ -355,6 +365,17 @@ def oasis_get_tuning(solver):
     t = oasis_tuning()
     check(lib().oasis_get_tuning(solver, C.byref(t)))
     return t.as_dict()
+
+
+def oasis_get_amg_info(solver):
+    t = oasis_amg_info()
+    check(lib().oasis_get_amg_info(solver, C.byref(t)))
+    return {"levels": t.levels, "rows": list(t.rows[:t.levels]), "nnz": list(t.nnz[:t.levels]),
+            "setup_s": t.setup_s}
+
+
+def oasis_amg_apply(solver, r, u, stream=None):
+    check(lib().oasis_amg_apply(solver, _ptr(r), _ptr(u), _stream(stream)))
 
 
 def oasis_solver_destroy(solver):

@@ -1,0 +1,561 @@
+// Smoothed-aggregation AMG for the pressure operator: host setup (once per
+// mesh, from the assembled float64 K) and the V(1,1) cycle kernels.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <thread>
+#include <vector>
+
+#include "amg.cuh"
+#include "solver.cuh"
+
+namespace oasis {
+
+namespace {
+
+constexpr double kTheta = 0.08;        // strength threshold of the finest level (halved per level)
+constexpr int64_t kMaxCoarse = 400;    // dense coarsest level at or below this size
+constexpr int kMaxLevels = 12;
+
+// ------------------------------------------------------------------ host CSR
+struct HCsr {
+    int64_t n = 0, m = 0;              // rows, columns
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<double> v;
+    int64_t nnz() const { return (int64_t)ci.size(); }
+};
+
+int host_threads() {
+    const unsigned h = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(h, 32u));
+}
+
+std::vector<double> diagonal(const HCsr& A) {
+    std::vector<double> d(A.n, 0.0);
+    for (int64_t i = 0; i < A.n; ++i)
+        for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
+            if (A.ci[q] == i) d[i] += A.v[q];
+    return d;
+}
+
+// Strong off-diagonal entries kept, weak ones added to the diagonal.  A row
+// whose off-diagonals are all weak keeps its largest one (no isolated dofs).
+HCsr filtered(const HCsr& A, const std::vector<double>& d, double theta) {
+    HCsr F;
+    F.n = A.n;
+    F.m = A.m;
+    F.rp.assign(A.n + 1, 0);
+    F.ci.reserve(A.ci.size());
+    F.v.reserve(A.v.size());
+    for (int64_t i = 0; i < A.n; ++i) {
+        double weak = 0.0;
+        int64_t dpos = -1;
+        int64_t qmax = -1;
+        bool any = false;
+        for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+            const int32_t j = A.ci[q];
+            if (j == i) continue;
+            if (qmax < 0 || std::fabs(A.v[q]) > std::fabs(A.v[qmax])) qmax = q;
+            any |= std::fabs(A.v[q]) >= theta * std::sqrt(std::fabs(d[i] * d[j]));
+        }
+        for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+            const int32_t j = A.ci[q];
+            if (j == i) {
+                dpos = (int64_t)F.ci.size();
+                F.ci.push_back(j);
+                F.v.push_back(A.v[q]);
+            } else if (std::fabs(A.v[q]) >= theta * std::sqrt(std::fabs(d[i] * d[j])) || (!any && q == qmax)) {
+                F.ci.push_back(j);
+                F.v.push_back(A.v[q]);
+            } else {
+                weak += A.v[q];
+            }
+        }
+        if (dpos < 0) {
+            dpos = (int64_t)F.ci.size();
+            F.ci.push_back((int32_t)i);
+            F.v.push_back(0.0);
+        }
+        F.v[dpos] += weak;
+        F.rp[i + 1] = (int64_t)F.ci.size();
+    }
+    return F;
+}
+
+// rho(D^-1 A) by power iteration from a fixed start vector, with a 5 % margin.
+double spectral_radius(const HCsr& A, const std::vector<double>& d) {
+    std::vector<double> x(A.n), y(A.n);
+    for (int64_t i = 0; i < A.n; ++i) x[i] = 1.0 + 0.5 * std::sin(0.7 * (double)i + 0.3 * (double)(i % 7));
+    double lam = 1.0;
+    for (int it = 0; it < 20; ++it) {
+        double yy = 0.0, xx = 0.0;
+        for (int64_t i = 0; i < A.n; ++i) {
+            double s = 0.0;
+            for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) s += A.v[q] * x[A.ci[q]];
+            y[i] = d[i] != 0.0 ? s / d[i] : 0.0;
+            yy += y[i] * y[i];
+            xx += x[i] * x[i];
+        }
+        if (yy == 0.0) return 1.0;
+        lam = std::sqrt(yy / xx);
+        const double inv = 1.0 / std::sqrt(yy);
+        for (int64_t i = 0; i < A.n; ++i) x[i] = y[i] * inv;
+    }
+    return 1.05 * lam;
+}
+
+// Greedy aggregation over the strong graph of F (every off-diagonal of F is strong).
+std::vector<int32_t> aggregate(const HCsr& F, int64_t& nagg) {
+    const int64_t n = F.n;
+    std::vector<int32_t> agg(n, -1);
+    nagg = 0;
+    // 1: a root whose strong neighbours are all free takes them
+    for (int64_t i = 0; i < n; ++i) {
+        if (agg[i] >= 0) continue;
+        bool free = true;
+        for (int64_t q = F.rp[i]; q < F.rp[i + 1] && free; ++q)
+            if (F.ci[q] != i && agg[F.ci[q]] >= 0) free = false;
+        if (!free) continue;
+        agg[i] = (int32_t)nagg;
+        for (int64_t q = F.rp[i]; q < F.rp[i + 1]; ++q) agg[F.ci[q]] = (int32_t)nagg;
+        ++nagg;
+    }
+    // 2: a free dof joins the first-phase aggregate it is most strongly tied to
+    std::vector<int32_t> first = agg;
+    for (int64_t i = 0; i < n; ++i) {
+        if (agg[i] >= 0) continue;
+        double best = -1.0;
+        int32_t pick = -1;
+        for (int64_t q = F.rp[i]; q < F.rp[i + 1]; ++q) {
+            const int32_t j = F.ci[q];
+            if (j != i && first[j] >= 0 && std::fabs(F.v[q]) > best) {
+                best = std::fabs(F.v[q]);
+                pick = first[j];
+            }
+        }
+        agg[i] = pick;
+    }
+    // 3: what is left forms aggregates with its free strong neighbours
+    for (int64_t i = 0; i < n; ++i) {
+        if (agg[i] >= 0) continue;
+        agg[i] = (int32_t)nagg;
+        for (int64_t q = F.rp[i]; q < F.rp[i + 1]; ++q)
+            if (agg[F.ci[q]] < 0) agg[F.ci[q]] = (int32_t)nagg;
+        ++nagg;
+    }
+    return agg;
+}
+
+// P = (I - w D_F^-1 F) P_tent, P_tent[i][agg[i]] = 1.
+HCsr smoothed_prolongator(const HCsr& F, const std::vector<int32_t>& agg, int64_t nagg, double w) {
+    const std::vector<double> dF = diagonal(F);
+    HCsr P;
+    P.n = F.n;
+    P.m = nagg;
+    P.rp.assign(F.n + 1, 0);
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t i = 0; i < F.n; ++i) {
+        row.clear();
+        row.emplace_back(agg[i], 1.0);
+        const double s = dF[i] != 0.0 ? w / dF[i] : 0.0;
+        for (int64_t q = F.rp[i]; q < F.rp[i + 1]; ++q) row.emplace_back(agg[F.ci[q]], -s * F.v[q]);
+        std::sort(row.begin(), row.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        for (size_t k = 0; k < row.size();) {
+            const int32_t c = row[k].first;
+            double v = 0.0;
+            while (k < row.size() && row[k].first == c) v += row[k++].second;
+            P.ci.push_back(c);
+            P.v.push_back(v);
+        }
+        P.rp[i + 1] = (int64_t)P.ci.size();
+    }
+    return P;
+}
+
+HCsr transpose(const HCsr& P) {
+    HCsr R;
+    R.n = P.m;
+    R.m = P.n;
+    R.rp.assign(P.m + 1, 0);
+    for (int32_t c : P.ci) R.rp[c + 1]++;
+    for (int64_t k = 0; k < P.m; ++k) R.rp[k + 1] += R.rp[k];
+    R.ci.resize(P.ci.size());
+    R.v.resize(P.v.size());
+    std::vector<int64_t> pos(R.rp.begin(), R.rp.end() - 1);
+    for (int64_t i = 0; i < P.n; ++i)
+        for (int64_t q = P.rp[i]; q < P.rp[i + 1]; ++q) {
+            const int64_t o = pos[P.ci[q]]++;
+            R.ci[o] = (int32_t)i;
+            R.v[o] = P.v[q];
+        }
+    return R;
+}
+
+// C = A B, row by row with a dense accumulator per thread; columns sorted.
+HCsr spgemm(const HCsr& A, const HCsr& B) {
+    const int64_t n = A.n;
+    const int T = (int)std::min<int64_t>(host_threads(), std::max<int64_t>(1, n / 4096));
+    std::vector<std::vector<int32_t>> cis(T);
+    std::vector<std::vector<double>> vs(T);
+    std::vector<int64_t> cnt(n, 0);
+    std::vector<std::thread> th;
+    auto work = [&](int t) {
+        const int64_t lo = n * t / T, hi = n * (t + 1) / T;
+        std::vector<double> acc(B.m, 0.0);
+        std::vector<char> mark(B.m, 0);
+        std::vector<int32_t> cols;
+        for (int64_t i = lo; i < hi; ++i) {
+            cols.clear();
+            for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+                const int32_t k = A.ci[q];
+                const double a = A.v[q];
+                for (int64_t r = B.rp[k]; r < B.rp[k + 1]; ++r) {
+                    const int32_t c = B.ci[r];
+                    if (!mark[c]) {
+                        mark[c] = 1;
+                        cols.push_back(c);
+                    }
+                    acc[c] += a * B.v[r];
+                }
+            }
+            std::sort(cols.begin(), cols.end());
+            for (int32_t c : cols) {
+                cis[t].push_back(c);
+                vs[t].push_back(acc[c]);
+                acc[c] = 0.0;
+                mark[c] = 0;
+            }
+            cnt[i] = (int64_t)cols.size();
+        }
+    };
+    if (T <= 1) {
+        work(0);
+    } else {
+        for (int t = 0; t < T; ++t) th.emplace_back(work, t);
+        for (auto& x : th) x.join();
+    }
+    HCsr C;
+    C.n = n;
+    C.m = B.m;
+    C.rp.assign(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) C.rp[i + 1] = C.rp[i] + cnt[i];
+    C.ci.reserve(C.rp[n]);
+    C.v.reserve(C.rp[n]);
+    for (int t = 0; t < T; ++t) {
+        C.ci.insert(C.ci.end(), cis[t].begin(), cis[t].end());
+        C.v.insert(C.v.end(), vs[t].begin(), vs[t].end());
+    }
+    return C;
+}
+
+// Dense inverse of A + sigma 1 1^T (Cholesky; A symmetric positive semi-definite
+// with null space 1), row-major.
+std::vector<double> coarse_inverse(const HCsr& A) {
+    const int64_t n = A.n;
+    std::vector<double> M((size_t)n * n, 0.0);
+    double tr = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+            M[(size_t)i * n + A.ci[q]] += A.v[q];
+            if (A.ci[q] == i) tr += A.v[q];
+        }
+    const double sigma = tr / ((double)n * (double)n);
+    for (auto& x : M) x += sigma;
+    // Cholesky M = L L^T in place (lower triangle)
+    for (int64_t j = 0; j < n; ++j) {
+        double s = M[(size_t)j * n + j];
+        for (int64_t k = 0; k < j; ++k) s -= M[(size_t)j * n + k] * M[(size_t)j * n + k];
+        OASIS_CHECK(s > 0.0, OASIS_EINVAL, "multigrid: coarsest operator is not positive on the complement of 1");
+        const double l = std::sqrt(s);
+        M[(size_t)j * n + j] = l;
+        for (int64_t i = j + 1; i < n; ++i) {
+            double t = M[(size_t)i * n + j];
+            for (int64_t k = 0; k < j; ++k) t -= M[(size_t)i * n + k] * M[(size_t)j * n + k];
+            M[(size_t)i * n + j] = t / l;
+        }
+    }
+    // inverse column by column: solve L y = e_c, then L^T x = y
+    std::vector<double> inv((size_t)n * n, 0.0), y(n);
+    for (int64_t c = 0; c < n; ++c) {
+        for (int64_t i = 0; i < n; ++i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int64_t k = 0; k < i; ++k) t -= M[(size_t)i * n + k] * y[k];
+            y[i] = t / M[(size_t)i * n + i];
+        }
+        for (int64_t i = n - 1; i >= 0; --i) {
+            double t = y[i];
+            for (int64_t k = i + 1; k < n; ++k) t -= M[(size_t)k * n + i] * inv[(size_t)k * n + c];
+            inv[(size_t)i * n + c] = t / M[(size_t)i * n + i];
+        }
+    }
+    return inv;
+}
+
+template <class T>
+void upload_vec(DBuf<T>& dst, const std::vector<T>& src, cudaStream_t s) {
+    dst.upload(src.data(), src.size(), s);
+}
+
+void upload_csr(DBuf<int32_t>& rp, DBuf<int32_t>& ci, DBuf<float>& v32, DBuf<double>& v64, const HCsr& A,
+                cudaStream_t s) {
+    OASIS_CHECK(A.nnz() < INT32_MAX, OASIS_EINVAL, "multigrid: level too large for int32 indices");
+    std::vector<int32_t> r32(A.rp.size());
+    for (size_t k = 0; k < A.rp.size(); ++k) r32[k] = (int32_t)A.rp[k];
+    std::vector<float> f(A.v.size());
+    for (size_t k = 0; k < A.v.size(); ++k) f[k] = (float)A.v[k];
+    upload_vec(rp, r32, s);
+    upload_vec(ci, A.ci, s);
+    upload_vec(v32, f, s);
+    upload_vec(v64, A.v, s);
+    OASIS_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+void amg_build(Mesh& m, cudaStream_t s) {
+    if (m.amg) return;
+    OASIS_CHECK(m.assembled, OASIS_EINVAL, "mesh not assembled");
+    const auto t0 = std::chrono::steady_clock::now();
+    auto h = std::make_shared<AmgHierarchy>();
+    HCsr A;
+    A.n = A.m = m.n;
+    A.rp.assign(m.h_row_ptr.begin(), m.h_row_ptr.end());
+    A.ci = m.h_col;
+    A.ci.resize(m.nnz);
+    A.v.resize(m.nnz);
+    OASIS_CUDA(cudaMemcpyAsync(A.v.data(), m.K64.p, m.nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+    OASIS_CUDA(cudaStreamSynchronize(s));
+    while (true) {
+        auto L = std::make_unique<AmgLevelDev>();
+        L->n = A.n;
+        L->nnz = A.nnz();
+        const std::vector<double> d = diagonal(A);
+        std::vector<double> dinv(A.n);
+        for (int64_t i = 0; i < A.n; ++i) dinv[i] = d[i] != 0.0 ? 1.0 / d[i] : 0.0;
+        std::vector<float> dinv32(dinv.begin(), dinv.end());
+        upload_vec(L->d64, dinv, s);
+        upload_vec(L->d32, dinv32, s);
+        L->omega = 4.0 / (3.0 * spectral_radius(A, d));
+        if (h->lv.empty()) {
+            L->rp = m.row_ptr.p;
+            L->ci = m.col.p;
+            L->a32 = m.K32.p;
+            L->a64 = m.K64.p;
+        } else {
+            upload_csr(L->own_rp, L->own_ci, L->own_a32, L->own_a64, A, s);
+            L->rp = L->own_rp.p;
+            L->ci = L->own_ci.p;
+            L->a32 = L->own_a32.p;
+            L->a64 = L->own_a64.p;
+        }
+        h->sizes.push_back(A.n);
+        h->nnzs.push_back(A.nnz());
+        // coarsen; a level that barely shrinks is aggregated again with every
+        // connection strong
+        const double theta = kTheta * std::pow(0.5, (double)h->lv.size());
+        HCsr F = filtered(A, d, theta);
+        int64_t nagg = 0;
+        std::vector<int32_t> agg = aggregate(F, nagg);
+        if ((double)nagg > 0.6 * (double)A.n) {
+            F = filtered(A, d, 0.0);
+            agg = aggregate(F, nagg);
+        }
+        const double wP = 4.0 / (3.0 * spectral_radius(F, diagonal(F)));
+        const HCsr P = smoothed_prolongator(F, agg, nagg, wP);
+        const HCsr R = transpose(P);
+        upload_csr(L->p_rp, L->p_ci, L->p32, L->p64, P, s);
+        upload_csr(L->r_rp, L->r_ci, L->r32, L->r64, R, s);
+        h->lv.push_back(std::move(L));
+        HCsr Ac = spgemm(R, spgemm(A, P));
+        A = std::move(Ac);
+        const bool small = A.n <= kMaxCoarse;
+        const bool stalled = (double)A.n > 0.8 * (double)h->sizes.back();
+        if (small || stalled || (int)h->lv.size() >= kMaxLevels) break;
+    }
+    OASIS_CHECK(A.n <= 4 * kMaxCoarse, OASIS_EINVAL, "multigrid: coarsening stalled above the dense size");
+    h->nc = A.n;
+    h->sizes.push_back(A.n);
+    h->nnzs.push_back(A.nnz());
+    const std::vector<double> inv = coarse_inverse(A);
+    std::vector<float> inv32(inv.begin(), inv.end());
+    upload_vec(h->inv64, inv, s);
+    upload_vec(h->inv32, inv32, s);
+    OASIS_CUDA(cudaStreamSynchronize(s));
+    h->setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    m.amg = std::move(h);
+}
+
+void AmgWork::alloc(const AmgHierarchy& h, size_t vbytes) {
+    const size_t L = h.lv.size();
+    x.resize(L + 1);
+    xo.resize(L + 1);
+    res.resize(L + 1);
+    rin.resize(L + 1);
+    for (size_t l = 0; l <= L; ++l) {
+        const int64_t n = l < L ? h.lv[l]->n : h.nc;
+        const size_t cnt = ((size_t)n * vbytes + 7) / 8;
+        x[l].alloc(cnt);
+        xo[l].alloc(cnt);
+        res[l].alloc(cnt);
+        rin[l].alloc(cnt);
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+namespace {
+
+__device__ __forceinline__ bool amg_done(const KrylovState* st) { return st->col_done[0] || st->in_done[0]; }
+
+template <int G, class V>
+__device__ __forceinline__ V group_sum(V v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Rows are served by groups of G lanes; the row loop is uniform across the warp
+// (all shuffles have the full warp), each group handling row base + group.
+#define AMG_ROWS(n)                                                                                 \
+    const int lg = threadIdx.x & (G - 1);                                                           \
+    const int64_t rows_per_warp = 32 / G;                                                           \
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;                        \
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;                                       \
+    for (int64_t base = w0 * rows_per_warp; base < (n); base += nw * rows_per_warp)
+
+// pre-smoothing from zero and the residual: x = w D^-1 r, res = r - A x
+template <class V, int G>
+__global__ void __launch_bounds__(kBlock) k_amg_pre(int64_t n, const int32_t* __restrict__ rp,
+                                                    const int32_t* __restrict__ ci, const V* __restrict__ a,
+                                                    const V* __restrict__ d, V w, const V* __restrict__ r,
+                                                    V* __restrict__ x, V* __restrict__ res, const KrylovState* st) {
+    if (amg_done(st)) return;
+    AMG_ROWS(n) {
+        const int64_t i = base + ((threadIdx.x & 31) / G);
+        V s = 0;
+        if (i < n)
+            for (int32_t q = rp[i] + lg; q < rp[i + 1]; q += G) {
+                const int32_t j = ci[q];
+                s += a[q] * (w * d[j] * r[j]);
+            }
+        s = group_sum<G>(s);
+        if (i < n && lg == 0) {
+            res[i] = r[i] - s;
+            x[i] = w * d[i] * r[i];
+        }
+    }
+}
+
+// y = M v for a CSR matrix M (restriction P^T or coarse dense rows).
+template <class V, int G, bool ADD>
+__global__ void __launch_bounds__(kBlock) k_amg_spmv(int64_t n, const int32_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ ci, const V* __restrict__ a,
+                                                     const V* __restrict__ v, V* __restrict__ y,
+                                                     const KrylovState* st) {
+    if (amg_done(st)) return;
+    AMG_ROWS(n) {
+        const int64_t i = base + ((threadIdx.x & 31) / G);
+        V s = 0;
+        if (i < n)
+            for (int32_t q = rp[i] + lg; q < rp[i + 1]; q += G) s += a[q] * v[ci[q]];
+        s = group_sum<G>(s);
+        if (i < n && lg == 0) y[i] = ADD ? y[i] + s : s;
+    }
+}
+
+// post-smoothing: out = x + w D^-1 (r - A x)
+template <class V, int G>
+__global__ void __launch_bounds__(kBlock) k_amg_post(int64_t n, const int32_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ ci, const V* __restrict__ a,
+                                                     const V* __restrict__ d, V w, const V* __restrict__ r,
+                                                     const V* __restrict__ x, V* __restrict__ out,
+                                                     const KrylovState* st) {
+    if (amg_done(st)) return;
+    AMG_ROWS(n) {
+        const int64_t i = base + ((threadIdx.x & 31) / G);
+        V s = 0;
+        if (i < n)
+            for (int32_t q = rp[i] + lg; q < rp[i + 1]; q += G) s += a[q] * x[ci[q]];
+        s = group_sum<G>(s);
+        if (i < n && lg == 0) out[i] = x[i] + w * d[i] * (r[i] - s);
+    }
+}
+
+// coarsest level: x = inv r (dense, row-major), one warp per row
+template <class V>
+__global__ void __launch_bounds__(kBlock) k_amg_dense(int64_t n, const V* __restrict__ inv, const V* __restrict__ r,
+                                                      V* __restrict__ x, const KrylovState* st) {
+    if (amg_done(st)) return;
+    constexpr int G = 32;
+    AMG_ROWS(n) {
+        const int64_t i = base;
+        V s = 0;
+        if (i < n)
+            for (int64_t c = lg; c < n; c += 32) s += inv[(size_t)i * n + c] * r[c];
+        s = group_sum<G>(s);
+        if (i < n && lg == 0) x[i] = s;
+    }
+}
+#undef AMG_ROWS
+
+int amg_grid(int64_t rows, int G) {
+    const int64_t per_block = (int64_t)kBlock / G;
+    const int64_t want = (rows + per_block - 1) / per_block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 8));
+}
+
+template <class V>
+const V* pick(const float* f, const double* d) {
+    if constexpr (sizeof(V) == 4) return reinterpret_cast<const V*>(f);
+    else return reinterpret_cast<const V*>(d);
+}
+
+}  // namespace
+
+template <class V>
+void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const KrylovState* st, cudaStream_t s) {
+    const int L = (int)h.lv.size();
+    auto vec = [](DBuf<double>& b) { return reinterpret_cast<V*>(b.p); };
+    // level inputs: rin[0] = r; outputs: xo[0] = u
+    auto rin = [&](int l) -> const V* { return l == 0 ? r : vec(wk.rin[l]); };
+    auto xo = [&](int l) -> V* { return l == 0 ? u : vec(wk.xo[l]); };
+    for (int l = 0; l < L; ++l) {
+        const AmgLevelDev& lv = *h.lv[l];
+        const V* a = pick<V>(lv.a32, lv.a64);
+        const V* d = pick<V>(lv.d32.p, lv.d64.p);
+        const V w = (V)lv.omega;
+        if (l == 0)
+            k_amg_pre<V, 4><<<amg_grid(lv.n, 4), kBlock, 0, s>>>(lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]),
+                                                                 vec(wk.res[l]), st);
+        else
+            k_amg_pre<V, 8><<<amg_grid(lv.n, 8), kBlock, 0, s>>>(lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]),
+                                                                 vec(wk.res[l]), st);
+        const int64_t nc = l + 1 < L ? h.lv[l + 1]->n : h.nc;
+        k_amg_spmv<V, 8, false><<<amg_grid(nc, 8), kBlock, 0, s>>>(
+            nc, lv.r_rp.p, lv.r_ci.p, pick<V>(lv.r32.p, lv.r64.p), vec(wk.res[l]), vec(wk.rin[l + 1]), st);
+    }
+    k_amg_dense<V><<<amg_grid(h.nc, 32), kBlock, 0, s>>>(h.nc, pick<V>(h.inv32.p, h.inv64.p), vec(wk.rin[L]),
+                                                         vec(wk.xo[L]), st);
+    for (int l = L - 1; l >= 0; --l) {
+        const AmgLevelDev& lv = *h.lv[l];
+        const V* a = pick<V>(lv.a32, lv.a64);
+        const V* d = pick<V>(lv.d32.p, lv.d64.p);
+        const V w = (V)lv.omega;
+        k_amg_spmv<V, 4, true><<<amg_grid(lv.n, 4), kBlock, 0, s>>>(lv.n, lv.p_rp.p, lv.p_ci.p,
+                                                                    pick<V>(lv.p32.p, lv.p64.p), xo(l + 1),
+                                                                    vec(wk.x[l]), st);
+        if (l == 0)
+            k_amg_post<V, 4><<<amg_grid(lv.n, 4), kBlock, 0, s>>>(lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]),
+                                                                  xo(l), st);
+        else
+            k_amg_post<V, 8><<<amg_grid(lv.n, 8), kBlock, 0, s>>>(lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]),
+                                                                  xo(l), st);
+    }
+    OASIS_CUDA(cudaGetLastError());
+}
+
+template void amg_vcycle<float>(const AmgHierarchy&, AmgWork&, const float*, float*, const KrylovState*, cudaStream_t);
+template void amg_vcycle<double>(const AmgHierarchy&, AmgWork&, const double*, double*, const KrylovState*,
+                                 cudaStream_t);
+
+}  // namespace oasis

@@ -1,0 +1,70 @@
+// Smoothed-aggregation algebraic multigrid for the pressure operator K.
+//
+// The paper preconditions the pressure solve with algebraic multigrid (hypre
+// BoomerAMG, Sec. 6); this is a smoothed-aggregation hierarchy built for the
+// pure-Neumann P1 Laplacian:
+//   * strength: |a_ij| >= theta sqrt(a_ii a_jj); the filtered operator A_F drops
+//     weak off-diagonal entries into the diagonal (row sums kept);
+//   * greedy aggregation over the strong graph (root + strong neighbours, then
+//     attach leftovers to the aggregate they connect to most strongly, then
+//     aggregate what remains), in dof order, so the hierarchy is deterministic;
+//   * prolongator P = (I - w_P D_F^-1 A_F) P_tent with P_tent = aggregate
+//     indicators (entries 1) and w_P = 4 / (3 rho(D_F^-1 A_F)); because A_F 1 = 0,
+//     P maps coarse constants to fine constants and every coarse operator
+//     A_c = P^T A P keeps the constant null space exactly;
+//   * coarsest level: the dense inverse of A_c + sigma 1 1^T, which acts as the
+//     pseudo-inverse of A_c on right-hand sides orthogonal to 1.
+// The V(1,1) cycle uses one damped-Jacobi sweep (w_s = 4 / (3 rho(D^-1 A)))
+// before and after the coarse correction, with restriction P^T: a symmetric
+// positive semi-definite preconditioner, as CG requires.
+#pragma once
+
+#include <memory>
+
+#include "internal.cuh"
+
+namespace oasis {
+
+struct AmgLevelDev {
+    int64_t n = 0, nnz = 0;
+    // operator of this level (level 0 points at the mesh's K)
+    const int32_t *rp = nullptr, *ci = nullptr;
+    const float* a32 = nullptr;
+    const double* a64 = nullptr;
+    DBuf<int32_t> own_rp, own_ci;
+    DBuf<float> own_a32;
+    DBuf<double> own_a64;
+    DBuf<float> d32;                   // 1 / a_ii
+    DBuf<double> d64;
+    double omega = 0.0;                // Jacobi weight of the smoother
+    // prolongation to this level from the next coarser one, and its transpose
+    DBuf<int32_t> p_rp, p_ci, r_rp, r_ci;
+    DBuf<float> p32, r32;
+    DBuf<double> p64, r64;
+};
+
+struct AmgHierarchy {
+    std::vector<std::unique_ptr<AmgLevelDev>> lv;   // lv[0] fine ... lv[L-1] coarsest
+    int64_t nc = 0;                                  // size of the dense coarsest level
+    DBuf<float> inv32;                               // [nc][nc]
+    DBuf<double> inv64;
+    double setup_s = 0.0;
+    std::vector<int64_t> sizes;                      // rows per level (incl. coarsest)
+    std::vector<int64_t> nnzs;
+};
+
+// Build (once per mesh) from the assembled float64 K; no-op if present.
+void amg_build(Mesh& m, cudaStream_t s);
+
+// Per-solver work vectors of the V-cycle.
+struct AmgWork {
+    std::vector<DBuf<double>> x, xo, res, rin;   // raw storage; viewed as V
+    void alloc(const AmgHierarchy& h, size_t vbytes);
+};
+
+// u = M r with one V(1,1) cycle (device arrays of n_0 values of type V).  The
+// kernels return at once when `done` (the CG's col_done / in_done flags) is set.
+template <class V>
+void amg_vcycle(const AmgHierarchy& h, AmgWork& w, const V* r, V* u, const KrylovState* st, cudaStream_t s);
+
+}  // namespace oasis

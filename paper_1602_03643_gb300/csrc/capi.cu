@@ -9,6 +9,7 @@
 #include "internal.cuh"
 #include "solver.cuh"
 #include "kern.cuh"
+#include "amg.cuh"
 #include "net.cuh"
 
 namespace oasis {
@@ -178,6 +179,8 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     OASIS_CHECK(prm->precision == OASIS_FP64 || prm->precision == OASIS_MIXED, OASIS_EINVAL, "precision");
     OASIS_CHECK(prm->guess >= 0 && prm->guess <= 2, OASIS_EINVAL, "guess");
     OASIS_CHECK(prm->spmv_variant >= 0 && prm->spmv_variant <= OASIS_MAX_VARIANTS, OASIS_EINVAL, "spmv_variant");
+    OASIS_CHECK(prm->pressure_pc == OASIS_PC_JACOBI || prm->pressure_pc == OASIS_PC_AMG, OASIS_EINVAL,
+                "pressure_pc");
     OASIS_CHECK(n_dir >= 0 && (n_dir == 0 || dir), OASIS_EINVAL, "dirichlet dofs");
     OASIS_CHECK(m->max_row <= 64, OASIS_EMESH, "rows with more than 64 pattern entries are not supported");
     auto S = std::make_unique<Solver>();
@@ -206,6 +209,11 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     for (auto& w : S->w) w.alloc(vb * n * D, s);
     for (auto& w : S->pw) w.alloc(vb * n, s);
     for (auto& q : S->pq) q.alloc(4 * vb * n, s);
+    if (prm->pressure_pc == OASIS_PC_AMG) {
+        amg_build(*m, s);
+        S->amgw.alloc(*m->amg, vb);
+        for (auto& v : S->amg_vec) v.alloc(vb * n, s);
+    }
     S->uIv.alloc(vb * n * D, s);
     S->feat.alloc((size_t)n * 3);
     S->gy.alloc((size_t)n);
@@ -629,6 +637,35 @@ int oasis_get_guess_sample(oasis_solver* solver, float* features, float* target,
         cudaStream_t s = as_stream(stream);
         OASIS_CUDA(cudaMemcpyAsync(features, S->feat.p, S->feat.bytes(), cudaMemcpyDeviceToDevice, s));
         S->impl->guess_target(s, target);
+    });
+}
+
+int oasis_get_amg_info(const oasis_solver* solver, oasis_amg_info* out) {
+    return guarded([&] {
+        const Solver* S = reinterpret_cast<const Solver*>(solver);
+        OASIS_CHECK(S && out, OASIS_EINVAL, "null pointer");
+        OASIS_CHECK(S->prm.pressure_pc == OASIS_PC_AMG && S->m->amg, OASIS_EINVAL,
+                    "the solver was not created with OASIS_PC_AMG");
+        std::memset(out, 0, sizeof(*out));
+        const AmgHierarchy& h = *S->m->amg;
+        out->levels = (int32_t)std::min<size_t>(16, h.sizes.size());
+        for (int k = 0; k < out->levels; ++k) {
+            out->rows[k] = h.sizes[k];
+            out->nnz[k] = h.nnzs[k];
+        }
+        out->setup_s = h.setup_s;
+    });
+}
+
+int oasis_amg_apply(oasis_solver* solver, const void* r, void* u, void* stream) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S && r && u, OASIS_EINVAL, "null pointer");
+        OASIS_CHECK(S->prm.pressure_pc == OASIS_PC_AMG && S->m->amg, OASIS_EINVAL,
+                    "the solver was not created with OASIS_PC_AMG");
+        cudaStream_t s = as_stream(stream);
+        S->impl->amg_apply(s, r, u);
+        OASIS_CUDA(cudaStreamSynchronize(s));
     });
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -41,6 +42,20 @@ struct DBuf {
     DBuf() = default;
     DBuf(const DBuf&) = delete;
     DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) {
+        o.p = nullptr;
+        o.n = 0;
+    }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p;
+            n = o.n;
+            o.p = nullptr;
+            o.n = 0;
+        }
+        return *this;
+    }
     ~DBuf() { release(); }
     void alloc(size_t count) {
         release();
@@ -58,6 +73,8 @@ struct DBuf {
     }
     size_t bytes() const { return n * sizeof(T); }
 };
+
+struct AmgHierarchy;
 
 // The mesh: sparsity pattern, incidence and constant matrices (all on device).
 struct Mesh {
@@ -102,6 +119,7 @@ struct Mesh {
     DBuf<uint32_t> red_ticket;
     DBuf<int32_t> err;                         // device error flag for setup kernels
     bool assembled = false;
+    std::shared_ptr<AmgHierarchy> amg;         // pressure multigrid, built on first use
 };
 
 // Device-resident scalars of one Krylov solve (up to 3 right-hand sides).

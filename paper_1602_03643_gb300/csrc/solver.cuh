@@ -6,6 +6,7 @@
 #include <utility>
 #include <vector>
 
+#include "amg.cuh"
 #include "internal.cuh"
 
 namespace oasis {
@@ -64,6 +65,7 @@ struct StepData {
     CgQuad<V> *pq0, *pq1;
     V *pp, *pdl, *xv;
     V* uIv;                           // u^I rounded to V, [n][D]
+    V *ar, *as, *aw, *au;             // multigrid-preconditioned CG: r, s, w = K u, u = M r
     float* feat;                      // learned guess: features [n][3]
     float* gy;                        // learned guess: network output [n]
     KrylovState *stu, *stp;
@@ -110,6 +112,7 @@ struct StepImpl {
     // the fastest (forced = k >= 1 takes shape k untimed)
     virtual void tune(cudaStream_t s, int forced) = 0;
     virtual void tuning(oasis_tuning* out) const = 0;
+    virtual void amg_apply(cudaStream_t s, const void* r, void* u) = 0;
 };
 
 // state buffers addressable by to_state / from_state
@@ -129,6 +132,8 @@ struct Solver {
     RBuf w[9];                                                         // V [n][D]
     RBuf pw[3];                                                        // V [n]
     RBuf pq[2];                                                        // CgQuad<V> [n]
+    RBuf amg_vec[4];                                                   // V [n]: r, s, w, u (multigrid CG)
+    AmgWork amgw;                                                      // V-cycle work vectors
     RBuf uIv;                                                          // V [n][D]
     DBuf<float> feat, gy;                                              // learned-guess features / output
     struct Net* net = nullptr;                                         // attached network (not owned)
@@ -143,7 +148,7 @@ struct Solver {
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     // eager-mode kernel timing (CUDA events around selected launches)
-    static constexpr int kProfFamilies = 7;
+    static constexpr int kProfFamilies = 8;
     bool prof_on = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
     std::vector<std::pair<int, int>> ev_used;

@@ -1127,6 +1127,99 @@ static const IterVariant<P>* iter_variant_table(int& count) {
 #undef OASIS_ITER_TMA
 #undef OASIS_ITER
 
+// ---------------------------------------------------------------- multigrid CG
+// Chronopoulos-Gear CG with a general preconditioner u = M r (one multigrid
+// V-cycle, amg.cu): per iteration the vector updates, the V-cycle, then
+// w = K u with the three dot products in one reduction.
+
+// Start of an inner solve: r from the sweep's residual (the quads written by
+// k_pcg_outer_sell, which also cleared p and the update); s = 0.
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_amg_cg_start(StepData<P> a) {
+    if (a.stp->col_done[0] || a.stp->in_done[0]) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        a.ar[i] = a.pq0[i].r;
+        a.as[i] = 0;
+    }
+}
+
+// p = u + beta p, s = w + beta s, delta += alpha p, r -= alpha s.
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_amg_cg_update(StepData<P> a) {
+    using V = typename P::V;
+    if (a.stp->col_done[0] || a.stp->in_done[0]) return;
+    const V alpha = coef<P>(a.stp->alpha[0], a.stp->alpha_f[0]);
+    const V beta = coef<P>(a.stp->beta[0], a.stp->beta_f[0]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const V u = a.au[i], w = a.aw[i];
+        const V pv = beta == V(0) ? u : u + beta * a.pp[i];
+        const V sv = beta == V(0) ? w : w + beta * a.as[i];
+        a.pp[i] = pv;
+        a.as[i] = sv;
+        a.pdl[i] += alpha * pv;
+        a.ar[i] -= alpha * sv;
+    }
+}
+
+// w = K u on SELL-32 with gamma = <r, u>, delta = <w, u> and <r, r>.  START:
+// first iteration of a sweep (alpha = gamma / delta, beta = 0); else the
+// Chronopoulos-Gear update of alpha, beta and the inner stopping test.
+template <class P, bool START>
+__global__ void __launch_bounds__(kBlock) k_amg_cg_spmv(StepData<P> a, Ctl ctl) {
+    using V = typename P::V;
+    if (a.stp->col_done[0] || a.stp->in_done[0]) return;
+    V part[3] = {};
+    int64_t i, base;
+    int len, lane;
+    if (sell_lane(a, i, len, base, lane)) {
+        V w = 0;
+        for (int k = 0; k < len; k += 4) {
+            int32_t j[4];
+            V kv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t q = base + 32 * (int64_t)(k + u);
+                const bool ok = k + u < len;
+                j[u] = ok ? a.sell_col[q] : 0;
+                kv[u] = ok ? a.Ks[q] : V(0);
+            }
+            V g[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) g[u] = a.au[j[u]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (k + u < len) w += kv[u] * g[u];
+        }
+        if (i < a.n) {
+            a.aw[i] = w;
+            const V u = a.au[i], r = a.ar[i];
+            part[0] += r * u;
+            part[1] += w * u;
+            part[2] += r * r;
+        }
+    }
+    double tot[3];
+    if (grid_sum_lite<3, V>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
+        if constexpr (START) {
+            KrylovState* st = a.stp;
+            const double g0 = tot[0], d0 = tot[1];
+            if (!(d0 > 0.0) || !isfinite(d0) || !isfinite(g0)) {
+                st->in_done[0] = 1;
+                st->it_total[0] += 1;
+                st->alpha[0] = 0.0;
+                set_cond(ctl.use_cond, ctl.h_inner, 0);
+            } else {
+                st->rho[0] = g0;
+                st->alpha[0] = g0 / d0;
+            }
+            st->beta[0] = 0.0;
+            mirror_coefs(st, 0);
+        } else {
+            pcg_iter_finish<P>(a, ctl, tot);
+        }
+    }
+}
+
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_pcg_correct(StepData<P> a) {
     if (a.stp->col_done[0]) return;
@@ -1311,6 +1404,8 @@ struct StepImplT final : StepImpl {
         for (int q = 0; q < 3; ++q) *pw[q] = Sv.pw[q].as<V>();
         a.pq0 = Sv.pq[0].as<CgQuad<V>>();
         a.pq1 = Sv.pq[1].as<CgQuad<V>>();
+        V** av[4] = {&a.ar, &a.as, &a.aw, &a.au};
+        for (int q = 0; q < 4; ++q) *av[q] = Sv.amg_vec[q].as<V>();
         a.uIv = Sv.uIv.as<V>();
         a.feat = Sv.feat.p;
         a.gy = Sv.gy.p;
@@ -1458,6 +1553,39 @@ struct StepImplT final : StepImpl {
         Sv.prof_end(s, pg);
         k_phi_guess<P><<<ge_n, kBlock, 0, s>>>(a, mode);
         OASIS_CUDA(cudaGetLastError());
+        if (Sv.prm.pressure_pc == OASIS_PC_AMG) {
+            const AmgHierarchy& H = *Sv.m->amg;
+            auto vcycle = [&](cudaStream_t ss) {
+                const int pa = Sv.prof_begin(ss, OASIS_PROF_AMG);
+                amg_vcycle<V>(H, Sv.amgw, a.ar, a.au, a.stp, ss);
+                Sv.prof_end(ss, pa);
+            };
+            Sv.run_loops(
+                s, graph, 1,
+                [&](cudaStream_t ss, const Loop& lp) {
+                    const Ctl c = ctl_p(lp);
+                    k_pcg_outer_sell<P><<<g_sell, kBlock, 0, ss>>>(a, c);
+                    k_amg_cg_start<P><<<ge_n, kBlock, 0, ss>>>(a);
+                    vcycle(ss);
+                    k_amg_cg_spmv<P, true><<<g_sell, kBlock, 0, ss>>>(a, c);
+                    OASIS_CUDA(cudaGetLastError());
+                },
+                [&](cudaStream_t ss, const Loop& lp) {
+                    const Ctl c = ctl_p(lp);
+                    k_amg_cg_update<P><<<ge_n, kBlock, 0, ss>>>(a);
+                    vcycle(ss);
+                    const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
+                    k_amg_cg_spmv<P, false><<<g_sell, kBlock, 0, ss>>>(a, c);
+                    Sv.prof_end(ss, pq);
+                    OASIS_CUDA(cudaGetLastError());
+                },
+                [&](cudaStream_t ss, const Loop&) {
+                    k_pcg_correct<P><<<ge_n, kBlock, 0, ss>>>(a);
+                    OASIS_CUDA(cudaGetLastError());
+                },
+                0, 1);
+            return;
+        }
         Sv.run_loops(
             s, graph, 1,
             [&](cudaStream_t ss, const Loop& lp) {
@@ -1610,6 +1738,14 @@ struct StepImplT final : StepImpl {
             out->warps_per_block[v] = t[v].wpb;
             out->us[v] = tune_us[v];
         }
+    }
+
+    void amg_apply(cudaStream_t s, const void* r, void* u) override {
+        DBuf<KrylovState> scratch;
+        scratch.alloc(1);
+        OASIS_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(KrylovState), s));
+        amg_vcycle<V>(*Sv.m->amg, Sv.amgw, reinterpret_cast<const V*>(r), reinterpret_cast<V*>(u), scratch.p, s);
+        OASIS_CUDA(cudaStreamSynchronize(s));
     }
 
     void guess_target(cudaStream_t s, float* target) override {

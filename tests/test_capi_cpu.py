@@ -33,6 +33,19 @@ def test_every_declared_symbol_is_exported(capi):
     assert sorted(capi.SIGNATURES) == names
 
 
+def test_header_constants_match_binding(capi):
+    """Every #define the binding mirrors has the header's value; struct sizes agree."""
+    import ctypes
+    src = open(os.path.join(ROOT, "include", "oasis.h")).read()
+    defs = dict(re.findall(r"#define\s+(OASIS_[A-Z0-9_]+)\s+(-?\d+)", src))
+    shared = [k for k in defs if hasattr(capi, k)]
+    assert len(shared) >= 8
+    for k in shared:
+        assert getattr(capi, k) == int(defs[k]), k
+    assert ctypes.sizeof(capi.oasis_tuning) == 4 * 2 + 6 * 4 * 16 + 8 * 16
+    assert ctypes.sizeof(capi.oasis_amg_info) == 8 + 2 * 8 * 16 + 8
+
+
 def test_version_and_error_string(capi):
     assert capi.oasis_version() >= 100
     assert isinstance(capi.lib().oasis_last_error(), bytes)

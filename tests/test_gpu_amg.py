@@ -1,0 +1,129 @@
+"""Multigrid-preconditioned pressure CG on the GPU.
+
+The preconditioner changes how fast the pressure CG converges, not what it
+converges to: steps with OASIS_PC_AMG must match the float64 oracle as the
+Jacobi steps do (1e-10 for float64 at rtol 1e-12, 1e-6 per field for the mixed
+path at rtol 1e-8).  The V-cycle itself must be symmetric and positive on the
+complement of the constants, as CG requires.
+"""
+import numpy as np
+import pytest
+
+from oracle.ipcs import IPCS
+from workloads import meshes as WM
+from workloads import problems as WP
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1602_03643_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+def capi():
+    from paper_1602_03643_gb300 import capi as c
+    return c
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def _run(pb, precision, pc, graph=1, rtol=None, guess=None):
+    from paper_1602_03643_gb300.driver import IPCSRun
+    c = capi()
+    rt = rtol if rtol is not None else (1e-12 if precision == c.OASIS_FP64 else 1e-8)
+    return IPCSRun(pb, precision=precision, rtol_u=rt, rtol_p=rt, use_graph=graph, pressure_pc=pc,
+                   guess=c.OASIS_GUESS_PREV_PHI if guess is None else guess)
+
+
+PROBLEMS = {
+    "tg3d_8": lambda: WP.taylor_green_3d(8, dt=1e-2),
+    "channel_8x7x6": lambda: WP.channel(nx=8, ny=7, nz=6),
+    "stress_10_random": lambda: WP.stress_cube(10, ordering="random"),
+    "tg2d_24": lambda: WP.taylor_green_2d(24),
+}
+
+
+@pytest.mark.parametrize("name", ["stress_10_random", "channel_8x7x6"])
+def test_vcycle_symmetric_positive(name):
+    import torch
+    c = capi()
+    pb = PROBLEMS[name]()
+    run = _run(pb, c.OASIS_FP64, c.OASIS_PC_AMG)
+    try:
+        info = c.oasis_get_amg_info(run.solver)
+        assert info["levels"] >= 2 and info["rows"][0] == pb.mesh.n_dofs
+        assert all(a > b for a, b in zip(info["rows"], info["rows"][1:]))
+        rng = np.random.default_rng(5)
+        x = rng.normal(size=pb.mesh.n_dofs)
+        y = rng.normal(size=pb.mesh.n_dofs)
+        x -= x.mean()
+        y -= y.mean()
+        X, Y = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        U, W = torch.empty_like(X), torch.empty_like(Y)
+        c.oasis_amg_apply(run.solver, X, U)
+        c.oasis_amg_apply(run.solver, Y, W)
+        u, w = U.cpu().numpy(), W.cpu().numpy()
+        assert abs(x @ w - y @ u) <= 1e-11 * np.sqrt((x @ u) * (y @ w))
+        assert x @ u > 0 and y @ w > 0
+    finally:
+        run.close()
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_amg_steps_match_oracle_fp64(name):
+    c = capi()
+    pb = PROBLEMS[name]()
+    run = _run(pb, c.OASIS_FP64, c.OASIS_PC_AMG)
+    try:
+        st = run.step(3)
+        u, p, _ = run.fields()
+    finally:
+        run.close()
+    assert st.status == c.OASIS_OK
+    s = IPCS(pb).run(3)
+    assert relerr(u, s.u_nm1) <= 1e-10
+    assert relerr(p, s.p) <= 1e-9
+
+
+def test_amg_mixed_per_field_error_and_fewer_iterations():
+    c = capi()
+    pb = WP.taylor_green_3d(12)
+    out = {}
+    for pc in (c.OASIS_PC_JACOBI, c.OASIS_PC_AMG):
+        run = _run(pb, c.OASIS_MIXED, pc)
+        try:
+            its = [run.step(1).it_p for _ in range(20)]
+            out[pc] = (its, run.fields())
+        finally:
+            run.close()
+    s = IPCS(pb).run(20)
+    u, p, _ = out[c.OASIS_PC_AMG][1]
+    for k in range(3):
+        if np.abs(s.u_nm1[k]).max() > 0:
+            assert relerr(u[k], s.u_nm1[k]) <= 1e-6
+    assert relerr(p, s.p) <= 1e-6
+    print("\nCG iterations per step, Jacobi:", out[c.OASIS_PC_JACOBI][0], "\nmultigrid:", out[c.OASIS_PC_AMG][0])
+    assert sum(out[c.OASIS_PC_AMG][0]) * 3 < sum(out[c.OASIS_PC_JACOBI][0])
+
+
+def test_amg_graph_equals_eager_bitwise():
+    c = capi()
+    pb = WP.stress_cube(8, ordering="rcm")
+    out = []
+    for g in (1, 0):
+        run = _run(pb, c.OASIS_MIXED, c.OASIS_PC_AMG, graph=g)
+        try:
+            run.step(3)
+            out.append(run.fields())
+        finally:
+            run.close()
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
