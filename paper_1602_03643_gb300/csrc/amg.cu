@@ -14,7 +14,7 @@ namespace oasis {
 namespace {
 
 constexpr double kTheta = 0.08;        // strength threshold of the finest level (halved per level)
-constexpr int64_t kMaxCoarse = 400;    // dense coarsest level at or below this size
+constexpr int64_t kMaxCoarse = 2048;   // dense coarsest level at or below this size
 constexpr int kMaxLevels = 12;
 
 // ------------------------------------------------------------------ host CSR
@@ -269,26 +269,46 @@ std::vector<double> coarse_inverse(const HCsr& A) {
         OASIS_CHECK(s > 0.0, OASIS_EINVAL, "multigrid: coarsest operator is not positive on the complement of 1");
         const double l = std::sqrt(s);
         M[(size_t)j * n + j] = l;
-        for (int64_t i = j + 1; i < n; ++i) {
-            double t = M[(size_t)i * n + j];
-            for (int64_t k = 0; k < j; ++k) t -= M[(size_t)i * n + k] * M[(size_t)j * n + k];
-            M[(size_t)i * n + j] = t / l;
+        auto rows = [&](int64_t i0, int64_t i1) {
+            for (int64_t i = i0; i < i1; ++i) {
+                double t = M[(size_t)i * n + j];
+                for (int64_t k = 0; k < j; ++k) t -= M[(size_t)i * n + k] * M[(size_t)j * n + k];
+                M[(size_t)i * n + j] = t / l;
+            }
+        };
+        const int64_t rem = n - (j + 1);
+        const int T = (int)std::min<int64_t>(host_threads(), std::max<int64_t>(1, rem * j / 2000000));
+        if (T <= 1) {
+            rows(j + 1, n);
+        } else {
+            std::vector<std::thread> th;
+            for (int t = 0; t < T; ++t) th.emplace_back(rows, j + 1 + rem * t / T, j + 1 + rem * (t + 1) / T);
+            for (auto& x : th) x.join();
         }
     }
-    // inverse column by column: solve L y = e_c, then L^T x = y
-    std::vector<double> inv((size_t)n * n, 0.0), y(n);
-    for (int64_t c = 0; c < n; ++c) {
-        for (int64_t i = 0; i < n; ++i) {
-            double t = (i == c) ? 1.0 : 0.0;
-            for (int64_t k = 0; k < i; ++k) t -= M[(size_t)i * n + k] * y[k];
-            y[i] = t / M[(size_t)i * n + i];
+    // inverse column by column (columns split over the host cores): solve
+    // L y = e_c, then L^T x = y
+    std::vector<double> inv((size_t)n * n, 0.0);
+    auto cols = [&](int64_t c0, int64_t c1) {
+        std::vector<double> y(n), x(n);
+        for (int64_t c = c0; c < c1; ++c) {
+            for (int64_t i = 0; i < n; ++i) {
+                double t = (i == c) ? 1.0 : 0.0;
+                for (int64_t k = 0; k < i; ++k) t -= M[(size_t)i * n + k] * y[k];
+                y[i] = t / M[(size_t)i * n + i];
+            }
+            for (int64_t i = n - 1; i >= 0; --i) {
+                double t = y[i];
+                for (int64_t k = i + 1; k < n; ++k) t -= M[(size_t)k * n + i] * x[k];
+                x[i] = t / M[(size_t)i * n + i];
+            }
+            for (int64_t i = 0; i < n; ++i) inv[(size_t)i * n + c] = x[i];
         }
-        for (int64_t i = n - 1; i >= 0; --i) {
-            double t = y[i];
-            for (int64_t k = i + 1; k < n; ++k) t -= M[(size_t)k * n + i] * inv[(size_t)k * n + c];
-            inv[(size_t)i * n + c] = t / M[(size_t)i * n + i];
-        }
-    }
+    };
+    const int T = (int)std::min<int64_t>(host_threads(), std::max<int64_t>(1, n / 64));
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; ++t) th.emplace_back(cols, n * t / T, n * (t + 1) / T);
+    for (auto& x : th) x.join();
     return inv;
 }
 
@@ -366,6 +386,15 @@ void amg_build(Mesh& m, cudaStream_t s) {
         const HCsr R = transpose(P);
         upload_csr(L->p_rp, L->p_ci, L->p32, L->p64, P, s);
         upload_csr(L->r_rp, L->r_ci, L->r32, L->r64, R, s);
+        auto lanes = [](int64_t nnz, int64_t rows) {
+            const double mean = rows ? (double)nnz / (double)rows : 1.0;
+            int g = 4;
+            while (g < 32 && g * 4 < mean) g *= 2;
+            return g;
+        };
+        L->g_a = lanes(A.nnz(), A.n);
+        L->g_r = lanes(R.nnz(), R.n);
+        L->g_p = lanes(P.nnz(), P.n);
         h->lv.push_back(std::move(L));
         HCsr Ac = spgemm(R, spgemm(A, P));
         A = std::move(Ac);
@@ -373,7 +402,7 @@ void amg_build(Mesh& m, cudaStream_t s) {
         const bool stalled = (double)A.n > 0.8 * (double)h->sizes.back();
         if (small || stalled || (int)h->lv.size() >= kMaxLevels) break;
     }
-    OASIS_CHECK(A.n <= 4 * kMaxCoarse, OASIS_EINVAL, "multigrid: coarsening stalled above the dense size");
+    OASIS_CHECK(A.n <= 2 * kMaxCoarse, OASIS_EINVAL, "multigrid: coarsening stalled above the dense size");
     h->nc = A.n;
     h->sizes.push_back(A.n);
     h->nnzs.push_back(A.nnz());
@@ -446,12 +475,11 @@ __global__ void __launch_bounds__(kBlock) k_amg_pre(int64_t n, const int32_t* __
     }
 }
 
-// y = M v for a CSR matrix M (restriction P^T or coarse dense rows).
+// y = M v (ADD: y += M v) for a CSR matrix M (restriction P^T or prolongation P).
 template <class V, int G, bool ADD>
-__global__ void __launch_bounds__(kBlock) k_amg_spmv(int64_t n, const int32_t* __restrict__ rp,
-                                                     const int32_t* __restrict__ ci, const V* __restrict__ a,
-                                                     const V* __restrict__ v, V* __restrict__ y,
-                                                     const KrylovState* st) {
+__device__ __forceinline__ void amg_row_product(int64_t n, const int32_t* __restrict__ rp,
+                                                const int32_t* __restrict__ ci, const V* __restrict__ a,
+                                                const V* __restrict__ v, V* __restrict__ y, const KrylovState* st) {
     if (amg_done(st)) return;
     AMG_ROWS(n) {
         const int64_t i = base + ((threadIdx.x & 31) / G);
@@ -512,6 +540,30 @@ const V* pick(const float* f, const double* d) {
 
 }  // namespace
 
+// Launch a row kernel with G lanes per row, G chosen at run time.
+#define AMG_DISPATCH(G, KERNEL, ROWS, ...)                                                      \
+    switch (G) {                                                                                \
+        case 4: KERNEL<V, 4><<<amg_grid(ROWS, 4), kBlock, 0, s>>>(__VA_ARGS__); break;           \
+        case 8: KERNEL<V, 8><<<amg_grid(ROWS, 8), kBlock, 0, s>>>(__VA_ARGS__); break;           \
+        case 16: KERNEL<V, 16><<<amg_grid(ROWS, 16), kBlock, 0, s>>>(__VA_ARGS__); break;        \
+        default: KERNEL<V, 32><<<amg_grid(ROWS, 32), kBlock, 0, s>>>(__VA_ARGS__); break;        \
+    }
+
+template <class V, int G>
+__global__ void __launch_bounds__(kBlock) k_amg_restrict(int64_t n, const int32_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ ci, const V* __restrict__ a,
+                                                         const V* __restrict__ v, V* __restrict__ y,
+                                                         const KrylovState* st) {
+    amg_row_product<V, G, false>(n, rp, ci, a, v, y, st);
+}
+template <class V, int G>
+__global__ void __launch_bounds__(kBlock) k_amg_prolong(int64_t n, const int32_t* __restrict__ rp,
+                                                        const int32_t* __restrict__ ci, const V* __restrict__ a,
+                                                        const V* __restrict__ v, V* __restrict__ y,
+                                                        const KrylovState* st) {
+    amg_row_product<V, G, true>(n, rp, ci, a, v, y, st);
+}
+
 template <class V>
 void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const KrylovState* st, cudaStream_t s) {
     const int L = (int)h.lv.size();
@@ -524,15 +576,11 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
         const V* a = pick<V>(lv.a32, lv.a64);
         const V* d = pick<V>(lv.d32.p, lv.d64.p);
         const V w = (V)lv.omega;
-        if (l == 0)
-            k_amg_pre<V, 4><<<amg_grid(lv.n, 4), kBlock, 0, s>>>(lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]),
-                                                                 vec(wk.res[l]), st);
-        else
-            k_amg_pre<V, 8><<<amg_grid(lv.n, 8), kBlock, 0, s>>>(lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]),
-                                                                 vec(wk.res[l]), st);
+        AMG_DISPATCH(lv.g_a, k_amg_pre, lv.n, lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]), vec(wk.res[l]), st);
         const int64_t nc = l + 1 < L ? h.lv[l + 1]->n : h.nc;
-        k_amg_spmv<V, 8, false><<<amg_grid(nc, 8), kBlock, 0, s>>>(
-            nc, lv.r_rp.p, lv.r_ci.p, pick<V>(lv.r32.p, lv.r64.p), vec(wk.res[l]), vec(wk.rin[l + 1]), st);
+        const V* rv = pick<V>(lv.r32.p, lv.r64.p);
+        AMG_DISPATCH(lv.g_r, k_amg_restrict, nc, nc, lv.r_rp.p, lv.r_ci.p, rv, vec(wk.res[l]), vec(wk.rin[l + 1]),
+                     st);
     }
     k_amg_dense<V><<<amg_grid(h.nc, 32), kBlock, 0, s>>>(h.nc, pick<V>(h.inv32.p, h.inv64.p), vec(wk.rin[L]),
                                                          vec(wk.xo[L]), st);
@@ -541,18 +589,13 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
         const V* a = pick<V>(lv.a32, lv.a64);
         const V* d = pick<V>(lv.d32.p, lv.d64.p);
         const V w = (V)lv.omega;
-        k_amg_spmv<V, 4, true><<<amg_grid(lv.n, 4), kBlock, 0, s>>>(lv.n, lv.p_rp.p, lv.p_ci.p,
-                                                                    pick<V>(lv.p32.p, lv.p64.p), xo(l + 1),
-                                                                    vec(wk.x[l]), st);
-        if (l == 0)
-            k_amg_post<V, 4><<<amg_grid(lv.n, 4), kBlock, 0, s>>>(lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]),
-                                                                  xo(l), st);
-        else
-            k_amg_post<V, 8><<<amg_grid(lv.n, 8), kBlock, 0, s>>>(lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]),
-                                                                  xo(l), st);
+        const V* pv = pick<V>(lv.p32.p, lv.p64.p);
+        AMG_DISPATCH(lv.g_p, k_amg_prolong, lv.n, lv.n, lv.p_rp.p, lv.p_ci.p, pv, xo(l + 1), vec(wk.x[l]), st);
+        AMG_DISPATCH(lv.g_a, k_amg_post, lv.n, lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]), xo(l), st);
     }
     OASIS_CUDA(cudaGetLastError());
 }
+#undef AMG_DISPATCH
 
 template void amg_vcycle<float>(const AmgHierarchy&, AmgWork&, const float*, float*, const KrylovState*, cudaStream_t);
 template void amg_vcycle<double>(const AmgHierarchy&, AmgWork&, const double*, double*, const KrylovState*,

@@ -12,8 +12,8 @@
 //     indicators (entries 1) and w_P = 4 / (3 rho(D_F^-1 A_F)); because A_F 1 = 0,
 //     P maps coarse constants to fine constants and every coarse operator
 //     A_c = P^T A P keeps the constant null space exactly;
-//   * coarsest level: the dense inverse of A_c + sigma 1 1^T, which acts as the
-//     pseudo-inverse of A_c on right-hand sides orthogonal to 1.
+//   * coarsest level (<= 2048 dofs): the dense inverse of A_c + sigma 1 1^T, which
+//     acts as the pseudo-inverse of A_c on right-hand sides orthogonal to 1.
 // The V(1,1) cycle uses one damped-Jacobi sweep (w_s = 4 / (3 rho(D^-1 A)))
 // before and after the coarse correction, with restriction P^T: a symmetric
 // positive semi-definite preconditioner, as CG requires.
@@ -37,6 +37,7 @@ struct AmgLevelDev {
     DBuf<float> d32;                   // 1 / a_ii
     DBuf<double> d64;
     double omega = 0.0;                // Jacobi weight of the smoother
+    int g_a = 4, g_r = 8, g_p = 4;     // lanes per row for A, R = P^T and P (from mean row lengths)
     // prolongation to this level from the next coarser one, and its transpose
     DBuf<int32_t> p_rp, p_ci, r_rp, r_ci;
     DBuf<float> p32, r32;

@@ -1143,13 +1143,17 @@ __global__ void __launch_bounds__(kBlock) k_amg_cg_start(StepData<P> a) {
     }
 }
 
-// p = u + beta p, s = w + beta s, delta += alpha p, r -= alpha s.
+// p = u + beta p, s = w + beta s, delta += alpha p, r -= alpha s, and ||r||^2:
+// when the new residual already meets the inner stopping test the iteration
+// ends here (counted), and the V-cycle and product of this iteration return
+// at once instead of computing what the test no longer needs.
 template <class P>
-__global__ void __launch_bounds__(kBlock) k_amg_cg_update(StepData<P> a) {
+__global__ void __launch_bounds__(kBlock) k_amg_cg_update(StepData<P> a, Ctl ctl) {
     using V = typename P::V;
     if (a.stp->col_done[0] || a.stp->in_done[0]) return;
     const V alpha = coef<P>(a.stp->alpha[0], a.stp->alpha_f[0]);
     const V beta = coef<P>(a.stp->beta[0], a.stp->beta_f[0]);
+    V part[1] = {};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
         const V u = a.au[i], w = a.aw[i];
         const V pv = beta == V(0) ? u : u + beta * a.pp[i];
@@ -1157,7 +1161,24 @@ __global__ void __launch_bounds__(kBlock) k_amg_cg_update(StepData<P> a) {
         a.pp[i] = pv;
         a.as[i] = sv;
         a.pdl[i] += alpha * pv;
-        a.ar[i] -= alpha * sv;
+        const V r = a.ar[i] - alpha * sv;
+        a.ar[i] = r;
+        part[0] += r * r;
+    }
+    double tot[1];
+    if (grid_sum_lite<1, V>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
+        KrylovState* st = a.stp;
+        const double rr = tot[0];
+        const bool stop = st->status != OASIS_OK || !isfinite(rr) || rr <= ctl.inner2 * st->rr0_in[0] ||
+                          rr <= ctl.abs2 * st->bb[0] || st->it_total[0] + 1 >= ctl.max_it ||
+                          st->it_in + 1 >= ctl.sweep_cap;
+        if (stop) {
+            st->it_total[0] += 1;
+            st->it_in += 1;
+            st->rr_in[0] = rr;
+            st->in_done[0] = 1;
+            set_cond(ctl.use_cond, ctl.h_inner, 0);
+        }
     }
 }
 
@@ -1572,7 +1593,7 @@ struct StepImplT final : StepImpl {
                 },
                 [&](cudaStream_t ss, const Loop& lp) {
                     const Ctl c = ctl_p(lp);
-                    k_amg_cg_update<P><<<ge_n, kBlock, 0, ss>>>(a);
+                    k_amg_cg_update<P><<<ge_n, kBlock, 0, ss>>>(a, c);
                     vcycle(ss);
                     const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
                     k_amg_cg_spmv<P, false><<<g_sell, kBlock, 0, ss>>>(a, c);
