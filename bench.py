@@ -324,8 +324,8 @@ def run_ours(args, rank, world):
     sw_u = float(np.mean([s["sweeps_u"] for s in stats]))
     sw_p = float(np.mean([s["sweeps_p"] for s in stats]))
     # kernels per step in the graph: beta + assembly 2; velocity: per sweep a residual
-    # and (all but the last) a correction, 5 per BiCGStab iteration; pressure: u^I,
-    # rhs and guess 3, per sweep residual + CG start + (all but the last) correction,
+    # and (all but the last) a correction, 5 per BiCGStab iteration; pressure: rhs
+    # and guess 2, per sweep residual + CG start + (all but the last) correction,
     # 1 per CG iteration; update 1
     # learned guess: input scales, inputs, two network layers, judge.  Multigrid:
     # a V-cycle is 4 kernels per operator level + the dense coarsest solve; per
@@ -336,7 +336,7 @@ def run_ours(args, rank, world):
         p_kernels = sw_p * (4 + vk) + it_p * (2 + vk)
     else:
         p_kernels = 3 * sw_p + it_p
-    launches = int(round(args.steps * (4 + 2 * sw_u + 5 * it_u + p_kernels + (5 if learned else 0))))
+    launches = int(round(args.steps * (3 + 2 * sw_u + 5 * it_u + p_kernels + (5 if learned else 0))))
     run.close()
 
     line = {

@@ -214,7 +214,6 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
         S->amgw.alloc(*m->amg, vb);
         for (auto& v : S->amg_vec) v.alloc(vb * n, s);
     }
-    S->uIv.alloc(vb * n * D, s);
     S->feat.alloc((size_t)n * 3);
     S->gy.alloc((size_t)n);
     OASIS_CUDA(cudaMemsetAsync(S->feat.p, 0, S->feat.bytes(), s));

@@ -101,6 +101,7 @@ struct Mesh {
     DBuf<double> ML64, invML64, dinvK64;       // [n]
     DBuf<float> ML32, invML32, dinvK32;
     DBuf<float2> Kff;                          // K as float-float (hi, lo)
+    DBuf<float2> Gff;                          // dP^k as float-float, [dim][nnz]
     int tile_cap = 0;                          // max entries of a 256-row tile
     // SELL-32 (sliced ELLPACK, slices of 32 rows, column-major inside a slice):
     // entry k of row 32 s + l sits at sell_ptr[s] + 32 k + l; short rows are

@@ -402,6 +402,12 @@ struct Vec {
     T v[N];
 };
 
+// Four values loaded or stored as one aligned vector access.
+template <class T>
+struct alignas(4 * sizeof(T)) Vec4A {
+    T v[4];
+};
+
 // Entry phase of a tile with U entries per thread in flight: `load(e)` reads
 // everything an entry needs (its value, column and gathered vector entries) into
 // an Item, `use(e, item)` consumes it.  All U loads of a thread are issued

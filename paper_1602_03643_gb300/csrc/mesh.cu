@@ -406,6 +406,8 @@ void assemble_constant(Mesh& m, cudaStream_t s) {
                                          m.ML32.p, m.invML32.p);
     m.Kff.alloc(m.nnz);
     k_to_ff<<<grid_for(m.nnz), kBlock, 0, s>>>(m.nnz, m.K64.p, m.Kff.p);
+    m.Gff.alloc((size_t)D * m.nnz);
+    k_to_ff<<<grid_for((int64_t)D * m.nnz), kBlock, 0, s>>>((int64_t)D * m.nnz, m.G64.p, m.Gff.p);
     m.M32.alloc(m.nnz);
     m.K32.alloc(m.nnz + 8);
     OASIS_CUDA(cudaMemsetAsync(m.K32.p, 0, (m.nnz + 8) * sizeof(float), s));

@@ -37,32 +37,44 @@ struct alignas(16) SW {
     float w1a[kH * 3], w1b[kH * 3], c1[kH];
     float w2a[kH * kH], w2b[kH * kH];     // [k][l] (row k = output channel)
     float w2aT[kH * kH], w2bT[kH * kH];   // [l][k]
-    float c2[kH], w3[kH], c3, a0, a1;
+    float c2[kH], w3[kH], c3, a0, a1, pad_;
 };
 
-__device__ void load_weights(SW& s, const __nv_bfloat16* __restrict__ p) {
-    for (int q = threadIdx.x; q < kH * 3; q += blockDim.x) {
-        s.w1a[q] = __bfloat162float(p[oW1a + q]);
-        s.w1b[q] = __bfloat162float(p[oW1b + q]);
-    }
-    for (int q = threadIdx.x; q < kH * kH; q += blockDim.x) {
+// The shared-memory image of the weights (bfloat16 values widened to float,
+// plus transposed copies of W2a and W2b) is built once per parameter update;
+// every block then copies it with coalesced 16-byte loads.
+__global__ void k_net_image(const __nv_bfloat16* __restrict__ p, float* __restrict__ img) {
+    SW& s = *reinterpret_cast<SW*>(img);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < kH * kH; q += gridDim.x * blockDim.x) {
         const int k = q / kH, l = q % kH;
         const float a = __bfloat162float(p[oW2a + q]), b = __bfloat162float(p[oW2b + q]);
         s.w2a[q] = a;
         s.w2b[q] = b;
         s.w2aT[l * kH + k] = a;
         s.w2bT[l * kH + k] = b;
+        if (q < kH * 3) {
+            s.w1a[q] = __bfloat162float(p[oW1a + q]);
+            s.w1b[q] = __bfloat162float(p[oW1b + q]);
+        }
+        if (q < kH) {
+            s.c1[q] = __bfloat162float(p[oC1 + q]);
+            s.c2[q] = __bfloat162float(p[oC2 + q]);
+            s.w3[q] = __bfloat162float(p[oW3 + q]);
+        }
+        if (q == 0) {
+            s.c3 = __bfloat162float(p[oC3]);
+            s.a0 = __bfloat162float(p[oA]);
+            s.a1 = __bfloat162float(p[oA + 1]);
+            s.pad_ = 0.f;
+        }
     }
-    for (int q = threadIdx.x; q < kH; q += blockDim.x) {
-        s.c1[q] = __bfloat162float(p[oC1 + q]);
-        s.c2[q] = __bfloat162float(p[oC2 + q]);
-        s.w3[q] = __bfloat162float(p[oW3 + q]);
-    }
-    if (threadIdx.x == 0) {
-        s.c3 = __bfloat162float(p[oC3]);
-        s.a0 = __bfloat162float(p[oA]);
-        s.a1 = __bfloat162float(p[oA + 1]);
-    }
+}
+
+__device__ void load_weights(SW& s, const float* __restrict__ img) {
+    static_assert(sizeof(SW) % 16 == 0, "weight image copied as 16-byte vectors");
+    const float4* src = reinterpret_cast<const float4*>(img);
+    float4* dst = reinterpret_cast<float4*>(&s);
+    for (int q = threadIdx.x; q < (int)(sizeof(SW) / 16); q += blockDim.x) dst[q] = src[q];
     __syncthreads();
 }
 
@@ -142,7 +154,7 @@ __device__ __forceinline__ float gsum8(float v) {
 
 __global__ void __launch_bounds__(kBlock) k_net_l1(NetArgs a) {
     __shared__ SW s;
-    load_weights(s, a.p16);
+    load_weights(s, a.img);
     const int lane = threadIdx.x & 31, lg = lane & (kGroup - 1);
     const int64_t w0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * kBlock) >> 5;
     for (int64_t r0 = w0 * kRowsPerWarp; r0 < a.n; r0 += nw * kRowsPerWarp) {
@@ -184,7 +196,7 @@ __global__ void __launch_bounds__(kBlock) k_net_l1(NetArgs a) {
 
 __global__ void __launch_bounds__(kBlock) k_net_l2(NetArgs a) {
     __shared__ SW s;
-    load_weights(s, a.p16);
+    load_weights(s, a.img);
     const int lane = threadIdx.x & 31, lg = lane & (kGroup - 1), gb = lane & ~(kGroup - 1);
     const float4* __restrict__ h4 = reinterpret_cast<const float4*>(a.h1);
     const int64_t w0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * kBlock) >> 5;
@@ -274,7 +286,7 @@ __device__ __forceinline__ float inv_degree(const int32_t* __restrict__ rp, cons
 __global__ void __launch_bounds__(kBlock) k_net_bwd2(NetArgs a) {
     __shared__ SW s;
     __shared__ float red[kNetPartial];
-    load_weights(s, a.p16);
+    load_weights(s, a.img);
     for (int q = threadIdx.x; q < kNetPartial; q += blockDim.x) red[q] = 0.f;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t w0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * kBlock) >> 5;
@@ -337,7 +349,7 @@ __global__ void __launch_bounds__(kBlock) k_net_bwd2(NetArgs a) {
 __global__ void __launch_bounds__(kBlock) k_net_bwd1(NetArgs a) {
     __shared__ SW s;
     __shared__ float red[oW2a];
-    load_weights(s, a.p16);
+    load_weights(s, a.img);
     for (int q = threadIdx.x; q < oW2a; q += blockDim.x) red[q] = 0.f;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t w0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * kBlock) >> 5;
@@ -434,7 +446,16 @@ Net* net_create(const Mesh& m) {
     N->dz2.alloc((size_t)m.n * kH);
     N->g.alloc((size_t)m.n * kH);
     N->grid = net_grid(m.n);
+    N->img.alloc(sizeof(SW) / sizeof(float));
+    k_net_image<<<4, 256>>>(N->p16.p, N->img.p);
+    OASIS_CUDA(cudaGetLastError());
+    int per_sm = 0;
+    OASIS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_net_l2, kBlock, 0));
+    const int64_t groups = (m.n + kRowsPerWarp - 1) / kRowsPerWarp;
+    N->grid_fwd = (int)std::max<int64_t>(
+        1, std::min<int64_t>((groups + kWarps - 1) / kWarps, (int64_t)std::max(per_sm, 1) * num_sms()));
     N->partial.alloc((size_t)N->grid * kNetPartialStride);
+    OASIS_CUDA(cudaDeviceSynchronize());
     return N.release();
 }
 
@@ -444,6 +465,7 @@ NetArgs net_args(Net& N, const float* x, float* y, const float* t) {
     a.col = N.m->col.p;
     a.n = N.n;
     a.p16 = N.p16.p;
+    a.img = N.img.p;
     a.x = x;
     a.y = y;
     a.t = t;
@@ -456,15 +478,14 @@ NetArgs net_args(Net& N, const float* x, float* y, const float* t) {
 
 void net_forward(Net& N, const float* x, float* y, cudaStream_t s) {
     const NetArgs a = net_args(N, x, y, nullptr);
-    const int g4 = net_grid((N.n + kRowsPerWarp - 1) / kRowsPerWarp);
-    k_net_l1<<<g4, kBlock, 0, s>>>(a);
-    k_net_l2<<<g4, kBlock, 0, s>>>(a);
+    k_net_l1<<<N.grid_fwd, kBlock, 0, s>>>(a);
+    k_net_l2<<<N.grid_fwd, kBlock, 0, s>>>(a);
     OASIS_CUDA(cudaGetLastError());
 }
 
 void net_backward(Net& N, const float* x, const float* t, float* grad, float* loss, cudaStream_t s) {
     const NetArgs a = net_args(N, x, nullptr, t);
-    k_net_l1<<<net_grid((N.n + kRowsPerWarp - 1) / kRowsPerWarp), kBlock, 0, s>>>(a);
+    k_net_l1<<<N.grid_fwd, kBlock, 0, s>>>(a);
     k_net_bwd2<<<N.grid, kBlock, 0, s>>>(a);
     k_net_bwd1<<<N.grid, kBlock, 0, s>>>(a);
     k_net_reduce<<<(kNetParams + 1 + 255) / 256, 256, 0, s>>>(N.partial.p, N.grid, grad ? grad : N.grad.p,
@@ -476,12 +497,14 @@ void net_adam(Net& N, const float* grad, float lr, float b1, float b2, float eps
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
     k_net_adam<<<(kNetParams + 255) / 256, 256, 0, s>>>(N.p32.p, N.p16.p, N.mom.p, N.var.p, grad ? grad : N.grad.p, lr,
                                                        b1, b2, eps, c1, c2);
+    k_net_image<<<4, 256, 0, s>>>(N.p16.p, N.img.p);
     OASIS_CUDA(cudaGetLastError());
 }
 
 void net_set_params(Net& N, const float* host) {
     OASIS_CUDA(cudaMemcpy(N.p32.p, host, kNetParams * sizeof(float), cudaMemcpyHostToDevice));
     k_net_to_bf16<<<(kNetParams + 255) / 256, 256>>>(N.p32.p, N.p16.p);
+    k_net_image<<<4, 256>>>(N.p16.p, N.img.p);
     OASIS_CUDA(cudaGetLastError());
     OASIS_CUDA(cudaMemset(N.mom.p, 0, N.mom.bytes()));
     OASIS_CUDA(cudaMemset(N.var.p, 0, N.var.bytes()));

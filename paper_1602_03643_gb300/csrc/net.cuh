@@ -17,6 +17,7 @@ struct NetArgs {
     const int32_t *rp, *col;
     int64_t n;
     const __nv_bfloat16* p16;
+    const float* img;    // the weights as the kernels' shared-memory image (floats)
     const float* x;      // [n][3] features
     float* y;            // [n] output
     const float* t;      // [n] target
@@ -30,7 +31,9 @@ struct Net {
     int grid = 1;
     DBuf<float> p32, mom, var, grad, loss;
     DBuf<__nv_bfloat16> p16;
+    DBuf<float> img;     // bfloat16 weights widened to float, in shared-memory layout
     DBuf<float> h1, dz2, g, partial;
+    int grid_fwd = 1;    // one resident wave of the forward kernels
 };
 
 Net* net_create(const Mesh& m);

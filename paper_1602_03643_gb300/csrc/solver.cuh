@@ -52,6 +52,7 @@ struct StepData {
     const uint32_t* inc_slots;
     const V *M, *K, *G, *gw, *ML;     // G: [D][nnz]; gw: [nc][D+1][D]
     const S* Kout;                    // float64-quality K for the pressure residual
+    const S* Gout;                    // float64-quality dP^k for the pressure right-hand side
     const V *dinvK, *invML;
     // state (S)
     S *u1, *u2, *du, *r0, *pstar, *x, *b, *phi, *phi_h1, *phi_h2;
@@ -64,7 +65,6 @@ struct StepData {
     // CG work: gathered quads double-buffered by iteration parity; p; delta; x rounded
     CgQuad<V> *pq0, *pq1;
     V *pp, *pdl, *xv;
-    V* uIv;                           // u^I rounded to V, [n][D]
     V *ar, *as, *aw, *au;             // multigrid-preconditioned CG: r, s, w = K u, u = M r
     float* feat;                      // learned guess: features [n][3]
     float* gy;                        // learned guess: network output [n]
@@ -134,7 +134,6 @@ struct Solver {
     RBuf pq[2];                                                        // CgQuad<V> [n]
     RBuf amg_vec[4];                                                   // V [n]: r, s, w, u (multigrid CG)
     AmgWork amgw;                                                      // V-cycle work vectors
-    RBuf uIv;                                                          // V [n][D]
     DBuf<float> feat, gy;                                              // learned-guess features / output
     struct Net* net = nullptr;                                         // attached network (not owned)
     bool record = false;                                               // compute features every step

@@ -126,11 +126,29 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
         if (r < T.nr) {
             const int32_t len = s_rp[r + 1] - s_rp[r];
             for (int32_t sl = 0; sl < len; ++sl) s_t1[sl * kTile + r] = 0;
-            for (int32_t q = a.inc_ptr[i]; q < a.inc_ptr[i + 1]; ++q) {
-                const int32_t c = a.inc_cell[q];
-                const uint32_t w = a.inc_slots[q];
+            // incident cells 8 at a time: their indices and slots, then their
+            // beta rows (one aligned 4-vector each), then the additions in cell
+            // order (the same order as one at a time)
+            constexpr int kU = 8;
+            const int32_t q0 = a.inc_ptr[i], q1 = a.inc_ptr[i + 1];
+            for (int32_t qb = q0; qb < q1; qb += kU) {
+                int32_t c[kU];
+                uint32_t w[kU];
 #pragma unroll
-                for (int m = 0; m <= D; ++m) s_t1[((w >> (8 * m)) & 0xffu) * kTile + r] += a.beta[(size_t)c * 4 + m];
+                for (int u = 0; u < kU; ++u) {
+                    const bool ok = qb + u < q1;
+                    c[u] = ok ? a.inc_cell[qb + u] : 0;
+                    w[u] = ok ? a.inc_slots[qb + u] : 0u;
+                }
+                Vec4A<V> bt[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) bt[u] = reinterpret_cast<const Vec4A<V>*>(a.beta)[c[u]];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    if (qb + u >= q1) break;
+#pragma unroll
+                    for (int m = 0; m <= D; ++m) s_t1[((w[u] >> (8 * m)) & 0xffu) * kTile + r] += bt[u].v[m];
+                }
             }
 #pragma unroll
             for (int k = 0; k < D; ++k) s_ub[k][r] = (V)1.5 * s_v(a.u1[i * D + k]) - (V)0.5 * s_v(a.u2[i * D + k]);
@@ -516,45 +534,47 @@ __global__ void __launch_bounds__(kBlock) k_bicg_correct(StepData<P> a, int k0) 
 
 // ================================================================ pressure
 // u^I = u^{n-1} + Delta rounded to the value type (for the divergence products).
-template <class P, int D>
-__global__ void __launch_bounds__(kBlock) k_make_uI(StepData<P> a) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.n * D; t += (int64_t)gridDim.x * blockDim.x)
-        a.uIv[t] = s_v(s_add(a.u1[t], a.du[t]));
-}
 
 // b_phi_i = -(1/dt) sum_k sum_j dP^k_ij u_k,j^I (Sec. 5, algebraic pressure
 // equation); its mean is stored for the projection on sum_i b_i = 0, and the
 // pressure solve state is reset.
 template <class P, int D>
 __global__ void __launch_bounds__(kBlock) k_pressure_rhs(StepData<P> a, Consts<typename P::V> k_) {
-    using V = typename P::V;
+    using S = typename P::S;
     using Acc = typename P::Acc;
     extern __shared__ __align__(16) unsigned char dsm[];
-    V* s_prod = reinterpret_cast<V*>(dsm);
+    Acc* s_prod = reinterpret_cast<Acc*>(dsm);
     __shared__ int32_t s_rp[kTile + 1];
     Acc part[1];
     acc_zero(part[0]);
+    // b_phi is a small difference of large terms (u^I is nearly divergence-free),
+    // so it is formed with float64-quality dP^k and u^I = u^{n-1} + delta
+    // (float-float in the mixed path), accumulated in float-float
+    const S mrdt = s_of_double<S>(-1.0 / a.dt);
     const int r = threadIdx.x;
     for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
         const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
-        tile_entries<8, V>(
+        tile_entries<8, Acc>(
             T,
             [&](int32_t e) {
                 const size_t j = (size_t)a.col[e] * D;
-                V acc = 0;
+                Acc acc;
+                acc_zero(acc);
 #pragma unroll
-                for (int k = 0; k < D; ++k) acc += a.G[(size_t)k * a.nnz + e] * a.uIv[j + k];
+                for (int k = 0; k < D; ++k)
+                    acc_add(acc, acc_of_s(s_mul_s(a.Gout[(size_t)k * a.nnz + e], s_add(a.u1[j + k], a.du[j + k]))));
                 return acc;
             },
-            [&](int32_t e, V v) { s_prod[e - T.e0] = v; });
+            [&](int32_t e, const Acc& v) { s_prod[e - T.e0] = v; });
         __syncthreads();
         if (r < T.nr) {
             const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
-            V acc = 0;
-            for (int32_t q = b0; q < b1; ++q) acc += s_prod[q];
-            const V bi = -acc * k_.rdt;
-            a.b[T.r0 + r] = s_from(bi);
-            acc_addv(part[0], bi);
+            Acc acc;
+            acc_zero(acc);
+            for (int32_t q = b0; q < b1; ++q) acc_add(acc, s_prod[q]);
+            const S bi = s_mul_s(s_of_acc(acc), mrdt);
+            a.b[T.r0 + r] = bi;
+            acc_add(part[0], acc_of_s(bi));
         }
         __syncthreads();
     }
@@ -1404,6 +1424,8 @@ struct StepImplT final : StepImpl {
         a.invML = mat<V>(m.invML64, m.invML32);
         if constexpr (P::mixed) a.Kout = reinterpret_cast<const S*>(m.Kff.p);
         else a.Kout = reinterpret_cast<const S*>(m.K64.p);
+        if constexpr (P::mixed) a.Gout = reinterpret_cast<const S*>(m.Gff.p);
+        else a.Gout = reinterpret_cast<const S*>(m.G64.p);
         a.u1 = Sv.u1.as<S>();
         a.u2 = Sv.u2.as<S>();
         a.du = Sv.du.as<S>();
@@ -1427,7 +1449,6 @@ struct StepImplT final : StepImpl {
         a.pq1 = Sv.pq[1].as<CgQuad<V>>();
         V** av[4] = {&a.ar, &a.as, &a.aw, &a.au};
         for (int q = 0; q < 4; ++q) *av[q] = Sv.amg_vec[q].as<V>();
-        a.uIv = Sv.uIv.as<V>();
         a.feat = Sv.feat.p;
         a.gy = Sv.gy.p;
         a.stu = Sv.st.p;
@@ -1473,7 +1494,7 @@ struct StepImplT final : StepImpl {
         g_spmm0_1 = tile_grid(k_bicg_spmm<P, D, 1, 0>, sm_spmm1, tiles);
         g_spmm1_1 = tile_grid(k_bicg_spmm<P, D, 1, 1>, sm_spmm1, tiles);
         g_sell = (int)std::max<int64_t>(1, ((m.n + 31) / 32 + kBlock / 32 - 1) / (kBlock / 32));
-        g_rhs = tile_grid(k_pressure_rhs<P, D>, sm_v1, tiles);
+        g_rhs = tile_grid(k_pressure_rhs<P, D>, sm_outp, tiles);
         g_upd = tile_grid(k_update<P, D>, sm_vd, tiles);
         ge_n = elem_grid(m.n);
         ge_nd = elem_grid(m.n * D);
@@ -1553,9 +1574,8 @@ struct StepImplT final : StepImpl {
     }
 
     void pressure_solve(cudaStream_t s, bool graph) override {
-        k_make_uI<P, D><<<ge_nd, kBlock, 0, s>>>(a);
         const int pr = Sv.prof_begin(s, OASIS_PROF_PRESSURE_RHS);
-        k_pressure_rhs<P, D><<<g_rhs, kBlock, sm_v1, s>>>(a, k_);
+        k_pressure_rhs<P, D><<<g_rhs, kBlock, sm_outp, s>>>(a, k_);
         Sv.prof_end(s, pr);
         const bool learned = Sv.prm.guess == OASIS_GUESS_LEARNED && Sv.net;
         int mode = Sv.prm.guess == OASIS_GUESS_ZERO ? OASIS_GUESS_ZERO : OASIS_GUESS_PREV_PHI;
