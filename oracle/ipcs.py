@@ -7,7 +7,7 @@ The step follows the naive formulation of Sec. 4 (every form assembled from
 element integrals each step), not the in-place Algorithm 2 of Sec. 5; the two
 are algebraically identical, which is what the GPU parity tests check.
 
-Per step, with d velocity components, inner iterations = 1 (Algorithm 1):
+Per step, with d velocity components (inner iterations: see below):
   ubar   = 1.5 u^{n-1} - 0.5 u^{n-2}                          (Eq. 22)
   A      = M/dt + C(ubar)/2 + nu K/2                          (Eq. 33, A_ij)
   b_k    = (M/dt - C/2 - nu K/2) u_k^{n-1} + int f_k phi - G^k p*   (Eqs. 33, 31)
@@ -17,6 +17,12 @@ Per step, with d velocity components, inner iterations = 1 (Algorithm 1):
       with the right-hand side projected on sum_i b_i = 0 (no pressure BC),
       p normalised to zero arithmetic mean, phi = p - p*
   u_k^n = u_k^I - dt (G^k phi)_i / ML_i, Dirichlet rows reset to g  (Eq. 41, lumping)
+
+Inner iterations (Algorithm 1): the tentative and pressure solves are repeated
+`inner_iters` times within a step, each time with p* = the newest pressure (the
+matrix A, which holds only old velocities, is unchanged); phi is the increment
+of the last repetition, and the lumped velocity update follows the loop with
+the last u^I and that phi.  inner_iters = 1 is the default of the paper's runs.
 
 Readings where the paper is silent or self-contradictory:
   * Eq. 18 and its weak form carry the opposite sign to Eq. 19; the algebraic
@@ -66,8 +72,9 @@ def _jacobi(A):
 
 class IPCS:
     def __init__(self, problem, iterative: bool = False, rtol: float = 1e-12,
-                 maxiter: int = 100000):
+                 maxiter: int = 100000, inner_iters: int = 1):
         self.pb = problem
+        self.inner_iters = max(1, int(inner_iters))
         self.disc = Discretization(problem.mesh)
         self.iterative = iterative
         self.rtol = rtol
@@ -129,15 +136,21 @@ class IPCS:
     def step(self, s: State):
         pb, D = self.pb, self.disc
         t_new = s.t + pb.dt
-        A, b = self.tentative_system(s.u_nm1, s.u_nm2, s.p, t_new)
-        u_I = self.solve_tentative(A, b, s.u_nm1)
-        bp = self.pressure_rhs(u_I, s.p)
-        p = self.solve_pressure(bp, s.p)
-        phi = p - s.p
+        p_star = s.p
+        increments = []
+        for _ in range(self.inner_iters):
+            A, b = self.tentative_system(s.u_nm1, s.u_nm2, p_star, t_new)
+            u_I = self.solve_tentative(A, b, s.u_nm1)
+            bp = self.pressure_rhs(u_I, p_star)
+            p = self.solve_pressure(bp, p_star)
+            phi = p - p_star
+            increments.append(phi)
+            p_star = p
         u_n = np.stack([u_I[k] - pb.dt * (D.G[k] @ phi) / D.ML for k in range(D.d)])
         u_n[:, self.dirichlet] = pb.g(t_new)
         out = State(u_n, s.u_nm1, p, t_new)
         out.u_I, out.phi, out.bp = u_I, phi, bp
+        out.increments = increments
         return out
 
     def initial_state(self) -> State:
