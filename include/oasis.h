@@ -93,6 +93,12 @@ typedef struct oasis_params {
                               fastest kept); k >= 1 = candidate k of oasis_get_tuning */
     int32_t pressure_pc;   /* OASIS_PC_JACOBI or OASIS_PC_AMG (preconditioner of the
                               pressure CG) */
+    int32_t inner_iters;   /* inner velocity/pressure iterations of Algorithm 1 (0 or 1 =
+                              one): the tentative and pressure solves are repeated with
+                              p* = the newest pressure (A unchanged), the last pressure
+                              increment drives the velocity update.  Repetitions after the
+                              first start the pressure solve from zero.  The statistics of
+                              a step describe its last repetition.  At most 16. */
 } oasis_params;
 
 /* Preconditioners of the pressure CG.  The paper preconditions its pressure solve

@@ -128,24 +128,35 @@ void Solver::step(cudaStream_t s) {
         if (!gexec) capture();
         OASIS_CUDA(cudaGraphLaunch(gexec, s));
     } else {
-        impl->assemble(s);
-        impl->tentative_solve(s, false);
-        impl->pressure_solve(s, false);
-        impl->update(s);
+        enqueue_step(s, false);
         OASIS_CUDA(cudaMemcpyAsync(h_st, st.p, 2 * sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
         if (prof_on) prof_collect();
     }
     t += prm.dt;
 }
 
+// One time step (Algorithm 1): assembly, then per inner repetition the
+// tentative and pressure solves (p* advanced and the tentative residual
+// re-formed between repetitions), then the lumped velocity update.
+void Solver::enqueue_step(cudaStream_t s, bool graph_mode) {
+    const int ni = std::max(1, prm.inner_iters);
+    impl->assemble(s);
+    for (int it = 0; it < ni; ++it) {
+        if (it > 0) {
+            impl->advance_pressure(s);
+            impl->assemble(s);
+        }
+        impl->tentative_solve(s, graph_mode);
+        impl->pressure_solve(s, graph_mode, it);
+    }
+    impl->update(s);
+}
+
 void Solver::capture() {
     cudaStream_t s = cap[0];
     OASIS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     try {
-        impl->assemble(s);
-        impl->tentative_solve(s, true);
-        impl->pressure_solve(s, true);
-        impl->update(s);
+        enqueue_step(s, true);
         OASIS_CUDA(cudaMemcpyAsync(h_st, st.p, 2 * sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
     } catch (...) {
         cudaGraph_t g;
@@ -181,6 +192,7 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     OASIS_CHECK(prm->spmv_variant >= 0 && prm->spmv_variant <= OASIS_MAX_VARIANTS, OASIS_EINVAL, "spmv_variant");
     OASIS_CHECK(prm->pressure_pc == OASIS_PC_JACOBI || prm->pressure_pc == OASIS_PC_AMG, OASIS_EINVAL,
                 "pressure_pc");
+    OASIS_CHECK(prm->inner_iters >= 0 && prm->inner_iters <= 16, OASIS_EINVAL, "inner_iters must be in [0, 16]");
     OASIS_CHECK(n_dir >= 0 && (n_dir == 0 || dir), OASIS_EINVAL, "dirichlet dofs");
     OASIS_CHECK(m->max_row <= 64, OASIS_EMESH, "rows with more than 64 pattern entries are not supported");
     auto S = std::make_unique<Solver>();

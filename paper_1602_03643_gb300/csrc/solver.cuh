@@ -102,7 +102,10 @@ struct StepImpl {
     virtual ~StepImpl() = default;
     virtual void assemble(cudaStream_t s) = 0;
     virtual void tentative_solve(cudaStream_t s, bool graph) = 0;
-    virtual void pressure_solve(cudaStream_t s, bool graph) = 0;
+    // inner = index of the repetition within the step (Algorithm 1)
+    virtual void pressure_solve(cudaStream_t s, bool graph, int inner) = 0;
+    // p* <- p (normalised) between repetitions, velocities untouched
+    virtual void advance_pressure(cudaStream_t s) = 0;
     virtual void update(cudaStream_t s) = 0;
     virtual void to_state(cudaStream_t s, const double* src_soa, int which, int64_t count, int comps) = 0;
     virtual void from_state(cudaStream_t s, double* dst_soa, int which, int64_t count, int comps) = 0;
@@ -161,6 +164,7 @@ struct Solver {
                    const LoopFn& correct, int k0 = 0, int nr = 3);
     void poll(cudaStream_t s, int which);
     void step(cudaStream_t s);
+    void enqueue_step(cudaStream_t s, bool graph);
     void capture();
     ~Solver();
 };

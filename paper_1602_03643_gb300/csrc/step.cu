@@ -1268,6 +1268,17 @@ __global__ void __launch_bounds__(kBlock) k_pcg_correct(StepData<P> a) {
         a.x[i] = s_addv(a.x[i], a.pdl[i]);
 }
 
+// Between inner repetitions (Algorithm 1): p* <- p* + phi, normalised to zero
+// mean as in the update (the mean of p* + x comes from the last outer sweep);
+// the velocities and the correction history are left as they are.
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_pressure_advance(StepData<P> a) {
+    using S = typename P::S;
+    const S meanp = mean_s<S>(a.stp, true);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
+        a.pstar[i] = s_sub(s_add(a.pstar[i], a.x[i]), meanp);
+}
+
 // ================================================================ update
 // u_k^n = u_k^I - dt (dP^k phi)_i / ML_i (Sec. 5, lumping), Dirichlet rows = g;
 // p = p* + phi normalised to zero mean; rotation u^{n-2} <- u^{n-1} <- u^n,
@@ -1573,14 +1584,21 @@ struct StepImplT final : StepImpl {
         return c;
     }
 
-    void pressure_solve(cudaStream_t s, bool graph) override {
+    void advance_pressure(cudaStream_t s) override {
+        k_pressure_advance<P><<<ge_n, kBlock, 0, s>>>(a);
+        OASIS_CUDA(cudaGetLastError());
+    }
+
+    void pressure_solve(cudaStream_t s, bool graph, int inner) override {
         const int pr = Sv.prof_begin(s, OASIS_PROF_PRESSURE_RHS);
         k_pressure_rhs<P, D><<<g_rhs, kBlock, sm_outp, s>>>(a, k_);
         Sv.prof_end(s, pr);
-        const bool learned = Sv.prm.guess == OASIS_GUESS_LEARNED && Sv.net;
-        int mode = Sv.prm.guess == OASIS_GUESS_ZERO ? OASIS_GUESS_ZERO : OASIS_GUESS_PREV_PHI;
+        // repetitions after the first start from zero: their increment is small and
+        // unrelated to the previous step's correction
+        const bool learned = inner == 0 && Sv.prm.guess == OASIS_GUESS_LEARNED && Sv.net;
+        int mode = (inner > 0 || Sv.prm.guess == OASIS_GUESS_ZERO) ? OASIS_GUESS_ZERO : OASIS_GUESS_PREV_PHI;
         const int pg = Sv.prof_begin(s, OASIS_PROF_GUESS);
-        if (learned || Sv.record) {
+        if (inner == 0 && (learned || Sv.record)) {
             k_guess_scales<P><<<ge_n, kBlock, 0, s>>>(a);
             k_guess_features<P><<<ge_n, kBlock, 0, s>>>(a);
             OASIS_CUDA(cudaGetLastError());

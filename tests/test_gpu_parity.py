@@ -215,6 +215,47 @@ def test_graph_equals_eager_bitwise():
         np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("name", ["tg2d_8", "tg3d_6", "channel_6x6x4"])
+@pytest.mark.parametrize("use_graph", [0, 1])
+@pytest.mark.parametrize("pc", [0, 1])
+def test_inner_iterations_match_oracle_fp64(name, use_graph, pc):
+    """Algorithm 1 with 3 inner iterations per step (p* advanced between the
+    repetitions, the last increment in the update) against the oracle."""
+    from paper_1602_03643_gb300.driver import IPCSRun
+    pb = _perturbed_state(PROBLEMS[name]())
+    run = IPCSRun(pb, rtol_u=1e-13, rtol_p=1e-13, use_graph=use_graph, inner_iters=3, pressure_pc=pc,
+                  guess=1)
+    o = IPCS(pb, inner_iters=3)
+    s = o.initial_state()
+    try:
+        for it in range(2):
+            st = run.step()
+            assert st.status == 0
+            s = o.step(s)
+            u, p, phi = run.fields()
+            assert relerr(u, s.u_nm1) < 1e-10, it
+            assert relerr(p, s.p) < 1e-10, it
+            assert relerr(phi, s.phi) < 1e-8, it
+    finally:
+        run.close()
+
+
+def test_inner_iterations_mixed_per_field():
+    from paper_1602_03643_gb300.driver import IPCSRun
+    pb = WP.taylor_green_3d(10)
+    run = IPCSRun(pb, precision=1, rtol_u=1e-8, rtol_p=1e-8, use_graph=1, inner_iters=2, pressure_pc=1)
+    try:
+        run.step(5)
+        u, p, _ = run.fields()
+    finally:
+        run.close()
+    s = IPCS(pb, inner_iters=2).run(5)
+    for k in range(3):
+        if np.abs(s.u_nm1[k]).max() > 0:
+            assert relerr(u[k], s.u_nm1[k]) <= 1e-6, k
+    assert relerr(p, s.p) <= 1e-6
+
+
 @pytest.mark.parametrize("precision,case", [(0, "stress"), (1, "stress"), (1, "channel")])
 def test_cg_shapes_bitwise_equal_and_tuned(precision, case):
     """Every candidate shape of the CG iteration kernel (including 16-bit column
