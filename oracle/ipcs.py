@@ -18,6 +18,15 @@ Per step, with d velocity components (inner iterations: see below):
       p normalised to zero arithmetic mean, phi = p - p*
   u_k^n = u_k^I - dt (G^k phi)_i / ML_i, Dirichlet rows reset to g  (Eq. 41, lumping)
 
+Convection (Sec. 3): `convection="abcn"` (default, Eq. 22) is the form above;
+`convection="abe"` is the explicit Adams-Bashforth form of Eq. 21,
+B = 1.5 u^{n-1}.grad u^{n-1} - 0.5 u^{n-2}.grad u^{n-2}, which moves convection
+to the right-hand side:
+  A   = M/dt + nu K/2   (constant)
+  b_k = (M/dt - nu K/2) u_k^{n-1} - 1.5 C(u^{n-1}) u_k^{n-1} + 0.5 C(u^{n-2}) u_k^{n-2}
+        + int f_k phi - G^k p*
+with C(w)_ij = int phi_i w . grad phi_j.
+
 Inner iterations (Algorithm 1): the tentative and pressure solves are repeated
 `inner_iters` times within a step, each time with p* = the newest pressure (the
 matrix A, which holds only old velocities, is unchanged); phi is the increment
@@ -72,9 +81,12 @@ def _jacobi(A):
 
 class IPCS:
     def __init__(self, problem, iterative: bool = False, rtol: float = 1e-12,
-                 maxiter: int = 100000, inner_iters: int = 1):
+                 maxiter: int = 100000, inner_iters: int = 1, convection: str = "abcn"):
         self.pb = problem
         self.inner_iters = max(1, int(inner_iters))
+        if convection not in ("abcn", "abe"):
+            raise ValueError(convection)
+        self.convection = convection
         self.disc = Discretization(problem.mesh)
         self.iterative = iterative
         self.rtol = rtol
@@ -90,11 +102,19 @@ class IPCS:
     # ------------------------------------------------------------------ pieces
     def tentative_system(self, u_nm1, u_nm2, p_star, t_new):
         D, pb = self.disc, self.pb
-        ubar = 1.5 * u_nm1 - 0.5 * u_nm2
-        C = D.convection(ubar)
-        A = D.M / pb.dt + 0.5 * C + 0.5 * pb.nu * D.K
-        E = D.M / pb.dt - 0.5 * C - 0.5 * pb.nu * D.K
-        b = np.stack([E @ u_nm1[k] + self.b0[k] - D.G[k] @ p_star for k in range(D.d)])
+        if self.convection == "abe":
+            C1 = D.convection(u_nm1)
+            C2 = D.convection(u_nm2)
+            A = D.M / pb.dt + 0.5 * pb.nu * D.K
+            E = D.M / pb.dt - 0.5 * pb.nu * D.K
+            b = np.stack([E @ u_nm1[k] - 1.5 * (C1 @ u_nm1[k]) + 0.5 * (C2 @ u_nm2[k]) + self.b0[k]
+                          - D.G[k] @ p_star for k in range(D.d)])
+        else:
+            ubar = 1.5 * u_nm1 - 0.5 * u_nm2
+            C = D.convection(ubar)
+            A = D.M / pb.dt + 0.5 * C + 0.5 * pb.nu * D.K
+            E = D.M / pb.dt - 0.5 * C - 0.5 * pb.nu * D.K
+            b = np.stack([E @ u_nm1[k] + self.b0[k] - D.G[k] @ p_star for k in range(D.d)])
         A = replace_rows(A, self.dirichlet)
         b[:, self.dirichlet] = pb.g(t_new)
         return A, b

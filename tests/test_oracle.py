@@ -149,14 +149,16 @@ def test_periodic_mesh_invariants():
 
 
 # ----------------------------------------------------------------- dense brute force
-def dense_step(pb, state):
+def dense_step(pb, state, form="abcn"):
     """One IPCS step by quadrature element integrals, dense algebra and the
-    in-place Algorithm 2 ordering (a second route to the same discrete step)."""
+    in-place Algorithm 2 ordering (a second route to the same discrete step).
+    form="abe": explicit Adams-Bashforth convection (Eq. 21) on the right-hand
+    side, each convection matrix from quadrature with its own velocity."""
     m = pb.mesh
     d, N = m.dim, m.n_dofs
     Md, Kd = np.zeros((N, N)), np.zeros((N, N))
     Gd = [np.zeros((N, N)) for _ in range(d)]
-    Cd = np.zeros((N, N))
+    Cd, C1, C2 = np.zeros((N, N)), np.zeros((N, N)), np.zeros((N, N))
     ubar = 1.5 * state.u_nm1 - 0.5 * state.u_nm2
     for c in m.cells:
         dofs = m.dof_of_vertex[c]
@@ -165,16 +167,23 @@ def dense_step(pb, state):
         np.add.at(Md, ix, Me)
         np.add.at(Kd, ix, Ke)
         np.add.at(Cd, ix, Ce)
+        np.add.at(C1, ix, quad_element(m.coords[c], state.u_nm1[:, dofs].T)[3])
+        np.add.at(C2, ix, quad_element(m.coords[c], state.u_nm2[:, dofs].T)[3])
         for k in range(d):
             np.add.at(Gd[k], ix, Ge[k])
     ML = Md.sum(axis=1)
     dt, nu = pb.dt, pb.nu
     t_new = state.t + dt
-    # Algorithm 2
-    A = Cd.copy()
-    A = Md / dt - A / 2 - nu * Kd / 2
-    b = np.stack([pb.f[k] * ML + A @ state.u_nm1[k] - Gd[k] @ state.p for k in range(d)])
-    A = -A + 2 * Md / dt
+    if form == "abe":
+        A = Md / dt + nu * Kd / 2
+        b = np.stack([pb.f[k] * ML + (Md / dt - nu * Kd / 2) @ state.u_nm1[k] - 1.5 * C1 @ state.u_nm1[k]
+                      + 0.5 * C2 @ state.u_nm2[k] - Gd[k] @ state.p for k in range(d)])
+    else:
+        # Algorithm 2
+        A = Cd.copy()
+        A = Md / dt - A / 2 - nu * Kd / 2
+        b = np.stack([pb.f[k] * ML + A @ state.u_nm1[k] - Gd[k] @ state.p for k in range(d)])
+        A = -A + 2 * Md / dt
     A[pb.dirichlet, :] = 0.0
     A[pb.dirichlet, pb.dirichlet] = 1.0
     b[:, pb.dirichlet] = pb.g(t_new)
@@ -188,21 +197,22 @@ def dense_step(pb, state):
     return un, p, uI
 
 
+@pytest.mark.parametrize("form", ["abcn", "abe"])
 @pytest.mark.parametrize("kind", ["tg2d", "tg3d", "channel"])
-def test_oracle_step_matches_dense_brute_force(kind):
+def test_oracle_step_matches_dense_brute_force(kind, form):
     if kind == "tg2d":
         pb = WP.taylor_green_2d(3)
     elif kind == "tg3d":
         pb = WP.taylor_green_3d(3)
     else:
         pb = WP.channel(nx=3, ny=4, nz=2, perturb=0.1)
-    o = IPCS(pb)
+    o = IPCS(pb, convection=form)
     s = o.initial_state()
     rng = np.random.default_rng(3)
     s.u_nm2 = s.u_nm2 + 0.05 * rng.normal(size=s.u_nm2.shape)   # make ubar != u^{n-1}
     s.u_nm2[:, pb.dirichlet] = s.u_nm1[:, pb.dirichlet]
     for _ in range(2):
-        un, p, uI = dense_step(pb, s)
+        un, p, uI = dense_step(pb, s, form)
         s2 = o.step(s)
         np.testing.assert_allclose(s2.u_I, uI, rtol=0, atol=1e-11 * np.abs(uI).max())
         np.testing.assert_allclose(s2.p, p, rtol=0, atol=1e-10 * max(np.abs(p).max(), 1e-3))
@@ -255,11 +265,12 @@ def test_table1_p1p1_values(row):
 
 
 # ----------------------------------------------------------------- scheme-level pins
-def test_unit_square_velocity_second_order():
+@pytest.mark.parametrize("form", ["abcn", "abe"])
+def test_unit_square_velocity_second_order(form):
     errs, hs = [], []
     for n in (16, 32, 64):
         pb = WP.taylor_green_2d(n)
-        s = IPCS(pb).run(100)
+        s = IPCS(pb, convection=form).run(100)
         x = pb.mesh.dof_coords()
         errs.append(_rms(s.u_nm1 - pb.exact_u(x, s.t)))
         hs.append(mesh_size(pb.mesh.coords, pb.mesh.cells))
@@ -268,9 +279,10 @@ def test_unit_square_velocity_second_order():
         assert 1.8 < k < 2.4, (errs, k)
 
 
-def test_poiseuille_is_a_discrete_steady_state():
+@pytest.mark.parametrize("form", ["abcn", "abe"])
+def test_poiseuille_is_a_discrete_steady_state(form):
     pb = WP.channel(nx=6, ny=7, nz=4, perturb=0.0)
-    o = IPCS(pb)
+    o = IPCS(pb, convection=form)
     s0 = o.initial_state()
     s = o.run(4)
     assert np.abs(s.u_nm1 - s0.u_nm1).max() < 1e-12 * np.abs(s0.u_nm1).max()
