@@ -143,7 +143,7 @@ def run_ours(args, rank, world):
         return IPCSRun(pb, precision=precision, rtol_u=RTOL, rtol_p=RTOL, max_it_u=5000, max_it_p=200000,
                        inner_rtol=args.inner_rtol, use_graph=graph, guess=guess, batch_rhs=batch,
                        pressure_pc=pc if pressure_pc is None else pressure_pc, inner_iters=args.inner_iters,
-                       stream=stream)
+                       convection=1 if args.convection == "abe" else 0, stream=stream)
 
     def timed_steps(run, k):
         evs = []
@@ -366,7 +366,7 @@ def run_ours(args, rank, world):
         "config": workload_config(args.workload, pb, "mixed") | {
             "parallelism": f"replicas x{world}",
             "pressure_guess": "learned (judged against previous phi)" if learned else "previous phi",
-            "pressure_pc": args.pc, "inner_iters": args.inner_iters},
+            "pressure_pc": args.pc, "inner_iters": args.inner_iters, "convection": args.convection},
         "e2e": {"value": world * k_e2e / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -456,6 +456,8 @@ def main():
     ap.add_argument("--skip-compare", action="store_true",
                     help="do not time the previous-phi form beside the learned one")
     ap.add_argument("--guess", default="learned", choices=["learned", "prev"])
+    ap.add_argument("--convection", default="abcn", choices=["abcn", "abe"],
+                    help="convection form: ubar.grad u~ (Eq. 22) or explicit Adams-Bashforth (Eq. 21)")
     ap.add_argument("--inner-iters", type=int, default=1,
                     help="inner velocity/pressure iterations per step (Algorithm 1)")
     ap.add_argument("--pc", default="amg", choices=["amg", "jacobi"],

@@ -99,7 +99,15 @@ typedef struct oasis_params {
                               increment drives the velocity update.  Repetitions after the
                               first start the pressure solve from zero.  The statistics of
                               a step describe its last repetition.  At most 16. */
+    int32_t convection;    /* OASIS_CONV_ABCN (Eq. 22, default) or OASIS_CONV_ABE (Eq. 21) */
 } oasis_params;
+
+/* Convection forms (Sec. 3).  ABCN: B = ubar . grad u~ with ubar = 1.5 u^{n-1} -
+ * 0.5 u^{n-2} and the Crank-Nicolson u~, implicit: A = M/dt + C(ubar)/2 + nu K/2.
+ * ABE: explicit Adams-Bashforth B = 1.5 u^{n-1}.grad u^{n-1} - 0.5 u^{n-2}.grad u^{n-2}
+ * on the right-hand side: A = M/dt + nu K/2 (the same matrix every step). */
+#define OASIS_CONV_ABCN 0
+#define OASIS_CONV_ABE 1
 
 /* Preconditioners of the pressure CG.  The paper preconditions its pressure solve
  * with algebraic multigrid (Sec. 6); OASIS_PC_AMG is a smoothed-aggregation

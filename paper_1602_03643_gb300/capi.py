@@ -30,6 +30,8 @@ OASIS_GUESS_PREV_PHI = 1
 OASIS_GUESS_LEARNED = 2
 OASIS_PC_JACOBI = 0
 OASIS_PC_AMG = 1
+OASIS_CONV_ABCN = 0
+OASIS_CONV_ABE = 1
 OASIS_MAT_M, OASIS_MAT_K, OASIS_MAT_G0, OASIS_MAT_G1, OASIS_MAT_G2, OASIS_MAT_A = range(6)
 
 ERROR_NAMES = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "EMESH", -4: "ENOTCONV", -5: "EBREAKDOWN",
@@ -42,7 +44,7 @@ class oasis_params(C.Structure):
                 ("max_it_u", C.c_int32), ("max_it_p", C.c_int32), ("precision", C.c_int32),
                 ("inner_rtol", C.c_double), ("batch_rhs", C.c_int32), ("use_graph", C.c_int32),
                 ("guess", C.c_int32), ("spmv_variant", C.c_int32), ("pressure_pc", C.c_int32),
-                ("inner_iters", C.c_int32)]
+                ("inner_iters", C.c_int32), ("convection", C.c_int32)]
 
 
 class oasis_amg_info(C.Structure):
@@ -231,7 +233,8 @@ def oasis_spmv_dot_f64_noalloc(mesh, which, x, y, xy, stream=None):
 
 def make_params(nu, dt, f=(0.0, 0.0, 0.0), rtol_u=1e-8, rtol_p=1e-8, max_it_u=1000, max_it_p=20000,
                 precision=OASIS_FP64, inner_rtol=1e-4, batch_rhs=1, use_graph=0, guess=OASIS_GUESS_ZERO,
-                spmv_variant=0, pressure_pc=0, inner_iters=1):
+                spmv_variant=0, pressure_pc=0, inner_iters=1,
+                convection=0):
     p = oasis_params()
     p.nu, p.dt = nu, dt
     ff = list(f) + [0.0] * (3 - len(f))
@@ -243,6 +246,7 @@ def make_params(nu, dt, f=(0.0, 0.0, 0.0), rtol_u=1e-8, rtol_p=1e-8, max_it_u=10
     p.batch_rhs, p.use_graph, p.guess, p.spmv_variant = batch_rhs, use_graph, guess, spmv_variant
     p.pressure_pc = pressure_pc
     p.inner_iters = inner_iters
+    p.convection = convection
     return p
 
 

@@ -193,6 +193,7 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     OASIS_CHECK(prm->pressure_pc == OASIS_PC_JACOBI || prm->pressure_pc == OASIS_PC_AMG, OASIS_EINVAL,
                 "pressure_pc");
     OASIS_CHECK(prm->inner_iters >= 0 && prm->inner_iters <= 16, OASIS_EINVAL, "inner_iters must be in [0, 16]");
+    OASIS_CHECK(prm->convection == OASIS_CONV_ABCN || prm->convection == OASIS_CONV_ABE, OASIS_EINVAL, "convection");
     OASIS_CHECK(n_dir >= 0 && (n_dir == 0 || dir), OASIS_EINVAL, "dirichlet dofs");
     OASIS_CHECK(m->max_row <= 64, OASIS_EMESH, "rows with more than 64 pattern entries are not supported");
     auto S = std::make_unique<Solver>();
@@ -218,6 +219,7 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     S->A.alloc(vb * m->nnz, s);
     S->dinvA.alloc(vb * n, s);
     S->beta.alloc(vb * m->nc * 4, s);
+    if (prm->convection == OASIS_CONV_ABE) S->beta2.alloc(vb * m->nc * 4, s);
     for (auto& w : S->w) w.alloc(vb * n * D, s);
     for (auto& w : S->pw) w.alloc(vb * n, s);
     for (auto& q : S->pq) q.alloc(4 * vb * n, s);

@@ -59,7 +59,7 @@ struct StepData {
     const S* g;                       // [n_dir][D]
     const int32_t* dir_index;
     // tentative system (V)
-    V *A, *dinvA, *beta;
+    V *A, *dinvA, *beta, *beta2;     // beta2: cell terms of u^{n-2} (explicit convection only)
     // BiCGStab work [n][D] (V)
     V *r, *rh, *p, *v, *s, *t, *ph, *sh, *dl;
     // CG work: gathered quads double-buffered by iteration parity; p; delta; x rounded
@@ -131,7 +131,7 @@ struct Solver {
     double t = 0.0;
     DBuf<int32_t> dir_index;
     RBuf g, u1, u2, du, r0, pstar, x, b, phi, phi_h1, phi_h2;          // S
-    RBuf A, dinvA, beta;                                               // V
+    RBuf A, dinvA, beta, beta2;                                        // V
     RBuf w[9];                                                         // V [n][D]
     RBuf pw[3];                                                        // V [n]
     RBuf pq[2];                                                        // CgQuad<V> [n]

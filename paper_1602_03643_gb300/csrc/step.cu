@@ -66,30 +66,46 @@ struct Consts {
 //   C^T_im = w_T grad lambda_m . (sum_l ubar_l + ubar_i) = beta[T][m] + ubar_i . w_T grad lambda_m;
 // the second term summed over the cells sharing an edge is ubar_i . dP_im / (d+2)
 // and is added in the row pass.
-template <class P, int D>
+// ABE (explicit Adams-Bashforth convection, Eq. 21): the same cell terms for
+// the two convecting velocities u^{n-1} (into beta) and u^{n-2} (into beta2).
+template <class P, int D, bool ABE>
 __global__ void __launch_bounds__(kBlock) k_cell_beta(StepData<P> a) {
     using V = typename P::V;
+    constexpr int NB = ABE ? 2 : 1;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < a.nc; c += (int64_t)gridDim.x * blockDim.x) {
-        V S[D];
+        V S[NB][D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) S[k] = 0;
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int k = 0; k < D; ++k) S[b][k] = 0;
 #pragma unroll
         for (int m = 0; m <= D; ++m) {
             const size_t j = (size_t)__ldg(&a.cell_dof[c * (D + 1) + m]) * D;
 #pragma unroll
-            for (int k = 0; k < D; ++k) S[k] += (V)1.5 * s_v(a.u1[j + k]) - (V)0.5 * s_v(a.u2[j + k]);
+            for (int k = 0; k < D; ++k) {
+                if constexpr (ABE) {
+                    S[0][k] += s_v(a.u1[j + k]);
+                    S[NB - 1][k] += s_v(a.u2[j + k]);
+                } else {
+                    S[0][k] += (V)1.5 * s_v(a.u1[j + k]) - (V)0.5 * s_v(a.u2[j + k]);
+                }
+            }
         }
-        V out[4];
 #pragma unroll
-        for (int m = 0; m <= D; ++m) {
-            V acc = 0;
+        for (int b = 0; b < NB; ++b) {
+            V out[4];
 #pragma unroll
-            for (int k = 0; k < D; ++k) acc += __ldg(&a.gw[((size_t)c * (D + 1) + m) * D + k]) * S[k];
-            out[m] = acc;
+            for (int m = 0; m <= D; ++m) {
+                V acc = 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) acc += __ldg(&a.gw[((size_t)c * (D + 1) + m) * D + k]) * S[b][k];
+                out[m] = acc;
+            }
+            if (D == 2) out[3] = 0;
+            V* dst = b == 0 ? a.beta : a.beta2;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) dst[c * 4 + m] = out[m];
         }
-        if (D == 2) out[3] = 0;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) a.beta[c * 4 + m] = out[m];
     }
 }
 
@@ -104,16 +120,21 @@ __global__ void __launch_bounds__(kBlock) k_cell_beta(StepData<P> a) {
 //    b_k - A u_k^{n-1} for b_k = f_k ML + (2M/dt - A) u^{n-1} - dP^k p*, the
 //    right-hand side formed by Algorithm 2.
 // Dirichlet rows become unit rows of A with r0 = g - u^{n-1}.
-template <class P, int D>
+// ABE: A = M/dt + nu K/2 and the shares -(nu K_ij u_j^{n-1} + 1.5 C1_ij u_j^{n-1}
+// - 0.5 C2_ij u_j^{n-2} + dP_ij p*_j), C1 from u^{n-1}, C2 from u^{n-2} (Eq. 21):
+// b - A u^{n-1} for b = (M/dt - nu K/2) u^{n-1} - 1.5 C1 u^{n-1} + 0.5 C2 u^{n-2}
+// + f ML - dP p*.
+template <class P, int D, bool ABE>
 __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typename P::V> k_) {
     using V = typename P::V;
     using S = typename P::S;
     using Acc = typename P::Acc;
+    constexpr int NB = ABE ? 2 : 1;
     extern __shared__ __align__(16) unsigned char dsm[];
-    V* s_t1 = reinterpret_cast<V*>(dsm);                       // [max_row][kTile]
-    V* s_con = s_t1 + (size_t)a.max_row * kTile;               // [tile_cap][D]
+    V* s_t1 = reinterpret_cast<V*>(dsm);                       // [NB][max_row][kTile]
+    V* s_con = s_t1 + (size_t)NB * a.max_row * kTile;          // [tile_cap][D]
     __shared__ int32_t s_rp[kTile + 1];
-    __shared__ V s_ub[D][kTile];
+    __shared__ V s_ub[NB][D][kTile];
     __shared__ int32_t s_dir[kTile];
     Acc part[D];
 #pragma unroll
@@ -125,7 +146,9 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
         const int64_t i = T.r0 + r;
         if (r < T.nr) {
             const int32_t len = s_rp[r + 1] - s_rp[r];
-            for (int32_t sl = 0; sl < len; ++sl) s_t1[sl * kTile + r] = 0;
+            for (int32_t sl = 0; sl < len; ++sl)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) s_t1[((size_t)b * a.max_row + sl) * kTile + r] = 0;
             // incident cells 8 at a time: their indices and slots, then their
             // beta rows (one aligned 4-vector each), then the additions in cell
             // order (the same order as one at a time)
@@ -140,18 +163,30 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
                     c[u] = ok ? a.inc_cell[qb + u] : 0;
                     w[u] = ok ? a.inc_slots[qb + u] : 0u;
                 }
-                Vec4A<V> bt[kU];
 #pragma unroll
-                for (int u = 0; u < kU; ++u) bt[u] = reinterpret_cast<const Vec4A<V>*>(a.beta)[c[u]];
+                for (int b = 0; b < NB; ++b) {
+                    const V* bsrc = b == 0 ? a.beta : a.beta2;
+                    V* t = s_t1 + (size_t)b * a.max_row * kTile;
+                    Vec4A<V> bt[kU];
 #pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    if (qb + u >= q1) break;
+                    for (int u = 0; u < kU; ++u) bt[u] = reinterpret_cast<const Vec4A<V>*>(bsrc)[c[u]];
 #pragma unroll
-                    for (int m = 0; m <= D; ++m) s_t1[((w[u] >> (8 * m)) & 0xffu) * kTile + r] += bt[u].v[m];
+                    for (int u = 0; u < kU; ++u) {
+                        if (qb + u >= q1) break;
+#pragma unroll
+                        for (int m = 0; m <= D; ++m) t[((w[u] >> (8 * m)) & 0xffu) * kTile + r] += bt[u].v[m];
+                    }
                 }
             }
 #pragma unroll
-            for (int k = 0; k < D; ++k) s_ub[k][r] = (V)1.5 * s_v(a.u1[i * D + k]) - (V)0.5 * s_v(a.u2[i * D + k]);
+            for (int k = 0; k < D; ++k) {
+                if constexpr (ABE) {
+                    s_ub[0][k][r] = s_v(a.u1[i * D + k]);
+                    s_ub[NB - 1][k][r] = s_v(a.u2[i * D + k]);
+                } else {
+                    s_ub[0][k][r] = (V)1.5 * s_v(a.u1[i * D + k]) - (V)0.5 * s_v(a.u2[i * D + k]);
+                }
+            }
             s_dir[r] = a.dir_index[i];
         }
         __syncthreads();
@@ -160,23 +195,34 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
             const int32_t sl = e - s_rp[rr];
             const int64_t ii = T.r0 + rr;
             const int32_t j = a.col[e];
-            V gv[D], gdot = 0;
+            V gv[D], gdot[NB] = {};
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 gv[k] = a.G[(size_t)k * a.nnz + e];
-                gdot += s_ub[k][rr] * gv[k];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) gdot[b] += s_ub[b][k][rr] * gv[k];
             }
-            const V c = s_t1[sl * kTile + rr] + gdot * inv_d2;
+            V cb[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) cb[b] = s_t1[((size_t)b * a.max_row + sl) * kTile + rr] + gdot[b] * inv_d2;
             const V kv = a.K[e];
-            V av = a.M[e] * k_.rdt + (V)0.5 * c + k_.hnu * kv;
+            V av = ABE ? a.M[e] * k_.rdt + k_.hnu * kv : a.M[e] * k_.rdt + (V)0.5 * cb[0] + k_.hnu * kv;
             if (s_dir[rr] >= 0) av = (j == ii) ? (V)1 : (V)0;
             a.A[e] = av;
             if (j == ii) a.dinvA[ii] = (V)1 / av;
-            const V ck = c + k_.nu * kv;
             const V ps = s_v(a.pstar[j]);
+            if constexpr (ABE) {
+                const V c1 = (V)1.5 * cb[0] + k_.nu * kv, c2 = (V)0.5 * cb[NB - 1];
 #pragma unroll
-            for (int k = 0; k < D; ++k)
-                s_con[(size_t)(e - T.e0) * D + k] = -(ck * s_v(a.u1[(size_t)j * D + k]) + gv[k] * ps);
+                for (int k = 0; k < D; ++k)
+                    s_con[(size_t)(e - T.e0) * D + k] =
+                        -(c1 * s_v(a.u1[(size_t)j * D + k]) - c2 * s_v(a.u2[(size_t)j * D + k]) + gv[k] * ps);
+            } else {
+                const V ck = cb[0] + k_.nu * kv;
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+                    s_con[(size_t)(e - T.e0) * D + k] = -(ck * s_v(a.u1[(size_t)j * D + k]) + gv[k] * ps);
+            }
         }
         __syncthreads();
         if (r < T.nr) {
@@ -1400,8 +1446,8 @@ struct StepImplT final : StepImpl {
     StepData<P> a{};
     Consts<V> k_{};
     int64_t tiles = 0;
-    size_t sm_asm = 0, sm_out_u = 0, sm_out_u1 = 0, sm_spmm = 0, sm_spmm1 = 0, sm_outp = 0, sm_v1 = 0, sm_vd = 0;
-    int g_asm = 1, g_out_u = 1, g_out_u1 = 1, g_spmm0 = 1, g_spmm1 = 1, g_spmm0_1 = 1, g_spmm1_1 = 1,
+    size_t sm_asm = 0, sm_asm2 = 0, sm_out_u = 0, sm_out_u1 = 0, sm_spmm = 0, sm_spmm1 = 0, sm_outp = 0, sm_v1 = 0, sm_vd = 0;
+    int g_asm = 1, g_asm2 = 1, g_out_u = 1, g_out_u1 = 1, g_spmm0 = 1, g_spmm1 = 1, g_spmm0_1 = 1, g_spmm1_1 = 1,
         g_rhs = 1, g_upd = 1;
     int ge_n = 1, ge_nd = 1, ge_c = 1;
     int g_sell = 1;
@@ -1452,6 +1498,7 @@ struct StepImplT final : StepImpl {
         a.A = Sv.A.as<V>();
         a.dinvA = Sv.dinvA.as<V>();
         a.beta = Sv.beta.as<V>();
+        a.beta2 = Sv.beta2.as<V>();
         V** w[9] = {&a.r, &a.rh, &a.p, &a.v, &a.s, &a.t, &a.ph, &a.sh, &a.dl};
         for (int q = 0; q < 9; ++q) *w[q] = Sv.w[q].as<V>();
         V** pw[3] = {&a.pp, &a.pdl, &a.xv};
@@ -1490,6 +1537,7 @@ struct StepImplT final : StepImpl {
         tiles = (m.n + kTile - 1) / kTile;
         const size_t cap = (size_t)std::max(1, m.tile_cap);
         sm_asm = (size_t)m.max_row * kTile * sizeof(V) + cap * D * sizeof(V);
+        sm_asm2 = 2 * (size_t)m.max_row * kTile * sizeof(V) + cap * D * sizeof(V);
         sm_out_u = cap * D * sizeof(Acc);
         sm_out_u1 = cap * sizeof(Acc);
         sm_spmm = cap * D * sizeof(V);
@@ -1497,7 +1545,8 @@ struct StepImplT final : StepImpl {
         sm_outp = cap * sizeof(Acc);
         sm_v1 = cap * sizeof(V);
         sm_vd = cap * D * sizeof(V);
-        g_asm = tile_grid(k_assemble<P, D>, sm_asm, tiles);
+        g_asm = tile_grid(k_assemble<P, D, false>, sm_asm, tiles);
+        if (Sv.prm.convection == OASIS_CONV_ABE) g_asm2 = tile_grid(k_assemble<P, D, true>, sm_asm2, tiles);
         g_out_u = tile_grid(k_bicg_outer<P, D, D>, sm_out_u, tiles);
         g_out_u1 = tile_grid(k_bicg_outer<P, D, 1>, sm_out_u1, tiles);
         g_spmm0 = tile_grid(k_bicg_spmm<P, D, D, 0>, sm_spmm, tiles);
@@ -1513,9 +1562,14 @@ struct StepImplT final : StepImpl {
     }
 
     void assemble(cudaStream_t s) override {
-        k_cell_beta<P, D><<<ge_c, kBlock, 0, s>>>(a);
         const int pa = Sv.prof_begin(s, OASIS_PROF_ASSEMBLE);
-        k_assemble<P, D><<<g_asm, kBlock, sm_asm, s>>>(a, k_);
+        if (Sv.prm.convection == OASIS_CONV_ABE) {
+            k_cell_beta<P, D, true><<<ge_c, kBlock, 0, s>>>(a);
+            k_assemble<P, D, true><<<g_asm2, kBlock, sm_asm2, s>>>(a, k_);
+        } else {
+            k_cell_beta<P, D, false><<<ge_c, kBlock, 0, s>>>(a);
+            k_assemble<P, D, false><<<g_asm, kBlock, sm_asm, s>>>(a, k_);
+        }
         Sv.prof_end(s, pa);
         OASIS_CUDA(cudaGetLastError());
     }
