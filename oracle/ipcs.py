@@ -27,6 +27,11 @@ to the right-hand side:
         + int f_k phi - G^k p*
 with C(w)_ij = int phi_i w . grad phi_j.
 
+Velocity update (Sec. 5): `velocity_update="lumped"` (default) is the lumped
+update above; `"consistent"` solves the update with the mass matrix,
+  M u_k^n = M u_k^I - dt G^k phi,   rows in the Dirichlet set: u_k^n = g_k,
+by a sparse LU solve.
+
 Inner iterations (Algorithm 1): the tentative and pressure solves are repeated
 `inner_iters` times within a step, each time with p* = the newest pressure (the
 matrix A, which holds only old velocities, is unchanged); phi is the increment
@@ -81,12 +86,17 @@ def _jacobi(A):
 
 class IPCS:
     def __init__(self, problem, iterative: bool = False, rtol: float = 1e-12,
-                 maxiter: int = 100000, inner_iters: int = 1, convection: str = "abcn"):
+                 maxiter: int = 100000, inner_iters: int = 1, convection: str = "abcn",
+                 velocity_update: str = "lumped"):
         self.pb = problem
         self.inner_iters = max(1, int(inner_iters))
         if convection not in ("abcn", "abe"):
             raise ValueError(convection)
         self.convection = convection
+        if velocity_update not in ("lumped", "consistent"):
+            raise ValueError(velocity_update)
+        self.velocity_update = velocity_update
+        self._Mlu = None
         self.disc = Discretization(problem.mesh)
         self.iterative = iterative
         self.rtol = rtol
@@ -166,7 +176,18 @@ class IPCS:
             phi = p - p_star
             increments.append(phi)
             p_star = p
-        u_n = np.stack([u_I[k] - pb.dt * (D.G[k] @ phi) / D.ML for k in range(D.d)])
+        if self.velocity_update == "consistent":
+            if self._Mlu is None:
+                self._Mlu = spla.splu(replace_rows(D.M, self.dirichlet).tocsc())
+            g = pb.g(t_new)
+            rows = []
+            for k in range(D.d):
+                rhs = D.M @ u_I[k] - pb.dt * (D.G[k] @ phi)
+                rhs[self.dirichlet] = g[k] if len(self.dirichlet) else rhs[self.dirichlet]
+                rows.append(self._Mlu.solve(rhs))
+            u_n = np.stack(rows)
+        else:
+            u_n = np.stack([u_I[k] - pb.dt * (D.G[k] @ phi) / D.ML for k in range(D.d)])
         u_n[:, self.dirichlet] = pb.g(t_new)
         out = State(u_n, s.u_nm1, p, t_new)
         out.u_I, out.phi, out.bp = u_I, phi, bp

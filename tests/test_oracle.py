@@ -149,7 +149,7 @@ def test_periodic_mesh_invariants():
 
 
 # ----------------------------------------------------------------- dense brute force
-def dense_step(pb, state, form="abcn"):
+def dense_step(pb, state, form="abcn", update="lumped"):
     """One IPCS step by quadrature element integrals, dense algebra and the
     in-place Algorithm 2 ordering (a second route to the same discrete step).
     form="abe": explicit Adams-Bashforth convection (Eq. 21) on the right-hand
@@ -192,27 +192,35 @@ def dense_step(pb, state, form="abcn"):
     bp -= bp.mean()
     p = np.linalg.lstsq(Kd, bp, rcond=None)[0]          # minimum norm = zero mean
     phi = p - state.p
-    un = np.stack([uI[k] - dt * (Gd[k] @ phi) / ML for k in range(d)])
+    if update == "consistent":
+        Mb = Md.copy()
+        Mb[pb.dirichlet, :] = 0.0
+        Mb[pb.dirichlet, pb.dirichlet] = 1.0
+        rhs = np.stack([Md @ uI[k] - dt * (Gd[k] @ phi) for k in range(d)])
+        rhs[:, pb.dirichlet] = pb.g(t_new)
+        un = np.stack([np.linalg.solve(Mb, rhs[k]) for k in range(d)])
+    else:
+        un = np.stack([uI[k] - dt * (Gd[k] @ phi) / ML for k in range(d)])
     un[:, pb.dirichlet] = pb.g(t_new)
     return un, p, uI
 
 
-@pytest.mark.parametrize("form", ["abcn", "abe"])
+@pytest.mark.parametrize("form,update", [("abcn", "lumped"), ("abe", "lumped"), ("abcn", "consistent")])
 @pytest.mark.parametrize("kind", ["tg2d", "tg3d", "channel"])
-def test_oracle_step_matches_dense_brute_force(kind, form):
+def test_oracle_step_matches_dense_brute_force(kind, form, update):
     if kind == "tg2d":
         pb = WP.taylor_green_2d(3)
     elif kind == "tg3d":
         pb = WP.taylor_green_3d(3)
     else:
         pb = WP.channel(nx=3, ny=4, nz=2, perturb=0.1)
-    o = IPCS(pb, convection=form)
+    o = IPCS(pb, convection=form, velocity_update=update)
     s = o.initial_state()
     rng = np.random.default_rng(3)
     s.u_nm2 = s.u_nm2 + 0.05 * rng.normal(size=s.u_nm2.shape)   # make ubar != u^{n-1}
     s.u_nm2[:, pb.dirichlet] = s.u_nm1[:, pb.dirichlet]
     for _ in range(2):
-        un, p, uI = dense_step(pb, s, form)
+        un, p, uI = dense_step(pb, s, form, update)
         s2 = o.step(s)
         np.testing.assert_allclose(s2.u_I, uI, rtol=0, atol=1e-11 * np.abs(uI).max())
         np.testing.assert_allclose(s2.p, p, rtol=0, atol=1e-10 * max(np.abs(p).max(), 1e-3))
@@ -265,12 +273,12 @@ def test_table1_p1p1_values(row):
 
 
 # ----------------------------------------------------------------- scheme-level pins
-@pytest.mark.parametrize("form", ["abcn", "abe"])
-def test_unit_square_velocity_second_order(form):
+@pytest.mark.parametrize("form,update", [("abcn", "lumped"), ("abe", "lumped"), ("abcn", "consistent")])
+def test_unit_square_velocity_second_order(form, update):
     errs, hs = [], []
     for n in (16, 32, 64):
         pb = WP.taylor_green_2d(n)
-        s = IPCS(pb, convection=form).run(100)
+        s = IPCS(pb, convection=form, velocity_update=update).run(100)
         x = pb.mesh.dof_coords()
         errs.append(_rms(s.u_nm1 - pb.exact_u(x, s.t)))
         hs.append(mesh_size(pb.mesh.coords, pb.mesh.cells))
