@@ -143,7 +143,9 @@ def run_ours(args, rank, world):
         return IPCSRun(pb, precision=precision, rtol_u=RTOL, rtol_p=RTOL, max_it_u=5000, max_it_p=200000,
                        inner_rtol=args.inner_rtol, use_graph=graph, guess=guess, batch_rhs=batch,
                        pressure_pc=pc if pressure_pc is None else pressure_pc, inner_iters=args.inner_iters,
-                       convection=1 if args.convection == "abe" else 0, stream=stream)
+                       convection=1 if args.convection == "abe" else 0,
+                       velocity_update=capi.OASIS_UPDATE_CONSISTENT if args.velocity_update == "consistent"
+                       else capi.OASIS_UPDATE_LUMPED, stream=stream)
 
     def timed_steps(run, k):
         evs = []
@@ -341,6 +343,7 @@ def run_ours(args, rank, world):
     it_p = float(np.mean([s["it_p"] for s in stats]))
     sw_u = float(np.mean([s["sweeps_u"] for s in stats]))
     sw_p = float(np.mean([s["sweeps_p"] for s in stats]))
+    it_m = float(np.mean([s["it_m"] for s in stats]))
     # kernels per step in the graph: beta + assembly 2; velocity: per sweep a residual
     # and (all but the last) a correction, 5 per BiCGStab iteration; pressure: rhs
     # and guess 2, per sweep residual + CG start + (all but the last) correction,
@@ -348,13 +351,19 @@ def run_ours(args, rank, world):
     # learned guess: input scales, inputs, two network layers, judge.  Multigrid:
     # a V-cycle is 4 kernels per operator level + the dense coarsest solve; per
     # sweep residual, start, V-cycle, product (and all but the last a
-    # correction); per iteration update, V-cycle, product.
+    # correction); per iteration update, V-cycle, product.  Inner iterations
+    # (Algorithm 1; the statistics describe the last repetition): per repetition
+    # after the first a pressure advance, the assembly and both solves again.
+    # Consistent-mass update: start 2, 2 per CG iteration, then the update.
     if amg_info:
         vk = 4 * (amg_info["levels"] - 1) + 1
         p_kernels = sw_p * (4 + vk) + it_p * (2 + vk)
     else:
         p_kernels = 3 * sw_p + it_p
-    launches = int(round(args.steps * (3 + 2 * sw_u + 5 * it_u + p_kernels + (5 if learned else 0))))
+    ni = max(1, args.inner_iters)
+    upd_kernels = 3 + 2 * it_m if args.velocity_update == "consistent" else 1
+    launches = int(round(args.steps * (ni * (2 + 2 * sw_u + 5 * it_u + p_kernels) + (ni - 1)
+                                       + (5 if learned else 0) + upd_kernels)))
     run.close()
 
     line = {
@@ -366,7 +375,8 @@ def run_ours(args, rank, world):
         "config": workload_config(args.workload, pb, "mixed") | {
             "parallelism": f"replicas x{world}",
             "pressure_guess": "learned (judged against previous phi)" if learned else "previous phi",
-            "pressure_pc": args.pc, "inner_iters": args.inner_iters, "convection": args.convection},
+            "pressure_pc": args.pc, "inner_iters": args.inner_iters, "convection": args.convection,
+            "velocity_update": args.velocity_update},
         "e2e": {"value": world * k_e2e / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -374,6 +384,7 @@ def run_ours(args, rank, world):
         "roofline": roofline,
         "roofline_next_kernel": roofline_other,
         "solver": {"it_u_mean": it_u, "it_p_mean": it_p, "sweeps_u_mean": sw_u, "sweeps_p_mean": sw_p,
+                   "it_mass_mean": it_m,
                    "failed_steps": len(bad), "res_p_last": stats[-1]["res_p"]},
         "fp64_gpu": fp64,
         "mixed_prev_phi": prev_form,
@@ -388,12 +399,19 @@ def run_ours(args, rank, world):
 
 
 # ---------------------------------------------------------------------- oracle (CPU)
+def oracle_options(args):
+    """The scheme options of the run, in the oracle's terms."""
+    return {"inner_iters": max(1, getattr(args, "inner_iters", 1)),
+            "convection": getattr(args, "convection", "abcn"),
+            "velocity_update": getattr(args, "velocity_update", "lumped")}
+
+
 def cpu_baseline(args, pb, budget_s=20.0):
     """The CPU float64 oracle, as it stands, on this host (iterative solves at 1e-8)."""
     import numpy as np  # noqa: F401
     from oracle.ipcs import IPCS
     t0 = time.perf_counter()
-    o = IPCS(pb, iterative=True, rtol=RTOL)
+    o = IPCS(pb, iterative=True, rtol=RTOL, **oracle_options(args))
     setup = time.perf_counter() - t0
     s = o.initial_state()
     n = 0
@@ -422,7 +440,7 @@ def run_reference(args, rank, world):
         return None
     pb = workload(args.workload)
     from oracle.ipcs import IPCS
-    o = IPCS(pb, iterative=True, rtol=RTOL)
+    o = IPCS(pb, iterative=True, rtol=RTOL, **oracle_options(args))
     s = o.initial_state()
     for _ in range(min(args.warmup, 1)):
         s = o.step(s)
@@ -458,6 +476,9 @@ def main():
     ap.add_argument("--guess", default="learned", choices=["learned", "prev"])
     ap.add_argument("--convection", default="abcn", choices=["abcn", "abe"],
                     help="convection form: ubar.grad u~ (Eq. 22) or explicit Adams-Bashforth (Eq. 21)")
+    ap.add_argument("--velocity-update", default="lumped", choices=["lumped", "consistent"],
+                    help="velocity update of the projection: lumped mass or a CG on the consistent mass "
+                         "matrix (Sec. 5)")
     ap.add_argument("--inner-iters", type=int, default=1,
                     help="inner velocity/pressure iterations per step (Algorithm 1)")
     ap.add_argument("--pc", default="amg", choices=["amg", "jacobi"],

@@ -100,7 +100,21 @@ typedef struct oasis_params {
                               first start the pressure solve from zero.  The statistics of
                               a step describe its last repetition.  At most 16. */
     int32_t convection;    /* OASIS_CONV_ABCN (Eq. 22, default) or OASIS_CONV_ABE (Eq. 21) */
+    int32_t velocity_update; /* OASIS_UPDATE_LUMPED (default) or OASIS_UPDATE_CONSISTENT */
 } oasis_params;
+
+/* Velocity update of the projection (Sec. 5).  LUMPED: u_k^n = u_k^I - dt
+ * (dP^k phi) / ML, one pass.  CONSISTENT: M u_k^n = M u_k^I - dt dP^k phi with
+ * Dirichlet rows u^n = g, solved for the increment u^n - u^I by a d-RHS CG on the
+ * interior block of M with the lumped mass as preconditioner (a multiple of
+ * diag M for P1 elements), started from the lumped increment and stopped at
+ * ||r|| <= tol ||dt dP^k phi|| per component (interior rows), tol = rtol_u for
+ * OASIS_FP64 and max(rtol_u, 1e-6) for OASIS_MIXED, whose solve runs in float32
+ * (the increment is O(dt), so its float32 error stays far below that of u^n).
+ * The solve's iterations count against max_it_u; hitting the cap sets the
+ * step's status to OASIS_ENOTCONV. */
+#define OASIS_UPDATE_LUMPED 0
+#define OASIS_UPDATE_CONSISTENT 1
 
 /* Convection forms (Sec. 3).  ABCN: B = ubar . grad u~ with ubar = 1.5 u^{n-1} -
  * 0.5 u^{n-2} and the Crank-Nicolson u~, implicit: A = M/dt + C(ubar)/2 + nu K/2.
@@ -113,7 +127,7 @@ typedef struct oasis_params {
  * with algebraic multigrid (Sec. 6); OASIS_PC_AMG is a smoothed-aggregation
  * hierarchy of K built once per mesh on the host (strength threshold 0.08,
  * greedy aggregation, Jacobi-smoothed prolongator, Galerkin coarse operators,
- * dense coarsest level <= 400 dofs) applied as one V(1,1) cycle with damped
+ * dense coarsest level <= 2048 dofs) applied as one V(1,1) cycle with damped
  * Jacobi smoothing: a symmetric positive semi-definite preconditioner. */
 #define OASIS_PC_JACOBI 0
 #define OASIS_PC_AMG 1
@@ -154,6 +168,9 @@ typedef struct oasis_step_stats {
     double t;              /* time t^n reached by the step */
     double guess_res[2];   /* OASIS_GUESS_LEARNED: ||b - K phi0|| / ||b|| of the network's
                               guess [0] and of the fallback phi^{n-1} [1]; else 0 */
+    double res_m[3];       /* OASIS_UPDATE_CONSISTENT: final recurrence ||r|| / ||dt dP^k phi||
+                              of the mass solve per component; else 0 */
+    int32_t it_m;          /* OASIS_UPDATE_CONSISTENT: CG iterations of the mass solve */
 } oasis_step_stats;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -343,10 +360,12 @@ int oasis_get_tuning(const oasis_solver* s, oasis_tuning* out);
 #define OASIS_PROF_BICG_SPMM 1     /* the d-RHS products of the tentative BiCGStab */
 #define OASIS_PROF_ASSEMBLE 2      /* fused convection assembly + Algorithm 2 row pass */
 #define OASIS_PROF_PCG_UPDATE 3    /* CG start of each refinement sweep (w0 = K M^-1 r0, dots) */
-#define OASIS_PROF_UPDATE 4        /* lumped velocity update + rotation */
+#define OASIS_PROF_UPDATE 4        /* velocity update (lumped, or the final pass of the
+                                      consistent one) + rotation */
 #define OASIS_PROF_PRESSURE_RHS 5  /* pressure right-hand side */
 #define OASIS_PROF_GUESS 6         /* learned guess: input scaling, network forward, judge */
 #define OASIS_PROF_AMG 7           /* multigrid V-cycles of the pressure CG */
+#define OASIS_PROF_MASS 8          /* consistent-mass update: the mass CG's start and iterations */
 
 /* enable = 1: from now on, eager steps record CUDA events around the launches
  * of the kernel families above; the counters are reset by every call. */

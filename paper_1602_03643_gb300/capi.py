@@ -32,6 +32,8 @@ OASIS_PC_JACOBI = 0
 OASIS_PC_AMG = 1
 OASIS_CONV_ABCN = 0
 OASIS_CONV_ABE = 1
+OASIS_UPDATE_LUMPED = 0
+OASIS_UPDATE_CONSISTENT = 1
 OASIS_MAT_M, OASIS_MAT_K, OASIS_MAT_G0, OASIS_MAT_G1, OASIS_MAT_G2, OASIS_MAT_A = range(6)
 
 ERROR_NAMES = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "EMESH", -4: "ENOTCONV", -5: "EBREAKDOWN",
@@ -44,7 +46,8 @@ class oasis_params(C.Structure):
                 ("max_it_u", C.c_int32), ("max_it_p", C.c_int32), ("precision", C.c_int32),
                 ("inner_rtol", C.c_double), ("batch_rhs", C.c_int32), ("use_graph", C.c_int32),
                 ("guess", C.c_int32), ("spmv_variant", C.c_int32), ("pressure_pc", C.c_int32),
-                ("inner_iters", C.c_int32), ("convection", C.c_int32)]
+                ("inner_iters", C.c_int32), ("convection", C.c_int32),
+                ("velocity_update", C.c_int32)]
 
 
 class oasis_amg_info(C.Structure):
@@ -71,13 +74,13 @@ class oasis_step_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("it_u", C.c_int32 * 3), ("sweeps_u", C.c_int32),
                 ("it_p", C.c_int32), ("sweeps_p", C.c_int32), ("guess_used", C.c_int32),
                 ("res_u", C.c_double * 3), ("res_p", C.c_double), ("t", C.c_double),
-                ("guess_res", C.c_double * 2)]
+                ("guess_res", C.c_double * 2), ("res_m", C.c_double * 3), ("it_m", C.c_int32)]
 
     def as_dict(self):
         return {"status": self.status, "it_u": list(self.it_u), "sweeps_u": self.sweeps_u,
                 "it_p": self.it_p, "sweeps_p": self.sweeps_p, "guess_used": self.guess_used,
                 "res_u": list(self.res_u), "res_p": self.res_p, "t": self.t,
-                "guess_res": list(self.guess_res)}
+                "guess_res": list(self.guess_res), "res_m": list(self.res_m), "it_m": self.it_m}
 
 
 class OasisError(RuntimeError):
@@ -234,7 +237,7 @@ def oasis_spmv_dot_f64_noalloc(mesh, which, x, y, xy, stream=None):
 def make_params(nu, dt, f=(0.0, 0.0, 0.0), rtol_u=1e-8, rtol_p=1e-8, max_it_u=1000, max_it_p=20000,
                 precision=OASIS_FP64, inner_rtol=1e-4, batch_rhs=1, use_graph=0, guess=OASIS_GUESS_ZERO,
                 spmv_variant=0, pressure_pc=0, inner_iters=1,
-                convection=0):
+                convection=0, velocity_update=0):
     p = oasis_params()
     p.nu, p.dt = nu, dt
     ff = list(f) + [0.0] * (3 - len(f))
@@ -247,6 +250,7 @@ def make_params(nu, dt, f=(0.0, 0.0, 0.0), rtol_u=1e-8, rtol_p=1e-8, max_it_u=10
     p.pressure_pc = pressure_pc
     p.inner_iters = inner_iters
     p.convection = convection
+    p.velocity_update = velocity_update
     return p
 
 
@@ -305,7 +309,7 @@ def oasis_get_tentative_system(solver, dim, n, nnz, stream=None):
 
 
 PROF_FAMILIES = {"pcg_spmv": 0, "bicg_spmm": 1, "assemble": 2, "pcg_update": 3, "update": 4,
-                 "pressure_rhs": 5, "guess": 6, "amg": 7}
+                 "pressure_rhs": 5, "guess": 6, "amg": 7, "mass": 8}
 
 
 def oasis_profile(solver, enable=True):

@@ -92,6 +92,31 @@ void Solver::run_loops(cudaStream_t s, bool graph_mode, int which, const LoopFn&
     OASIS_CUDA(cudaStreamEndCapture(s1, &tmp));
 }
 
+void Solver::run_single(cudaStream_t s, bool graph_mode, int which, const LoopFn& start, const LoopFn& iter) {
+    if (!graph_mode) {
+        Loop lp;
+        const int chunk = 4;
+        start(s, lp);
+        for (int guard = 0; guard < 1000000; ++guard) {
+            poll(s, which);
+            if (h_st[which].in_done[0]) return;
+            for (int c = 0; c < chunk; ++c) iter(s, lp);
+        }
+        throw Error(OASIS_ENOTCONV, "Krylov loop did not terminate");
+    }
+    cudaGraph_t g = capture_graph_of(s);
+    Loop lp;
+    lp.graph = 1;
+    OASIS_CUDA(cudaGraphConditionalHandleCreate(&lp.h_inner, g, 0, 0));
+    start(s, lp);
+    cudaGraph_t body = add_while(s, lp.h_inner);
+    cudaStream_t s1 = cap[1];
+    OASIS_CUDA(cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    iter(s1, lp);
+    cudaGraph_t tmp;
+    OASIS_CUDA(cudaStreamEndCapture(s1, &tmp));
+}
+
 int Solver::prof_begin(cudaStream_t s, int family) {
     if (!prof_on || prm.use_graph) return -1;
     const size_t idx = ev_used.size();
@@ -129,7 +154,7 @@ void Solver::step(cudaStream_t s) {
         OASIS_CUDA(cudaGraphLaunch(gexec, s));
     } else {
         enqueue_step(s, false);
-        OASIS_CUDA(cudaMemcpyAsync(h_st, st.p, 2 * sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
+        OASIS_CUDA(cudaMemcpyAsync(h_st, st.p, kStates * sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
         if (prof_on) prof_collect();
     }
     t += prm.dt;
@@ -137,7 +162,7 @@ void Solver::step(cudaStream_t s) {
 
 // One time step (Algorithm 1): assembly, then per inner repetition the
 // tentative and pressure solves (p* advanced and the tentative residual
-// re-formed between repetitions), then the lumped velocity update.
+// re-formed between repetitions), then the velocity update (lumped, or the consistent-mass solve).
 void Solver::enqueue_step(cudaStream_t s, bool graph_mode) {
     const int ni = std::max(1, prm.inner_iters);
     impl->assemble(s);
@@ -149,7 +174,7 @@ void Solver::enqueue_step(cudaStream_t s, bool graph_mode) {
         impl->tentative_solve(s, graph_mode);
         impl->pressure_solve(s, graph_mode, it);
     }
-    impl->update(s);
+    impl->update(s, graph_mode);
 }
 
 void Solver::capture() {
@@ -157,7 +182,7 @@ void Solver::capture() {
     OASIS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     try {
         enqueue_step(s, true);
-        OASIS_CUDA(cudaMemcpyAsync(h_st, st.p, 2 * sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
+        OASIS_CUDA(cudaMemcpyAsync(h_st, st.p, kStates * sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
     } catch (...) {
         cudaGraph_t g;
         cudaStreamEndCapture(s, &g);
@@ -194,6 +219,8 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
                 "pressure_pc");
     OASIS_CHECK(prm->inner_iters >= 0 && prm->inner_iters <= 16, OASIS_EINVAL, "inner_iters must be in [0, 16]");
     OASIS_CHECK(prm->convection == OASIS_CONV_ABCN || prm->convection == OASIS_CONV_ABE, OASIS_EINVAL, "convection");
+    OASIS_CHECK(prm->velocity_update == OASIS_UPDATE_LUMPED || prm->velocity_update == OASIS_UPDATE_CONSISTENT,
+                OASIS_EINVAL, "velocity_update");
     OASIS_CHECK(n_dir >= 0 && (n_dir == 0 || dir), OASIS_EINVAL, "dirichlet dofs");
     OASIS_CHECK(m->max_row <= 64, OASIS_EMESH, "rows with more than 64 pattern entries are not supported");
     auto S = std::make_unique<Solver>();
@@ -223,6 +250,8 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     for (auto& w : S->w) w.alloc(vb * n * D, s);
     for (auto& w : S->pw) w.alloc(vb * n, s);
     for (auto& q : S->pq) q.alloc(4 * vb * n, s);
+    if (prm->velocity_update == OASIS_UPDATE_CONSISTENT)
+        for (auto& w : S->mw) w.alloc(vb * n * D, s);
     if (prm->pressure_pc == OASIS_PC_AMG) {
         amg_build(*m, s);
         S->amgw.alloc(*m->amg, vb);
@@ -233,14 +262,14 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     OASIS_CUDA(cudaMemsetAsync(S->feat.p, 0, S->feat.bytes(), s));
     OASIS_CUDA(cudaMemsetAsync(S->gy.p, 0, S->gy.bytes(), s));
     S->stage.alloc(std::max<int64_t>(n, n_dir) * D);
-    S->st.alloc(2);
+    S->st.alloc(Solver::kStates);
     OASIS_CUDA(cudaMemsetAsync(S->st.p, 0, S->st.bytes(), s));
     // per-block partial sums: up to 8 values of 16 bytes per block, for grids of
     // at most max(8 blocks per SM, one block per 256 rows)
     const int64_t max_blocks = std::max<int64_t>((int64_t)num_sms() * 8, (n + kBlock - 1) / kBlock + 1);
     S->partial.alloc((size_t)max_blocks * 8 * 16, s);
-    OASIS_CUDA(cudaHostAlloc(&S->h_st, 2 * sizeof(KrylovState), cudaHostAllocDefault));
-    std::memset(S->h_st, 0, 2 * sizeof(KrylovState));
+    OASIS_CUDA(cudaHostAlloc(&S->h_st, Solver::kStates * sizeof(KrylovState), cudaHostAllocDefault));
+    std::memset(S->h_st, 0, Solver::kStates * sizeof(KrylovState));
     for (auto& c : S->cap) OASIS_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
     S->impl.reset(make_step_impl(*S));
     S->impl->tune(s, prm->spmv_variant);
@@ -252,7 +281,13 @@ static void fill_stats(const Solver& S, oasis_step_stats* o) {
     std::memset(o, 0, sizeof(*o));
     const KrylovState& u = S.h_st[0];
     const KrylovState& p = S.h_st[1];
-    o->status = u.status != OASIS_OK ? u.status : p.status;
+    const KrylovState& mm = S.h_st[2];
+    const bool cons = S.prm.velocity_update == OASIS_UPDATE_CONSISTENT;
+    o->status = u.status != OASIS_OK ? u.status : p.status != OASIS_OK ? p.status : cons ? mm.status : OASIS_OK;
+    if (cons) {
+        o->it_m = mm.it_total[0];
+        for (int k = 0; k < S.m->dim && k < 3; ++k) o->res_m[k] = mm.bb[k] > 0 ? std::sqrt(mm.rr[k] / mm.bb[k]) : 0.0;
+    }
     for (int k = 0; k < 3; ++k) {
         o->it_u[k] = k < S.m->dim ? u.it_total[k] : 0;
         o->res_u[k] = (k < S.m->dim && u.bb[k] > 0) ? std::sqrt(u.rr[k] / u.bb[k]) : 0.0;

@@ -68,7 +68,8 @@ struct StepData {
     V *ar, *as, *aw, *au;             // multigrid-preconditioned CG: r, s, w = K u, u = M r
     float* feat;                      // learned guess: features [n][3]
     float* gy;                        // learned guess: network output [n]
-    KrylovState *stu, *stp;
+    V *mx, *mr, *mz, *mp, *mq;        // consistent-mass update [n][D]: increment, r, z, p, q = M p
+    KrylovState *stu, *stp, *stm;
     void* partial;
     double f[3];
     double dt, nu;
@@ -106,7 +107,8 @@ struct StepImpl {
     virtual void pressure_solve(cudaStream_t s, bool graph, int inner) = 0;
     // p* <- p (normalised) between repetitions, velocities untouched
     virtual void advance_pressure(cudaStream_t s) = 0;
-    virtual void update(cudaStream_t s) = 0;
+    // velocity update (lumped, or the consistent-mass solve then the update)
+    virtual void update(cudaStream_t s, bool graph) = 0;
     virtual void to_state(cudaStream_t s, const double* src_soa, int which, int64_t count, int comps) = 0;
     virtual void from_state(cudaStream_t s, double* dst_soa, int which, int64_t count, int comps) = 0;
     virtual void a_to_double(cudaStream_t s, double* dst) = 0;
@@ -136,21 +138,23 @@ struct Solver {
     RBuf pw[3];                                                        // V [n]
     RBuf pq[2];                                                        // CgQuad<V> [n]
     RBuf amg_vec[4];                                                   // V [n]: r, s, w, u (multigrid CG)
+    RBuf mw[5];                                                        // V [n][D]: consistent-mass CG
     AmgWork amgw;                                                      // V-cycle work vectors
     DBuf<float> feat, gy;                                              // learned-guess features / output
     struct Net* net = nullptr;                                         // attached network (not owned)
     bool record = false;                                               // compute features every step
     RBuf Kout;                                                         // S [nnz]
     DBuf<double> stage;                                                // [max(n, n_dir) * D]
-    DBuf<KrylovState> st;                                              // [0] velocity, [1] pressure
+    static constexpr int kStates = 3;
+    DBuf<KrylovState> st;                                              // [0] velocity, [1] pressure, [2] mass
     RBuf partial;
-    KrylovState* h_st = nullptr;                                       // pinned mirror [2]
+    KrylovState* h_st = nullptr;                                       // pinned mirror [kStates]
     std::unique_ptr<StepImpl> impl;
     cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     // eager-mode kernel timing (CUDA events around selected launches)
-    static constexpr int kProfFamilies = 8;
+    static constexpr int kProfFamilies = 9;
     bool prof_on = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
     std::vector<std::pair<int, int>> ev_used;
@@ -162,6 +166,9 @@ struct Solver {
 
     void run_loops(cudaStream_t s, bool graph_mode, int which, const LoopFn& outer, const LoopFn& inner,
                    const LoopFn& correct, int k0 = 0, int nr = 3);
+    // start; while (inner cond) { iter }: a single Krylov sweep whose kernels
+    // set h_inner (graph) or in_done[0] of state `which` (eager polls)
+    void run_single(cudaStream_t s, bool graph_mode, int which, const LoopFn& start, const LoopFn& iter);
     void poll(cudaStream_t s, int which);
     void step(cudaStream_t s);
     void enqueue_step(cudaStream_t s, bool graph);

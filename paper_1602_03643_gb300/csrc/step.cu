@@ -1325,11 +1325,280 @@ __global__ void __launch_bounds__(kBlock) k_pressure_advance(StepData<P> a) {
         a.pstar[i] = s_sub(s_add(a.pstar[i], a.x[i]), meanp);
 }
 
+// ================================================================ consistent-mass update
+// Sec. 5 without lumping: M u^n = M u^I - dt dP^k phi with Dirichlet rows
+// u^n = g, solved for the increment delta = u^n - u^I (the d components as d
+// right-hand sides of one CG).  Dirichlet rows hold delta = g - u^I and stay out
+// of the Krylov space (r = z = p = q = 0 there), so the CG runs on the interior
+// block of M, which is symmetric positive definite.  The preconditioner is the
+// lumped mass: for P1 elements every row sum of M is (d + 2) / 2 times its
+// diagonal, so this is Jacobi.  Start: delta_0 = -dt dP^k phi / ML (the lumped
+// update), stopping test ||r|| <= tol ||dt dP^k phi|| over the interior rows.
+// Per iteration two kernels: q = M z + beta q, p = z + beta p with <p, q>, then
+// delta += alpha p, r -= alpha q, z = r / ML with <r, z> and <r, r>; a converged
+// component is frozen (its coefficients are no longer updated).
+
+// delta_0 and -dt dP^k phi (kept in q until the residual kernel); block 0
+// resets the solve's scalars (nothing else in this kernel reads them).
+template <class P, int D>
+__global__ void __launch_bounds__(kBlock) k_mass_guess(StepData<P> a, Consts<typename P::V> k_) {
+    using V = typename P::V;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        KrylovState* st = a.stm;
+        for (int k = 0; k < 3; ++k) {
+            st->bb[k] = st->rr[k] = st->rho[k] = 0.0;
+            st->alpha[k] = st->beta[k] = st->omega[k] = 0.0;
+            mirror_coefs(st, k);
+            st->col_done[k] = 1;
+            st->it_total[k] = 0;
+        }
+        st->in_done[0] = 1;
+        st->status = OASIS_OK;
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int dir = a.dir_index[i];
+        if (dir >= 0) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const size_t o = (size_t)i * D + k;
+                a.mx[o] = s_v(s_sub(a.g[(size_t)dir * D + k], s_add(a.u1[o], a.du[o])));
+                a.mq[o] = V(0);
+            }
+            continue;
+        }
+        V gp[D] = {};
+        for (int32_t e = a.rp[i]; e < a.rp[i + 1]; ++e) {
+            const V ph = a.xv[a.col[e]];
+#pragma unroll
+            for (int k = 0; k < D; ++k) gp[k] += a.G[(size_t)k * a.nnz + e] * ph;
+        }
+        const V iml = a.invML[i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const size_t o = (size_t)i * D + k;
+            const V b = -k_.dt * gp[k];
+            a.mq[o] = b;
+            a.mx[o] = b * iml;
+        }
+    }
+}
+
+// Interior rows: b = -dt dP^k phi - sum over Dirichlet columns of M_ij delta_j
+// (the right-hand side of the interior system), r = b - M delta_0 over the
+// interior columns; Dirichlet rows r = 0.  z = r / ML.  <r, z>, <r, r> and
+// <b, b> per component, the stopping test ||r|| <= tol ||b||, beta = 0.  p and
+// q are written by the first iteration (beta = 0 there).
+template <class P, int D>
+__global__ void __launch_bounds__(kBlock) k_mass_residual(StepData<P> a, Ctl ctl) {
+    using V = typename P::V;
+    V part[3 * D] = {};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        V r[D] = {};
+        if (a.dir_index[i] < 0) {
+            V b[D], mi[D] = {};
+#pragma unroll
+            for (int k = 0; k < D; ++k) b[k] = a.mq[(size_t)i * D + k];
+            for (int32_t e = a.rp[i]; e < a.rp[i + 1]; ++e) {
+                const int32_t j = a.col[e];
+                const V mv = a.M[e];
+                const size_t oj = (size_t)j * D;
+                if (a.dir_index[j] >= 0) {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) b[k] -= mv * a.mx[oj + k];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) mi[k] += mv * a.mx[oj + k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                r[k] = b[k] - mi[k];
+                part[2 * D + k] += b[k] * b[k];
+            }
+        }
+        const V iml = a.invML[i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const size_t o = (size_t)i * D + k;
+            const V z = r[k] * iml;
+            a.mr[o] = r[k];
+            a.mz[o] = z;
+            part[k] += r[k] * z;
+            part[D + k] += r[k] * r[k];
+        }
+    }
+    double tot[3 * D];
+    if (grid_sum_lite<3 * D, V>(part, tot, a.partial, &a.stm->ticket) && threadIdx.x == 0) {
+        KrylovState* st = a.stm;
+        bool live = false;
+        for (int k = 0; k < D; ++k) {
+            st->rho[k] = tot[k];
+            st->rr[k] = tot[D + k];
+            st->bb[k] = tot[2 * D + k];
+            st->beta[k] = 0.0;
+            mirror_coefs(st, k);
+            if (!isfinite(tot[k]) || !isfinite(tot[D + k]) || !isfinite(tot[2 * D + k])) st->status = OASIS_ENAN;
+            const bool done = !(tot[D + k] > ctl.rtol2 * tot[2 * D + k]);
+            st->col_done[k] = done ? 1 : 0;
+            live |= !done;
+        }
+        if (st->status != OASIS_OK) live = false;
+        st->in_done[0] = live ? 0 : 1;
+        set_cond(ctl.use_cond, ctl.h_inner, live ? 1 : 0);
+    }
+}
+
+// q = M z + beta q, p = z + beta p (interior rows; beta = 0 also clears what
+// the start left there), alpha = <r, z> / <p, q> per live component.  Row
+// tiles: the tile's entries M_ij z_j are formed with coalesced loads of M and
+// the columns (8 in flight per thread), staged in shared memory and summed per
+// row in entry order.
+template <class P, int D>
+__global__ void __launch_bounds__(kBlock) k_mass_spmv(StepData<P> a, Ctl ctl) {
+    using V = typename P::V;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    V* s_prod = reinterpret_cast<V*>(dsm);                     // [tile_cap][D]
+    __shared__ int32_t s_rp[kTile + 1];
+    const KrylovState* sc = a.stm;
+    if (sc->in_done[0]) return;
+    bool live[D];
+    V beta[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        live[k] = !sc->col_done[k];
+        beta[k] = coef<P>(sc->beta[k], sc->beta_f[k]);
+    }
+    V part[D] = {};
+    const int r = threadIdx.x;
+    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
+        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
+        tile_entries<8, Vec<V, D>>(
+            T,
+            [&](int32_t e) {
+                const V mv = a.M[e];
+                const size_t oj = (size_t)a.col[e] * D;
+                Vec<V, D> it;
+#pragma unroll
+                for (int k = 0; k < D; ++k) it.v[k] = mv * a.mz[oj + k];
+                return it;
+            },
+            [&](int32_t e, const Vec<V, D>& it) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) s_prod[(size_t)(e - T.e0) * D + k] = it.v[k];
+            });
+        __syncthreads();
+        if (r < T.nr) {
+            const int64_t i = T.r0 + r;
+            const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
+            const bool dir = a.dir_index[i] >= 0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const size_t o = (size_t)i * D + k;
+                if (dir) {
+                    a.mp[o] = V(0);
+                    a.mq[o] = V(0);
+                    continue;
+                }
+                if (!live[k]) continue;
+                V w = 0;
+                for (int32_t q = b0; q < b1; ++q) w += s_prod[(size_t)q * D + k];
+                const V p = beta[k] == V(0) ? a.mz[o] : a.mz[o] + beta[k] * a.mp[o];
+                const V qv = beta[k] == V(0) ? w : w + beta[k] * a.mq[o];
+                a.mp[o] = p;
+                a.mq[o] = qv;
+                part[k] += p * qv;
+            }
+        }
+        __syncthreads();
+    }
+    double tot[D];
+    if (grid_sum_lite<D, V>(part, tot, a.partial, &a.stm->ticket) && threadIdx.x == 0) {
+        KrylovState* st = a.stm;
+        for (int k = 0; k < D; ++k) {
+            if (st->col_done[k]) continue;
+            if (tot[k] > 0.0 && isfinite(tot[k])) {
+                st->alpha[k] = st->rho[k] / tot[k];
+            } else {
+                // <p, q> = 0 with r != 0 cannot happen for SPD M: a breakdown
+                st->alpha[k] = 0.0;
+                st->col_done[k] = 1;
+                st->status = isfinite(tot[k]) ? OASIS_EBREAKDOWN : OASIS_ENAN;
+            }
+            mirror_coefs(st, k);
+        }
+    }
+}
+
+// delta += alpha p, r -= alpha q, z = r / ML; <r, z>, <r, r>; beta = <r, z>_new /
+// <r, z>_old, the stopping test per component and of the loop.
+template <class P, int D>
+__global__ void __launch_bounds__(kBlock) k_mass_update(StepData<P> a, Ctl ctl) {
+    using V = typename P::V;
+    const KrylovState* sc = a.stm;
+    if (sc->in_done[0]) return;
+    bool live[D];
+    V alpha[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        live[k] = !sc->col_done[k];
+        alpha[k] = coef<P>(sc->alpha[k], sc->alpha_f[k]);
+    }
+    V part[2 * D] = {};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const V iml = a.invML[i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (!live[k]) continue;
+            const size_t o = (size_t)i * D + k;
+            a.mx[o] += alpha[k] * a.mp[o];
+            const V r = a.mr[o] - alpha[k] * a.mq[o];
+            const V z = r * iml;
+            a.mr[o] = r;
+            a.mz[o] = z;
+            part[k] += r * z;
+            part[D + k] += r * r;
+        }
+    }
+    double tot[2 * D];
+    if (grid_sum_lite<2 * D, V>(part, tot, a.partial, &a.stm->ticket) && threadIdx.x == 0) {
+        KrylovState* st = a.stm;
+        const int it = ++st->it_total[0];
+        bool any = false;
+        for (int k = 0; k < D; ++k) {
+            if (st->col_done[k]) continue;
+            const double rz = tot[k], rr = tot[D + k];
+            st->rr[k] = rr;
+            if (!isfinite(rz) || !isfinite(rr)) {
+                st->status = OASIS_ENAN;
+                st->col_done[k] = 1;
+                continue;
+            }
+            if (!(rr > ctl.rtol2 * st->bb[k])) {
+                st->col_done[k] = 1;
+                continue;
+            }
+            st->beta[k] = st->rho[k] > 0.0 ? rz / st->rho[k] : 0.0;
+            st->rho[k] = rz;
+            mirror_coefs(st, k);
+            any = true;
+        }
+        if (any && it >= ctl.max_it) {
+            st->status = OASIS_ENOTCONV;
+            any = false;
+        }
+        if (!any) {
+            st->in_done[0] = 1;
+            set_cond(ctl.use_cond, ctl.h_inner, 0);
+        }
+    }
+}
+
 // ================================================================ update
 // u_k^n = u_k^I - dt (dP^k phi)_i / ML_i (Sec. 5, lumping), Dirichlet rows = g;
 // p = p* + phi normalised to zero mean; rotation u^{n-2} <- u^{n-1} <- u^n,
 // p* <- p, and the history of normalised corrections.
-template <class P, int D>
+// CONS: u_k^n = u_k^I + delta_k, delta from the consistent-mass solve above.
+template <class P, int D, bool CONS>
 __global__ void __launch_bounds__(kBlock) k_update(StepData<P> a, Consts<typename P::V> k_) {
     using V = typename P::V;
     using S = typename P::S;
@@ -1340,7 +1609,7 @@ __global__ void __launch_bounds__(kBlock) k_update(StepData<P> a, Consts<typenam
     const int r = threadIdx.x;
     for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
         const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
-        tile_entries<8, Vec<V, D>>(
+        if constexpr (!CONS) tile_entries<8, Vec<V, D>>(
             T,
             [&](int32_t e) {
                 const V ph = a.xv[a.col[e]];
@@ -1361,11 +1630,16 @@ __global__ void __launch_bounds__(kBlock) k_update(StepData<P> a, Consts<typenam
             const V iml = a.invML[i];
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                V gp = 0;
-                for (int32_t q = b0; q < b1; ++q) gp += s_prod[(size_t)q * D + k];
                 const size_t o = (size_t)i * D + k;
                 const S u1 = a.u1[o];
-                S un = s_sub(s_add(u1, a.du[o]), s_from(k_.dt * gp * iml));
+                S un;
+                if constexpr (CONS) {
+                    un = s_addv(s_add(u1, a.du[o]), a.mx[o]);
+                } else {
+                    V gp = 0;
+                    for (int32_t q = b0; q < b1; ++q) gp += s_prod[(size_t)q * D + k];
+                    un = s_sub(s_add(u1, a.du[o]), s_from(k_.dt * gp * iml));
+                }
                 if (dir >= 0) un = a.g[(size_t)dir * D + k];
                 a.u2[o] = u1;
                 a.u1[o] = un;
@@ -1448,7 +1722,7 @@ struct StepImplT final : StepImpl {
     int64_t tiles = 0;
     size_t sm_asm = 0, sm_asm2 = 0, sm_out_u = 0, sm_out_u1 = 0, sm_spmm = 0, sm_spmm1 = 0, sm_outp = 0, sm_v1 = 0, sm_vd = 0;
     int g_asm = 1, g_asm2 = 1, g_out_u = 1, g_out_u1 = 1, g_spmm0 = 1, g_spmm1 = 1, g_spmm0_1 = 1, g_spmm1_1 = 1,
-        g_rhs = 1, g_upd = 1;
+        g_rhs = 1, g_upd = 1, g_upd_c = 1, g_mspmv = 1;
     int ge_n = 1, ge_nd = 1, ge_c = 1;
     int g_sell = 1;
     int iter_v = 0;                                   // chosen CG iteration shape
@@ -1511,6 +1785,9 @@ struct StepImplT final : StepImpl {
         a.gy = Sv.gy.p;
         a.stu = Sv.st.p;
         a.stp = Sv.st.p + 1;
+        a.stm = Sv.st.p + 2;
+        V** mv[5] = {&a.mx, &a.mr, &a.mz, &a.mp, &a.mq};
+        for (int q = 0; q < 5; ++q) *mv[q] = Sv.mw[q].as<V>();
         a.partial = Sv.partial.p;
         for (int k = 0; k < 3; ++k) a.f[k] = Sv.prm.f[k];
         a.dt = Sv.prm.dt;
@@ -1555,7 +1832,9 @@ struct StepImplT final : StepImpl {
         g_spmm1_1 = tile_grid(k_bicg_spmm<P, D, 1, 1>, sm_spmm1, tiles);
         g_sell = (int)std::max<int64_t>(1, ((m.n + 31) / 32 + kBlock / 32 - 1) / (kBlock / 32));
         g_rhs = tile_grid(k_pressure_rhs<P, D>, sm_outp, tiles);
-        g_upd = tile_grid(k_update<P, D>, sm_vd, tiles);
+        g_upd = tile_grid(k_update<P, D, false>, sm_vd, tiles);
+        g_upd_c = tile_grid(k_update<P, D, true>, 0, tiles);
+        g_mspmv = tile_grid(k_mass_spmv<P, D>, sm_vd, tiles);
         ge_n = elem_grid(m.n);
         ge_nd = elem_grid(m.n * D);
         ge_c = elem_grid(m.nc);
@@ -1723,9 +2002,44 @@ struct StepImplT final : StepImpl {
             0, 1);
     }
 
-    void update(cudaStream_t s) override {
+    Ctl ctl_m(const Loop& lp) const {
+        Ctl c{};
+        const double tol = P::mixed ? std::max(Sv.prm.rtol_u, 1e-6) : Sv.prm.rtol_u;
+        c.rtol2 = tol * tol;
+        c.max_it = Sv.prm.max_it_u;
+        c.use_cond = lp.graph;
+        c.h_outer = lp.h_outer;
+        c.h_inner = lp.h_inner;
+        return c;
+    }
+
+    void update(cudaStream_t s, bool graph) override {
+        if (Sv.prm.velocity_update == OASIS_UPDATE_CONSISTENT) {
+            Sv.run_single(
+                s, graph, 2,
+                [&](cudaStream_t ss, const Loop& lp) {
+                    const int pm = Sv.prof_begin(ss, OASIS_PROF_MASS);
+                    k_mass_guess<P, D><<<ge_n, kBlock, 0, ss>>>(a, k_);
+                    k_mass_residual<P, D><<<ge_n, kBlock, 0, ss>>>(a, ctl_m(lp));
+                    Sv.prof_end(ss, pm);
+                    OASIS_CUDA(cudaGetLastError());
+                },
+                [&](cudaStream_t ss, const Loop& lp) {
+                    const Ctl c = ctl_m(lp);
+                    const int pm = Sv.prof_begin(ss, OASIS_PROF_MASS);
+                    k_mass_spmv<P, D><<<g_mspmv, kBlock, sm_vd, ss>>>(a, c);
+                    k_mass_update<P, D><<<ge_n, kBlock, 0, ss>>>(a, c);
+                    Sv.prof_end(ss, pm);
+                    OASIS_CUDA(cudaGetLastError());
+                });
+            const int pu = Sv.prof_begin(s, OASIS_PROF_UPDATE);
+            k_update<P, D, true><<<g_upd_c, kBlock, 0, s>>>(a, k_);
+            Sv.prof_end(s, pu);
+            OASIS_CUDA(cudaGetLastError());
+            return;
+        }
         const int pu = Sv.prof_begin(s, OASIS_PROF_UPDATE);
-        k_update<P, D><<<g_upd, kBlock, sm_vd, s>>>(a, k_);
+        k_update<P, D, false><<<g_upd, kBlock, sm_vd, s>>>(a, k_);
         Sv.prof_end(s, pu);
         OASIS_CUDA(cudaGetLastError());
     }

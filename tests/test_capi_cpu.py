@@ -44,6 +44,14 @@ def test_header_constants_match_binding(capi):
         assert getattr(capi, k) == int(defs[k]), k
     assert ctypes.sizeof(capi.oasis_tuning) == 4 * 2 + 6 * 4 * 16 + 8 * 16
     assert ctypes.sizeof(capi.oasis_amg_info) == 8 + 2 * 8 * 16 + 8
+    # C layouts written out by hand: 5 doubles + f[3], 3 int32 (+4 padding), a
+    # double, 8 int32; stats: 8 int32, 7 doubles, res_m[3], it_m (+4 padding)
+    assert ctypes.sizeof(capi.oasis_params) == 8 * 7 + 4 * 3 + 4 + 8 + 4 * 8
+    assert ctypes.sizeof(capi.oasis_step_stats) == 4 * 8 + 8 * 7 + 8 * 3 + 4 + 4
+    # kernel families of oasis_profile_read
+    for name, v in capi.PROF_FAMILIES.items():
+        assert int(defs["OASIS_PROF_" + name.upper()]) == v, name
+    assert len(capi.PROF_FAMILIES) == len([k for k in defs if k.startswith("OASIS_PROF_")])
 
 
 def test_version_and_error_string(capi):
@@ -84,3 +92,31 @@ def test_bad_dim_is_einval(capi):
 def test_graft_entry_build():
     import __graft_entry__ as g
     g.build()
+
+
+def test_struct_layouts_match_c_compiler(tmp_path, capi):
+    """Field offsets of the ctypes mirrors equal what a C compiler makes of the header."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"oasis_params": capi.oasis_params, "oasis_step_stats": capi.oasis_step_stats,
+               "oasis_tuning": capi.oasis_tuning, "oasis_amg_info": capi.oasis_amg_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "oasis.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{name}.{f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for f in cls._fields_:
+            assert int(out[f"{name}.{f[0]}"]) == getattr(cls, f[0]).offset, (name, f[0])

@@ -317,6 +317,95 @@ def test_inner_iterations_mixed_per_field():
     assert relerr(p, s.p) <= 1e-6
 
 
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_consistent_update_matches_oracle_fp64(name, use_graph):
+    """Consistent-mass velocity update (Sec. 5): M u^n = M u^I - dt dP^k phi with
+    Dirichlet rows u^n = g, against the oracle's direct solve; the lumped oracle
+    is farther away than the tolerance, so the comparison tells the two apart."""
+    from paper_1602_03643_gb300.driver import IPCSRun
+    c = capi()
+    pb = _perturbed_state(PROBLEMS[name]())
+    run = IPCSRun(pb, rtol_u=1e-13, rtol_p=1e-13, use_graph=use_graph, guess=1,
+                  velocity_update=c.OASIS_UPDATE_CONSISTENT)
+    o = IPCS(pb, velocity_update="consistent")
+    ol = IPCS(pb)
+    s, sl = o.initial_state(), ol.initial_state()
+    try:
+        for it in range(3):
+            st = run.step()
+            assert st.status == 0
+            assert st.it_m > 0
+            assert max(st.res_m[:pb.mesh.dim]) <= 1e-13
+            s, sl = o.step(s), ol.step(sl)
+            u, p, phi = run.fields()
+            assert relerr(u, s.u_nm1) < 1e-10, it
+            assert relerr(p, s.p) < 1e-10, it
+            assert relerr(sl.u_nm1, s.u_nm1) > 1e-8, it
+    finally:
+        run.close()
+
+
+@pytest.mark.parametrize("pc", [0, 1])
+def test_consistent_update_with_inner_iterations_and_explicit_convection(pc):
+    """All three options at once: explicit convection (Eq. 21), 2 inner
+    iterations (Algorithm 1), consistent-mass update, graph mode."""
+    from paper_1602_03643_gb300.driver import IPCSRun
+    c = capi()
+    pb = _perturbed_state(PROBLEMS["channel_6x6x4"]())
+    run = IPCSRun(pb, rtol_u=1e-13, rtol_p=1e-13, use_graph=1, guess=1, pressure_pc=pc, inner_iters=2,
+                  convection=1, velocity_update=c.OASIS_UPDATE_CONSISTENT)
+    o = IPCS(pb, inner_iters=2, convection="abe", velocity_update="consistent")
+    s = o.initial_state()
+    try:
+        for it in range(3):
+            assert run.step().status == 0
+            s = o.step(s)
+            u, p, _ = run.fields()
+            assert relerr(u, s.u_nm1) < 1e-10, it
+            assert relerr(p, s.p) < 1e-10, it
+    finally:
+        run.close()
+
+
+def test_consistent_update_mixed_per_field():
+    from paper_1602_03643_gb300.driver import IPCSRun
+    c = capi()
+    pb = WP.taylor_green_3d(10)
+    run = IPCSRun(pb, precision=1, rtol_u=1e-8, rtol_p=1e-8, use_graph=1, pressure_pc=1, guess=1,
+                  velocity_update=c.OASIS_UPDATE_CONSISTENT)
+    try:
+        for _ in range(10):
+            st = run.step()
+            assert st.status == 0 and st.it_m > 0
+            assert max(st.res_m) <= 1e-6
+        u, p, _ = run.fields()
+    finally:
+        run.close()
+    s = IPCS(pb, velocity_update="consistent").run(10)
+    for k in range(3):
+        if np.abs(s.u_nm1[k]).max() > 0:
+            assert relerr(u[k], s.u_nm1[k]) <= 1e-6, k
+    assert relerr(p, s.p) <= 1e-6
+
+
+def test_consistent_update_graph_equals_eager_bitwise():
+    from paper_1602_03643_gb300.driver import IPCSRun
+    c = capi()
+    out = []
+    for g in (0, 1):
+        pb = WP.taylor_green_3d(6)
+        run = IPCSRun(pb, precision=1, rtol_u=1e-8, rtol_p=1e-8, use_graph=g,
+                      velocity_update=c.OASIS_UPDATE_CONSISTENT)
+        try:
+            run.step(4)
+            out.append(run.fields())
+        finally:
+            run.close()
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
+
+
 @pytest.mark.parametrize("precision,case", [(0, "stress"), (1, "stress"), (1, "channel")])
 def test_cg_shapes_bitwise_equal_and_tuned(precision, case):
     """Every candidate shape of the CG iteration kernel (including 16-bit column
