@@ -32,6 +32,16 @@ update above; `"consistent"` solves the update with the mass matrix,
   M u_k^n = M u_k^I - dt G^k phi,   rows in the Dirichlet set: u_k^n = g_k,
 by a sparse LU solve.
 
+Passive scalars (the scalar equation of Sec. 3, solved after the velocity
+update in Algorithm 1), when the problem carries them: for each scalar alpha
+with diffusivity D_a and constant source f_a, convected by the same
+ubar = 1.5 u^{n-1} - 0.5 u^{n-2} (B_a = ubar . grad c~, c~ = (c^n + c^{n-1}) / 2),
+  A_a = M/dt + C(ubar)/2 + D_a K/2
+  b_a = (M/dt - C(ubar)/2 - D_a K/2) c_a^{n-1} + f_a ML
+  rows i in the scalars' Dirichlet set: A_a,i. = e_i, b_a,i = g_a(x_i, t^n)
+  (the values are re-imposed after the solve, as for the velocity)
+whichever form the velocity's convection takes.
+
 Inner iterations (Algorithm 1): the tentative and pressure solves are repeated
 `inner_iters` times within a step, each time with p* = the newest pressure (the
 matrix A, which holds only old velocities, is unchanged); phi is the increment
@@ -68,6 +78,7 @@ class State:
     u_nm2: np.ndarray      # [d, N]
     p: np.ndarray          # [N]  (p* of the next step)
     t: float
+    c: np.ndarray | None = None   # [ns, N] passive scalars, if the problem has any
 
 
 def replace_rows(A: sp.csr_matrix, rows: np.ndarray) -> sp.csr_matrix:
@@ -127,6 +138,21 @@ class IPCS:
             b = np.stack([E @ u_nm1[k] + self.b0[k] - D.G[k] @ p_star for k in range(D.d)])
         A = replace_rows(A, self.dirichlet)
         b[:, self.dirichlet] = pb.g(t_new)
+        return A, b
+
+    def scalar_system(self, u_nm1, u_nm2, c_nm1, alpha, t_new):
+        """A_a, b_a of scalar ``alpha`` (Sec. 3, the scalar equation)."""
+        D, pb = self.disc, self.pb
+        sc = pb.scalars
+        C = D.convection(1.5 * u_nm1 - 0.5 * u_nm2)
+        Da = float(sc.diffusivity[alpha])
+        A = D.M / pb.dt + 0.5 * C + 0.5 * Da * D.K
+        E = D.M / pb.dt - 0.5 * C - 0.5 * Da * D.K
+        b = E @ c_nm1 + float(sc.source[alpha]) * D.ML
+        rows = np.asarray(sc.dirichlet, dtype=np.int64)
+        A = replace_rows(A, rows)
+        if len(rows):
+            b[rows] = sc.g(t_new)[alpha]
         return A, b
 
     def pressure_rhs(self, u_I, p_star):
@@ -189,14 +215,24 @@ class IPCS:
         else:
             u_n = np.stack([u_I[k] - pb.dt * (D.G[k] @ phi) / D.ML for k in range(D.d)])
         u_n[:, self.dirichlet] = pb.g(t_new)
-        out = State(u_n, s.u_nm1, p, t_new)
+        c_n = None
+        if s.c is not None:
+            c_n = np.empty_like(s.c)
+            for a in range(s.c.shape[0]):
+                Aa, ba = self.scalar_system(s.u_nm1, s.u_nm2, s.c[a], a, t_new)
+                c_n[a] = self.solve_tentative(Aa, ba[None, :], s.c[a][None, :])[0]
+            rows = np.asarray(pb.scalars.dirichlet, dtype=np.int64)
+            if len(rows):
+                c_n[:, rows] = pb.scalars.g(t_new)
+        out = State(u_n, s.u_nm1, p, t_new, c_n)
         out.u_I, out.phi, out.bp = u_I, phi, bp
         out.increments = increments
         return out
 
     def initial_state(self) -> State:
         pb = self.pb
-        return State(pb.u_nm1.copy(), pb.u_nm2.copy(), pb.p.copy(), pb.t0)
+        c = None if getattr(pb, "scalars", None) is None else pb.scalars.c0.copy()
+        return State(pb.u_nm1.copy(), pb.u_nm2.copy(), pb.p.copy(), pb.t0, c)
 
     def run(self, n_steps: int, state: State | None = None) -> State:
         s = state if state is not None else self.initial_state()

@@ -349,3 +349,107 @@ def test_inner_iterations_reduce_increment_and_divergence():
     assert divs[-1] < 0.6 * divs[0]
     # one inner iteration is the plain step
     np.testing.assert_allclose(IPCS(pb, inner_iters=1).step(o1.initial_state()).u_nm1, s1.u_nm1, rtol=0, atol=0)
+
+
+# ----------------------------------------------------------------- passive scalars
+def dense_scalar_step(pb, state):
+    """c^n of every scalar by quadrature element integrals and dense algebra (the
+    scalar equation of Sec. 3: Crank-Nicolson c~, convecting ubar)."""
+    m, sc = pb.mesh, pb.scalars
+    N = m.n_dofs
+    Md, Kd, Cd = np.zeros((N, N)), np.zeros((N, N)), np.zeros((N, N))
+    ubar = 1.5 * state.u_nm1 - 0.5 * state.u_nm2
+    for c in m.cells:
+        dofs = m.dof_of_vertex[c]
+        Me, Ke, _, Ce = quad_element(m.coords[c], ubar[:, dofs].T)
+        ix = np.ix_(dofs, dofs)
+        np.add.at(Md, ix, Me)
+        np.add.at(Kd, ix, Ke)
+        np.add.at(Cd, ix, Ce)
+    ML = Md.sum(axis=1)
+    out = np.empty_like(state.c)
+    rows = np.asarray(sc.dirichlet, dtype=np.int64)
+    for a in range(state.c.shape[0]):
+        Da = sc.diffusivity[a]
+        A = Md / pb.dt + Cd / 2 + Da * Kd / 2
+        b = (Md / pb.dt - Cd / 2 - Da * Kd / 2) @ state.c[a] + sc.source[a] * ML
+        A[rows, :] = 0.0
+        A[rows, rows] = 1.0
+        if len(rows):
+            b[rows] = sc.g(state.t + pb.dt)[a]
+        out[a] = np.linalg.solve(A, b)
+    return out
+
+
+@pytest.mark.parametrize("form", ["abcn", "abe"])
+@pytest.mark.parametrize("kind", ["tg2d", "tg3d", "channel"])
+def test_oracle_scalars_match_dense_brute_force(kind, form):
+    """Scalars use ubar = 1.5 u^{n-1} - 0.5 u^{n-2} under either velocity form;
+    channel scalars have their own Dirichlet walls, the others share the
+    velocity's set."""
+    if kind == "tg2d":
+        pb = WP.taylor_green_2d(3)
+    elif kind == "tg3d":
+        pb = WP.taylor_green_3d(3)
+    else:
+        pb = WP.channel(nx=3, ny=4, nz=2, perturb=0.1)
+    WP.with_scalars(pb, ns=2)
+    o = IPCS(pb, convection=form)
+    s = o.initial_state()
+    rng = np.random.default_rng(9)
+    s.u_nm2 = s.u_nm2 + 0.05 * rng.normal(size=s.u_nm2.shape)
+    s.u_nm2[:, pb.dirichlet] = s.u_nm1[:, pb.dirichlet]
+    for _ in range(2):
+        want = dense_scalar_step(pb, s)
+        s = o.step(s)
+        np.testing.assert_allclose(s.c, want, rtol=0, atol=1e-12 * np.abs(want).max())
+    np.testing.assert_allclose(s.c[:, pb.scalars.dirichlet], pb.scalars.g(s.t), rtol=0, atol=1e-14)
+
+
+def test_scalar_uniform_advection_second_order():
+    """Exact solution of advection-diffusion by a uniform flow (periodic): the
+    error falls at second order as h and dt are halved together."""
+    errs, hs = [], []
+    for n in (8, 16, 32):
+        pb = WP.uniform_advection_2d(n=n, dt=0.04 * 8 / n)
+        o = IPCS(pb)
+        steps = int(round(0.2 / pb.dt))
+        s = o.run(steps)
+        assert abs(s.t - 0.2) < 1e-12
+        # the flow itself stays uniform and the pressure zero
+        np.testing.assert_allclose(s.u_nm1, pb.u_nm1, rtol=0, atol=1e-12)
+        err = s.c[0] - pb.scalars.exact(pb.mesh.dof_coords(), s.t)[0]
+        errs.append(float(np.sqrt(np.mean(err ** 2))))
+        hs.append(1.0 / n)
+    orders = [convergence_order(errs[i - 1], errs[i], hs[i - 1], hs[i]) for i in (1, 2)]
+    assert min(orders) > 1.8, (errs, orders)
+    assert errs[-1] < 2e-3
+
+
+def test_scalar_pure_diffusion_eigenmode():
+    """u = 0: a generalised eigenvector K v = lam M v is multiplied per step by the
+    Crank-Nicolson factor (1 - dt D lam / 2) / (1 + dt D lam / 2)."""
+    import scipy.linalg as sla
+    pb = WP.uniform_advection_2d(n=6, U=(0.0, 0.0), D=0.05, dt=0.1)
+    D = p1.Discretization(pb.mesh)
+    lam, V = sla.eigh(D.K.toarray(), D.M.toarray())
+    j = 7
+    pb.scalars.c0 = V[:, j][None, :].copy()
+    o = IPCS(pb)
+    s = o.run(4)
+    g = (1 - 0.5 * pb.dt * 0.05 * lam[j]) / (1 + 0.5 * pb.dt * 0.05 * lam[j])
+    np.testing.assert_allclose(s.c[0], g ** 4 * V[:, j], rtol=0, atol=1e-12 * np.abs(V[:, j]).max())
+    assert 0 < g < 1
+
+
+def test_scalar_source_and_constants():
+    """A constant source adds dt f_a per step to a constant field (int f phi_i =
+    f ML_i, M 1 = ML), and a constant is kept by any flow (C 1 = K 1 = 0)."""
+    pb = WP.taylor_green_2d_periodic(6, dt=0.05)
+    WP.with_scalars(pb, ns=2, diffusivity=(0.0, 0.3), source=(0.7, 0.0))
+    pb.scalars.c0[0] = 0.0
+    pb.scalars.c0[1] = 2.5
+    o = IPCS(pb)
+    s = o.run(3)
+    np.testing.assert_allclose(s.c[0], 3 * 0.05 * 0.7, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(s.c[1], 2.5, rtol=0, atol=1e-13)

@@ -25,6 +25,19 @@ from . import meshes as M
 
 
 @dataclass
+class Scalars:
+    """Passive scalars c_alpha (the scalar equation of Sec. 3): initial values,
+    diffusivities D_alpha, constant sources f_alpha, one Dirichlet dof set shared
+    by every scalar and a callable giving its values at a time t."""
+    c0: np.ndarray                      # [ns, N] float64
+    diffusivity: np.ndarray             # [ns]
+    source: np.ndarray                  # [ns] constant f_alpha
+    dirichlet: np.ndarray               # [n_sdir] int32 dofs
+    g: Callable[[float], np.ndarray]    # t -> [ns, n_sdir]
+    exact: Callable | None = None       # (x [N,d], t) -> [ns, N]
+
+
+@dataclass
 class Problem:
     name: str
     mesh: M.Mesh
@@ -41,6 +54,7 @@ class Problem:
     rtol: float
     exact_u: Callable | None = None     # (x [N,d], t) -> [d, N]
     exact_p: Callable | None = None     # (x [N,d], t) -> [N]
+    scalars: Scalars | None = None      # passive scalars transported by the flow
 
 
 # ---------------------------------------------------------------- 2D Taylor-Green
@@ -168,6 +182,56 @@ def stress_cube(n: int = 128, nu: float = 1e-3, dt: float = 1e-3, n_steps: int =
     X = 2 * np.pi * mesh.dof_coords() - np.pi
     return _held_problem(f"stress_{n}_{ordering}", mesh, nu, dt, np.zeros(3), tg3d_u(X),
                          tg3d_p(X), n_steps, rtol, mesh.boundary_dofs["all"])
+
+
+# ---------------------------------------------------------------- scalars
+def with_scalars(pb: Problem, ns: int = 2, diffusivity=(1e-3, 2e-2), source=(0.0, 0.5),
+                 seed: int = 7) -> Problem:
+    """Attach ``ns`` seeded scalars to a problem: a smooth field (a product of
+    cosines in the box's own coordinates) plus 5 % seeded noise; Dirichlet set:
+    the walls of a channel (c = (1 + y) / 2 there), else the velocity's Dirichlet
+    set with the initial values held."""
+    x = pb.mesh.dof_coords()
+    lo, hi = x.min(axis=0), x.max(axis=0)
+    xi = (x - lo) / np.maximum(hi - lo, 1e-300)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c0 = np.empty((ns, pb.mesh.n_dofs))
+    for a in range(ns):
+        c0[a] = np.prod(np.cos(np.pi * (a + 1) * xi), axis=1) + 0.05 * rng.uniform(-1.0, 1.0, pb.mesh.n_dofs)
+    walls = pb.mesh.boundary_dofs.get("walls_y") if pb.mesh.boundary_dofs else None
+    if walls is not None and pb.name.startswith("channel"):
+        sd = np.asarray(walls, dtype=np.int32)
+        c0[:, sd] = 0.5 * (1.0 + x[sd, 1])[None, :]
+    else:
+        sd = np.asarray(pb.dirichlet, dtype=np.int32)
+    held = c0[:, sd].copy()
+    dif = np.resize(np.asarray(diffusivity, dtype=np.float64), ns)
+    src = np.resize(np.asarray(source, dtype=np.float64), ns)
+    pb.scalars = Scalars(c0=c0, diffusivity=dif, source=src, dirichlet=sd, g=lambda t: held)
+    return pb
+
+
+def uniform_advection_2d(n: int = 16, U=(1.0, 0.5), nu: float = 0.01, D: float = 0.01,
+                         dt: float = 1e-2, n_steps: int = 50) -> Problem:
+    """Doubly periodic unit square with the uniform flow u = U, p = 0 (an exact
+    Navier-Stokes solution) carrying one scalar with the exact solution
+    c = exp(-8 pi^2 D t) sin(2 pi (x - U_x t)) sin(2 pi (y - U_y t))."""
+    mesh = M.box_mesh_2d(n, n, 0.0, 1.0, 0.0, 1.0, periodic=True)
+    x = mesh.dof_coords()
+    N = mesh.n_dofs
+    u0 = np.tile(np.asarray(U, dtype=np.float64)[:, None], (1, N))
+    empty = np.zeros(0, dtype=np.int32)
+
+    def exact(xx, t):
+        e = np.exp(-8.0 * np.pi ** 2 * D * t)
+        return (e * np.sin(2 * np.pi * (xx[:, 0] - U[0] * t)) * np.sin(2 * np.pi * (xx[:, 1] - U[1] * t)))[None, :]
+
+    pb = Problem(name=f"advection_2d_{n}", mesh=mesh, nu=nu, dt=dt, f=np.zeros(2), dirichlet=empty,
+                 u_nm1=u0.copy(), u_nm2=u0.copy(), p=np.zeros(N), t0=0.0, g=lambda t: np.zeros((2, 0)),
+                 n_steps=n_steps, rtol=1e-12)
+    pb.scalars = Scalars(c0=exact(x, 0.0), diffusivity=np.array([D]), source=np.zeros(1),
+                         dirichlet=empty, g=lambda t: np.zeros((1, 0)), exact=exact)
+    return pb
 
 
 def by_name(name: str, **kw) -> Problem:
