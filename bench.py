@@ -31,7 +31,15 @@ METRIC = "IPCS steps/s at matched residual, mixed+learned vs FP64; SpMV HBM GB/s
 RTOL = 1e-8
 
 
-def workload(name):
+def workload(name, scalars=0):
+    pb = _workload(name)
+    if scalars:
+        from workloads import problems as WP
+        WP.with_scalars(pb, ns=scalars)
+    return pb
+
+
+def _workload(name):
     from workloads import problems as WP
     if name == "tg3d_64":
         return WP.taylor_green_3d(64, n_steps=200, rtol=RTOL)
@@ -133,7 +141,7 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    pb = workload(args.workload)
+    pb = workload(args.workload, args.scalars)
     N = pb.mesh.n_dofs
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -344,6 +352,7 @@ def run_ours(args, rank, world):
     sw_u = float(np.mean([s["sweeps_u"] for s in stats]))
     sw_p = float(np.mean([s["sweeps_p"] for s in stats]))
     it_m = float(np.mean([s["it_m"] for s in stats]))
+    it_c = float(np.mean([s["it_c"] for s in stats]))
     # kernels per step in the graph: beta + assembly 2; velocity: per sweep a residual
     # and (all but the last) a correction, 5 per BiCGStab iteration; pressure: rhs
     # and guess 2, per sweep residual + CG start + (all but the last) correction,
@@ -355,6 +364,9 @@ def run_ours(args, rank, world):
     # (Algorithm 1; the statistics describe the last repetition): per repetition
     # after the first a pressure advance, the assembly and both solves again.
     # Consistent-mass update: start 2, 2 per CG iteration, then the update.
+    # Scalars (approximate: the statistics give the largest iteration count):
+    # assembly, two residual sweeps and a correction, 5 per BiCGStab iteration,
+    # the final update.
     if amg_info:
         vk = 4 * (amg_info["levels"] - 1) + 1
         p_kernels = sw_p * (4 + vk) + it_p * (2 + vk)
@@ -362,6 +374,7 @@ def run_ours(args, rank, world):
         p_kernels = 3 * sw_p + it_p
     ni = max(1, args.inner_iters)
     upd_kernels = 3 + 2 * it_m if args.velocity_update == "consistent" else 1
+    upd_kernels += args.scalars * (5 + 5 * it_c)
     launches = int(round(args.steps * (ni * (2 + 2 * sw_u + 5 * it_u + p_kernels) + (ni - 1)
                                        + (5 if learned else 0) + upd_kernels)))
     run.close()
@@ -376,7 +389,7 @@ def run_ours(args, rank, world):
             "parallelism": f"replicas x{world}",
             "pressure_guess": "learned (judged against previous phi)" if learned else "previous phi",
             "pressure_pc": args.pc, "inner_iters": args.inner_iters, "convection": args.convection,
-            "velocity_update": args.velocity_update},
+            "velocity_update": args.velocity_update, "scalars": args.scalars},
         "e2e": {"value": world * k_e2e / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -384,7 +397,7 @@ def run_ours(args, rank, world):
         "roofline": roofline,
         "roofline_next_kernel": roofline_other,
         "solver": {"it_u_mean": it_u, "it_p_mean": it_p, "sweeps_u_mean": sw_u, "sweeps_p_mean": sw_p,
-                   "it_mass_mean": it_m,
+                   "it_mass_mean": it_m, "it_scalar_max_mean": it_c,
                    "failed_steps": len(bad), "res_p_last": stats[-1]["res_p"]},
         "fp64_gpu": fp64,
         "mixed_prev_phi": prev_form,
@@ -438,7 +451,7 @@ def _threads():
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    pb = workload(args.workload)
+    pb = workload(args.workload, getattr(args, "scalars", 0))
     from oracle.ipcs import IPCS
     o = IPCS(pb, iterative=True, rtol=RTOL, **oracle_options(args))
     s = o.initial_state()
@@ -479,6 +492,8 @@ def main():
     ap.add_argument("--velocity-update", default="lumped", choices=["lumped", "consistent"],
                     help="velocity update of the projection: lumped mass or a CG on the consistent mass "
                          "matrix (Sec. 5)")
+    ap.add_argument("--scalars", type=int, default=0,
+                    help="passive scalars transported with the flow (Sec. 3 scalar equation)")
     ap.add_argument("--inner-iters", type=int, default=1,
                     help="inner velocity/pressure iterations per step (Algorithm 1)")
     ap.add_argument("--pc", default="amg", choices=["amg", "jacobi"],

@@ -171,6 +171,8 @@ typedef struct oasis_step_stats {
     double res_m[3];       /* OASIS_UPDATE_CONSISTENT: final recurrence ||r|| / ||dt dP^k phi||
                               of the mass solve per component; else 0 */
     int32_t it_m;          /* OASIS_UPDATE_CONSISTENT: CG iterations of the mass solve */
+    int32_t it_c;          /* passive scalars: most BiCGStab iterations over the scalars */
+    double res_c;          /* passive scalars: largest final ||r|| / ||r_0|| over the scalars */
 } oasis_step_stats;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -271,11 +273,12 @@ int oasis_set_fields(oasis_solver* s, const double* u_nm1, const double* u_nm2, 
  * at the time t^n of the next step.  Values persist until the next call. */
 int oasis_set_dirichlet(oasis_solver* s, const double* g, int32_t on_device, void* stream);
 
-/* Advance one time step (Algorithm 1, one inner iteration):
+/* Advance one time step (Algorithm 1; params.inner_iters repetitions):
  *   assemble C into A and form the tentative right-hand side (Algorithm 2),
  *   solve A u_k^I = b_k for the dim components, solve the pressure correction,
- *   normalise p, update u with the lumped mass, rotate u^{n-2} <- u^{n-1} <- u^n
- *   and p* <- p.
+ *   solve the passive scalars if any (oasis_solver_set_scalars), normalise p,
+ *   update u (params.velocity_update), rotate u^{n-2} <- u^{n-1} <- u^n and
+ *   p* <- p.
  * If stats is NULL the call only enqueues work on `stream` and returns OASIS_OK;
  * a failure of the step is reported by the next oasis_last_stats().  If stats is
  * non-NULL the call waits for the step and returns its status. */
@@ -283,6 +286,33 @@ int oasis_step(oasis_solver* s, void* stream, oasis_step_stats* stats);
 
 /* Wait for the last step and return its statistics and status. */
 int oasis_last_stats(oasis_solver* s, oasis_step_stats* stats);
+
+/* ---- Passive scalars (the scalar equation of Sec. 3) -------------------------
+ * Scalar alpha with diffusivity D_a and constant source f_a is advanced after the
+ * tentative and pressure solves of every step (Algorithm 1 solves it after the
+ * velocity correction; it uses only the old velocities, so the order is free):
+ *   A_a = M/dt + C(ubar)/2 + D_a K/2,  ubar = 1.5 u^{n-1} - 0.5 u^{n-2} (whichever
+ *   convection form the velocity uses), b_a = (M/dt - C/2 - D_a K/2) c^{n-1} + f_a ML,
+ *   rows of the scalars' Dirichlet set: unit rows, c^n = g_a(t^n) (values re-imposed
+ *   after the solve).
+ * Solved in delta form A_a (c^n - c^{n-1}) = b_a - A_a c^{n-1} by the tentative
+ * solver's BiCGStab (Jacobi, refinement in OASIS_MIXED) with rtol_u and max_it_u.
+ * C(ubar) is kept from the velocity assembly (one extra nnz array).
+ *
+ * oasis_solver_set_scalars: n_scalars in [0, OASIS_MAX_SCALARS] (0 removes them);
+ * diffusivity and source host arrays [n_scalars] (D_a >= 0); dirichlet_dofs host
+ * [n_dirichlet], distinct, in range (may differ from the velocity's set).  The
+ * fields start at 0 and the Dirichlet values at 0.  Drops a captured graph.
+ * Errors: OASIS_EINVAL (sizes, index, negative diffusivity), OASIS_ENOMEM. */
+#define OASIS_MAX_SCALARS 8
+int oasis_solver_set_scalars(oasis_solver* s, int32_t n_scalars, const double* diffusivity,
+                             const double* source, int64_t n_dirichlet, const int32_t* dirichlet_dofs);
+/* c[a * n_dofs + i] = c_a at dof i (float64; on_device as for oasis_set_fields). */
+int oasis_set_scalar_fields(oasis_solver* s, const double* c, int32_t on_device, void* stream);
+int oasis_get_scalar_fields(oasis_solver* s, double* c, int32_t on_device, void* stream);
+/* g[a * n_dirichlet + m]: value of scalar a at dirichlet_dofs[m] at the time t^n of
+ * the next step.  Values persist until the next call. */
+int oasis_set_scalar_dirichlet(oasis_solver* s, const double* g, int32_t on_device, void* stream);
 
 /* Copy out the current state: u = u^n ([dim][n_dofs]), p = p^{n-1/2} ([n_dofs]),
  * phi = p^{n-1/2} - p* ([n_dofs]); any of them may be NULL.  on_device as above.

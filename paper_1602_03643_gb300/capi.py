@@ -34,6 +34,7 @@ OASIS_CONV_ABCN = 0
 OASIS_CONV_ABE = 1
 OASIS_UPDATE_LUMPED = 0
 OASIS_UPDATE_CONSISTENT = 1
+OASIS_MAX_SCALARS = 8
 OASIS_MAT_M, OASIS_MAT_K, OASIS_MAT_G0, OASIS_MAT_G1, OASIS_MAT_G2, OASIS_MAT_A = range(6)
 
 ERROR_NAMES = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "EMESH", -4: "ENOTCONV", -5: "EBREAKDOWN",
@@ -74,13 +75,15 @@ class oasis_step_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("it_u", C.c_int32 * 3), ("sweeps_u", C.c_int32),
                 ("it_p", C.c_int32), ("sweeps_p", C.c_int32), ("guess_used", C.c_int32),
                 ("res_u", C.c_double * 3), ("res_p", C.c_double), ("t", C.c_double),
-                ("guess_res", C.c_double * 2), ("res_m", C.c_double * 3), ("it_m", C.c_int32)]
+                ("guess_res", C.c_double * 2), ("res_m", C.c_double * 3), ("it_m", C.c_int32),
+                ("it_c", C.c_int32), ("res_c", C.c_double)]
 
     def as_dict(self):
         return {"status": self.status, "it_u": list(self.it_u), "sweeps_u": self.sweeps_u,
                 "it_p": self.it_p, "sweeps_p": self.sweeps_p, "guess_used": self.guess_used,
                 "res_u": list(self.res_u), "res_p": self.res_p, "t": self.t,
-                "guess_res": list(self.guess_res), "res_m": list(self.res_m), "it_m": self.it_m}
+                "guess_res": list(self.guess_res), "res_m": list(self.res_m), "it_m": self.it_m,
+                "it_c": self.it_c, "res_c": self.res_c}
 
 
 class OasisError(RuntimeError):
@@ -116,6 +119,10 @@ SIGNATURES = {
     "oasis_step": (C.c_int, [P, P, C.POINTER(oasis_step_stats)]),
     "oasis_last_stats": (C.c_int, [P, C.POINTER(oasis_step_stats)]),
     "oasis_get_fields": (C.c_int, [P, DPTR, DPTR, DPTR, I32, P]),
+    "oasis_solver_set_scalars": (C.c_int, [P, I32, DPTR, DPTR, I64, DPTR]),
+    "oasis_set_scalar_fields": (C.c_int, [P, DPTR, I32, P]),
+    "oasis_get_scalar_fields": (C.c_int, [P, DPTR, I32, P]),
+    "oasis_set_scalar_dirichlet": (C.c_int, [P, DPTR, I32, P]),
     "oasis_get_tentative_system": (C.c_int, [P, DPTR, DPTR, P]),
     "oasis_profile": (C.c_int, [P, I32]),
     "oasis_profile_read": (C.c_int, [P, I32, C.POINTER(I64), C.POINTER(C.c_double)]),
@@ -299,6 +306,34 @@ def oasis_get_fields(solver, dim, n, on_device=False, u=None, p=None, phi=None, 
         phi = np.empty(n) if phi is None else phi
     check(lib().oasis_get_fields(solver, _ptr(u), _ptr(p), _ptr(phi), int(on_device), _stream(stream)))
     return u, p, phi
+
+
+def oasis_solver_set_scalars(solver, diffusivity, source, dirichlet_dofs):
+    dif = np.ascontiguousarray(diffusivity, dtype=np.float64).reshape(-1)
+    src = np.ascontiguousarray(source, dtype=np.float64).reshape(-1)
+    d = np.ascontiguousarray(dirichlet_dofs, dtype=np.int32).reshape(-1)
+    check(lib().oasis_solver_set_scalars(solver, int(dif.size), _ptr(dif) if dif.size else None,
+                                         _ptr(src) if src.size else None, int(d.size),
+                                         _ptr(d) if d.size else None))
+
+
+def oasis_set_scalar_fields(solver, c, on_device=False, stream=None):
+    if not on_device:
+        c = np.ascontiguousarray(c, dtype=np.float64)
+    check(lib().oasis_set_scalar_fields(solver, _ptr(c), int(on_device), _stream(stream)))
+
+
+def oasis_get_scalar_fields(solver, ns, n, on_device=False, c=None, stream=None):
+    if not on_device:
+        c = np.empty((ns, n)) if c is None else c
+    check(lib().oasis_get_scalar_fields(solver, _ptr(c), int(on_device), _stream(stream)))
+    return c
+
+
+def oasis_set_scalar_dirichlet(solver, g, on_device=False, stream=None):
+    if not on_device:
+        g = np.ascontiguousarray(g, dtype=np.float64)
+    check(lib().oasis_set_scalar_dirichlet(solver, _ptr(g), int(on_device), _stream(stream)))
 
 
 def oasis_get_tentative_system(solver, dim, n, nnz, stream=None):

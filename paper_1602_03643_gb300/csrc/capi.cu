@@ -154,7 +154,7 @@ void Solver::step(cudaStream_t s) {
         OASIS_CUDA(cudaGraphLaunch(gexec, s));
     } else {
         enqueue_step(s, false);
-        OASIS_CUDA(cudaMemcpyAsync(h_st, st.p, kStates * sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
+        OASIS_CUDA(cudaMemcpyAsync(h_st, st.p, n_states() * sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
         if (prof_on) prof_collect();
     }
     t += prm.dt;
@@ -162,7 +162,8 @@ void Solver::step(cudaStream_t s) {
 
 // One time step (Algorithm 1): assembly, then per inner repetition the
 // tentative and pressure solves (p* advanced and the tentative residual
-// re-formed between repetitions), then the velocity update (lumped, or the consistent-mass solve).
+// re-formed between repetitions), the passive scalars (they use only the old
+// velocities), then the velocity update (lumped, or the consistent-mass solve).
 void Solver::enqueue_step(cudaStream_t s, bool graph_mode) {
     const int ni = std::max(1, prm.inner_iters);
     impl->assemble(s);
@@ -174,6 +175,7 @@ void Solver::enqueue_step(cudaStream_t s, bool graph_mode) {
         impl->tentative_solve(s, graph_mode);
         impl->pressure_solve(s, graph_mode, it);
     }
+    if (ns > 0) impl->scalar_solve(s, graph_mode);
     impl->update(s, graph_mode);
 }
 
@@ -182,7 +184,7 @@ void Solver::capture() {
     OASIS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     try {
         enqueue_step(s, true);
-        OASIS_CUDA(cudaMemcpyAsync(h_st, st.p, kStates * sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
+        OASIS_CUDA(cudaMemcpyAsync(h_st, st.p, n_states() * sizeof(KrylovState), cudaMemcpyDeviceToHost, s));
     } catch (...) {
         cudaGraph_t g;
         cudaStreamEndCapture(s, &g);
@@ -281,9 +283,15 @@ static void fill_stats(const Solver& S, oasis_step_stats* o) {
     std::memset(o, 0, sizeof(*o));
     const KrylovState& u = S.h_st[0];
     const KrylovState& p = S.h_st[1];
+    for (int al = 0; al < S.ns; ++al) {
+        const KrylovState& cs = S.h_st[3 + al];
+        o->it_c = std::max(o->it_c, cs.it_total[0]);
+        o->res_c = std::max(o->res_c, cs.bb[0] > 0 ? std::sqrt(cs.rr[0] / cs.bb[0]) : 0.0);
+    }
     const KrylovState& mm = S.h_st[2];
     const bool cons = S.prm.velocity_update == OASIS_UPDATE_CONSISTENT;
     o->status = u.status != OASIS_OK ? u.status : p.status != OASIS_OK ? p.status : cons ? mm.status : OASIS_OK;
+    for (int al = 0; al < S.ns && o->status == OASIS_OK; ++al) o->status = S.h_st[3 + al].status;
     if (cons) {
         o->it_m = mm.it_total[0];
         for (int k = 0; k < S.m->dim && k < 3; ++k) o->res_m[k] = mm.bb[k] > 0 ? std::sqrt(mm.rr[k] / mm.bb[k]) : 0.0;
@@ -494,6 +502,113 @@ int oasis_set_dirichlet(oasis_solver* solver, const double* g, int32_t on_device
         }
         S->impl->to_state(s, src, ST_G, nd, D);
         if (!on_device) OASIS_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+static void drop_graph(Solver* S);
+
+int oasis_solver_set_scalars(oasis_solver* solver, int32_t n_scalars, const double* diffusivity,
+                             const double* source, int64_t n_dirichlet, const int32_t* dirichlet_dofs) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S, OASIS_EINVAL, "null solver");
+        OASIS_CHECK(n_scalars >= 0 && n_scalars <= OASIS_MAX_SCALARS, OASIS_EINVAL, "n_scalars out of range");
+        OASIS_CHECK(n_scalars == 0 || (diffusivity && source), OASIS_EINVAL, "null diffusivity or source");
+        OASIS_CHECK(n_dirichlet >= 0 && (n_dirichlet == 0 || dirichlet_dofs), OASIS_EINVAL, "scalar dirichlet dofs");
+        const int64_t n = S->m->n;
+        for (int al = 0; al < n_scalars; ++al)
+            OASIS_CHECK(diffusivity[al] >= 0 && std::isfinite(diffusivity[al]) && std::isfinite(source[al]),
+                        OASIS_EINVAL, "diffusivity must be finite and >= 0, source finite");
+        std::vector<int32_t> di(n, -1);
+        for (int64_t q = 0; q < n_dirichlet; ++q) {
+            OASIS_CHECK(dirichlet_dofs[q] >= 0 && dirichlet_dofs[q] < n, OASIS_EINVAL, "scalar dirichlet dof out of range");
+            OASIS_CHECK(di[dirichlet_dofs[q]] < 0, OASIS_EINVAL, "repeated scalar dirichlet dof");
+            di[dirichlet_dofs[q]] = (int32_t)q;
+        }
+        drop_graph(S);
+        cudaStream_t s = nullptr;
+        OASIS_CUDA(cudaDeviceSynchronize());
+        const size_t vb = S->mixed ? sizeof(float) : sizeof(double), sb = 8;
+        const int64_t nnz = S->m->nnz;
+        const bool on = n_scalars > 0;
+        S->ns = n_scalars;
+        S->n_sdir = on ? n_dirichlet : 0;
+        for (int al = 0; al < OASIS_MAX_SCALARS; ++al) {
+            S->sc_diff[al] = al < n_scalars ? diffusivity[al] : 0.0;
+            S->sc_src[al] = al < n_scalars ? source[al] : 0.0;
+        }
+        if (on) S->sdir_index.upload(di.data(), n, s);
+        else S->sdir_index.alloc(0);
+        S->c.alloc(on ? sb * n * n_scalars : 0, s);
+        S->gc.alloc(on ? sb * std::max<int64_t>(1, n_dirichlet * n_scalars) : 0, s);
+        S->cbar.alloc(on ? vb * nnz : 0, s);
+        S->Ac.alloc(on ? vb * nnz : 0, s);
+        S->dinvAc.alloc(on ? vb * n : 0, s);
+        S->r0c.alloc(on ? sb * n : 0, s);
+        S->dc.alloc(on ? sb * n : 0, s);
+        for (auto& w : S->sw) w.alloc(on ? vb * n : 0, s);
+        OASIS_CUDA(cudaMemsetAsync(S->st.p + 3, 0, OASIS_MAX_SCALARS * sizeof(KrylovState), s));
+        OASIS_CUDA(cudaStreamSynchronize(s));
+        S->impl->scalars_changed();
+    });
+}
+
+int oasis_set_scalar_fields(oasis_solver* solver, const double* c, int32_t on_device, void* stream) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S && c, OASIS_EINVAL, "null pointer");
+        OASIS_CHECK(S->ns > 0, OASIS_EINVAL, "no scalars (oasis_solver_set_scalars)");
+        cudaStream_t s = as_stream(stream);
+        const int64_t count = S->m->n * S->ns;
+        const double* src = c;
+        DBuf<double> tmp;
+        if (!on_device) {
+            tmp.alloc(count);
+            OASIS_CUDA(cudaMemcpyAsync(tmp.p, c, count * sizeof(double), cudaMemcpyHostToDevice, s));
+            src = tmp.p;
+        }
+        S->impl->to_state(s, src, ST_C, count, 1);
+        OASIS_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int oasis_get_scalar_fields(oasis_solver* solver, double* c, int32_t on_device, void* stream) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S && c, OASIS_EINVAL, "null pointer");
+        OASIS_CHECK(S->ns > 0, OASIS_EINVAL, "no scalars (oasis_solver_set_scalars)");
+        cudaStream_t s = as_stream(stream);
+        const int64_t count = S->m->n * S->ns;
+        if (on_device) {
+            S->impl->from_state(s, c, ST_C, count, 1);
+            return;
+        }
+        DBuf<double> tmp;
+        tmp.alloc(count);
+        S->impl->from_state(s, tmp.p, ST_C, count, 1);
+        OASIS_CUDA(cudaMemcpyAsync(c, tmp.p, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+        OASIS_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int oasis_set_scalar_dirichlet(oasis_solver* solver, const double* g, int32_t on_device, void* stream) {
+    return guarded([&] {
+        Solver* S = reinterpret_cast<Solver*>(solver);
+        OASIS_CHECK(S, OASIS_EINVAL, "null solver");
+        OASIS_CHECK(S->ns > 0, OASIS_EINVAL, "no scalars (oasis_solver_set_scalars)");
+        if (S->n_sdir == 0) return;
+        OASIS_CHECK(g, OASIS_EINVAL, "null values");
+        cudaStream_t s = as_stream(stream);
+        const int64_t count = S->n_sdir * S->ns;
+        const double* src = g;
+        DBuf<double> tmp;
+        if (!on_device) {
+            tmp.alloc(count);
+            OASIS_CUDA(cudaMemcpyAsync(tmp.p, g, count * sizeof(double), cudaMemcpyHostToDevice, s));
+            src = tmp.p;
+        }
+        S->impl->to_state(s, src, ST_GC, count, 1);
+        OASIS_CUDA(cudaStreamSynchronize(s));
     });
 }
 

@@ -69,6 +69,8 @@ struct StepData {
     float* feat;                      // learned guess: features [n][3]
     float* gy;                        // learned guess: network output [n]
     V *mx, *mr, *mz, *mp, *mq;        // consistent-mass update [n][D]: increment, r, z, p, q = M p
+    V* cbar;                          // passive scalars: C(ubar) per pattern entry, written by the
+                                      // velocity assembly when non-null
     KrylovState *stu, *stp, *stm;
     void* partial;
     double f[3];
@@ -109,6 +111,10 @@ struct StepImpl {
     virtual void advance_pressure(cudaStream_t s) = 0;
     // velocity update (lumped, or the consistent-mass solve then the update)
     virtual void update(cudaStream_t s, bool graph) = 0;
+    // passive scalars: assembly, BiCGStab and update of every scalar
+    virtual void scalar_solve(cudaStream_t s, bool graph) = 0;
+    // the solver's scalar buffers were (re)allocated or removed
+    virtual void scalars_changed() = 0;
     virtual void to_state(cudaStream_t s, const double* src_soa, int which, int64_t count, int comps) = 0;
     virtual void from_state(cudaStream_t s, double* dst_soa, int which, int64_t count, int comps) = 0;
     virtual void a_to_double(cudaStream_t s, double* dst) = 0;
@@ -121,7 +127,7 @@ struct StepImpl {
 };
 
 // state buffers addressable by to_state / from_state
-enum StateId { ST_U1 = 0, ST_U2, ST_PSTAR, ST_PHI, ST_G, ST_R0, ST_COUNT };
+enum StateId { ST_U1 = 0, ST_U2, ST_PSTAR, ST_PHI, ST_G, ST_R0, ST_C, ST_GC, ST_COUNT };
 
 using LoopFn = std::function<void(cudaStream_t, const Loop&)>;
 
@@ -139,14 +145,26 @@ struct Solver {
     RBuf pq[2];                                                        // CgQuad<V> [n]
     RBuf amg_vec[4];                                                   // V [n]: r, s, w, u (multigrid CG)
     RBuf mw[5];                                                        // V [n][D]: consistent-mass CG
+    // passive scalars (oasis_solver_set_scalars)
+    int ns = 0;
+    int64_t n_sdir = 0;
+    double sc_diff[OASIS_MAX_SCALARS] = {0}, sc_src[OASIS_MAX_SCALARS] = {0};
+    DBuf<int32_t> sdir_index;                                          // [n]: index in the set, or -1
+    RBuf c, gc;                                                        // S [ns][n], S [ns][n_sdir]
+    RBuf cbar, Ac;                                                     // V [nnz]
+    RBuf dinvAc;                                                       // V [n]
+    RBuf r0c, dc;                                                      // S [n]
+    RBuf sw[9];                                                        // V [n]: BiCGStab work
     AmgWork amgw;                                                      // V-cycle work vectors
     DBuf<float> feat, gy;                                              // learned-guess features / output
     struct Net* net = nullptr;                                         // attached network (not owned)
     bool record = false;                                               // compute features every step
     RBuf Kout;                                                         // S [nnz]
     DBuf<double> stage;                                                // [max(n, n_dir) * D]
-    static constexpr int kStates = 3;
-    DBuf<KrylovState> st;                                              // [0] velocity, [1] pressure, [2] mass
+    static constexpr int kStates = 3 + OASIS_MAX_SCALARS;
+    DBuf<KrylovState> st;                                              // [0] velocity, [1] pressure, [2] mass,
+                                                                       // [3 + a] scalar a
+    int n_states() const { return 3 + ns; }                            // mirrored to the host each step
     RBuf partial;
     KrylovState* h_st = nullptr;                                       // pinned mirror [kStates]
     std::unique_ptr<StepImpl> impl;

@@ -206,6 +206,8 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
 #pragma unroll
             for (int b = 0; b < NB; ++b) cb[b] = s_t1[((size_t)b * a.max_row + sl) * kTile + rr] + gdot[b] * inv_d2;
             const V kv = a.K[e];
+            // passive scalars: C(ubar), linear in the convecting velocity
+            if (a.cbar) a.cbar[e] = ABE ? (V)1.5 * cb[0] - (V)0.5 * cb[NB - 1] : cb[0];
             V av = ABE ? a.M[e] * k_.rdt + k_.hnu * kv : a.M[e] * k_.rdt + (V)0.5 * cb[0] + k_.hnu * kv;
             if (s_dir[rr] >= 0) av = (j == ii) ? (V)1 : (V)0;
             a.A[e] = av;
@@ -1325,6 +1327,83 @@ __global__ void __launch_bounds__(kBlock) k_pressure_advance(StepData<P> a) {
         a.pstar[i] = s_sub(s_add(a.pstar[i], a.x[i]), meanp);
 }
 
+// ================================================================ passive scalars
+// Scalar equation of Sec. 3 for one scalar.  The fields of `a` point at that
+// scalar's buffers: u1 = c^{n-1} [n], A / dinvA / r0 / du = its system, and
+// dir_index / g = the scalars' Dirichlet set and this scalar's values;
+// k_.nu = D_a, k_.hnu = D_a / 2, k_.f[0] = f_a.  With C(ubar) from the velocity
+// assembly: A_a = M/dt + C/2 + D_a K/2 and r0 = f_a ML - (C + D_a K) c^{n-1},
+// which is b_a - A_a c^{n-1} for b_a = (M/dt - C/2 - D_a K/2) c^{n-1} + f_a ML;
+// Dirichlet rows are unit rows with r0 = g - c^{n-1}.  Resets the solve's
+// scalars as the velocity assembly does.
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_scalar_assemble(StepData<P> a, Consts<typename P::V> k_) {
+    using V = typename P::V;
+    using S = typename P::S;
+    using Acc = typename P::Acc;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    V* s_sh = reinterpret_cast<V*>(dsm);                       // [tile_cap]
+    __shared__ int32_t s_rp[kTile + 1];
+    __shared__ int32_t s_dir[kTile];
+    Acc part[1];
+    acc_zero(part[0]);
+    const int r = threadIdx.x;
+    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
+        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
+        if (r < T.nr) s_dir[r] = a.dir_index[T.r0 + r];
+        __syncthreads();
+        for (int32_t e = T.e0 + r; e < T.e1; e += kTile) {
+            const int rr = tile_row_of(s_rp, T.nr, e);
+            const int64_t ii = T.r0 + rr;
+            const int32_t j = a.col[e];
+            const V cv = a.cbar[e], kv = a.K[e];
+            V av = a.M[e] * k_.rdt + (V)0.5 * cv + k_.hnu * kv;
+            if (s_dir[rr] >= 0) av = (j == ii) ? (V)1 : (V)0;
+            a.A[e] = av;
+            if (j == ii) a.dinvA[ii] = (V)1 / av;
+            s_sh[e - T.e0] = -(cv + k_.nu * kv) * s_v(a.u1[j]);
+        }
+        __syncthreads();
+        if (r < T.nr) {
+            const int64_t i = T.r0 + r;
+            const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
+            V acc = 0;
+            for (int32_t q = b0; q < b1; ++q) acc += s_sh[q];
+            const int dir = s_dir[r];
+            const S r0v = dir >= 0 ? s_sub(a.g[dir], a.u1[i]) : s_addv(s_from(k_.f[0] * a.ML[i]), acc);
+            a.r0[i] = r0v;
+            a.du[i] = s_zero<S>();
+            const V rv = s_v(r0v);
+            acc_prod(part[0], rv, rv);
+        }
+        __syncthreads();
+    }
+    double tot[1];
+    if (grid_sum<1, Acc>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0) {
+        KrylovState* st = a.stu;
+        for (int k = 0; k < 3; ++k) {
+            st->bb[k] = k == 0 ? tot[0] : 0.0;
+            st->col_done[k] = k == 0 ? 0 : 1;
+            st->in_done[k] = 1;
+            st->it_total[k] = 0;
+            st->rr[k] = k == 0 ? tot[0] : 0.0;
+        }
+        st->sweeps = 0;
+        st->it_in = 0;
+        st->status = OASIS_OK;
+        st->first = 1;
+    }
+}
+
+// c^n = c^{n-1} + delta, Dirichlet rows = g.
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_scalar_finish(StepData<P> a) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int dir = a.dir_index[i];
+        a.u1[i] = dir >= 0 ? a.g[dir] : s_add(a.u1[i], a.du[i]);
+    }
+}
+
 // ================================================================ consistent-mass update
 // Sec. 5 without lumping: M u^n = M u^I - dt dP^k phi with Dirichlet rows
 // u^n = g, solved for the increment delta = u^n - u^I (the d components as d
@@ -1722,7 +1801,7 @@ struct StepImplT final : StepImpl {
     int64_t tiles = 0;
     size_t sm_asm = 0, sm_asm2 = 0, sm_out_u = 0, sm_out_u1 = 0, sm_spmm = 0, sm_spmm1 = 0, sm_outp = 0, sm_v1 = 0, sm_vd = 0;
     int g_asm = 1, g_asm2 = 1, g_out_u = 1, g_out_u1 = 1, g_spmm0 = 1, g_spmm1 = 1, g_spmm0_1 = 1, g_spmm1_1 = 1,
-        g_rhs = 1, g_upd = 1, g_upd_c = 1, g_mspmv = 1;
+        g_rhs = 1, g_upd = 1, g_upd_c = 1, g_mspmv = 1, g_out_s = 1, g_spmm0_s = 1, g_spmm1_s = 1, g_sasm = 1;
     int ge_n = 1, ge_nd = 1, ge_c = 1;
     int g_sell = 1;
     int iter_v = 0;                                   // chosen CG iteration shape
@@ -1835,6 +1914,10 @@ struct StepImplT final : StepImpl {
         g_upd = tile_grid(k_update<P, D, false>, sm_vd, tiles);
         g_upd_c = tile_grid(k_update<P, D, true>, 0, tiles);
         g_mspmv = tile_grid(k_mass_spmv<P, D>, sm_vd, tiles);
+        g_out_s = tile_grid(k_bicg_outer<P, 1, 1>, sm_out_u1, tiles);
+        g_spmm0_s = tile_grid(k_bicg_spmm<P, 1, 1, 0>, sm_spmm1, tiles);
+        g_spmm1_s = tile_grid(k_bicg_spmm<P, 1, 1, 1>, sm_spmm1, tiles);
+        g_sasm = tile_grid(k_scalar_assemble<P>, sm_v1, tiles);
         ge_n = elem_grid(m.n);
         ge_nd = elem_grid(m.n * D);
         ge_c = elem_grid(m.nc);
@@ -1866,36 +1949,86 @@ struct StepImplT final : StepImpl {
         return c;
     }
 
-    template <int NR>
-    void bicg_solve(cudaStream_t s, int k0, bool graph) {
-        const int go = NR == 1 ? g_out_u1 : g_out_u;
-        const size_t so = NR == 1 ? sm_out_u1 : sm_out_u;
-        const int gs0 = NR == 1 ? g_spmm0_1 : g_spmm0, gs1 = NR == 1 ? g_spmm1_1 : g_spmm1;
-        const size_t ss = NR == 1 ? sm_spmm1 : sm_spmm;
+    // Launch shapes of the BiCGStab kernels for NR right-hand sides of a [n][DD]
+    // system (DD = D: velocity; DD = 1: a scalar).
+    struct BicgGrids {
+        int go, gs0, gs1;
+        size_t so, ss;
+    };
+    template <int DD, int NR>
+    BicgGrids bicg_grids() const {
+        if constexpr (DD == 1) return {g_out_s, g_spmm0_s, g_spmm1_s, sm_out_u1, sm_spmm1};
+        else if constexpr (NR == 1) return {g_out_u1, g_spmm0_1, g_spmm1_1, sm_out_u1, sm_spmm1};
+        else return {g_out_u, g_spmm0, g_spmm1, sm_out_u, sm_spmm};
+    }
+
+    // BiCGStab with refinement sweeps on the system of q (state index `which`).
+    template <int DD, int NR>
+    void bicg_run(const StepData<P>& q, cudaStream_t s, int which, int k0, bool graph) {
+        const BicgGrids G = bicg_grids<DD, NR>();
         Sv.run_loops(
-            s, graph, 0,
+            s, graph, which,
             [&](cudaStream_t ss_, const Loop& lp) {
-                k_bicg_outer<P, D, NR><<<go, kBlock, so, ss_>>>(a, k0, ctl_u(lp));
+                k_bicg_outer<P, DD, NR><<<G.go, kBlock, G.so, ss_>>>(q, k0, ctl_u(lp));
                 OASIS_CUDA(cudaGetLastError());
             },
             [&](cudaStream_t ss_, const Loop& lp) {
                 const Ctl c = ctl_u(lp);
-                k_bicg_dir<P, D, NR><<<ge_n, kBlock, 0, ss_>>>(a, k0);
+                k_bicg_dir<P, DD, NR><<<ge_n, kBlock, 0, ss_>>>(q, k0);
                 int pb = Sv.prof_begin(ss_, OASIS_PROF_BICG_SPMM);
-                k_bicg_spmm<P, D, NR, 0><<<gs0, kBlock, ss, ss_>>>(a, k0, c);
+                k_bicg_spmm<P, DD, NR, 0><<<G.gs0, kBlock, G.ss, ss_>>>(q, k0, c);
                 Sv.prof_end(ss_, pb);
-                k_bicg_s<P, D, NR><<<ge_n, kBlock, 0, ss_>>>(a, k0);
+                k_bicg_s<P, DD, NR><<<ge_n, kBlock, 0, ss_>>>(q, k0);
                 pb = Sv.prof_begin(ss_, OASIS_PROF_BICG_SPMM);
-                k_bicg_spmm<P, D, NR, 1><<<gs1, kBlock, ss, ss_>>>(a, k0, c);
+                k_bicg_spmm<P, DD, NR, 1><<<G.gs1, kBlock, G.ss, ss_>>>(q, k0, c);
                 Sv.prof_end(ss_, pb);
-                k_bicg_xr<P, D, NR><<<ge_n, kBlock, 0, ss_>>>(a, k0, c);
+                k_bicg_xr<P, DD, NR><<<ge_n, kBlock, 0, ss_>>>(q, k0, c);
                 OASIS_CUDA(cudaGetLastError());
             },
             [&](cudaStream_t ss_, const Loop&) {
-                k_bicg_correct<P, D, NR><<<ge_n, kBlock, 0, ss_>>>(a, k0);
+                k_bicg_correct<P, DD, NR><<<ge_n, kBlock, 0, ss_>>>(q, k0);
                 OASIS_CUDA(cudaGetLastError());
             },
             k0, NR);
+    }
+
+    template <int NR>
+    void bicg_solve(cudaStream_t s, int k0, bool graph) {
+        bicg_run<D, NR>(a, s, 0, k0, graph);
+    }
+
+    // StepData of scalar `al`: its field, system, work vectors and state.
+    StepData<P> scalar_data(int al) const {
+        StepData<P> q = a;
+        const int64_t n = Sv.m->n;
+        q.u1 = Sv.c.as<S>() + (size_t)al * n;
+        q.g = Sv.gc.as<S>() + (size_t)al * Sv.n_sdir;
+        q.dir_index = Sv.sdir_index.p;
+        q.A = Sv.Ac.as<V>();
+        q.dinvA = Sv.dinvAc.as<V>();
+        q.r0 = Sv.r0c.as<S>();
+        q.du = Sv.dc.as<S>();
+        V** w[9] = {&q.r, &q.rh, &q.p, &q.v, &q.s, &q.t, &q.ph, &q.sh, &q.dl};
+        for (int k = 0; k < 9; ++k) *w[k] = Sv.sw[k].as<V>();
+        q.stu = Sv.st.p + 3 + al;
+        return q;
+    }
+
+    void scalars_changed() override { a.cbar = Sv.ns > 0 ? Sv.cbar.as<V>() : nullptr; }
+
+    void scalar_solve(cudaStream_t s, bool graph) override {
+        for (int al = 0; al < Sv.ns; ++al) {
+            const StepData<P> q = scalar_data(al);
+            Consts<V> kc = k_;
+            kc.nu = (V)Sv.sc_diff[al];
+            kc.hnu = (V)(0.5 * Sv.sc_diff[al]);
+            kc.f[0] = (V)Sv.sc_src[al];
+            k_scalar_assemble<P><<<g_sasm, kBlock, sm_v1, s>>>(q, kc);
+            OASIS_CUDA(cudaGetLastError());
+            bicg_run<1, 1>(q, s, 3 + al, 0, graph);
+            k_scalar_finish<P><<<ge_n, kBlock, 0, s>>>(q);
+            OASIS_CUDA(cudaGetLastError());
+        }
     }
 
     void tentative_solve(cudaStream_t s, bool graph) override {
@@ -2052,6 +2185,8 @@ struct StepImplT final : StepImpl {
             case ST_PHI: return a.phi;
             case ST_G: return const_cast<S*>(a.g);
             case ST_R0: return a.r0;
+            case ST_C: return Sv.c.as<S>();
+            case ST_GC: return Sv.gc.as<S>();
             default: throw Error(OASIS_EINVAL, "unknown state buffer");
         }
     }

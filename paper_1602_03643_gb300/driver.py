@@ -15,7 +15,7 @@ class IPCSRun:
     def __init__(self, problem, precision=capi.OASIS_FP64, rtol_u=1e-12, rtol_p=1e-12, max_it_u=2000,
                  max_it_p=50000, inner_rtol=1e-4, batch_rhs=1, use_graph=0, guess=capi.OASIS_GUESS_ZERO,
                  spmv_variant=0, pressure_pc=0, inner_iters=1, convection=0, velocity_update=0,
-                 stream=None):
+                 scalars=True, stream=None):
         pb = problem
         self.pb = pb
         self.stream = stream
@@ -32,10 +32,23 @@ class IPCSRun:
         capi.oasis_set_fields(self.solver, pb.u_nm1, pb.u_nm2, pb.p, pb.t0, False, stream)
         self.stats = []
         self.net = None
+        self.ns = 0
+        sc = getattr(pb, "scalars", None)
+        if sc is not None and scalars:
+            self.ns = sc.c0.shape[0]
+            capi.oasis_solver_set_scalars(self.solver, sc.diffusivity, sc.source, sc.dirichlet)
+            capi.oasis_set_scalar_fields(self.solver, sc.c0, False, stream)
 
     def set_dirichlet_for_next_step(self):
         if len(self.pb.dirichlet):
             capi.oasis_set_dirichlet(self.solver, self.pb.g(self.t + self.pb.dt), False, self.stream)
+        if self.ns and len(self.pb.scalars.dirichlet):
+            capi.oasis_set_scalar_dirichlet(self.solver, self.pb.scalars.g(self.t + self.pb.dt), False,
+                                            self.stream)
+
+    def scalar_fields(self):
+        """c^n of every scalar, [ns, n] (host)."""
+        return capi.oasis_get_scalar_fields(self.solver, self.ns, self.n, False, None, self.stream)
 
     def step(self, n_steps=1, want_stats=True, time_dependent_bc=True):
         st = None
