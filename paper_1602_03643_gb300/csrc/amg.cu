@@ -358,6 +358,14 @@ void amg_build(Mesh& m, cudaStream_t s) {
         upload_vec(L->d32, dinv32, s);
         L->omega = 4.0 / (3.0 * spectral_radius(A, d));
         if (h->lv.empty()) {
+            h->fine.n = m.n;
+            h->fine.n_slices = (m.n + 31) / 32;
+            h->fine.ptr = m.sell_ptr.p;
+            h->fine.len = m.sell_len.p;
+            h->fine.col = m.sell_col.p;
+            h->fine.dcol = m.sell_dcol.p;
+            h->fine.v32 = m.K32s.p;
+            h->fine.v64 = m.K64s.p;
             L->rp = m.row_ptr.p;
             L->ci = m.col.p;
             L->a32 = m.K32.p;
@@ -509,22 +517,108 @@ __global__ void __launch_bounds__(kBlock) k_amg_post(int64_t n, const int32_t* _
     }
 }
 
-// coarsest level: x = inv r (dense, row-major), one warp per row
+// Finest level on SELL-32: one warp per slice of 32 rows, lane l owns row
+// 32 s + l; entry k of the row sits at ptr[s] + 32 k + l (padding: a valid
+// column and a zero value).  Four entries per lane have their column and value
+// loads issued together, then their gathers; products are added in entry order.
+template <bool D16>
+__device__ __forceinline__ int32_t fine_col(const AmgSellView& F, int64_t q, int32_t row) {
+    if constexpr (D16) {
+        int32_t j = row + (int32_t)F.dcol[q];
+        const int32_t n = (int32_t)F.n;
+        j = j < 0 ? j + n : j;
+        return j >= n ? j - n : j;
+    } else {
+        return F.col[q];
+    }
+}
+
+// PRE: x = w D^-1 r and res = r - A x (smoothing from zero); else
+// out = x + w D^-1 (r - A x).  The gathered operand is w d_j r_j (PRE) or x_j.
+template <class V, bool D16, bool PRE>
+__global__ void __launch_bounds__(kBlock) k_amg_fine(AmgSellView F, const V* __restrict__ av,
+                                                     const V* __restrict__ d, V w, const V* __restrict__ r,
+                                                     const V* __restrict__ x, V* __restrict__ out,
+                                                     V* __restrict__ res, const KrylovState* st) {
+    if (amg_done(st)) return;
+    constexpr int C = 4;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = w0; sl < F.n_slices; sl += nw) {
+        const int64_t i = sl * 32 + lane;
+        const int32_t row = (int32_t)i;
+        const int len = F.len[sl];
+        const int64_t base = (int64_t)F.ptr[sl] + lane;
+        V s = 0;
+        for (int k = 0; k < len; k += C) {
+            int32_t j[C];
+            V kv[C];
+#pragma unroll
+            for (int u = 0; u < C; ++u) {
+                const int64_t q = base + 32 * (int64_t)(k + u);
+                const bool ok = k + u < len;
+                j[u] = ok ? fine_col<D16>(F, q, row) : 0;
+                kv[u] = ok ? av[q] : V(0);
+            }
+            V g[C];
+#pragma unroll
+            for (int u = 0; u < C; ++u) g[u] = PRE ? w * d[j[u]] * r[j[u]] : x[j[u]];
+#pragma unroll
+            for (int u = 0; u < C; ++u)
+                if (k + u < len) s += kv[u] * g[u];
+        }
+        if (i < F.n) {
+            if constexpr (PRE) {
+                res[i] = r[i] - s;
+                out[i] = w * d[i] * r[i];
+            } else {
+                out[i] = x[i] + w * d[i] * (r[i] - s);
+            }
+        }
+    }
+}
+
+// coarsest level: x = inv r (dense, row-major), one warp per row; each lane
+// keeps 8 column loads in flight and 8 partial sums (added pairwise at the end)
 template <class V>
 __global__ void __launch_bounds__(kBlock) k_amg_dense(int64_t n, const V* __restrict__ inv, const V* __restrict__ r,
                                                       V* __restrict__ x, const KrylovState* st) {
     if (amg_done(st)) return;
-    constexpr int G = 32;
+    constexpr int G = 32, U = 8;
     AMG_ROWS(n) {
         const int64_t i = base;
-        V s = 0;
-        if (i < n)
-            for (int64_t c = lg; c < n; c += 32) s += inv[(size_t)i * n + c] * r[c];
-        s = group_sum<G>(s);
+        V acc[U] = {};
+        if (i < n) {
+            const V* row = inv + (size_t)i * n;
+            const int nn = (int)n;
+            int c = lg;
+            for (; c + 32 * (U - 1) < nn; c += 32 * U) {
+                V av[U], rv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    av[u] = row[c + 32 * u];
+                    rv[u] = r[c + 32 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) acc[u] += av[u] * rv[u];
+            }
+            for (; c < nn; c += 32) acc[U - 1] += row[c] * r[c];
+        }
+#pragma unroll
+        for (int h = U / 2; h > 0; h >>= 1)
+#pragma unroll
+            for (int u = 0; u < h; ++u) acc[u] += acc[u + h];
+        const V s = group_sum<G>(acc[0]);
         if (i < n && lg == 0) x[i] = s;
     }
 }
 #undef AMG_ROWS
+
+int fine_grid(const AmgSellView& F) {
+    const int64_t want = (F.n_slices + kBlock / 32 - 1) / (kBlock / 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 8));
+}
 
 int amg_grid(int64_t rows, int G) {
     const int64_t per_block = (int64_t)kBlock / G;
@@ -576,7 +670,19 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
         const V* a = pick<V>(lv.a32, lv.a64);
         const V* d = pick<V>(lv.d32.p, lv.d64.p);
         const V w = (V)lv.omega;
-        AMG_DISPATCH(lv.g_a, k_amg_pre, lv.n, lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]), vec(wk.res[l]), st);
+        if (l == 0 && h.fine.ptr) {
+            const V* fv = pick<V>(h.fine.v32, h.fine.v64);
+            const int g = fine_grid(h.fine);
+            if (h.fine.dcol)
+                k_amg_fine<V, true, true><<<g, kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), nullptr, vec(wk.x[0]),
+                                                               vec(wk.res[0]), st);
+            else
+                k_amg_fine<V, false, true><<<g, kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), nullptr, vec(wk.x[0]),
+                                                                vec(wk.res[0]), st);
+        } else {
+            AMG_DISPATCH(lv.g_a, k_amg_pre, lv.n, lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]),
+                         vec(wk.res[l]), st);
+        }
         const int64_t nc = l + 1 < L ? h.lv[l + 1]->n : h.nc;
         const V* rv = pick<V>(lv.r32.p, lv.r64.p);
         AMG_DISPATCH(lv.g_r, k_amg_restrict, nc, nc, lv.r_rp.p, lv.r_ci.p, rv, vec(wk.res[l]), vec(wk.rin[l + 1]),
@@ -591,7 +697,18 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
         const V w = (V)lv.omega;
         const V* pv = pick<V>(lv.p32.p, lv.p64.p);
         AMG_DISPATCH(lv.g_p, k_amg_prolong, lv.n, lv.n, lv.p_rp.p, lv.p_ci.p, pv, xo(l + 1), vec(wk.x[l]), st);
-        AMG_DISPATCH(lv.g_a, k_amg_post, lv.n, lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]), xo(l), st);
+        if (l == 0 && h.fine.ptr) {
+            const V* fv = pick<V>(h.fine.v32, h.fine.v64);
+            const int g = fine_grid(h.fine);
+            if (h.fine.dcol)
+                k_amg_fine<V, true, false><<<g, kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), vec(wk.x[0]), xo(0),
+                                                                nullptr, st);
+            else
+                k_amg_fine<V, false, false><<<g, kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), vec(wk.x[0]), xo(0),
+                                                                 nullptr, st);
+        } else {
+            AMG_DISPATCH(lv.g_a, k_amg_post, lv.n, lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]), xo(l), st);
+        }
     }
     OASIS_CUDA(cudaGetLastError());
 }

@@ -16,7 +16,8 @@
 //     acts as the pseudo-inverse of A_c on right-hand sides orthogonal to 1.
 // The V(1,1) cycle uses one damped-Jacobi sweep (w_s = 4 / (3 rho(D^-1 A)))
 // before and after the coarse correction, with restriction P^T: a symmetric
-// positive semi-definite preconditioner, as CG requires.
+// positive semi-definite preconditioner, as CG requires.  The finest level's
+// sweeps read K in the mesh's SELL-32 layout; coarser levels are CSR.
 #pragma once
 
 #include <memory>
@@ -44,7 +45,19 @@ struct AmgLevelDev {
     DBuf<double> p64, r64;
 };
 
+// SELL-32 view of the finest operator (the mesh's K): the fine-level smoothers
+// read it with one lane per row, coalesced column/value loads, and 16-bit column
+// offsets where the mesh has them.
+struct AmgSellView {
+    int64_t n = 0, n_slices = 0;
+    const int32_t *ptr = nullptr, *len = nullptr, *col = nullptr;
+    const int16_t* dcol = nullptr;
+    const float* v32 = nullptr;
+    const double* v64 = nullptr;
+};
+
 struct AmgHierarchy {
+    AmgSellView fine;
     std::vector<std::unique_ptr<AmgLevelDev>> lv;   // lv[0] fine ... lv[L-1] coarsest
     int64_t nc = 0;                                  // size of the dense coarsest level
     DBuf<float> inv32;                               // [nc][nc]

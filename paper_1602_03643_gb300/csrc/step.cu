@@ -1253,7 +1253,7 @@ __global__ void __launch_bounds__(kBlock) k_amg_cg_update(StepData<P> a, Ctl ctl
 // w = K u on SELL-32 with gamma = <r, u>, delta = <w, u> and <r, r>.  START:
 // first iteration of a sweep (alpha = gamma / delta, beta = 0); else the
 // Chronopoulos-Gear update of alpha, beta and the inner stopping test.
-template <class P, bool START>
+template <class P, bool START, bool D16>
 __global__ void __launch_bounds__(kBlock) k_amg_cg_spmv(StepData<P> a, Ctl ctl) {
     using V = typename P::V;
     if (a.stp->col_done[0] || a.stp->in_done[0]) return;
@@ -1261,6 +1261,7 @@ __global__ void __launch_bounds__(kBlock) k_amg_cg_spmv(StepData<P> a, Ctl ctl) 
     int64_t i, base;
     int len, lane;
     if (sell_lane(a, i, len, base, lane)) {
+        const int32_t row = (int32_t)i;
         V w = 0;
         for (int k = 0; k < len; k += 4) {
             int32_t j[4];
@@ -1269,7 +1270,7 @@ __global__ void __launch_bounds__(kBlock) k_amg_cg_spmv(StepData<P> a, Ctl ctl) 
             for (int u = 0; u < 4; ++u) {
                 const int64_t q = base + 32 * (int64_t)(k + u);
                 const bool ok = k + u < len;
-                j[u] = ok ? a.sell_col[q] : 0;
+                j[u] = ok ? sell_j<D16>(a, q, row) : 0;
                 kv[u] = ok ? a.Ks[q] : V(0);
             }
             V g[4];
@@ -2092,7 +2093,8 @@ struct StepImplT final : StepImpl {
                     k_pcg_outer_sell<P><<<g_sell, kBlock, 0, ss>>>(a, c);
                     k_amg_cg_start<P><<<ge_n, kBlock, 0, ss>>>(a);
                     vcycle(ss);
-                    k_amg_cg_spmv<P, true><<<g_sell, kBlock, 0, ss>>>(a, c);
+                    if (a.sell_dcol) k_amg_cg_spmv<P, true, true><<<g_sell, kBlock, 0, ss>>>(a, c);
+                    else k_amg_cg_spmv<P, true, false><<<g_sell, kBlock, 0, ss>>>(a, c);
                     OASIS_CUDA(cudaGetLastError());
                 },
                 [&](cudaStream_t ss, const Loop& lp) {
@@ -2100,7 +2102,8 @@ struct StepImplT final : StepImpl {
                     k_amg_cg_update<P><<<ge_n, kBlock, 0, ss>>>(a, c);
                     vcycle(ss);
                     const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
-                    k_amg_cg_spmv<P, false><<<g_sell, kBlock, 0, ss>>>(a, c);
+                    if (a.sell_dcol) k_amg_cg_spmv<P, false, true><<<g_sell, kBlock, 0, ss>>>(a, c);
+                    else k_amg_cg_spmv<P, false, false><<<g_sell, kBlock, 0, ss>>>(a, c);
                     Sv.prof_end(ss, pq);
                     OASIS_CUDA(cudaGetLastError());
                 },

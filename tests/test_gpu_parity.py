@@ -489,13 +489,34 @@ def test_permutation_invariance():
     np.testing.assert_allclose(p2_[perm], p1_, atol=1e-9 * np.abs(p1_).max())
 
 
-def test_table1_first_row_on_gpu():
-    """The GPU path reproduces the first P1P1 row of Table 1 (periodic Taylor-Green)."""
+def _table1_rows():
+    import os
+    rows = []
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_p1p1.txt")
+    with open(path) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                n, h, eu, ku, ep, kp = line.split()
+                rows.append((int(n), float(eu), float(ep)))
+    return rows
+
+
+@pytest.mark.parametrize("row", range(5))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_table1_p1p1_rows_on_gpu(row, precision):
+    """The GPU path reproduces the printed P1P1 errors of Table 1 (periodic
+    Taylor-Green on [0, 2]^2, 10..50 cells per side, 1000 steps to t = 1), in
+    float64 and in the mixed path (rtol 1e-8), to the oracle's tolerances."""
     from paper_1602_03643_gb300.driver import IPCSRun
-    pb = WP.taylor_green_2d_periodic(10)
-    run = IPCSRun(pb, rtol_u=1e-12, rtol_p=1e-12, use_graph=1)
+    n, eu_paper, ep_paper = _table1_rows()[row]
+    pb = WP.taylor_green_2d_periodic(n)
+    rtol = 1e-12 if precision == 0 else 1e-8
+    run = IPCSRun(pb, precision=precision, rtol_u=rtol, rtol_p=rtol, use_graph=1, guess=1,
+                  pressure_pc=1 if precision else 0)
     try:
         run.step(1000, want_stats=False)
+        st = capi().oasis_last_stats(run.solver)
+        assert st.status == 0
         u, p, _ = run.fields()
     finally:
         run.close()
@@ -504,8 +525,8 @@ def test_table1_first_row_on_gpu():
     eu = np.sqrt(np.mean((u - pb.exact_u(x, t)) ** 2))
     pe = pb.exact_p(x, t - 0.5 * pb.dt)
     ep = np.sqrt(np.mean(((p - p.mean()) - (pe - pe.mean())) ** 2))
-    assert abs(eu - 9.31e-3) < 0.006 * 9.31e-3
-    assert abs(ep - 4.97e-3) < 0.01 * 4.97e-3
+    assert abs(eu - eu_paper) < 0.006 * eu_paper, (eu, eu_paper)
+    assert abs(ep - ep_paper) < 0.01 * ep_paper, (ep, ep_paper)
 
 
 def test_notconv_status():
