@@ -75,7 +75,8 @@ typedef struct oasis_params {
     double dt;             /* time step (constant, Sec. 2) */
     double f[3];           /* constant body force; int f_k phi_i = f_k * ML_i */
     double rtol_u;         /* tentative velocity: stop when ||r|| <= rtol_u ||r_0||,
-                              r_0 the residual of the initial guess u^{n-1} */
+                              r_0 = b - A u^{n-1}; the iteration starts from the
+                              extrapolation 2 u^{n-1} - u^{n-2} */
     double rtol_p;         /* pressure correction: stop when ||r|| <= rtol_p ||b_phi||,
                               b_phi the right-hand side (the residual of phi = 0) */
     int32_t max_it_u;      /* cap on BiCGStab iterations per solve (all sweeps) */

@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "amg.cuh"
@@ -415,8 +416,13 @@ void amg_build(Mesh& m, cudaStream_t s) {
     h->sizes.push_back(A.n);
     h->nnzs.push_back(A.nnz());
     const std::vector<double> inv = coarse_inverse(A);
-    std::vector<float> inv32(inv.begin(), inv.end());
-    upload_vec(h->inv64, inv, s);
+    // rows padded to a multiple of 4 entries (16-byte vector loads)
+    h->ld = (A.n + 3) / 4 * 4;
+    std::vector<double> inv_ld((size_t)A.n * h->ld, 0.0);
+    for (int64_t i = 0; i < A.n; ++i)
+        for (int64_t c = 0; c < A.n; ++c) inv_ld[(size_t)i * h->ld + c] = inv[(size_t)i * A.n + c];
+    std::vector<float> inv32(inv_ld.begin(), inv_ld.end());
+    upload_vec(h->inv64, inv_ld, s);
     upload_vec(h->inv32, inv32, s);
     OASIS_CUDA(cudaStreamSynchronize(s));
     h->setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -430,12 +436,14 @@ void AmgWork::alloc(const AmgHierarchy& h, size_t vbytes) {
     res.resize(L + 1);
     rin.resize(L + 1);
     for (size_t l = 0; l <= L; ++l) {
-        const int64_t n = l < L ? h.lv[l]->n : h.nc;
+        // the dense level's input is read with vector loads up to ld: zero padding
+        const int64_t n = l < L ? h.lv[l]->n : h.ld;
         const size_t cnt = ((size_t)n * vbytes + 7) / 8;
         x[l].alloc(cnt);
         xo[l].alloc(cnt);
         res[l].alloc(cnt);
         rin[l].alloc(cnt);
+        if (l == L) OASIS_CUDA(cudaMemset(rin[l].p, 0, rin[l].bytes()));
     }
 }
 
@@ -579,38 +587,37 @@ __global__ void __launch_bounds__(kBlock) k_amg_fine(AmgSellView F, const V* __r
     }
 }
 
-// coarsest level: x = inv r (dense, row-major), one warp per row; each lane
-// keeps 8 column loads in flight and 8 partial sums (added pairwise at the end)
+// coarsest level: x = inv r with inv dense and row-major, leading dimension ld
+// (a multiple of 4, zero-padded) and r zero-padded to ld; one block of 128
+// threads per row, 16-byte loads (float4 / double2), the block's sum in a fixed
+// order.
+__device__ __forceinline__ float dot_vec(const float4& a, const float4& b) {
+    return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
+__device__ __forceinline__ double dot_vec(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
+
+constexpr int kDenseBlock = 128;
+
 template <class V>
-__global__ void __launch_bounds__(kBlock) k_amg_dense(int64_t n, const V* __restrict__ inv, const V* __restrict__ r,
-                                                      V* __restrict__ x, const KrylovState* st) {
+__global__ void __launch_bounds__(kDenseBlock) k_amg_dense(int64_t n, int64_t ld, const V* __restrict__ inv,
+                                                           const V* __restrict__ r, V* __restrict__ x,
+                                                           const KrylovState* st) {
     if (amg_done(st)) return;
-    constexpr int G = 32, U = 8;
-    AMG_ROWS(n) {
-        const int64_t i = base;
-        V acc[U] = {};
-        if (i < n) {
-            const V* row = inv + (size_t)i * n;
-            const int nn = (int)n;
-            int c = lg;
-            for (; c + 32 * (U - 1) < nn; c += 32 * U) {
-                V av[U], rv[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    av[u] = row[c + 32 * u];
-                    rv[u] = r[c + 32 * u];
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) acc[u] += av[u] * rv[u];
-            }
-            for (; c < nn; c += 32) acc[U - 1] += row[c] * r[c];
-        }
-#pragma unroll
-        for (int h = U / 2; h > 0; h >>= 1)
-#pragma unroll
-            for (int u = 0; u < h; ++u) acc[u] += acc[u + h];
-        const V s = group_sum<G>(acc[0]);
-        if (i < n && lg == 0) x[i] = s;
+    using V2 = typename std::conditional<sizeof(V) == 4, float4, double2>::type;
+    constexpr int E = (int)(sizeof(V2) / sizeof(V));
+    __shared__ V sh[kDenseBlock / 32];
+    const int64_t nv = ld / E;
+    const V2* rv = reinterpret_cast<const V2*>(r);
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const V2* row = reinterpret_cast<const V2*>(inv + (size_t)i * ld);
+        V acc = 0;
+#pragma unroll 4
+        for (int64_t c = threadIdx.x; c < nv; c += kDenseBlock) acc += dot_vec(row[c], rv[c]);
+        acc = group_sum<32>(acc);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) x[i] = (sh[0] + sh[1]) + (sh[2] + sh[3]);
+        __syncthreads();
     }
 }
 #undef AMG_ROWS
@@ -688,7 +695,8 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
         AMG_DISPATCH(lv.g_r, k_amg_restrict, nc, nc, lv.r_rp.p, lv.r_ci.p, rv, vec(wk.res[l]), vec(wk.rin[l + 1]),
                      st);
     }
-    k_amg_dense<V><<<amg_grid(h.nc, 32), kBlock, 0, s>>>(h.nc, pick<V>(h.inv32.p, h.inv64.p), vec(wk.rin[L]),
+    k_amg_dense<V><<<(int)std::max<int64_t>(1, h.nc), kDenseBlock, 0, s>>>(h.nc, h.ld, pick<V>(h.inv32.p, h.inv64.p),
+                                                                     vec(wk.rin[L]),
                                                          vec(wk.xo[L]), st);
     for (int l = L - 1; l >= 0; --l) {
         const AmgLevelDev& lv = *h.lv[l];

@@ -60,7 +60,8 @@ struct AmgHierarchy {
     AmgSellView fine;
     std::vector<std::unique_ptr<AmgLevelDev>> lv;   // lv[0] fine ... lv[L-1] coarsest
     int64_t nc = 0;                                  // size of the dense coarsest level
-    DBuf<float> inv32;                               // [nc][nc]
+    int64_t ld = 0;                                  // its row stride: nc rounded up to 4
+    DBuf<float> inv32;                               // [nc][ld], zero-padded
     DBuf<double> inv64;
     double setup_s = 0.0;
     std::vector<int64_t> sizes;                      // rows per level (incl. coarsest)

@@ -238,7 +238,10 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
                 if (dir >= 0) r0v = s_sub(a.g[(size_t)dir * D + k], a.u1[i * D + k]);
                 else r0v = s_addv(s_from(k_.f[k] * a.ML[i]), acc);
                 a.r0[i * D + k] = r0v;
-                a.du[i * D + k] = s_zero<S>();
+                // initial guess of the solve: u^I_0 = 2 u^{n-1} - u^{n-2} (Delta_0 =
+                // u^{n-1} - u^{n-2}); Dirichlet rows exact.  The stopping test stays
+                // relative to r0 = b - A u^{n-1}, so the guess changes only the count.
+                a.du[i * D + k] = dir >= 0 ? r0v : s_sub(a.u1[i * D + k], a.u2[i * D + k]);
                 const V rv = s_v(r0v);
                 acc_prod(part[k], rv, rv);
             }
