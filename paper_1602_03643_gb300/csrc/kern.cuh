@@ -174,6 +174,17 @@ __device__ __forceinline__ void block_reduce(A (&v)[NV]) {
     __syncthreads();
 }
 
+// The block's ticket of a last-block reduction, taken by the thread that wrote
+// the block's partials: an atomic increment with release semantics (those
+// writes become visible no later than the ticket) and acquire semantics.  True
+// in the block that takes the last ticket; that block still fences before it
+// reads the other blocks' partials.
+__device__ __forceinline__ bool take_last_ticket(uint32_t* ticket) {
+    uint32_t old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(ticket) : "memory");
+    return old == gridDim.x - 1;
+}
+
 // Deterministic grid reduction: every block publishes its NV partial sums; the
 // block taking the last ticket sums them in block order.  Returns true in that
 // block; its thread 0 then holds the totals (converted to double) in `tot`.
@@ -187,8 +198,7 @@ __device__ __forceinline__ bool grid_sum(A (&v)[NV], double (&tot)[NV], void* pa
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) partial[(size_t)blockIdx.x * NV + k] = v[k];
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        last = take_last_ticket(ticket);
     }
     __syncthreads();
     if (!last) return false;
@@ -258,10 +268,7 @@ __device__ __forceinline__ bool grid_finish_lite(double (&tot)[NV], const T* par
     __shared__ T sh[NV][32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    }
+    if (threadIdx.x == 0) last = take_last_ticket(ticket);
     __syncthreads();
     if (!last) return false;
     __threadfence();

@@ -1794,6 +1794,13 @@ static int elem_grid(int64_t items) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 8));
 }
 
+// Elementwise kernels that end in a last-block reduction: two blocks per SM
+// (fewer partials and tickets; measured faster than one row per thread).
+static int red_grid(int64_t items) {
+    const int64_t want = (items + kBlock - 1) / kBlock;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 2));
+}
+
 template <class P, int D>
 struct StepImplT final : StepImpl {
     using V = typename P::V;
@@ -1806,7 +1813,7 @@ struct StepImplT final : StepImpl {
     size_t sm_asm = 0, sm_asm2 = 0, sm_out_u = 0, sm_out_u1 = 0, sm_spmm = 0, sm_spmm1 = 0, sm_outp = 0, sm_v1 = 0, sm_vd = 0;
     int g_asm = 1, g_asm2 = 1, g_out_u = 1, g_out_u1 = 1, g_spmm0 = 1, g_spmm1 = 1, g_spmm0_1 = 1, g_spmm1_1 = 1,
         g_rhs = 1, g_upd = 1, g_upd_c = 1, g_mspmv = 1, g_out_s = 1, g_spmm0_s = 1, g_spmm1_s = 1, g_sasm = 1;
-    int ge_n = 1, ge_nd = 1, ge_c = 1;
+    int ge_n = 1, ge_nd = 1, ge_c = 1, ge_red = 1;
     int g_sell = 1;
     int iter_v = 0;                                   // chosen CG iteration shape
     double tune_us[OASIS_MAX_VARIANTS] = {0};
@@ -1923,6 +1930,7 @@ struct StepImplT final : StepImpl {
         g_spmm1_s = tile_grid(k_bicg_spmm<P, 1, 1, 1>, sm_spmm1, tiles);
         g_sasm = tile_grid(k_scalar_assemble<P>, sm_v1, tiles);
         ge_n = elem_grid(m.n);
+        ge_red = red_grid(m.n);
         ge_nd = elem_grid(m.n * D);
         ge_c = elem_grid(m.nc);
     }
@@ -1986,7 +1994,7 @@ struct StepImplT final : StepImpl {
                 pb = Sv.prof_begin(ss_, OASIS_PROF_BICG_SPMM);
                 k_bicg_spmm<P, DD, NR, 1><<<G.gs1, kBlock, G.ss, ss_>>>(q, k0, c);
                 Sv.prof_end(ss_, pb);
-                k_bicg_xr<P, DD, NR><<<ge_n, kBlock, 0, ss_>>>(q, k0, c);
+                k_bicg_xr<P, DD, NR><<<ge_red, kBlock, 0, ss_>>>(q, k0, c);
                 OASIS_CUDA(cudaGetLastError());
             },
             [&](cudaStream_t ss_, const Loop&) {
@@ -2102,7 +2110,7 @@ struct StepImplT final : StepImpl {
                 },
                 [&](cudaStream_t ss, const Loop& lp) {
                     const Ctl c = ctl_p(lp);
-                    k_amg_cg_update<P><<<ge_n, kBlock, 0, ss>>>(a, c);
+                    k_amg_cg_update<P><<<ge_red, kBlock, 0, ss>>>(a, c);
                     vcycle(ss);
                     const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
                     if (a.sell_dcol) k_amg_cg_spmv<P, false, true><<<g_sell, kBlock, 0, ss>>>(a, c);
@@ -2159,7 +2167,7 @@ struct StepImplT final : StepImpl {
                 [&](cudaStream_t ss, const Loop& lp) {
                     const int pm = Sv.prof_begin(ss, OASIS_PROF_MASS);
                     k_mass_guess<P, D><<<ge_n, kBlock, 0, ss>>>(a, k_);
-                    k_mass_residual<P, D><<<ge_n, kBlock, 0, ss>>>(a, ctl_m(lp));
+                    k_mass_residual<P, D><<<ge_red, kBlock, 0, ss>>>(a, ctl_m(lp));
                     Sv.prof_end(ss, pm);
                     OASIS_CUDA(cudaGetLastError());
                 },
@@ -2167,7 +2175,7 @@ struct StepImplT final : StepImpl {
                     const Ctl c = ctl_m(lp);
                     const int pm = Sv.prof_begin(ss, OASIS_PROF_MASS);
                     k_mass_spmv<P, D><<<g_mspmv, kBlock, sm_vd, ss>>>(a, c);
-                    k_mass_update<P, D><<<ge_n, kBlock, 0, ss>>>(a, c);
+                    k_mass_update<P, D><<<ge_red, kBlock, 0, ss>>>(a, c);
                     Sv.prof_end(ss, pm);
                     OASIS_CUDA(cudaGetLastError());
                 });
