@@ -345,7 +345,11 @@ int oasis_net_create(const oasis_mesh* mesh, oasis_net** out);
  * setting also refreshes the bfloat16 copy used by the kernels and resets Adam. */
 int oasis_net_set_params(oasis_net* net, const float* params);
 int oasis_net_get_params(const oasis_net* net, float* params);
-/* y = net(features); device arrays [n_dofs][3] and [n_dofs]. */
+/* y = net(features); device arrays [n_dofs][3] and [n_dofs].  Layer 2's dense
+ * product runs on the tensor cores (tcgen05, bfloat16 weights, float32
+ * accumulation, float32 activations split into three bfloat16 terms).  Waits for
+ * `stream`; OASIS_EWAIT if the kernel's bounded wait for the tensor core ran out
+ * (y is then incomplete). */
 int oasis_net_forward(oasis_net* net, const float* features, float* y, void* stream);
 /* Gradient of the loss with respect to the parameters (device [OASIS_NET_PARAMS],
  * or NULL for the network's own buffer) and the loss (device [1] or NULL) for one

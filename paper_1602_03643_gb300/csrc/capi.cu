@@ -742,6 +742,7 @@ int oasis_net_forward(oasis_net* net, const float* features, float* y, void* str
         Net* N = reinterpret_cast<Net*>(net);
         OASIS_CHECK(N && features && y, OASIS_EINVAL, "null pointer");
         net_forward(*N, features, y, as_stream(stream));
+        net_check(*N, as_stream(stream));
     });
 }
 
