@@ -33,6 +33,11 @@ struct Error : std::runtime_error {
     } while (0)
 
 constexpr int kBlock = 256;          // threads per block for every kernel here
+constexpr int kTile = kBlock;        // rows of a row tile (kern.cuh)
+// Narrow tiles (half the rows, same block size) for kernels whose per-entry
+// shared-memory staging would otherwise limit residency: the entry phase still
+// runs on every thread, the row phase on the first kTileN.
+constexpr int kTileN = kBlock / 2;
 
 // Owning device buffer (cudaMalloc at creation, cudaFree at destruction).
 template <class T>
@@ -103,6 +108,7 @@ struct Mesh {
     DBuf<float2> Kff;                          // K as float-float (hi, lo)
     DBuf<float2> Gff;                          // dP^k as float-float, [dim][nnz]
     int tile_cap = 0;                          // max entries of a 256-row tile
+    int tile_cap_n = 0;                        // max entries of a 128-row tile
     // SELL-32 (sliced ELLPACK, slices of 32 rows, column-major inside a slice):
     // entry k of row 32 s + l sits at sell_ptr[s] + 32 k + l; short rows are
     // padded with their own index and a zero value.  sell_of_csr maps a CSR

@@ -372,7 +372,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // phase (coalesced reads of values and columns, one product per entry, results
 // in shared memory) and a row-parallel phase (one thread per row sums its
 // entries from shared memory and runs the row's epilogue with every lane busy).
-constexpr int kTile = kBlock;
 
 struct TileRange {
     int64_t r0;
@@ -380,12 +379,14 @@ struct TileRange {
     int32_t e0, e1;
 };
 
-// Loads the tile's row pointers into s_rp[0..nr] and returns its range.
+// Loads the tile's row pointers into s_rp[0..nr] and returns its range (R rows
+// per tile).
+template <int R = kTile>
 __device__ __forceinline__ TileRange load_tile(int64_t tile, int64_t n, const int32_t* __restrict__ rp,
                                                int32_t* s_rp) {
     TileRange t;
-    t.r0 = tile * kTile;
-    t.nr = (int)min((int64_t)kTile, n - t.r0);
+    t.r0 = tile * R;
+    t.nr = (int)min((int64_t)R, n - t.r0);
     for (int k = threadIdx.x; k <= t.nr; k += blockDim.x) s_rp[k] = rp[t.r0 + k];
     __syncthreads();
     t.e0 = s_rp[0];

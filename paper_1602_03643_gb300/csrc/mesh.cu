@@ -124,6 +124,10 @@ Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const in
         const int64_t r1 = std::min<int64_t>(n, r0 + kBlock);
         m->tile_cap = std::max<int>(m->tile_cap, row_ptr[r1] - row_ptr[r0]);
     }
+    for (int64_t r0 = 0; r0 < n; r0 += kTileN) {
+        const int64_t r1 = std::min<int64_t>(n, r0 + kTileN);
+        m->tile_cap_n = std::max<int>(m->tile_cap_n, row_ptr[r1] - row_ptr[r0]);
+    }
     // row_ptr and col carry 8 padding entries so that 16-byte aligned bulk copies
     // of a tile's range never read past the allocation
     {

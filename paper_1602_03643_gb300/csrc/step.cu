@@ -124,31 +124,31 @@ __global__ void __launch_bounds__(kBlock) k_cell_beta(StepData<P> a) {
 // - 0.5 C2_ij u_j^{n-2} + dP_ij p*_j), C1 from u^{n-1}, C2 from u^{n-2} (Eq. 21):
 // b - A u^{n-1} for b = (M/dt - nu K/2) u^{n-1} - 1.5 C1 u^{n-1} + 0.5 C2 u^{n-2}
 // + f ML - dP p*.
-template <class P, int D, bool ABE>
+template <class P, int D, bool ABE, int R>
 __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typename P::V> k_) {
     using V = typename P::V;
     using S = typename P::S;
     using Acc = typename P::Acc;
     constexpr int NB = ABE ? 2 : 1;
     extern __shared__ __align__(16) unsigned char dsm[];
-    V* s_t1 = reinterpret_cast<V*>(dsm);                       // [NB][max_row][kTile]
-    V* s_con = s_t1 + (size_t)NB * a.max_row * kTile;          // [tile_cap][D]
-    __shared__ int32_t s_rp[kTile + 1];
-    __shared__ V s_ub[NB][D][kTile];
-    __shared__ int32_t s_dir[kTile];
+    V* s_t1 = reinterpret_cast<V*>(dsm);                       // [NB][max_row][R]
+    V* s_con = s_t1 + (size_t)NB * a.max_row * R;          // [tile_cap][D]
+    __shared__ int32_t s_rp[R + 1];
+    __shared__ V s_ub[NB][D][R];
+    __shared__ int32_t s_dir[R];
     Acc part[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) acc_zero(part[k]);
     const V inv_d2 = (V)1 / (V)(D + 2);
     const int r = threadIdx.x;
-    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
-        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
+    for (int64_t tile = blockIdx.x; tile * R < a.n; tile += gridDim.x) {
+        const TileRange T = load_tile<R>(tile, a.n, a.rp, s_rp);
         const int64_t i = T.r0 + r;
         if (r < T.nr) {
             const int32_t len = s_rp[r + 1] - s_rp[r];
             for (int32_t sl = 0; sl < len; ++sl)
 #pragma unroll
-                for (int b = 0; b < NB; ++b) s_t1[((size_t)b * a.max_row + sl) * kTile + r] = 0;
+                for (int b = 0; b < NB; ++b) s_t1[((size_t)b * a.max_row + sl) * R + r] = 0;
             // incident cells 8 at a time: their indices and slots, then their
             // beta rows (one aligned 4-vector each), then the additions in cell
             // order (the same order as one at a time)
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
                     const V* bsrc = b == 0 ? a.beta : a.beta2;
-                    V* t = s_t1 + (size_t)b * a.max_row * kTile;
+                    V* t = s_t1 + (size_t)b * a.max_row * R;
                     Vec4A<V> bt[kU];
 #pragma unroll
                     for (int u = 0; u < kU; ++u) bt[u] = reinterpret_cast<const Vec4A<V>*>(bsrc)[c[u]];
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
                     for (int u = 0; u < kU; ++u) {
                         if (qb + u >= q1) break;
 #pragma unroll
-                        for (int m = 0; m <= D; ++m) t[((w[u] >> (8 * m)) & 0xffu) * kTile + r] += bt[u].v[m];
+                        for (int m = 0; m <= D; ++m) t[((w[u] >> (8 * m)) & 0xffu) * R + r] += bt[u].v[m];
                     }
                 }
             }
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
             s_dir[r] = a.dir_index[i];
         }
         __syncthreads();
-        for (int32_t e = T.e0 + r; e < T.e1; e += kTile) {
+        for (int32_t e = T.e0 + r; e < T.e1; e += kBlock) {
             const int rr = tile_row_of(s_rp, T.nr, e);
             const int32_t sl = e - s_rp[rr];
             const int64_t ii = T.r0 + rr;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
             }
             V cb[NB];
 #pragma unroll
-            for (int b = 0; b < NB; ++b) cb[b] = s_t1[((size_t)b * a.max_row + sl) * kTile + rr] + gdot[b] * inv_d2;
+            for (int b = 0; b < NB; ++b) cb[b] = s_t1[((size_t)b * a.max_row + sl) * R + rr] + gdot[b] * inv_d2;
             const V kv = a.K[e];
             // passive scalars: C(ubar), linear in the convecting velocity
             if (a.cbar) a.cbar[e] = ABE ? (V)1.5 * cb[0] - (V)0.5 * cb[NB - 1] : cb[0];
@@ -295,14 +295,14 @@ __device__ __forceinline__ void mirror_coefs(KrylovState* st, int k) {
 
 // Outer sweep: r = r0 - A Delta with float64-quality products (float-float in
 // the mixed path), convergence test, start of a new inner solve.
-template <class P, int D, int NR>
+template <class P, int D, int NR, int R>
 __global__ void __launch_bounds__(kBlock) k_bicg_outer(StepData<P> a, int k0, Ctl ctl) {
     using V = typename P::V;
     using S = typename P::S;
     using Acc = typename P::Acc;
     extern __shared__ __align__(16) unsigned char dsm[];
     Acc* s_prod = reinterpret_cast<Acc*>(dsm);                 // [tile_cap][NR]
-    __shared__ int32_t s_rp[kTile + 1];
+    __shared__ int32_t s_rp[R + 1];
     int live[NR];
 #pragma unroll
     for (int c = 0; c < NR; ++c) live[c] = !a.stu->col_done[k0 + c];
@@ -310,8 +310,8 @@ __global__ void __launch_bounds__(kBlock) k_bicg_outer(StepData<P> a, int k0, Ct
 #pragma unroll
     for (int c = 0; c < NR; ++c) acc_zero(part[c]);
     const int r = threadIdx.x;
-    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
-        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
+    for (int64_t tile = blockIdx.x; tile * R < a.n; tile += gridDim.x) {
+        const TileRange T = load_tile<R>(tile, a.n, a.rp, s_rp);
         tile_entries<4, Vec<Acc, NR>>(
             T,
             [&](int32_t e) {
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kBlock) k_bicg_dir(StepData<P> a, int k0) {
 // y = A x with the dot products needed next:
 //   MODE 0: v = A ph, <rhat, v>          -> alpha = rho / <rhat, v>
 //   MODE 1: t = A sh, <t, s>, <t, t>     -> omega = <t, s> / <t, t>
-template <class P, int D, int NR, int MODE>
+template <class P, int D, int NR, int MODE, int R>
 __global__ void __launch_bounds__(kBlock) k_bicg_spmm(StepData<P> a, int k0, Ctl ctl) {
     using V = typename P::V;
     using Acc = typename P::Acc;
@@ -423,13 +423,13 @@ __global__ void __launch_bounds__(kBlock) k_bicg_spmm(StepData<P> a, int k0, Ctl
     constexpr int NV = MODE == 0 ? NR : 2 * NR;
     extern __shared__ __align__(16) unsigned char dsm[];
     V* s_prod = reinterpret_cast<V*>(dsm);                     // [tile_cap][NR]
-    __shared__ int32_t s_rp[kTile + 1];
+    __shared__ int32_t s_rp[R + 1];
     const V* __restrict__ x = MODE == 0 ? a.ph : a.sh;
     V* __restrict__ y = MODE == 0 ? a.v : a.t;
     V part[NV] = {};
     const int r = threadIdx.x;
-    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
-        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
+    for (int64_t tile = blockIdx.x; tile * R < a.n; tile += gridDim.x) {
+        const TileRange T = load_tile<R>(tile, a.n, a.rp, s_rp);
         tile_entries<8, Vec<V, NR>>(
             T,
             [&](int32_t e) {
@@ -1809,7 +1809,7 @@ struct StepImplT final : StepImpl {
     Solver& Sv;
     StepData<P> a{};
     Consts<V> k_{};
-    int64_t tiles = 0;
+    int64_t tiles = 0, tiles_n = 0;
     size_t sm_asm = 0, sm_asm2 = 0, sm_out_u = 0, sm_out_u1 = 0, sm_spmm = 0, sm_spmm1 = 0, sm_outp = 0, sm_v1 = 0, sm_vd = 0;
     int g_asm = 1, g_asm2 = 1, g_out_u = 1, g_out_u1 = 1, g_spmm0 = 1, g_spmm1 = 1, g_spmm0_1 = 1, g_spmm1_1 = 1,
         g_rhs = 1, g_upd = 1, g_upd_c = 1, g_mspmv = 1, g_out_s = 1, g_spmm0_s = 1, g_spmm1_s = 1, g_sasm = 1;
@@ -1902,32 +1902,35 @@ struct StepImplT final : StepImpl {
         for (int k = 0; k < 3; ++k) k_.f[k] = (V)Sv.prm.f[k];
 
         tiles = (m.n + kTile - 1) / kTile;
+        tiles_n = (m.n + kTileN - 1) / kTileN;
         const size_t cap = (size_t)std::max(1, m.tile_cap);
-        sm_asm = (size_t)m.max_row * kTile * sizeof(V) + cap * D * sizeof(V);
-        sm_asm2 = 2 * (size_t)m.max_row * kTile * sizeof(V) + cap * D * sizeof(V);
-        sm_out_u = cap * D * sizeof(Acc);
-        sm_out_u1 = cap * sizeof(Acc);
-        sm_spmm = cap * D * sizeof(V);
-        sm_spmm1 = cap * sizeof(V);
+        const size_t cap_n = (size_t)std::max(1, m.tile_cap_n);
+        // assembly and BiCGStab products: narrow tiles (their per-entry staging)
+        sm_asm = (size_t)m.max_row * kTileN * sizeof(V) + cap_n * D * sizeof(V);
+        sm_asm2 = 2 * (size_t)m.max_row * kTileN * sizeof(V) + cap_n * D * sizeof(V);
+        sm_out_u = cap_n * D * sizeof(Acc);
+        sm_out_u1 = cap_n * sizeof(Acc);
+        sm_spmm = cap_n * D * sizeof(V);
+        sm_spmm1 = cap_n * sizeof(V);
         sm_outp = cap * sizeof(Acc);
         sm_v1 = cap * sizeof(V);
         sm_vd = cap * D * sizeof(V);
-        g_asm = tile_grid(k_assemble<P, D, false>, sm_asm, tiles);
-        if (Sv.prm.convection == OASIS_CONV_ABE) g_asm2 = tile_grid(k_assemble<P, D, true>, sm_asm2, tiles);
-        g_out_u = tile_grid(k_bicg_outer<P, D, D>, sm_out_u, tiles);
-        g_out_u1 = tile_grid(k_bicg_outer<P, D, 1>, sm_out_u1, tiles);
-        g_spmm0 = tile_grid(k_bicg_spmm<P, D, D, 0>, sm_spmm, tiles);
-        g_spmm1 = tile_grid(k_bicg_spmm<P, D, D, 1>, sm_spmm, tiles);
-        g_spmm0_1 = tile_grid(k_bicg_spmm<P, D, 1, 0>, sm_spmm1, tiles);
-        g_spmm1_1 = tile_grid(k_bicg_spmm<P, D, 1, 1>, sm_spmm1, tiles);
+        g_asm = tile_grid(k_assemble<P, D, false, kTileN>, sm_asm, tiles_n);
+        if (Sv.prm.convection == OASIS_CONV_ABE) g_asm2 = tile_grid(k_assemble<P, D, true, kTileN>, sm_asm2, tiles_n);
+        g_out_u = tile_grid(k_bicg_outer<P, D, D, kTileN>, sm_out_u, tiles_n);
+        g_out_u1 = tile_grid(k_bicg_outer<P, D, 1, kTileN>, sm_out_u1, tiles_n);
+        g_spmm0 = tile_grid(k_bicg_spmm<P, D, D, 0, kTileN>, sm_spmm, tiles_n);
+        g_spmm1 = tile_grid(k_bicg_spmm<P, D, D, 1, kTileN>, sm_spmm, tiles_n);
+        g_spmm0_1 = tile_grid(k_bicg_spmm<P, D, 1, 0, kTileN>, sm_spmm1, tiles_n);
+        g_spmm1_1 = tile_grid(k_bicg_spmm<P, D, 1, 1, kTileN>, sm_spmm1, tiles_n);
         g_sell = (int)std::max<int64_t>(1, ((m.n + 31) / 32 + kBlock / 32 - 1) / (kBlock / 32));
         g_rhs = tile_grid(k_pressure_rhs<P, D>, sm_outp, tiles);
         g_upd = tile_grid(k_update<P, D, false>, sm_vd, tiles);
         g_upd_c = tile_grid(k_update<P, D, true>, 0, tiles);
         g_mspmv = tile_grid(k_mass_spmv<P, D>, sm_vd, tiles);
-        g_out_s = tile_grid(k_bicg_outer<P, 1, 1>, sm_out_u1, tiles);
-        g_spmm0_s = tile_grid(k_bicg_spmm<P, 1, 1, 0>, sm_spmm1, tiles);
-        g_spmm1_s = tile_grid(k_bicg_spmm<P, 1, 1, 1>, sm_spmm1, tiles);
+        g_out_s = tile_grid(k_bicg_outer<P, 1, 1, kTileN>, sm_out_u1, tiles_n);
+        g_spmm0_s = tile_grid(k_bicg_spmm<P, 1, 1, 0, kTileN>, sm_spmm1, tiles_n);
+        g_spmm1_s = tile_grid(k_bicg_spmm<P, 1, 1, 1, kTileN>, sm_spmm1, tiles_n);
         g_sasm = tile_grid(k_scalar_assemble<P>, sm_v1, tiles);
         ge_n = elem_grid(m.n);
         ge_red = red_grid(m.n);
@@ -1939,10 +1942,10 @@ struct StepImplT final : StepImpl {
         const int pa = Sv.prof_begin(s, OASIS_PROF_ASSEMBLE);
         if (Sv.prm.convection == OASIS_CONV_ABE) {
             k_cell_beta<P, D, true><<<ge_c, kBlock, 0, s>>>(a);
-            k_assemble<P, D, true><<<g_asm2, kBlock, sm_asm2, s>>>(a, k_);
+            k_assemble<P, D, true, kTileN><<<g_asm2, kBlock, sm_asm2, s>>>(a, k_);
         } else {
             k_cell_beta<P, D, false><<<ge_c, kBlock, 0, s>>>(a);
-            k_assemble<P, D, false><<<g_asm, kBlock, sm_asm, s>>>(a, k_);
+            k_assemble<P, D, false, kTileN><<<g_asm, kBlock, sm_asm, s>>>(a, k_);
         }
         Sv.prof_end(s, pa);
         OASIS_CUDA(cudaGetLastError());
@@ -1981,18 +1984,18 @@ struct StepImplT final : StepImpl {
         Sv.run_loops(
             s, graph, which,
             [&](cudaStream_t ss_, const Loop& lp) {
-                k_bicg_outer<P, DD, NR><<<G.go, kBlock, G.so, ss_>>>(q, k0, ctl_u(lp));
+                k_bicg_outer<P, DD, NR, kTileN><<<G.go, kBlock, G.so, ss_>>>(q, k0, ctl_u(lp));
                 OASIS_CUDA(cudaGetLastError());
             },
             [&](cudaStream_t ss_, const Loop& lp) {
                 const Ctl c = ctl_u(lp);
                 k_bicg_dir<P, DD, NR><<<ge_n, kBlock, 0, ss_>>>(q, k0);
                 int pb = Sv.prof_begin(ss_, OASIS_PROF_BICG_SPMM);
-                k_bicg_spmm<P, DD, NR, 0><<<G.gs0, kBlock, G.ss, ss_>>>(q, k0, c);
+                k_bicg_spmm<P, DD, NR, 0, kTileN><<<G.gs0, kBlock, G.ss, ss_>>>(q, k0, c);
                 Sv.prof_end(ss_, pb);
                 k_bicg_s<P, DD, NR><<<ge_n, kBlock, 0, ss_>>>(q, k0);
                 pb = Sv.prof_begin(ss_, OASIS_PROF_BICG_SPMM);
-                k_bicg_spmm<P, DD, NR, 1><<<G.gs1, kBlock, G.ss, ss_>>>(q, k0, c);
+                k_bicg_spmm<P, DD, NR, 1, kTileN><<<G.gs1, kBlock, G.ss, ss_>>>(q, k0, c);
                 Sv.prof_end(ss_, pb);
                 k_bicg_xr<P, DD, NR><<<ge_red, kBlock, 0, ss_>>>(q, k0, c);
                 OASIS_CUDA(cudaGetLastError());
