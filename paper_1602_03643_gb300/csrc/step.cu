@@ -526,15 +526,24 @@ __global__ void __launch_bounds__(kBlock) k_bicg_xr(StepData<P> a, int k0, Ctl c
         omega[c] = coef<P>(a.stu->omega[k0 + c], a.stu->omega_f[k0 + c]);
     }
     V part[2 * NR] = {};
+    // distinct arrays: restrict lets the loads of later rows start early
+    V* __restrict__ dl = a.dl;
+    V* __restrict__ rr_ = a.r;
+    const V* __restrict__ ph = a.ph;
+    const V* __restrict__ sh = a.sh;
+    const V* __restrict__ sv_ = a.s;
+    const V* __restrict__ tv = a.t;
+    const V* __restrict__ rh = a.rh;
+#pragma unroll 4
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < NR; ++c) {
             if (!act[c]) continue;
             const size_t o = (size_t)i * D + k0 + c;
-            a.dl[o] += alpha[c] * a.ph[o] + omega[c] * a.sh[o];
-            const V rv = a.s[o] - omega[c] * a.t[o];
-            a.r[o] = rv;
-            part[c] += a.rh[o] * rv;
+            dl[o] += alpha[c] * ph[o] + omega[c] * sh[o];
+            const V rv = sv_[o] - omega[c] * tv[o];
+            rr_[o] = rv;
+            part[c] += rh[o] * rv;
             part[NR + c] += rv * rv;
         }
     }
@@ -1225,15 +1234,22 @@ __global__ void __launch_bounds__(kBlock) k_amg_cg_update(StepData<P> a, Ctl ctl
     const V alpha = coef<P>(a.stp->alpha[0], a.stp->alpha_f[0]);
     const V beta = coef<P>(a.stp->beta[0], a.stp->beta_f[0]);
     V part[1] = {};
+    const V* __restrict__ au = a.au;
+    const V* __restrict__ aw = a.aw;
+    V* __restrict__ pp = a.pp;
+    V* __restrict__ as_ = a.as;
+    V* __restrict__ pdl = a.pdl;
+    V* __restrict__ ar = a.ar;
+#pragma unroll 4
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const V u = a.au[i], w = a.aw[i];
-        const V pv = beta == V(0) ? u : u + beta * a.pp[i];
-        const V sv = beta == V(0) ? w : w + beta * a.as[i];
-        a.pp[i] = pv;
-        a.as[i] = sv;
-        a.pdl[i] += alpha * pv;
-        const V r = a.ar[i] - alpha * sv;
-        a.ar[i] = r;
+        const V u = au[i], w = aw[i];
+        const V pv = beta == V(0) ? u : u + beta * pp[i];
+        const V sv = beta == V(0) ? w : w + beta * as_[i];
+        pp[i] = pv;
+        as_[i] = sv;
+        pdl[i] += alpha * pv;
+        const V r = ar[i] - alpha * sv;
+        ar[i] = r;
         part[0] += r * r;
     }
     double tot[1];
