@@ -269,10 +269,12 @@ def run_ours(args, rank, world):
     # int32 columns; N dofs, nnz pattern entries)
     cands = {}
     if pc == capi.OASIS_PC_AMG:
-        # w = K u on SELL-32 with three dot products: K values + columns, u
-        # gathered (4 N), r read (4 N), w written (4 N), slice pointers/lengths
-        cands["pcg_spmv"] = ("k_amg_cg_spmv<Mixed> (multigrid CG: w = K u on SELL-32 + 3 dots)", None,
-                             8 * nnz + 12 * N + 8 * n_slices)
+        # w = K u on SELL-32 with three dot products: K values + columns (16-bit
+        # offsets where the mesh has them), u gathered (4 N), r read (4 N), w
+        # written (4 N), slice pointers/lengths
+        have16 = any(c["col16"] and c["us"] > 0 for c in tun_e["candidates"])
+        cands["pcg_spmv"] = ("k_amg_cg_spmv<Mixed> (multigrid CG: w = K u on SELL-32 + 3 dots)",
+                             {"col16": bool(have16)}, (4 + (2 if have16 else 4)) * nnz + 12 * N + 8 * n_slices)
     else:
         shape = tun_e["candidates"][tun_e["chosen"] - 1]
         col_bytes = 2 if shape["col16"] else 4
@@ -303,11 +305,17 @@ def run_ours(args, rank, world):
                 "algorithmic_bytes_per_launch": nbytes, "launches_timed": n_l,
                 "avg_launch_us": (ms_l / n_l * 1e3) if n_l else None,
                 "share_of_timed_families": ms_l / max(sum(m for _, m in fam_t.values()), 1e-30),
-                "traffic": None,
+                "traffic": measured_traffic.get((args.workload, fam, args.pc), (None,))[0],
+                "traffic_source": measured_traffic.get((args.workload, fam, args.pc), (None, None))[1],
                 "note": ("algorithmic bytes %.1f MB per launch vs 129 MB L2: at this size the matrix and vectors "
                          "stay L2-resident across iterations" % (nbytes / 1e6))
                 if nbytes < 100e6 else "working set larger than L2"}
 
+    # DRAM bytes per launch from ncu captures of these kernels on this workload
+    # (cold caches), valid for the kernels as they stand
+    measured_traffic = {("tg3d_64", "bicg_spmm", "amg"): (39.88e6, "profiles/k_bicg_spmm_tg3d64_traffic.md"),
+                        ("tg3d_64", "bicg_spmm", "jacobi"): (39.88e6, "profiles/k_bicg_spmm_tg3d64_traffic.md"),
+                        ("tg3d_64", "pcg_spmv", "amg"): (26.65e6, "profiles/k_bicg_spmm_tg3d64_traffic.md")}
     fam_t = {f: fam[f] for f in cands}
     dominant = max(cands, key=lambda f: fam_t[f][1])
     roofline = roof(dominant)
