@@ -47,8 +47,10 @@ def _workload(name):
         return WP.taylor_green_2d(32)
     if name == "channel":
         return WP.channel()
-    if name.startswith("stress128"):
-        return WP.stress_cube(128, ordering=name.split("_")[1] if "_" in name else "natural")
+    if name.startswith("stress"):
+        # stress<n>[_<ordering>], e.g. stress128_rcm (the 128^3 configuration) or a smaller cube
+        head, _, order = name.partition("_")
+        return WP.stress_cube(int(head[len("stress"):] or 128), ordering=order or "natural")
     raise ValueError(name)
 
 
