@@ -422,6 +422,103 @@ def run_ours(args, rank, world):
 
 
 # ---------------------------------------------------------------------- oracle (CPU)
+def run_guess_study(args):
+    """The learned-guess experiment on the channel (held-out seed): the network is
+    trained on samples that the plain solver records in runs from other seeds,
+    then the held-out run is stepped with the zero, previous-phi and learned
+    guesses; every pressure solve ends at the same 1e-8 residual.  Reported:
+    mean CG iterations and device steps/s of each form (one GPU)."""
+    import ctypes
+    import numpy as np
+    import torch
+    from paper_1602_03643_gb300 import build, capi
+    from paper_1602_03643_gb300.driver import IPCSRun
+    from paper_1602_03643_gb300.guess import GuessNet
+    from workloads import problems as WP
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def make(seed, guess):
+        pb = WP.channel(seed=seed)
+        run = IPCSRun(pb, precision=capi.OASIS_MIXED, rtol_u=RTOL, rtol_p=RTOL, max_it_u=20000,
+                      max_it_p=200000, inner_rtol=args.inner_rtol, use_graph=1, guess=guess,
+                      pressure_pc=capi.OASIS_PC_AMG, stream=stream)
+        run.set_dirichlet_for_next_step()
+        return run
+
+    t0 = time.perf_counter()
+    samples = []
+    train_seeds = list(range(100, 100 + args.study_seeds))
+    with torch.cuda.stream(stream):
+        for sd in train_seeds:
+            run = make(sd, capi.OASIS_GUESS_PREV_PHI)
+            run.record_guess(True)
+            for k in range(args.study_steps):
+                capi.oasis_step(run.solver, stream, want_stats=False)
+                if k >= 2:
+                    samples.append(run.guess_sample())
+            run.record_guess(False)
+            torch.cuda.synchronize(dev)
+            run.close()
+    t_collect = time.perf_counter() - t0
+    test = {}
+    for form, guess in (("zero", capi.OASIS_GUESS_ZERO), ("previous_phi", capi.OASIS_GUESS_PREV_PHI),
+                        ("learned", capi.OASIS_GUESS_LEARNED)):
+        run = make(110, guess)
+        net = None
+        if form == "learned":
+            with torch.cuda.stream(stream):
+                # the records and the network live on the mesh of the run that uses them
+                net = GuessNet(run.mesh, run.n, seed=1)
+                t1 = time.perf_counter()
+                losses = net.fit(samples, epochs=args.train_epochs, lr=2e-3)
+                torch.cuda.synchronize(dev)
+                t_fit = time.perf_counter() - t1
+                run.attach_guess_net(net)
+        for _ in range(args.warmup):
+            capi.oasis_step(run.solver, stream, want_stats=False)
+        torch.cuda.synchronize(dev)
+        evs, stats = [], []
+        with torch.cuda.stream(stream):
+            for _ in range(args.study_test_steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                capi.oasis_step(run.solver, stream, want_stats=False)
+                e1.record(stream)
+                evs.append((e0, e1))
+                # a failed solve is counted, not raised (its stats are still filled)
+                st = capi.oasis_step_stats()
+                capi.lib().oasis_last_stats(run.solver, ctypes.byref(st))
+                stats.append(st.as_dict())
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        it_p = [st["it_p"] for st in stats]
+        entry = {"steps_per_s": 1e3 * len(evs) / ms, "ms_per_step": ms / len(evs),
+                 "it_p_mean": float(np.mean(it_p)), "it_u_mean": float(np.mean([max(st["it_u"]) for st in stats])),
+                 "failed_steps": sum(st["status"] != 0 for st in stats),
+                 "first_failed_step": next((k for k, st in enumerate(stats) if st["status"] != 0), None),
+                 "statuses": sorted({st["status"] for st in stats})}
+        if form == "learned":
+            gr = np.array([st["guess_res"] for st in stats])
+            entry |= {"used_fraction": float(np.mean([st["guess_used"] == capi.OASIS_GUESS_LEARNED
+                                                      for st in stats])),
+                      "residual_ratio_mean": float(np.mean(gr[:, 0] / np.maximum(gr[:, 1], 1e-300))),
+                      "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1]),
+                      "fit_s": t_fit}
+            net.close()
+        run.close()
+        test[form] = entry
+    return {"study": "learned pressure guess, channel 128x96x96, held-out seed 110",
+            "train": {"seeds": train_seeds, "steps_per_seed": args.study_steps, "samples": len(samples),
+                      "epochs": args.train_epochs, "collect_s": t_collect},
+            "test": {"seed": 110, "warmup": args.warmup, "steps": args.study_test_steps} | test,
+            "solver": "mixed, 3-RHS BiCGStab, multigrid CG, CUDA graph, every solve to 1e-8",
+            "data": "synthetic (seeded perturbed Poiseuille flow in the channel)"}
+
+
 def oracle_options(args):
     """The scheme options of the run, in the oracle's terms."""
     return {"inner_iters": max(1, getattr(args, "inner_iters", 1)),
@@ -515,8 +612,16 @@ def main():
     ap.add_argument("--eager", action="store_true",
                     help="run the headline form as eager launches (profilers cannot see kernels "
                          "inside graphs with conditional nodes)")
+    ap.add_argument("--guess-study", action="store_true",
+                    help="the learned-guess experiment on the channel with a held-out seed (one GPU)")
+    ap.add_argument("--study-seeds", type=int, default=6)
+    ap.add_argument("--study-steps", type=int, default=40)
+    ap.add_argument("--study-test-steps", type=int, default=40)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.guess_study:
+        print(json.dumps(run_guess_study(args)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
