@@ -3,14 +3,15 @@
  * (IPCS, "ABCN" convection) Navier-Stokes time step on simplex meshes.
  *
  * The scheme is the fractional-step method of Sec. 2 (Eqs. 17-19, convection
- * Eq. 22, Algorithm 1 with one inner iteration), discretised with P1 elements
- * for velocity and pressure as in Sec. 3, and organised as the high-performance
- * solver of Sec. 5: constant matrices M, K, dP^k preassembled once, the
- * convection matrix reassembled every step into the fixed sparsity pattern and
- * combined with M and K by Algorithm 2, a Krylov solve per velocity component
- * with one shared coefficient matrix (Eq. 35), a pressure-correction Poisson
- * solve (Sec. 5, the algebraic form of Eq. 18), and the lumped-mass velocity
- * update (Sec. 5, "lumping").
+ * Eq. 22 or Eq. 21, Algorithm 1 with one or more inner iterations), discretised
+ * with P1 elements for velocity and pressure as in Sec. 3, and organised as the
+ * high-performance solver of Sec. 5: constant matrices M, K, dP^k preassembled
+ * once, the convection matrix reassembled every step into the fixed sparsity
+ * pattern and combined with M and K by Algorithm 2, a Krylov solve per velocity
+ * component with one shared coefficient matrix (Eq. 35), a pressure-correction
+ * Poisson solve (Sec. 5, the algebraic form of Eq. 18), the velocity update
+ * with the lumped or the consistent mass matrix (Sec. 5), and optional passive
+ * scalars (the scalar equation of Sec. 3).
  *
  * Conventions shared by every entry point
  *   - Return value: 0 on success, a negative OASIS_E* code on failure.  No C++
@@ -20,8 +21,12 @@
  *     All device work of a call is ordered on that stream.
  *   - Host arrays are read during the call only and never retained.  Device
  *     memory behind oasis_mesh / oasis_solver is allocated by the library at
- *     creation time and released by the matching destroy call; no entry point
- *     allocates device memory after creation.
+ *     creation time (and by the configuration call oasis_solver_set_scalars)
+ *     and released by the matching destroy call.  The field copies and the
+ *     kernels of oasis_step allocate no device memory; the first oasis_step of
+ *     a graph-mode solver captures and instantiates the step's CUDA graph, and
+ *     the test hooks oasis_get_tentative_system and oasis_amg_apply use
+ *     temporary buffers.
  *   - Fields are float64, component-major: u[k * n_dofs + i] is component k of
  *     dof i.  Indices are int32, zero based.
  *   - Handles are not reentrant: calls on one solver must not overlap.

@@ -547,6 +547,7 @@ int oasis_solver_set_scalars(oasis_solver* solver, int32_t n_scalars, const doub
         S->r0c.alloc(on ? sb * n : 0, s);
         S->dc.alloc(on ? sb * n : 0, s);
         for (auto& w : S->sw) w.alloc(on ? vb * n : 0, s);
+        S->cstage.alloc(on ? (size_t)n_scalars * std::max<int64_t>(n, n_dirichlet) : 0);
         OASIS_CUDA(cudaMemsetAsync(S->st.p + 3, 0, OASIS_MAX_SCALARS * sizeof(KrylovState), s));
         OASIS_CUDA(cudaStreamSynchronize(s));
         S->impl->scalars_changed();
@@ -561,11 +562,9 @@ int oasis_set_scalar_fields(oasis_solver* solver, const double* c, int32_t on_de
         cudaStream_t s = as_stream(stream);
         const int64_t count = S->m->n * S->ns;
         const double* src = c;
-        DBuf<double> tmp;
         if (!on_device) {
-            tmp.alloc(count);
-            OASIS_CUDA(cudaMemcpyAsync(tmp.p, c, count * sizeof(double), cudaMemcpyHostToDevice, s));
-            src = tmp.p;
+            OASIS_CUDA(cudaMemcpyAsync(S->cstage.p, c, count * sizeof(double), cudaMemcpyHostToDevice, s));
+            src = S->cstage.p;
         }
         S->impl->to_state(s, src, ST_C, count, 1);
         OASIS_CUDA(cudaStreamSynchronize(s));
@@ -583,10 +582,8 @@ int oasis_get_scalar_fields(oasis_solver* solver, double* c, int32_t on_device, 
             S->impl->from_state(s, c, ST_C, count, 1);
             return;
         }
-        DBuf<double> tmp;
-        tmp.alloc(count);
-        S->impl->from_state(s, tmp.p, ST_C, count, 1);
-        OASIS_CUDA(cudaMemcpyAsync(c, tmp.p, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+        S->impl->from_state(s, S->cstage.p, ST_C, count, 1);
+        OASIS_CUDA(cudaMemcpyAsync(c, S->cstage.p, count * sizeof(double), cudaMemcpyDeviceToHost, s));
         OASIS_CUDA(cudaStreamSynchronize(s));
     });
 }
@@ -601,11 +598,9 @@ int oasis_set_scalar_dirichlet(oasis_solver* solver, const double* g, int32_t on
         cudaStream_t s = as_stream(stream);
         const int64_t count = S->n_sdir * S->ns;
         const double* src = g;
-        DBuf<double> tmp;
         if (!on_device) {
-            tmp.alloc(count);
-            OASIS_CUDA(cudaMemcpyAsync(tmp.p, g, count * sizeof(double), cudaMemcpyHostToDevice, s));
-            src = tmp.p;
+            OASIS_CUDA(cudaMemcpyAsync(S->cstage.p, g, count * sizeof(double), cudaMemcpyHostToDevice, s));
+            src = S->cstage.p;
         }
         S->impl->to_state(s, src, ST_GC, count, 1);
         OASIS_CUDA(cudaStreamSynchronize(s));

@@ -155,6 +155,7 @@ struct Solver {
     RBuf dinvAc;                                                       // V [n]
     RBuf r0c, dc;                                                      // S [n]
     RBuf sw[9];                                                        // V [n]: BiCGStab work
+    DBuf<double> cstage;                                               // [ns][max(n, n_sdir)] host copies
     AmgWork amgw;                                                      // V-cycle work vectors
     DBuf<float> feat, gy;                                              // learned-guess features / output
     struct Net* net = nullptr;                                         // attached network (not owned)
