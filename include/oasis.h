@@ -94,9 +94,11 @@ typedef struct oasis_params {
     int32_t use_graph;     /* 1: the whole step runs as one CUDA graph, Krylov loops as
                               conditional WHILE nodes; 0: eager launches with host polls */
     int32_t guess;         /* OASIS_GUESS_* */
-    int32_t spmv_variant;  /* shape of the pressure-CG iteration kernel: 0 = autotune at
-                              solver creation (every candidate timed on this matrix, the
-                              fastest kept); k >= 1 = candidate k of oasis_get_tuning */
+    int32_t spmv_variant;  /* shape of the pressure-CG product kernel (the fused Jacobi
+                              iteration, or the multigrid CG product with OASIS_PC_AMG):
+                              0 = autotune at solver creation (every candidate timed on
+                              this matrix, the fastest kept); k >= 1 = candidate k of
+                              oasis_get_tuning */
     int32_t pressure_pc;   /* OASIS_PC_JACOBI or OASIS_PC_AMG (preconditioner of the
                               pressure CG) */
     int32_t inner_iters;   /* inner velocity/pressure iterations of Algorithm 1 (0 or 1 =
@@ -138,8 +140,10 @@ typedef struct oasis_params {
 #define OASIS_PC_JACOBI 0
 #define OASIS_PC_AMG 1
 
-/* Candidate shapes of the pressure-CG iteration kernel (SELL-32, one warp per
- * 32 rows) and what the autotuner measured.  A shape is the number of entries
+/* Candidate shapes of the pressure-CG product kernel (SELL-32, one warp per
+ * 32 rows; with OASIS_PC_AMG the multigrid CG product, whose candidates vary
+ * the entries per lane and the blocks per SM only) and what the autotuner
+ * measured.  A shape is the number of entries
  * per lane whose column/value loads are issued before their gathers, the
  * resident blocks per SM that the register budget is sized for, whether the
  * next chunk's loads are issued before the current products (prefetch), and

@@ -1272,8 +1272,8 @@ __global__ void __launch_bounds__(kBlock) k_amg_cg_update(StepData<P> a, Ctl ctl
 // w = K u on SELL-32 with gamma = <r, u>, delta = <w, u> and <r, r>.  START:
 // first iteration of a sweep (alpha = gamma / delta, beta = 0); else the
 // Chronopoulos-Gear update of alpha, beta and the inner stopping test.
-template <class P, bool START, bool D16>
-__global__ void __launch_bounds__(kBlock) k_amg_cg_spmv(StepData<P> a, Ctl ctl) {
+template <class P, bool START, bool D16, int C = 4, int MINB = 1>
+__global__ void __launch_bounds__(kBlock, MINB) k_amg_cg_spmv(StepData<P> a, Ctl ctl) {
     using V = typename P::V;
     if (a.stp->col_done[0] || a.stp->in_done[0]) return;
     V part[3] = {};
@@ -1282,21 +1282,21 @@ __global__ void __launch_bounds__(kBlock) k_amg_cg_spmv(StepData<P> a, Ctl ctl) 
     if (sell_lane(a, i, len, base, lane)) {
         const int32_t row = (int32_t)i;
         V w = 0;
-        for (int k = 0; k < len; k += 4) {
-            int32_t j[4];
-            V kv[4];
+        for (int k = 0; k < len; k += C) {
+            int32_t j[C];
+            V kv[C];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < C; ++u) {
                 const int64_t q = base + 32 * (int64_t)(k + u);
                 const bool ok = k + u < len;
                 j[u] = ok ? sell_j<D16>(a, q, row) : 0;
                 kv[u] = ok ? a.Ks[q] : V(0);
             }
-            V g[4];
+            V g[C];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) g[u] = a.au[j[u]];
+            for (int u = 0; u < C; ++u) g[u] = a.au[j[u]];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < C; ++u)
                 if (k + u < len) w += kv[u] * g[u];
         }
         if (i < a.n) {
@@ -1328,6 +1328,26 @@ __global__ void __launch_bounds__(kBlock) k_amg_cg_spmv(StepData<P> a, Ctl ctl) 
         }
     }
 }
+
+// Candidate shapes of the multigrid CG product: entries per lane whose column
+// and value loads are issued together (C) and the blocks per SM the registers
+// are sized for.  The grid (one warp per slice) and every sum's order are the
+// same for all shapes: same bits.
+template <class P>
+struct AmgVariant {
+    void (*fn16)(StepData<P>, Ctl);
+    void (*fn32)(StepData<P>, Ctl);
+    int chunk, minb;
+};
+#define OASIS_AMGV(C, B) {k_amg_cg_spmv<P, false, true, C, B>, k_amg_cg_spmv<P, false, false, C, B>, C, B}
+constexpr int kAmgVariants = 4;
+template <class P>
+static const AmgVariant<P>* amg_variant_table() {
+    static const AmgVariant<P> t[kAmgVariants] = {OASIS_AMGV(4, 1), OASIS_AMGV(2, 8), OASIS_AMGV(4, 8),
+                                                  OASIS_AMGV(8, 4)};
+    return t;
+}
+#undef OASIS_AMGV
 
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_pcg_correct(StepData<P> a) {
@@ -1832,6 +1852,8 @@ struct StepImplT final : StepImpl {
     int ge_n = 1, ge_nd = 1, ge_c = 1, ge_red = 1;
     int g_sell = 1;
     int iter_v = 0;                                   // chosen CG iteration shape
+    int amg_v = 0;                                    // chosen multigrid CG product shape
+    double amg_us[kAmgVariants] = {0};
     double tune_us[OASIS_MAX_VARIANTS] = {0};
     int it_grid[OASIS_MAX_VARIANTS] = {0}, it_block[OASIS_MAX_VARIANTS] = {0};
     size_t it_smem[OASIS_MAX_VARIANTS] = {0};
@@ -2132,8 +2154,8 @@ struct StepImplT final : StepImpl {
                     k_amg_cg_update<P><<<ge_red, kBlock, 0, ss>>>(a, c);
                     vcycle(ss);
                     const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
-                    if (a.sell_dcol) k_amg_cg_spmv<P, false, true><<<g_sell, kBlock, 0, ss>>>(a, c);
-                    else k_amg_cg_spmv<P, false, false><<<g_sell, kBlock, 0, ss>>>(a, c);
+                    const AmgVariant<P>& av = amg_variant_table<P>()[amg_v];
+                    (a.sell_dcol ? av.fn16 : av.fn32)<<<g_sell, kBlock, 0, ss>>>(a, c);
                     Sv.prof_end(ss, pq);
                     OASIS_CUDA(cudaGetLastError());
                 },
@@ -2272,7 +2294,51 @@ struct StepImplT final : StepImpl {
     // kept) against a scratch Krylov state, so the solver's own state is not
     // touched; the iteration buffers hold no solve yet.  Every shape computes
     // the same bits, so only speed decides.
+    // the multigrid CG product's shapes, timed on this matrix like the fused
+    // Jacobi iteration's (forced = k >= 1 takes shape k untimed)
+    void tune_amg(cudaStream_t s, int forced) {
+        OASIS_CHECK(forced <= kAmgVariants, OASIS_EINVAL, "spmv_variant: no such candidate");
+        for (auto& u : amg_us) u = 0.0;
+        if (forced >= 1) {
+            amg_v = forced - 1;
+            return;
+        }
+        const AmgVariant<P>* t = amg_variant_table<P>();
+        DBuf<KrylovState> scratch;
+        scratch.alloc(1);
+        StepData<P> d = a;
+        d.stp = scratch.p;
+        const Ctl c{};
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        OASIS_CUDA(cudaEventCreate(&e0));
+        OASIS_CUDA(cudaEventCreate(&e1));
+        constexpr int kWarm = 2, kTimed = 7;
+        int best = 0;
+        for (int v = 0; v < kAmgVariants; ++v) {
+            float ts[kTimed];
+            for (int r = 0; r < kWarm + kTimed; ++r) {
+                OASIS_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(KrylovState), s));
+                OASIS_CUDA(cudaEventRecord(e0, s));
+                (a.sell_dcol ? t[v].fn16 : t[v].fn32)<<<g_sell, kBlock, 0, s>>>(d, c);
+                OASIS_CUDA(cudaGetLastError());
+                OASIS_CUDA(cudaEventRecord(e1, s));
+                OASIS_CUDA(cudaEventSynchronize(e1));
+                if (r >= kWarm) OASIS_CUDA(cudaEventElapsedTime(&ts[r - kWarm], e0, e1));
+            }
+            std::sort(ts, ts + kTimed);
+            amg_us[v] = 1e3 * (double)ts[kTimed / 2];
+            if (amg_us[v] < amg_us[best]) best = v;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        amg_v = best;
+    }
+
     void tune(cudaStream_t s, int forced) override {
+        if (Sv.prm.pressure_pc == OASIS_PC_AMG) {
+            tune_amg(s, forced);
+            return;
+        }
         int count = 0;
         const IterVariant<P>* t = iter_variant_table<P>(count);
         OASIS_CHECK(forced <= count, OASIS_EINVAL, "spmv_variant: no such candidate");
@@ -2320,6 +2386,21 @@ struct StepImplT final : StepImpl {
     }
 
     void tuning(oasis_tuning* out) const override {
+        if (Sv.prm.pressure_pc == OASIS_PC_AMG) {
+            const AmgVariant<P>* t = amg_variant_table<P>();
+            out->n_variants = kAmgVariants;
+            out->chosen = amg_v + 1;
+            for (int v = 0; v < kAmgVariants; ++v) {
+                out->chunk[v] = t[v].chunk;
+                out->min_blocks[v] = t[v].minb;
+                out->prefetch[v] = 0;
+                out->col16[v] = a.sell_dcol != nullptr;
+                out->streamed[v] = 0;
+                out->warps_per_block[v] = kBlock / 32;
+                out->us[v] = amg_us[v];
+            }
+            return;
+        }
         int count = 0;
         const IterVariant<P>* t = iter_variant_table<P>(count);
         out->n_variants = count;

@@ -408,15 +408,18 @@ def test_consistent_update_graph_equals_eager_bitwise():
         np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("pc", [0, 1])
 @pytest.mark.parametrize("precision,case", [(0, "stress"), (1, "stress"), (1, "channel")])
-def test_cg_shapes_bitwise_equal_and_tuned(precision, case):
-    """Every candidate shape of the CG iteration kernel (including 16-bit column
-    offsets taken modulo n, which the periodic channel needs) gives the same
-    bits; the autotuner timed every candidate and kept the fastest."""
+def test_cg_shapes_bitwise_equal_and_tuned(precision, case, pc):
+    """Every candidate shape of the pressure-CG product kernel -- the fused
+    Jacobi iteration (pc 0; including 16-bit column offsets taken modulo n,
+    which the periodic channel needs) or the multigrid CG product (pc 1) --
+    gives the same bits; the autotuner timed every candidate and kept the
+    fastest."""
     from paper_1602_03643_gb300.driver import IPCSRun
     c = capi()
     pb = WP.stress_cube(12, ordering="random") if case == "stress" else WP.channel(nx=12, ny=9, nz=10)
-    run = IPCSRun(pb, precision=precision, rtol_u=1e-9, rtol_p=1e-9, use_graph=1)
+    run = IPCSRun(pb, precision=precision, rtol_u=1e-9, rtol_p=1e-9, use_graph=1, pressure_pc=pc)
     try:
         tun = c.oasis_get_tuning(run.solver)
     finally:
@@ -427,7 +430,8 @@ def test_cg_shapes_bitwise_equal_and_tuned(precision, case):
     assert cands[tun["chosen"] - 1]["us"] == min(x["us"] for x in cands)
     out = []
     for v in range(1, len(cands) + 1):
-        run = IPCSRun(pb, precision=precision, rtol_u=1e-9, rtol_p=1e-9, use_graph=1, spmv_variant=v)
+        run = IPCSRun(pb, precision=precision, rtol_u=1e-9, rtol_p=1e-9, use_graph=1, spmv_variant=v,
+                      pressure_pc=pc)
         try:
             assert c.oasis_get_tuning(run.solver)["chosen"] == v
             st = run.step(3)
