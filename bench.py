@@ -316,8 +316,7 @@ def run_ours(args, rank, world):
     # DRAM bytes per launch from ncu captures of these kernels on this workload
     # (cold caches), valid for the kernels as they stand
     measured_traffic = {("tg3d_64", "bicg_spmm", "amg"): (39.88e6, "profiles/k_bicg_spmm_tg3d64_traffic.md"),
-                        ("tg3d_64", "bicg_spmm", "jacobi"): (39.88e6, "profiles/k_bicg_spmm_tg3d64_traffic.md"),
-                        ("tg3d_64", "pcg_spmv", "amg"): (26.65e6, "profiles/k_bicg_spmm_tg3d64_traffic.md")}
+                        ("tg3d_64", "bicg_spmm", "jacobi"): (39.88e6, "profiles/k_bicg_spmm_tg3d64_traffic.md")}
     fam_t = {f: fam[f] for f in cands}
     dominant = max(cands, key=lambda f: fam_t[f][1])
     roofline = roof(dominant)
