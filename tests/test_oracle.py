@@ -453,3 +453,23 @@ def test_scalar_source_and_constants():
     s = o.run(3)
     np.testing.assert_allclose(s.c[0], 3 * 0.05 * 0.7, rtol=0, atol=1e-13)
     np.testing.assert_allclose(s.c[1], 2.5, rtol=0, atol=1e-13)
+
+
+def test_consistent_update_conserves_the_mean_velocity():
+    """On a periodic mesh sum_i (dP^k phi)_i = int d_k phi_h = 0, so the
+    consistent update keeps int u_h = 1^T M u exactly (M u^n = M u^I - dt dP^k phi),
+    and the lumped update keeps sum_i ML_i u_i = 1^T M u the same way; both from
+    the same step data."""
+    pb = WP.taylor_green_2d_periodic(8, dt=0.05)
+    for update in ("consistent", "lumped"):
+        o = IPCS(pb, velocity_update=update)
+        s = o.initial_state()
+        rng = np.random.default_rng(2)
+        s.u_nm2 = s.u_nm2 + 0.05 * rng.normal(size=s.u_nm2.shape)
+        s2 = o.step(s)
+        M = o.disc.M
+        for k in range(2):
+            assert abs(np.ones(M.shape[0]) @ (M @ (s2.u_nm1[k] - s2.u_I[k]))) <= 1e-13 * np.abs(M @ s2.u_I[k]).sum()
+        # the two updates differ (the test above is not vacuous)
+        assert np.abs(s2.u_nm1 - IPCS(pb, velocity_update="lumped" if update == "consistent"
+                                      else "consistent").step(s).u_nm1).max() > 1e-10
