@@ -3,9 +3,8 @@
 TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark baseline).  Shares no
 code with the CUDA path.
 
-The paper has no learned component; this is the network the north star of
-this project asks for, defined here (and in the design doc) and implemented
-independently on the GPU:
+The paper has no learned component; this project adds one.  The network is
+defined here and implemented independently on the GPU:
 
   per dof i, inputs x_i = (b_i / s_b, phi1_i / s_phi, phi2_i / s_phi), where b is
   the projected right-hand side of the pressure-correction system, phi1, phi2
