@@ -120,3 +120,31 @@ def test_struct_layouts_match_c_compiler(tmp_path, capi):
         assert int(out[name]) == ctypes.sizeof(cls), name
         for f in cls._fields_:
             assert int(out[f"{name}.{f[0]}"]) == getattr(cls, f[0]).offset, (name, f[0])
+
+
+def test_mesh_create_rejects_bad_input_before_any_device_work(capi):
+    """oasis_mesh_create validates on the host first: these fail the same way
+    with or without a GPU."""
+    import ctypes as C
+    lib = capi.lib()
+    tri = np.array([[0, 0], [1, 0], [0, 1]], dtype=np.float64)
+
+    def create(dim, cells, dof=None, n_dofs=3, coords=tri, n_cells=None):
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        d = None if dof is None else np.ascontiguousarray(dof, dtype=np.int32)
+        out = C.c_void_p()
+        rc = lib.oasis_mesh_create(dim, coords.shape[0], coords.ctypes.data,
+                                   cells.shape[0] if n_cells is None else n_cells, cells.ctypes.data,
+                                   None if d is None else d.ctypes.data, n_dofs, C.byref(out))
+        return rc, lib.oasis_last_error().decode()
+
+    assert create(4, [[0, 1, 2]])[0] == capi.OASIS_EINVAL                      # dimension
+    assert create(2, [[0, 1, 2]], n_cells=0)[0] == capi.OASIS_EINVAL           # empty
+    assert create(2, [[0, 1, 5]])[0] == capi.OASIS_EINVAL                      # vertex index
+    assert create(2, [[0, 1, -1]])[0] == capi.OASIS_EINVAL
+    assert create(2, [[0, 1, 2]], dof=[0, 1, 7])[0] == capi.OASIS_EINVAL       # dof map entry
+    assert create(2, [[0, 1, 2]], dof=[0, 1, 2], n_dofs=4)[0] == capi.OASIS_EINVAL   # n_dofs > vertices
+    rc, msg = create(2, [[0, 1, 1]])                                            # repeated vertex
+    assert rc == capi.OASIS_EMESH and "repeated" in msg
+    rc, msg = create(2, [[0, 1, 2]], dof=[0, 1, 1], n_dofs=2)                   # repeated dof (periodic map)
+    assert rc == capi.OASIS_EMESH and "repeated" in msg
