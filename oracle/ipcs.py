@@ -203,15 +203,19 @@ class IPCS:
             increments.append(phi)
             p_star = p
         if self.velocity_update == "consistent":
-            if self._Mlu is None:
-                self._Mlu = spla.splu(replace_rows(D.M, self.dirichlet).tocsc())
+            Mr = replace_rows(D.M, self.dirichlet)
             g = pb.g(t_new)
-            rows = []
-            for k in range(D.d):
-                rhs = D.M @ u_I[k] - pb.dt * (D.G[k] @ phi)
-                rhs[self.dirichlet] = g[k] if len(self.dirichlet) else rhs[self.dirichlet]
-                rows.append(self._Mlu.solve(rhs))
-            u_n = np.stack(rows)
+            rhs = np.stack([D.M @ u_I[k] - pb.dt * (D.G[k] @ phi) for k in range(D.d)])
+            if len(self.dirichlet):
+                rhs[:, self.dirichlet] = g
+            if not self.iterative:
+                if self._Mlu is None:
+                    self._Mlu = spla.splu(Mr.tocsc())
+                u_n = np.stack([self._Mlu.solve(rhs[k]) for k in range(D.d)])
+            else:
+                # iterative mode (the timed baseline): the same system by the
+                # tentative solver's Jacobi BiCGStab, from u^I
+                u_n = self.solve_tentative(Mr, rhs, u_I)
         else:
             u_n = np.stack([u_I[k] - pb.dt * (D.G[k] @ phi) / D.ML for k in range(D.d)])
         u_n[:, self.dirichlet] = pb.g(t_new)

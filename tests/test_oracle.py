@@ -297,10 +297,11 @@ def test_poiseuille_is_a_discrete_steady_state(form):
     assert np.abs(s.p - s.p.mean()).max() < 1e-9
 
 
-def test_iterative_oracle_matches_direct():
+@pytest.mark.parametrize("update", ["lumped", "consistent"])
+def test_iterative_oracle_matches_direct(update):
     pb = WP.taylor_green_3d(6)
-    a = IPCS(pb).run(3)
-    b = IPCS(pb, iterative=True, rtol=1e-13).run(3)
+    a = IPCS(pb, velocity_update=update).run(3)
+    b = IPCS(pb, iterative=True, rtol=1e-13, velocity_update=update).run(3)
     np.testing.assert_allclose(b.u_nm1, a.u_nm1, atol=1e-10)
     np.testing.assert_allclose(b.p, a.p, atol=1e-9 * np.abs(a.p).max())
 
