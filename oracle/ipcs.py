@@ -245,12 +245,6 @@ class IPCS:
         return s
 
 
-def mass_norm(M: sp.csr_matrix, e: np.ndarray) -> float:
-    """sqrt(sum_k e_k^T M e_k): discrete L2 norm of a nodal field [d, N] or [N]."""
-    e = np.atleast_2d(e)
-    return float(np.sqrt(sum(float(ek @ (M @ ek)) for ek in e)))
-
-
 def mesh_size(coords: np.ndarray, cells: np.ndarray) -> float:
     """h = 2 x (largest) circumradius over the cells, the convention of Sec. 6.1."""
     d = coords.shape[1]
@@ -267,41 +261,3 @@ def mesh_size(coords: np.ndarray, cells: np.ndarray) -> float:
 def convergence_order(E_prev, E, h_prev, h):
     """k = ln(E_i / E_{i-1}) / ln(h_i / h_{i-1}) (Sec. 6.1)."""
     return float(np.log(E / E_prev) / np.log(h / h_prev))
-
-
-def triangle_rule(n: int = 6):
-    """Collapsed (Duffy) tensor Gauss-Legendre rule on the reference triangle.
-
-    Points (xi, eta) = (a (1 - b), b) with a, b Gauss points on [0, 1] and the
-    Jacobian (1 - b); with n points per direction it integrates polynomials of
-    total degree 2n - 2 exactly.  Returns barycentric coordinates [Q, 3] and
-    weights [Q] summing to 1/2.
-    """
-    x, w = np.polynomial.legendre.leggauss(n)
-    x = 0.5 * (x + 1.0)
-    w = 0.5 * w
-    A, B = np.meshgrid(x, x, indexing="ij")
-    WA, WB = np.meshgrid(w, w, indexing="ij")
-    xi = (A * (1.0 - B)).ravel()
-    eta = B.ravel()
-    wq = (WA * WB * (1.0 - B)).ravel()
-    lam = np.stack([1.0 - xi - eta, xi, eta], axis=1)
-    return lam, wq
-
-
-def l2_error_2d(mesh, nodal: np.ndarray, exact, n_quad: int = 6) -> float:
-    """sqrt(int_Omega sum_c (u_h,c - u_e,c)^2 dx) on a triangle mesh.
-
-    ``nodal`` is [c, N] (dof values), ``exact(x [Q,2]) -> [c, Q]``; the
-    P1 interpolant u_h is evaluated at quadrature points of every cell.
-    """
-    nodal = np.atleast_2d(nodal)
-    lam, wq = triangle_rule(n_quad)
-    coords, cells = mesh.coords, mesh.cells
-    x = coords[cells]                                     # [T, 3, 2]
-    det = np.abs(np.linalg.det(np.stack([x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]], axis=2)))
-    xq = np.einsum("qv,tvd->tqd", lam, x)                 # [T, Q, 2]
-    cd = mesh.dof_of_vertex[cells]
-    uh = np.einsum("qv,ctv->ctq", lam, nodal[:, cd])      # [c, T, Q]
-    ue = exact(xq.reshape(-1, 2)).reshape(nodal.shape[0], *xq.shape[:2])
-    return float(np.sqrt(((uh - ue) ** 2 * wq[None, None, :] * det[None, :, None]).sum()))

@@ -77,6 +77,72 @@ def test_adam_training_reduces_loss():
     assert L < 0.05 * L0, (L0, L)
 
 
+# ---------------------------------------------------------------- Adam pins
+# Kingma & Ba (2015), Algorithm 1: m_t = b1 m + (1 - b1) g, v_t = b2 v + (1 - b2) g^2,
+# step lr * mhat / (sqrt(vhat) + eps) with mhat = m_t / (1 - b1^t), vhat = v_t / (1 - b2^t).
+# The pins below use consequences of that definition, evaluated by hand, so that a
+# dropped bias correction, swapped moments or a wrong sign each fail one of them.
+
+def test_adam_first_step_moves_by_lr_times_sign():
+    """t = 1: mhat = g and vhat = g^2 exactly, so every parameter moves by
+    -lr g / (|g| + eps), i.e. lr against the sign of its gradient."""
+    g = np.array([0.5, -3.0, 1e-3, 250.0])
+    p0 = np.array([1.0, 2.0, -1.0, 0.0])
+    p, m, v = N.adam(p0, np.zeros(4), np.zeros(4), g, 1, 0.01, eps=1e-8)
+    np.testing.assert_allclose(p - p0, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-13, atol=0)
+    np.testing.assert_allclose(m, 0.1 * g, rtol=1e-15)          # (1 - b1) g
+    np.testing.assert_allclose(v, 0.001 * g * g, rtol=1e-13)    # (1 - b2) g^2
+
+
+def test_adam_constant_gradient_keeps_step_size():
+    """With a constant gradient m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2, so
+    after bias correction every step has the size of the first one."""
+    g = np.array([0.5, -2.0])
+    p = np.array([0.0, 0.0])
+    m, v = np.zeros(2), np.zeros(2)
+    for t in range(1, 41):
+        p_prev = p
+        p, m, v = N.adam(p, m, v, g, t, 0.05, eps=0.0)
+        np.testing.assert_allclose(p - p_prev, [-0.05, 0.05], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(p, [-2.0, 2.0], rtol=1e-12)
+
+
+def test_adam_three_steps_by_hand():
+    """Two scalars, b1 = 0.9, b2 = 0.999, lr = 0.01, eps = 0, moments by hand.
+
+    Scalar A, gradients 1, -1, 1 (|g| = 1, so v_t = 1 - b2^t and vhat = 1):
+      t=1  m = 0.1                      mhat = 0.1 / 0.1 = 1
+      t=2  m = 0.09 - 0.1 = -0.01        mhat = -0.01 / 0.19 = -1/19
+      t=3  m = -0.009 + 0.1 = 0.091      mhat = 0.091 / 0.271 = 91/271
+    Scalar B, gradients 2, 0, -4:
+      t=1  m = 0.2,    v = 0.004           mhat = 2,            vhat = 4
+      t=2  m = 0.18,   v = 0.003996        mhat = 18/19,        vhat = 3996/1999
+      t=3  m = -0.238, v = 0.019992004     mhat = -0.238/0.271, vhat = 0.019992004/0.002997001
+    """
+    lr = 0.01
+    want_steps = [
+        [1.0, 2.0 / 2.0],
+        [-1.0 / 19.0, (18.0 / 19.0) / np.sqrt(3996.0 / 1999.0)],
+        [91.0 / 271.0, (-0.238 / 0.271) / np.sqrt(0.019992004 / 0.002997001)],
+    ]
+    grads = [[1.0, 2.0], [-1.0, 0.0], [1.0, -4.0]]
+    p = np.array([0.3, -0.7])
+    m, v = np.zeros(2), np.zeros(2)
+    for t, (g, want) in enumerate(zip(grads, want_steps), start=1):
+        p_prev = p
+        p, m, v = N.adam(p, m, v, np.array(g), t, lr, b1=0.9, b2=0.999, eps=0.0)
+        np.testing.assert_allclose(p_prev - p, lr * np.array(want), rtol=1e-12, atol=0)
+    np.testing.assert_allclose(m, [0.091, -0.238], rtol=1e-12)
+    np.testing.assert_allclose(v, [0.002997001, 0.019992004], rtol=1e-12)
+
+
+def test_adam_eps_bounds_the_step_of_a_tiny_gradient():
+    """t = 1 with |g| << eps: the step is lr g / (|g| + eps) ~ lr g / eps, not lr."""
+    g = np.array([1e-12])
+    p, _, _ = N.adam(np.zeros(1), np.zeros(1), np.zeros(1), g, 1, 1.0, eps=1e-8)
+    np.testing.assert_allclose(-p, 1e-12 / (1e-12 + 1e-8), rtol=1e-12)
+
+
 def test_features_scale_invariance():
     rng = np.random.default_rng(2)
     b, f1, f2 = rng.normal(size=(3, 50))
