@@ -54,10 +54,16 @@ def _workload(name):
     raise ValueError(name)
 
 
-def workload_config(name, pb, precision):
-    return {"workload": name, "n_dofs": int(pb.mesh.n_dofs), "n_cells": int(pb.mesh.n_cells),
-            "dt": pb.dt, "nu": pb.nu, "rtol": RTOL, "precision": precision,
-            "batch_rhs": True, "cuda_graph": True, "l2": "flushed between steps (256 MiB write)"}
+def workload_config(name, pb, precision, gpu=True):
+    """The workload (and, for the GPU arm, the solver form) a line was measured on."""
+    c = {"workload": name, "n_dofs": int(pb.mesh.n_dofs), "n_cells": int(pb.mesh.n_cells),
+         "dt": pb.dt, "nu": pb.nu, "rtol": RTOL, "precision": precision}
+    if gpu:
+        c |= {"batch_rhs": True, "cuda_graph": True, "l2": "flushed between steps (256 MiB write)"}
+    else:
+        c |= {"solver": "scipy BiCGStab (velocity, one solve per component) and CG (pressure), Jacobi, "
+                        "sparse matrices assembled per step, host cores"}
+    return c
 
 
 # ---------------------------------------------------------------------- clocks
@@ -580,7 +586,7 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world,
             "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.workload, pb, "fp64 (CPU oracle)"),
+            "config": workload_config(args.workload, pb, "fp64 (CPU oracle)", gpu=False),
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{n} full steps (iterative float64 oracle, rtol 1e-8)"},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

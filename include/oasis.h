@@ -29,6 +29,17 @@
  *     temporary buffers.
  *   - Fields are float64, component-major: u[k * n_dofs + i] is component k of
  *     dof i.  Indices are int32, zero based.
+ *   - Dof order.  Every per-dof array and dof index that crosses a field call
+ *     (oasis_set_fields, oasis_get_fields, oasis_set_scalar_fields,
+ *     oasis_get_scalar_fields, oasis_get_tentative_system, the Dirichlet dof
+ *     lists of oasis_solver_create and oasis_solver_set_scalars) and the pattern
+ *     and matrices of oasis_mesh_get_pattern / oasis_mesh_get_matrix are in the
+ *     CALLER's dof order.  The library stores and computes in its internal order,
+ *     the caller's renumbered by the `perm` of oasis_mesh_create (identical when
+ *     perm is NULL).  The kernel-level vector entry points (oasis_spmv_*,
+ *     oasis_net_forward / _backward, oasis_get_guess_sample, oasis_amg_apply)
+ *     exchange device vectors in the internal order: entry perm[d] belongs to
+ *     caller dof d.
  *   - Handles are not reentrant: calls on one solver must not overlap.
  *     Different solvers (and meshes) are independent.
  */
@@ -198,14 +209,25 @@ const char* oasis_last_error(void);
  *   dof_of_vertex host, [n_vertices] dof of each vertex, or NULL for the identity
  *                 (periodic meshes identify image vertices through this map)
  *   n_dofs        number of dofs (max(dof_of_vertex) + 1; n_vertices if the map is NULL)
+ *   perm          host, [n_dofs] or NULL: a renumbering of the dofs (for example
+ *                 reverse Cuthill-McKee, for locality of the sparse products),
+ *                 perm[d] = the library's internal index of the caller's dof d.
+ *                 It must be a permutation of 0 .. n_dofs-1.  The library stores
+ *                 the pattern, the matrices and the state in that internal order;
+ *                 the field calls still take and return the caller's order (see
+ *                 "Dof order" above), so results do not depend on perm beyond
+ *                 the solvers' tolerances (the order of floating-point sums and
+ *                 the multigrid aggregation follow the internal numbering).
  * Builds the shared CSR sparsity pattern of all matrices (Sec. 5: "computed on
- * the first assemble") and the dof-to-cell incidence used by the assembly
- * kernels; copies everything to the current device.
- * Errors: OASIS_EINVAL (sizes, out-of-range index), OASIS_EMESH (a cell whose
- * dofs repeat, or more than 255 pattern entries in one row), OASIS_ENOMEM. */
+ * the first assemble"; the assembled system's dof numbering is free, Sec. 5) and
+ * the dof-to-cell incidence used by the assembly kernels; copies everything to
+ * the current device.
+ * Errors: OASIS_EINVAL (sizes, out-of-range index, perm not a permutation),
+ * OASIS_EMESH (a cell whose dofs repeat, or more than 255 pattern entries in one
+ * row), OASIS_ENOMEM. */
 int oasis_mesh_create(int32_t dim, int64_t n_vertices, const double* coords, int64_t n_cells,
                       const int32_t* cells, const int32_t* dof_of_vertex, int64_t n_dofs,
-                      oasis_mesh** out);
+                      const int32_t* perm, oasis_mesh** out);
 
 /* Sizes of the mesh and of its sparsity pattern (any pointer may be NULL). */
 int oasis_mesh_info(const oasis_mesh* mesh, int64_t* n_dofs, int64_t* n_cells, int64_t* nnz);
@@ -217,17 +239,18 @@ int oasis_mesh_info(const oasis_mesh* mesh, int64_t* n_dofs, int64_t* n_cells, i
  * Errors: OASIS_EMESH if a cell has zero volume; OASIS_ECUDA. */
 int oasis_assemble_constant(oasis_mesh* mesh, void* stream);
 
-/* Copy the sparsity pattern to host: row_ptr [n_dofs+1], col [nnz] (sorted per row). */
+/* Copy the sparsity pattern to host in the caller's dof order: row_ptr [n_dofs+1],
+ * col [nnz] (sorted per row). */
 int oasis_mesh_get_pattern(const oasis_mesh* mesh, int32_t* row_ptr, int32_t* col);
 
 /* Copy the float64 values of a constant matrix (OASIS_MAT_M, _K, _G0.._G2) to a
- * host array [nnz] in pattern order, or with which = -1 the lumped mass [n_dofs].
- * Synchronises the device. */
+ * host array [nnz] in the order of oasis_mesh_get_pattern (caller's dof order), or
+ * with which = -1 the lumped mass [n_dofs].  Synchronises the device. */
 int oasis_mesh_get_matrix(const oasis_mesh* mesh, int32_t which, double* values);
 
-/* y = Mat x on device vectors of length n_dofs (float64), Mat one of the constant
- * matrices, with `lanes` lanes per row (0 = 16).  For kernel-level tests and
- * bandwidth measurements. */
+/* y = Mat x on device vectors of length n_dofs (float64, internal dof order), Mat
+ * one of the constant matrices, with `lanes` lanes per row (0 = 16).  For
+ * kernel-level tests and bandwidth measurements. */
 int oasis_spmv_f64(const oasis_mesh* mesh, int32_t which, const double* x, double* y,
                    int32_t lanes, void* stream);
 /* Same in float32 values and vectors (the values are the float32 copy of the matrix). */
@@ -331,8 +354,9 @@ int oasis_get_fields(oasis_solver* s, double* u, double* p, double* phi, int32_t
                      void* stream);
 
 /* Run only the assembly of the next step (Algorithm 2) on the current state and
- * copy to host the coefficient matrix A [nnz] (Dirichlet rows already unit rows)
- * and the initial tentative residual r0 = b - A u^{n-1} ([dim][n_dofs]).  The
+ * copy to host the coefficient matrix A [nnz] (in the order of
+ * oasis_mesh_get_pattern; Dirichlet rows already unit rows) and the initial
+ * tentative residual r0 = b - A u^{n-1} ([dim][n_dofs], caller's dof order).  The
  * state is not advanced.  For parity tests. */
 int oasis_get_tentative_system(oasis_solver* s, double* A_values, double* r0, void* stream);
 

@@ -104,7 +104,7 @@ DPTR = C.c_void_p
 SIGNATURES = {
     "oasis_version": (C.c_int, []),
     "oasis_last_error": (C.c_char_p, []),
-    "oasis_mesh_create": (C.c_int, [I32, I64, DPTR, I64, DPTR, DPTR, I64, PP]),
+    "oasis_mesh_create": (C.c_int, [I32, I64, DPTR, I64, DPTR, DPTR, I64, DPTR, PP]),
     "oasis_mesh_info": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
     "oasis_assemble_constant": (C.c_int, [P, P]),
     "oasis_mesh_get_pattern": (C.c_int, [P, DPTR, DPTR]),
@@ -188,15 +188,17 @@ def oasis_version():
     return lib().oasis_version()
 
 
-def oasis_mesh_create(dim, coords, cells, dof_of_vertex=None, n_dofs=None):
+def oasis_mesh_create(dim, coords, cells, dof_of_vertex=None, n_dofs=None, perm=None):
+    """perm: optional dof renumbering, perm[d] = the library's internal index of dof d."""
     coords = np.ascontiguousarray(coords, dtype=np.float64)
     cells = np.ascontiguousarray(cells, dtype=np.int32)
     dov = None if dof_of_vertex is None else np.ascontiguousarray(dof_of_vertex, dtype=np.int32)
+    prm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
     if n_dofs is None:
         n_dofs = coords.shape[0] if dov is None else int(dov.max()) + 1
     out = C.c_void_p()
     check(lib().oasis_mesh_create(dim, coords.shape[0], _ptr(coords), cells.shape[0], _ptr(cells),
-                                  _ptr(dov), int(n_dofs), C.byref(out)))
+                                  _ptr(dov), int(n_dofs), _ptr(prm), C.byref(out)))
     return out
 
 

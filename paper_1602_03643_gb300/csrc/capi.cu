@@ -238,8 +238,9 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     std::vector<int32_t> di(n, -1);
     for (int64_t q = 0; q < n_dir; ++q) {
         OASIS_CHECK(dir[q] >= 0 && dir[q] < n, OASIS_EINVAL, "dirichlet dof out of range");
-        OASIS_CHECK(di[dir[q]] < 0, OASIS_EINVAL, "repeated dirichlet dof");
-        di[dir[q]] = (int32_t)q;
+        const int32_t i = m->internal_dof(dir[q]);
+        OASIS_CHECK(di[i] < 0, OASIS_EINVAL, "repeated dirichlet dof");
+        di[i] = (int32_t)q;
     }
     S->dir_index.upload(di.data(), n, s);
     S->g.alloc(sb * std::max<int64_t>(1, n_dir * D), s);
@@ -335,6 +336,23 @@ static int guarded(F&& f) {
 
 static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Host copy of a per-entry (pattern order) or per-dof array in the internal
+// order, written out in the caller's order.
+static void to_caller_order(const Mesh& m, bool per_dof, const std::vector<double>& internal, double* out) {
+    if (m.h_perm.empty()) {
+        std::memcpy(out, internal.data(), internal.size() * sizeof(double));
+        return;
+    }
+    if (per_dof) {
+        for (int64_t d = 0; d < m.n; ++d) out[d] = internal[m.h_perm[d]];
+        return;
+    }
+    std::vector<int32_t> rp, ci;
+    std::vector<int64_t> src;
+    caller_pattern(m, rp, ci, src);
+    for (int64_t e = 0; e < m.nnz; ++e) out[e] = internal[src[e]];
+}
+
 extern "C" {
 
 int oasis_version(void) { return 100; }
@@ -342,10 +360,12 @@ int oasis_version(void) { return 100; }
 const char* oasis_last_error(void) { return g_last_error.c_str(); }
 
 int oasis_mesh_create(int32_t dim, int64_t n_vertices, const double* coords, int64_t n_cells,
-                      const int32_t* cells, const int32_t* dof_of_vertex, int64_t n_dofs, oasis_mesh** out) {
+                      const int32_t* cells, const int32_t* dof_of_vertex, int64_t n_dofs, const int32_t* perm,
+                      oasis_mesh** out) {
     return guarded([&] {
         OASIS_CHECK(out, OASIS_EINVAL, "null output pointer");
-        *out = reinterpret_cast<oasis_mesh*>(build_mesh(dim, n_vertices, coords, n_cells, cells, dof_of_vertex, n_dofs));
+        *out = reinterpret_cast<oasis_mesh*>(
+            build_mesh(dim, n_vertices, coords, n_cells, cells, dof_of_vertex, n_dofs, perm));
     });
 }
 
@@ -371,8 +391,11 @@ int oasis_mesh_get_pattern(const oasis_mesh* mesh, int32_t* row_ptr, int32_t* co
     return guarded([&] {
         const Mesh* m = reinterpret_cast<const Mesh*>(mesh);
         OASIS_CHECK(m && row_ptr && col, OASIS_EINVAL, "null pointer");
-        std::memcpy(row_ptr, m->h_row_ptr.data(), m->h_row_ptr.size() * sizeof(int32_t));
-        std::memcpy(col, m->h_col.data(), m->h_col.size() * sizeof(int32_t));
+        std::vector<int32_t> rp, ci;
+        std::vector<int64_t> src;
+        caller_pattern(*m, rp, ci, src);
+        std::memcpy(row_ptr, rp.data(), rp.size() * sizeof(int32_t));
+        std::memcpy(col, ci.data(), ci.size() * sizeof(int32_t));
     });
 }
 
@@ -392,7 +415,9 @@ int oasis_mesh_get_matrix(const oasis_mesh* mesh, int32_t which, double* values)
         } else
             throw Error(OASIS_EINVAL, "unknown matrix");
         OASIS_CUDA(cudaDeviceSynchronize());
-        OASIS_CUDA(cudaMemcpy(values, src, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+        std::vector<double> internal(cnt);
+        OASIS_CUDA(cudaMemcpy(internal.data(), src, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+        to_caller_order(*m, which == -1, internal, values);
     });
 }
 
@@ -440,10 +465,11 @@ int oasis_spmv_dot_f64_noalloc(const oasis_mesh* mesh, int32_t which, const doub
     return guarded([&] {
         const Mesh* m = reinterpret_cast<const Mesh*>(mesh);
         OASIS_CHECK(m && x && y && xy, OASIS_EINVAL, "null pointer");
-        OASIS_CHECK(m->assembled, OASIS_EINVAL, "mesh not assembled");
+        // the size bound depends on the mesh alone, so it is checked first
         OASIS_CHECK(m->n <= noalloc_max_rows(), OASIS_EINVAL,
                     "n_dofs = " + std::to_string(m->n) + " exceeds the static scratch of the no-alloc entry point (at "
                     "most " + std::to_string(noalloc_max_rows()) + " rows); use oasis_spmv_dot_f64");
+        OASIS_CHECK(m->assembled, OASIS_EINVAL, "mesh not assembled");
         double* partial = nullptr;
         uint32_t* ticket = nullptr;
         noalloc_scratch(&partial, &ticket);
@@ -477,7 +503,7 @@ int oasis_set_fields(oasis_solver* solver, const double* u_nm1, const double* u_
                 OASIS_CUDA(cudaMemcpyAsync(S->stage.p, src, n * comps[q] * sizeof(double), cudaMemcpyHostToDevice, s));
                 src = S->stage.p;
             }
-            S->impl->to_state(s, src, ids[q], n, comps[q]);
+            S->impl->to_state(s, src, ids[q], n, comps[q], S->m->perm.p);
             OASIS_CUDA(cudaStreamSynchronize(s));
         }
         for (RBuf* b : {&S->phi, &S->phi_h1, &S->phi_h2}) OASIS_CUDA(cudaMemsetAsync(b->p, 0, b->bytes, s));
@@ -500,7 +526,7 @@ int oasis_set_dirichlet(oasis_solver* solver, const double* g, int32_t on_device
             OASIS_CUDA(cudaMemcpyAsync(S->stage.p, g, nd * D * sizeof(double), cudaMemcpyHostToDevice, s));
             src = S->stage.p;
         }
-        S->impl->to_state(s, src, ST_G, nd, D);
+        S->impl->to_state(s, src, ST_G, nd, D, nullptr);
         if (!on_device) OASIS_CUDA(cudaStreamSynchronize(s));
     });
 }
@@ -522,8 +548,9 @@ int oasis_solver_set_scalars(oasis_solver* solver, int32_t n_scalars, const doub
         std::vector<int32_t> di(n, -1);
         for (int64_t q = 0; q < n_dirichlet; ++q) {
             OASIS_CHECK(dirichlet_dofs[q] >= 0 && dirichlet_dofs[q] < n, OASIS_EINVAL, "scalar dirichlet dof out of range");
-            OASIS_CHECK(di[dirichlet_dofs[q]] < 0, OASIS_EINVAL, "repeated scalar dirichlet dof");
-            di[dirichlet_dofs[q]] = (int32_t)q;
+            const int32_t i = S->m->internal_dof(dirichlet_dofs[q]);
+            OASIS_CHECK(di[i] < 0, OASIS_EINVAL, "repeated scalar dirichlet dof");
+            di[i] = (int32_t)q;
         }
         drop_graph(S);
         cudaStream_t s = nullptr;
@@ -566,7 +593,7 @@ int oasis_set_scalar_fields(oasis_solver* solver, const double* c, int32_t on_de
             OASIS_CUDA(cudaMemcpyAsync(S->cstage.p, c, count * sizeof(double), cudaMemcpyHostToDevice, s));
             src = S->cstage.p;
         }
-        S->impl->to_state(s, src, ST_C, count, 1);
+        S->impl->to_state(s, src, ST_C, count, 1, S->m->perm.p);
         OASIS_CUDA(cudaStreamSynchronize(s));
     });
 }
@@ -579,10 +606,10 @@ int oasis_get_scalar_fields(oasis_solver* solver, double* c, int32_t on_device, 
         cudaStream_t s = as_stream(stream);
         const int64_t count = S->m->n * S->ns;
         if (on_device) {
-            S->impl->from_state(s, c, ST_C, count, 1);
+            S->impl->from_state(s, c, ST_C, count, 1, S->m->perm.p);
             return;
         }
-        S->impl->from_state(s, S->cstage.p, ST_C, count, 1);
+        S->impl->from_state(s, S->cstage.p, ST_C, count, 1, S->m->perm.p);
         OASIS_CUDA(cudaMemcpyAsync(c, S->cstage.p, count * sizeof(double), cudaMemcpyDeviceToHost, s));
         OASIS_CUDA(cudaStreamSynchronize(s));
     });
@@ -602,7 +629,7 @@ int oasis_set_scalar_dirichlet(oasis_solver* solver, const double* g, int32_t on
             OASIS_CUDA(cudaMemcpyAsync(S->cstage.p, g, count * sizeof(double), cudaMemcpyHostToDevice, s));
             src = S->cstage.p;
         }
-        S->impl->to_state(s, src, ST_GC, count, 1);
+        S->impl->to_state(s, src, ST_GC, count, 1, nullptr);
         OASIS_CUDA(cudaStreamSynchronize(s));
     });
 }
@@ -645,7 +672,7 @@ int oasis_get_fields(oasis_solver* solver, double* u, double* p, double* phi, in
         for (int q = 0; q < 3; ++q) {
             if (!outs[q]) continue;
             double* dst = on_device ? outs[q] : S->stage.p;
-            S->impl->from_state(s, dst, ids[q], n, comps[q]);
+            S->impl->from_state(s, dst, ids[q], n, comps[q], S->m->perm.p);
             if (!on_device) {
                 OASIS_CUDA(cudaMemcpyAsync(outs[q], S->stage.p, n * comps[q] * sizeof(double), cudaMemcpyDeviceToHost, s));
                 OASIS_CUDA(cudaStreamSynchronize(s));
@@ -666,11 +693,13 @@ int oasis_get_tentative_system(oasis_solver* solver, double* A_values, double* r
             DBuf<double> tmp;
             tmp.alloc(nnz);
             S->impl->a_to_double(s, tmp.p);
-            OASIS_CUDA(cudaMemcpyAsync(A_values, tmp.p, nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+            std::vector<double> internal(nnz);
+            OASIS_CUDA(cudaMemcpyAsync(internal.data(), tmp.p, nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
             OASIS_CUDA(cudaStreamSynchronize(s));
+            to_caller_order(*S->m, false, internal, A_values);
         }
         if (r0) {
-            S->impl->from_state(s, S->stage.p, ST_R0, n, D);
+            S->impl->from_state(s, S->stage.p, ST_R0, n, D, S->m->perm.p);
             OASIS_CUDA(cudaMemcpyAsync(r0, S->stage.p, n * D * sizeof(double), cudaMemcpyDeviceToHost, s));
         }
         OASIS_CUDA(cudaStreamSynchronize(s));

@@ -88,6 +88,12 @@ struct Mesh {
     int max_row = 0;
     // host copies needed later
     std::vector<int32_t> h_row_ptr, h_col;
+    // Dof renumbering given at creation: internal dof = h_perm[caller dof]
+    // (empty: the caller's order is the internal one).  `perm` is its device
+    // copy, used by the field transfers.
+    std::vector<int32_t> h_perm;
+    DBuf<int32_t> perm;
+    int32_t internal_dof(int32_t caller) const { return h_perm.empty() ? caller : h_perm[caller]; }
     // device: pattern
     DBuf<int32_t> row_ptr, col, diag;          // diag[i] = position of (i, i)
     // device: cells

@@ -38,7 +38,7 @@ static void parallel_for(int64_t n, F f) {
 }
 
 Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const int32_t* cells,
-                 const int32_t* dof_of_vertex, int64_t n_dofs) {
+                 const int32_t* dof_of_vertex, int64_t n_dofs, const int32_t* perm) {
     OASIS_CHECK(dim == 2 || dim == 3, OASIS_EINVAL, "dim must be 2 or 3");
     OASIS_CHECK(nv > 0 && nc > 0 && coords && cells, OASIS_EINVAL, "empty mesh or null pointer");
     OASIS_CHECK(nv < INT32_MAX && nc * (dim + 1) < INT32_MAX, OASIS_EINVAL, "mesh too large for int32 indices");
@@ -51,6 +51,16 @@ Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const in
     m->nv = nv;
     m->nc = nc;
     m->n = n_dofs;
+    if (perm) {
+        // a permutation of 0 .. n_dofs-1: every value in range and seen once
+        std::vector<uint8_t> seen(n_dofs, 0);
+        for (int64_t d = 0; d < n_dofs; ++d) {
+            OASIS_CHECK(perm[d] >= 0 && perm[d] < n_dofs, OASIS_EINVAL, "perm entry out of range");
+            OASIS_CHECK(!seen[perm[d]], OASIS_EINVAL, "perm is not a permutation (repeated entry)");
+            seen[perm[d]] = 1;
+        }
+        m->h_perm.assign(perm, perm + n_dofs);
+    }
     std::vector<int32_t> cdof((size_t)nc * d1);
     for (int64_t c = 0; c < nc; ++c) {
         for (int a = 0; a < d1; ++a) {
@@ -58,7 +68,7 @@ Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const in
             OASIS_CHECK(v >= 0 && v < nv, OASIS_EINVAL, "cell vertex index out of range");
             const int32_t dof = dof_of_vertex ? dof_of_vertex[v] : v;
             OASIS_CHECK(dof >= 0 && dof < n_dofs, OASIS_EINVAL, "dof_of_vertex entry out of range");
-            cdof[c * d1 + a] = dof;
+            cdof[c * d1 + a] = perm ? perm[dof] : dof;
         }
         for (int a = 0; a < d1; ++a)
             for (int b = a + 1; b < d1; ++b)
@@ -145,6 +155,7 @@ Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const in
     m->inc_ptr.upload(inc_ptr.data(), inc_ptr.size(), s);
     m->inc_cell.upload(inc_cell.data(), inc_cell.size(), s);
     m->inc_slots.upload(inc_slots.data(), inc_slots.size(), s);
+    if (!m->h_perm.empty()) m->perm.upload(m->h_perm.data(), m->h_perm.size(), s);
     m->err.alloc(1);
     OASIS_CUDA(cudaMemsetAsync(m->err.p, 0, sizeof(int32_t), s));
     OASIS_CUDA(cudaStreamSynchronize(s));
@@ -208,6 +219,39 @@ Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const in
     m->h_row_ptr = std::move(row_ptr);
     m->h_col = std::move(col);
     return m.release();
+}
+
+void caller_pattern(const Mesh& m, std::vector<int32_t>& row_ptr, std::vector<int32_t>& col,
+                    std::vector<int64_t>& src) {
+    const int64_t n = m.n;
+    row_ptr.assign(n + 1, 0);
+    col.assign(m.nnz, 0);
+    src.assign(m.nnz, 0);
+    if (m.h_perm.empty()) {
+        std::copy(m.h_row_ptr.begin(), m.h_row_ptr.begin() + n + 1, row_ptr.begin());
+        std::copy(m.h_col.begin(), m.h_col.begin() + m.nnz, col.begin());
+        for (int64_t e = 0; e < m.nnz; ++e) src[e] = e;
+        return;
+    }
+    std::vector<int32_t> caller_of(n);
+    for (int64_t d = 0; d < n; ++d) caller_of[m.h_perm[d]] = (int32_t)d;
+    for (int64_t d = 0; d < n; ++d) {
+        const int32_t r = m.h_perm[d];
+        row_ptr[d + 1] = row_ptr[d] + (m.h_row_ptr[r + 1] - m.h_row_ptr[r]);
+    }
+    parallel_for(n, [&](int64_t a, int64_t b) {
+        std::vector<std::pair<int32_t, int64_t>> buf;
+        for (int64_t d = a; d < b; ++d) {
+            const int32_t r = m.h_perm[d];
+            buf.clear();
+            for (int32_t e = m.h_row_ptr[r]; e < m.h_row_ptr[r + 1]; ++e) buf.emplace_back(caller_of[m.h_col[e]], e);
+            std::sort(buf.begin(), buf.end());
+            for (size_t q = 0; q < buf.size(); ++q) {
+                col[row_ptr[d] + q] = buf[q].first;
+                src[row_ptr[d] + q] = buf[q].second;
+            }
+        }
+    });
 }
 
 // ------------------------------------------------------------------ geometry
@@ -529,15 +573,27 @@ void spmv_dot_f64(const Mesh& m, const double* vals, const double* x, double* y,
                   uint32_t* ticket, cudaStream_t s) {
     const int64_t ntiles = (m.n + kBlock - 1) / kBlock;
     const size_t smem = (size_t)std::max(1, m.tile_cap) * sizeof(double);
-    static int room = 0;
-    if (!room) {
-        int dev = 0, optin = 0;
-        OASIS_CUDA(cudaGetDevice(&dev));
-        OASIS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        cudaFuncAttributes fa{};
-        OASIS_CUDA(cudaFuncGetAttributes(&fa, k_spmv_dot_tiles));
-        room = optin - (int)fa.sharedSizeBytes;
-        OASIS_CUDA(cudaFuncSetAttribute(k_spmv_dot_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, room));
+    // The opt-in dynamic shared-memory size is a per-device attribute of the
+    // kernel: it is set once per device (with that device current) and cached
+    // under a lock, so concurrent first calls and later devices are covered.
+    static std::mutex mu;
+    static int rooms[256] = {0};
+    int dev = 0;
+    OASIS_CUDA(cudaGetDevice(&dev));
+    OASIS_CHECK(dev >= 0 && dev < 256, OASIS_EINVAL, "device ordinal out of range");
+    int room = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!rooms[dev]) {
+            int optin = 0;
+            OASIS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            cudaFuncAttributes fa{};
+            OASIS_CUDA(cudaFuncGetAttributes(&fa, k_spmv_dot_tiles));
+            const int r = optin - (int)fa.sharedSizeBytes;
+            OASIS_CUDA(cudaFuncSetAttribute(k_spmv_dot_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, r));
+            rooms[dev] = r;
+        }
+        room = rooms[dev];
     }
     OASIS_CHECK(smem <= (size_t)room, OASIS_EINVAL, "a row tile needs more shared memory than the device offers");
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * 4));

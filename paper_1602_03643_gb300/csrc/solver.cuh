@@ -115,8 +115,14 @@ struct StepImpl {
     virtual void scalar_solve(cudaStream_t s, bool graph) = 0;
     // the solver's scalar buffers were (re)allocated or removed
     virtual void scalars_changed() = 0;
-    virtual void to_state(cudaStream_t s, const double* src_soa, int which, int64_t count, int comps) = 0;
-    virtual void from_state(cudaStream_t s, double* dst_soa, int which, int64_t count, int comps) = 0;
+    // Component-major float64 arrays [comps][count] <-> the state (dof-major,
+    // storage type).  With `perm` (the mesh's device renumbering, period n_dofs)
+    // entry i of the array is caller index i: it lands at internal index
+    // (i / n) n + perm[i mod n]; without it the indices are equal.
+    virtual void to_state(cudaStream_t s, const double* src_soa, int which, int64_t count, int comps,
+                          const int32_t* perm) = 0;
+    virtual void from_state(cudaStream_t s, double* dst_soa, int which, int64_t count, int comps,
+                            const int32_t* perm) = 0;
     virtual void a_to_double(cudaStream_t s, double* dst) = 0;
     virtual void guess_target(cudaStream_t s, float* target) = 0;
     // time the candidate shapes of the CG iteration kernel on this matrix and keep
@@ -197,7 +203,12 @@ struct Solver {
 
 StepImpl* make_step_impl(Solver& s);
 Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const int32_t* cells,
-                 const int32_t* dof_of_vertex, int64_t n_dofs);
+                 const int32_t* dof_of_vertex, int64_t n_dofs, const int32_t* perm);
+// Pattern of the mesh in the caller's dof order (see Mesh::h_perm): row_ptr,
+// col, and for each caller entry the index of the same entry in the internal
+// pattern.
+void caller_pattern(const Mesh& m, std::vector<int32_t>& row_ptr, std::vector<int32_t>& col,
+                    std::vector<int64_t>& src);
 void assemble_constant(Mesh& m, cudaStream_t s);
 
 }  // namespace oasis

@@ -1776,20 +1776,30 @@ __global__ void __launch_bounds__(kBlock) k_update(StepData<P> a, Consts<typenam
 }
 
 // ================================================================ conversions
+// Internal index of caller index i under a renumbering of period pn (arrays of
+// several fields of pn dofs each are renumbered field by field).
+__device__ __forceinline__ int64_t renumbered(int64_t i, const int32_t* __restrict__ perm, int64_t pn) {
+    if (!perm) return i;
+    const int64_t f = i / pn;
+    return f * pn + perm[i - f * pn];
+}
+// [comps][n] float64, caller order -> state [n][comps], internal order
 template <class P>
-__global__ void k_to_state(const double* __restrict__ src, typename P::S* __restrict__ dst, int64_t n, int comps) {
+__global__ void k_to_state(const double* __restrict__ src, typename P::S* __restrict__ dst, int64_t n, int comps,
+                           const int32_t* __restrict__ perm, int64_t pn) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * comps; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = t / comps;
         const int k = (int)(t - i * comps);
-        dst[t] = s_of_double<typename P::S>(src[(int64_t)k * n + i]);
+        dst[renumbered(i, perm, pn) * comps + k] = s_of_double<typename P::S>(src[(int64_t)k * n + i]);
     }
 }
 template <class P>
-__global__ void k_from_state(const typename P::S* __restrict__ src, double* __restrict__ dst, int64_t n, int comps) {
+__global__ void k_from_state(const typename P::S* __restrict__ src, double* __restrict__ dst, int64_t n, int comps,
+                             const int32_t* __restrict__ perm, int64_t pn) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * comps; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = t / comps;
         const int k = (int)(t - i * comps);
-        dst[(int64_t)k * n + i] = s_to_double(src[t]);
+        dst[(int64_t)k * n + i] = s_to_double(src[renumbered(i, perm, pn) * comps + k]);
     }
 }
 template <class V>
@@ -2246,12 +2256,18 @@ struct StepImplT final : StepImpl {
         }
     }
 
-    void to_state(cudaStream_t s, const double* src, int which, int64_t count, int comps) override {
-        k_to_state<P><<<elem_grid(count * comps), kBlock, 0, s>>>(src, state_ptr(which), count, comps);
+    void to_state(cudaStream_t s, const double* src, int which, int64_t count, int comps,
+                  const int32_t* perm) override {
+        OASIS_CHECK(!perm || count % Sv.m->n == 0, OASIS_EINVAL, "renumbered transfer of a partial field");
+        k_to_state<P><<<elem_grid(count * comps), kBlock, 0, s>>>(src, state_ptr(which), count, comps, perm,
+                                                                  Sv.m->n);
         OASIS_CUDA(cudaGetLastError());
     }
-    void from_state(cudaStream_t s, double* dst, int which, int64_t count, int comps) override {
-        k_from_state<P><<<elem_grid(count * comps), kBlock, 0, s>>>(state_ptr(which), dst, count, comps);
+    void from_state(cudaStream_t s, double* dst, int which, int64_t count, int comps,
+                    const int32_t* perm) override {
+        OASIS_CHECK(!perm || count % Sv.m->n == 0, OASIS_EINVAL, "renumbered transfer of a partial field");
+        k_from_state<P><<<elem_grid(count * comps), kBlock, 0, s>>>(state_ptr(which), dst, count, comps, perm,
+                                                                    Sv.m->n);
         OASIS_CUDA(cudaGetLastError());
     }
     const IterVariant<P>* iter_variants() const {

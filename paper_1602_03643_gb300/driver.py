@@ -2,7 +2,8 @@
 
 Argument marshalling only; the problem object needs the attributes ``mesh``
 (dim, coords, cells, dof_of_vertex, n_dofs), ``nu``, ``dt``, ``f``,
-``dirichlet``, ``u_nm1``, ``u_nm2``, ``p``, ``t0`` and ``g(t)``.
+``dirichlet``, ``u_nm1``, ``u_nm2``, ``p``, ``t0`` and ``g(t)``, and may carry
+``perm`` (a dof renumbering for the library; fields stay in the problem's order).
 """
 from __future__ import annotations
 
@@ -21,7 +22,8 @@ class IPCSRun:
         self.stream = stream
         m = pb.mesh
         self.dim, self.n = m.dim, m.n_dofs
-        self.mesh = capi.oasis_mesh_create(m.dim, m.coords, m.cells, m.dof_of_vertex, m.n_dofs)
+        self.mesh = capi.oasis_mesh_create(m.dim, m.coords, m.cells, m.dof_of_vertex, m.n_dofs,
+                                           perm=getattr(pb, "perm", None))
         capi.oasis_assemble_constant(self.mesh, stream)
         self.nnz = capi.oasis_mesh_info(self.mesh)[2]
         self.params = capi.make_params(pb.nu, pb.dt, tuple(pb.f), rtol_u, rtol_p, max_it_u, max_it_p,

@@ -62,7 +62,7 @@ def test_version_and_error_string(capi):
 def test_null_pointer_is_einval(capi):
     import ctypes as C
     out = C.c_void_p()
-    rc = capi.lib().oasis_mesh_create(3, 4, None, 1, None, None, 4, C.byref(out))
+    rc = capi.lib().oasis_mesh_create(3, 4, None, 1, None, None, 4, None, C.byref(out))
     assert rc == capi.OASIS_EINVAL
     assert b"null" in capi.lib().oasis_last_error()
 
@@ -129,13 +129,15 @@ def test_mesh_create_rejects_bad_input_before_any_device_work(capi):
     lib = capi.lib()
     tri = np.array([[0, 0], [1, 0], [0, 1]], dtype=np.float64)
 
-    def create(dim, cells, dof=None, n_dofs=3, coords=tri, n_cells=None):
+    def create(dim, cells, dof=None, n_dofs=3, coords=tri, n_cells=None, perm=None):
         cells = np.ascontiguousarray(cells, dtype=np.int32)
         d = None if dof is None else np.ascontiguousarray(dof, dtype=np.int32)
+        pm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
         out = C.c_void_p()
         rc = lib.oasis_mesh_create(dim, coords.shape[0], coords.ctypes.data,
                                    cells.shape[0] if n_cells is None else n_cells, cells.ctypes.data,
-                                   None if d is None else d.ctypes.data, n_dofs, C.byref(out))
+                                   None if d is None else d.ctypes.data, n_dofs,
+                                   None if pm is None else pm.ctypes.data, C.byref(out))
         return rc, lib.oasis_last_error().decode()
 
     assert create(4, [[0, 1, 2]])[0] == capi.OASIS_EINVAL                      # dimension
@@ -147,4 +149,14 @@ def test_mesh_create_rejects_bad_input_before_any_device_work(capi):
     rc, msg = create(2, [[0, 1, 1]])                                            # repeated vertex
     assert rc == capi.OASIS_EMESH and "repeated" in msg
     rc, msg = create(2, [[0, 1, 2]], dof=[0, 1, 1], n_dofs=2)                   # repeated dof (periodic map)
+    assert rc == capi.OASIS_EMESH and "repeated" in msg
+    # the dof renumbering must be a permutation of 0 .. n_dofs-1
+    rc, msg = create(2, [[0, 1, 2]], perm=[0, 1, 3])
+    assert rc == capi.OASIS_EINVAL and "perm" in msg
+    rc, msg = create(2, [[0, 1, 2]], perm=[0, -1, 2])
+    assert rc == capi.OASIS_EINVAL and "perm" in msg
+    rc, msg = create(2, [[0, 1, 2]], perm=[2, 0, 2])
+    assert rc == capi.OASIS_EINVAL and "permutation" in msg
+    # a renumbered periodic map: perm has one entry per dof, not per vertex
+    rc, msg = create(2, [[0, 1, 2]], dof=[0, 1, 1], n_dofs=2, perm=[1, 0])
     assert rc == capi.OASIS_EMESH and "repeated" in msg

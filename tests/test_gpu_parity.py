@@ -52,12 +52,17 @@ MESHES = {
 }
 
 
+@pytest.mark.parametrize("renumber", [False, True])
 @pytest.mark.parametrize("name", list(MESHES))
-def test_constant_matrices_match_oracle(name):
+def test_constant_matrices_match_oracle(name, renumber):
+    """Every constant matrix against the oracle's, in the caller's order; with
+    `renumber` the library stores the mesh under a seeded random dof permutation
+    (the perm of oasis_mesh_create) and must still return the caller's order."""
     c = capi()
     m = MESHES[name]()
     D = p1.Discretization(m)
-    h = c.oasis_mesh_create(m.dim, m.coords, m.cells, m.dof_of_vertex, m.n_dofs)
+    perm = WM.random_permutation(m.n_dofs, 17) if renumber else None
+    h = c.oasis_mesh_create(m.dim, m.coords, m.cells, m.dof_of_vertex, m.n_dofs, perm=perm)
     try:
         c.oasis_assemble_constant(h)
         rp, col = c.oasis_mesh_get_pattern(h)
@@ -476,23 +481,44 @@ def test_mixed_precision_per_field_error():
     assert relerr(p, s.p) <= 1e-6
 
 
-def test_permutation_invariance():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_permutation_invariance(precision):
+    """A dof renumbering handed to oasis_mesh_create (random, RCM) changes the
+    library's internal order only: the same caller-order arrays go in, and the
+    fields, the pattern and the matrices come out in the caller's order, equal to
+    the unrenumbered run to the solvers' tolerance (sums run in another order).
+    No renumbering happens on the host."""
     from paper_1602_03643_gb300.driver import IPCSRun
-    base = WP.stress_cube(6, ordering="natural")
-    perm = WM.random_permutation(base.mesh.n_dofs, 44)
-    pbp = WP.stress_cube(6, ordering="random")
-    r1 = IPCSRun(base, rtol_u=1e-12, rtol_p=1e-12)
-    r2 = IPCSRun(pbp, rtol_u=1e-12, rtol_p=1e-12)
-    try:
-        r1.step(3)
-        r2.step(3)
-        u1, p1_, _ = r1.fields()
-        u2, p2_, _ = r2.fields()
-    finally:
-        r1.close()
-        r2.close()
-    np.testing.assert_allclose(u2[:, perm], u1, atol=1e-10)
-    np.testing.assert_allclose(p2_[perm], p1_, atol=1e-9 * np.abs(p1_).max())
+    c = capi()
+    rtol = 1e-12 if precision == 0 else 1e-8
+    out = {}
+    for ordering in ("natural", "random", "rcm"):
+        pb = WP.stress_cube(6, ordering=ordering)
+        assert (pb.perm is None) == (ordering == "natural")
+        run = IPCSRun(pb, precision=precision, rtol_u=rtol, rtol_p=rtol, use_graph=1,
+                      pressure_pc=c.OASIS_PC_AMG if precision else c.OASIS_PC_JACOBI,
+                      guess=c.OASIS_GUESS_PREV_PHI)
+        try:
+            A, r0 = run.tentative_system()
+            run.step(3)
+            rp, col = c.oasis_mesh_get_pattern(run.mesh)
+            K = c.oasis_mesh_get_matrix(run.mesh, c.OASIS_MAT_K)
+            ML = c.oasis_mesh_get_matrix(run.mesh, -1)
+            out[ordering] = (run.fields(), rp, col, K, ML, A, r0)
+        finally:
+            run.close()
+    (u1, p1, f1), rp1, col1, K1, ML1, A1, r01 = out["natural"]
+    tol_u = 1e-10 if precision == 0 else 1e-6
+    for ordering in ("random", "rcm"):
+        (u2, p2, f2), rp2, col2, K2, ML2, A2, r02 = out[ordering]
+        np.testing.assert_array_equal(rp2, rp1)
+        np.testing.assert_array_equal(col2, col1)
+        np.testing.assert_allclose(K2, K1, rtol=0, atol=1e-14 * np.abs(K1).max())
+        np.testing.assert_allclose(ML2, ML1, rtol=1e-14)
+        np.testing.assert_allclose(A2, A1, rtol=0, atol=(1e-13 if precision == 0 else 1e-6) * np.abs(A1).max())
+        np.testing.assert_allclose(r02, r01, rtol=0, atol=(1e-12 if precision == 0 else 1e-6) * np.abs(r01).max())
+        assert relerr(u2, u1) <= tol_u, (ordering, relerr(u2, u1))
+        assert relerr(p2, p1) <= 10 * tol_u, (ordering, relerr(p2, p1))
 
 
 def _table1_rows():
