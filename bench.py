@@ -5,9 +5,14 @@
 
 One "step" is one full IPCS time step (assembly + Algorithm 2, d-RHS BiCGStab,
 pressure CG, normalisation, lumped update) on the device, every solve to the
-same relative residual (1e-8).  Default workload: the 3D Taylor-Green vortex on
-[-pi, pi]^3 with 64^3 x 6 tetrahedra (274,625 dofs), mixed precision, the
-three velocity components in one 3-RHS solve, the step captured in one CUDA graph.
+same relative residual (1e-8).  Default workload: the unstructured-stress cube,
+128^3 cells x 6 tetrahedra (2,146,689 dofs, 12,582,912 cells), interior vertices
+jittered by up to 20 % of the spacing, dofs in reverse Cuthill-McKee order, 3D
+Taylor-Green data; mixed precision, the three velocity components in one 3-RHS
+solve, the multigrid-preconditioned pressure CG started from the learned guess,
+the step captured in one CUDA graph.  Beside it: the same form with the previous
+correction as the guess, the same form in float64, and the plain float64 form
+(one solve per component, eager launches, Jacobi, zero guess).
 
 Prints one JSON line.  Under torchrun (N > 1) every rank runs an independent
 replica of the workload on its own GPU (the single-GPU method has no exchange
@@ -64,6 +69,67 @@ def workload_config(name, pb, precision, gpu=True):
         c |= {"solver": "scipy BiCGStab (velocity, one solve per component) and CG (pressure), Jacobi, "
                         "sparse matrices assembled per step, host cores"}
     return c
+
+
+# ---------------------------------------------------------------------- rooflines
+# DRAM bytes per launch of a family's kernel from an ncu capture (cold caches),
+# per workload, with the profile summary it comes from; valid for the kernels as
+# they stand (an entry is removed when its kernel changes)
+_S112 = "profiles/dram_traffic_products_stress112_rcm.md (stress112_rcm capture, scaled by algorithmic bytes)"
+MEASURED_TRAFFIC = {("stress128_rcm", "bicg_spmm"): (331.9e6, _S112),
+                    ("stress128_rcm", "amg_fine"): (221.9e6, _S112),
+                    ("stress128_rcm", "pcg_spmv"): (215.2e6, _S112)}
+
+
+def family_bytes(pb, nnz, args, tuning, amg):
+    """Algorithmic bytes per launch of every timed kernel family (float32 values,
+    int32 indices unless stated; N dofs, Z pattern entries, T cells, D dims; each
+    array counted once per launch, gathered operands once per row):
+      pcg_spmv     multigrid CG product w = K u on SELL-32 + 3 dots: K values and
+                   columns (16-bit offsets where the mesh has them), u gathered, r read,
+                   w written, slice pointers/lengths
+      bicg_spmm    d-RHS product of the BiCGStab: A values + columns, row pointers,
+                   x gathered, y written, the dot operand read
+      amg_fine     finest-level smoothing sweep (pre or post, SELL-32): K values +
+                   columns, 4 vectors of N, slice pointers/lengths
+      amg_transfer restriction/prolongation, averaged over the 2(L-1) launches of a
+                   V-cycle: per level 16 nnz(P) + 16 n_l + 12 n_(l+1)
+      amg_coarse   coarser-level sweeps and the dense coarsest product, averaged over
+                   their 2(L-2)+1 launches: per sweep 8 nnz_l + 20 n_l; dense 4 nc ld + 8 nc
+      bicg_vec     BiCGStab vector kernels, averaged over dir (64 N), s (52 N), and
+                   the solution/residual update with its dots (96 N), for D = 3
+      assemble     convection cell terms (80 T + 48 N) and the fused row pass (incidence
+                   and cell terms 48 T, per entry 28 Z, per row 168 N), one pair per step
+    Returns {family: (kernel, bytes per launch, formula)}."""
+    N, Z, T, D = pb.mesh.n_dofs, nnz, pb.mesh.n_cells, pb.mesh.dim
+    n_slices = (N + 31) // 32
+    out = {}
+    if amg:
+        have16 = any(c["col16"] and c["us"] > 0 for c in tuning["candidates"])
+        cb = 2 if have16 else 4
+        out["pcg_spmv"] = ("k_amg_cg_spmv<Mixed> (multigrid CG: w = K u on SELL-32 + 3 dots)",
+                           (4 + cb) * Z + 12 * N + 8 * n_slices, f"(4+{cb}) Z + 12 N + 8 N/32")
+        out["amg_fine"] = ("k_amg_fine<float> (finest-level damped-Jacobi sweep on SELL-32)",
+                           (4 + cb) * Z + 16 * N + 8 * n_slices, f"(4+{cb}) Z + 16 N + 8 N/32")
+        rows, nz, pn = amg["rows"], amg["nnz"], amg["p_nnz"]
+        L = amg["levels"]
+        if pn:
+            tb = sum(16 * pn[l] + 16 * rows[l] + 12 * rows[l + 1] for l in range(len(pn)))
+            out["amg_transfer"] = ("k_amg_restrict / k_amg_prolong (CSR, every level)", tb / (2 * len(pn)),
+                                   "per V-cycle sum_l 16 nnz(P_l) + 16 n_l + 12 n_(l+1), over 2(L-1) launches")
+        nc = rows[L - 1]
+        ld = (nc + 3) // 4 * 4
+        cbytes = sum(2 * (8 * nz[l] + 20 * rows[l]) for l in range(1, L - 1)) + 4 * nc * ld + 8 * nc
+        out["amg_coarse"] = ("k_amg_pre / k_amg_post (CSR, levels >= 1) and k_amg_dense",
+                             cbytes / (2 * (L - 2) + 1), "per V-cycle sum_l 2 (8 nnz_l + 20 n_l) + 4 nc ld + 8 nc, "
+                                                         "over 2(L-2)+1 launches")
+    out["bicg_spmm"] = (f"k_bicg_spmm<Mixed,{D},{D}> (tentative BiCGStab: {D}-RHS product A x + dots, row tiles)",
+                        8 * Z + 4 * (N + 1) + 12 * D * N, f"8 Z + 4 N + 12 D N")
+    out["bicg_vec"] = ("k_bicg_dir / k_bicg_s / k_bicg_xr (BiCGStab vector updates + dots)",
+                       (64 + 52 + 96) * N * D / 3 / 3, "(64 + 52 + 96) N / 3 per launch (D = 3)")
+    out["assemble"] = ("k_cell_beta + k_assemble (convection assembly + Algorithm 2, one pair per step)",
+                       80 * T + 48 * N + 48 * T + 28 * Z + 168 * N, "128 T + 28 Z + 216 N per pair")
+    return out
 
 
 # ---------------------------------------------------------------------- clocks
@@ -256,7 +322,8 @@ def run_ours(args, rank, world):
     h2d = len(pb.dirichlet) * pb.mesh.dim * 8
     d2h = (pb.mesh.dim + 1) * N * 8
 
-    # ---- dominant kernel, timed live with CUDA events (eager steps, same solver)
+    # ---- every kernel family, timed live with CUDA events (eager steps of the same
+    # configuration; the library records events around each launch of a family)
     run_e = make(capi.OASIS_MIXED, graph=0,
                  guess=capi.OASIS_GUESS_LEARNED if learned else capi.OASIS_GUESS_PREV_PHI)
     net_e = None
@@ -266,92 +333,83 @@ def run_ours(args, rank, world):
     run_e.set_dirichlet_for_next_step()
     capi.oasis_step(run_e.solver, stream, want_stats=False)
     capi.oasis_profile(run_e.solver, True)
-    for _ in range(2):
+    n_prof = 2
+    for _ in range(n_prof):
         flush.fill_(1.0)
         capi.oasis_step(run_e.solver, stream, want_stats=False)
     torch.cuda.synchronize(dev)
     fam = {f: capi.oasis_profile_read(run_e.solver, f) for f in capi.PROF_FAMILIES}
-    nnz = run.nnz
-    # algorithmic bytes of one fused pressure-CG iteration (SELL-32 K, float32
-    # values, int32 columns or 16-bit offsets, as the tuned kernel reads them):
-    # K values + columns; slice pointers/lengths 8 per 32 rows; vectors read
-    # dinv, r, w, s, p, x-delta (24 N) and written p, s, x-delta, r, w (20 N)
-    n_slices = (N + 31) // 32
     tun_e = capi.oasis_get_tuning(run_e.solver)
     amg_info = capi.oasis_get_amg_info(run_e.solver) if pc == capi.OASIS_PC_AMG else None
-    D = pb.mesh.dim
-    # candidate kernels and their algorithmic bytes per launch (float32 values,
-    # int32 columns; N dofs, nnz pattern entries)
-    cands = {}
-    if pc == capi.OASIS_PC_AMG:
-        # w = K u on SELL-32 with three dot products: K values + columns (16-bit
-        # offsets where the mesh has them), u gathered (4 N), r read (4 N), w
-        # written (4 N), slice pointers/lengths
-        have16 = any(c["col16"] and c["us"] > 0 for c in tun_e["candidates"])
-        cands["pcg_spmv"] = ("k_amg_cg_spmv<Mixed> (multigrid CG: w = K u on SELL-32 + 3 dots)",
-                             {"col16": bool(have16)}, (4 + (2 if have16 else 4)) * nnz + 12 * N + 8 * n_slices)
-    else:
-        shape = tun_e["candidates"][tun_e["chosen"] - 1]
-        col_bytes = 2 if shape["col16"] else 4
-        cands["pcg_spmv"] = ("k_pcg_iter_sell<Mixed> (fused Jacobi-CG iteration on SELL-32 + vector updates + 3 dots)",
-                             shape, (4 + col_bytes) * nnz + 44 * N + 8 * n_slices)
-    # d-RHS product of the tentative BiCGStab (both modes): A values + columns
-    # (8 nnz), row pointers (4 N), x gathered (4 D N), y written (4 D N), the
-    # dot operand read (4 D N)
-    cands["bicg_spmm"] = (f"k_bicg_spmm<Mixed,{D},{D}> (tentative BiCGStab: {D}-RHS product A x + dots, row tiles)",
-                          None, 8 * nnz + 4 * (N + 1) + 12 * D * N)
+    run_e.close()
+    if net_e is not None:
+        net_e.close()
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
-    run_e.close()
-
-    def roof(fam):
-        kernel, shape, nbytes = cands[fam]
-        n_l, ms_l = fam_t[fam]
-        ach = nbytes / (ms_l / n_l / 1e3) / 1e9 if n_l else None
-        return {"bound": "hbm", "kernel": kernel, "shape": shape,
-                "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": (ach / peak) if ach else None,
-                "peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if "hbm_gbs" in peaks
-                                else "of fallback 6.8 TB/s"),
-                "algorithmic_bytes_per_launch": nbytes, "launches_timed": n_l,
-                "avg_launch_us": (ms_l / n_l * 1e3) if n_l else None,
-                "share_of_timed_families": ms_l / max(sum(m for _, m in fam_t.values()), 1e-30),
-                "traffic": measured_traffic.get((args.workload, fam, args.pc), (None,))[0],
-                "traffic_source": measured_traffic.get((args.workload, fam, args.pc), (None, None))[1],
-                "note": ("algorithmic bytes %.1f MB per launch vs 129 MB L2: at this size the matrix and vectors "
-                         "stay L2-resident across iterations" % (nbytes / 1e6))
-                if nbytes < 100e6 else "working set larger than L2"}
-
-    # DRAM bytes per launch from ncu captures of these kernels on this workload
-    # (cold caches), valid for the kernels as they stand
-    measured_traffic = {("tg3d_64", "bicg_spmm", "amg"): (39.88e6, "profiles/k_bicg_spmm_tg3d64_traffic.md"),
-                        ("tg3d_64", "bicg_spmm", "jacobi"): (39.88e6, "profiles/k_bicg_spmm_tg3d64_traffic.md")}
-    fam_t = {f: fam[f] for f in cands}
-    dominant = max(cands, key=lambda f: fam_t[f][1])
-    roofline = roof(dominant)
-    roofline_other = roof([f for f in cands if f != dominant][0])
+    fams = family_bytes(pb, run.nnz, args, tun_e, amg_info)
+    table = {}
+    for f, (kernel, nbytes, per) in fams.items():
+        n_l, ms_l = fam.get(f, (0, 0.0))
+        if not n_l:
+            continue
+        ach = nbytes / (ms_l / n_l / 1e3) / 1e9
+        table[f] = {"kernel": kernel, "bound": "hbm", "algorithmic_bytes_per_launch": nbytes,
+                    "bytes_counted": per, "launches": n_l, "avg_launch_us": ms_l / n_l * 1e3,
+                    "ms_per_step": ms_l / n_prof, "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak,
+                    "traffic": MEASURED_TRAFFIC.get((args.workload, f), (None,))[0],
+                    "traffic_source": MEASURED_TRAFFIC.get((args.workload, f), (None, None))[1]}
+    # the dominant kernel: the single-kernel family (one kernel, one launch shape)
+    # that takes the most time in the step
+    single = [f for f in ("pcg_spmv", "bicg_spmm", "amg_fine") if f in table]
+    dominant = max(single, key=lambda f: table[f]["ms_per_step"])
+    roofline = dict(table[dominant])
+    roofline["family"] = dominant
+    roofline["peak_source"] = ("of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if "hbm_gbs" in peaks
+                               else "of fallback 6.8 TB/s")
+    roofline["note"] = ("working set larger than L2" if table[dominant]["algorithmic_bytes_per_launch"] > 129e6
+                        else "algorithmic bytes below the 129 MB L2: the operands stay L2-resident across "
+                             "iterations; an L2 figure")
     kernel_share = {f: {"launches": n, "ms": m} for f, (n, m) in fam.items()}
 
-    # ---- the plain float64 GPU form at the same residual (comparison): float64,
-    # one solve per velocity component, eager launches, pressure guess p = p*
-    fp64 = None
+    # ---- float64 forms at the same 1e-8 residual (comparison arms)
+    def short_form(run_, k):
+        for _ in range(max(1, args.warmup // 2)):
+            capi.oasis_step(run_.solver, stream, want_stats=False)
+        ms_, st_ = timed_steps(run_, k)
+        return ms_, st_
+
+    fp64 = fp64_matched = None
     if not args.skip_fp64:
+        # the same form as the headline but float64 throughout (graph, batched,
+        # multigrid, previous-phi guess): isolates what the precision buys
+        runm = make(capi.OASIS_FP64, graph=0 if args.eager else 1, guess=capi.OASIS_GUESS_PREV_PHI)
+        runm.set_dirichlet_for_next_step()
+        km = max(3, args.steps // 4)
+        msm, stm = short_form(runm, km)
+        runm.close()
+        fp64_matched = {"form": "float64, batched, graph, multigrid, previous-phi guess",
+                        "steps_per_s": km / (msm / 1e3), "ms_per_step": msm / km,
+                        "it_u_mean": float(np.mean([max(s["it_u"]) for s in stm])),
+                        "it_p_mean": float(np.mean([s["it_p"] for s in stm])),
+                        "failed_steps": sum(s["status"] != 0 for s in stm)}
+        # the plain float64 GPU form: float64, one solve per velocity component,
+        # eager launches, pressure guess p = p*, Jacobi-PCG
         run64 = make(capi.OASIS_FP64, graph=0, guess=capi.OASIS_GUESS_ZERO, batch=0,
                      pressure_pc=capi.OASIS_PC_JACOBI)
         run64.set_dirichlet_for_next_step()
-        for _ in range(max(1, args.warmup // 2)):
-            capi.oasis_step(run64.solver, stream, want_stats=False)
-        k64 = max(3, args.steps // 2)
-        ms64, st64 = timed_steps(run64, k64)
+        k64 = max(3, args.steps // 10)
+        ms64, st64 = short_form(run64, k64)
         run64.close()
         fp64 = {"form": "float64, unbatched, eager, guess p*, Jacobi-PCG",
                 "steps_per_s": k64 / (ms64 / 1e3), "ms_per_step": ms64 / k64,
                 "it_u_mean": float(np.mean([max(s["it_u"]) for s in st64])),
-                "it_p_mean": float(np.mean([s["it_p"] for s in st64]))}
+                "it_p_mean": float(np.mean([s["it_p"] for s in st64])),
+                "failed_steps": sum(s["status"] != 0 for s in st64)}
 
     prev_form = None
     if learned and not args.skip_compare:
@@ -360,9 +418,20 @@ def run_ours(args, rank, world):
         runp.set_dirichlet_for_next_step()
         msp, stp, _ = timed_form(runp)
         runp.close()
-        prev_form = {"form": "mixed, batched, graph, previous-phi guess (no network)",
+        prev_form = {"form": "mixed, batched, graph, multigrid, previous-phi guess (no network)",
                      "steps_per_s": world * args.steps / (msp / 1e3), "ms_per_step": msp / args.steps,
                      "it_p_mean": float(np.mean([s["it_p"] for s in stp]))}
+    per_rank = value / world
+    ratios = {}
+    if fp64_matched:
+        ratios["headline_over_fp64_matched"] = per_rank / fp64_matched["steps_per_s"]
+    if fp64:
+        ratios["headline_over_fp64_plain"] = per_rank / fp64["steps_per_s"]
+    if prev_form:
+        ratios["learned_over_previous_phi"] = per_rank / (prev_form["steps_per_s"] / world)
+        if fp64_matched:
+            ratios["mixed_over_fp64_matched_previous_phi"] = (prev_form["steps_per_s"] / world) / \
+                fp64_matched["steps_per_s"]
     if learned:
         gr = np.array([s["guess_res"] for s in stats])
         train_info |= {"used_fraction": float(np.mean([s["guess_used"] == capi.OASIS_GUESS_LEARNED
@@ -406,7 +475,10 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed: f32 inner Krylov, f64 residual)"
                  + ("; bf16 network weights, f32 accumulation" if learned else ""),
-        "data": "synthetic (seeded Taylor-Green initial field on a Kuhn tetrahedral mesh)",
+        "data": "synthetic (seeded Taylor-Green initial field on a jittered Kuhn tetrahedral mesh)"
+                if args.workload.startswith("stress") else
+                "synthetic (seeded perturbed Poiseuille flow in the channel)" if args.workload == "channel" else
+                "synthetic (Taylor-Green initial field on a Kuhn simplex mesh)",
         "config": workload_config(args.workload, pb, "mixed") | {
             "parallelism": f"replicas x{world}",
             "pressure_guess": "learned (judged against previous phi)" if learned else "previous phi",
@@ -417,12 +489,14 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "clocks": clocks,
         "roofline": roofline,
-        "roofline_next_kernel": roofline_other,
+        "roofline_families": table,
         "solver": {"it_u_mean": it_u, "it_p_mean": it_p, "sweeps_u_mean": sw_u, "sweeps_p_mean": sw_p,
                    "it_mass_mean": it_m, "it_scalar_max_mean": it_c,
                    "failed_steps": len(bad), "res_p_last": stats[-1]["res_p"]},
         "fp64_gpu": fp64,
+        "fp64_matched": fp64_matched,
         "mixed_prev_phi": prev_form,
+        "ratios": ratios,
         "learned_guess": train_info,
         "cg_autotune": tuning,
         "multigrid": amg_info,
@@ -595,10 +669,10 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tg3d_64")
+    ap.add_argument("--workload", default="stress128_rcm")
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

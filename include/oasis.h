@@ -410,6 +410,9 @@ typedef struct oasis_amg_info {
     int64_t rows[16];
     int64_t nnz[16];
     double setup_s;                /* host setup time (once per mesh) */
+    int64_t p_nnz[16];             /* entries of the prolongation from level k+1 to level k
+                                      (k < levels - 1); its transpose, the restriction, has
+                                      as many */
 } oasis_amg_info;
 int oasis_get_amg_info(const oasis_solver* s, oasis_amg_info* out);
 
@@ -434,6 +437,13 @@ int oasis_get_tuning(const oasis_solver* s, oasis_tuning* out);
 #define OASIS_PROF_GUESS 6         /* learned guess: input scaling, network forward, judge */
 #define OASIS_PROF_AMG 7           /* multigrid V-cycles of the pressure CG */
 #define OASIS_PROF_MASS 8          /* consistent-mass update: the mass CG's start and iterations */
+/* Parts of OASIS_PROF_AMG (each V-cycle kernel is counted in one of them): */
+#define OASIS_PROF_AMG_FINE 9      /* smoothing sweeps of the finest level (the mesh's K) */
+#define OASIS_PROF_AMG_TRANSFER 10 /* restriction P^T and prolongation P, every level */
+#define OASIS_PROF_AMG_COARSE 11   /* smoothing sweeps of the coarser levels and the dense
+                                      coarsest solve */
+#define OASIS_PROF_BICG_VEC 12     /* vector kernels of the tentative BiCGStab iteration (search
+                                      direction, s update, solution/residual update + dots) */
 
 /* enable = 1: from now on, eager steps record CUDA events around the launches
  * of the kernel families above; the counters are reset by every call. */

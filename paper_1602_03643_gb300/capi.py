@@ -53,7 +53,7 @@ class oasis_params(C.Structure):
 
 class oasis_amg_info(C.Structure):
     _fields_ = [("levels", C.c_int32), ("rows", C.c_int64 * 16), ("nnz", C.c_int64 * 16),
-                ("setup_s", C.c_double)]
+                ("setup_s", C.c_double), ("p_nnz", C.c_int64 * 16)]
 
 
 class oasis_tuning(C.Structure):
@@ -346,7 +346,8 @@ def oasis_get_tentative_system(solver, dim, n, nnz, stream=None):
 
 
 PROF_FAMILIES = {"pcg_spmv": 0, "bicg_spmm": 1, "assemble": 2, "pcg_update": 3, "update": 4,
-                 "pressure_rhs": 5, "guess": 6, "amg": 7, "mass": 8}
+                 "pressure_rhs": 5, "guess": 6, "amg": 7, "mass": 8, "amg_fine": 9, "amg_transfer": 10,
+                 "amg_coarse": 11, "bicg_vec": 12}
 
 
 def oasis_profile(solver, enable=True):
@@ -418,7 +419,7 @@ def oasis_get_amg_info(solver):
     t = oasis_amg_info()
     check(lib().oasis_get_amg_info(solver, C.byref(t)))
     return {"levels": t.levels, "rows": list(t.rows[:t.levels]), "nnz": list(t.nnz[:t.levels]),
-            "setup_s": t.setup_s}
+            "setup_s": t.setup_s, "p_nnz": list(t.p_nnz[:max(0, t.levels - 1)])}
 
 
 def oasis_amg_apply(solver, r, u, stream=None):

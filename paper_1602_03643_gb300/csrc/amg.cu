@@ -393,6 +393,7 @@ void amg_build(Mesh& m, cudaStream_t s) {
         const double wP = 4.0 / (3.0 * spectral_radius(F, diagonal(F)));
         const HCsr P = smoothed_prolongator(F, agg, nagg, wP);
         const HCsr R = transpose(P);
+        h->pnnzs.push_back(P.nnz());
         upload_csr(L->p_rp, L->p_ci, L->p32, L->p64, P, s);
         upload_csr(L->r_rp, L->r_ci, L->r32, L->r64, R, s);
         auto lanes = [](int64_t nnz, int64_t rows) {
@@ -666,8 +667,16 @@ __global__ void __launch_bounds__(kBlock) k_amg_prolong(int64_t n, const int32_t
 }
 
 template <class V>
-void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const KrylovState* st, cudaStream_t s) {
+void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const KrylovState* st, cudaStream_t s,
+                const ProfHook* prof) {
     const int L = (int)h.lv.size();
+    int ph = -1;
+    auto pbeg = [&](int family) {
+        if (prof && prof->begin) ph = prof->begin(prof->ctx, s, family);
+    };
+    auto pend = [&]() {
+        if (prof && prof->end) prof->end(prof->ctx, s, ph);
+    };
     auto vec = [](DBuf<double>& b) { return reinterpret_cast<V*>(b.p); };
     // level inputs: rin[0] = r; outputs: xo[0] = u
     auto rin = [&](int l) -> const V* { return l == 0 ? r : vec(wk.rin[l]); };
@@ -680,50 +689,65 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
         if (l == 0 && h.fine.ptr) {
             const V* fv = pick<V>(h.fine.v32, h.fine.v64);
             const int g = fine_grid(h.fine);
+            pbeg(OASIS_PROF_AMG_FINE);
             if (h.fine.dcol)
                 k_amg_fine<V, true, true><<<g, kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), nullptr, vec(wk.x[0]),
                                                                vec(wk.res[0]), st);
             else
                 k_amg_fine<V, false, true><<<g, kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), nullptr, vec(wk.x[0]),
                                                                 vec(wk.res[0]), st);
+            pend();
         } else {
+            pbeg(l == 0 ? OASIS_PROF_AMG_FINE : OASIS_PROF_AMG_COARSE);
             AMG_DISPATCH(lv.g_a, k_amg_pre, lv.n, lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]),
                          vec(wk.res[l]), st);
+            pend();
         }
         const int64_t nc = l + 1 < L ? h.lv[l + 1]->n : h.nc;
         const V* rv = pick<V>(lv.r32.p, lv.r64.p);
+        pbeg(OASIS_PROF_AMG_TRANSFER);
         AMG_DISPATCH(lv.g_r, k_amg_restrict, nc, nc, lv.r_rp.p, lv.r_ci.p, rv, vec(wk.res[l]), vec(wk.rin[l + 1]),
                      st);
+        pend();
     }
+    pbeg(OASIS_PROF_AMG_COARSE);
     k_amg_dense<V><<<(int)std::max<int64_t>(1, h.nc), kDenseBlock, 0, s>>>(h.nc, h.ld, pick<V>(h.inv32.p, h.inv64.p),
                                                                      vec(wk.rin[L]),
                                                          vec(wk.xo[L]), st);
+    pend();
     for (int l = L - 1; l >= 0; --l) {
         const AmgLevelDev& lv = *h.lv[l];
         const V* a = pick<V>(lv.a32, lv.a64);
         const V* d = pick<V>(lv.d32.p, lv.d64.p);
         const V w = (V)lv.omega;
         const V* pv = pick<V>(lv.p32.p, lv.p64.p);
+        pbeg(OASIS_PROF_AMG_TRANSFER);
         AMG_DISPATCH(lv.g_p, k_amg_prolong, lv.n, lv.n, lv.p_rp.p, lv.p_ci.p, pv, xo(l + 1), vec(wk.x[l]), st);
+        pend();
         if (l == 0 && h.fine.ptr) {
             const V* fv = pick<V>(h.fine.v32, h.fine.v64);
             const int g = fine_grid(h.fine);
+            pbeg(OASIS_PROF_AMG_FINE);
             if (h.fine.dcol)
                 k_amg_fine<V, true, false><<<g, kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), vec(wk.x[0]), xo(0),
                                                                 nullptr, st);
             else
                 k_amg_fine<V, false, false><<<g, kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), vec(wk.x[0]), xo(0),
                                                                  nullptr, st);
+            pend();
         } else {
+            pbeg(l == 0 ? OASIS_PROF_AMG_FINE : OASIS_PROF_AMG_COARSE);
             AMG_DISPATCH(lv.g_a, k_amg_post, lv.n, lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]), xo(l), st);
+            pend();
         }
     }
     OASIS_CUDA(cudaGetLastError());
 }
 #undef AMG_DISPATCH
 
-template void amg_vcycle<float>(const AmgHierarchy&, AmgWork&, const float*, float*, const KrylovState*, cudaStream_t);
+template void amg_vcycle<float>(const AmgHierarchy&, AmgWork&, const float*, float*, const KrylovState*, cudaStream_t,
+                                const ProfHook*);
 template void amg_vcycle<double>(const AmgHierarchy&, AmgWork&, const double*, double*, const KrylovState*,
-                                 cudaStream_t);
+                                 cudaStream_t, const ProfHook*);
 
 }  // namespace oasis

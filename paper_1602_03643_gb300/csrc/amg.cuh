@@ -66,6 +66,7 @@ struct AmgHierarchy {
     double setup_s = 0.0;
     std::vector<int64_t> sizes;                      // rows per level (incl. coarsest)
     std::vector<int64_t> nnzs;
+    std::vector<int64_t> pnnzs;                      // prolongator nnz per level (level k+1 -> k)
 };
 
 // Build (once per mesh) from the assembled float64 K; no-op if present.
@@ -77,9 +78,18 @@ struct AmgWork {
     void alloc(const AmgHierarchy& h, size_t vbytes);
 };
 
+// Optional timing of the V-cycle's kernels by family (eager profiling): begin
+// returns a handle that end closes; both are no-ops when the hook is absent.
+struct ProfHook {
+    void* ctx = nullptr;
+    int (*begin)(void* ctx, cudaStream_t s, int family) = nullptr;
+    void (*end)(void* ctx, cudaStream_t s, int handle) = nullptr;
+};
+
 // u = M r with one V(1,1) cycle (device arrays of n_0 values of type V).  The
 // kernels return at once when `done` (the CG's col_done / in_done flags) is set.
 template <class V>
-void amg_vcycle(const AmgHierarchy& h, AmgWork& w, const V* r, V* u, const KrylovState* st, cudaStream_t s);
+void amg_vcycle(const AmgHierarchy& h, AmgWork& w, const V* r, V* u, const KrylovState* st, cudaStream_t s,
+                const ProfHook* prof = nullptr);
 
 }  // namespace oasis

@@ -840,6 +840,7 @@ int oasis_get_amg_info(const oasis_solver* solver, oasis_amg_info* out) {
         for (int k = 0; k < out->levels; ++k) {
             out->rows[k] = h.sizes[k];
             out->nnz[k] = h.nnzs[k];
+            out->p_nnz[k] = k < (int)h.pnnzs.size() ? h.pnnzs[k] : 0;
         }
         out->setup_s = h.setup_s;
     });

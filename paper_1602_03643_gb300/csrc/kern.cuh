@@ -228,17 +228,40 @@ __device__ __forceinline__ bool grid_sum(A (&v)[NV], double (&tot)[NV], void* pa
     return true;
 }
 
-// Lightweight deterministic grid sum for per-iteration Krylov scalars: values in
-// the kernel's value type T (float in the mixed path, whose inner iterations are
-// float32 anyway; double in the float64 path), shuffle trees inside warps and
-// blocks, one partial per block, and a pairwise-ordered sum of the partials by
-// the block that takes the last ticket.  A handful of instructions per value
-// and warp, against ~100 for a float-float tree.
-// Stage 1: the block's sum of v (warp shuffle trees, then the warps' sums in a
-// shuffle tree) stored as partial[index][0..NV).  Every thread of the block
-// calls it; on return the shared scratch may be reused.
+// Deterministic grid sum for the per-iteration Krylov scalars (dot products of
+// the inner solves).  T is the kernel's value type: double in the float64 path;
+// float in the mixed path, where each thread's products and its running sum over
+// its rows stay float32 and the 32 lanes of a warp are summed by a float32
+// shuffle tree (pairwise), while every sum above the warp -- the block's partial
+// over its warps and the sum of the blocks' partials -- is carried in
+// float-float (~48 bits), so the totals reach float64 quality however many
+// blocks there are.  A float-float partial costs a few dozen float
+// instructions per value in one warp per block (a float64 instruction is ~1/64
+// of the float32 rate on GB300 and would cost microseconds per reduction).
+// Partial storage per value: double (T = double) or float2 (hi, lo).
+template <class T>
+struct LiteAcc {
+    using type = double;
+};
+template <>
+struct LiteAcc<float> {
+    using type = ff;
+};
+__device__ __forceinline__ double lite_of(double x) { return x; }
+__device__ __forceinline__ ff lite_of(float x) { return {x, 0.f}; }
+__device__ __forceinline__ double lite_load(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ ff lite_load(const ff* p) {
+    const float2 f = __ldcg(reinterpret_cast<const float2*>(p));
+    return {f.x, f.y};
+}
+
+// Stage 1: the block's sum of v stored as partial[index][0..NV) (type
+// LiteAcc<T>::type).  Every thread of the block calls it; on return the shared
+// scratch may be reused.
 template <int NV, class T>
-__device__ __forceinline__ void block_partial_lite(T (&v)[NV], T* partial, int64_t index) {
+__device__ __forceinline__ void block_partial_lite(T (&v)[NV], void* partial_raw, int64_t index) {
+    using A = typename LiteAcc<T>::type;
+    A* partial = reinterpret_cast<A*>(partial_raw);
     __shared__ T sh[NV][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
 #pragma unroll
@@ -251,9 +274,9 @@ __device__ __forceinline__ void block_partial_lite(T (&v)[NV], T* partial, int64
     if (wid == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            T x = lane < nw ? sh[k][lane] : (T)0;
+            A x = lite_of(lane < nw ? sh[k][lane] : (T)0);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            for (int o = 16; o > 0; o >>= 1) acc_add(x, acc_shfl(x, o));
             if (lane == 0) partial[(size_t)index * NV + k] = x;
         }
     }
@@ -261,52 +284,57 @@ __device__ __forceinline__ void block_partial_lite(T (&v)[NV], T* partial, int64
 }
 
 // Stage 2: after the block has stored its partials, the block that takes the
-// last ticket sums all `count` partials (pairwise order fixed by the block
-// size) and returns true with the totals; the ticket is reset for the next use.
+// last ticket sums all `count` partials in LiteAcc precision (order fixed by the
+// block size) and returns true with the totals; the ticket is reset for the
+// next use.
 template <int NV, class T>
-__device__ __forceinline__ bool grid_finish_lite(double (&tot)[NV], const T* partial, int64_t count, uint32_t* ticket) {
-    __shared__ T sh[NV][32];
+__device__ __forceinline__ bool grid_finish_lite(double (&tot)[NV], const void* partial_raw, int64_t count,
+                                                 uint32_t* ticket) {
+    using A = typename LiteAcc<T>::type;
+    const A* partial = reinterpret_cast<const A*>(partial_raw);
+    __shared__ A sh[NV][32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
     if (threadIdx.x == 0) last = take_last_ticket(ticket);
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    T s[NV];
+    A s[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) s[k] = 0;
+    for (int k = 0; k < NV; ++k) acc_zero(s[k]);
     // the partials are read 4 per thread at a time (independent loads in
     // flight) and added in the same order as a plain strided loop would
     const int64_t G = count, B = (int64_t)blockDim.x;
     int64_t b = threadIdx.x;
     for (; b + 3 * B < G; b += 4 * B) {
-        T x[4][NV];
+        A x[4][NV];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int k = 0; k < NV; ++k) x[u][k] = __ldcg(&partial[(size_t)(b + u * B) * NV + k]);
+            for (int k = 0; k < NV; ++k) x[u][k] = lite_load(&partial[(size_t)(b + u * B) * NV + k]);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int k = 0; k < NV; ++k) s[k] += x[u][k];
+            for (int k = 0; k < NV; ++k) acc_add(s[k], x[u][k]);
     }
     for (; b < G; b += B) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) s[k] += __ldcg(&partial[(size_t)b * NV + k]);
+        for (int k = 0; k < NV; ++k) acc_add(s[k], lite_load(&partial[(size_t)b * NV + k]));
     }
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+        for (int o = 16; o > 0; o >>= 1) acc_add(s[k], acc_shfl(s[k], o));
         if (lane == 0) sh[k][wid] = s[k];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            T x = 0;
-            for (int w = 0; w < nw; ++w) x += sh[k][w];
-            tot[k] = (double)x;
+            A x;
+            acc_zero(x);
+            for (int w = 0; w < nw; ++w) acc_add(x, sh[k][w]);
+            tot[k] = acc_double(x);
         }
         *ticket = 0u;
     }
@@ -316,9 +344,8 @@ __device__ __forceinline__ bool grid_finish_lite(double (&tot)[NV], const T* par
 // One partial per block, then the last block sums them.
 template <int NV, class T>
 __device__ __forceinline__ bool grid_sum_lite(T (&v)[NV], double (&tot)[NV], void* partial_raw, uint32_t* ticket) {
-    T* partial = reinterpret_cast<T*>(partial_raw);
-    block_partial_lite<NV, T>(v, partial, blockIdx.x);
-    return grid_finish_lite<NV, T>(tot, partial, gridDim.x, ticket);
+    block_partial_lite<NV, T>(v, partial_raw, blockIdx.x);
+    return grid_finish_lite<NV, T>(tot, partial_raw, gridDim.x, ticket);
 }
 
 // Limit of every bounded device-side wait (~2 s at 2 GHz).

@@ -216,6 +216,9 @@ __global__ void __launch_bounds__(kBlock) k_net_l1(NetArgs a) {
 // epilogue (relu, readout, skip terms), the two column halves added in a fixed
 // order.
 constexpr int kRec = 8;                            // floats per inference record
+// Inference path: layer 1 stores h1 and layer 2 gathers it (true), or layer 1
+// writes the 32-byte records and layer 2 rebuilds h1 of every neighbour (false).
+constexpr bool kInferStoredH1 = true;
 
 __global__ void __launch_bounds__(kBlock) k_net_rec(NetArgs a) {
     const int lane = threadIdx.x & 31, lg = lane & (kGroup - 1);
@@ -348,6 +351,11 @@ struct L1Lane {
     }
 };
 
+// STORED: h1 of every row was written by k_net_l1 ([n][32] float32); a row's
+// group loads its own h1 and each neighbour's as one 16-byte load per lane (the
+// lane's 4 channels), the neighbour's index broadcast by one shuffle.  Else h1
+// of the row and of each neighbour is rebuilt from the 32-byte records.
+template <bool STORED>
 __global__ void __launch_bounds__(kTcThreads, 4) k_net_l2_tc(NetArgs a) {
     extern __shared__ __align__(1024) unsigned char tc_dsm[];
     unsigned char* base = tc_dsm + ((1024 - (smem_addr(tc_dsm) & 1023)) & 1023);
@@ -402,13 +410,44 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_net_l2_tc(NetArgs a) {
             const int cnt = (int)(e - b);
             const int maxcnt = __reduce_max_sync(0xffffffffu, cnt);
             float hv[4] = {0.f, 0.f, 0.f, 0.f};
+            float ms[4] = {0.f, 0.f, 0.f, 0.f};
+            float deg = 0.f;
+            if constexpr (STORED) {
+                const float4* __restrict__ h4 = reinterpret_cast<const float4*>(a.h1);
+                if (ok) {
+                    const float4 hi = h4[(size_t)i * (kH / 4) + lg];
+                    hv[0] = hi.x;
+                    hv[1] = hi.y;
+                    hv[2] = hi.z;
+                    hv[3] = hi.w;
+                }
+                for (int c0 = 0; c0 < maxcnt; c0 += kGroup) {
+                    const int32_t jl = c0 + lg < cnt ? a.col[b + c0 + lg] : -1;
+                    float4 v[kGroup];
+                    int use[kGroup];
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u) {
+                        const int32_t j = __shfl_sync(0xffffffffu, jl, gb + u);
+                        use[u] = j >= 0 && j != i;
+                        v[u] = use[u] ? h4[(size_t)j * (kH / 4) + lg] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u) {
+                        if (use[u]) {
+                            ms[0] += v[u].x;
+                            ms[1] += v[u].y;
+                            ms[2] += v[u].z;
+                            ms[3] += v[u].w;
+                            deg += 1.f;
+                        }
+                    }
+                }
+            } else {
             if (ok) {
                 const float4 r0 = rec4[(size_t)i * 2], r1 = rec4[(size_t)i * 2 + 1];
                 const float in[6] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y};
                 w1.h(in, hv);
             }
-            float ms[4] = {0.f, 0.f, 0.f, 0.f};
-            float deg = 0.f;
             for (int c0 = 0; c0 < maxcnt; c0 += kGroup) {
                 const int32_t j = c0 + lg < cnt ? a.col[b + c0 + lg] : -1;
                 const bool use = j >= 0 && j != i;
@@ -430,6 +469,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_net_l2_tc(NetArgs a) {
                         deg += 1.f;
                     }
                 }
+            }
             }
             const float invdeg = deg > 0.f ? 1.f / deg : 0.f;
             const float mv[4] = {ms[0] * invdeg, ms[1] * invdeg, ms[2] * invdeg, ms[3] * invdeg};
@@ -687,8 +727,9 @@ Net* net_create(const Mesh& m) {
     N->rec.alloc((size_t)m.n * kRec);
     OASIS_CUDA(cudaMemset(N->err.p, 0, sizeof(int32_t)));
     OASIS_CUDA(cudaGetLastError());
-    OASIS_CUDA(cudaFuncSetAttribute(k_net_l2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
-    OASIS_CUDA(cudaFuncSetAttribute(k_net_l2_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+    OASIS_CUDA(cudaFuncSetAttribute(k_net_l2_tc<kInferStoredH1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kTcSmem));
+    OASIS_CUDA(cudaFuncSetAttribute(k_net_l2_tc<kInferStoredH1>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                     (int)cudaSharedmemCarveoutMaxShared));
     // resident blocks per SM from the kernel's registers, shared memory, threads
     // and tensor-memory columns (the runtime's occupancy query reports one block
@@ -696,7 +737,7 @@ Net* net_create(const Mesh& m) {
     int per_sm_tc = 0;
     {
         cudaFuncAttributes fa{};
-        OASIS_CUDA(cudaFuncGetAttributes(&fa, k_net_l2_tc));
+        OASIS_CUDA(cudaFuncGetAttributes(&fa, k_net_l2_tc<kInferStoredH1>));
         int dev = 0, regs_sm = 0, smem_sm = 0, thr_sm = 0, resv = 0;
         OASIS_CUDA(cudaGetDevice(&dev));
         OASIS_CUDA(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
@@ -744,8 +785,13 @@ NetArgs net_args(Net& N, const float* x, float* y, const float* t) {
 
 void net_forward(Net& N, const float* x, float* y, cudaStream_t s) {
     const NetArgs a = net_args(N, x, y, nullptr);
-    k_net_rec<<<N.grid_fwd, kBlock, 0, s>>>(a);
-    k_net_l2_tc<<<N.grid_tc, kTcThreads, kTcSmem, s>>>(a);
+    if (kInferStoredH1) {
+        k_net_l1<<<N.grid_fwd, kBlock, 0, s>>>(a);
+        k_net_l2_tc<true><<<N.grid_tc, kTcThreads, kTcSmem, s>>>(a);
+    } else {
+        k_net_rec<<<N.grid_fwd, kBlock, 0, s>>>(a);
+        k_net_l2_tc<false><<<N.grid_tc, kTcThreads, kTcSmem, s>>>(a);
+    }
     OASIS_CUDA(cudaGetLastError());
 }
 

@@ -1158,7 +1158,7 @@ __global__ void __launch_bounds__(WPB * 32, MINB) k_pcg_iter_tma(StepData<P> a, 
             }
             __syncwarp();
         }
-        block_partial_lite<3, V>(part, reinterpret_cast<V*>(a.partial), vb);
+        block_partial_lite<3, V>(part, a.partial, vb);
     }
     if (timed_out) {
         // record the failure; let the copies this warp started finish (bounded)
@@ -1170,7 +1170,7 @@ __global__ void __launch_bounds__(WPB * 32, MINB) k_pcg_iter_tma(StepData<P> a, 
         __syncwarp();
     }
     double tot[3];
-    if (grid_finish_lite<3, V>(tot, reinterpret_cast<const V*>(a.partial), n_vb, &a.stp->ticket) &&
+    if (grid_finish_lite<3, V>(tot, a.partial, n_vb, &a.stp->ticket) &&
         threadIdx.x == 0)
         pcg_iter_finish<P>(a, ctl, tot);
 }
@@ -2037,15 +2037,21 @@ struct StepImplT final : StepImpl {
             },
             [&](cudaStream_t ss_, const Loop& lp) {
                 const Ctl c = ctl_u(lp);
+                int pv = Sv.prof_begin(ss_, OASIS_PROF_BICG_VEC);
                 k_bicg_dir<P, DD, NR><<<ge_n, kBlock, 0, ss_>>>(q, k0);
+                Sv.prof_end(ss_, pv);
                 int pb = Sv.prof_begin(ss_, OASIS_PROF_BICG_SPMM);
                 k_bicg_spmm<P, DD, NR, 0, kTileN><<<G.gs0, kBlock, G.ss, ss_>>>(q, k0, c);
                 Sv.prof_end(ss_, pb);
+                pv = Sv.prof_begin(ss_, OASIS_PROF_BICG_VEC);
                 k_bicg_s<P, DD, NR><<<ge_n, kBlock, 0, ss_>>>(q, k0);
+                Sv.prof_end(ss_, pv);
                 pb = Sv.prof_begin(ss_, OASIS_PROF_BICG_SPMM);
                 k_bicg_spmm<P, DD, NR, 1, kTileN><<<G.gs1, kBlock, G.ss, ss_>>>(q, k0, c);
                 Sv.prof_end(ss_, pb);
+                pv = Sv.prof_begin(ss_, OASIS_PROF_BICG_VEC);
                 k_bicg_xr<P, DD, NR><<<ge_red, kBlock, 0, ss_>>>(q, k0, c);
+                Sv.prof_end(ss_, pv);
                 OASIS_CUDA(cudaGetLastError());
             },
             [&](cudaStream_t ss_, const Loop&) {
@@ -2143,9 +2149,13 @@ struct StepImplT final : StepImpl {
         OASIS_CUDA(cudaGetLastError());
         if (Sv.prm.pressure_pc == OASIS_PC_AMG) {
             const AmgHierarchy& H = *Sv.m->amg;
+            ProfHook hook;
+            hook.ctx = &Sv;
+            hook.begin = [](void* c, cudaStream_t st_, int f) { return static_cast<Solver*>(c)->prof_begin(st_, f); };
+            hook.end = [](void* c, cudaStream_t st_, int h) { static_cast<Solver*>(c)->prof_end(st_, h); };
             auto vcycle = [&](cudaStream_t ss) {
                 const int pa = Sv.prof_begin(ss, OASIS_PROF_AMG);
-                amg_vcycle<V>(H, Sv.amgw, a.ar, a.au, a.stp, ss);
+                amg_vcycle<V>(H, Sv.amgw, a.ar, a.au, a.stp, ss, &hook);
                 Sv.prof_end(ss, pa);
             };
             Sv.run_loops(

@@ -58,3 +58,29 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(12.5, 1, "cpu") == 12.5
     assert bench.whole_job_value(4, 1, 500.0) == pytest.approx(8.0)
+
+
+def test_family_bytes_model_on_a_small_mesh():
+    """The algorithmic-byte model of the bench's roofline, on a mesh whose sizes are
+    known: each family's per-launch bytes follow its stated formula."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from workloads import problems as WP
+    pb = WP.stress_cube(4)
+    N, T = pb.mesh.n_dofs, pb.mesh.n_cells
+    Z = 1000
+    tuning = {"candidates": [{"col16": 1, "us": 1.0}]}
+    amg = {"levels": 3, "rows": [N, 20, 3], "nnz": [Z, 200, 9], "p_nnz": [300, 40]}
+    f = bench.family_bytes(pb, Z, None, tuning, amg)
+    ns = (N + 31) // 32
+    assert f["pcg_spmv"][1] == 6 * Z + 12 * N + 8 * ns
+    assert f["amg_fine"][1] == 6 * Z + 16 * N + 8 * ns
+    assert f["bicg_spmm"][1] == 8 * Z + 4 * (N + 1) + 36 * N
+    want_t = (16 * 300 + 16 * N + 12 * 20) + (16 * 40 + 16 * 20 + 12 * 3)
+    assert abs(f["amg_transfer"][1] - want_t / 4) < 1e-9
+    want_c = 2 * (8 * 200 + 20 * 20) + 4 * 3 * 4 + 8 * 3
+    assert abs(f["amg_coarse"][1] - want_c / 3) < 1e-9
+    assert f["assemble"][1] == 128 * T + 28 * Z + 216 * N
+    # without 16-bit columns the column bytes are 4 per entry
+    f32 = bench.family_bytes(pb, Z, None, {"candidates": [{"col16": 0, "us": 1.0}]}, amg)
+    assert f32["pcg_spmv"][1] - f["pcg_spmv"][1] == 2 * Z
