@@ -1,6 +1,8 @@
 // Smoothed-aggregation AMG for the pressure operator: host setup (once per
 // mesh, from the assembled float64 K) and the V(1,1) cycle kernels.
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <chrono>
 #include <cmath>
 #include <thread>
@@ -460,70 +462,126 @@ __device__ __forceinline__ V group_sum(V v) {
     return v;
 }
 
-// Rows are served by groups of G lanes; the row loop is uniform across the warp
-// (all shuffles have the full warp), each group handling row base + group.
-#define AMG_ROWS(n)                                                                                 \
-    const int lg = threadIdx.x & (G - 1);                                                           \
-    const int64_t rows_per_warp = 32 / G;                                                           \
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;                        \
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;                                       \
-    for (int64_t base = w0 * rows_per_warp; base < (n); base += nw * rows_per_warp)
+// CSR row kernels of the coarser levels and the transfers.  Rows are served by
+// groups of G lanes (G divides 32); every group keeps U rows in flight: the row
+// pointers of its U rows are loaded together, then per round one entry of each
+// unfinished row (value, column, then the gathered operand), so that a warp has
+// U independent load chains where one row at a time would wait on each chain in
+// turn.  Lane lg of a group adds the entries lg, lg + G, ... of its row in that
+// order and the group sums the lanes with a fixed shuffle tree, whatever U is.
+// The batch loop is uniform across the warp (all shuffles have the full warp).
+enum AmgRowMode { kRowPre = 0, kRowPost = 1, kRowProlong = 2, kRowRestrict = 3 };
 
-// pre-smoothing from zero and the residual: x = w D^-1 r, res = r - A x
-template <class V, int G>
-__global__ void __launch_bounds__(kBlock) k_amg_pre(int64_t n, const int32_t* __restrict__ rp,
-                                                    const int32_t* __restrict__ ci, const V* __restrict__ a,
-                                                    const V* __restrict__ d, V w, const V* __restrict__ r,
-                                                    V* __restrict__ x, V* __restrict__ res, const KrylovState* st) {
-    if (amg_done(st)) return;
-    AMG_ROWS(n) {
-        const int64_t i = base + ((threadIdx.x & 31) / G);
-        V s = 0;
-        if (i < n)
-            for (int32_t q = rp[i] + lg; q < rp[i + 1]; q += G) {
-                const int32_t j = ci[q];
-                s += a[q] * (w * d[j] * r[j]);
+template <class V>
+struct AmgRowArgs {
+    int64_t n;
+    const int32_t* __restrict__ rp;
+    const int32_t* __restrict__ ci;
+    const V* __restrict__ a;
+    const V* __restrict__ d;     // 1 / a_ii (smoothing)
+    V w;                         // Jacobi weight (smoothing)
+    const V* __restrict__ r;     // right-hand side of the level (smoothing)
+    const V* __restrict__ x;     // post: the iterate
+    const V* __restrict__ v;     // transfers: the vector multiplied
+    V* __restrict__ out;         // pre: x; post: the smoothed iterate; transfers: y
+    V* __restrict__ res;         // pre: the residual
+    const KrylovState* st;
+};
+
+// MODE kRowPre:      x = w D^-1 r, res = r - A x (smoothing from zero; the gathered
+//                    operand is w d_j r_j);
+//      kRowPost:     out = x + w D^-1 (r - A x);
+//      kRowProlong:  out += P v;
+//      kRowRestrict: out = R v.
+template <class V, int G, int U, int MODE>
+__device__ __forceinline__ void amg_rows(const AmgRowArgs<V>& p) {
+    if (amg_done(p.st)) return;
+    constexpr int RPW = 32 / G;
+    const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = w0 * RPW * U; base < p.n; base += nw * RPW * U) {
+        int64_t i[U];
+        int32_t q[U], e[U];
+        V sum[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            i[u] = base + u * RPW + grp;
+            const bool ok = i[u] < p.n;
+            q[u] = ok ? p.rp[i[u]] + lg : 0;
+            e[u] = ok ? p.rp[i[u] + 1] : 0;
+            sum[u] = 0;
+        }
+        bool more = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) more |= q[u] < e[u];
+        while (more) {
+            int32_t j[U];
+            V av[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool has = q[u] < e[u];
+                j[u] = has ? p.ci[q[u]] : 0;
+                av[u] = has ? p.a[q[u]] : V(0);
             }
-        s = group_sum<G>(s);
-        if (i < n && lg == 0) {
-            res[i] = r[i] - s;
-            x[i] = w * d[i] * r[i];
+            V g[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if constexpr (MODE == kRowPre) g[u] = p.w * p.d[j[u]] * p.r[j[u]];
+                else if constexpr (MODE == kRowPost) g[u] = p.x[j[u]];
+                else g[u] = p.v[j[u]];
+            }
+            more = false;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (q[u] < e[u]) {
+                    sum[u] += av[u] * g[u];
+                    q[u] += G;
+                }
+                more |= q[u] < e[u];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const V t = group_sum<G>(sum[u]);
+            if (i[u] < p.n && lg == 0) {
+                const int64_t ii = i[u];
+                if constexpr (MODE == kRowPre) {
+                    p.res[ii] = p.r[ii] - t;
+                    p.out[ii] = p.w * p.d[ii] * p.r[ii];
+                } else if constexpr (MODE == kRowPost) {
+                    p.out[ii] = p.x[ii] + p.w * p.d[ii] * (p.r[ii] - t);
+                } else if constexpr (MODE == kRowProlong) {
+                    p.out[ii] = p.out[ii] + t;
+                } else {
+                    p.out[ii] = t;
+                }
+            }
         }
     }
 }
 
-// y = M v (ADD: y += M v) for a CSR matrix M (restriction P^T or prolongation P).
-template <class V, int G, bool ADD>
-__device__ __forceinline__ void amg_row_product(int64_t n, const int32_t* __restrict__ rp,
-                                                const int32_t* __restrict__ ci, const V* __restrict__ a,
-                                                const V* __restrict__ v, V* __restrict__ y, const KrylovState* st) {
-    if (amg_done(st)) return;
-    AMG_ROWS(n) {
-        const int64_t i = base + ((threadIdx.x & 31) / G);
-        V s = 0;
-        if (i < n)
-            for (int32_t q = rp[i] + lg; q < rp[i + 1]; q += G) s += a[q] * v[ci[q]];
-        s = group_sum<G>(s);
-        if (i < n && lg == 0) y[i] = ADD ? y[i] + s : s;
-    }
+// rows in flight per lane group: more for short rows (few entries per lane)
+template <int G>
+constexpr int amg_rows_u() {
+    return G <= 8 ? 4 : 2;
 }
 
-// post-smoothing: out = x + w D^-1 (r - A x)
 template <class V, int G>
-__global__ void __launch_bounds__(kBlock) k_amg_post(int64_t n, const int32_t* __restrict__ rp,
-                                                     const int32_t* __restrict__ ci, const V* __restrict__ a,
-                                                     const V* __restrict__ d, V w, const V* __restrict__ r,
-                                                     const V* __restrict__ x, V* __restrict__ out,
-                                                     const KrylovState* st) {
-    if (amg_done(st)) return;
-    AMG_ROWS(n) {
-        const int64_t i = base + ((threadIdx.x & 31) / G);
-        V s = 0;
-        if (i < n)
-            for (int32_t q = rp[i] + lg; q < rp[i + 1]; q += G) s += a[q] * x[ci[q]];
-        s = group_sum<G>(s);
-        if (i < n && lg == 0) out[i] = x[i] + w * d[i] * (r[i] - s);
-    }
+__global__ void __launch_bounds__(kBlock) k_amg_pre(AmgRowArgs<V> p) {
+    amg_rows<V, G, amg_rows_u<G>(), kRowPre>(p);
+}
+template <class V, int G>
+__global__ void __launch_bounds__(kBlock) k_amg_post(AmgRowArgs<V> p) {
+    amg_rows<V, G, amg_rows_u<G>(), kRowPost>(p);
+}
+template <class V, int G>
+__global__ void __launch_bounds__(kBlock) k_amg_restrict(AmgRowArgs<V> p) {
+    amg_rows<V, G, amg_rows_u<G>(), kRowRestrict>(p);
+}
+template <class V, int G>
+__global__ void __launch_bounds__(kBlock) k_amg_prolong(AmgRowArgs<V> p) {
+    amg_rows<V, G, amg_rows_u<G>(), kRowProlong>(p);
 }
 
 // Finest level on SELL-32: one warp per slice of 32 rows, lane l owns row
@@ -621,17 +679,34 @@ __global__ void __launch_bounds__(kDenseBlock) k_amg_dense(int64_t n, int64_t ld
         __syncthreads();
     }
 }
-#undef AMG_ROWS
 
 int fine_grid(const AmgSellView& F) {
     const int64_t want = (F.n_slices + kBlock / 32 - 1) / (kBlock / 32);
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 8));
 }
 
-int amg_grid(int64_t rows, int G) {
-    const int64_t per_block = (int64_t)kBlock / G;
+// Blocks of `fn` (kBlock threads, no dynamic shared memory) resident on one SM
+// of the current device, from the occupancy calculator, cached per device and
+// kernel: grids of grid-stride kernels stay within one wave.
+int resident_blocks(const void* fn) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> cache;
+    int dev = 0;
+    OASIS_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find({dev, fn});
+    if (it != cache.end()) return it->second;
+    int per_sm = 0;
+    OASIS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0));
+    per_sm = std::max(1, per_sm);
+    cache[{dev, fn}] = per_sm;
+    return per_sm;
+}
+
+int amg_grid(int64_t rows, int G, int U, const void* fn) {
+    const int64_t per_block = (int64_t)kBlock / G * U;
     const int64_t want = (rows + per_block - 1) / per_block;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 8));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * resident_blocks(fn)));
 }
 
 template <class V>
@@ -643,28 +718,15 @@ const V* pick(const float* f, const double* d) {
 }  // namespace
 
 // Launch a row kernel with G lanes per row, G chosen at run time.
-#define AMG_DISPATCH(G, KERNEL, ROWS, ...)                                                      \
-    switch (G) {                                                                                \
-        case 4: KERNEL<V, 4><<<amg_grid(ROWS, 4), kBlock, 0, s>>>(__VA_ARGS__); break;           \
-        case 8: KERNEL<V, 8><<<amg_grid(ROWS, 8), kBlock, 0, s>>>(__VA_ARGS__); break;           \
-        case 16: KERNEL<V, 16><<<amg_grid(ROWS, 16), kBlock, 0, s>>>(__VA_ARGS__); break;        \
-        default: KERNEL<V, 32><<<amg_grid(ROWS, 32), kBlock, 0, s>>>(__VA_ARGS__); break;        \
+#define AMG_LAUNCH(GG, KERNEL, ROWS, ARGS)                                                                  \
+    KERNEL<V, GG><<<amg_grid(ROWS, GG, amg_rows_u<GG>(), (const void*)KERNEL<V, GG>), kBlock, 0, s>>>(ARGS)
+#define AMG_DISPATCH(G, KERNEL, ROWS, ARGS)                                                                   \
+    switch (G) {                                                                                              \
+        case 4: AMG_LAUNCH(4, KERNEL, ROWS, ARGS); break;                                                     \
+        case 8: AMG_LAUNCH(8, KERNEL, ROWS, ARGS); break;                                                     \
+        case 16: AMG_LAUNCH(16, KERNEL, ROWS, ARGS); break;                                                   \
+        default: AMG_LAUNCH(32, KERNEL, ROWS, ARGS); break;                                                   \
     }
-
-template <class V, int G>
-__global__ void __launch_bounds__(kBlock) k_amg_restrict(int64_t n, const int32_t* __restrict__ rp,
-                                                         const int32_t* __restrict__ ci, const V* __restrict__ a,
-                                                         const V* __restrict__ v, V* __restrict__ y,
-                                                         const KrylovState* st) {
-    amg_row_product<V, G, false>(n, rp, ci, a, v, y, st);
-}
-template <class V, int G>
-__global__ void __launch_bounds__(kBlock) k_amg_prolong(int64_t n, const int32_t* __restrict__ rp,
-                                                        const int32_t* __restrict__ ci, const V* __restrict__ a,
-                                                        const V* __restrict__ v, V* __restrict__ y,
-                                                        const KrylovState* st) {
-    amg_row_product<V, G, true>(n, rp, ci, a, v, y, st);
-}
 
 template <class V>
 void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const KrylovState* st, cudaStream_t s,
@@ -699,15 +761,16 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
             pend();
         } else {
             pbeg(l == 0 ? OASIS_PROF_AMG_FINE : OASIS_PROF_AMG_COARSE);
-            AMG_DISPATCH(lv.g_a, k_amg_pre, lv.n, lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]),
-                         vec(wk.res[l]), st);
+            AmgRowArgs<V> ra{lv.n, lv.rp, lv.ci, a, d, w, rin(l), nullptr, nullptr, vec(wk.x[l]), vec(wk.res[l]), st};
+            AMG_DISPATCH(lv.g_a, k_amg_pre, lv.n, ra);
             pend();
         }
         const int64_t nc = l + 1 < L ? h.lv[l + 1]->n : h.nc;
         const V* rv = pick<V>(lv.r32.p, lv.r64.p);
         pbeg(OASIS_PROF_AMG_TRANSFER);
-        AMG_DISPATCH(lv.g_r, k_amg_restrict, nc, nc, lv.r_rp.p, lv.r_ci.p, rv, vec(wk.res[l]), vec(wk.rin[l + 1]),
-                     st);
+        AmgRowArgs<V> rr{nc, lv.r_rp.p, lv.r_ci.p, rv, nullptr, V(0), nullptr, nullptr, vec(wk.res[l]),
+                         vec(wk.rin[l + 1]), nullptr, st};
+        AMG_DISPATCH(lv.g_r, k_amg_restrict, nc, rr);
         pend();
     }
     pbeg(OASIS_PROF_AMG_COARSE);
@@ -722,7 +785,9 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
         const V w = (V)lv.omega;
         const V* pv = pick<V>(lv.p32.p, lv.p64.p);
         pbeg(OASIS_PROF_AMG_TRANSFER);
-        AMG_DISPATCH(lv.g_p, k_amg_prolong, lv.n, lv.n, lv.p_rp.p, lv.p_ci.p, pv, xo(l + 1), vec(wk.x[l]), st);
+        AmgRowArgs<V> pr{lv.n, lv.p_rp.p, lv.p_ci.p, pv, nullptr, V(0), nullptr, nullptr, xo(l + 1), vec(wk.x[l]),
+                         nullptr, st};
+        AMG_DISPATCH(lv.g_p, k_amg_prolong, lv.n, pr);
         pend();
         if (l == 0 && h.fine.ptr) {
             const V* fv = pick<V>(h.fine.v32, h.fine.v64);
@@ -737,13 +802,15 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
             pend();
         } else {
             pbeg(l == 0 ? OASIS_PROF_AMG_FINE : OASIS_PROF_AMG_COARSE);
-            AMG_DISPATCH(lv.g_a, k_amg_post, lv.n, lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]), xo(l), st);
+            AmgRowArgs<V> po{lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]), nullptr, xo(l), nullptr, st};
+            AMG_DISPATCH(lv.g_a, k_amg_post, lv.n, po);
             pend();
         }
     }
     OASIS_CUDA(cudaGetLastError());
 }
 #undef AMG_DISPATCH
+#undef AMG_LAUNCH
 
 template void amg_vcycle<float>(const AmgHierarchy&, AmgWork&, const float*, float*, const KrylovState*, cudaStream_t,
                                 const ProfHook*);

@@ -670,6 +670,18 @@ __device__ __forceinline__ float2 mean_s<float2>(const KrylovState* st, bool of_
     return of_p ? make_float2(st->meanp_hi, st->meanp_lo) : make_float2(st->mean_hi, st->mean_lo);
 }
 
+// Grid-stride walk over the SELL-32 slices, one warp per slice at a time: the
+// reduction kernels run on a grid of one resident wave, so that their last
+// block sums few partials.  body(i, len, base, lane) is called per slice with
+// the lane's row i, the slice length and the lane's first SELL position.
+template <class P, class F>
+__device__ __forceinline__ void sell_slices(const StepData<P>& a, F&& body) {
+    const int lane = (int)(threadIdx.x & 31);
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < a.n_slices; sl += nw)
+        body(sl * 32 + lane, a.sell_len[sl], (int64_t)a.sell_ptr[sl] + lane, lane);
+}
+
 template <class P>
 __device__ __forceinline__ bool sell_lane(const StepData<P>& a, int64_t& i, int& len, int64_t& base, int& lane) {
     lane = threadIdx.x & 31;
@@ -726,9 +738,7 @@ __global__ void __launch_bounds__(kBlock) k_guess_judge(StepData<P> a) {
     const S mean = mean_s<S>(a.stp, false);
     const V sp = (V)a.stp->gscale_f[1];
     V part[2] = {};
-    int64_t i, base;
-    int len, lane;
-    if (sell_lane(a, i, len, base, lane)) {
+    sell_slices(a, [&](int64_t i, int len, int64_t base, int) {
         V kl = 0, kp = 0;
         for (int k = 0; k < len; ++k) {
             const int64_t q = base + 32 * (int64_t)k;
@@ -742,7 +752,7 @@ __global__ void __launch_bounds__(kBlock) k_guess_judge(StepData<P> a) {
             part[0] += (bv - kl) * (bv - kl);
             part[1] += (bv - kp) * (bv - kp);
         }
-    }
+    });
     double tot[2];
     if (grid_sum_lite<2, V>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
         a.stp->guess_rr[0] = tot[0];
@@ -791,9 +801,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_outer_sell(StepData<P> a, Ctl ct
     Acc part[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) acc_zero(part[k]);
-    int64_t i, base;
-    int len, lane;
-    if (sell_lane(a, i, len, base, lane)) {
+    sell_slices(a, [&](int64_t i, int len, int64_t base, int) {
         Acc kx;
         acc_zero(kx);
         for (int k = 0; k < len; ++k) {
@@ -821,7 +829,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_outer_sell(StepData<P> a, Ctl ct
             acc_addv(part[2], s_v(a.pstar[i]));
             acc_addv(part[2], xv);
         }
-    }
+    });
     double tot[3];
     if (grid_sum<3, Acc>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
         KrylovState* st = a.stp;
@@ -1277,9 +1285,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_amg_cg_spmv(StepData<P> a, Ctl
     using V = typename P::V;
     if (a.stp->col_done[0] || a.stp->in_done[0]) return;
     V part[3] = {};
-    int64_t i, base;
-    int len, lane;
-    if (sell_lane(a, i, len, base, lane)) {
+    sell_slices(a, [&](int64_t i, int len, int64_t base, int) {
         const int32_t row = (int32_t)i;
         V w = 0;
         for (int k = 0; k < len; k += C) {
@@ -1306,7 +1312,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_amg_cg_spmv(StepData<P> a, Ctl
             part[1] += w * u;
             part[2] += r * r;
         }
-    }
+    });
     double tot[3];
     if (grid_sum_lite<3, V>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
         if constexpr (START) {
@@ -1861,6 +1867,7 @@ struct StepImplT final : StepImpl {
         g_rhs = 1, g_upd = 1, g_upd_c = 1, g_mspmv = 1, g_out_s = 1, g_spmm0_s = 1, g_spmm1_s = 1, g_sasm = 1;
     int ge_n = 1, ge_nd = 1, ge_c = 1, ge_red = 1;
     int g_sell = 1;
+    int g_sellr = 1;     // grid-stride SELL kernels ending in a reduction: one resident wave
     int iter_v = 0;                                   // chosen CG iteration shape
     int amg_v = 0;                                    // chosen multigrid CG product shape
     double amg_us[kAmgVariants] = {0};
@@ -1972,6 +1979,7 @@ struct StepImplT final : StepImpl {
         g_spmm0_1 = tile_grid(k_bicg_spmm<P, D, 1, 0, kTileN>, sm_spmm1, tiles_n);
         g_spmm1_1 = tile_grid(k_bicg_spmm<P, D, 1, 1, kTileN>, sm_spmm1, tiles_n);
         g_sell = (int)std::max<int64_t>(1, ((m.n + 31) / 32 + kBlock / 32 - 1) / (kBlock / 32));
+        g_sellr = (int)std::min<int64_t>(g_sell, (int64_t)num_sms() * 8);
         g_rhs = tile_grid(k_pressure_rhs<P, D>, sm_outp, tiles);
         g_upd = tile_grid(k_update<P, D, false>, sm_vd, tiles);
         g_upd_c = tile_grid(k_update<P, D, true>, 0, tiles);
@@ -2140,7 +2148,7 @@ struct StepImplT final : StepImpl {
         }
         if (learned) {
             net_forward(*Sv.net, a.feat, a.gy, s);
-            k_guess_judge<P><<<g_sell, kBlock, 0, s>>>(a);
+            k_guess_judge<P><<<g_sellr, kBlock, 0, s>>>(a);
             OASIS_CUDA(cudaGetLastError());
             mode = OASIS_GUESS_LEARNED;
         }
@@ -2162,11 +2170,11 @@ struct StepImplT final : StepImpl {
                 s, graph, 1,
                 [&](cudaStream_t ss, const Loop& lp) {
                     const Ctl c = ctl_p(lp);
-                    k_pcg_outer_sell<P><<<g_sell, kBlock, 0, ss>>>(a, c);
+                    k_pcg_outer_sell<P><<<g_sellr, kBlock, 0, ss>>>(a, c);
                     k_amg_cg_start<P><<<ge_n, kBlock, 0, ss>>>(a);
                     vcycle(ss);
-                    if (a.sell_dcol) k_amg_cg_spmv<P, true, true><<<g_sell, kBlock, 0, ss>>>(a, c);
-                    else k_amg_cg_spmv<P, true, false><<<g_sell, kBlock, 0, ss>>>(a, c);
+                    if (a.sell_dcol) k_amg_cg_spmv<P, true, true><<<g_sellr, kBlock, 0, ss>>>(a, c);
+                    else k_amg_cg_spmv<P, true, false><<<g_sellr, kBlock, 0, ss>>>(a, c);
                     OASIS_CUDA(cudaGetLastError());
                 },
                 [&](cudaStream_t ss, const Loop& lp) {
@@ -2175,7 +2183,7 @@ struct StepImplT final : StepImpl {
                     vcycle(ss);
                     const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
                     const AmgVariant<P>& av = amg_variant_table<P>()[amg_v];
-                    (a.sell_dcol ? av.fn16 : av.fn32)<<<g_sell, kBlock, 0, ss>>>(a, c);
+                    (a.sell_dcol ? av.fn16 : av.fn32)<<<g_sellr, kBlock, 0, ss>>>(a, c);
                     Sv.prof_end(ss, pq);
                     OASIS_CUDA(cudaGetLastError());
                 },
@@ -2190,7 +2198,7 @@ struct StepImplT final : StepImpl {
             s, graph, 1,
             [&](cudaStream_t ss, const Loop& lp) {
                 const Ctl c = ctl_p(lp);
-                k_pcg_outer_sell<P><<<g_sell, kBlock, 0, ss>>>(a, c);
+                k_pcg_outer_sell<P><<<g_sellr, kBlock, 0, ss>>>(a, c);
                 const int pu = Sv.prof_begin(ss, OASIS_PROF_PCG_UPDATE);
                 k_pcg_init_sell<P><<<g_sell, kBlock, 0, ss>>>(a, c);
                 Sv.prof_end(ss, pu);
@@ -2345,7 +2353,7 @@ struct StepImplT final : StepImpl {
             for (int r = 0; r < kWarm + kTimed; ++r) {
                 OASIS_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(KrylovState), s));
                 OASIS_CUDA(cudaEventRecord(e0, s));
-                (a.sell_dcol ? t[v].fn16 : t[v].fn32)<<<g_sell, kBlock, 0, s>>>(d, c);
+                (a.sell_dcol ? t[v].fn16 : t[v].fn32)<<<g_sellr, kBlock, 0, s>>>(d, c);
                 OASIS_CUDA(cudaGetLastError());
                 OASIS_CUDA(cudaEventRecord(e1, s));
                 OASIS_CUDA(cudaEventSynchronize(e1));
