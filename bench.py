@@ -100,6 +100,11 @@ def family_bytes(pb, nnz, args, tuning, amg):
                    the solution/residual update with its dots (96 N), for D = 3
       assemble     convection cell terms (80 T + 48 N) and the fused row pass (incidence
                    and cell terms 48 T, per entry 28 Z, per row 168 N), one pair per step
+      outer        float64-quality residuals of the sweeps, averaged over the tentative
+                   solve's (A + columns 8 Z; r0, Delta gathered, r, rh, p, v, dl: 112 N)
+                   and the pressure's (K as float-float + columns 12 Z; 56 N)
+      pcg_update   multigrid CG vector update: u, w, p, s, increment, r read, p, s,
+                   increment, r written (40 N)
     Returns {family: (kernel, bytes per launch, formula)}."""
     N, Z, T, D = pb.mesh.n_dofs, nnz, pb.mesh.n_cells, pb.mesh.dim
     n_slices = (N + 31) // 32
@@ -129,6 +134,10 @@ def family_bytes(pb, nnz, args, tuning, amg):
                        (64 + 52 + 96) * N * D / 3 / 3, "(64 + 52 + 96) N / 3 per launch (D = 3)")
     out["assemble"] = ("k_cell_beta + k_assemble (convection assembly + Algorithm 2, one pair per step)",
                        80 * T + 48 * N + 48 * T + 28 * Z + 168 * N, "128 T + 28 Z + 216 N per pair")
+    out["outer"] = ("k_bicg_outer(_rows) / k_pcg_outer_sell (float-float residuals of the sweeps)",
+                    10 * Z + 84 * N, "(8 Z + 112 N + 12 Z + 56 N) / 2 per launch")
+    if amg:
+        out["pcg_update"] = ("k_amg_cg_update (multigrid CG vector update + ||r||^2)", 40 * N, "40 N")
     return out
 
 

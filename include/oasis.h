@@ -120,6 +120,12 @@ typedef struct oasis_params {
                               a step describe its last repetition.  At most 16. */
     int32_t convection;    /* OASIS_CONV_ABCN (Eq. 22, default) or OASIS_CONV_ABE (Eq. 21) */
     int32_t velocity_update; /* OASIS_UPDATE_LUMPED (default) or OASIS_UPDATE_CONSISTENT */
+    int32_t bicg_variant;  /* shape of the d-RHS product of the batched tentative BiCGStab:
+                              0 = autotune at solver creation (every candidate timed on this
+                              mesh's pattern, the fastest kept); k >= 1 = candidate k of
+                              oasis_get_tuning's bicg_* fields.  The shapes add a row's
+                              products in different orders: they agree to rounding, and a
+                              solver keeps its shape for its life. */
 } oasis_params;
 
 /* Velocity update of the projection (Sec. 5).  LUMPED: u_k^n = u_k^I - dt
@@ -174,6 +180,16 @@ typedef struct oasis_tuning {
                                               memory by bulk copies (persistent grid) */
     int32_t warps_per_block[OASIS_MAX_VARIANTS];
     double us[OASIS_MAX_VARIANTS];         /* median time per launch; 0 if not timed */
+    /* The d-RHS product of the batched tentative BiCGStab (both products of one
+     * iteration timed together): lanes = 0 is the row-tile form (rows per tile in
+     * bicg_rows, the entries of a tile read coalesced and summed per row through
+     * shared memory); lanes = G > 0 is the row-split form, G lanes per row and
+     * bicg_rows rows in flight per lane group. */
+    int32_t bicg_n_variants;
+    int32_t bicg_chosen;                   /* 1-based */
+    int32_t bicg_lanes[8];
+    int32_t bicg_rows[8];
+    double bicg_us[8];                     /* median time of the two products; 0 if not timed */
 } oasis_tuning;
 
 /* Per-step solver statistics. */
@@ -430,7 +446,9 @@ int oasis_get_tuning(const oasis_solver* s, oasis_tuning* out);
                                       with the vector updates and the three dot products */
 #define OASIS_PROF_BICG_SPMM 1     /* the d-RHS products of the tentative BiCGStab */
 #define OASIS_PROF_ASSEMBLE 2      /* fused convection assembly + Algorithm 2 row pass */
-#define OASIS_PROF_PCG_UPDATE 3    /* CG start of each refinement sweep (w0 = K M^-1 r0, dots) */
+#define OASIS_PROF_PCG_UPDATE 3    /* Jacobi CG: start of each refinement sweep (w0 = K M^-1 r0,
+                                      dots); multigrid CG: the vector update of every iteration
+                                      (p, s, the increment, r and ||r||^2) */
 #define OASIS_PROF_UPDATE 4        /* velocity update (lumped, or the final pass of the
                                       consistent one) + rotation */
 #define OASIS_PROF_PRESSURE_RHS 5  /* pressure right-hand side */
@@ -444,6 +462,9 @@ int oasis_get_tuning(const oasis_solver* s, oasis_tuning* out);
                                       coarsest solve */
 #define OASIS_PROF_BICG_VEC 12     /* vector kernels of the tentative BiCGStab iteration (search
                                       direction, s update, solution/residual update + dots) */
+#define OASIS_PROF_OUTER 13        /* float64-quality residuals of the refinement sweeps (the
+                                      tentative solve's r = r0 - A Delta and the pressure's
+                                      r = b - K x) */
 
 /* enable = 1: from now on, eager steps record CUDA events around the launches
  * of the kernel families above; the counters are reset by every call. */

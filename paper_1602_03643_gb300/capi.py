@@ -48,7 +48,7 @@ class oasis_params(C.Structure):
                 ("inner_rtol", C.c_double), ("batch_rhs", C.c_int32), ("use_graph", C.c_int32),
                 ("guess", C.c_int32), ("spmv_variant", C.c_int32), ("pressure_pc", C.c_int32),
                 ("inner_iters", C.c_int32), ("convection", C.c_int32),
-                ("velocity_update", C.c_int32)]
+                ("velocity_update", C.c_int32), ("bicg_variant", C.c_int32)]
 
 
 class oasis_amg_info(C.Structure):
@@ -59,7 +59,9 @@ class oasis_amg_info(C.Structure):
 class oasis_tuning(C.Structure):
     _fields_ = [("n_variants", C.c_int32), ("chosen", C.c_int32), ("chunk", C.c_int32 * 16),
                 ("min_blocks", C.c_int32 * 16), ("prefetch", C.c_int32 * 16), ("col16", C.c_int32 * 16),
-                ("streamed", C.c_int32 * 16), ("warps_per_block", C.c_int32 * 16), ("us", C.c_double * 16)]
+                ("streamed", C.c_int32 * 16), ("warps_per_block", C.c_int32 * 16), ("us", C.c_double * 16),
+                ("bicg_n_variants", C.c_int32), ("bicg_chosen", C.c_int32), ("bicg_lanes", C.c_int32 * 8),
+                ("bicg_rows", C.c_int32 * 8), ("bicg_us", C.c_double * 8)]
 
     def as_dict(self):
         n = self.n_variants
@@ -68,7 +70,10 @@ class oasis_tuning(C.Structure):
                                 "prefetch": self.prefetch[k], "col16": self.col16[k],
                                 "streamed": self.streamed[k], "warps_per_block": self.warps_per_block[k],
                                 "us": self.us[k]}
-                               for k in range(n)]}
+                               for k in range(n)],
+                "bicg_chosen": self.bicg_chosen,
+                "bicg_candidates": [{"lanes": self.bicg_lanes[k], "rows": self.bicg_rows[k],
+                                     "us": self.bicg_us[k]} for k in range(self.bicg_n_variants)]}
 
 
 class oasis_step_stats(C.Structure):
@@ -246,7 +251,7 @@ def oasis_spmv_dot_f64_noalloc(mesh, which, x, y, xy, stream=None):
 def make_params(nu, dt, f=(0.0, 0.0, 0.0), rtol_u=1e-8, rtol_p=1e-8, max_it_u=1000, max_it_p=20000,
                 precision=OASIS_FP64, inner_rtol=1e-4, batch_rhs=1, use_graph=0, guess=OASIS_GUESS_ZERO,
                 spmv_variant=0, pressure_pc=0, inner_iters=1,
-                convection=0, velocity_update=0):
+                convection=0, velocity_update=0, bicg_variant=0):
     p = oasis_params()
     p.nu, p.dt = nu, dt
     ff = list(f) + [0.0] * (3 - len(f))
@@ -260,6 +265,7 @@ def make_params(nu, dt, f=(0.0, 0.0, 0.0), rtol_u=1e-8, rtol_p=1e-8, max_it_u=10
     p.inner_iters = inner_iters
     p.convection = convection
     p.velocity_update = velocity_update
+    p.bicg_variant = bicg_variant
     return p
 
 
@@ -347,7 +353,7 @@ def oasis_get_tentative_system(solver, dim, n, nnz, stream=None):
 
 PROF_FAMILIES = {"pcg_spmv": 0, "bicg_spmm": 1, "assemble": 2, "pcg_update": 3, "update": 4,
                  "pressure_rhs": 5, "guess": 6, "amg": 7, "mass": 8, "amg_fine": 9, "amg_transfer": 10,
-                 "amg_coarse": 11, "bicg_vec": 12}
+                 "amg_coarse": 11, "bicg_vec": 12, "outer": 13}
 
 
 def oasis_profile(solver, enable=True):

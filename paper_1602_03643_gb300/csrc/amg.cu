@@ -602,6 +602,9 @@ __device__ __forceinline__ int32_t fine_col(const AmgSellView& F, int64_t q, int
 
 // PRE: x = w D^-1 r and res = r - A x (smoothing from zero); else
 // out = x + w D^-1 (r - A x).  The gathered operand is w d_j r_j (PRE) or x_j.
+// (Two slices per warp in flight were measured slower at 128^3: 61 against
+// 47 us per sweep, the extra registers costing more resident warps than the
+// second chain gains.)
 template <class V, bool D16, bool PRE>
 __global__ void __launch_bounds__(kBlock) k_amg_fine(AmgSellView F, const V* __restrict__ av,
                                                      const V* __restrict__ d, V w, const V* __restrict__ r,
@@ -680,11 +683,6 @@ __global__ void __launch_bounds__(kDenseBlock) k_amg_dense(int64_t n, int64_t ld
     }
 }
 
-int fine_grid(const AmgSellView& F) {
-    const int64_t want = (F.n_slices + kBlock / 32 - 1) / (kBlock / 32);
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 8));
-}
-
 // Blocks of `fn` (kBlock threads, no dynamic shared memory) resident on one SM
 // of the current device, from the occupancy calculator, cached per device and
 // kernel: grids of grid-stride kernels stay within one wave.
@@ -701,6 +699,12 @@ int resident_blocks(const void* fn) {
     per_sm = std::max(1, per_sm);
     cache[{dev, fn}] = per_sm;
     return per_sm;
+}
+
+// finest-level sweeps: one warp per slice pair at a time, one resident wave
+int fine_grid(const AmgSellView& F, const void* fn) {
+    const int64_t want = (F.n_slices + kBlock / 32 - 1) / (kBlock / 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * resident_blocks(fn)));
 }
 
 int amg_grid(int64_t rows, int G, int U, const void* fn) {
@@ -750,13 +754,12 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
         const V w = (V)lv.omega;
         if (l == 0 && h.fine.ptr) {
             const V* fv = pick<V>(h.fine.v32, h.fine.v64);
-            const int g = fine_grid(h.fine);
             pbeg(OASIS_PROF_AMG_FINE);
             if (h.fine.dcol)
-                k_amg_fine<V, true, true><<<g, kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), nullptr, vec(wk.x[0]),
+                k_amg_fine<V, true, true><<<fine_grid(h.fine, (const void*)k_amg_fine<V, true, true>), kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), nullptr, vec(wk.x[0]),
                                                                vec(wk.res[0]), st);
             else
-                k_amg_fine<V, false, true><<<g, kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), nullptr, vec(wk.x[0]),
+                k_amg_fine<V, false, true><<<fine_grid(h.fine, (const void*)k_amg_fine<V, false, true>), kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), nullptr, vec(wk.x[0]),
                                                                 vec(wk.res[0]), st);
             pend();
         } else {
@@ -791,13 +794,12 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
         pend();
         if (l == 0 && h.fine.ptr) {
             const V* fv = pick<V>(h.fine.v32, h.fine.v64);
-            const int g = fine_grid(h.fine);
             pbeg(OASIS_PROF_AMG_FINE);
             if (h.fine.dcol)
-                k_amg_fine<V, true, false><<<g, kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), vec(wk.x[0]), xo(0),
+                k_amg_fine<V, true, false><<<fine_grid(h.fine, (const void*)k_amg_fine<V, true, false>), kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), vec(wk.x[0]), xo(0),
                                                                 nullptr, st);
             else
-                k_amg_fine<V, false, false><<<g, kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), vec(wk.x[0]), xo(0),
+                k_amg_fine<V, false, false><<<fine_grid(h.fine, (const void*)k_amg_fine<V, false, false>), kBlock, 0, s>>>(h.fine, fv, d, w, rin(0), vec(wk.x[0]), xo(0),
                                                                  nullptr, st);
             pend();
         } else {

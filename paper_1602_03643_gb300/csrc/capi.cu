@@ -217,6 +217,7 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     OASIS_CHECK(prm->precision == OASIS_FP64 || prm->precision == OASIS_MIXED, OASIS_EINVAL, "precision");
     OASIS_CHECK(prm->guess >= 0 && prm->guess <= 2, OASIS_EINVAL, "guess");
     OASIS_CHECK(prm->spmv_variant >= 0 && prm->spmv_variant <= OASIS_MAX_VARIANTS, OASIS_EINVAL, "spmv_variant");
+    OASIS_CHECK(prm->bicg_variant >= 0 && prm->bicg_variant <= 8, OASIS_EINVAL, "bicg_variant");
     OASIS_CHECK(prm->pressure_pc == OASIS_PC_JACOBI || prm->pressure_pc == OASIS_PC_AMG, OASIS_EINVAL,
                 "pressure_pc");
     OASIS_CHECK(prm->inner_iters >= 0 && prm->inner_iters <= 16, OASIS_EINVAL, "inner_iters must be in [0, 16]");

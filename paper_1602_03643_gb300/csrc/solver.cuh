@@ -179,7 +179,7 @@ struct Solver {
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     // eager-mode kernel timing (CUDA events around selected launches)
-    static constexpr int kProfFamilies = 13;
+    static constexpr int kProfFamilies = 14;
     bool prof_on = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
     std::vector<std::pair<int, int>> ev_used;

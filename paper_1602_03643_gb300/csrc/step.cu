@@ -293,6 +293,43 @@ __device__ __forceinline__ void mirror_coefs(KrylovState* st, int k) {
     st->beta_f[k] = (float)st->beta[k];
 }
 
+// Convergence test of an outer sweep and start of a new inner solve (last
+// block, thread 0), from the squared norms of the float64-quality residuals.
+template <int NR>
+__device__ __forceinline__ void bicg_outer_finish(KrylovState* st, int k0, const double* tot, const Ctl& ctl) {
+    int outer = 0;
+    for (int c = 0; c < NR; ++c) {
+        const int k = k0 + c;
+        if (st->col_done[k]) continue;
+        const double rr = tot[c];
+        st->rr[k] = rr;
+        if (!isfinite(rr)) {
+            st->status = OASIS_ENAN;
+            st->col_done[k] = 1;
+        } else if (rr <= ctl.rtol2 * st->bb[k]) {
+            st->col_done[k] = 1;
+        } else if (st->it_total[k] >= ctl.max_it || st->sweeps >= kMaxSweeps) {
+            st->status = OASIS_ENOTCONV;
+            st->col_done[k] = 1;
+        } else {
+            st->in_done[k] = 0;
+            st->rho[k] = 1.0;
+            st->alpha[k] = 1.0;
+            st->omega[k] = 1.0;
+            st->beta[k] = 0.0;
+            mirror_coefs(st, k);
+            st->rho_new[k] = rr;
+            st->rr0_in[k] = rr;
+            st->rr_in[k] = rr;
+            outer = 1;
+        }
+    }
+    st->sweeps += 1;
+    st->it_in = 0;
+    set_cond(ctl.use_cond, ctl.h_outer, outer);
+    set_cond(ctl.use_cond, ctl.h_inner, any_inner<NR>(st, k0));
+}
+
 // Outer sweep: r = r0 - A Delta with float64-quality products (float-float in
 // the mixed path), convergence test, start of a new inner solve.
 template <class P, int D, int NR, int R>
@@ -350,40 +387,117 @@ __global__ void __launch_bounds__(kBlock) k_bicg_outer(StepData<P> a, int k0, Ct
         __syncthreads();
     }
     double tot[NR];
-    if (grid_sum<NR, Acc>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0) {
-        KrylovState* st = a.stu;
-        int outer = 0;
-        for (int c = 0; c < NR; ++c) {
-            const int k = k0 + c;
-            if (st->col_done[k]) continue;
-            const double rr = tot[c];
-            st->rr[k] = rr;
-            if (!isfinite(rr)) {
-                st->status = OASIS_ENAN;
-                st->col_done[k] = 1;
-            } else if (rr <= ctl.rtol2 * st->bb[k]) {
-                st->col_done[k] = 1;
-            } else if (st->it_total[k] >= ctl.max_it || st->sweeps >= kMaxSweeps) {
-                st->status = OASIS_ENOTCONV;
-                st->col_done[k] = 1;
-            } else {
-                st->in_done[k] = 0;
-                st->rho[k] = 1.0;
-                st->alpha[k] = 1.0;
-                st->omega[k] = 1.0;
-                st->beta[k] = 0.0;
-                mirror_coefs(st, k);
-                st->rho_new[k] = rr;
-                st->rr0_in[k] = rr;
-                st->rr_in[k] = rr;
-                outer = 1;
+    if (grid_sum<NR, Acc>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0)
+        bicg_outer_finish<NR>(a.stu, k0, tot, ctl);
+}
+
+// A product S * V added to an accumulator with the product's rounding error kept:
+// float64 exactly as before; float-float lazily (the high parts summed by an
+// error-free two-sum, every low part and error added in float, normalised once
+// by lazy_norm), about 11 float operations instead of a full float-float add's 26.
+__device__ __forceinline__ void lazy_add_prod(double& acc, double x, double v) { acc = fma(x, v, acc); }
+__device__ __forceinline__ void lazy_add_prod(ff& acc, float2 x, float v) {
+    const float p = x.x * v;
+    const float e = __fmaf_rn(x.y, v, __fmaf_rn(x.x, v, -p));
+    const ff t = two_sum(acc.hi, p);
+    acc.hi = t.hi;
+    acc.lo += t.lo + e;
+}
+__device__ __forceinline__ double lazy_norm(double a) { return a; }
+__device__ __forceinline__ ff lazy_norm(ff a) { return two_sum(a.hi, a.lo); }
+
+// The outer sweep in row-split form (G lanes per row, U rows in flight, as the
+// row-split product): r = r0 - A Delta with float64-quality products, each
+// lane's entries accumulated lazily, the group's lanes summed in a float-float
+// shuffle tree; no shared-memory staging.
+template <class P, int D, int NR, int G, int U>
+__global__ void __launch_bounds__(kBlock) k_bicg_outer_rows(StepData<P> a, int k0, Ctl ctl) {
+    using V = typename P::V;
+    using S = typename P::S;
+    using Acc = typename P::Acc;
+    constexpr int RPW = 32 / G;
+    int live[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) live[c] = !a.stu->col_done[k0 + c];
+    Acc part[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc_zero(part[c]);
+    const int32_t* __restrict__ rp = a.rp;
+    const int32_t* __restrict__ col = a.col;
+    const V* __restrict__ A = a.A;
+    const S* __restrict__ du = a.du;
+    const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = w0 * RPW * U; base < a.n; base += nw * RPW * U) {
+        int64_t i[U];
+        int32_t q[U], e[U];
+        Acc acc[U][NR];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            i[u] = base + u * RPW + grp;
+            const bool ok = i[u] < a.n;
+            q[u] = ok ? rp[i[u]] + lg : 0;
+            e[u] = ok ? rp[i[u] + 1] : 0;
+#pragma unroll
+            for (int c = 0; c < NR; ++c) acc_zero(acc[u][c]);
+        }
+        bool more = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) more |= q[u] < e[u];
+        while (more) {
+            size_t j[U];
+            V av[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool has = q[u] < e[u];
+                j[u] = has ? (size_t)col[q[u]] * D + k0 : (size_t)k0;
+                av[u] = has ? A[q[u]] : V(0);
+            }
+            S g[U][NR];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int c = 0; c < NR; ++c) g[u][c] = du[j[u] + c];
+            more = false;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (q[u] < e[u]) {
+#pragma unroll
+                    for (int c = 0; c < NR; ++c) lazy_add_prod(acc[u][c], g[u][c], av[u]);
+                    q[u] += G;
+                }
+                more |= q[u] < e[u];
             }
         }
-        st->sweeps += 1;
-        st->it_in = 0;
-        set_cond(ctl.use_cond, ctl.h_outer, outer);
-        set_cond(ctl.use_cond, ctl.h_inner, any_inner<NR>(st, k0));
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                acc[u][c] = lazy_norm(acc[u][c]);
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) acc_add(acc[u][c], acc_shfl(acc[u][c], o));
+            }
+            if (i[u] < a.n && lg == 0) {
+#pragma unroll
+                for (int c = 0; c < NR; ++c) {
+                    if (!live[c]) continue;
+                    const size_t o = (size_t)i[u] * D + k0 + c;
+                    const S rs = s_sub(a.r0[o], s_of_acc(acc[u][c]));
+                    const V rv = s_v(rs);
+                    a.r[o] = rv;
+                    a.rh[o] = rv;
+                    a.p[o] = 0;
+                    a.v[o] = 0;
+                    a.dl[o] = 0;
+                    acc_prod(part[c], rv, rv);
+                }
+            }
+        }
     }
+    double tot[NR];
+    if (grid_sum<NR, Acc>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0)
+        bicg_outer_finish<NR>(a.stu, k0, tot, ctl);
 }
 
 // p = r + beta (p - omega v),  ph = D^{-1} p
@@ -409,6 +523,31 @@ __global__ void __launch_bounds__(kBlock) k_bicg_dir(StepData<P> a, int k0) {
             a.ph[o] = di * pv;
         }
     }
+}
+
+// Coefficients from the product's dot products (last block, thread 0).
+template <int MODE, int NR>
+__device__ __forceinline__ void bicg_spmm_finish(KrylovState* st, int k0, const int (&act)[NR],
+                                                 const double* tot, const Ctl& ctl) {
+    for (int c = 0; c < NR; ++c) {
+        if (!act[c]) continue;
+        const int k = k0 + c;
+        if (MODE == 0) {
+            const double rv = tot[c];
+            if (rv == 0.0 || !isfinite(rv)) {
+                st->in_done[k] = 1;      // breakdown: restart from the float64-quality residual
+                st->it_total[k] += 1;    // counted, so that restarts end at the cap
+                st->alpha[k] = 0.0;
+            } else {
+                st->alpha[k] = st->rho_new[k] / rv;
+            }
+        } else {
+            const double ts = tot[c], tt = tot[NR + c];
+            st->omega[k] = (tt > 0.0 && isfinite(tt)) ? ts / tt : 0.0;
+        }
+        mirror_coefs(st, k);
+    }
+    if (MODE == 0) set_cond(ctl.use_cond, ctl.h_inner, any_inner<NR>(st, k0));
 }
 
 // y = A x with the dot products needed next:
@@ -466,28 +605,125 @@ __global__ void __launch_bounds__(kBlock) k_bicg_spmm(StepData<P> a, int k0, Ctl
         __syncthreads();
     }
     double tot[NV];
-    if (grid_sum_lite<NV, V>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0) {
-        KrylovState* st = a.stu;
-        for (int c = 0; c < NR; ++c) {
-            if (!act[c]) continue;
-            const int k = k0 + c;
-            if (MODE == 0) {
-                const double rv = tot[c];
-                if (rv == 0.0 || !isfinite(rv)) {
-                    st->in_done[k] = 1;      // breakdown: restart from the float64-quality residual
-                    st->it_total[k] += 1;    // counted, so that restarts end at the cap
-                    st->alpha[k] = 0.0;
-                } else {
-                    st->alpha[k] = st->rho_new[k] / rv;
-                }
-            } else {
-                const double ts = tot[c], tt = tot[NR + c];
-                st->omega[k] = (tt > 0.0 && isfinite(tt)) ? ts / tt : 0.0;
-            }
-            mirror_coefs(st, k);
+    if (grid_sum_lite<NV, V>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0)
+        bicg_spmm_finish<MODE, NR>(a.stu, k0, act, tot, ctl);
+}
+
+// The same product and dots in row-split form: rows are served by groups of G
+// lanes (lane lg takes the row's entries lg, lg + G, ...), and every group keeps
+// U rows in flight (row pointers, then per round one entry of each unfinished
+// row: value and column, then the NR gathered values), with no shared-memory
+// staging; the lanes' sums meet in a fixed shuffle tree.  Grid: one resident
+// wave, rows walked grid-stride.
+template <class P, int D, int NR, int MODE, int G, int U>
+__global__ void __launch_bounds__(kBlock) k_bicg_spmm_rows(StepData<P> a, int k0, Ctl ctl) {
+    using V = typename P::V;
+    int act[NR];
+    if (!load_active<NR>(a.stu, k0, act)) return;
+    constexpr int NV = MODE == 0 ? NR : 2 * NR;
+    constexpr int RPW = 32 / G;
+    const V* __restrict__ x = MODE == 0 ? a.ph : a.sh;
+    V* __restrict__ y = MODE == 0 ? a.v : a.t;
+    const int32_t* __restrict__ rp = a.rp;
+    const int32_t* __restrict__ col = a.col;
+    const V* __restrict__ A = a.A;
+    const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    V part[NV] = {};
+    for (int64_t base = w0 * RPW * U; base < a.n; base += nw * RPW * U) {
+        int64_t i[U];
+        int32_t q[U], e[U];
+        V acc[U][NR];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            i[u] = base + u * RPW + grp;
+            const bool ok = i[u] < a.n;
+            q[u] = ok ? rp[i[u]] + lg : 0;
+            e[u] = ok ? rp[i[u] + 1] : 0;
+#pragma unroll
+            for (int c = 0; c < NR; ++c) acc[u][c] = 0;
         }
-        if (MODE == 0) set_cond(ctl.use_cond, ctl.h_inner, any_inner<NR>(st, k0));
+        bool more = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) more |= q[u] < e[u];
+        while (more) {
+            size_t j[U];
+            V av[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool has = q[u] < e[u];
+                j[u] = has ? (size_t)col[q[u]] * D + k0 : (size_t)k0;
+                av[u] = has ? A[q[u]] : V(0);
+            }
+            V g[U][NR];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int c = 0; c < NR; ++c) g[u][c] = x[j[u] + c];
+            more = false;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (q[u] < e[u]) {
+#pragma unroll
+                    for (int c = 0; c < NR; ++c) acc[u][c] += av[u] * g[u][c];
+                    q[u] += G;
+                }
+                more |= q[u] < e[u];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) acc[u][c] += __shfl_xor_sync(0xffffffffu, acc[u][c], o);
+            }
+            if (i[u] < a.n && lg == 0) {
+#pragma unroll
+                for (int c = 0; c < NR; ++c) {
+                    if (!act[c]) continue;
+                    const size_t o = (size_t)i[u] * D + k0 + c;
+                    y[o] = acc[u][c];
+                    if (MODE == 0) {
+                        part[c] += a.rh[o] * acc[u][c];
+                    } else {
+                        part[c] += acc[u][c] * a.s[o];
+                        part[NR + c] += acc[u][c] * acc[u][c];
+                    }
+                }
+            }
+        }
     }
+    double tot[NV];
+    if (grid_sum_lite<NV, V>(part, tot, a.partial, &a.stu->ticket) && threadIdx.x == 0)
+        bicg_spmm_finish<MODE, NR>(a.stu, k0, act, tot, ctl);
+}
+
+// Candidate shapes of the d-RHS BiCGStab product for the autotuner: the row-tile
+// form (lanes = 0) and row-split forms (G lanes per row, U rows in flight).  The
+// shapes add a row's products in different orders, so the candidates agree to
+// rounding, not bitwise; a solver keeps one shape for its whole life (and a
+// caller may force one with bicg_variant).
+// A row-split shape also runs the sweeps' outer residual in row-split form
+// (same lanes per row, two rows in flight), the row-tile shape in tile form.
+template <class P, int D>
+struct BicgVariant {
+    void (*fn0)(StepData<P>, int, Ctl);
+    void (*fn1)(StepData<P>, int, Ctl);
+    void (*outer)(StepData<P>, int, Ctl);   // row-split outer residual (null: tile form)
+    int lanes, rows;
+};
+constexpr int kBicgVariants = 5;
+template <class P, int D>
+static const BicgVariant<P, D>* bicg_variant_table() {
+#define OASIS_BICGV(G, U)                                                                                   \
+    {k_bicg_spmm_rows<P, D, D, 0, G, U>, k_bicg_spmm_rows<P, D, D, 1, G, U>, k_bicg_outer_rows<P, D, D, G, 2>, G, U}
+    static const BicgVariant<P, D> t[kBicgVariants] = {
+        {k_bicg_spmm<P, D, D, 0, kTileN>, k_bicg_spmm<P, D, D, 1, kTileN>, nullptr, 0, kTileN},
+        OASIS_BICGV(4, 4), OASIS_BICGV(4, 2), OASIS_BICGV(8, 2), OASIS_BICGV(2, 4)};
+#undef OASIS_BICGV
+    return t;
 }
 
 // s = r - alpha v,  sh = D^{-1} s
@@ -804,9 +1040,22 @@ __global__ void __launch_bounds__(kBlock) k_pcg_outer_sell(StepData<P> a, Ctl ct
     sell_slices(a, [&](int64_t i, int len, int64_t base, int) {
         Acc kx;
         acc_zero(kx);
-        for (int k = 0; k < len; ++k) {
-            const int64_t q = base + 32 * (int64_t)k;
-            acc_add(kx, acc_of_s(s_mul_s(a.Kouts[q], a.x[a.sell_col[q]])));
+        // four entries' column, value and gathered operand loads issued together,
+        // then their products added in entry order
+        constexpr int C = 4;
+        for (int k = 0; k < len; k += C) {
+            S kv[C], xv[C];
+#pragma unroll
+            for (int u = 0; u < C; ++u) {
+                const int64_t q = base + 32 * (int64_t)(k + u);
+                const bool ok = k + u < len;
+                const int32_t j = ok ? a.sell_col[q] : 0;
+                kv[u] = ok ? a.Kouts[q] : s_zero<S>();
+                xv[u] = a.x[j];
+            }
+#pragma unroll
+            for (int u = 0; u < C; ++u)
+                if (k + u < len) acc_add(kx, acc_of_s(s_mul_s(kv[u], xv[u])));
         }
         if (i < a.n) {
             const S bi = s_sub(a.b[i], mean);
@@ -1847,10 +2096,15 @@ static int elem_grid(int64_t items) {
 }
 
 // Elementwise kernels that end in a last-block reduction: two blocks per SM
-// (fewer partials and tickets; measured faster than one row per thread).
+// while the vectors fit in L2 (fewer partials and tickets; measured faster than
+// one row per thread at 275k rows), a full resident wave of eight blocks per SM
+// for larger systems, whose HBM streams need every warp's loads in flight
+// (measured at 1.4M rows: 16 warps per SM left the CG update at 8 % of the DRAM
+// bandwidth, stalled on latency).
 static int red_grid(int64_t items) {
     const int64_t want = (items + kBlock - 1) / kBlock;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 2));
+    const int per_sm = items >= (int64_t(1) << 20) ? 8 : 2;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * per_sm));
 }
 
 template <class P, int D>
@@ -1870,6 +2124,10 @@ struct StepImplT final : StepImpl {
     int g_sellr = 1;     // grid-stride SELL kernels ending in a reduction: one resident wave
     int iter_v = 0;                                   // chosen CG iteration shape
     int amg_v = 0;                                    // chosen multigrid CG product shape
+    int bicg_v = 0;                                   // chosen d-RHS BiCGStab product shape
+    double bicg_us[kBicgVariants] = {0};
+    int bicg_grid[kBicgVariants] = {0};
+    int bicg_outer_grid[kBicgVariants] = {0};
     double amg_us[kAmgVariants] = {0};
     double tune_us[OASIS_MAX_VARIANTS] = {0};
     int it_grid[OASIS_MAX_VARIANTS] = {0}, it_block[OASIS_MAX_VARIANTS] = {0};
@@ -2040,7 +2298,10 @@ struct StepImplT final : StepImpl {
         Sv.run_loops(
             s, graph, which,
             [&](cudaStream_t ss_, const Loop& lp) {
-                k_bicg_outer<P, DD, NR, kTileN><<<G.go, kBlock, G.so, ss_>>>(q, k0, ctl_u(lp));
+                const int po = Sv.prof_begin(ss_, OASIS_PROF_OUTER);
+                if constexpr (DD == D && NR == D) launch_bicg_outer(q, k0, ctl_u(lp), ss_);
+                else k_bicg_outer<P, DD, NR, kTileN><<<G.go, kBlock, G.so, ss_>>>(q, k0, ctl_u(lp));
+                Sv.prof_end(ss_, po);
                 OASIS_CUDA(cudaGetLastError());
             },
             [&](cudaStream_t ss_, const Loop& lp) {
@@ -2049,13 +2310,15 @@ struct StepImplT final : StepImpl {
                 k_bicg_dir<P, DD, NR><<<ge_n, kBlock, 0, ss_>>>(q, k0);
                 Sv.prof_end(ss_, pv);
                 int pb = Sv.prof_begin(ss_, OASIS_PROF_BICG_SPMM);
-                k_bicg_spmm<P, DD, NR, 0, kTileN><<<G.gs0, kBlock, G.ss, ss_>>>(q, k0, c);
+                if constexpr (DD == D && NR == D) launch_bicg_spmm(0, q, k0, c, ss_);
+                else k_bicg_spmm<P, DD, NR, 0, kTileN><<<G.gs0, kBlock, G.ss, ss_>>>(q, k0, c);
                 Sv.prof_end(ss_, pb);
                 pv = Sv.prof_begin(ss_, OASIS_PROF_BICG_VEC);
                 k_bicg_s<P, DD, NR><<<ge_n, kBlock, 0, ss_>>>(q, k0);
                 Sv.prof_end(ss_, pv);
                 pb = Sv.prof_begin(ss_, OASIS_PROF_BICG_SPMM);
-                k_bicg_spmm<P, DD, NR, 1, kTileN><<<G.gs1, kBlock, G.ss, ss_>>>(q, k0, c);
+                if constexpr (DD == D && NR == D) launch_bicg_spmm(1, q, k0, c, ss_);
+                else k_bicg_spmm<P, DD, NR, 1, kTileN><<<G.gs1, kBlock, G.ss, ss_>>>(q, k0, c);
                 Sv.prof_end(ss_, pb);
                 pv = Sv.prof_begin(ss_, OASIS_PROF_BICG_VEC);
                 k_bicg_xr<P, DD, NR><<<ge_red, kBlock, 0, ss_>>>(q, k0, c);
@@ -2170,7 +2433,9 @@ struct StepImplT final : StepImpl {
                 s, graph, 1,
                 [&](cudaStream_t ss, const Loop& lp) {
                     const Ctl c = ctl_p(lp);
+                    const int po = Sv.prof_begin(ss, OASIS_PROF_OUTER);
                     k_pcg_outer_sell<P><<<g_sellr, kBlock, 0, ss>>>(a, c);
+                    Sv.prof_end(ss, po);
                     k_amg_cg_start<P><<<ge_n, kBlock, 0, ss>>>(a);
                     vcycle(ss);
                     if (a.sell_dcol) k_amg_cg_spmv<P, true, true><<<g_sellr, kBlock, 0, ss>>>(a, c);
@@ -2179,7 +2444,9 @@ struct StepImplT final : StepImpl {
                 },
                 [&](cudaStream_t ss, const Loop& lp) {
                     const Ctl c = ctl_p(lp);
+                    const int pu = Sv.prof_begin(ss, OASIS_PROF_PCG_UPDATE);
                     k_amg_cg_update<P><<<ge_red, kBlock, 0, ss>>>(a, c);
+                    Sv.prof_end(ss, pu);
                     vcycle(ss);
                     const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
                     const AmgVariant<P>& av = amg_variant_table<P>()[amg_v];
@@ -2198,7 +2465,9 @@ struct StepImplT final : StepImpl {
             s, graph, 1,
             [&](cudaStream_t ss, const Loop& lp) {
                 const Ctl c = ctl_p(lp);
+                const int po = Sv.prof_begin(ss, OASIS_PROF_OUTER);
                 k_pcg_outer_sell<P><<<g_sellr, kBlock, 0, ss>>>(a, c);
+                Sv.prof_end(ss, po);
                 const int pu = Sv.prof_begin(ss, OASIS_PROF_PCG_UPDATE);
                 k_pcg_init_sell<P><<<g_sell, kBlock, 0, ss>>>(a, c);
                 Sv.prof_end(ss, pu);
@@ -2368,7 +2637,89 @@ struct StepImplT final : StepImpl {
         amg_v = best;
     }
 
+    // the outer residual of the velocity solve's sweeps in the chosen form
+    void launch_bicg_outer(const StepData<P>& q, int k0, const Ctl& c, cudaStream_t ss) const {
+        const BicgVariant<P, D>& bv = bicg_variant_table<P, D>()[bicg_v];
+        if (bv.outer) bv.outer<<<bicg_outer_grid[bicg_v], kBlock, 0, ss>>>(q, k0, c);
+        else k_bicg_outer<P, D, D, kTileN><<<g_out_u, kBlock, sm_out_u, ss>>>(q, k0, c);
+        OASIS_CUDA(cudaGetLastError());
+    }
+
+    // the d-RHS product of the velocity solve in the chosen shape
+    void launch_bicg_spmm(int mode, const StepData<P>& q, int k0, const Ctl& c, cudaStream_t ss) const {
+        const BicgVariant<P, D>& bv = bicg_variant_table<P, D>()[bicg_v];
+        if (bv.lanes == 0) {
+            if (mode == 0) bv.fn0<<<g_spmm0, kBlock, sm_spmm, ss>>>(q, k0, c);
+            else bv.fn1<<<g_spmm1, kBlock, sm_spmm, ss>>>(q, k0, c);
+        } else {
+            (mode == 0 ? bv.fn0 : bv.fn1)<<<bicg_grid[bicg_v], kBlock, 0, ss>>>(q, k0, c);
+        }
+        OASIS_CUDA(cudaGetLastError());
+    }
+
+    // Time both products of every shape on this solver's pattern (values zeroed,
+    // scratch Krylov state, 2 untimed + 7 timed launches each, median) and keep
+    // the fastest; forced = k >= 1 takes shape k untimed.
+    void tune_bicg(cudaStream_t s, int forced) {
+        const BicgVariant<P, D>* t = bicg_variant_table<P, D>();
+        OASIS_CHECK(forced >= 0 && forced <= kBicgVariants, OASIS_EINVAL, "bicg_variant: no such candidate");
+        const int64_t rows = Sv.m->n;
+        auto wave = [&](void (*fn)(StepData<P>, int, Ctl), int lanes, int in_flight) {
+            int per_sm = 0;
+            OASIS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0));
+            const int64_t per_block = (int64_t)kBlock / lanes * in_flight;
+            return (int)std::max<int64_t>(
+                1, std::min<int64_t>((rows + per_block - 1) / per_block, (int64_t)std::max(per_sm, 1) * num_sms()));
+        };
+        for (int v = 0; v < kBicgVariants; ++v) {
+            if (t[v].lanes == 0) {
+                bicg_grid[v] = g_spmm0;
+                bicg_outer_grid[v] = g_out_u;
+                continue;
+            }
+            bicg_grid[v] = wave(t[v].fn0, t[v].lanes, t[v].rows);
+            bicg_outer_grid[v] = wave(t[v].outer, t[v].lanes, 2);
+        }
+        for (auto& u : bicg_us) u = 0.0;
+        if (forced >= 1) {
+            bicg_v = forced - 1;
+            return;
+        }
+        OASIS_CUDA(cudaMemsetAsync(Sv.A.p, 0, Sv.A.bytes, s));
+        for (auto& w : Sv.w) OASIS_CUDA(cudaMemsetAsync(w.p, 0, w.bytes, s));
+        DBuf<KrylovState> scratch;
+        scratch.alloc(1);
+        StepData<P> d = a;
+        d.stu = scratch.p;
+        const Ctl c{};
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        OASIS_CUDA(cudaEventCreate(&e0));
+        OASIS_CUDA(cudaEventCreate(&e1));
+        constexpr int kWarm = 2, kTimed = 7;
+        int best = 0;
+        for (int v = 0; v < kBicgVariants; ++v) {
+            bicg_v = v;
+            float ts[kTimed];
+            for (int r = 0; r < kWarm + kTimed; ++r) {
+                OASIS_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(KrylovState), s));
+                OASIS_CUDA(cudaEventRecord(e0, s));
+                launch_bicg_spmm(0, d, 0, c, s);
+                launch_bicg_spmm(1, d, 0, c, s);
+                OASIS_CUDA(cudaEventRecord(e1, s));
+                OASIS_CUDA(cudaEventSynchronize(e1));
+                if (r >= kWarm) OASIS_CUDA(cudaEventElapsedTime(&ts[r - kWarm], e0, e1));
+            }
+            std::sort(ts, ts + kTimed);
+            bicg_us[v] = 1e3 * (double)ts[kTimed / 2];
+            if (bicg_us[v] < bicg_us[best]) best = v;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        bicg_v = best;
+    }
+
     void tune(cudaStream_t s, int forced) override {
+        tune_bicg(s, Sv.prm.bicg_variant);
         if (Sv.prm.pressure_pc == OASIS_PC_AMG) {
             tune_amg(s, forced);
             return;
@@ -2420,6 +2771,14 @@ struct StepImplT final : StepImpl {
     }
 
     void tuning(oasis_tuning* out) const override {
+        const BicgVariant<P, D>* bt = bicg_variant_table<P, D>();
+        out->bicg_n_variants = kBicgVariants;
+        out->bicg_chosen = bicg_v + 1;
+        for (int v = 0; v < kBicgVariants; ++v) {
+            out->bicg_lanes[v] = bt[v].lanes;
+            out->bicg_rows[v] = bt[v].rows;
+            out->bicg_us[v] = bicg_us[v];
+        }
         if (Sv.prm.pressure_pc == OASIS_PC_AMG) {
             const AmgVariant<P>* t = amg_variant_table<P>();
             out->n_variants = kAmgVariants;

@@ -16,7 +16,7 @@ class IPCSRun:
     def __init__(self, problem, precision=capi.OASIS_FP64, rtol_u=1e-12, rtol_p=1e-12, max_it_u=2000,
                  max_it_p=50000, inner_rtol=1e-4, batch_rhs=1, use_graph=0, guess=capi.OASIS_GUESS_ZERO,
                  spmv_variant=0, pressure_pc=0, inner_iters=1, convection=0, velocity_update=0,
-                 scalars=True, stream=None):
+                 scalars=True, stream=None, bicg_variant=0):
         pb = problem
         self.pb = pb
         self.stream = stream
@@ -28,7 +28,7 @@ class IPCSRun:
         self.nnz = capi.oasis_mesh_info(self.mesh)[2]
         self.params = capi.make_params(pb.nu, pb.dt, tuple(pb.f), rtol_u, rtol_p, max_it_u, max_it_p,
                                        precision, inner_rtol, batch_rhs, use_graph, guess, spmv_variant,
-                                       pressure_pc, inner_iters, convection, velocity_update)
+                                       pressure_pc, inner_iters, convection, velocity_update, bicg_variant)
         self.solver = capi.oasis_solver_create(self.mesh, self.params, pb.dirichlet, stream)
         self.t = pb.t0
         capi.oasis_set_fields(self.solver, pb.u_nm1, pb.u_nm2, pb.p, pb.t0, False, stream)

@@ -35,12 +35,12 @@ def relerr(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
-def _run(pb, precision, pc, graph=1, rtol=None, guess=None):
+def _run(pb, precision, pc, graph=1, rtol=None, guess=None, bicg_variant=0):
     from paper_1602_03643_gb300.driver import IPCSRun
     c = capi()
     rt = rtol if rtol is not None else (1e-12 if precision == c.OASIS_FP64 else 1e-8)
     return IPCSRun(pb, precision=precision, rtol_u=rt, rtol_p=rt, use_graph=graph, pressure_pc=pc,
-                   guess=c.OASIS_GUESS_PREV_PHI if guess is None else guess)
+                   guess=c.OASIS_GUESS_PREV_PHI if guess is None else guess, bicg_variant=bicg_variant)
 
 
 PROBLEMS = {
@@ -115,11 +115,13 @@ def test_amg_mixed_per_field_error_and_fewer_iterations():
 
 
 def test_amg_graph_equals_eager_bitwise():
+    """Same bits from the graph and the eager step (the BiCGStab product shape is
+    fixed: the autotuner of each solver could pick another summation order)."""
     c = capi()
     pb = WP.stress_cube(8, ordering="rcm")
     out = []
     for g in (1, 0):
-        run = _run(pb, c.OASIS_MIXED, c.OASIS_PC_AMG, graph=g)
+        run = _run(pb, c.OASIS_MIXED, c.OASIS_PC_AMG, graph=g, bicg_variant=2)
         try:
             run.step(3)
             out.append(run.fields())

@@ -207,12 +207,15 @@ def test_fp64_100_steps_tg2d_32():
     assert relerr(p, s.p) <= 1e-9
 
 
-def test_graph_equals_eager_bitwise():
+@pytest.mark.parametrize("bicg_variant", [1, 2])
+def test_graph_equals_eager_bitwise(bicg_variant):
+    """Same bits from the graph and the eager step, for a row-tile and a
+    row-split BiCGStab product (each solver would otherwise tune its own)."""
     from paper_1602_03643_gb300.driver import IPCSRun
     out = []
     for g in (0, 1):
         pb = WP.taylor_green_3d(8)
-        run = IPCSRun(pb, rtol_u=1e-10, rtol_p=1e-10, use_graph=g, precision=1)
+        run = IPCSRun(pb, rtol_u=1e-10, rtol_p=1e-10, use_graph=g, precision=1, bicg_variant=bicg_variant)
         run.step(4)
         out.append(run.fields())
         run.close()
@@ -403,7 +406,7 @@ def test_consistent_update_graph_equals_eager_bitwise():
     for g in (0, 1):
         pb = WP.taylor_green_3d(6)
         run = IPCSRun(pb, precision=1, rtol_u=1e-8, rtol_p=1e-8, use_graph=g,
-                      velocity_update=c.OASIS_UPDATE_CONSISTENT)
+                      velocity_update=c.OASIS_UPDATE_CONSISTENT, bicg_variant=3)
         try:
             run.step(4)
             out.append(run.fields())
@@ -436,7 +439,7 @@ def test_cg_shapes_bitwise_equal_and_tuned(precision, case, pc):
     out = []
     for v in range(1, len(cands) + 1):
         run = IPCSRun(pb, precision=precision, rtol_u=1e-9, rtol_p=1e-9, use_graph=1, spmv_variant=v,
-                      pressure_pc=pc)
+                      pressure_pc=pc, bicg_variant=1)
         try:
             assert c.oasis_get_tuning(run.solver)["chosen"] == v
             st = run.step(3)
@@ -447,6 +450,41 @@ def test_cg_shapes_bitwise_equal_and_tuned(precision, case, pc):
         assert it == out[0][1]
         for a, b in zip(f, out[0][0]):
             np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_bicg_product_shapes_agree_with_oracle_and_tuned(precision):
+    """Every candidate shape of the batched BiCGStab product (row tiles, or G
+    lanes per row with several rows in flight) gives steps that match the
+    oracle (the shapes differ in summation order only); the autotuner timed
+    every candidate and kept the fastest; a forced shape is kept."""
+    from paper_1602_03643_gb300.driver import IPCSRun
+    c = capi()
+    pb = WP.stress_cube(10, ordering="random")
+    rtol = 1e-12 if precision == 0 else 1e-9
+    run = IPCSRun(pb, precision=precision, rtol_u=rtol, rtol_p=rtol, use_graph=1, pressure_pc=c.OASIS_PC_AMG)
+    try:
+        tun = c.oasis_get_tuning(run.solver)
+    finally:
+        run.close()
+    cands = tun["bicg_candidates"]
+    assert len(cands) >= 4 and cands[0]["lanes"] == 0
+    assert all(x["us"] > 0 for x in cands)
+    assert cands[tun["bicg_chosen"] - 1]["us"] == min(x["us"] for x in cands)
+    ref = IPCS(pb).run(3)
+    tol = 1e-10 if precision == 0 else 1e-6
+    for v in range(1, len(cands) + 1):
+        run = IPCSRun(pb, precision=precision, rtol_u=rtol, rtol_p=rtol, use_graph=1,
+                      pressure_pc=c.OASIS_PC_AMG, bicg_variant=v)
+        try:
+            assert c.oasis_get_tuning(run.solver)["bicg_chosen"] == v
+            st = run.step(3)
+            u, p, _ = run.fields()
+        finally:
+            run.close()
+        assert st.status == c.OASIS_OK
+        assert relerr(u, ref.u_nm1) <= tol, (v, relerr(u, ref.u_nm1))
+        assert relerr(p, ref.p) <= 10 * tol, (v, relerr(p, ref.p))
 
 
 @pytest.mark.parametrize("precision", [0, 1])

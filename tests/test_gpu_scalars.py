@@ -132,7 +132,7 @@ def test_scalars_graph_equals_eager_bitwise():
     out = []
     for g in (0, 1):
         pb = WP.with_scalars(WP.taylor_green_3d(6), ns=2)
-        run = IPCSRun(pb, precision=1, rtol_u=1e-8, rtol_p=1e-8, use_graph=g)
+        run = IPCSRun(pb, precision=1, rtol_u=1e-8, rtol_p=1e-8, use_graph=g, bicg_variant=4)
         try:
             run.step(4)
             out.append(run.scalar_fields())
