@@ -76,9 +76,8 @@ def workload_config(name, pb, precision, gpu=True):
 # per workload, with the profile summary it comes from; valid for the kernels as
 # they stand (an entry is removed when its kernel changes)
 _S112 = "profiles/dram_traffic_products_stress112_rcm.md (stress112_rcm capture, scaled by algorithmic bytes)"
-MEASURED_TRAFFIC = {("stress128_rcm", "bicg_spmm"): (331.9e6, _S112),
-                    ("stress128_rcm", "amg_fine"): (221.9e6, _S112),
-                    ("stress128_rcm", "pcg_spmv"): (215.2e6, _S112)}
+MEASURED_TRAFFIC = {("stress128_rcm", "amg_fine"): (222.0e6, _S112),
+                    ("stress128_rcm", "pcg_spmv"): (215.0e6, _S112)}
 
 
 def family_bytes(pb, nnz, args, tuning, amg):
@@ -98,8 +97,9 @@ def family_bytes(pb, nnz, args, tuning, amg):
                    their 2(L-2)+1 launches: per sweep 8 nnz_l + 20 n_l; dense 4 nc ld + 8 nc
       bicg_vec     BiCGStab vector kernels, averaged over dir (64 N), s (52 N), and
                    the solution/residual update with its dots (96 N), for D = 3
-      assemble     convection cell terms (80 T + 48 N) and the fused row pass (incidence
-                   and cell terms 48 T, per entry 28 Z, per row 168 N), one pair per step
+      assemble     convecting velocity per dof (u^{n-1}, u^{n-2} read, ubar written: 60 N),
+                   convection cell terms (80 T + 12 N) and the fused row pass (incidence and
+                   cell terms 48 T, per entry 28 Z, per row 132 N), once per step
       outer        float64-quality residuals of the sweeps, averaged over the tentative
                    solve's (A + columns 8 Z; r0, Delta gathered, r, rh, p, v, dl: 112 N)
                    and the pressure's (K as float-float + columns 12 Z; 56 N)
@@ -132,8 +132,8 @@ def family_bytes(pb, nnz, args, tuning, amg):
                         8 * Z + 4 * (N + 1) + 12 * D * N, f"8 Z + 4 N + 12 D N")
     out["bicg_vec"] = ("k_bicg_dir / k_bicg_s / k_bicg_xr (BiCGStab vector updates + dots)",
                        (64 + 52 + 96) * N * D / 3 / 3, "(64 + 52 + 96) N / 3 per launch (D = 3)")
-    out["assemble"] = ("k_cell_beta + k_assemble (convection assembly + Algorithm 2, one pair per step)",
-                       80 * T + 48 * N + 48 * T + 28 * Z + 168 * N, "128 T + 28 Z + 216 N per pair")
+    out["assemble"] = ("k_ubar + k_cell_beta + k_assemble (convection assembly + Algorithm 2, once per step)",
+                       60 * N + 80 * T + 12 * N + 48 * T + 28 * Z + 132 * N, "128 T + 28 Z + 204 N per step")
     out["outer"] = ("k_bicg_outer(_rows) / k_pcg_outer_sell (float-float residuals of the sweeps)",
                     10 * Z + 84 * N, "(8 Z + 112 N + 12 Z + 56 N) / 2 per launch")
     if amg:
@@ -361,6 +361,8 @@ def run_ours(args, rank, world):
     peak = peaks.get("hbm_gbs", 6800.0)
     fams = family_bytes(pb, run.nnz, args, tun_e, amg_info)
     table = {}
+    bc = tuning["bicg_candidates"][tuning["bicg_chosen"] - 1]
+    shape = {"bicg_spmm": "@%dx%dx%d" % (bc["lanes"], bc["rows"], bc["min_blocks"]) if bc["lanes"] else "@tile"}
     for f, (kernel, nbytes, per) in fams.items():
         n_l, ms_l = fam.get(f, (0, 0.0))
         if not n_l:
@@ -370,8 +372,8 @@ def run_ours(args, rank, world):
                     "bytes_counted": per, "launches": n_l, "avg_launch_us": ms_l / n_l * 1e3,
                     "ms_per_step": ms_l / n_prof, "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": ach / peak,
-                    "traffic": MEASURED_TRAFFIC.get((args.workload, f), (None,))[0],
-                    "traffic_source": MEASURED_TRAFFIC.get((args.workload, f), (None, None))[1]}
+                    "traffic": MEASURED_TRAFFIC.get((args.workload, f + shape.get(f, "")), (None,))[0],
+                    "traffic_source": MEASURED_TRAFFIC.get((args.workload, f + shape.get(f, "")), (None, None))[1]}
     # the dominant kernel: the single-kernel family (one kernel, one launch shape)
     # that takes the most time in the step
     single = [f for f in ("pcg_spmv", "bicg_spmm", "amg_fine") if f in table]
@@ -453,7 +455,8 @@ def run_ours(args, rank, world):
     sw_p = float(np.mean([s["sweeps_p"] for s in stats]))
     it_m = float(np.mean([s["it_m"] for s in stats]))
     it_c = float(np.mean([s["it_c"] for s in stats]))
-    # kernels per step in the graph: beta + assembly 2; velocity: per sweep a residual
+    # kernels per step in the graph: ubar + beta + assembly 3 (explicit convection:
+    # beta + assembly 2); velocity: per sweep a residual
     # and (all but the last) a correction, 5 per BiCGStab iteration; pressure: rhs
     # and guess 2, per sweep residual + CG start + (all but the last) correction,
     # 1 per CG iteration; update 1
@@ -475,7 +478,8 @@ def run_ours(args, rank, world):
     ni = max(1, args.inner_iters)
     upd_kernels = 3 + 2 * it_m if args.velocity_update == "consistent" else 1
     upd_kernels += args.scalars * (5 + 5 * it_c)
-    launches = int(round(args.steps * (ni * (2 + 2 * sw_u + 5 * it_u + p_kernels) + (ni - 1)
+    n_asm = 2 if args.convection == "abe" else 3
+    launches = int(round(args.steps * (ni * (n_asm + 2 * sw_u + 5 * it_u + p_kernels) + (ni - 1)
                                        + (5 if learned else 0) + upd_kernels)))
     run.close()
 
@@ -546,14 +550,24 @@ def run_guess_study(args):
     t0 = time.perf_counter()
     samples = []
     train_seeds = list(range(100, 100 + args.study_seeds))
+    stopped = {}
     with torch.cuda.stream(stream):
         for sd in train_seeds:
             run = make(sd, capi.OASIS_GUESS_PREV_PHI)
             run.record_guess(True)
             for k in range(args.study_steps):
                 capi.oasis_step(run.solver, stream, want_stats=False)
+                # a run that has left the scheme's stable range (a failed solve,
+                # non-finite fields) gives no further training samples
+                st = capi.oasis_step_stats()
+                capi.lib().oasis_last_stats(run.solver, ctypes.byref(st))
+                if st.status != 0:
+                    stopped[sd] = k
+                    break
                 if k >= 2:
-                    samples.append(run.guess_sample())
+                    feat, target = run.guess_sample()
+                    if bool(torch.isfinite(feat).all()) and bool(torch.isfinite(target).all()):
+                        samples.append((feat, target))
             run.record_guess(False)
             torch.cuda.synchronize(dev)
             run.close()
@@ -608,6 +622,7 @@ def run_guess_study(args):
         test[form] = entry
     return {"study": "learned pressure guess, channel 128x96x96, held-out seed 110",
             "train": {"seeds": train_seeds, "steps_per_seed": args.study_steps, "samples": len(samples),
+                      "runs_stopped_at_failed_step": stopped,
                       "epochs": args.train_epochs, "collect_s": t_collect},
             "test": {"seed": 110, "warmup": args.warmup, "steps": args.study_test_steps} | test,
             "solver": "mixed, 3-RHS BiCGStab, multigrid CG, CUDA graph, every solve to 1e-8",

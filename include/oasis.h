@@ -184,11 +184,13 @@ typedef struct oasis_tuning {
      * iteration timed together): lanes = 0 is the row-tile form (rows per tile in
      * bicg_rows, the entries of a tile read coalesced and summed per row through
      * shared memory); lanes = G > 0 is the row-split form, G lanes per row and
-     * bicg_rows rows in flight per lane group. */
+     * bicg_rows rows in flight per lane group, its registers capped for
+     * bicg_min_blocks resident blocks per SM (1: no cap). */
     int32_t bicg_n_variants;
     int32_t bicg_chosen;                   /* 1-based */
     int32_t bicg_lanes[8];
     int32_t bicg_rows[8];
+    int32_t bicg_min_blocks[8];
     double bicg_us[8];                     /* median time of the two products; 0 if not timed */
 } oasis_tuning;
 

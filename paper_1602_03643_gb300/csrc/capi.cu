@@ -251,6 +251,7 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     S->dinvA.alloc(vb * n, s);
     S->beta.alloc(vb * m->nc * 4, s);
     if (prm->convection == OASIS_CONV_ABE) S->beta2.alloc(vb * m->nc * 4, s);
+    else S->ubar.alloc(vb * n * D, s);
     for (auto& w : S->w) w.alloc(vb * n * D, s);
     for (auto& w : S->pw) w.alloc(vb * n, s);
     for (auto& q : S->pq) q.alloc(4 * vb * n, s);

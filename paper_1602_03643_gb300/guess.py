@@ -22,12 +22,15 @@ N_PARAMS = capi.OASIS_NET_PARAMS
 
 
 def initial_params(seed: int = 0) -> np.ndarray:
-    """He-scaled random hidden weights, zero biases, small readout weights and
-    a skip term that starts as the previous correction (a0 = 1, a1 = 0)."""
+    """He-scaled random hidden weights, zero biases, a zero readout and a skip
+    term that starts as the previous correction (a0 = 1, a1 = 0): the untrained
+    network returns the fallback phi^{n-1} exactly, so training starts from it
+    (a random readout would start it ~10 % away, far beyond the step-to-step
+    change of phi on smooth flows)."""
     g = np.random.default_rng(seed)
     w1 = g.standard_normal((2, H * 3)) * np.sqrt(2.0 / 6.0)
     w2 = g.standard_normal((2, H * H)) * np.sqrt(2.0 / (2 * H))
-    w3 = g.standard_normal(H) * 0.02
+    w3 = np.zeros(H)
     p = np.concatenate([w1[0], w1[1], np.zeros(H), w2[0], w2[1], np.zeros(H), w3, [0.0], [1.0, 0.0]])
     assert p.size == N_PARAMS
     return p.astype(np.float32)

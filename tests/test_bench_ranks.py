@@ -80,7 +80,7 @@ def test_family_bytes_model_on_a_small_mesh():
     assert abs(f["amg_transfer"][1] - want_t / 4) < 1e-9
     want_c = 2 * (8 * 200 + 20 * 20) + 4 * 3 * 4 + 8 * 3
     assert abs(f["amg_coarse"][1] - want_c / 3) < 1e-9
-    assert f["assemble"][1] == 128 * T + 28 * Z + 216 * N
+    assert f["assemble"][1] == 128 * T + 28 * Z + 204 * N
     assert f["outer"][1] == 10 * Z + 84 * N
     assert f["pcg_update"][1] == 40 * N
     # without 16-bit columns the column bytes are 4 per entry
