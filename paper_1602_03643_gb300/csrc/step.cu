@@ -120,9 +120,10 @@ __global__ void __launch_bounds__(kBlock) k_cell_beta(StepData<P> a) {
 }
 
 // Row pass of the convection assembly fused with Algorithm 2.  Per tile:
-//  A (two threads per row, all of the block): each thread sums the cell terms
-//    beta of one half of the row's incident cells into its own per-row,
-//    per-slot buffer in shared memory (increasing cell order, no atomics);
+//  A (thread per row): the cell terms beta of the incident cells are summed
+//    into a per-row, per-slot buffer in shared memory (increasing cell order,
+//    no atomics).  (Splitting a row's cells over two threads, with a second
+//    buffer, was measured slower at 128^3: 1.18 against 0.82 ms);
 //  B (entry-parallel): C_ij = t1 + ubar_i . dP_ij / (d+2),
 //    A_ij = M_ij/dt + C_ij/2 + nu K_ij/2 (Eq. 34), and the entry's share of
 //    -(C_ij + nu K_ij) u_j^{n-1} - dP^k_ij p*_j;
@@ -141,9 +142,8 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
     using Acc = typename P::Acc;
     constexpr int NB = ABE ? 2 : 1;
     extern __shared__ __align__(16) unsigned char dsm[];
-    V* s_t1 = reinterpret_cast<V*>(dsm);                       // [2][NB][max_row][R]
-    const size_t half_t1 = (size_t)NB * a.max_row * R;
-    V* s_con = s_t1 + 2 * half_t1;                             // [tile_cap][D]
+    V* s_t1 = reinterpret_cast<V*>(dsm);                       // [NB][max_row][R]
+    V* s_con = s_t1 + (size_t)NB * a.max_row * R;          // [tile_cap][D]
     __shared__ int32_t s_rp[R + 1];
     __shared__ V s_ub[NB][D][R];
     __shared__ int32_t s_dir[R];
@@ -152,23 +152,19 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
     for (int k = 0; k < D; ++k) acc_zero(part[k]);
     const V inv_d2 = (V)1 / (V)(D + 2);
     const int r = threadIdx.x;
-    static_assert(2 * R <= kBlock, "two threads per row");
-    const int rh = r % R, hf = r / R;                          // row and half of the incident cells
     for (int64_t tile = blockIdx.x; tile * R < a.n; tile += gridDim.x) {
         const TileRange T = load_tile<R>(tile, a.n, a.rp, s_rp);
-        if (hf < 2 && rh < T.nr) {
-            const int64_t i = T.r0 + rh;
-            const int32_t len = s_rp[rh + 1] - s_rp[rh];
-            V* t1h = s_t1 + hf * half_t1;
+        if (r < T.nr) {
+            const int64_t i = T.r0 + r;
+            const int32_t len = s_rp[r + 1] - s_rp[r];
             for (int32_t sl = 0; sl < len; ++sl)
 #pragma unroll
-                for (int b = 0; b < NB; ++b) t1h[((size_t)b * a.max_row + sl) * R + rh] = 0;
-            // this half's incident cells 8 at a time: their indices and slots,
-            // then their beta rows (one aligned 4-vector each), then the
-            // additions in cell order (the same order as one at a time)
+                for (int b = 0; b < NB; ++b) s_t1[((size_t)b * a.max_row + sl) * R + r] = 0;
+            // incident cells 8 at a time: their indices and slots, then their
+            // beta rows (one aligned 4-vector each), then the additions in cell
+            // order (the same order as one at a time)
             constexpr int kU = 8;
-            const int32_t qa = a.inc_ptr[i], qz = a.inc_ptr[i + 1], qm = qa + (qz - qa + 1) / 2;
-            const int32_t q0 = hf == 0 ? qa : qm, q1 = hf == 0 ? qm : qz;
+            const int32_t q0 = a.inc_ptr[i], q1 = a.inc_ptr[i + 1];
             for (int32_t qb = q0; qb < q1; qb += kU) {
                 int32_t c[kU];
                 uint32_t w[kU];
@@ -181,7 +177,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
                     const V* bsrc = b == 0 ? a.beta : a.beta2;
-                    V* t = t1h + (size_t)b * a.max_row * R;
+                    V* t = s_t1 + (size_t)b * a.max_row * R;
                     Vec4A<V> bt[kU];
 #pragma unroll
                     for (int u = 0; u < kU; ++u) bt[u] = reinterpret_cast<const Vec4A<V>*>(bsrc)[c[u]];
@@ -189,22 +185,20 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
                     for (int u = 0; u < kU; ++u) {
                         if (qb + u >= q1) break;
 #pragma unroll
-                        for (int m = 0; m <= D; ++m) t[((w[u] >> (8 * m)) & 0xffu) * R + rh] += bt[u].v[m];
+                        for (int m = 0; m <= D; ++m) t[((w[u] >> (8 * m)) & 0xffu) * R + r] += bt[u].v[m];
                     }
                 }
             }
-            if (hf == 0) {
 #pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    if constexpr (ABE) {
-                        s_ub[0][k][rh] = s_v(a.u1[i * D + k]);
-                        s_ub[NB - 1][k][rh] = s_v(a.u2[i * D + k]);
-                    } else {
-                        s_ub[0][k][rh] = a.ubar[i * D + k];
-                    }
+            for (int k = 0; k < D; ++k) {
+                if constexpr (ABE) {
+                    s_ub[0][k][r] = s_v(a.u1[i * D + k]);
+                    s_ub[NB - 1][k][r] = s_v(a.u2[i * D + k]);
+                } else {
+                    s_ub[0][k][r] = a.ubar[i * D + k];
                 }
-                s_dir[rh] = a.dir_index[i];
             }
+            s_dir[r] = a.dir_index[i];
         }
         __syncthreads();
         for (int32_t e = T.e0 + r; e < T.e1; e += kBlock) {
@@ -221,10 +215,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble(StepData<P> a, Consts<typen
             }
             V cb[NB];
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const size_t o = ((size_t)b * a.max_row + sl) * R + rr;
-                cb[b] = (s_t1[o] + s_t1[half_t1 + o]) + gdot[b] * inv_d2;
-            }
+            for (int b = 0; b < NB; ++b) cb[b] = s_t1[((size_t)b * a.max_row + sl) * R + rr] + gdot[b] * inv_d2;
             const V kv = a.K[e];
             // passive scalars: C(ubar), linear in the convecting velocity
             if (a.cbar) a.cbar[e] = ABE ? (V)1.5 * cb[0] - (V)0.5 * cb[NB - 1] : cb[0];
@@ -2248,8 +2239,8 @@ struct StepImplT final : StepImpl {
         const size_t cap = (size_t)std::max(1, m.tile_cap);
         const size_t cap_n = (size_t)std::max(1, m.tile_cap_n);
         // assembly and BiCGStab products: narrow tiles (their per-entry staging)
-        sm_asm = 2 * (size_t)m.max_row * kTileN * sizeof(V) + cap_n * D * sizeof(V);
-        sm_asm2 = 4 * (size_t)m.max_row * kTileN * sizeof(V) + cap_n * D * sizeof(V);
+        sm_asm = (size_t)m.max_row * kTileN * sizeof(V) + cap_n * D * sizeof(V);
+        sm_asm2 = 2 * (size_t)m.max_row * kTileN * sizeof(V) + cap_n * D * sizeof(V);
         sm_out_u = cap_n * D * sizeof(Acc);
         sm_out_u1 = cap_n * sizeof(Acc);
         sm_spmm = cap_n * D * sizeof(V);
