@@ -479,6 +479,7 @@ def run_ours(args, rank, world):
     upd_kernels = 3 + 2 * it_m if args.velocity_update == "consistent" else 1
     upd_kernels += args.scalars * (5 + 5 * it_c)
     n_asm = 2 if args.convection == "abe" else 3
+    n_asm += 1   # the tentative velocity u^I formed once per dof for the pressure right-hand side
     launches = int(round(args.steps * (ni * (n_asm + 2 * sw_u + 5 * it_u + p_kernels) + (ni - 1)
                                        + (5 if learned else 0) + upd_kernels)))
     run.close()

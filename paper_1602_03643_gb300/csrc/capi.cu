@@ -245,7 +245,7 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     }
     S->dir_index.upload(di.data(), n, s);
     S->g.alloc(sb * std::max<int64_t>(1, n_dir * D), s);
-    for (RBuf* b : {&S->u1, &S->u2, &S->du, &S->r0}) b->alloc(sb * n * D, s);
+    for (RBuf* b : {&S->u1, &S->u2, &S->du, &S->r0, &S->uI}) b->alloc(sb * n * D, s);
     for (RBuf* b : {&S->pstar, &S->x, &S->b, &S->phi, &S->phi_h1, &S->phi_h2}) b->alloc(sb * n, s);
     S->A.alloc(vb * m->nnz, s);
     S->dinvA.alloc(vb * n, s);

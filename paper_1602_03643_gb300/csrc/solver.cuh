@@ -61,6 +61,7 @@ struct StepData {
     // tentative system (V)
     V *A, *dinvA, *beta, *beta2;     // beta2: cell terms of u^{n-2} (explicit convection only)
     V* ubar;                          // [n][D] convecting velocity 1.5 u^{n-1} - 0.5 u^{n-2} (Eq. 22)
+    S* uI;                            // [n][D] tentative velocity u^{n-1} + Delta (pressure right-hand side)
     // BiCGStab work [n][D] (V)
     V *r, *rh, *p, *v, *s, *t, *ph, *sh, *dl;
     // CG work: gathered quads double-buffered by iteration parity; p; delta; x rounded
@@ -148,6 +149,7 @@ struct Solver {
     RBuf g, u1, u2, du, r0, pstar, x, b, phi, phi_h1, phi_h2;          // S
     RBuf A, dinvA, beta, beta2;                                        // V
     RBuf ubar;                                                         // V [n][D]
+    RBuf uI;                                                           // S [n][D]
     RBuf w[9];                                                         // V [n][D]
     RBuf pw[3];                                                        // V [n]
     RBuf pq[2];                                                        // CgQuad<V> [n]

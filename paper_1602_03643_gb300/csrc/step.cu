@@ -850,66 +850,122 @@ __global__ void __launch_bounds__(kBlock) k_bicg_correct(StepData<P> a, int k0) 
 // ================================================================ pressure
 // u^I = u^{n-1} + Delta rounded to the value type (for the divergence products).
 
-// b_phi_i = -(1/dt) sum_k sum_j dP^k_ij u_k,j^I (Sec. 5, algebraic pressure
-// equation); its mean is stored for the projection on sum_i b_i = 0, and the
-// pressure solve state is reset.
+// The mean of the right-hand side (for the projection on sum_i b_i = 0) and a
+// reset of the pressure solve's state (last block, thread 0).
+__device__ __forceinline__ void pressure_rhs_finish(KrylovState* st, double total, int64_t n) {
+    st->mean = total / (double)n;
+    const float mh = (float)st->mean;
+    st->mean_hi = mh;
+    st->mean_lo = (float)(st->mean - (double)mh);
+    for (int k = 0; k < 3; ++k) {
+        st->col_done[k] = k == 0 ? 0 : 1;
+        st->in_done[k] = 1;
+        st->it_total[k] = 0;
+    }
+    st->sweeps = 0;
+    st->it_in = 0;
+    st->status = OASIS_OK;
+    st->first = 1;
+}
+
+// u^I = u^{n-1} + Delta once per dof (float64 quality), for the pressure
+// right-hand side
 template <class P, int D>
-__global__ void __launch_bounds__(kBlock) k_pressure_rhs(StepData<P> a, Consts<typename P::V> k_) {
+__global__ void __launch_bounds__(kBlock) k_tentative_velocity(StepData<P> a) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.n * D; t += (int64_t)gridDim.x * blockDim.x)
+        a.uI[t] = s_add(a.u1[t], a.du[t]);
+}
+
+// S * S added lazily to an accumulator (the product's rounding error and the
+// cross terms kept, the high parts summed by an error-free two-sum, the low
+// parts in float; normalised once by lazy_norm): float64 exactly as before
+__device__ __forceinline__ void lazy_add_prod_s(double& acc, double x, double y) { acc = fma(x, y, acc); }
+__device__ __forceinline__ void lazy_add_prod_s(ff& acc, float2 x, float2 y) {
+    const float p = x.x * y.x;
+    float e = __fmaf_rn(x.x, y.x, -p);
+    e = __fmaf_rn(x.x, y.y, e);
+    e = __fmaf_rn(x.y, y.x, e);
+    const ff t = two_sum(acc.hi, p);
+    acc.hi = t.hi;
+    acc.lo += t.lo + e;
+}
+
+// The pressure right-hand side in row-split form (G lanes per row, U rows in
+// flight): b_phi_i = -(1/dt) sum_k sum_j dP^k_ij u_k,j^I with float-float dP^k
+// and u^I, each lane's products accumulated lazily, the group's lanes summed in
+// a float-float shuffle tree, then the projection's mean as before.
+template <class P, int D, int G, int U>
+__global__ void __launch_bounds__(kBlock) k_pressure_rhs_rows(StepData<P> a) {
     using S = typename P::S;
     using Acc = typename P::Acc;
-    extern __shared__ __align__(16) unsigned char dsm[];
-    Acc* s_prod = reinterpret_cast<Acc*>(dsm);
-    __shared__ int32_t s_rp[kTile + 1];
+    constexpr int RPW = 32 / G;
+    const int32_t* __restrict__ rp = a.rp;
+    const int32_t* __restrict__ col = a.col;
+    const S* __restrict__ Gout = a.Gout;
+    const S* __restrict__ uI = a.uI;
+    S* __restrict__ bo = a.b;
+    const S mrdt = s_of_double<S>(-1.0 / a.dt);
+    const int64_t nnz = a.nnz;
+    const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     Acc part[1];
     acc_zero(part[0]);
-    // b_phi is a small difference of large terms (u^I is nearly divergence-free),
-    // so it is formed with float64-quality dP^k and u^I = u^{n-1} + delta
-    // (float-float in the mixed path), accumulated in float-float
-    const S mrdt = s_of_double<S>(-1.0 / a.dt);
-    const int r = threadIdx.x;
-    for (int64_t tile = blockIdx.x; tile * kTile < a.n; tile += gridDim.x) {
-        const TileRange T = load_tile(tile, a.n, a.rp, s_rp);
-        tile_entries<8, Acc>(
-            T,
-            [&](int32_t e) {
-                const size_t j = (size_t)a.col[e] * D;
-                Acc acc;
-                acc_zero(acc);
+    for (int64_t base = w0 * RPW * U; base < a.n; base += nw * RPW * U) {
+        int64_t i[U];
+        int32_t q[U], e[U];
+        Acc acc[U];
 #pragma unroll
-                for (int k = 0; k < D; ++k)
-                    acc_add(acc, acc_of_s(s_mul_s(a.Gout[(size_t)k * a.nnz + e], s_add(a.u1[j + k], a.du[j + k]))));
-                return acc;
-            },
-            [&](int32_t e, const Acc& v) { s_prod[e - T.e0] = v; });
-        __syncthreads();
-        if (r < T.nr) {
-            const int32_t b0 = s_rp[r] - T.e0, b1 = s_rp[r + 1] - T.e0;
-            Acc acc;
-            acc_zero(acc);
-            for (int32_t q = b0; q < b1; ++q) acc_add(acc, s_prod[q]);
-            const S bi = s_mul_s(s_of_acc(acc), mrdt);
-            a.b[T.r0 + r] = bi;
-            acc_add(part[0], acc_of_s(bi));
+        for (int u = 0; u < U; ++u) {
+            i[u] = base + u * RPW + grp;
+            const bool ok = i[u] < a.n;
+            q[u] = ok ? rp[i[u]] + lg : 0;
+            e[u] = ok ? rp[i[u] + 1] : 0;
+            acc_zero(acc[u]);
         }
-        __syncthreads();
+        bool more = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) more |= q[u] < e[u];
+        while (more) {
+            int64_t j[U];
+            S gk[U][D], xk[U][D];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool has = q[u] < e[u];
+                j[u] = has ? (int64_t)col[q[u]] * D : 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) gk[u][k] = has ? Gout[(size_t)k * nnz + q[u]] : s_zero<S>();
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int k = 0; k < D; ++k) xk[u][k] = uI[j[u] + k];
+            more = false;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (q[u] < e[u]) {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) lazy_add_prod_s(acc[u], gk[u][k], xk[u][k]);
+                    q[u] += G;
+                }
+                more |= q[u] < e[u];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            acc[u] = lazy_norm(acc[u]);
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) acc_add(acc[u], acc_shfl(acc[u], o));
+            if (i[u] < a.n && lg == 0) {
+                const S bi = s_mul_s(s_of_acc(acc[u]), mrdt);
+                bo[i[u]] = bi;
+                acc_add(part[0], acc_of_s(bi));
+            }
+        }
     }
     double tot[1];
-    if (grid_sum<1, Acc>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
-        KrylovState* st = a.stp;
-        st->mean = tot[0] / (double)a.n;
-        const float mh = (float)st->mean;
-        st->mean_hi = mh;
-        st->mean_lo = (float)(st->mean - (double)mh);
-        for (int k = 0; k < 3; ++k) {
-            st->col_done[k] = k == 0 ? 0 : 1;
-            st->in_done[k] = 1;
-            st->it_total[k] = 0;
-        }
-        st->sweeps = 0;
-        st->it_in = 0;
-        st->status = OASIS_OK;
-        st->first = 1;
-    }
+    if (grid_sum<1, Acc>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0)
+        pressure_rhs_finish(a.stp, tot[0], a.n);
 }
 
 // mean of the pressure right-hand side (of_p = false) or of p = p* + phi
@@ -1056,6 +1112,11 @@ __global__ void __launch_bounds__(kBlock) k_pcg_outer_sell(StepData<P> a, Ctl ct
     Acc part[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) acc_zero(part[k]);
+    // restrict-qualified locals: the stores of one slice do not hold back the
+    // next slice's loads
+    const S* __restrict__ Kouts = a.Kouts;
+    const S* __restrict__ xs = a.x;
+    const int32_t* __restrict__ scol = a.sell_col;
     sell_slices(a, [&](int64_t i, int len, int64_t base, int) {
         Acc kx;
         acc_zero(kx);
@@ -1068,9 +1129,9 @@ __global__ void __launch_bounds__(kBlock) k_pcg_outer_sell(StepData<P> a, Ctl ct
             for (int u = 0; u < C; ++u) {
                 const int64_t q = base + 32 * (int64_t)(k + u);
                 const bool ok = k + u < len;
-                const int32_t j = ok ? a.sell_col[q] : 0;
-                kv[u] = ok ? a.Kouts[q] : s_zero<S>();
-                xv[u] = a.x[j];
+                const int32_t j = ok ? scol[q] : 0;
+                kv[u] = ok ? Kouts[q] : s_zero<S>();
+                xv[u] = xs[j];
             }
 #pragma unroll
             for (int u = 0; u < C; ++u)
@@ -1553,6 +1614,16 @@ __global__ void __launch_bounds__(kBlock, MINB) k_amg_cg_spmv(StepData<P> a, Ctl
     using V = typename P::V;
     if (a.stp->col_done[0] || a.stp->in_done[0]) return;
     V part[3] = {};
+    // the arrays through restrict-qualified locals: w is stored between slices,
+    // and without them the next slice's loads could not move above that store
+    // nor use the read-only path
+    const V* __restrict__ Ks = a.Ks;
+    const V* __restrict__ au = a.au;
+    const V* __restrict__ ar = a.ar;
+    V* __restrict__ aw = a.aw;
+    const int16_t* __restrict__ dcol = a.sell_dcol;
+    const int32_t* __restrict__ scol = a.sell_col;
+    const int32_t n32 = (int32_t)a.n;
     sell_slices(a, [&](int64_t i, int len, int64_t base, int) {
         const int32_t row = (int32_t)i;
         V w = 0;
@@ -1563,19 +1634,29 @@ __global__ void __launch_bounds__(kBlock, MINB) k_amg_cg_spmv(StepData<P> a, Ctl
             for (int u = 0; u < C; ++u) {
                 const int64_t q = base + 32 * (int64_t)(k + u);
                 const bool ok = k + u < len;
-                j[u] = ok ? sell_j<D16>(a, q, row) : 0;
-                kv[u] = ok ? a.Ks[q] : V(0);
+                int32_t jj = 0;
+                if (ok) {
+                    if constexpr (D16) {
+                        jj = row + (int32_t)dcol[q];
+                        jj = jj < 0 ? jj + n32 : jj;
+                        jj = jj >= n32 ? jj - n32 : jj;
+                    } else {
+                        jj = scol[q];
+                    }
+                }
+                j[u] = jj;
+                kv[u] = ok ? Ks[q] : V(0);
             }
             V g[C];
 #pragma unroll
-            for (int u = 0; u < C; ++u) g[u] = a.au[j[u]];
+            for (int u = 0; u < C; ++u) g[u] = au[j[u]];
 #pragma unroll
             for (int u = 0; u < C; ++u)
                 if (k + u < len) w += kv[u] * g[u];
         }
         if (i < a.n) {
-            a.aw[i] = w;
-            const V u = a.au[i], r = a.ar[i];
+            aw[i] = w;
+            const V u = au[i], r = ar[i];
             part[0] += r * u;
             part[1] += w * u;
             part[2] += r * r;
@@ -2135,7 +2216,7 @@ struct StepImplT final : StepImpl {
     StepData<P> a{};
     Consts<V> k_{};
     int64_t tiles = 0, tiles_n = 0;
-    size_t sm_asm = 0, sm_asm2 = 0, sm_out_u = 0, sm_out_u1 = 0, sm_spmm = 0, sm_spmm1 = 0, sm_outp = 0, sm_v1 = 0, sm_vd = 0;
+    size_t sm_asm = 0, sm_asm2 = 0, sm_out_u = 0, sm_out_u1 = 0, sm_spmm = 0, sm_spmm1 = 0, sm_v1 = 0, sm_vd = 0;
     int g_asm = 1, g_asm2 = 1, g_out_u = 1, g_out_u1 = 1, g_spmm0 = 1, g_spmm1 = 1, g_spmm0_1 = 1, g_spmm1_1 = 1,
         g_rhs = 1, g_upd = 1, g_upd_c = 1, g_mspmv = 1, g_out_s = 1, g_spmm0_s = 1, g_spmm1_s = 1, g_sasm = 1;
     int ge_n = 1, ge_nd = 1, ge_c = 1, ge_red = 1;
@@ -2196,6 +2277,7 @@ struct StepImplT final : StepImpl {
         a.beta = Sv.beta.as<V>();
         a.beta2 = Sv.beta2.as<V>();
         a.ubar = Sv.ubar.as<V>();
+        a.uI = Sv.uI.as<S>();
         V** w[9] = {&a.r, &a.rh, &a.p, &a.v, &a.s, &a.t, &a.ph, &a.sh, &a.dl};
         for (int q = 0; q < 9; ++q) *w[q] = Sv.w[q].as<V>();
         V** pw[3] = {&a.pp, &a.pdl, &a.xv};
@@ -2245,7 +2327,6 @@ struct StepImplT final : StepImpl {
         sm_out_u1 = cap_n * sizeof(Acc);
         sm_spmm = cap_n * D * sizeof(V);
         sm_spmm1 = cap_n * sizeof(V);
-        sm_outp = cap * sizeof(Acc);
         sm_v1 = cap * sizeof(V);
         sm_vd = cap * D * sizeof(V);
         g_asm = tile_grid(k_assemble<P, D, false, kTileN>, sm_asm, tiles_n);
@@ -2258,7 +2339,13 @@ struct StepImplT final : StepImpl {
         g_spmm1_1 = tile_grid(k_bicg_spmm<P, D, 1, 1, kTileN>, sm_spmm1, tiles_n);
         g_sell = (int)std::max<int64_t>(1, ((m.n + 31) / 32 + kBlock / 32 - 1) / (kBlock / 32));
         g_sellr = (int)std::min<int64_t>(g_sell, (int64_t)num_sms() * 8);
-        g_rhs = tile_grid(k_pressure_rhs<P, D>, sm_outp, tiles);
+        {
+            int per_sm = 0;
+            OASIS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pressure_rhs_rows<P, D, 4, 2>, kBlock, 0));
+            const int64_t per_block = (int64_t)kBlock / 4 * 2;
+            g_rhs = (int)std::max<int64_t>(
+                1, std::min<int64_t>((m.n + per_block - 1) / per_block, (int64_t)std::max(per_sm, 1) * num_sms()));
+        }
         g_upd = tile_grid(k_update<P, D, false>, sm_vd, tiles);
         g_upd_c = tile_grid(k_update<P, D, true>, 0, tiles);
         g_mspmv = tile_grid(k_mass_spmv<P, D>, sm_vd, tiles);
@@ -2418,7 +2505,8 @@ struct StepImplT final : StepImpl {
 
     void pressure_solve(cudaStream_t s, bool graph, int inner) override {
         const int pr = Sv.prof_begin(s, OASIS_PROF_PRESSURE_RHS);
-        k_pressure_rhs<P, D><<<g_rhs, kBlock, sm_outp, s>>>(a, k_);
+        k_tentative_velocity<P, D><<<ge_nd, kBlock, 0, s>>>(a);
+        k_pressure_rhs_rows<P, D, 4, 2><<<g_rhs, kBlock, 0, s>>>(a);
         Sv.prof_end(s, pr);
         // repetitions after the first start from zero: their increment is small and
         // unrelated to the previous step's correction
