@@ -76,8 +76,7 @@ def workload_config(name, pb, precision, gpu=True):
 # per workload, with the profile summary it comes from; valid for the kernels as
 # they stand (an entry is removed when its kernel changes)
 _S112 = "profiles/dram_traffic_products_stress112_rcm.md (stress112_rcm capture, scaled by algorithmic bytes)"
-MEASURED_TRAFFIC = {("stress128_rcm", "amg_fine"): (222.0e6, _S112),
-                    ("stress128_rcm", "pcg_spmv"): (215.0e6, _S112)}
+MEASURED_TRAFFIC = {("stress128_rcm", "pcg_spmv"): (215.0e6, _S112)}
 
 
 def family_bytes(pb, nnz, args, tuning, amg):
@@ -89,12 +88,13 @@ def family_bytes(pb, nnz, args, tuning, amg):
                    w written, slice pointers/lengths
       bicg_spmm    d-RHS product of the BiCGStab: A values + columns, row pointers,
                    x gathered, y written, the dot operand read
-      amg_fine     finest-level smoothing sweep (pre or post, SELL-32): K values +
-                   columns, 4 vectors of N, slice pointers/lengths
-      amg_transfer restriction/prolongation, averaged over the 2(L-1) launches of a
-                   V-cycle: per level 16 nnz(P) + 16 n_l + 12 n_(l+1)
-      amg_coarse   coarser-level sweeps and the dense coarsest product, averaged over
-                   their 2(L-2)+1 launches: per sweep 8 nnz_l + 20 n_l; dense 4 nc ld + 8 nc
+      amg_fine     finest-level smoothing sweep (pre or post, SELL-32): K values as
+                   bfloat16 + columns, 4 vectors of N, slice pointers/lengths
+      amg_transfer restriction/prolongation (bfloat16 values), averaged over the 2(L-1)
+                   launches of a V-cycle: per level 12 nnz(P) + 16 n_l + 12 n_(l+1)
+      amg_coarse   coarser-level sweeps (bfloat16 values) and the dense coarsest product,
+                   averaged over their 2(L-2)+1 launches: per sweep 6 nnz_l + 20 n_l;
+                   dense 4 nc ld + 8 nc
       bicg_vec     BiCGStab vector kernels, averaged over dir (64 N), s (52 N), and
                    the solution/residual update with its dots (96 N), for D = 3
       assemble     convecting velocity per dof (u^{n-1}, u^{n-2} read, ubar written: 60 N),
@@ -114,19 +114,20 @@ def family_bytes(pb, nnz, args, tuning, amg):
         cb = 2 if have16 else 4
         out["pcg_spmv"] = ("k_amg_cg_spmv<Mixed> (multigrid CG: w = K u on SELL-32 + 3 dots)",
                            (4 + cb) * Z + 12 * N + 8 * n_slices, f"(4+{cb}) Z + 12 N + 8 N/32")
-        out["amg_fine"] = ("k_amg_fine<float> (finest-level damped-Jacobi sweep on SELL-32)",
-                           (4 + cb) * Z + 16 * N + 8 * n_slices, f"(4+{cb}) Z + 16 N + 8 N/32")
+        out["amg_fine"] = ("k_amg_fine<float> (finest-level damped-Jacobi sweep on SELL-32, bfloat16 K)",
+                           (2 + cb) * Z + 16 * N + 8 * n_slices, f"(2+{cb}) Z + 16 N + 8 N/32")
         rows, nz, pn = amg["rows"], amg["nnz"], amg["p_nnz"]
         L = amg["levels"]
         if pn:
-            tb = sum(16 * pn[l] + 16 * rows[l] + 12 * rows[l + 1] for l in range(len(pn)))
-            out["amg_transfer"] = ("k_amg_restrict / k_amg_prolong (CSR, every level)", tb / (2 * len(pn)),
-                                   "per V-cycle sum_l 16 nnz(P_l) + 16 n_l + 12 n_(l+1), over 2(L-1) launches")
+            tb = sum(12 * pn[l] + 16 * rows[l] + 12 * rows[l + 1] for l in range(len(pn)))
+            out["amg_transfer"] = ("k_amg_restrict / k_amg_prolong (CSR, bfloat16 values, every level)",
+                                   tb / (2 * len(pn)),
+                                   "per V-cycle sum_l 12 nnz(P_l) + 16 n_l + 12 n_(l+1), over 2(L-1) launches")
         nc = rows[L - 1]
         ld = (nc + 3) // 4 * 4
-        cbytes = sum(2 * (8 * nz[l] + 20 * rows[l]) for l in range(1, L - 1)) + 4 * nc * ld + 8 * nc
-        out["amg_coarse"] = ("k_amg_pre / k_amg_post (CSR, levels >= 1) and k_amg_dense",
-                             cbytes / (2 * (L - 2) + 1), "per V-cycle sum_l 2 (8 nnz_l + 20 n_l) + 4 nc ld + 8 nc, "
+        cbytes = sum(2 * (6 * nz[l] + 20 * rows[l]) for l in range(1, L - 1)) + 4 * nc * ld + 8 * nc
+        out["amg_coarse"] = ("k_amg_pre / k_amg_post (CSR, bfloat16 values, levels >= 1) and k_amg_dense",
+                             cbytes / (2 * (L - 2) + 1), "per V-cycle sum_l 2 (6 nnz_l + 20 n_l) + 4 nc ld + 8 nc, "
                                                          "over 2(L-2)+1 launches")
     out["bicg_spmm"] = (f"k_bicg_spmm<Mixed,{D},{D}> (tentative BiCGStab: {D}-RHS product A x + dots, row tiles)",
                         8 * Z + 4 * (N + 1) + 12 * D * N, f"8 Z + 4 N + 12 D N")

@@ -30,34 +30,41 @@ struct AmgLevelDev {
     int64_t n = 0, nnz = 0;
     // operator of this level (level 0 points at the mesh's K)
     const int32_t *rp = nullptr, *ci = nullptr;
-    const float* a32 = nullptr;
     const double* a64 = nullptr;
+    const uint16_t* a16 = nullptr;     // bfloat16 bit patterns (the float32 cycle; null on level 0,
+                                       // whose sweeps read the SELL-32 view)
     DBuf<int32_t> own_rp, own_ci;
-    DBuf<float> own_a32;
     DBuf<double> own_a64;
+    DBuf<uint16_t> own_a16;
     DBuf<float> d32;                   // 1 / a_ii
     DBuf<double> d64;
     double omega = 0.0;                // Jacobi weight of the smoother
     int g_a = 4, g_r = 8, g_p = 4;     // lanes per row for A, R = P^T and P (from mean row lengths)
     // prolongation to this level from the next coarser one, and its transpose
     DBuf<int32_t> p_rp, p_ci, r_rp, r_ci;
-    DBuf<float> p32, r32;
     DBuf<double> p64, r64;
+    DBuf<uint16_t> p16, r16;
 };
 
 // SELL-32 view of the finest operator (the mesh's K): the fine-level smoothers
 // read it with one lane per row, coalesced column/value loads, and 16-bit column
-// offsets where the mesh has them.
+// offsets where the mesh has them.  The float32 cycle reads its values rounded
+// to bfloat16 (v16, the bit patterns), as it does every level's operator and
+// transfer: a preconditioner needs no more than a few digits of them, the
+// rounded operators are still symmetric (equal entries round alike) and the
+// rounded restriction is still the transpose of the rounded prolongation, so
+// the cycle stays a symmetric preconditioner.
 struct AmgSellView {
     int64_t n = 0, n_slices = 0;
     const int32_t *ptr = nullptr, *len = nullptr, *col = nullptr;
     const int16_t* dcol = nullptr;
-    const float* v32 = nullptr;
     const double* v64 = nullptr;
+    const uint16_t* v16 = nullptr;
 };
 
 struct AmgHierarchy {
     AmgSellView fine;
+    DBuf<uint16_t> fine16;                           // storage of fine.v16
     std::vector<std::unique_ptr<AmgLevelDev>> lv;   // lv[0] fine ... lv[L-1] coarsest
     int64_t nc = 0;                                  // size of the dense coarsest level
     int64_t ld = 0;                                  // its row stride: nc rounded up to 4

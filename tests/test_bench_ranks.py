@@ -74,11 +74,11 @@ def test_family_bytes_model_on_a_small_mesh():
     f = bench.family_bytes(pb, Z, None, tuning, amg)
     ns = (N + 31) // 32
     assert f["pcg_spmv"][1] == 6 * Z + 12 * N + 8 * ns
-    assert f["amg_fine"][1] == 6 * Z + 16 * N + 8 * ns
+    assert f["amg_fine"][1] == 4 * Z + 16 * N + 8 * ns
     assert f["bicg_spmm"][1] == 8 * Z + 4 * (N + 1) + 36 * N
-    want_t = (16 * 300 + 16 * N + 12 * 20) + (16 * 40 + 16 * 20 + 12 * 3)
+    want_t = (12 * 300 + 16 * N + 12 * 20) + (12 * 40 + 16 * 20 + 12 * 3)
     assert abs(f["amg_transfer"][1] - want_t / 4) < 1e-9
-    want_c = 2 * (8 * 200 + 20 * 20) + 4 * 3 * 4 + 8 * 3
+    want_c = 2 * (6 * 200 + 20 * 20) + 4 * 3 * 4 + 8 * 3
     assert abs(f["amg_coarse"][1] - want_c / 3) < 1e-9
     assert f["assemble"][1] == 128 * T + 28 * Z + 204 * N
     assert f["outer"][1] == 10 * Z + 84 * N

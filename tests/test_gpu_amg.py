@@ -77,6 +77,39 @@ def test_vcycle_symmetric_positive(name):
         run.close()
 
 
+@pytest.mark.parametrize("name", ["stress_10_random", "channel_8x7x6"])
+def test_float32_vcycle_symmetric_and_close_to_float64(name):
+    """The float32 cycle (its finest-level smoother reading K rounded to
+    bfloat16) is symmetric and positive to float32 rounding, and within the
+    smoother's few digits of the float64 cycle."""
+    import torch
+    c = capi()
+    pb = PROBLEMS[name]()
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=pb.mesh.n_dofs)
+    y = rng.normal(size=pb.mesh.n_dofs)
+    x -= x.mean()
+    y -= y.mean()
+    out = {}
+    for prec, dt in ((c.OASIS_FP64, torch.float64), (c.OASIS_MIXED, torch.float32)):
+        run = _run(pb, prec, c.OASIS_PC_AMG)
+        try:
+            X, Y = torch.from_numpy(x).to(dt).cuda(), torch.from_numpy(y).to(dt).cuda()
+            U, W = torch.empty_like(X), torch.empty_like(Y)
+            c.oasis_amg_apply(run.solver, X, U)
+            c.oasis_amg_apply(run.solver, Y, W)
+            out[prec] = (U.double().cpu().numpy(), W.double().cpu().numpy())
+        finally:
+            run.close()
+    u, w = out[c.OASIS_MIXED]
+    assert abs(x @ w - y @ u) <= 2e-6 * np.sqrt((x @ u) * (y @ w))
+    assert x @ u > 0 and y @ w > 0
+    u64, w64 = out[c.OASIS_FP64]
+    # bfloat16 keeps 8 significant bits (relative rounding 2^-9) of each entry
+    assert 1e-9 < relerr(u, u64) <= 2e-2
+    assert 1e-9 < relerr(w, w64) <= 2e-2
+
+
 @pytest.mark.parametrize("name", list(PROBLEMS))
 def test_amg_steps_match_oracle_fp64(name):
     c = capi()
