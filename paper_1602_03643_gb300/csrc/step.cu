@@ -1686,8 +1686,10 @@ __global__ void __launch_bounds__(kBlock, MINB) k_amg_cg_spmv(StepData<P> a, Ctl
 
 // Candidate shapes of the multigrid CG product: entries per lane whose column
 // and value loads are issued together (C) and the blocks per SM the registers
-// are sized for.  The grid (one warp per slice) and every sum's order are the
-// same for all shapes: same bits.
+// are sized for.  Every shape adds a row's products in entry order (same w);
+// each runs one resident wave of its own, so on large meshes the dot products'
+// partials can fall into other blocks and differ in the last bits, while every
+// mesh small enough for one grid of a warp per slice gets the same bits.
 template <class P>
 struct AmgVariant {
     void (*fn16)(StepData<P>, Ctl);
@@ -2221,7 +2223,11 @@ struct StepImplT final : StepImpl {
         g_rhs = 1, g_upd = 1, g_upd_c = 1, g_mspmv = 1, g_out_s = 1, g_spmm0_s = 1, g_spmm1_s = 1, g_sasm = 1;
     int ge_n = 1, ge_nd = 1, ge_c = 1, ge_red = 1;
     int g_sell = 1;
-    int g_sellr = 1;     // grid-stride SELL kernels ending in a reduction: one resident wave
+    // grid-stride SELL kernels ending in a reduction: one resident wave of each
+    // kernel (its registers set the blocks per SM; a grid of 8 blocks per SM for a
+    // kernel that fits 5 or 6 ran its latency-bound second wave nearly empty)
+    int g_outer_sell = 1, g_judge = 1, g_cg_first[2] = {1, 1};
+    int amg_grid_v[kAmgVariants][2] = {};             // per shape: 16-bit, 32-bit columns
     int iter_v = 0;                                   // chosen CG iteration shape
     int amg_v = 0;                                    // chosen multigrid CG product shape
     int bicg_v = 0;                                   // chosen d-RHS BiCGStab product shape
@@ -2233,6 +2239,14 @@ struct StepImplT final : StepImpl {
     int it_grid[OASIS_MAX_VARIANTS] = {0}, it_block[OASIS_MAX_VARIANTS] = {0};
     size_t it_smem[OASIS_MAX_VARIANTS] = {0};
 
+
+    // one resident wave of a grid-stride SELL kernel (kBlock threads, no shared memory)
+    template <class K>
+    int sell_wave(K kernel) const {
+        int per_sm = 0;
+        OASIS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0));
+        return (int)std::max<int64_t>(1, std::min<int64_t>(g_sell, (int64_t)std::max(per_sm, 1) * num_sms()));
+    }
 
     template <class T>
     static T* mat(const DBuf<double>& d, const DBuf<float>& f) {
@@ -2338,7 +2352,14 @@ struct StepImplT final : StepImpl {
         g_spmm0_1 = tile_grid(k_bicg_spmm<P, D, 1, 0, kTileN>, sm_spmm1, tiles_n);
         g_spmm1_1 = tile_grid(k_bicg_spmm<P, D, 1, 1, kTileN>, sm_spmm1, tiles_n);
         g_sell = (int)std::max<int64_t>(1, ((m.n + 31) / 32 + kBlock / 32 - 1) / (kBlock / 32));
-        g_sellr = (int)std::min<int64_t>(g_sell, (int64_t)num_sms() * 8);
+        g_outer_sell = sell_wave(k_pcg_outer_sell<P>);
+        g_judge = sell_wave(k_guess_judge<P>);
+        g_cg_first[0] = sell_wave(k_amg_cg_spmv<P, true, true>);
+        g_cg_first[1] = sell_wave(k_amg_cg_spmv<P, true, false>);
+        for (int v = 0; v < kAmgVariants; ++v) {
+            amg_grid_v[v][0] = sell_wave(amg_variant_table<P>()[v].fn16);
+            amg_grid_v[v][1] = sell_wave(amg_variant_table<P>()[v].fn32);
+        }
         {
             int per_sm = 0;
             OASIS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pressure_rhs_rows<P, D, 4, 2>, kBlock, 0));
@@ -2520,7 +2541,7 @@ struct StepImplT final : StepImpl {
         }
         if (learned) {
             net_forward(*Sv.net, a.feat, a.gy, s);
-            k_guess_judge<P><<<g_sellr, kBlock, 0, s>>>(a);
+            k_guess_judge<P><<<g_judge, kBlock, 0, s>>>(a);
             OASIS_CUDA(cudaGetLastError());
             mode = OASIS_GUESS_LEARNED;
         }
@@ -2543,12 +2564,12 @@ struct StepImplT final : StepImpl {
                 [&](cudaStream_t ss, const Loop& lp) {
                     const Ctl c = ctl_p(lp);
                     const int po = Sv.prof_begin(ss, OASIS_PROF_OUTER);
-                    k_pcg_outer_sell<P><<<g_sellr, kBlock, 0, ss>>>(a, c);
+                    k_pcg_outer_sell<P><<<g_outer_sell, kBlock, 0, ss>>>(a, c);
                     Sv.prof_end(ss, po);
                     k_amg_cg_start<P><<<ge_n, kBlock, 0, ss>>>(a);
                     vcycle(ss);
-                    if (a.sell_dcol) k_amg_cg_spmv<P, true, true><<<g_sellr, kBlock, 0, ss>>>(a, c);
-                    else k_amg_cg_spmv<P, true, false><<<g_sellr, kBlock, 0, ss>>>(a, c);
+                    if (a.sell_dcol) k_amg_cg_spmv<P, true, true><<<g_cg_first[0], kBlock, 0, ss>>>(a, c);
+                    else k_amg_cg_spmv<P, true, false><<<g_cg_first[1], kBlock, 0, ss>>>(a, c);
                     OASIS_CUDA(cudaGetLastError());
                 },
                 [&](cudaStream_t ss, const Loop& lp) {
@@ -2559,7 +2580,7 @@ struct StepImplT final : StepImpl {
                     vcycle(ss);
                     const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
                     const AmgVariant<P>& av = amg_variant_table<P>()[amg_v];
-                    (a.sell_dcol ? av.fn16 : av.fn32)<<<g_sellr, kBlock, 0, ss>>>(a, c);
+                    (a.sell_dcol ? av.fn16 : av.fn32)<<<amg_grid_v[amg_v][a.sell_dcol ? 0 : 1], kBlock, 0, ss>>>(a, c);
                     Sv.prof_end(ss, pq);
                     OASIS_CUDA(cudaGetLastError());
                 },
@@ -2575,7 +2596,7 @@ struct StepImplT final : StepImpl {
             [&](cudaStream_t ss, const Loop& lp) {
                 const Ctl c = ctl_p(lp);
                 const int po = Sv.prof_begin(ss, OASIS_PROF_OUTER);
-                k_pcg_outer_sell<P><<<g_sellr, kBlock, 0, ss>>>(a, c);
+                k_pcg_outer_sell<P><<<g_outer_sell, kBlock, 0, ss>>>(a, c);
                 Sv.prof_end(ss, po);
                 const int pu = Sv.prof_begin(ss, OASIS_PROF_PCG_UPDATE);
                 k_pcg_init_sell<P><<<g_sell, kBlock, 0, ss>>>(a, c);
@@ -2731,7 +2752,7 @@ struct StepImplT final : StepImpl {
             for (int r = 0; r < kWarm + kTimed; ++r) {
                 OASIS_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(KrylovState), s));
                 OASIS_CUDA(cudaEventRecord(e0, s));
-                (a.sell_dcol ? t[v].fn16 : t[v].fn32)<<<g_sellr, kBlock, 0, s>>>(d, c);
+                (a.sell_dcol ? t[v].fn16 : t[v].fn32)<<<amg_grid_v[v][a.sell_dcol ? 0 : 1], kBlock, 0, s>>>(d, c);
                 OASIS_CUDA(cudaGetLastError());
                 OASIS_CUDA(cudaEventRecord(e1, s));
                 OASIS_CUDA(cudaEventSynchronize(e1));
