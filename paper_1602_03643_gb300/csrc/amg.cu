@@ -352,6 +352,56 @@ __global__ void k_round_bf16(int64_t n, const float* __restrict__ in, uint16_t* 
         out[i] = __bfloat16_as_ushort(__float2bfloat16_rn(in[i]));
 }
 
+// Pair-packed copy of the finest level's bfloat16 values and 16-bit column
+// offsets (layout in amg.cuh).  One thread per (slice, lane); the padding entry
+// of an odd-length slice takes value 0 and the lane's previous offset, so its
+// gathered operand is a valid row.
+__global__ void k_pack_pairs(int64_t n_slices, const int32_t* __restrict__ ptr, const int32_t* __restrict__ len,
+                             const int32_t* __restrict__ ptr2, const uint16_t* __restrict__ v16,
+                             const int16_t* __restrict__ dcol, uint16_t* __restrict__ vp, uint16_t* __restrict__ cp) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_slices * 32;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sl = t >> 5;
+        const int l = (int)(t & 31), ln = len[sl], lp = (ln + 1) & ~1;
+        uint16_t c = 0;
+        for (int k = 0; k < lp; ++k) {
+            uint16_t v = 0;
+            if (k < ln) {
+                const int64_t q = (int64_t)ptr[sl] + 32 * (int64_t)k + l;
+                v = v16[q];
+                c = (uint16_t)dcol[q];
+            }
+            const int64_t o = (int64_t)ptr2[sl] + 64 * (int64_t)(k >> 1) + 2 * l + (k & 1);
+            vp[o] = v;
+            cp[o] = c;
+        }
+    }
+}
+
+void pack_pairs(AmgHierarchy& h, const Mesh& m, cudaStream_t s) {
+    const int64_t ns = h.fine.n_slices;
+    std::vector<int32_t> len(ns), ptr2(ns);
+    OASIS_CUDA(cudaMemcpyAsync(len.data(), m.sell_len.p, ns * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    OASIS_CUDA(cudaStreamSynchronize(s));
+    int64_t total = 0;
+    for (int64_t sl = 0; sl < ns; ++sl) {
+        ptr2[sl] = (int32_t)total;
+        total += 32 * (int64_t)((len[sl] + 1) & ~1);
+        OASIS_CHECK(total < INT32_MAX, OASIS_EINVAL, "multigrid: finest level too large for int32 positions");
+    }
+    upload_vec(h.fine_ptr2, ptr2, s);
+    h.fine_vp.alloc((size_t)std::max<int64_t>(total / 2, 1));
+    h.fine_cp.alloc((size_t)std::max<int64_t>(total / 2, 1));
+    k_pack_pairs<<<(int)std::max<int64_t>(1, std::min<int64_t>((ns * 32 + kBlock - 1) / kBlock, 4096)), kBlock, 0, s>>>(
+        ns, m.sell_ptr.p, m.sell_len.p, h.fine_ptr2.p, h.fine16.p, m.sell_dcol.p,
+        reinterpret_cast<uint16_t*>(h.fine_vp.p), reinterpret_cast<uint16_t*>(h.fine_cp.p));
+    OASIS_CUDA(cudaGetLastError());
+    OASIS_CUDA(cudaStreamSynchronize(s));
+    h.fine.ptr2 = h.fine_ptr2.p;
+    h.fine.vp = h.fine_vp.p;
+    h.fine.cp = h.fine_cp.p;
+}
+
 }  // namespace
 
 void amg_build(Mesh& m, cudaStream_t s) {
@@ -392,6 +442,7 @@ void amg_build(Mesh& m, cudaStream_t s) {
                 m.n_sell, m.K32s.p, h->fine16.p);
             OASIS_CUDA(cudaGetLastError());
             h->fine.v16 = h->fine16.p;
+            if (m.sell_dcol.p) pack_pairs(*h, m, s);
             L->rp = m.row_ptr.p;
             L->ci = m.col.p;
             L->a64 = m.K64.p;
@@ -687,6 +738,65 @@ __global__ void __launch_bounds__(kBlock) k_amg_fine(AmgSellView F, const AV* __
     }
 }
 
+// The float32 sweep on the pair-packed copy: per round C2 words of values and
+// C2 of offsets (2 C2 entries) are loaded, then their 2 C2 gathers; products
+// are added in entry order, as in k_amg_fine (same bits: the padding entry
+// adds 0 times a valid operand).
+constexpr int kFinePairWords = 4;
+template <bool PRE, int C2>
+__global__ void __launch_bounds__(kBlock) k_amg_fine_pairs(AmgSellView F, const float* __restrict__ d, float w,
+                                                           const float* __restrict__ r, const float* __restrict__ x,
+                                                           float* __restrict__ out, float* __restrict__ res,
+                                                           const KrylovState* st) {
+    if (amg_done(st)) return;
+    const uint32_t* __restrict__ vp = F.vp;
+    const uint32_t* __restrict__ cp = F.cp;
+    const int32_t n32 = (int32_t)F.n;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = w0; sl < F.n_slices; sl += nw) {
+        const int64_t i = sl * 32 + lane;
+        const int32_t row = (int32_t)i;
+        const int words = (F.len[sl] + 1) >> 1;
+        const int64_t base = (int64_t)(F.ptr2[sl] >> 1) + lane;
+        float sum = 0.f;
+        for (int k = 0; k < words; k += C2) {
+            uint32_t vw[C2], cw[C2];
+#pragma unroll
+            for (int u = 0; u < C2; ++u) {
+                const int64_t q = base + 32 * (int64_t)(k + u);
+                const bool ok = k + u < words;
+                vw[u] = ok ? vp[q] : 0u;
+                cw[u] = ok ? cp[q] : 0u;
+            }
+            float g[2 * C2];
+#pragma unroll
+            for (int e = 0; e < 2 * C2; ++e) {
+                const uint32_t half = (e & 1) ? (cw[e >> 1] >> 16) : (cw[e >> 1] & 0xFFFFu);
+                int32_t j = row + (int32_t)(int16_t)half;
+                j = j < 0 ? j + n32 : j;
+                j = j >= n32 ? j - n32 : j;
+                g[e] = PRE ? w * d[j] * r[j] : x[j];
+            }
+#pragma unroll
+            for (int u = 0; u < C2; ++u)
+                if (k + u < words) {
+                    sum += __uint_as_float(vw[u] << 16) * g[2 * u];
+                    sum += __uint_as_float(vw[u] & 0xFFFF0000u) * g[2 * u + 1];
+                }
+        }
+        if (i < F.n) {
+            if constexpr (PRE) {
+                res[i] = r[i] - sum;
+                out[i] = w * d[i] * r[i];
+            } else {
+                out[i] = x[i] + w * d[i] * (r[i] - sum);
+            }
+        }
+    }
+}
+
 // coarsest level: x = inv r with inv dense and row-major, leading dimension ld
 // (a multiple of 4, zero-padded) and r zero-padded to ld; one block of 128
 // threads per row, 16-byte loads (float4 / double2), the block's sum in a fixed
@@ -764,6 +874,14 @@ void launch_fine(const AmgSellView& F, const V* d, V w, const V* r, const V* x, 
                  const KrylovState* st, cudaStream_t s) {
     using AV = StoredT<V>;
     const AV* av = stored<V>(F.v16, F.v64);
+    if constexpr (sizeof(V) == 4) {
+        if (F.vp) {
+            constexpr int C2 = kFinePairWords;
+            k_amg_fine_pairs<PRE, C2><<<fine_grid(F, (const void*)k_amg_fine_pairs<PRE, C2>), kBlock, 0, s>>>(
+                F, d, w, r, x, out, res, st);
+            return;
+        }
+    }
     if (F.dcol)
         k_amg_fine<V, AV, true, PRE><<<fine_grid(F, (const void*)k_amg_fine<V, AV, true, PRE>), kBlock, 0, s>>>(
             F, av, d, w, r, x, out, res, st);

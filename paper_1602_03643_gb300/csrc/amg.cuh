@@ -54,17 +54,26 @@ struct AmgLevelDev {
 // rounded operators are still symmetric (equal entries round alike) and the
 // rounded restriction is still the transpose of the rounded prolongation, so
 // the cycle stays a symmetric preconditioner.
+//
+// Where the 16-bit offsets exist, the float32 cycle reads a pair-packed copy:
+// a slice's rows padded to an even length, entries k and k+1 of lane l in one
+// 32-bit word at word ptr2[s] / 2 + 32 (k / 2) + l (vp: two bfloat16 values,
+// low half entry k; cp: two column offsets), so one load brings two entries.
 struct AmgSellView {
     int64_t n = 0, n_slices = 0;
     const int32_t *ptr = nullptr, *len = nullptr, *col = nullptr;
     const int16_t* dcol = nullptr;
     const double* v64 = nullptr;
     const uint16_t* v16 = nullptr;
+    const int32_t* ptr2 = nullptr;
+    const uint32_t *vp = nullptr, *cp = nullptr;
 };
 
 struct AmgHierarchy {
     AmgSellView fine;
     DBuf<uint16_t> fine16;                           // storage of fine.v16
+    DBuf<int32_t> fine_ptr2;                         // storage of the pair-packed copy
+    DBuf<uint32_t> fine_vp, fine_cp;
     std::vector<std::unique_ptr<AmgLevelDev>> lv;   // lv[0] fine ... lv[L-1] coarsest
     int64_t nc = 0;                                  // size of the dense coarsest level
     int64_t ld = 0;                                  // its row stride: nc rounded up to 4

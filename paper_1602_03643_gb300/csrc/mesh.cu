@@ -196,9 +196,16 @@ Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const in
                     const int64_t i = sl * 32 + l;
                     for (int k = 0; k < slen[sl]; ++k) {
                         const int64_t pos = sptr[sl] + 32 * k + l;
-                        int64_t d = ((int64_t)scol[pos] - i) % n;
-                        if (d < 0) d += n;
-                        if (d > n / 2) d -= n;
+                        // the plain offset where it fits (always for the padding
+                        // lanes past the last row, whose column is n - 1), else
+                        // the offset modulo n, nearest to zero: the decode adds it
+                        // to the row and wraps once into [0, n)
+                        int64_t d = (int64_t)scol[pos] - i;
+                        if (d < -32768 || d > 32767) {
+                            d %= n;
+                            if (d < 0) d += n;
+                            if (d > n / 2) d -= n;
+                        }
                         if (d < -32768 || d > 32767) {
                             fits = false;
                             break;
