@@ -73,10 +73,13 @@ def workload_config(name, pb, precision, gpu=True):
 
 # ---------------------------------------------------------------------- rooflines
 # DRAM bytes per launch of a family's kernel from an ncu capture (cold caches),
-# per workload, with the profile summary it comes from; valid for the kernels as
-# they stand (an entry is removed when its kernel changes)
+# per workload and layout, with the profile summary it comes from; valid for the
+# kernels as they stand (an entry is removed when its kernel changes)
 _S112 = "profiles/dram_traffic_products_stress112_rcm.md (stress112_rcm capture, scaled by algorithmic bytes)"
-MEASURED_TRAFFIC = {("stress128_rcm", "pcg_spmv"): (215.0e6, _S112)}
+MEASURED_TRAFFIC = {("stress128_rcm", "pcg_spmv@sell"): (215.0e6, _S112),
+                    ("stress128_rcm", "pcg_spmv@pairs"): (229.8e6, _S112),
+                    ("stress128_rcm", "amg_fine@pairs"): (163.3e6, _S112),
+                    ("stress128_rcm", "bicg_spmm@rows"): (332.4e6, _S112)}
 
 
 def family_bytes(pb, nnz, args, tuning, amg):
@@ -111,11 +114,14 @@ def family_bytes(pb, nnz, args, tuning, amg):
     out = {}
     if amg:
         have16 = any(c["col16"] and c["us"] > 0 for c in tuning["candidates"])
+        chosen = tuning["candidates"][tuning.get("chosen", 1) - 1]
         cb = 2 if have16 else 4
-        out["pcg_spmv"] = ("k_amg_cg_spmv<Mixed> (multigrid CG: w = K u on SELL-32 + 3 dots)",
-                           (4 + cb) * Z + 12 * N + 8 * n_slices, f"(4+{cb}) Z + 12 N + 8 N/32")
-        out["amg_fine"] = ("k_amg_fine<float> (finest-level damped-Jacobi sweep on SELL-32, bfloat16 K)",
-                           (2 + cb) * Z + 16 * N + 8 * n_slices, f"(2+{cb}) Z + 16 N + 8 N/32")
+        pcg = ("k_amg_cg_spmv_pairs<Mixed> (multigrid CG: w = K u on the pair-packed SELL-32 copy + 3 dots)"
+               if chosen["col16"] == 2 else "k_amg_cg_spmv<Mixed> (multigrid CG: w = K u on SELL-32 + 3 dots)")
+        out["pcg_spmv"] = (pcg, (4 + cb) * Z + 12 * N + 8 * n_slices, f"(4+{cb}) Z + 12 N + 8 N/32")
+        fine = ("k_amg_fine_pairs (finest-level damped-Jacobi sweep, pair-packed SELL-32, bfloat16 K)" if have16
+                else "k_amg_fine<float> (finest-level damped-Jacobi sweep on SELL-32, bfloat16 K)")
+        out["amg_fine"] = (fine, (2 + cb) * Z + 16 * N + 8 * n_slices, f"(2+{cb}) Z + 16 N + 8 N/32")
         rows, nz, pn = amg["rows"], amg["nnz"], amg["p_nnz"]
         L = amg["levels"]
         if pn:
@@ -129,8 +135,15 @@ def family_bytes(pb, nnz, args, tuning, amg):
         out["amg_coarse"] = ("k_amg_pre / k_amg_post (CSR, bfloat16 values, levels >= 1) and k_amg_dense",
                              cbytes / (2 * (L - 2) + 1), "per V-cycle sum_l 2 (6 nnz_l + 20 n_l) + 4 nc ld + 8 nc, "
                                                          "over 2(L-2)+1 launches")
-    out["bicg_spmm"] = (f"k_bicg_spmm<Mixed,{D},{D}> (tentative BiCGStab: {D}-RHS product A x + dots, row tiles)",
-                        8 * Z + 4 * (N + 1) + 12 * D * N, f"8 Z + 4 N + 12 D N")
+    bcs = tuning.get("bicg_candidates")
+    bc = bcs[tuning["bicg_chosen"] - 1] if bcs else {"lanes": 0}
+    if bc["lanes"]:
+        spmm = (f"k_bicg_spmm_rows<Mixed,{D},{D}> (tentative BiCGStab: {D}-RHS product A x + dots; "
+                f"{bc['lanes']} lanes per row, {bc['rows']} rows in flight, registers for {bc['min_blocks']} "
+                f"blocks per SM)")
+    else:
+        spmm = f"k_bicg_spmm<Mixed,{D},{D}> (tentative BiCGStab: {D}-RHS product A x + dots, row tiles)"
+    out["bicg_spmm"] = (spmm, 8 * Z + 4 * (N + 1) + 12 * D * N, f"8 Z + 4 N + 12 D N")
     out["bicg_vec"] = ("k_bicg_dir / k_bicg_s / k_bicg_xr (BiCGStab vector updates + dots)",
                        (64 + 52 + 96) * N * D / 3 / 3, "(64 + 52 + 96) N / 3 per launch (D = 3)")
     out["assemble"] = ("k_ubar + k_cell_beta + k_assemble (convection assembly + Algorithm 2, once per step)",
@@ -362,8 +375,14 @@ def run_ours(args, rank, world):
     peak = peaks.get("hbm_gbs", 6800.0)
     fams = family_bytes(pb, run.nnz, args, tun_e, amg_info)
     table = {}
-    bc = tuning["bicg_candidates"][tuning["bicg_chosen"] - 1]
-    shape = {"bicg_spmm": "@%dx%dx%d" % (bc["lanes"], bc["rows"], bc["min_blocks"]) if bc["lanes"] else "@tile"}
+    bc = tun_e["bicg_candidates"][tun_e["bicg_chosen"] - 1]
+    pc_chosen = tun_e["candidates"][tun_e["chosen"] - 1] if tun_e["candidates"] else {"col16": 0}
+    pairs16 = any(c["col16"] and c["us"] > 0 for c in tun_e["candidates"])
+    # the layout a measured traffic figure belongs to (every shape of one layout
+    # reads the same arrays once per launch)
+    shape = {"bicg_spmm": "@rows" if bc["lanes"] else "@tile",
+             "pcg_spmv": "@pairs" if pc_chosen["col16"] == 2 else "@sell",
+             "amg_fine": "@pairs" if pairs16 else "@sell"}
     for f, (kernel, nbytes, per) in fams.items():
         n_l, ms_l = fam.get(f, (0, 0.0))
         if not n_l:

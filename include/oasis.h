@@ -165,7 +165,10 @@ typedef struct oasis_params {
  * resident blocks per SM that the register budget is sized for, whether the
  * next chunk's loads are issued before the current products (prefetch), and
  * whether columns are read as 16-bit offsets from the row taken modulo the dof
- * count (col16; only where every offset fits, else the candidate is not timed),
+ * count (col16 = 1; only where every offset fits, else the candidate is not
+ * timed; col16 = 2: the float32 multigrid CG product on the pair-packed copy of
+ * K, two entries' values and offsets per load, where the multigrid hierarchy
+ * has one; chunk is then entries per round),
  * and whether the slice's values and columns are streamed into shared memory
  * by the bulk-copy engine, two slices ahead per warp (streamed). */
 #define OASIS_MAX_VARIANTS 16

@@ -358,7 +358,8 @@ __global__ void k_round_bf16(int64_t n, const float* __restrict__ in, uint16_t* 
 // gathered operand is a valid row.
 __global__ void k_pack_pairs(int64_t n_slices, const int32_t* __restrict__ ptr, const int32_t* __restrict__ len,
                              const int32_t* __restrict__ ptr2, const uint16_t* __restrict__ v16,
-                             const int16_t* __restrict__ dcol, uint16_t* __restrict__ vp, uint16_t* __restrict__ cp) {
+                             const float* __restrict__ v32, const int16_t* __restrict__ dcol,
+                             uint16_t* __restrict__ vp, uint16_t* __restrict__ cp, float* __restrict__ kp) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_slices * 32;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t sl = t >> 5;
@@ -366,14 +367,17 @@ __global__ void k_pack_pairs(int64_t n_slices, const int32_t* __restrict__ ptr, 
         uint16_t c = 0;
         for (int k = 0; k < lp; ++k) {
             uint16_t v = 0;
+            float f = 0.f;
             if (k < ln) {
                 const int64_t q = (int64_t)ptr[sl] + 32 * (int64_t)k + l;
                 v = v16[q];
+                f = v32[q];
                 c = (uint16_t)dcol[q];
             }
             const int64_t o = (int64_t)ptr2[sl] + 64 * (int64_t)(k >> 1) + 2 * l + (k & 1);
             vp[o] = v;
             cp[o] = c;
+            kp[o] = f;
         }
     }
 }
@@ -392,14 +396,17 @@ void pack_pairs(AmgHierarchy& h, const Mesh& m, cudaStream_t s) {
     upload_vec(h.fine_ptr2, ptr2, s);
     h.fine_vp.alloc((size_t)std::max<int64_t>(total / 2, 1));
     h.fine_cp.alloc((size_t)std::max<int64_t>(total / 2, 1));
+    h.fine_kp.alloc((size_t)std::max<int64_t>(total / 2, 1));
     k_pack_pairs<<<(int)std::max<int64_t>(1, std::min<int64_t>((ns * 32 + kBlock - 1) / kBlock, 4096)), kBlock, 0, s>>>(
-        ns, m.sell_ptr.p, m.sell_len.p, h.fine_ptr2.p, h.fine16.p, m.sell_dcol.p,
-        reinterpret_cast<uint16_t*>(h.fine_vp.p), reinterpret_cast<uint16_t*>(h.fine_cp.p));
+        ns, m.sell_ptr.p, m.sell_len.p, h.fine_ptr2.p, h.fine16.p, m.K32s.p, m.sell_dcol.p,
+        reinterpret_cast<uint16_t*>(h.fine_vp.p), reinterpret_cast<uint16_t*>(h.fine_cp.p),
+        reinterpret_cast<float*>(h.fine_kp.p));
     OASIS_CUDA(cudaGetLastError());
     OASIS_CUDA(cudaStreamSynchronize(s));
     h.fine.ptr2 = h.fine_ptr2.p;
     h.fine.vp = h.fine_vp.p;
     h.fine.cp = h.fine_cp.p;
+    h.fine.kp = h.fine_kp.p;
 }
 
 }  // namespace
@@ -759,13 +766,14 @@ __global__ void __launch_bounds__(kBlock) k_amg_fine_pairs(AmgSellView F, const 
         const int64_t i = sl * 32 + lane;
         const int32_t row = (int32_t)i;
         const int words = (F.len[sl] + 1) >> 1;
-        const int64_t base = (int64_t)(F.ptr2[sl] >> 1) + lane;
+        // 32-bit word offsets (the copy holds fewer than 2^31 entries)
+        const uint32_t base = (uint32_t)(F.ptr2[sl] >> 1) + (uint32_t)lane;
         float sum = 0.f;
         for (int k = 0; k < words; k += C2) {
             uint32_t vw[C2], cw[C2];
 #pragma unroll
             for (int u = 0; u < C2; ++u) {
-                const int64_t q = base + 32 * (int64_t)(k + u);
+                const uint32_t q = base + 32u * (uint32_t)(k + u);
                 const bool ok = k + u < words;
                 vw[u] = ok ? vp[q] : 0u;
                 cw[u] = ok ? cp[q] : 0u;

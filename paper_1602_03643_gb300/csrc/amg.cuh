@@ -59,6 +59,8 @@ struct AmgLevelDev {
 // a slice's rows padded to an even length, entries k and k+1 of lane l in one
 // 32-bit word at word ptr2[s] / 2 + 32 (k / 2) + l (vp: two bfloat16 values,
 // low half entry k; cp: two column offsets), so one load brings two entries.
+// kp holds the float32 values in the same layout, two per 8-byte word, for the
+// float32 CG product w = K u (which needs K exactly as the inner system has it).
 struct AmgSellView {
     int64_t n = 0, n_slices = 0;
     const int32_t *ptr = nullptr, *len = nullptr, *col = nullptr;
@@ -67,6 +69,7 @@ struct AmgSellView {
     const uint16_t* v16 = nullptr;
     const int32_t* ptr2 = nullptr;
     const uint32_t *vp = nullptr, *cp = nullptr;
+    const float2* kp = nullptr;
 };
 
 struct AmgHierarchy {
@@ -74,6 +77,7 @@ struct AmgHierarchy {
     DBuf<uint16_t> fine16;                           // storage of fine.v16
     DBuf<int32_t> fine_ptr2;                         // storage of the pair-packed copy
     DBuf<uint32_t> fine_vp, fine_cp;
+    DBuf<float2> fine_kp;
     std::vector<std::unique_ptr<AmgLevelDev>> lv;   // lv[0] fine ... lv[L-1] coarsest
     int64_t nc = 0;                                  // size of the dense coarsest level
     int64_t ld = 0;                                  // its row stride: nc rounded up to 4

@@ -1606,9 +1606,37 @@ __global__ void __launch_bounds__(kBlock) k_amg_cg_update(StepData<P> a, Ctl ctl
     }
 }
 
-// w = K u on SELL-32 with gamma = <r, u>, delta = <w, u> and <r, r>.  START:
-// first iteration of a sweep (alpha = gamma / delta, beta = 0); else the
+// End of the multigrid CG product: the three dots over the grid; START: first
+// iteration of a sweep (alpha = gamma / delta, beta = 0); else the
 // Chronopoulos-Gear update of alpha, beta and the inner stopping test.
+template <class P, bool START>
+__device__ __forceinline__ void amg_cg_spmv_finish(const StepData<P>& a, const Ctl& ctl,
+                                                   typename P::V (&part)[3]) {
+    using V = typename P::V;
+    double tot[3];
+    if (grid_sum_lite<3, V>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
+        if constexpr (START) {
+            KrylovState* st = a.stp;
+            const double g0 = tot[0], d0 = tot[1];
+            if (!(d0 > 0.0) || !isfinite(d0) || !isfinite(g0)) {
+                st->in_done[0] = 1;
+                st->it_total[0] += 1;
+                st->alpha[0] = 0.0;
+                set_cond(ctl.use_cond, ctl.h_inner, 0);
+            } else {
+                st->rho[0] = g0;
+                st->alpha[0] = g0 / d0;
+            }
+            st->beta[0] = 0.0;
+            mirror_coefs(st, 0);
+        } else {
+            pcg_iter_finish<P>(a, ctl, tot);
+        }
+    }
+}
+
+// w = K u on SELL-32 with gamma = <r, u>, delta = <w, u> and <r, r>, then
+// amg_cg_spmv_finish.
 template <class P, bool START, bool D16, int C = 4, int MINB = 1>
 __global__ void __launch_bounds__(kBlock, MINB) k_amg_cg_spmv(StepData<P> a, Ctl ctl) {
     using V = typename P::V;
@@ -1662,26 +1690,69 @@ __global__ void __launch_bounds__(kBlock, MINB) k_amg_cg_spmv(StepData<P> a, Ctl
             part[2] += r * r;
         }
     });
-    double tot[3];
-    if (grid_sum_lite<3, V>(part, tot, a.partial, &a.stp->ticket) && threadIdx.x == 0) {
-        if constexpr (START) {
-            KrylovState* st = a.stp;
-            const double g0 = tot[0], d0 = tot[1];
-            if (!(d0 > 0.0) || !isfinite(d0) || !isfinite(g0)) {
-                st->in_done[0] = 1;
-                st->it_total[0] += 1;
-                st->alpha[0] = 0.0;
-                set_cond(ctl.use_cond, ctl.h_inner, 0);
-            } else {
-                st->rho[0] = g0;
-                st->alpha[0] = g0 / d0;
+    amg_cg_spmv_finish<P, START>(a, ctl, part);
+}
+
+// The same product on the pair-packed copy of K (float32 mixed path): per round
+// C2 words of values (two entries each, 8 bytes) and C2 words of offsets are
+// loaded, then their 2 C2 gathers; a row's products are added in entry order,
+// as in k_amg_cg_spmv (the padding entry adds 0 times a valid operand).
+template <class P, bool START, int C2, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_amg_cg_spmv_pairs(StepData<P> a, Ctl ctl) {
+    using V = typename P::V;
+    static_assert(sizeof(V) == 4, "the pair-packed copy holds float32 values");
+    if (a.stp->col_done[0] || a.stp->in_done[0]) return;
+    V part[3] = {};
+    const float2* __restrict__ kp = a.kpair;
+    const uint32_t* __restrict__ cp = a.cpair;
+    const V* __restrict__ au = a.au;
+    const V* __restrict__ ar = a.ar;
+    V* __restrict__ aw = a.aw;
+    const int32_t n32 = (int32_t)a.n;
+    const int lane = (int)(threadIdx.x & 31);
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < a.n_slices; sl += nw) {
+        const int64_t i = sl * 32 + lane;
+        const int32_t row = (int32_t)i;
+        const int words = (a.sell_len[sl] + 1) >> 1;
+        // 32-bit word offsets (the copy holds fewer than 2^31 entries)
+        const uint32_t base = (uint32_t)(a.ptr2[sl] >> 1) + (uint32_t)lane;
+        V w = 0;
+        for (int k = 0; k < words; k += C2) {
+            float2 kv[C2];
+            uint32_t cw[C2];
+#pragma unroll
+            for (int u = 0; u < C2; ++u) {
+                const uint32_t q = base + 32u * (uint32_t)(k + u);
+                const bool ok = k + u < words;
+                kv[u] = ok ? kp[q] : make_float2(0.f, 0.f);
+                cw[u] = ok ? cp[q] : 0u;
             }
-            st->beta[0] = 0.0;
-            mirror_coefs(st, 0);
-        } else {
-            pcg_iter_finish<P>(a, ctl, tot);
+            V g[2 * C2];
+#pragma unroll
+            for (int e = 0; e < 2 * C2; ++e) {
+                const uint32_t half = (e & 1) ? (cw[e >> 1] >> 16) : (cw[e >> 1] & 0xFFFFu);
+                int32_t j = row + (int32_t)(int16_t)half;
+                j = j < 0 ? j + n32 : j;
+                j = j >= n32 ? j - n32 : j;
+                g[e] = au[j];
+            }
+#pragma unroll
+            for (int u = 0; u < C2; ++u)
+                if (k + u < words) {
+                    w += kv[u].x * g[2 * u];
+                    w += kv[u].y * g[2 * u + 1];
+                }
+        }
+        if (i < a.n) {
+            aw[i] = w;
+            const V u = au[i], r = ar[i];
+            part[0] += r * u;
+            part[1] += w * u;
+            part[2] += r * r;
         }
     }
+    amg_cg_spmv_finish<P, START>(a, ctl, part);
 }
 
 // Candidate shapes of the multigrid CG product: entries per lane whose column
@@ -1692,19 +1763,34 @@ __global__ void __launch_bounds__(kBlock, MINB) k_amg_cg_spmv(StepData<P> a, Ctl
 // mesh small enough for one grid of a warp per slice gets the same bits.
 template <class P>
 struct AmgVariant {
-    void (*fn16)(StepData<P>, Ctl);
-    void (*fn32)(StepData<P>, Ctl);
-    int chunk, minb;
+    void (*fn16)(StepData<P>, Ctl);    // 16-bit offsets
+    void (*fn32)(StepData<P>, Ctl);    // 32-bit columns
+    void (*fnp)(StepData<P>, Ctl);     // pair-packed copy (float32 path with a multigrid hierarchy)
+    int chunk, minb;                   // entries per round, blocks per SM the registers are sized for
+    // the kernel for the layout at hand, or null where the shape does not apply
+    void (*pick(const StepData<P>& a) const)(StepData<P>, Ctl) {
+        if (fnp) return a.kpair ? fnp : nullptr;
+        return a.sell_dcol ? fn16 : fn32;
+    }
 };
-#define OASIS_AMGV(C, B) {k_amg_cg_spmv<P, false, true, C, B>, k_amg_cg_spmv<P, false, false, C, B>, C, B}
-constexpr int kAmgVariants = 4;
+#define OASIS_AMGV(C, B) {k_amg_cg_spmv<P, false, true, C, B>, k_amg_cg_spmv<P, false, false, C, B>, nullptr, C, B}
+#define OASIS_AMGP(C2, B) {nullptr, nullptr, k_amg_cg_spmv_pairs<P, false, C2, B>, 2 * C2, B}
+constexpr int kAmgVariants = 7;                        // room for the longest table
 template <class P>
-static const AmgVariant<P>* amg_variant_table() {
-    static const AmgVariant<P> t[kAmgVariants] = {OASIS_AMGV(4, 1), OASIS_AMGV(2, 8), OASIS_AMGV(4, 8),
-                                                  OASIS_AMGV(8, 4)};
-    return t;
+static const AmgVariant<P>* amg_variant_table(int& count) {
+    if constexpr (P::mixed) {
+        static const AmgVariant<P> t[] = {OASIS_AMGV(4, 1), OASIS_AMGV(2, 8), OASIS_AMGV(4, 8), OASIS_AMGV(8, 4),
+                                          OASIS_AMGP(2, 8), OASIS_AMGP(4, 6), OASIS_AMGP(4, 4)};
+        count = (int)(sizeof(t) / sizeof(t[0]));
+        return t;
+    } else {
+        static const AmgVariant<P> t[] = {OASIS_AMGV(4, 1), OASIS_AMGV(2, 8), OASIS_AMGV(4, 8), OASIS_AMGV(8, 4)};
+        count = (int)(sizeof(t) / sizeof(t[0]));
+        return t;
+    }
 }
 #undef OASIS_AMGV
+#undef OASIS_AMGP
 
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_pcg_correct(StepData<P> a) {
@@ -2226,8 +2312,9 @@ struct StepImplT final : StepImpl {
     // grid-stride SELL kernels ending in a reduction: one resident wave of each
     // kernel (its registers set the blocks per SM; a grid of 8 blocks per SM for a
     // kernel that fits 5 or 6 ran its latency-bound second wave nearly empty)
-    int g_outer_sell = 1, g_judge = 1, g_cg_first[2] = {1, 1};
-    int amg_grid_v[kAmgVariants][2] = {};             // per shape: 16-bit, 32-bit columns
+    int g_outer_sell = 1, g_judge = 1, g_cg_first = 1;
+    int n_amg_v = 0;                                  // multigrid CG product shapes for this precision
+    int amg_grid_v[kAmgVariants] = {};                // per shape, for the layout at hand
     int iter_v = 0;                                   // chosen CG iteration shape
     int amg_v = 0;                                    // chosen multigrid CG product shape
     int bicg_v = 0;                                   // chosen d-RHS BiCGStab product shape
@@ -2239,6 +2326,14 @@ struct StepImplT final : StepImpl {
     int it_grid[OASIS_MAX_VARIANTS] = {0}, it_block[OASIS_MAX_VARIANTS] = {0};
     size_t it_smem[OASIS_MAX_VARIANTS] = {0};
 
+
+    // first multigrid CG product of a sweep, in the layout at hand
+    void (*cg_first_fn() const)(StepData<P>, Ctl) {
+        if constexpr (P::mixed) {
+            if (a.kpair) return k_amg_cg_spmv_pairs<P, true, 4, 1>;
+        }
+        return a.sell_dcol ? k_amg_cg_spmv<P, true, true> : k_amg_cg_spmv<P, true, false>;
+    }
 
     // one resident wave of a grid-stride SELL kernel (kBlock threads, no shared memory)
     template <class K>
@@ -2322,6 +2417,13 @@ struct StepImplT final : StepImpl {
         a.sell_col = m.sell_col.p;
         a.sell_dcol = m.sell_dcol.p;
         a.Ks = mat<V>(m.K64s, m.K32s);
+        if constexpr (P::mixed) {
+            if (Sv.prm.pressure_pc == OASIS_PC_AMG && m.amg && m.amg->fine.kp) {
+                a.kpair = m.amg->fine.kp;
+                a.cpair = m.amg->fine.cp;
+                a.ptr2 = m.amg->fine.ptr2;
+            }
+        }
         if constexpr (P::mixed) a.Kouts = reinterpret_cast<const S*>(m.Kffs.p);
         else a.Kouts = reinterpret_cast<const S*>(m.K64s.p);
         k_.rdt = (V)(1.0 / Sv.prm.dt);
@@ -2354,11 +2456,13 @@ struct StepImplT final : StepImpl {
         g_sell = (int)std::max<int64_t>(1, ((m.n + 31) / 32 + kBlock / 32 - 1) / (kBlock / 32));
         g_outer_sell = sell_wave(k_pcg_outer_sell<P>);
         g_judge = sell_wave(k_guess_judge<P>);
-        g_cg_first[0] = sell_wave(k_amg_cg_spmv<P, true, true>);
-        g_cg_first[1] = sell_wave(k_amg_cg_spmv<P, true, false>);
-        for (int v = 0; v < kAmgVariants; ++v) {
-            amg_grid_v[v][0] = sell_wave(amg_variant_table<P>()[v].fn16);
-            amg_grid_v[v][1] = sell_wave(amg_variant_table<P>()[v].fn32);
+        g_cg_first = sell_wave(cg_first_fn());
+        {
+            const AmgVariant<P>* t = amg_variant_table<P>(n_amg_v);
+            for (int v = 0; v < n_amg_v; ++v) {
+                const auto fn = t[v].pick(a);
+                amg_grid_v[v] = fn ? sell_wave(fn) : 1;
+            }
         }
         {
             int per_sm = 0;
@@ -2568,8 +2672,7 @@ struct StepImplT final : StepImpl {
                     Sv.prof_end(ss, po);
                     k_amg_cg_start<P><<<ge_n, kBlock, 0, ss>>>(a);
                     vcycle(ss);
-                    if (a.sell_dcol) k_amg_cg_spmv<P, true, true><<<g_cg_first[0], kBlock, 0, ss>>>(a, c);
-                    else k_amg_cg_spmv<P, true, false><<<g_cg_first[1], kBlock, 0, ss>>>(a, c);
+                    cg_first_fn()<<<g_cg_first, kBlock, 0, ss>>>(a, c);
                     OASIS_CUDA(cudaGetLastError());
                 },
                 [&](cudaStream_t ss, const Loop& lp) {
@@ -2579,8 +2682,7 @@ struct StepImplT final : StepImpl {
                     Sv.prof_end(ss, pu);
                     vcycle(ss);
                     const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
-                    const AmgVariant<P>& av = amg_variant_table<P>()[amg_v];
-                    (a.sell_dcol ? av.fn16 : av.fn32)<<<amg_grid_v[amg_v][a.sell_dcol ? 0 : 1], kBlock, 0, ss>>>(a, c);
+                    amg_variant_table<P>(n_amg_v)[amg_v].pick(a)<<<amg_grid_v[amg_v], kBlock, 0, ss>>>(a, c);
                     Sv.prof_end(ss, pq);
                     OASIS_CUDA(cudaGetLastError());
                 },
@@ -2730,13 +2832,16 @@ struct StepImplT final : StepImpl {
     // the multigrid CG product's shapes, timed on this matrix like the fused
     // Jacobi iteration's (forced = k >= 1 takes shape k untimed)
     void tune_amg(cudaStream_t s, int forced) {
-        OASIS_CHECK(forced <= kAmgVariants, OASIS_EINVAL, "spmv_variant: no such candidate");
+        int count = 0;
+        const AmgVariant<P>* t = amg_variant_table<P>(count);
+        OASIS_CHECK(forced <= count, OASIS_EINVAL, "spmv_variant: no such candidate");
+        OASIS_CHECK(forced < 1 || t[forced - 1].pick(a), OASIS_EINVAL,
+                    "spmv_variant: the shape needs a layout this mesh does not have");
         for (auto& u : amg_us) u = 0.0;
         if (forced >= 1) {
             amg_v = forced - 1;
             return;
         }
-        const AmgVariant<P>* t = amg_variant_table<P>();
         DBuf<KrylovState> scratch;
         scratch.alloc(1);
         StepData<P> d = a;
@@ -2745,22 +2850,28 @@ struct StepImplT final : StepImpl {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         OASIS_CUDA(cudaEventCreate(&e0));
         OASIS_CUDA(cudaEventCreate(&e1));
+        // rounds over all candidates (2 untimed, then 7 timed), so that a drift of
+        // the clocks or of the caches during tuning falls on every candidate alike
         constexpr int kWarm = 2, kTimed = 7;
-        int best = 0;
-        for (int v = 0; v < kAmgVariants; ++v) {
-            float ts[kTimed];
-            for (int r = 0; r < kWarm + kTimed; ++r) {
+        float ts[kAmgVariants][kTimed] = {};
+        for (int r = 0; r < kWarm + kTimed; ++r)
+            for (int v = 0; v < count; ++v) {
+                const auto fn = t[v].pick(a);
+                if (!fn) continue;                     // not timed: us stays 0
                 OASIS_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(KrylovState), s));
                 OASIS_CUDA(cudaEventRecord(e0, s));
-                (a.sell_dcol ? t[v].fn16 : t[v].fn32)<<<amg_grid_v[v][a.sell_dcol ? 0 : 1], kBlock, 0, s>>>(d, c);
+                fn<<<amg_grid_v[v], kBlock, 0, s>>>(d, c);
                 OASIS_CUDA(cudaGetLastError());
                 OASIS_CUDA(cudaEventRecord(e1, s));
                 OASIS_CUDA(cudaEventSynchronize(e1));
-                if (r >= kWarm) OASIS_CUDA(cudaEventElapsedTime(&ts[r - kWarm], e0, e1));
+                if (r >= kWarm) OASIS_CUDA(cudaEventElapsedTime(&ts[v][r - kWarm], e0, e1));
             }
-            std::sort(ts, ts + kTimed);
-            amg_us[v] = 1e3 * (double)ts[kTimed / 2];
-            if (amg_us[v] < amg_us[best]) best = v;
+        int best = -1;
+        for (int v = 0; v < count; ++v) {
+            if (!t[v].pick(a)) continue;
+            std::sort(ts[v], ts[v] + kTimed);
+            amg_us[v] = 1e3 * (double)ts[v][kTimed / 2];
+            if (best < 0 || amg_us[v] < amg_us[best]) best = v;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -2828,12 +2939,13 @@ struct StepImplT final : StepImpl {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         OASIS_CUDA(cudaEventCreate(&e0));
         OASIS_CUDA(cudaEventCreate(&e1));
+        // rounds over all candidates (2 untimed, then 7 timed), so that a drift of
+        // the clocks or of the caches during tuning falls on every candidate alike
         constexpr int kWarm = 2, kTimed = 7;
-        int best = 0;
-        for (int v = 0; v < kBicgVariants; ++v) {
-            bicg_v = v;
-            float ts[kTimed];
-            for (int r = 0; r < kWarm + kTimed; ++r) {
+        float ts[kBicgVariants][kTimed] = {};
+        for (int r = 0; r < kWarm + kTimed; ++r)
+            for (int v = 0; v < kBicgVariants; ++v) {
+                bicg_v = v;
                 // each product from a fresh scratch state: with zeroed values the first
                 // product's dots are zero, and its breakdown branch would otherwise mark
                 // every column done and let the second return at once
@@ -2846,10 +2958,12 @@ struct StepImplT final : StepImpl {
                     OASIS_CUDA(cudaEventSynchronize(e1));
                     OASIS_CUDA(cudaEventElapsedTime(&t2[mode], e0, e1));
                 }
-                if (r >= kWarm) ts[r - kWarm] = t2[0] + t2[1];
+                if (r >= kWarm) ts[v][r - kWarm] = t2[0] + t2[1];
             }
-            std::sort(ts, ts + kTimed);
-            bicg_us[v] = 1e3 * (double)ts[kTimed / 2];
+        int best = 0;
+        for (int v = 0; v < kBicgVariants; ++v) {
+            std::sort(ts[v], ts[v] + kTimed);
+            bicg_us[v] = 1e3 * (double)ts[v][kTimed / 2];
             if (bicg_us[v] < bicg_us[best]) best = v;
         }
         cudaEventDestroy(e0);
@@ -2920,14 +3034,15 @@ struct StepImplT final : StepImpl {
             out->bicg_us[v] = bicg_us[v];
         }
         if (Sv.prm.pressure_pc == OASIS_PC_AMG) {
-            const AmgVariant<P>* t = amg_variant_table<P>();
-            out->n_variants = kAmgVariants;
+            int count = 0;
+            const AmgVariant<P>* t = amg_variant_table<P>(count);
+            out->n_variants = count;
             out->chosen = amg_v + 1;
-            for (int v = 0; v < kAmgVariants; ++v) {
+            for (int v = 0; v < count; ++v) {
                 out->chunk[v] = t[v].chunk;
                 out->min_blocks[v] = t[v].minb;
                 out->prefetch[v] = 0;
-                out->col16[v] = a.sell_dcol != nullptr;
+                out->col16[v] = t[v].fnp ? 2 : a.sell_dcol != nullptr;
                 out->streamed[v] = 0;
                 out->warps_per_block[v] = kBlock / 32;
                 out->us[v] = amg_us[v];
