@@ -482,8 +482,9 @@ def run_ours(args, rank, world):
     # 1 per CG iteration; update 1
     # learned guess: input scales, inputs, two network layers, judge.  Multigrid:
     # a V-cycle is 4 kernels per operator level + the dense coarsest solve; per
-    # sweep residual, start, V-cycle, product (and all but the last a
-    # correction); per iteration update, V-cycle, product.  Inner iterations
+    # sweep residual, start, V-cycle, product, update (and all but the last a
+    # correction); per further iteration of an inner solve (every sweep but the
+    # last runs one) V-cycle, product, update.  Inner iterations
     # (Algorithm 1; the statistics describe the last repetition): per repetition
     # after the first a pressure advance, the assembly and both solves again.
     # Consistent-mass update: start 2, 2 per CG iteration, then the update.
@@ -492,7 +493,7 @@ def run_ours(args, rank, world):
     # the final update.
     if amg_info:
         vk = 4 * (amg_info["levels"] - 1) + 1
-        p_kernels = sw_p * (4 + vk) + it_p * (2 + vk)
+        p_kernels = sw_p * (5 + vk) + max(0, it_p - (sw_p - 1)) * (2 + vk)
     else:
         p_kernels = 3 * sw_p + it_p
     ni = max(1, args.inner_iters)

@@ -1561,9 +1561,8 @@ __global__ void __launch_bounds__(kBlock) k_amg_cg_start(StepData<P> a) {
 }
 
 // p = u + beta p, s = w + beta s, delta += alpha p, r -= alpha s, and ||r||^2:
-// when the new residual already meets the inner stopping test the iteration
-// ends here (counted), and the V-cycle and product of this iteration return
-// at once instead of computing what the test no longer needs.
+// when the new residual already meets the inner stopping test the inner solve
+// ends here (counted; the loop's condition is cleared, so no V-cycle follows).
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_amg_cg_update(StepData<P> a, Ctl ctl) {
     using V = typename P::V;
@@ -2663,6 +2662,12 @@ struct StepImplT final : StepImpl {
                 amg_vcycle<V>(H, Sv.amgw, a.ar, a.au, a.stp, ss, &hook);
                 Sv.prof_end(ss, pa);
             };
+            auto update = [&](cudaStream_t ss, const Ctl& c) {
+                const int pu = Sv.prof_begin(ss, OASIS_PROF_PCG_UPDATE);
+                k_amg_cg_update<P><<<ge_red, kBlock, 0, ss>>>(a, c);
+                Sv.prof_end(ss, pu);
+                OASIS_CUDA(cudaGetLastError());
+            };
             Sv.run_loops(
                 s, graph, 1,
                 [&](cudaStream_t ss, const Loop& lp) {
@@ -2674,17 +2679,19 @@ struct StepImplT final : StepImpl {
                     vcycle(ss);
                     cg_first_fn()<<<g_cg_first, kBlock, 0, ss>>>(a, c);
                     OASIS_CUDA(cudaGetLastError());
+                    update(ss, c);
                 },
+                // an iteration ends with the update, whose residual test sets the
+                // loop's condition: a converged solve leaves the loop before another
+                // V-cycle (same kernels in the same order as with the update first)
                 [&](cudaStream_t ss, const Loop& lp) {
                     const Ctl c = ctl_p(lp);
-                    const int pu = Sv.prof_begin(ss, OASIS_PROF_PCG_UPDATE);
-                    k_amg_cg_update<P><<<ge_red, kBlock, 0, ss>>>(a, c);
-                    Sv.prof_end(ss, pu);
                     vcycle(ss);
                     const int pq = Sv.prof_begin(ss, OASIS_PROF_PCG_SPMV);
                     amg_variant_table<P>(n_amg_v)[amg_v].pick(a)<<<amg_grid_v[amg_v], kBlock, 0, ss>>>(a, c);
                     Sv.prof_end(ss, pq);
                     OASIS_CUDA(cudaGetLastError());
+                    update(ss, c);
                 },
                 [&](cudaStream_t ss, const Loop&) {
                     k_pcg_correct<P><<<ge_n, kBlock, 0, ss>>>(a);
