@@ -94,10 +94,13 @@ def family_bytes(pb, nnz, args, tuning, amg):
       amg_fine     finest-level smoothing sweep (pre or post, SELL-32): K values as
                    bfloat16 + columns, 4 vectors of N, slice pointers/lengths
       amg_transfer restriction/prolongation (bfloat16 values), averaged over the 2(L-1)
-                   launches of a V-cycle: per level 12 nnz(P) + 16 n_l + 12 n_(l+1)
+                   launches of a V-cycle: per level 12 nnz(P) + 16 n_l + 12 n_(l+1) in CSR
+                   form; 8 nnz(P) + 12.5 n_l + 8.5 n_(l+1) with both pair-packed (16-bit
+                   offsets, 16-byte slice headers; 6 bytes per entry where a packed copy
+                   keeps 32-bit columns)
       amg_coarse   coarser-level sweeps (bfloat16 values) and the dense coarsest product,
-                   averaged over their 2(L-2)+1 launches: per sweep 6 nnz_l + 20 n_l;
-                   dense 4 nc ld + 8 nc
+                   averaged over their 2(L-2)+1 launches: per sweep 6 nnz_l + 20 n_l (CSR)
+                   or 4 nnz_l + 16.5 n_l (pair-packed); dense 4 nc ld + 8 nc
       bicg_vec     BiCGStab vector kernels, averaged over dir (64 N), s (52 N), and
                    the solution/residual update with its dots (96 N), for D = 3
       assemble     convecting velocity per dof (u^{n-1}, u^{n-2} read, ubar written: 60 N),
@@ -123,17 +126,40 @@ def family_bytes(pb, nnz, args, tuning, amg):
                 else "k_amg_fine<float> (finest-level damped-Jacobi sweep on SELL-32, bfloat16 K)")
         out["amg_fine"] = (fine, (2 + cb) * Z + 16 * N + 8 * n_slices, f"(2+{cb}) Z + 16 N + 8 N/32")
         rows, nz, pn = amg["rows"], amg["nnz"], amg["p_nnz"]
+        packed = amg.get("packed") or [0] * len(pn)
         L = amg["levels"]
         if pn:
-            tb = sum(12 * pn[l] + 16 * rows[l] + 12 * rows[l + 1] for l in range(len(pn)))
-            out["amg_transfer"] = ("k_amg_restrict / k_amg_prolong (CSR, bfloat16 values, every level)",
-                                   tb / (2 * len(pn)),
-                                   "per V-cycle sum_l 12 nnz(P_l) + 16 n_l + 12 n_(l+1), over 2(L-1) launches")
+            # restriction: entries, R's row pointers (CSR) or slice headers (packed), the
+            # fine residual gathered, the coarse vector written; prolongation: entries,
+            # P's row pointers or slice headers, the coarse vector gathered, the fine
+            # iterate read and written
+            # (a packed copy with 32-bit columns reads 6 bytes per entry, as CSR does)
+            def restrict_b(l):
+                eb = 6 if packed[l] & 16 else 4
+                return (eb * pn[l] + 4 * rows[l] + 4.5 * rows[l + 1] if packed[l] & 2
+                        else 6 * pn[l] + 4 * rows[l] + 8 * rows[l + 1])
+
+            def prolong_b(l):
+                eb = 6 if packed[l] & 32 else 4
+                return (eb * pn[l] + 8.5 * rows[l] + 4 * rows[l + 1] if packed[l] & 4
+                        else 6 * pn[l] + 12 * rows[l] + 4 * rows[l + 1])
+            tb = sum(restrict_b(l) + prolong_b(l) for l in range(len(pn)))
+            out["amg_transfer"] = ("k_amg_restrict / k_amg_prolong (CSR) and k_amg_sellp (pair-packed SELL-32), "
+                                   "bfloat16 values, every level", tb / (2 * len(pn)),
+                                   "per V-cycle sum_l: restriction 6 nnz(P_l) + 4 n_l + 8 n_(l+1) (CSR) or "
+                                   "4 nnz(P_l) + 4 n_l + 4.5 n_(l+1) (packed); prolongation 6 nnz(P_l) + 12 n_l "
+                                   "+ 4 n_(l+1) or 4 nnz(P_l) + 8.5 n_l + 4 n_(l+1); over 2(L-1) launches")
         nc = rows[L - 1]
         ld = (nc + 3) // 4 * 4
-        cbytes = sum(2 * (6 * nz[l] + 20 * rows[l]) for l in range(1, L - 1)) + 4 * nc * ld + 8 * nc
-        out["amg_coarse"] = ("k_amg_pre / k_amg_post (CSR, bfloat16 values, levels >= 1) and k_amg_dense",
-                             cbytes / (2 * (L - 2) + 1), "per V-cycle sum_l 2 (6 nnz_l + 20 n_l) + 4 nc ld + 8 nc, "
+
+        def sweep_b(l):
+            eb = 6 if packed[l] & 8 else 4
+            return eb * nz[l] + 16.5 * rows[l] if packed[l] & 1 else 6 * nz[l] + 20 * rows[l]
+        cbytes = sum(2 * sweep_b(l) for l in range(1, L - 1)) + 4 * nc * ld + 8 * nc
+        out["amg_coarse"] = ("k_amg_pre / k_amg_post (CSR) and k_amg_sellp (pair-packed SELL-32), bfloat16 values, "
+                             "levels >= 1, and k_amg_dense",
+                             cbytes / (2 * (L - 2) + 1), "per V-cycle sum_l 2 (6 nnz_l + 20 n_l) (CSR) or "
+                                                         "2 (4 nnz_l + 16.5 n_l) (packed) + 4 nc ld + 8 nc, "
                                                          "over 2(L-2)+1 launches")
     bcs = tuning.get("bicg_candidates")
     bc = bcs[tuning["bicg_chosen"] - 1] if bcs else {"lanes": 0}

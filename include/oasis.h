@@ -434,6 +434,12 @@ typedef struct oasis_amg_info {
     int64_t p_nnz[16];             /* entries of the prolongation from level k+1 to level k
                                       (k < levels - 1); its transpose, the restriction, has
                                       as many */
+    int32_t packed[16];            /* operators of level k that the float32 cycle reads in
+                                      pair-packed SELL-32 form (bfloat16 values, 16-bit
+                                      column offsets) instead of CSR: bit 0 the level's
+                                      matrix, bit 1 the restriction to level k+1, bit 2 the
+                                      prolongation from it; bits 3, 4, 5: that copy keeps
+                                      32-bit columns (its columns spread too far) */
 } oasis_amg_info;
 int oasis_get_amg_info(const oasis_solver* s, oasis_amg_info* out);
 

@@ -53,7 +53,7 @@ class oasis_params(C.Structure):
 
 class oasis_amg_info(C.Structure):
     _fields_ = [("levels", C.c_int32), ("rows", C.c_int64 * 16), ("nnz", C.c_int64 * 16),
-                ("setup_s", C.c_double), ("p_nnz", C.c_int64 * 16)]
+                ("setup_s", C.c_double), ("p_nnz", C.c_int64 * 16), ("packed", C.c_int32 * 16)]
 
 
 class oasis_tuning(C.Structure):
@@ -426,7 +426,8 @@ def oasis_get_amg_info(solver):
     t = oasis_amg_info()
     check(lib().oasis_get_amg_info(solver, C.byref(t)))
     return {"levels": t.levels, "rows": list(t.rows[:t.levels]), "nnz": list(t.nnz[:t.levels]),
-            "setup_s": t.setup_s, "p_nnz": list(t.p_nnz[:max(0, t.levels - 1)])}
+            "setup_s": t.setup_s, "p_nnz": list(t.p_nnz[:max(0, t.levels - 1)]),
+            "packed": list(t.packed[:max(0, t.levels - 1)])}
 
 
 def oasis_amg_apply(solver, r, u, stream=None):

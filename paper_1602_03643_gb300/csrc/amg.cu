@@ -346,6 +346,69 @@ void upload_csr(DBuf<int32_t>& rp, DBuf<int32_t>& ci, DBuf<double>& v64, DBuf<ui
     OASIS_CUDA(cudaStreamSynchronize(s));
 }
 
+// Pair-packed SELL-32 copy of A for the float32 cycle (layout in amg.cuh), if A
+// has at least kSellMinRows rows; otherwise `out` stays empty.  The copy is wide
+// (32-bit columns) if some slice's columns span 2^16 values or more.  Entries
+// keep their CSR order within a row, so a row's products are added in the same
+// order as in CSR.
+void build_sellp(const HCsr& A, AmgSellP& out, cudaStream_t s) {
+    if (A.n < kSellMinRows) return;
+    const int64_t ns = (A.n + 31) / 32;
+    std::vector<int4> hdr(ns);
+    int64_t words = 0;
+    bool wide = false;
+    for (int64_t sl = 0; sl < ns; ++sl) {
+        int64_t maxlen = 0;
+        int32_t lo = INT32_MAX, hi = -1;
+        for (int64_t i = sl * 32; i < std::min<int64_t>(A.n, sl * 32 + 32); ++i) {
+            maxlen = std::max<int64_t>(maxlen, A.rp[i + 1] - A.rp[i]);
+            for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+                lo = std::min(lo, A.ci[q]);
+                hi = std::max(hi, A.ci[q]);
+            }
+        }
+        if (hi < 0) lo = hi = 0;
+        wide |= (int64_t)hi - (int64_t)lo > 65535;
+        const int64_t w = (maxlen + 1) / 2;
+        hdr[sl] = make_int4((int)words, (int)w, lo, 0);
+        words += 32 * w;
+        if (words >= INT32_MAX) return;
+    }
+    if (wide)
+        for (auto& h : hdr) h.z = 0;
+    const size_t nw = (size_t)std::max<int64_t>(words, 1);
+    std::vector<uint32_t> vp(nw, 0u), cp(wide ? 0 : nw, 0u);
+    std::vector<uint2> cw(wide ? nw : 0, make_uint2(0u, 0u));
+    double mean_w = 0.0;
+    for (int64_t sl = 0; sl < ns; ++sl) {
+        mean_w += hdr[sl].y;
+        for (int l = 0; l < 32; ++l) {
+            const int64_t i = sl * 32 + l;
+            if (i >= A.n) break;
+            for (int64_t k = 0; k < A.rp[i + 1] - A.rp[i]; ++k) {
+                const int64_t q = A.rp[i] + k;
+                const size_t o = (size_t)hdr[sl].x + 32 * (size_t)(k >> 1) + (size_t)l;
+                const int sh = (int)(k & 1) * 16;
+                vp[o] |= (uint32_t)bf16_bits((float)A.v[q]) << sh;
+                if (wide)
+                    ((k & 1) ? cw[o].y : cw[o].x) = (uint32_t)A.ci[q];
+                else
+                    cp[o] |= (uint32_t)(A.ci[q] - hdr[sl].z) << sh;
+            }
+        }
+    }
+    mean_w /= (double)ns;
+    upload_vec(out.hdr, hdr, s);
+    upload_vec(out.vp, vp, s);
+    if (wide) upload_vec(out.cw, cw, s);
+    else upload_vec(out.cp, cp, s);
+    OASIS_CUDA(cudaStreamSynchronize(s));
+    out.n = A.n;
+    out.n_slices = ns;
+    out.wide = wide;
+    out.c2 = mean_w >= 12.0 ? 8 : 4;
+}
+
 // bfloat16 bit patterns of float values, round to nearest even
 __global__ void k_round_bf16(int64_t n, const float* __restrict__ in, uint16_t* __restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -459,6 +522,7 @@ void amg_build(Mesh& m, cudaStream_t s) {
             L->ci = L->own_ci.p;
             L->a64 = L->own_a64.p;
             L->a16 = L->own_a16.p;
+            build_sellp(A, L->sa, s);
         }
         h->sizes.push_back(A.n);
         h->nnzs.push_back(A.nnz());
@@ -478,6 +542,8 @@ void amg_build(Mesh& m, cudaStream_t s) {
         h->pnnzs.push_back(P.nnz());
         upload_csr(L->p_rp, L->p_ci, L->p64, L->p16, P, s);
         upload_csr(L->r_rp, L->r_ci, L->r64, L->r16, R, s);
+        build_sellp(R, L->sr, s);
+        build_sellp(P, L->sp, s);
         auto lanes = [](int64_t nnz, int64_t rows) {
             const double mean = rows ? (double)nnz / (double)rows : 1.0;
             int g = 4;
@@ -805,6 +871,80 @@ __global__ void __launch_bounds__(kBlock) k_amg_fine_pairs(AmgSellView F, const 
     }
 }
 
+// A pair-packed SELL-32 operator of the float32 cycle (AmgSellP) as the kernels
+// see it.
+struct SellPView {
+    int64_t n, n_slices;
+    const int4* __restrict__ hdr;
+    const uint32_t* __restrict__ vp;
+    const uint32_t* __restrict__ cp;
+    const uint2* __restrict__ cw;
+};
+
+// Row kernels of the float32 cycle on a pair-packed SELL-32 operator, the modes
+// of amg_rows (pre: x = w D^-1 r, res = r - A x; post: out = src + w D^-1 (r - A src);
+// prolong: out += P src; restrict: out = R src).  One warp per slice; per round
+// C2 words of values and C2 of offsets (W: C2 pairs of whole columns) per lane
+// (2 C2 entries) are loaded, then their 2 C2 gathers; products are added in
+// entry order.
+template <int MODE, int C2, bool W>
+__global__ void __launch_bounds__(kBlock) k_amg_sellp(SellPView S, const float* __restrict__ d, float w,
+                                                      const float* __restrict__ r, const float* __restrict__ src,
+                                                      float* __restrict__ out, float* __restrict__ res,
+                                                      const KrylovState* st) {
+    if (amg_done(st)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = w0; sl < S.n_slices; sl += nw) {
+        const int4 h = S.hdr[sl];
+        const int64_t i = sl * 32 + lane;
+        const uint32_t base = (uint32_t)h.x + (uint32_t)lane;
+        float sum = 0.f;
+        for (int k = 0; k < h.y; k += C2) {
+            uint32_t vw[C2];
+            uint2 cw[C2];
+#pragma unroll
+            for (int u = 0; u < C2; ++u) {
+                const uint32_t q = base + 32u * (uint32_t)(k + u);
+                const bool ok = k + u < h.y;
+                vw[u] = ok ? S.vp[q] : 0u;
+                if constexpr (W) {
+                    cw[u] = ok ? S.cw[q] : make_uint2(0u, 0u);
+                } else {
+                    const uint32_t c = ok ? S.cp[q] : 0u;
+                    cw[u] = make_uint2(c & 0xFFFFu, c >> 16);
+                }
+            }
+            float g[2 * C2];
+#pragma unroll
+            for (int e = 0; e < 2 * C2; ++e) {
+                const int32_t j = h.z + (int32_t)((e & 1) ? cw[e >> 1].y : cw[e >> 1].x);
+                if constexpr (MODE == kRowPre) g[e] = w * d[j] * r[j];
+                else g[e] = src[j];
+            }
+#pragma unroll
+            for (int u = 0; u < C2; ++u)
+                if (k + u < h.y) {
+                    sum += __uint_as_float(vw[u] << 16) * g[2 * u];
+                    sum += __uint_as_float(vw[u] & 0xFFFF0000u) * g[2 * u + 1];
+                }
+        }
+        if (i < S.n) {
+            if constexpr (MODE == kRowPre) {
+                res[i] = r[i] - sum;
+                out[i] = w * d[i] * r[i];
+            } else if constexpr (MODE == kRowPost) {
+                out[i] = src[i] + w * d[i] * (r[i] - sum);
+            } else if constexpr (MODE == kRowProlong) {
+                out[i] = out[i] + sum;
+            } else {
+                out[i] = sum;
+            }
+        }
+    }
+}
+
 // coarsest level: x = inv r with inv dense and row-major, leading dimension ld
 // (a multiple of 4, zero-padded) and r zero-padded to ld; one block of 128
 // threads per row, 16-byte loads (float4 / double2), the block's sum in a fixed
@@ -898,6 +1038,30 @@ void launch_fine(const AmgSellView& F, const V* d, V w, const V* r, const V* x, 
             F, av, d, w, r, x, out, res, st);
 }
 
+// one float32-cycle row kernel on a pair-packed SELL-32 operator: one warp per
+// slice at a time, one resident wave
+template <int MODE, int C2, bool W>
+void launch_sellp_c(const SellPView& v, const float* d, float w, const float* r, const float* src, float* out,
+                    float* res, const KrylovState* st, cudaStream_t s) {
+    const int64_t want = (v.n_slices + kBlock / 32 - 1) / (kBlock / 32);
+    const int per_sm = resident_blocks((const void*)k_amg_sellp<MODE, C2, W>);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * per_sm));
+    k_amg_sellp<MODE, C2, W><<<grid, kBlock, 0, s>>>(v, d, w, r, src, out, res, st);
+}
+
+template <int MODE>
+void launch_sellp(const AmgSellP& A, const float* d, float w, const float* r, const float* src, float* out,
+                  float* res, const KrylovState* st, cudaStream_t s) {
+    const SellPView v{A.n, A.n_slices, A.hdr.p, A.vp.p, A.cp.p, A.cw.p};
+    if (A.wide) {
+        if (A.c2 == 8) launch_sellp_c<MODE, 8, true>(v, d, w, r, src, out, res, st, s);
+        else launch_sellp_c<MODE, 4, true>(v, d, w, r, src, out, res, st, s);
+    } else {
+        if (A.c2 == 8) launch_sellp_c<MODE, 8, false>(v, d, w, r, src, out, res, st, s);
+        else launch_sellp_c<MODE, 4, false>(v, d, w, r, src, out, res, st, s);
+    }
+}
+
 }  // namespace
 
 // Launch a row kernel with G lanes per row, G chosen at run time.
@@ -915,6 +1079,8 @@ template <class V>
 void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const KrylovState* st, cudaStream_t s,
                 const ProfHook* prof) {
     const int L = (int)h.lv.size();
+    // the pair-packed copies serve the float32 cycle only
+    auto sellp_ok = [](const AmgSellP& A) { return sizeof(V) == 4 && A.n > 0; };
     int ph = -1;
     auto pbeg = [&](int family) {
         if (prof && prof->begin) ph = prof->begin(prof->ctx, s, family);
@@ -938,16 +1104,28 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
             pend();
         } else {
             pbeg(OASIS_PROF_AMG_COARSE);
-            AmgRowArgs<V, AV> ra{lv.n, lv.rp, lv.ci, a, d, w, rin(l), nullptr, nullptr, vec(wk.x[l]), vec(wk.res[l]), st};
-            AMG_DISPATCH(lv.g_a, k_amg_pre, lv.n, ra);
+            if (sellp_ok(lv.sa)) {
+                if constexpr (sizeof(V) == 4)
+                    launch_sellp<kRowPre>(lv.sa, d, w, rin(l), nullptr, vec(wk.x[l]), vec(wk.res[l]), st, s);
+            } else {
+                AmgRowArgs<V, AV> ra{lv.n, lv.rp, lv.ci, a, d, w, rin(l), nullptr, nullptr, vec(wk.x[l]),
+                                     vec(wk.res[l]), st};
+                AMG_DISPATCH(lv.g_a, k_amg_pre, lv.n, ra);
+            }
             pend();
         }
         const int64_t nc = l + 1 < L ? h.lv[l + 1]->n : h.nc;
         const AV* rv = stored<V>(lv.r16.p, lv.r64.p);
         pbeg(OASIS_PROF_AMG_TRANSFER);
-        AmgRowArgs<V, AV> rr{nc, lv.r_rp.p, lv.r_ci.p, rv, nullptr, V(0), nullptr, nullptr, vec(wk.res[l]),
-                         vec(wk.rin[l + 1]), nullptr, st};
-        AMG_DISPATCH(lv.g_r, k_amg_restrict, nc, rr);
+        if (sellp_ok(lv.sr)) {
+            if constexpr (sizeof(V) == 4)
+                launch_sellp<kRowRestrict>(lv.sr, nullptr, 0.f, nullptr, vec(wk.res[l]), vec(wk.rin[l + 1]), nullptr,
+                                           st, s);
+        } else {
+            AmgRowArgs<V, AV> rr{nc, lv.r_rp.p, lv.r_ci.p, rv, nullptr, V(0), nullptr, nullptr, vec(wk.res[l]),
+                                 vec(wk.rin[l + 1]), nullptr, st};
+            AMG_DISPATCH(lv.g_r, k_amg_restrict, nc, rr);
+        }
         pend();
     }
     pbeg(OASIS_PROF_AMG_COARSE);
@@ -962,9 +1140,14 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
         const V w = (V)lv.omega;
         const AV* pv = stored<V>(lv.p16.p, lv.p64.p);
         pbeg(OASIS_PROF_AMG_TRANSFER);
-        AmgRowArgs<V, AV> pr{lv.n, lv.p_rp.p, lv.p_ci.p, pv, nullptr, V(0), nullptr, nullptr, xo(l + 1), vec(wk.x[l]),
-                         nullptr, st};
-        AMG_DISPATCH(lv.g_p, k_amg_prolong, lv.n, pr);
+        if (sellp_ok(lv.sp)) {
+            if constexpr (sizeof(V) == 4)
+                launch_sellp<kRowProlong>(lv.sp, nullptr, 0.f, nullptr, xo(l + 1), vec(wk.x[l]), nullptr, st, s);
+        } else {
+            AmgRowArgs<V, AV> pr{lv.n, lv.p_rp.p, lv.p_ci.p, pv, nullptr, V(0), nullptr, nullptr, xo(l + 1),
+                                 vec(wk.x[l]), nullptr, st};
+            AMG_DISPATCH(lv.g_p, k_amg_prolong, lv.n, pr);
+        }
         pend();
         if (l == 0) {
             pbeg(OASIS_PROF_AMG_FINE);
@@ -972,8 +1155,13 @@ void amg_vcycle(const AmgHierarchy& h, AmgWork& wk, const V* r, V* u, const Kryl
             pend();
         } else {
             pbeg(OASIS_PROF_AMG_COARSE);
-            AmgRowArgs<V, AV> po{lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]), nullptr, xo(l), nullptr, st};
-            AMG_DISPATCH(lv.g_a, k_amg_post, lv.n, po);
+            if (sellp_ok(lv.sa)) {
+                if constexpr (sizeof(V) == 4)
+                    launch_sellp<kRowPost>(lv.sa, d, w, rin(l), vec(wk.x[l]), xo(l), nullptr, st, s);
+            } else {
+                AmgRowArgs<V, AV> po{lv.n, lv.rp, lv.ci, a, d, w, rin(l), vec(wk.x[l]), nullptr, xo(l), nullptr, st};
+                AMG_DISPATCH(lv.g_a, k_amg_post, lv.n, po);
+            }
             pend();
         }
     }

@@ -17,7 +17,9 @@
 // The V(1,1) cycle uses one damped-Jacobi sweep (w_s = 4 / (3 rho(D^-1 A)))
 // before and after the coarse correction, with restriction P^T: a symmetric
 // positive semi-definite preconditioner, as CG requires.  The finest level's
-// sweeps read K in the mesh's SELL-32 layout; coarser levels are CSR.
+// sweeps read K in the mesh's SELL-32 layout; coarser levels and the transfers
+// are CSR, and the float32 cycle reads a pair-packed SELL-32 copy of each of
+// them that is large enough (AmgSellP; 16-bit column offsets where they fit).
 #pragma once
 
 #include <memory>
@@ -25,6 +27,24 @@
 #include "internal.cuh"
 
 namespace oasis {
+
+// Pair-packed SELL-32 copy of a CSR operator of the float32 cycle (a coarser
+// level's matrix, a restriction or a prolongation): rows in slices of 32, lane l
+// of slice s owns row 32 s + l; hdr[s] = {word offset, words per lane, base
+// column, 0}; entries 2k and 2k + 1 of lane l sit in the 32-bit word at
+// hdr[s].x + 32 k + l, as two bfloat16 values in vp (low half: entry 2k) and two
+// 16-bit offsets from the slice's base column in cp.  Padding entries carry value
+// 0 and offset 0 (column = base, a valid row of the operand).  Where some
+// slice's columns spread over 2^16 or more values, the copy is wide: the two
+// columns of word w are stored whole in cw[w] (base 0), cp is empty.
+struct AmgSellP {
+    int64_t n = 0, n_slices = 0;
+    int c2 = 4;                        // words per lane loaded per round
+    bool wide = false;
+    DBuf<int4> hdr;
+    DBuf<uint32_t> vp, cp;
+    DBuf<uint2> cw;
+};
 
 struct AmgLevelDev {
     int64_t n = 0, nnz = 0;
@@ -44,7 +64,13 @@ struct AmgLevelDev {
     DBuf<int32_t> p_rp, p_ci, r_rp, r_ci;
     DBuf<double> p64, r64;
     DBuf<uint16_t> p16, r16;
+    // pair-packed SELL-32 copies for the float32 cycle of this level's operator
+    // (levels >= 1), of R and of P, where the operator has at least
+    // kSellMinRows rows (n = 0: the CSR kernels serve)
+    AmgSellP sa, sr, sp;
 };
+
+constexpr int64_t kSellMinRows = 65536;
 
 // SELL-32 view of the finest operator (the mesh's K): the fine-level smoothers
 // read it with one lane per row, coalesced column/value loads, and 16-bit column

@@ -843,6 +843,11 @@ int oasis_get_amg_info(const oasis_solver* solver, oasis_amg_info* out) {
             out->rows[k] = h.sizes[k];
             out->nnz[k] = h.nnzs[k];
             out->p_nnz[k] = k < (int)h.pnnzs.size() ? h.pnnzs[k] : 0;
+            if (k < (int)h.lv.size()) {
+                const AmgLevelDev& lv = *h.lv[k];
+                out->packed[k] = (lv.sa.n > 0 ? 1 : 0) | (lv.sr.n > 0 ? 2 : 0) | (lv.sp.n > 0 ? 4 : 0) |
+                                 (lv.sa.wide ? 8 : 0) | (lv.sr.wide ? 16 : 0) | (lv.sp.wide ? 32 : 0);
+            }
         }
         out->setup_s = h.setup_s;
     });

@@ -86,3 +86,12 @@ def test_family_bytes_model_on_a_small_mesh():
     # without 16-bit columns the column bytes are 4 per entry
     f32 = bench.family_bytes(pb, Z, None, {"candidates": [{"col16": 0, "us": 1.0}]}, amg)
     assert f32["pcg_spmv"][1] - f["pcg_spmv"][1] == 2 * Z
+    # pair-packed level-1 matrix and level-0 transfers: 4 bytes per entry, slice headers
+    fp = bench.family_bytes(pb, Z, None, tuning, dict(amg, packed=[6, 1]))
+    want_tp = (8 * 300 + 12.5 * N + 8.5 * 20) + (12 * 40 + 16 * 20 + 12 * 3)
+    assert abs(fp["amg_transfer"][1] - want_tp / 4) < 1e-9
+    want_cp = 2 * (4 * 200 + 16.5 * 20) + 4 * 3 * 4 + 8 * 3
+    assert abs(fp["amg_coarse"][1] - want_cp / 3) < 1e-9
+    # a packed restriction that keeps 32-bit columns: 6 bytes per entry
+    fw = bench.family_bytes(pb, Z, None, tuning, dict(amg, packed=[6 | 16, 1]))
+    assert abs((fw["amg_transfer"][1] - fp["amg_transfer"][1]) * 4 - 2 * 300) < 1e-9

@@ -110,6 +110,48 @@ def test_float32_vcycle_symmetric_and_close_to_float64(name):
     assert 1e-9 < relerr(w, w64) <= 2e-2
 
 
+@pytest.mark.parametrize("n,ordering", [(90, "rcm"), (96, "random")])
+def test_float32_vcycle_on_packed_operators(n, ordering):
+    """Meshes large enough that the float32 cycle reads its level-1 matrix and
+    the level-0 transfers in pair-packed SELL-32 form (16-bit column offsets in
+    RCM order, whole 32-bit columns in random order, where columns spread over
+    the whole level): the cycle stays symmetric and positive to float32 rounding
+    and within bfloat16's few digits of the float64 cycle (CSR, never packed)."""
+    import torch
+    c = capi()
+    pb = WP.stress_cube(n, ordering=ordering)
+    rng = np.random.default_rng(7)
+    x = rng.normal(size=pb.mesh.n_dofs)
+    y = rng.normal(size=pb.mesh.n_dofs)
+    x -= x.mean()
+    y -= y.mean()
+    out = {}
+    for prec, dt in ((c.OASIS_FP64, torch.float64), (c.OASIS_MIXED, torch.float32)):
+        run = _run(pb, prec, c.OASIS_PC_AMG)
+        try:
+            info = c.oasis_get_amg_info(run.solver)
+            X, Y = torch.from_numpy(x).to(dt).cuda(), torch.from_numpy(y).to(dt).cuda()
+            U, W = torch.empty_like(X), torch.empty_like(Y)
+            c.oasis_amg_apply(run.solver, X, U)
+            c.oasis_amg_apply(run.solver, Y, W)
+            out[prec] = (U.double().cpu().numpy(), W.double().cpu().numpy())
+        finally:
+            run.close()
+    packed = info["packed"]
+    # level 0: restriction and prolongation packed; level 1: its matrix packed
+    assert packed[0] & 6 == 6 and packed[1] & 1, packed
+    if ordering == "random":
+        assert packed[0] & 48 == 48 and packed[1] & 8, packed      # 32-bit columns
+    else:
+        assert packed[0] & 32 == 0 and packed[1] & 8 == 0, packed  # 16-bit offsets
+    u, w = out[c.OASIS_MIXED]
+    assert abs(x @ w - y @ u) <= 2e-6 * np.sqrt((x @ u) * (y @ w))
+    assert x @ u > 0 and y @ w > 0
+    u64, w64 = out[c.OASIS_FP64]
+    assert 1e-9 < relerr(u, u64) <= 2e-2
+    assert 1e-9 < relerr(w, w64) <= 2e-2
+
+
 @pytest.mark.parametrize("name", list(PROBLEMS))
 def test_amg_steps_match_oracle_fp64(name):
     c = capi()
