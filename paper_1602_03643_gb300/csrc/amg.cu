@@ -406,7 +406,12 @@ void build_sellp(const HCsr& A, AmgSellP& out, cudaStream_t s) {
     out.n = A.n;
     out.n_slices = ns;
     out.wide = wide;
-    out.c2 = mean_w >= 12.0 ? 8 : 4;
+    // warps per slice: enough slices x warps to fill ~2 resident waves (64 warps
+    // per SM), while every warp keeps at least one full round of C2 = 4 words
+    int sp = 1;
+    while (sp < 4 && (double)ns * sp < 2.0 * num_sms() * 64 && mean_w >= 4.0 * 2 * sp) sp *= 2;
+    out.sp = sp;
+    out.c2 = sp > 1 ? 4 : (mean_w >= 12.0 ? 8 : 4);
 }
 
 // bfloat16 bit patterns of float values, round to nearest even
@@ -883,54 +888,74 @@ struct SellPView {
 
 // Row kernels of the float32 cycle on a pair-packed SELL-32 operator, the modes
 // of amg_rows (pre: x = w D^-1 r, res = r - A x; post: out = src + w D^-1 (r - A src);
-// prolong: out += P src; restrict: out = R src).  One warp per slice; per round
-// C2 words of values and C2 of offsets (W: C2 pairs of whole columns) per lane
-// (2 C2 entries) are loaded, then their 2 C2 gathers; products are added in
-// entry order.
-template <int MODE, int C2, bool W>
+// prolong: out += P src; restrict: out = R src).  SP warps serve one slice: warp
+// p of the slice takes the rounds p, p + SP, ... of C2 words each; per round it
+// loads C2 words of values and C2 of offsets (W: C2 pairs of whole columns) per
+// lane (2 C2 entries), then their 2 C2 gathers, and adds the products in entry
+// order.  With SP > 1 the partial sums meet in shared memory and the slice's
+// first warp adds them in warp order.  (A level of 250k rows is only ~7,800
+// slices: one warp per slice leaves half the SM's warp slots empty and every
+// warp a long chain of dependent loads.)
+template <int MODE, int C2, bool W, int SP>
 __global__ void __launch_bounds__(kBlock) k_amg_sellp(SellPView S, const float* __restrict__ d, float w,
                                                       const float* __restrict__ r, const float* __restrict__ src,
                                                       float* __restrict__ out, float* __restrict__ res,
                                                       const KrylovState* st) {
     if (amg_done(st)) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t sl = w0; sl < S.n_slices; sl += nw) {
-        const int4 h = S.hdr[sl];
-        const int64_t i = sl * 32 + lane;
-        const uint32_t base = (uint32_t)h.x + (uint32_t)lane;
+    constexpr int kWarps = kBlock / 32, kSlices = kWarps / SP;
+    static_assert(kWarps % SP == 0, "warps per slice must divide the block's warps");
+    __shared__ float part[SP > 1 ? kWarps : 1][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int sub = wib % SP, ls = wib / SP;
+    const int64_t groups = (S.n_slices + kSlices - 1) / kSlices;
+    for (int64_t gi = blockIdx.x; gi < groups; gi += gridDim.x) {     // uniform over the block
+        const int64_t sl = gi * kSlices + ls;
         float sum = 0.f;
-        for (int k = 0; k < h.y; k += C2) {
-            uint32_t vw[C2];
-            uint2 cw[C2];
+        if (sl < S.n_slices) {
+            const int4 h = S.hdr[sl];
+            const uint32_t base = (uint32_t)h.x + (uint32_t)lane;
+            for (int k = sub * C2; k < h.y; k += SP * C2) {
+                uint32_t vw[C2];
+                uint2 cw[C2];
 #pragma unroll
-            for (int u = 0; u < C2; ++u) {
-                const uint32_t q = base + 32u * (uint32_t)(k + u);
-                const bool ok = k + u < h.y;
-                vw[u] = ok ? S.vp[q] : 0u;
-                if constexpr (W) {
-                    cw[u] = ok ? S.cw[q] : make_uint2(0u, 0u);
-                } else {
-                    const uint32_t c = ok ? S.cp[q] : 0u;
-                    cw[u] = make_uint2(c & 0xFFFFu, c >> 16);
+                for (int u = 0; u < C2; ++u) {
+                    const uint32_t q = base + 32u * (uint32_t)(k + u);
+                    const bool ok = k + u < h.y;
+                    vw[u] = ok ? S.vp[q] : 0u;
+                    if constexpr (W) {
+                        cw[u] = ok ? S.cw[q] : make_uint2(0u, 0u);
+                    } else {
+                        const uint32_t c = ok ? S.cp[q] : 0u;
+                        cw[u] = make_uint2(c & 0xFFFFu, c >> 16);
+                    }
                 }
-            }
-            float g[2 * C2];
+                float g[2 * C2];
 #pragma unroll
-            for (int e = 0; e < 2 * C2; ++e) {
-                const int32_t j = h.z + (int32_t)((e & 1) ? cw[e >> 1].y : cw[e >> 1].x);
-                if constexpr (MODE == kRowPre) g[e] = w * d[j] * r[j];
-                else g[e] = src[j];
-            }
-#pragma unroll
-            for (int u = 0; u < C2; ++u)
-                if (k + u < h.y) {
-                    sum += __uint_as_float(vw[u] << 16) * g[2 * u];
-                    sum += __uint_as_float(vw[u] & 0xFFFF0000u) * g[2 * u + 1];
+                for (int e = 0; e < 2 * C2; ++e) {
+                    const int32_t j = h.z + (int32_t)((e & 1) ? cw[e >> 1].y : cw[e >> 1].x);
+                    if constexpr (MODE == kRowPre) g[e] = w * d[j] * r[j];
+                    else g[e] = src[j];
                 }
+#pragma unroll
+                for (int u = 0; u < C2; ++u)
+                    if (k + u < h.y) {
+                        sum += __uint_as_float(vw[u] << 16) * g[2 * u];
+                        sum += __uint_as_float(vw[u] & 0xFFFF0000u) * g[2 * u + 1];
+                    }
+            }
         }
-        if (i < S.n) {
+        if constexpr (SP > 1) {
+            part[wib][lane] = sum;
+            __syncthreads();
+            if (sub == 0) {
+                sum = part[wib][lane];
+#pragma unroll
+                for (int p = 1; p < SP; ++p) sum += part[wib + p][lane];
+            }
+            __syncthreads();
+        }
+        const int64_t i = sl * 32 + lane;
+        if (sub == 0 && sl < S.n_slices && i < S.n) {
             if constexpr (MODE == kRowPre) {
                 res[i] = r[i] - sum;
                 out[i] = w * d[i] * r[i];
@@ -1040,26 +1065,33 @@ void launch_fine(const AmgSellView& F, const V* d, V w, const V* r, const V* x, 
 
 // one float32-cycle row kernel on a pair-packed SELL-32 operator: one warp per
 // slice at a time, one resident wave
-template <int MODE, int C2, bool W>
+template <int MODE, int C2, bool W, int SP>
 void launch_sellp_c(const SellPView& v, const float* d, float w, const float* r, const float* src, float* out,
                     float* res, const KrylovState* st, cudaStream_t s) {
-    const int64_t want = (v.n_slices + kBlock / 32 - 1) / (kBlock / 32);
-    const int per_sm = resident_blocks((const void*)k_amg_sellp<MODE, C2, W>);
+    constexpr int kSlices = kBlock / 32 / SP;
+    const int64_t want = (v.n_slices + kSlices - 1) / kSlices;
+    const int per_sm = resident_blocks((const void*)k_amg_sellp<MODE, C2, W, SP>);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * per_sm));
-    k_amg_sellp<MODE, C2, W><<<grid, kBlock, 0, s>>>(v, d, w, r, src, out, res, st);
+    k_amg_sellp<MODE, C2, W, SP><<<grid, kBlock, 0, s>>>(v, d, w, r, src, out, res, st);
+}
+
+template <int MODE, bool W>
+void launch_sellp_w(const AmgSellP& A, const SellPView& v, const float* d, float w, const float* r, const float* src,
+                    float* out, float* res, const KrylovState* st, cudaStream_t s) {
+    switch (A.sp * 16 + A.c2) {
+        case 4 * 16 + 4: launch_sellp_c<MODE, 4, W, 4>(v, d, w, r, src, out, res, st, s); break;
+        case 2 * 16 + 4: launch_sellp_c<MODE, 4, W, 2>(v, d, w, r, src, out, res, st, s); break;
+        case 1 * 16 + 8: launch_sellp_c<MODE, 8, W, 1>(v, d, w, r, src, out, res, st, s); break;
+        default: launch_sellp_c<MODE, 4, W, 1>(v, d, w, r, src, out, res, st, s); break;
+    }
 }
 
 template <int MODE>
 void launch_sellp(const AmgSellP& A, const float* d, float w, const float* r, const float* src, float* out,
                   float* res, const KrylovState* st, cudaStream_t s) {
     const SellPView v{A.n, A.n_slices, A.hdr.p, A.vp.p, A.cp.p, A.cw.p};
-    if (A.wide) {
-        if (A.c2 == 8) launch_sellp_c<MODE, 8, true>(v, d, w, r, src, out, res, st, s);
-        else launch_sellp_c<MODE, 4, true>(v, d, w, r, src, out, res, st, s);
-    } else {
-        if (A.c2 == 8) launch_sellp_c<MODE, 8, false>(v, d, w, r, src, out, res, st, s);
-        else launch_sellp_c<MODE, 4, false>(v, d, w, r, src, out, res, st, s);
-    }
+    if (A.wide) launch_sellp_w<MODE, true>(A, v, d, w, r, src, out, res, st, s);
+    else launch_sellp_w<MODE, false>(A, v, d, w, r, src, out, res, st, s);
 }
 
 }  // namespace

@@ -40,6 +40,7 @@ namespace oasis {
 struct AmgSellP {
     int64_t n = 0, n_slices = 0;
     int c2 = 4;                        // words per lane loaded per round
+    int sp = 1;                        // warps serving one slice (1, 2 or 4)
     bool wide = false;
     DBuf<int4> hdr;
     DBuf<uint32_t> vp, cp;
