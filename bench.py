@@ -89,8 +89,9 @@ def family_bytes(pb, nnz, args, tuning, amg):
       pcg_spmv     multigrid CG product w = K u on SELL-32 + 3 dots: K values and
                    columns (16-bit offsets where the mesh has them), u gathered, r read,
                    w written, slice pointers/lengths
-      bicg_spmm    d-RHS product of the BiCGStab: A values + columns, row pointers,
-                   x gathered, y written, the dot operand read
+      bicg_spmm    d-RHS product of the BiCGStab: A values + columns (int32, or 16-bit
+                   offsets for a col16 shape), row pointers, x gathered, y written, the
+                   dot operand read
       amg_fine     finest-level smoothing sweep (pre or post, SELL-32): K values as
                    bfloat16 + columns, 4 vectors of N, slice pointers/lengths
       amg_transfer restriction/prolongation (bfloat16 values), averaged over the 2(L-1)
@@ -163,13 +164,15 @@ def family_bytes(pb, nnz, args, tuning, amg):
                                                          "over 2(L-2)+1 launches")
     bcs = tuning.get("bicg_candidates")
     bc = bcs[tuning["bicg_chosen"] - 1] if bcs else {"lanes": 0}
+    c16 = bool(bc.get("col16"))
     if bc["lanes"]:
         spmm = (f"k_bicg_spmm_rows<Mixed,{D},{D}> (tentative BiCGStab: {D}-RHS product A x + dots; "
                 f"{bc['lanes']} lanes per row, {bc['rows']} rows in flight, registers for {bc['min_blocks']} "
-                f"blocks per SM)")
+                f"blocks per SM{', 16-bit column offsets' if c16 else ''})")
     else:
         spmm = f"k_bicg_spmm<Mixed,{D},{D}> (tentative BiCGStab: {D}-RHS product A x + dots, row tiles)"
-    out["bicg_spmm"] = (spmm, 8 * Z + 4 * (N + 1) + 12 * D * N, f"8 Z + 4 N + 12 D N")
+    zb = 6 if c16 else 8
+    out["bicg_spmm"] = (spmm, zb * Z + 4 * (N + 1) + 12 * D * N, f"{zb} Z + 4 N + 12 D N")
     out["bicg_vec"] = ("k_bicg_dir / k_bicg_s / k_bicg_xr (BiCGStab vector updates + dots)",
                        (64 + 52 + 96) * N * D / 3 / 3, "(64 + 52 + 96) N / 3 per launch (D = 3)")
     out["assemble"] = ("k_ubar + k_cell_beta + k_assemble (convection assembly + Algorithm 2, once per step)",
@@ -406,7 +409,7 @@ def run_ours(args, rank, world):
     pairs16 = any(c["col16"] and c["us"] > 0 for c in tun_e["candidates"])
     # the layout a measured traffic figure belongs to (every shape of one layout
     # reads the same arrays once per launch)
-    shape = {"bicg_spmm": "@rows" if bc["lanes"] else "@tile",
+    shape = {"bicg_spmm": ("@rows16" if bc.get("col16") else "@rows") if bc["lanes"] else "@tile",
              "pcg_spmv": "@pairs" if pc_chosen["col16"] == 2 else "@sell",
              "amg_fine": "@pairs" if pairs16 else "@sell"}
     for f, (kernel, nbytes, per) in fams.items():

@@ -188,13 +188,16 @@ typedef struct oasis_tuning {
      * bicg_rows, the entries of a tile read coalesced and summed per row through
      * shared memory); lanes = G > 0 is the row-split form, G lanes per row and
      * bicg_rows rows in flight per lane group, its registers capped for
-     * bicg_min_blocks resident blocks per SM (1: no cap). */
+     * bicg_min_blocks resident blocks per SM (1: no cap); bicg_col16 = 1: the
+     * columns are read as 16-bit offsets from the row, modulo n (only where every
+     * neighbour of the mesh's ordering fits; not timed, us = 0, elsewhere). */
     int32_t bicg_n_variants;
     int32_t bicg_chosen;                   /* 1-based */
     int32_t bicg_lanes[8];
     int32_t bicg_rows[8];
     int32_t bicg_min_blocks[8];
     double bicg_us[8];                     /* median time of the two products; 0 if not timed */
+    int32_t bicg_col16[8];
 } oasis_tuning;
 
 /* Per-step solver statistics. */

@@ -61,7 +61,8 @@ class oasis_tuning(C.Structure):
                 ("min_blocks", C.c_int32 * 16), ("prefetch", C.c_int32 * 16), ("col16", C.c_int32 * 16),
                 ("streamed", C.c_int32 * 16), ("warps_per_block", C.c_int32 * 16), ("us", C.c_double * 16),
                 ("bicg_n_variants", C.c_int32), ("bicg_chosen", C.c_int32), ("bicg_lanes", C.c_int32 * 8),
-                ("bicg_rows", C.c_int32 * 8), ("bicg_min_blocks", C.c_int32 * 8), ("bicg_us", C.c_double * 8)]
+                ("bicg_rows", C.c_int32 * 8), ("bicg_min_blocks", C.c_int32 * 8), ("bicg_us", C.c_double * 8),
+                ("bicg_col16", C.c_int32 * 8)]
 
     def as_dict(self):
         n = self.n_variants
@@ -73,7 +74,8 @@ class oasis_tuning(C.Structure):
                                for k in range(n)],
                 "bicg_chosen": self.bicg_chosen,
                 "bicg_candidates": [{"lanes": self.bicg_lanes[k], "rows": self.bicg_rows[k],
-                                     "min_blocks": self.bicg_min_blocks[k], "us": self.bicg_us[k]}
+                                     "min_blocks": self.bicg_min_blocks[k], "col16": self.bicg_col16[k],
+                                     "us": self.bicg_us[k]}
                                     for k in range(self.bicg_n_variants)]}
 
 

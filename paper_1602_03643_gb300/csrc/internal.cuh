@@ -125,6 +125,7 @@ struct Mesh {
     // periodic wrap-around neighbours stay short): j = row + d, then + n if
     // negative, - n if >= n.  Built only when every offset fits (empty else).
     DBuf<int16_t> sell_dcol;
+    DBuf<int16_t> csr_dcol;                    // the same offsets in CSR order (built with sell_dcol)
     DBuf<float> K32s;
     DBuf<double> K64s;
     DBuf<float2> Kffs;

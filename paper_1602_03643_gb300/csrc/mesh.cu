@@ -214,7 +214,13 @@ Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const in
                     }
                 }
             }
-            if (fits) m->sell_dcol.upload(dcol.data(), dcol.size(), s);
+            if (fits) {
+                m->sell_dcol.upload(dcol.data(), dcol.size(), s);
+                std::vector<int16_t> ccol((size_t)m->nnz);
+                for (int64_t q = 0; q < m->nnz; ++q) ccol[q] = dcol[sof[q]];
+                m->csr_dcol.upload(ccol.data(), ccol.size(), s);
+                OASIS_CUDA(cudaStreamSynchronize(s));
+            }
         }
         m->n_sell = nsell;
         m->sell_ptr.upload(sptr.data(), sptr.size(), s);

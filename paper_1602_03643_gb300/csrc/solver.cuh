@@ -84,6 +84,7 @@ struct StepData {
     int64_t n_slices;
     const int32_t *sell_ptr, *sell_len, *sell_col;
     const int16_t* sell_dcol;         // modular 16-bit column offsets, or null
+    const int16_t* csr_dcol;          // the same offsets in CSR order, or null
     // the finest multigrid level's pair-packed copy of K (float32 values two per
     // word, offsets two per word, word offset of each slice x 2), or null
     const float2* kpair;

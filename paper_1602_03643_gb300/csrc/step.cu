@@ -626,9 +626,10 @@ __global__ void __launch_bounds__(kBlock) k_bicg_spmm(StepData<P> a, int k0, Ctl
 // U rows in flight (row pointers, then per round one entry of each unfinished
 // row: value and column, then the NR gathered values), with no shared-memory
 // staging; the lanes' sums meet in a fixed shuffle tree.  MINB: resident blocks
-// per SM the registers are capped for (1 = no cap).  Grid: one resident wave,
-// rows walked grid-stride.
-template <class P, int D, int NR, int MODE, int G, int U, int MINB>
+// per SM the registers are capped for (1 = no cap).  C16: columns read as the
+// pattern's modular 16-bit offsets from the row (csr_dcol), 6 bytes per entry
+// instead of 8.  Grid: one resident wave, rows walked grid-stride.
+template <class P, int D, int NR, int MODE, int G, int U, int MINB, bool C16>
 __global__ void __launch_bounds__(kBlock, MINB) k_bicg_spmm_rows(StepData<P> a, int k0, Ctl ctl) {
     using V = typename P::V;
     int act[NR];
@@ -639,6 +640,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_bicg_spmm_rows(StepData<P> a, 
     V* __restrict__ y = MODE == 0 ? a.v : a.t;
     const int32_t* __restrict__ rp = a.rp;
     const int32_t* __restrict__ col = a.col;
+    const int16_t* __restrict__ dcol = a.csr_dcol;
     const V* __restrict__ A = a.A;
     const int lane = threadIdx.x & 31, lg = lane & (G - 1), grp = lane / G;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -670,7 +672,16 @@ __global__ void __launch_bounds__(kBlock, MINB) k_bicg_spmm_rows(StepData<P> a, 
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const bool has = q[u] < e[u];
-                j[u] = has ? (uint32_t)col[q[u]] * D + k0 : (uint32_t)k0;
+                uint32_t jc;
+                if constexpr (C16) {
+                    // row + offset, wrapped once into [0, n)
+                    int32_t jj = (int32_t)i[u] + (int32_t)(has ? dcol[q[u]] : (int16_t)0);
+                    jj = jj < 0 ? jj + (int32_t)n32 : jj;
+                    jc = (uint32_t)jj >= n32 ? (uint32_t)jj - n32 : (uint32_t)jj;
+                } else {
+                    jc = has ? (uint32_t)col[q[u]] : 0u;
+                }
+                j[u] = has ? jc * D + k0 : (uint32_t)k0;
                 av[u] = has ? A[q[u]] : V(0);
             }
             V g[U][NR];
@@ -724,23 +735,27 @@ __global__ void __launch_bounds__(kBlock, MINB) k_bicg_spmm_rows(StepData<P> a, 
 // caller may force one with bicg_variant).
 // A row-split shape also runs the sweeps' outer residual in row-split form
 // (same lanes per row, two rows in flight), the row-tile shape in tile form.
+// Shapes with c16 = 1 read the columns as 16-bit offsets (meshes whose ordering
+// keeps every neighbour within 2^15 of its row, modulo n); the tuner skips them
+// elsewhere.
 template <class P, int D>
 struct BicgVariant {
     void (*fn0)(StepData<P>, int, Ctl);
     void (*fn1)(StepData<P>, int, Ctl);
     void (*outer)(StepData<P>, int, Ctl);   // row-split outer residual (null: tile form)
-    int lanes, rows, minb;
+    int lanes, rows, minb, c16;
 };
-constexpr int kBicgVariants = 7;
+constexpr int kBicgVariants = 8;
 template <class P, int D>
 static const BicgVariant<P, D>* bicg_variant_table() {
-#define OASIS_BICGV(G, U, B)                                                                                  \
-    {k_bicg_spmm_rows<P, D, D, 0, G, U, B>, k_bicg_spmm_rows<P, D, D, 1, G, U, B>, k_bicg_outer_rows<P, D, D, G, 2>, \
-     G, U, B}
+#define OASIS_BICGV(G, U, B, C)                                                                              \
+    {k_bicg_spmm_rows<P, D, D, 0, G, U, B, C>, k_bicg_spmm_rows<P, D, D, 1, G, U, B, C>,                    \
+     k_bicg_outer_rows<P, D, D, G, 2>, G, U, B, C}
     static const BicgVariant<P, D> t[kBicgVariants] = {
-        {k_bicg_spmm<P, D, D, 0, kTileN>, k_bicg_spmm<P, D, D, 1, kTileN>, nullptr, 0, kTileN, 1},
-        OASIS_BICGV(4, 4, 1), OASIS_BICGV(4, 4, 5), OASIS_BICGV(4, 2, 1), OASIS_BICGV(8, 2, 1),
-        OASIS_BICGV(2, 4, 1), OASIS_BICGV(2, 4, 5)};
+        {k_bicg_spmm<P, D, D, 0, kTileN>, k_bicg_spmm<P, D, D, 1, kTileN>, nullptr, 0, kTileN, 1, 0},
+        OASIS_BICGV(4, 4, 1, false), OASIS_BICGV(4, 4, 5, false), OASIS_BICGV(2, 4, 1, false),
+        OASIS_BICGV(2, 4, 5, false), OASIS_BICGV(4, 4, 1, true), OASIS_BICGV(4, 4, 5, true),
+        OASIS_BICGV(2, 4, 1, true)};
 #undef OASIS_BICGV
     return t;
 }
@@ -2415,6 +2430,7 @@ struct StepImplT final : StepImpl {
         a.sell_len = m.sell_len.p;
         a.sell_col = m.sell_col.p;
         a.sell_dcol = m.sell_dcol.p;
+        a.csr_dcol = m.csr_dcol.p;
         a.Ks = mat<V>(m.K64s, m.K32s);
         if constexpr (P::mixed) {
             if (Sv.prm.pressure_pc == OASIS_PC_AMG && m.amg && m.amg->fine.kp) {
@@ -2911,6 +2927,9 @@ struct StepImplT final : StepImpl {
     void tune_bicg(cudaStream_t s, int forced) {
         const BicgVariant<P, D>* t = bicg_variant_table<P, D>();
         OASIS_CHECK(forced >= 0 && forced <= kBicgVariants, OASIS_EINVAL, "bicg_variant: no such candidate");
+        const bool have16 = a.csr_dcol != nullptr;
+        OASIS_CHECK(forced < 1 || have16 || !t[forced - 1].c16, OASIS_EINVAL,
+                    "bicg_variant: 16-bit column offsets do not fit this mesh's ordering");
         const int64_t rows = Sv.m->n;
         auto wave = [&](void (*fn)(StepData<P>, int, Ctl), int lanes, int in_flight) {
             int per_sm = 0;
@@ -2952,6 +2971,7 @@ struct StepImplT final : StepImpl {
         float ts[kBicgVariants][kTimed] = {};
         for (int r = 0; r < kWarm + kTimed; ++r)
             for (int v = 0; v < kBicgVariants; ++v) {
+                if (t[v].c16 && !have16) continue;
                 bicg_v = v;
                 // each product from a fresh scratch state: with zeroed values the first
                 // product's dots are zero, and its breakdown branch would otherwise mark
@@ -2969,6 +2989,7 @@ struct StepImplT final : StepImpl {
             }
         int best = 0;
         for (int v = 0; v < kBicgVariants; ++v) {
+            if (t[v].c16 && !have16) continue;      // not timed: bicg_us stays 0
             std::sort(ts[v], ts[v] + kTimed);
             bicg_us[v] = 1e3 * (double)ts[v][kTimed / 2];
             if (bicg_us[v] < bicg_us[best]) best = v;
@@ -3038,6 +3059,7 @@ struct StepImplT final : StepImpl {
             out->bicg_lanes[v] = bt[v].lanes;
             out->bicg_rows[v] = bt[v].rows;
             out->bicg_min_blocks[v] = bt[v].minb;
+            out->bicg_col16[v] = bt[v].c16;
             out->bicg_us[v] = bicg_us[v];
         }
         if (Sv.prm.pressure_pc == OASIS_PC_AMG) {

@@ -95,3 +95,8 @@ def test_family_bytes_model_on_a_small_mesh():
     # a packed restriction that keeps 32-bit columns: 6 bytes per entry
     fw = bench.family_bytes(pb, Z, None, tuning, dict(amg, packed=[6 | 16, 1]))
     assert abs((fw["amg_transfer"][1] - fp["amg_transfer"][1]) * 4 - 2 * 300) < 1e-9
+    # a BiCGStab product shape with 16-bit column offsets: 6 bytes per entry
+    t16 = dict(tuning, bicg_chosen=2, bicg_candidates=[{"lanes": 0, "col16": 0},
+                                                       {"lanes": 2, "rows": 4, "min_blocks": 1, "col16": 1}])
+    f16 = bench.family_bytes(pb, Z, None, t16, amg)
+    assert f16["bicg_spmm"][1] == 6 * Z + 4 * (N + 1) + 36 * N

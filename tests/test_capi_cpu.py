@@ -42,7 +42,7 @@ def test_header_constants_match_binding(capi):
     assert len(shared) >= 8
     for k in shared:
         assert getattr(capi, k) == int(defs[k]), k
-    assert ctypes.sizeof(capi.oasis_tuning) == 4 * 2 + 6 * 4 * 16 + 8 * 16 + 4 * 2 + 3 * 4 * 8 + 8 * 8
+    assert ctypes.sizeof(capi.oasis_tuning) == 4 * 2 + 6 * 4 * 16 + 8 * 16 + 4 * 2 + 3 * 4 * 8 + 8 * 8 + 4 * 8
     assert ctypes.sizeof(capi.oasis_amg_info) == 8 + 2 * 8 * 16 + 8 + 8 * 16 + 4 * 16
     # C layouts written out by hand: 5 doubles + f[3], 3 int32 (+4 padding), a
     # double, 9 int32 (+4 padding); stats: 8 int32, 7 doubles, res_m[3], it_m, it_c, res_c

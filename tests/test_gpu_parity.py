@@ -207,7 +207,7 @@ def test_fp64_100_steps_tg2d_32():
     assert relerr(p, s.p) <= 1e-9
 
 
-@pytest.mark.parametrize("bicg_variant", [1, 2])
+@pytest.mark.parametrize("bicg_variant", [1, 2, 7])
 def test_graph_equals_eager_bitwise(bicg_variant):
     """Same bits from the graph and the eager step, for a row-tile and a
     row-split BiCGStab product (each solver would otherwise tune its own)."""
@@ -219,6 +219,32 @@ def test_graph_equals_eager_bitwise(bicg_variant):
         run.step(4)
         out.append(run.fields())
         run.close()
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("pb_name", ["tg3d_8", "stress_9_rcm", "channel_6x5x6"])
+def test_bicg_product_16bit_columns_bitwise(pb_name):
+    """The BiCGStab product shape reading its columns as 16-bit offsets from the
+    row (modulo n: periodic neighbours wrap) gives the same bits as the same
+    shape reading int32 columns: the decoded columns are the same and the
+    products are added in the same order (small meshes: the same grid)."""
+    from paper_1602_03643_gb300.driver import IPCSRun
+    make = {"tg3d_8": lambda: WP.taylor_green_3d(8),
+            "stress_9_rcm": lambda: WP.stress_cube(9, ordering="rcm"),
+            "channel_6x5x6": lambda: WP.channel(nx=6, ny=5, nz=6)}[pb_name]
+    out = []
+    for v in (3, 7):                          # (4 lanes, 4 rows, 5 blocks/SM): int32, 16-bit columns
+        run = IPCSRun(make(), rtol_u=1e-10, rtol_p=1e-10, use_graph=1, precision=1, bicg_variant=v)
+        try:
+            tun = capi().oasis_get_tuning(run.solver)
+            cand = tun["bicg_candidates"][v - 1]
+            assert (cand["lanes"], cand["rows"], cand["min_blocks"], cand["col16"]) == (4, 4, 5, int(v == 7))
+            st = run.step(3)
+            assert st.status == 0
+            out.append(run.fields())
+        finally:
+            run.close()
     for a, b in zip(*out):
         np.testing.assert_array_equal(a, b)
 
