@@ -266,7 +266,9 @@ static Solver* create_solver(Mesh* m, const oasis_params* prm, int64_t n_dir, co
     S->gy.alloc((size_t)n);
     OASIS_CUDA(cudaMemsetAsync(S->feat.p, 0, S->feat.bytes(), s));
     OASIS_CUDA(cudaMemsetAsync(S->gy.p, 0, S->gy.bytes(), s));
-    S->stage.alloc(std::max<int64_t>(n, n_dir) * D);
+    // host transfers stage through here: the fields u, p, phi side by side, or the
+    // Dirichlet values
+    S->stage.alloc(std::max<int64_t>(n * (D + 2), n_dir * D));
     S->st.alloc(Solver::kStates);
     OASIS_CUDA(cudaMemsetAsync(S->st.p, 0, S->st.bytes(), s));
     // per-block partial sums: up to 8 values of 16 bytes per block, for grids of
@@ -671,15 +673,20 @@ int oasis_get_fields(oasis_solver* solver, double* u, double* p, double* phi, in
         double* outs[3] = {u, p, phi};
         const int ids[3] = {ST_U1, ST_PSTAR, ST_PHI};
         const int comps[3] = {D, 1, 1};
+        const int64_t at[3] = {0, (int64_t)D * n, (int64_t)(D + 1) * n};   // places in the stage
+        // every field converted first, then the copies to the host, then one
+        // synchronisation (a copy overlaps the next field's conversion)
+        bool any = false;
         for (int q = 0; q < 3; ++q) {
             if (!outs[q]) continue;
-            double* dst = on_device ? outs[q] : S->stage.p;
+            double* dst = on_device ? outs[q] : S->stage.p + at[q];
             S->impl->from_state(s, dst, ids[q], n, comps[q], S->m->perm.p);
-            if (!on_device) {
-                OASIS_CUDA(cudaMemcpyAsync(outs[q], S->stage.p, n * comps[q] * sizeof(double), cudaMemcpyDeviceToHost, s));
-                OASIS_CUDA(cudaStreamSynchronize(s));
-            }
+            if (!on_device)
+                OASIS_CUDA(cudaMemcpyAsync(outs[q], S->stage.p + at[q], n * comps[q] * sizeof(double),
+                                           cudaMemcpyDeviceToHost, s));
+            any = true;
         }
+        if (any && !on_device) OASIS_CUDA(cudaStreamSynchronize(s));
     });
 }
 
