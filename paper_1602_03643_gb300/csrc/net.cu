@@ -198,10 +198,15 @@ __global__ void __launch_bounds__(kBlock) k_net_l1(NetArgs a) {
 }
 
 // ------------------------------------------------------------------ inference
-// Inference does not store h1: layer 1 only forms each row's record
-// (x_i, mean_{N(i)} x, 0, 0) (32 bytes), and layer 2 recomputes h1_j of every
-// neighbour from its record (6 inputs, 32 channels), which moves 32 bytes per
-// neighbour instead of h1's 128.  Layer 2's dense product then runs on the
+// Two forms of inference (kInferStoredH1 picks one).  Stored (in use): layer 1
+// writes h1 of every row ([n][32] float32, k_net_l1, as training does) and
+// layer 2 gathers each neighbour's h1.  Records: layer 1 only forms each row's
+// record (x_i, mean_{N(i)} x, 0, 0) (32 bytes, k_net_rec), and layer 2
+// recomputes h1_j of every neighbour from its record (6 inputs, 32 channels),
+// which moves 32 bytes per neighbour instead of h1's 128 but costs more
+// arithmetic and shuffles than it saves (723 against 594 us per forward at
+// 128^3 for records against stored h1 with its layer 1).  Layer 2's dense
+// product then runs on the
 // 5th-generation tensor cores: per tile of 128 rows, A = [h1_i | mean h1]
 // (128 x 64), B = [W2a | W2b] (32 x 64, the bfloat16 weights), D = A B^T
 // (128 x 32, float32 in tensor memory) by tcgen05.mma kind::f16 with M = 128,
