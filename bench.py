@@ -79,7 +79,8 @@ _S112 = "profiles/dram_traffic_products_stress112_rcm.md (stress112_rcm capture,
 MEASURED_TRAFFIC = {("stress128_rcm", "pcg_spmv@sell"): (215.0e6, _S112),
                     ("stress128_rcm", "pcg_spmv@pairs"): (229.8e6, _S112),
                     ("stress128_rcm", "amg_fine@pairs"): (163.3e6, _S112),
-                    ("stress128_rcm", "bicg_spmm@rows"): (332.4e6, _S112)}
+                    ("stress128_rcm", "bicg_spmm@rows"): (332.4e6, _S112),
+                    ("stress128_rcm", "bicg_spmm@rows16"): (263.6e6, _S112)}
 
 
 def family_bytes(pb, nnz, args, tuning, amg):
@@ -286,7 +287,8 @@ def run_ours(args, rank, world):
                        pressure_pc=pc if pressure_pc is None else pressure_pc, inner_iters=args.inner_iters,
                        convection=1 if args.convection == "abe" else 0,
                        velocity_update=capi.OASIS_UPDATE_CONSISTENT if args.velocity_update == "consistent"
-                       else capi.OASIS_UPDATE_LUMPED, stream=stream)
+                       else capi.OASIS_UPDATE_LUMPED, stream=stream,
+                       bicg_variant=args.bicg_variant if batch else 0)
 
     def timed_steps(run, k):
         evs = []
@@ -764,6 +766,9 @@ def main():
                     help="passive scalars transported with the flow (Sec. 3 scalar equation)")
     ap.add_argument("--inner-iters", type=int, default=1,
                     help="inner velocity/pressure iterations per step (Algorithm 1)")
+    ap.add_argument("--bicg-variant", type=int, default=0,
+                    help="shape of the batched BiCGStab product: 0 = autotuned at solver creation, k >= 1 = "
+                         "candidate k of the tuning report (bicg_variant of the solver parameters)")
     ap.add_argument("--pc", default="amg", choices=["amg", "jacobi"],
                     help="pressure-CG preconditioner (multigrid V-cycle or Jacobi)")
     ap.add_argument("--train-steps", type=int, default=14)
