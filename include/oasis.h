@@ -245,7 +245,9 @@ const char* oasis_last_error(void);
  * Builds the shared CSR sparsity pattern of all matrices (Sec. 5: "computed on
  * the first assemble"; the assembled system's dof numbering is free, Sec. 5) and
  * the dof-to-cell incidence used by the assembly kernels; copies everything to
- * the current device.
+ * the current device.  The cells are stored in the order of their lowest
+ * internal dof (ties in the given order), so the given cell order matters only
+ * through the order of floating-point sums.
  * Errors: OASIS_EINVAL (sizes, out-of-range index, perm not a permutation),
  * OASIS_EMESH (a cell whose dofs repeat, or more than 255 pattern entries in one
  * row), OASIS_ENOMEM. */

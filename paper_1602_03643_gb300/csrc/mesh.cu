@@ -76,6 +76,32 @@ Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const in
                             "cell " + std::to_string(c) + " has a repeated dof");
     }
     const int64_t n = n_dofs;
+    // cells stored in the order of their lowest (internal) dof, ties in the given
+    // order (a counting sort): under a renumbering such as RCM, the cells a tile of
+    // consecutive rows touches then sit close together, so the assembly's gathers
+    // of their cell terms, and the cell pass's gathers of dof values, stay local.
+    // Results depend on it only through the order of sums.
+    std::vector<int32_t> cells_in((size_t)nc * d1);
+    {
+        std::vector<int64_t> start(n + 1, 0);
+        std::vector<int32_t> low(nc);
+        for (int64_t c = 0; c < nc; ++c) {
+            int32_t lo = cdof[c * d1];
+            for (int a = 1; a < d1; ++a) lo = std::min(lo, cdof[c * d1 + a]);
+            low[c] = lo;
+            start[lo + 1]++;
+        }
+        for (int64_t i = 0; i < n; ++i) start[i + 1] += start[i];
+        std::vector<int32_t> cdof_in(cdof.size());
+        for (int64_t c = 0; c < nc; ++c) {
+            const int64_t o = start[low[c]]++;
+            for (int a = 0; a < d1; ++a) {
+                cdof_in[o * d1 + a] = cdof[c * d1 + a];
+                cells_in[o * d1 + a] = cells[c * d1 + a];
+            }
+        }
+        cdof.swap(cdof_in);
+    }
     // dof -> cell incidence (counting sort keeps cells in increasing order)
     std::vector<int32_t> inc_ptr(n + 1, 0), inc_cell((size_t)nc * d1);
     for (size_t q = 0; q < cdof.size(); ++q) inc_ptr[cdof[q] + 1]++;
@@ -149,7 +175,7 @@ Mesh* build_mesh(int dim, int64_t nv, const double* coords, int64_t nc, const in
         m->col.upload(col_pad.data(), col_pad.size(), s);
     }
     m->diag.upload(diag.data(), diag.size(), s);
-    m->cell_vert.upload(cells, (size_t)nc * d1, s);
+    m->cell_vert.upload(cells_in.data(), cells_in.size(), s);
     m->cell_dof.upload(cdof.data(), cdof.size(), s);
     m->coords.upload(coords, (size_t)nv * dim, s);
     m->inc_ptr.upload(inc_ptr.data(), inc_ptr.size(), s);
